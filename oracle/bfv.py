@@ -1,0 +1,386 @@
+"""Oracle BFV: key generation, encryption, decryption and the homomorphic
+operations, each written as its mathematical definition.
+
+TEST INFRASTRUCTURE ONLY (CPU oracle for the parity tests).
+
+The paper fixes the scheme (BFV, Sec. 3.1: E, D, the operators (+) and (x)
+with D(E(x1) (+) E(x2)) = x1 + x2 and D(E(x1) (x) E(x2)) = x1 * x2, plus the
+row/column rotations) but not SEAL's internals.  The readings used here:
+
+* Keys and ciphertexts live in coefficient form, reduced mod each prime of
+  the ciphertext basis Q = q_0 ... q_{L-1}; key-switching keys additionally
+  mod the special prime P = q_L when K = 1.
+* Public key: p1 = a, p0 = [-(a s + e)]_Q.
+* Encryption of m in [0, t)^n:  c = ([Delta m + p0 u + e1]_Q, [p1 u + e2]_Q),
+  Delta = floor(Q / t).
+* Decryption: x = [c0 + c1 s]_Q in [0, Q), m = round(t x / Q) mod t.
+* Plaintext / scalar multiplicands are lifted to the centered range
+  [-(t-1)/2, (t-1)/2] before reduction mod q_j.
+* ct (x) ct: centered lifts of both ciphertexts to Z, the negacyclic tensor
+  product over Z, then [round(t d_k / Q)]_Q for each of the three parts.
+* Key switching of a polynomial d from s' to s: digits d_i = [d]_{q_i} in
+  [0, q_i) (one per ciphertext prime); key row i is
+  b_i = -a_i s + e_i + (i == j) [P]_{q_i} s'  (mod q_j), b_i = -a_i s + e_i
+  (mod P); u = sum_i d_i (b_i, a_i) over Q*P; result (x - x~) P^-1 mod Q
+  with x~ the centered residue of x mod P.  With K = 0 there is no P and no
+  division.
+* Rotation by k (0 < k < n/2) is the Galois automorphism x -> x^g with
+  g = 3^(n/2 - k) mod 2n followed by a key switch from tau_g(s) to s; it
+  shifts each row of the 2 x n/2 slot matrix right by k (Sec. 3.1).  The row
+  swap uses g = 2n - 1.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from functools import lru_cache
+from math import prod
+
+import numpy as np
+
+from . import ring, sampling
+from .ring import Basis
+from .sampling import (TAG_ENC_E1, TAG_ENC_E2, TAG_ENC_U, TAG_KSK_A, TAG_KSK_E,
+                       TAG_PK_A, TAG_PK_E, TAG_SECRET)
+
+
+@dataclass
+class Params:
+    n: int
+    q: list            # L + K primes, special prime last when K == 1
+    L: int
+    K: int
+    t: list            # plaintext CRT moduli
+
+    def __post_init__(self):
+        self.q = [int(x) for x in self.q]
+        self.t = [int(x) for x in self.t]
+        assert len(self.q) == self.L + self.K and self.K in (0, 1)
+
+    @property
+    def Q(self) -> int:
+        return prod(self.q[:self.L])
+
+    @property
+    def P(self) -> int:
+        return self.q[self.L] if self.K else 1
+
+    @property
+    def qbasis(self) -> Basis:
+        return Basis(self.q[:self.L])
+
+
+def galois_for_rotation(n: int, k: int) -> int:
+    """Galois element of the right shift by k within each row (0 < k < n/2)."""
+    assert 0 < k < n // 2
+    return pow(3, n // 2 - k, 2 * n)
+
+
+def galois_row_swap(n: int) -> int:
+    return 2 * n - 1
+
+
+# ------------------------------------------------------------------- helpers
+
+def _reduce_int_poly(vals, primes) -> np.ndarray:
+    return np.array([[int(v) % p for v in vals] for p in primes], dtype=np.uint64)
+
+
+def _mul_rns(a: np.ndarray, b: np.ndarray, primes) -> np.ndarray:
+    return np.stack([ring.poly_mul(a[j], b[j], p) for j, p in enumerate(primes)])
+
+
+def _add_rns(a, b, primes):
+    return np.stack([ring.vec_add(a[j], b[j], p) for j, p in enumerate(primes)])
+
+
+def _sub_rns(a, b, primes):
+    return np.stack([ring.vec_sub(a[j], b[j], p) for j, p in enumerate(primes)])
+
+
+def _neg_rns(a, primes):
+    return np.stack([ring.vec_neg(a[j], p) for j, p in enumerate(primes)])
+
+
+def _auto_rns(a, g, primes):
+    return np.stack([ring.automorphism(a[j], g, p) for j, p in enumerate(primes)])
+
+
+def centered(x: int, m: int) -> int:
+    """Representative of x mod m in [-(m-1)/2, (m-1)/2] (m odd)."""
+    x %= m
+    return x - m if x > m // 2 else x
+
+
+# ---------------------------------------------------------------------- keys
+
+@dataclass
+class SecretKey:
+    s: list                    # ternary integer coefficients
+
+
+@dataclass
+class PublicKey:
+    p0: np.ndarray             # (L, n)
+    p1: np.ndarray
+
+
+@dataclass
+class KeySwitchKey:
+    b: np.ndarray              # (L digits, L+K primes, n)
+    a: np.ndarray
+
+
+@dataclass
+class Keys:
+    params: Params
+    sk: SecretKey
+    pk: PublicKey
+    relin: KeySwitchKey | None = None
+    galois: dict = field(default_factory=dict)    # g -> KeySwitchKey
+
+
+def gen_secret(params: Params, seed: int) -> SecretKey:
+    return SecretKey(sampling.sample_ternary(seed, TAG_SECRET, 0, 0, params.n))
+
+
+def gen_public(params: Params, sk: SecretKey, seed: int) -> PublicKey:
+    n, qs = params.n, params.q[:params.L]
+    e = sampling.sample_gaussian(seed, TAG_PK_E, 0, 0, n)
+    s = _reduce_int_poly(sk.s, qs)
+    er = _reduce_int_poly(e, qs)
+    a = np.stack([sampling.sample_uniform(seed, TAG_PK_A, j, 0, q, n) for j, q in enumerate(qs)])
+    p0 = _neg_rns(_add_rns(_mul_rns(a, s, qs), er, qs), qs)
+    return PublicKey(p0, a)
+
+
+def gen_switch_key(params: Params, sk: SecretKey, s_from: np.ndarray, key_id: int, seed: int) -> KeySwitchKey:
+    """Key that switches a polynomial multiplying s_from (given mod every prime
+    of Q*P, shape (L+K, n)) to one multiplying s.  key_id selects the stream
+    (0 = relinearisation, else the Galois element)."""
+    n, L, K = params.n, params.L, params.K
+    primes = params.q
+    s = _reduce_int_poly(sk.s, primes)
+    P = params.P
+    b = np.zeros((L, L + K, n), dtype=np.uint64)
+    a = np.zeros((L, L + K, n), dtype=np.uint64)
+    for i in range(L):
+        e = sampling.sample_gaussian(seed, TAG_KSK_E, key_id, i, n)
+        for j, pj in enumerate(primes):
+            aij = sampling.sample_uniform(seed, TAG_KSK_A, key_id, i * 256 + j, pj, n)
+            v = ring.vec_neg(ring.poly_mul(aij, s[j], pj), pj)
+            v = ring.vec_add(v, ring.reduce_signed(e, pj), pj)
+            if i == j:
+                v = ring.vec_add(v, ring.vec_scalar_mul(s_from[j], P % pj, pj), pj)
+            b[i, j] = v
+            a[i, j] = aij
+    return KeySwitchKey(b, a)
+
+
+def keygen(params: Params, seed: int, rotations=(), relin=True, row_swap=False) -> Keys:
+    sk = gen_secret(params, seed)
+    pk = gen_public(params, sk, seed)
+    keys = Keys(params, sk, pk)
+    primes = params.q
+    s_all = _reduce_int_poly(sk.s, primes)
+    if relin:
+        s2 = _mul_rns(s_all, s_all, primes)
+        keys.relin = gen_switch_key(params, sk, s2, 0, seed)
+    gs = [galois_for_rotation(params.n, k) for k in rotations]
+    if row_swap:
+        gs.append(galois_row_swap(params.n))
+    for g in gs:
+        if g not in keys.galois:
+            keys.galois[g] = gen_switch_key(params, sk, _auto_rns(s_all, g, primes), g, seed)
+    return keys
+
+
+# ---------------------------------------------------------------- ciphertext
+
+@dataclass
+class Ciphertext:
+    c: list          # 2 (or 3 before relinearisation) arrays of shape (L, n)
+    t: int           # plaintext modulus this ciphertext encrypts under
+
+    def copy(self):
+        return Ciphertext([x.copy() for x in self.c], self.t)
+
+
+def delta(params: Params, t: int) -> int:
+    return params.Q // t
+
+
+def encrypt(params: Params, pk: PublicKey, m: np.ndarray, t: int, seed: int, ct_id: int) -> Ciphertext:
+    """m: plaintext polynomial coefficients in [0, t)."""
+    n, qs = params.n, params.q[:params.L]
+    u = _reduce_int_poly(sampling.sample_ternary(seed, TAG_ENC_U, ct_id, 0, n), qs)
+    e1 = _reduce_int_poly(sampling.sample_gaussian(seed, TAG_ENC_E1, ct_id, 0, n), qs)
+    e2 = _reduce_int_poly(sampling.sample_gaussian(seed, TAG_ENC_E2, ct_id, 0, n), qs)
+    D = delta(params, t)
+    dm = np.stack([ring.vec_scalar_mul(ring.reduce_signed(m, q), D % q, q) for q in qs])
+    c0 = _add_rns(_add_rns(dm, _mul_rns(pk.p0, u, qs), qs), e1, qs)
+    c1 = _add_rns(_mul_rns(pk.p1, u, qs), e2, qs)
+    return Ciphertext([c0, c1], t)
+
+
+def _phase(params: Params, sk: SecretKey, ct: Ciphertext) -> list:
+    """[c0 + c1 s (+ c2 s^2)]_Q as ints in [0, Q)."""
+    qs = params.q[:params.L]
+    s = _reduce_int_poly(sk.s, qs)
+    acc = ct.c[0]
+    spow = s
+    for k in range(1, len(ct.c)):
+        acc = _add_rns(acc, _mul_rns(ct.c[k], spow, qs), qs)
+        spow = _mul_rns(spow, s, qs)
+    return params.qbasis.lift(acc)
+
+
+def decrypt(params: Params, sk: SecretKey, ct: Ciphertext) -> np.ndarray:
+    """m = round(t x / Q) mod t; no ties since Q is odd and coprime to t."""
+    Q, t = params.Q, ct.t
+    xs = _phase(params, sk, ct)
+    return np.array([((2 * t * x + Q) // (2 * Q)) % t for x in xs], dtype=np.uint64)
+
+
+def noise_margin_bits(params: Params, sk: SecretKey, ct: Ciphertext, m_expected) -> float:
+    """log2(Q/2) - log2(max |t x - Q m|), with t x - Q m taken centered mod tQ.
+
+    Decryption returns m_expected exactly when the margin is positive."""
+    Q, t = params.Q, ct.t
+    xs = _phase(params, sk, ct)
+    worst = 0
+    for x, m in zip(xs, m_expected):
+        w = centered(t * x - Q * int(m), t * Q)
+        worst = max(worst, abs(w))
+    if worst == 0:
+        return float("inf")
+    return math.log2(Q) - 1.0 - math.log2(worst)
+
+
+def add(params: Params, a: Ciphertext, b: Ciphertext) -> Ciphertext:
+    qs = params.q[:params.L]
+    assert a.t == b.t and len(a.c) == len(b.c)
+    return Ciphertext([_add_rns(x, y, qs) for x, y in zip(a.c, b.c)], a.t)
+
+
+def sub(params: Params, a: Ciphertext, b: Ciphertext) -> Ciphertext:
+    qs = params.q[:params.L]
+    return Ciphertext([_sub_rns(x, y, qs) for x, y in zip(a.c, b.c)], a.t)
+
+
+def mul_plain(params: Params, ct: Ciphertext, m: np.ndarray) -> Ciphertext:
+    """ct times the plaintext polynomial m (coefficients in [0, t)), centered lift."""
+    qs = params.q[:params.L]
+    t = ct.t
+    p = _reduce_int_poly([centered(int(v), t) for v in m], qs)
+    return Ciphertext([_mul_rns(x, p, qs) for x in ct.c], t)
+
+
+def mul_scalar(params: Params, ct: Ciphertext, w: int) -> Ciphertext:
+    """ct times the constant polynomial w (any integer; centered lift mod t)."""
+    qs = params.q[:params.L]
+    wc = centered(int(w), ct.t)
+    return Ciphertext([np.stack([ring.vec_scalar_mul(x[j], wc % q, q) for j, q in enumerate(qs)])
+                       for x in ct.c], ct.t)
+
+
+def key_switch(params: Params, d: np.ndarray, ksk: KeySwitchKey):
+    """Switch d (shape (L, n), mod Q) from s' to s; returns (u0, u1) mod Q."""
+    L, K, primes = params.L, params.K, params.q
+    digits = [d[i] for i in range(L)]          # [d]_{q_i} in [0, q_i)
+    u = []
+    for comp in (ksk.b, ksk.a):
+        acc = []
+        for j, pj in enumerate(primes):
+            s = np.zeros(params.n, dtype=np.uint64)
+            for i in range(L):
+                di = ring.u64(digits[i] % np.uint64(pj))
+                s = ring.vec_add(s, ring.poly_mul(di, comp[i, j], pj), pj)
+            acc.append(s)
+        u.append(np.stack(acc))
+    if K == 0:
+        return u[0], u[1]
+    P = params.P
+    out = []
+    for x in u:
+        xt = [centered(int(v), P) for v in x[L]]
+        res = []
+        for j in range(L):
+            qj = primes[j]
+            pinv = pow(P, -1, qj)
+            res.append(np.array([((int(x[j][c]) - xt[c]) * pinv) % qj for c in range(params.n)],
+                                dtype=np.uint64))
+        out.append(np.stack(res))
+    return out[0], out[1]
+
+
+def apply_galois(params: Params, ct: Ciphertext, g: int, ksk: KeySwitchKey) -> Ciphertext:
+    qs = params.q[:params.L]
+    c0 = _auto_rns(ct.c[0], g, qs)
+    c1 = _auto_rns(ct.c[1], g, qs)
+    u0, u1 = key_switch(params, c1, ksk)
+    return Ciphertext([_add_rns(c0, u0, qs), u1], ct.t)
+
+
+def rotate(params: Params, keys: Keys, ct: Ciphertext, k: int) -> Ciphertext:
+    g = galois_for_rotation(params.n, k)
+    return apply_galois(params, ct, g, keys.galois[g])
+
+
+def rotate_rows(params: Params, keys: Keys, ct: Ciphertext) -> Ciphertext:
+    g = galois_row_swap(params.n)
+    return apply_galois(params, ct, g, keys.galois[g])
+
+
+@lru_cache(maxsize=None)
+def _aux_primes(n: int, bits_needed: int) -> list:
+    """The oracle's own auxiliary primes (= 1 mod 2n, descending below 2^61)
+    whose product exceeds 2^bits_needed; used only to compute products over Z."""
+    out, x = [], ((1 << 61) - 1) // (2 * n) * (2 * n) + 1
+    while sum(p.bit_length() - 1 for p in out) < bits_needed:
+        if x < (1 << 61) and ring.is_prime(x):
+            out.append(x)
+        x -= 2 * n
+    return tuple(out)
+
+
+def poly_mul_over_Z(a: list, b: list, n: int, bound_bits: int) -> list:
+    """Exact negacyclic product of two integer polynomials whose product
+    coefficients are below 2^bound_bits in magnitude: computed mod enough
+    primes and lifted back by CRT (centered)."""
+    aux = _aux_primes(n, bound_bits + 2)
+    basis = Basis(aux)
+    ar = _reduce_int_poly(a, aux)
+    br = _reduce_int_poly(b, aux)
+    return basis.lift_centered(_mul_rns(ar, br, aux))
+
+
+def multiply(params: Params, x: Ciphertext, y: Ciphertext) -> Ciphertext:
+    """ct (x) ct without relinearisation: three parts, each
+    [round(t * d_k / Q)]_Q of the tensor product over Z of centered lifts."""
+    assert x.t == y.t
+    n, Q, t = params.n, params.Q, x.t
+    qb = params.qbasis
+    a0, a1 = qb.lift_centered(x.c[0]), qb.lift_centered(x.c[1])
+    b0, b1 = qb.lift_centered(y.c[0]), qb.lift_centered(y.c[1])
+    bound = 2 * (Q.bit_length()) + n.bit_length() + 1
+    d0 = poly_mul_over_Z(a0, b0, n, bound)
+    d1a = poly_mul_over_Z(a0, b1, n, bound)
+    d1b = poly_mul_over_Z(a1, b0, n, bound)
+    d2 = poly_mul_over_Z(a1, b1, n, bound)
+    d1 = [u + v for u, v in zip(d1a, d1b)]
+    qs = params.q[:params.L]
+    # round(t d / Q) = floor((2 t d + Q) / (2 Q)); never a tie (Q odd, gcd(Q, t) = 1)
+    parts = [[(2 * t * v + Q) // (2 * Q) for v in d] for d in (d0, d1, d2)]
+    return Ciphertext([_reduce_int_poly(p, qs) for p in parts], t)
+
+
+def relinearize(params: Params, keys: Keys, ct: Ciphertext) -> Ciphertext:
+    qs = params.q[:params.L]
+    assert len(ct.c) == 3
+    u0, u1 = key_switch(params, ct.c[2], keys.relin)
+    return Ciphertext([_add_rns(ct.c[0], u0, qs), _add_rns(ct.c[1], u1, qs)], ct.t)
+
+
+def square(params: Params, keys: Keys, ct: Ciphertext) -> Ciphertext:
+    return relinearize(params, keys, multiply(params, ct, ct))

@@ -1,0 +1,329 @@
+"""Oracle LoLa layers: the paper's message representations and matrix-vector
+algorithms, run either on oracle BFV ciphertexts or on plain slot vectors.
+
+TEST INFRASTRUCTURE ONLY (CPU oracle for the parity tests).
+
+One plan, two evaluators: ``HEEval`` runs every step with the oracle's BFV
+(``oracle.bfv``); ``SlotEval`` runs the same steps on plain Z_t slot vectors
+with the rotation semantics of Sec. 3.1 (the slot simulator).  The integer
+network (``int_network``) evaluates the same layers over Z with no
+encryption at all.  Every rotation, add and multiply below is in the order
+the paper's algorithms state it; the readings where the paper is silent are
+listed in each function.
+
+Layer list entries (dicts):
+  {"op": "conv", "weights": W[maps][r]}                 Sec. 4.2.2 convolution vector - row major
+  {"op": "combine", "stride": s}                        Sec. 4.3 / App. C: combine messages
+  {"op": "square"}                                      Sec. 3.2 square activation
+  {"op": "stack", "d": d, "copies": c}                  Sec. 4.2.1 stacked representation
+  {"op": "stacked_rowmajor", "weights": W, "d": d, "copies": c}
+                                                        Sec. 4.2.2 stacked vector - row major
+  {"op": "interleaved_rowmajor", "weights": W}          Sec. 4.2.2 interleaved vector - row major
+  {"op": "dense_rowmajor", "weights": W}                Sec. 4.2.2 dense vector - row major
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import bfv, encoding
+
+
+# ----------------------------------------------------------------- evaluators
+
+class SlotEval:
+    """Plain slot vectors mod t with the paper's rotation semantics."""
+
+    def __init__(self, n: int, t: int):
+        self.n, self.t = n, t
+
+    def add(self, a, b):
+        return (a + b) % self.t
+
+    def rot(self, a, k):
+        """Right shift by k within each row of the 2 x n/2 slot matrix (Sec. 3.1)."""
+        h = self.n // 2
+        return np.concatenate([np.roll(a[:h], k), np.roll(a[h:], k)])
+
+    def rot_rows(self, a):
+        h = self.n // 2
+        return np.concatenate([a[h:], a[:h]])
+
+    def mul_plain(self, a, slots):
+        return (a * (np.asarray(slots, dtype=np.int64) % self.t)) % self.t
+
+    def mul_scalar(self, a, w):
+        return (a * (int(w) % self.t)) % self.t
+
+    def square(self, a):
+        return (a * a) % self.t
+
+
+class HEEval:
+    """The same steps on oracle ciphertexts."""
+
+    def __init__(self, params: bfv.Params, keys: bfv.Keys, t: int):
+        self.p, self.keys, self.t = params, keys, t
+        self.n = params.n
+        self.counts = {"rot": 0, "mul_plain": 0, "mul_scalar": 0, "square": 0, "add": 0}
+
+    def add(self, a, b):
+        self.counts["add"] += 1
+        return bfv.add(self.p, a, b)
+
+    def rot(self, a, k):
+        self.counts["rot"] += 1
+        return bfv.rotate(self.p, self.keys, a, k)
+
+    def rot_rows(self, a):
+        self.counts["rot"] += 1
+        return bfv.rotate_rows(self.p, self.keys, a)
+
+    def mul_plain(self, a, slots):
+        self.counts["mul_plain"] += 1
+        return bfv.mul_plain(self.p, a, encoding.encode(slots, self.t))
+
+    def mul_scalar(self, a, w):
+        self.counts["mul_scalar"] += 1
+        return bfv.mul_scalar(self.p, a, w)
+
+    def square(self, a):
+        self.counts["square"] += 1
+        return bfv.square(self.p, self.keys, a)
+
+
+# ------------------------------------------------------------------ the plan
+
+@dataclass
+class State:
+    msgs: list          # messages (ciphertexts or slot vectors)
+    pos: list           # element i -> (message index, slot)
+    block: int = 0      # stacked block size (0 if not stacked)
+    copies: int = 0
+
+
+def rotate_and_sum(ev, x, shifts):
+    """x <- x + rot(x, s) for s in shifts, in order (Sec. 4.1 and its footnote)."""
+    for s in shifts:
+        x = ev.add(x, ev.rot(x, s))
+    return x
+
+
+def layer_conv(ev, st: State, W) -> State:
+    """Convolution vector - row major (Sec. 4.2.2): map m = sum_j W[m][j] * M^j,
+    scalar weights (sparse representation of w).  Output: one dense message
+    per map; element (m, w) sits at slot w of message m."""
+    R = len(st.msgs)
+    out = []
+    for m in range(len(W)):
+        acc = ev.mul_scalar(st.msgs[0], W[m][0])
+        for j in range(1, R):
+            acc = ev.add(acc, ev.mul_scalar(st.msgs[j], W[m][j]))
+        out.append(acc)
+    width = len(st.pos)
+    pos = [(m, w) for m in range(len(W)) for w in range(width)]
+    return State(out, pos)
+
+
+def layer_combine(ev, st: State, stride: int) -> State:
+    """Combine k messages into one (Sec. 4.3, App. C): message m is rotated
+    right by m * stride so active slots do not collide, then all are added."""
+    h = ev.n // 2
+    acc = st.msgs[0]
+    for m in range(1, len(st.msgs)):
+        acc = ev.add(acc, ev.rot(st.msgs[m], m * stride))
+    pos = []
+    for (m, slot) in st.pos:
+        assert slot + m * stride < h, "combine must not wrap a row"
+        pos.append((0, slot + m * stride))
+    return State([acc], pos)
+
+
+def layer_square(ev, st: State) -> State:
+    return State([ev.square(x) for x in st.msgs], st.pos, st.block, st.copies)
+
+
+def layer_stack(ev, st: State, d: int, copies: int) -> State:
+    """Stacked representation (Sec. 4.2.1): copies of the vector every 2^d
+    slots.  Built by x <- x + rot(x, s) for s = 2^d, 2^(d+1), ... within a
+    row, then x <- x + rot_rows(x) when the copies fill both rows."""
+    n, h, s = ev.n, ev.n // 2, 1 << d
+    assert len(st.msgs) == 1 and all(m == 0 and slot < s for m, slot in st.pos)
+    assert copies & (copies - 1) == 0 and copies * s <= n
+    per_row = min(copies, h // s)
+    x = st.msgs[0]
+    shift = s
+    while shift < per_row * s:
+        x = ev.add(x, ev.rot(x, shift))
+        shift *= 2
+    if copies > per_row:
+        x = ev.add(x, ev.rot_rows(x))
+    return State([x], st.pos, s, copies)
+
+
+def stacked_output_slot(n: int, s: int, b: int, r: int) -> int:
+    h = n // 2
+    base = b * s + s - 1
+    row, col = divmod(base, h)
+    return row * h + (col + r) % h
+
+
+def layer_stacked_rowmajor(ev, st: State, W, d: int, copies: int) -> State:
+    """Stacked vector - row major (Sec. 4.2.2 and its footnote).
+
+    Round r multiplies the stacked vector by rows r*c .. r*c+c-1 of W
+    concatenated (block b holds row r*c+b), then sums each block with right
+    rotations 1, 2, ..., 2^(d-1); row r*c+b ends at the last slot of block b.
+    With more than one round, each round's result is multiplied by a 0/1
+    mask of its valid block ends (rotate-and-sum leaves partial sums in the
+    other slots), rotated right by r and added (App. C: message i shifted by
+    i-1 positions)."""
+    n, s = ev.n, 1 << d
+    assert st.block == s and st.copies == copies
+    rows, k = len(W), len(W[0])
+    assert k == len(st.pos)
+    R = -(-rows // copies)
+    assert R <= s
+    x = st.msgs[0]
+    outs = []
+    for r in range(R):
+        P = [0] * n
+        for b in range(copies):
+            row = r * copies + b
+            if row >= rows:
+                continue
+            for i, (_, slot) in enumerate(st.pos):
+                P[b * s + slot] = int(W[row][i])
+        y = ev.mul_plain(x, P)
+        y = rotate_and_sum(ev, y, [1 << j for j in range(d)])
+        outs.append(y)
+    if R == 1:
+        pos = [(0, stacked_output_slot(n, s, b, 0)) for b in range(rows)]
+        return State([outs[0]], pos)
+    acc = None
+    for r, y in enumerate(outs):
+        mask = [0] * n
+        for b in range(copies):
+            if r * copies + b < rows:
+                mask[b * s + s - 1] = 1
+        z = ev.mul_plain(y, mask)
+        if r > 0:
+            z = ev.rot(z, r)
+        acc = z if acc is None else ev.add(acc, z)
+    pos = [(0, stacked_output_slot(n, s, o % copies, o // copies)) for o in range(rows)]
+    return State([acc], pos)
+
+
+def layer_interleaved_rowmajor(ev, st: State, W) -> State:
+    """Interleaved vector - row major (Sec. 4.2.2): the dense row-major dot
+    product with the columns of W placed at the vector's slots.  Each output
+    sums all n slots: right rotations 1, 2, ..., n/4 within the rows, then
+    the row swap; every slot then holds the result (sparse representation)."""
+    n = ev.n
+    assert len(st.msgs) == 1 and len(W[0]) == len(st.pos)
+    shifts = [1 << j for j in range((n // 2).bit_length() - 1)]
+    outs = []
+    for o in range(len(W)):
+        V = [0] * n
+        for i, (_, slot) in enumerate(st.pos):
+            V[slot] = int(W[o][i])
+        y = ev.mul_plain(st.msgs[0], V)
+        y = rotate_and_sum(ev, y, shifts)
+        y = ev.add(y, ev.rot_rows(y))
+        outs.append(y)
+    return State(outs, [(o, 0) for o in range(len(W))])
+
+
+def run_network(ev, layers, st: State) -> State:
+    for L in layers:
+        op = L["op"]
+        if op == "conv":
+            st = layer_conv(ev, st, L["weights"])
+        elif op == "combine":
+            st = layer_combine(ev, st, L["stride"])
+        elif op == "square":
+            st = layer_square(ev, st)
+        elif op == "stack":
+            st = layer_stack(ev, st, L["d"], L["copies"])
+        elif op == "stacked_rowmajor":
+            st = layer_stacked_rowmajor(ev, st, L["weights"], L["d"], L["copies"])
+        elif op in ("interleaved_rowmajor", "dense_rowmajor"):
+            st = layer_interleaved_rowmajor(ev, st, L["weights"])
+        else:
+            raise ValueError(op)
+    return st
+
+
+# ---------------------------------------------------------- input packing
+
+def conv_windows(h: int, w: int, kh: int, kw: int, stride: int):
+    """Window upper-left corners, row-major.  Reading of Sec. 4.3 (845 = 5*13*13
+    on a 28x28 image): pad bottom/right with zeros so that
+    ceil((h - kh) / stride) + 1 windows fit per axis."""
+    oh = -(-(h - kh) // stride) + 1
+    ow = -(-(w - kw) // stride) + 1
+    return oh, ow
+
+
+def pack_convolution(img, kh: int, kw: int, stride: int, n: int):
+    """Convolution representation (Sec. 4.2.1 and its footnote): message
+    r = dr*kw + dc (window offset, row-major) holds, at slot i*ow + j, the
+    pixel at (stride*i + dr, stride*j + dc) (zero in the padding)."""
+    img = np.asarray(img)
+    h, w = img.shape
+    oh, ow = conv_windows(h, w, kh, kw, stride)
+    msgs = []
+    for dr in range(kh):
+        for dc in range(kw):
+            v = [0] * n
+            for i in range(oh):
+                for j in range(ow):
+                    r, c = stride * i + dr, stride * j + dc
+                    v[i * ow + j] = int(img[r, c]) if (r < h and c < w) else 0
+            msgs.append(v)
+    return msgs, [(0, i) for i in range(oh * ow)]
+
+
+def pack_dense(vec, n: int):
+    v = [0] * n
+    for i, x in enumerate(vec):
+        v[i] = int(x)
+    return v, [(0, i) for i in range(len(vec))]
+
+
+def pack_stacked(vec, d: int, copies: int, n: int):
+    s = 1 << d
+    v = [0] * n
+    for b in range(copies):
+        for i, x in enumerate(vec):
+            v[b * s + i] = int(x)
+    return v, [(0, i) for i in range(len(vec))]
+
+
+# ------------------------------------------------------- integer network
+
+def int_conv(img, W, kh: int, kw: int, stride: int):
+    img = np.asarray(img)
+    h, w = img.shape
+    oh, ow = conv_windows(h, w, kh, kw, stride)
+    out = []
+    for m in range(len(W)):
+        for i in range(oh):
+            for j in range(ow):
+                acc = 0
+                for dr in range(kh):
+                    for dc in range(kw):
+                        r, c = stride * i + dr, stride * j + dc
+                        if r < h and c < w:
+                            acc += int(W[m][dr * kw + dc]) * int(img[r, c])
+                out.append(acc)
+    return out
+
+
+def int_dense(x, W):
+    return [sum(int(W[o][i]) * int(x[i]) for i in range(len(x))) for o in range(len(W))]
+
+
+def int_square(x):
+    return [int(v) * int(v) for v in x]

@@ -1,0 +1,234 @@
+"""Pins for the oracle's BFV scheme and batch encoding (CPU only).
+
+Pinned against: the homomorphic identities the paper states (Sec. 3.1:
+D(E(x1) (+) E(x2)) = x1 + x2, D(E(x1) (x) E(x2)) = x1 x2), the slot-matrix
+rotation semantics (Sec. 3.1), brute-force evaluation of the encoded
+polynomial, and a brute-force tensor product over Z with exact rational
+rounding on tiny rings.
+"""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import bfv, encoding, ring
+
+
+def mkparams(n, L=3, K=1, t=65537):
+    ps = W.params_small(n, L=L, K=K, t=[t])
+    return bfv.Params(ps.n, ps.q, ps.L, ps.K, ps.t)
+
+
+def row_shift(v, k):
+    h = len(v) // 2
+    return np.concatenate([np.roll(v[:h], k), np.roll(v[h:], k)])
+
+
+# ------------------------------------------------------------------ encoding
+
+@pytest.mark.parametrize("n,t", [(8, 65537), (32, 65537), (64, W.T30[0])])
+def test_decode_is_evaluation_at_slot_points(n, t):
+    m = np.random.default_rng(n).integers(0, t, n, dtype=np.uint64)
+    slots = encoding.decode(m, t)
+    exps = encoding.slot_exponents(n)
+    for j in range(n):
+        assert int(slots[j]) == encoding.evaluate(m, t, exps[j])
+    # slot points are the n distinct primitive 2n-th roots psi^(odd)
+    assert sorted(exps) == list(range(1, 2 * n, 2))
+
+
+@pytest.mark.parametrize("n,t", [(16, 65537), (4096, 65537), (16384, W.T30[2])])
+def test_encode_decode_round_trip_and_multiplicativity(n, t):
+    g = np.random.default_rng(n)
+    a = g.integers(0, t, n)
+    b = g.integers(0, t, n)
+    ma, mb = encoding.encode(a, t), encoding.encode(b, t)
+    assert np.array_equal(encoding.decode(ma, t), a)
+    if n <= 4096:
+        prod = ring.poly_mul(ma, mb, t)
+        assert np.array_equal(encoding.decode(prod, t), (a * b) % t)
+
+
+def test_constant_polynomial_is_all_equal_slots():
+    # Sec. 4.2.1 footnote: a vector with the same value in every coordinate
+    # is the constant polynomial.
+    n, t = 32, 65537
+    m = encoding.encode([7] * n, t)
+    assert int(m[0]) == 7 and not m[1:].any()
+
+
+@pytest.mark.parametrize("k", [1, 2, 5, 15])
+def test_galois_element_rotates_rows_right(k):
+    # Sec. 3.1: rotating the columns of the 2 x n/2 matrix by one to the right
+    # sends m_1 ... m_{n/2} to m_{n/2}, m_1, ..., m_{n/2-1}.
+    n, t = 32, 65537
+    v = np.arange(n) + 100
+    m = encoding.encode(v, t)
+    g = bfv.galois_for_rotation(n, k)
+    out = encoding.decode(ring.automorphism(m, g, t), t)
+    assert np.array_equal(out, row_shift(v, k))
+    out = encoding.decode(ring.automorphism(m, bfv.galois_row_swap(n), t), t)
+    assert np.array_equal(out, np.concatenate([v[n // 2:], v[:n // 2]]))
+
+
+# ----------------------------------------------------------------- BFV scheme
+
+@pytest.fixture(scope="module")
+def small():
+    P = mkparams(32)
+    keys = bfv.keygen(P, 3, rotations=[1, 2, 4, 7], relin=True, row_swap=True)
+    return P, keys
+
+
+def enc(P, keys, v, seed=1, ct_id=0):
+    t = P.t[0]
+    return bfv.encrypt(P, keys.pk, encoding.encode(v, t), t, seed, ct_id)
+
+
+def dec(P, keys, ct):
+    return encoding.decode(bfv.decrypt(P, keys.sk, ct), ct.t)
+
+
+def test_encrypt_decrypt(small):
+    P, keys = small
+    v = np.random.default_rng(0).integers(0, 65537, P.n)
+    assert np.array_equal(dec(P, keys, enc(P, keys, v)), v)
+
+
+def test_homomorphic_add_and_mul(small):
+    P, keys = small
+    g = np.random.default_rng(1)
+    a, b = g.integers(0, 65537, P.n), g.integers(0, 65537, P.n)
+    ca, cb = enc(P, keys, a, 1, 0), enc(P, keys, b, 1, 1)
+    assert np.array_equal(dec(P, keys, bfv.add(P, ca, cb)), (a + b) % 65537)
+    assert np.array_equal(dec(P, keys, bfv.sub(P, ca, cb)), (a - b) % 65537)
+    prod3 = bfv.multiply(P, ca, cb)
+    assert len(prod3.c) == 3
+    assert np.array_equal(dec(P, keys, prod3), (a * b) % 65537)
+    rel = bfv.relinearize(P, keys, prod3)
+    assert len(rel.c) == 2
+    assert np.array_equal(dec(P, keys, rel), (a * b) % 65537)
+    assert np.array_equal(dec(P, keys, bfv.square(P, keys, ca)), (a * a) % 65537)
+
+
+def test_mul_plain_and_scalar(small):
+    P, keys = small
+    g = np.random.default_rng(2)
+    a = g.integers(0, 16, P.n)
+    w = g.integers(-3, 4, P.n)
+    ca = enc(P, keys, a)
+    assert np.array_equal(dec(P, keys, bfv.mul_plain(P, ca, encoding.encode(w, 65537))), (a * w) % 65537)
+    assert np.array_equal(dec(P, keys, bfv.mul_scalar(P, ca, -3)), (-3 * a) % 65537)
+
+
+@pytest.mark.parametrize("k", [1, 2, 4, 7])
+def test_rotation_semantics(small, k):
+    P, keys = small
+    v = np.random.default_rng(k).integers(0, 65537, P.n)
+    assert np.array_equal(dec(P, keys, bfv.rotate(P, keys, enc(P, keys, v), k)), row_shift(v, k))
+
+
+def test_row_swap(small):
+    P, keys = small
+    v = np.random.default_rng(9).integers(0, 65537, P.n)
+    h = P.n // 2
+    assert np.array_equal(dec(P, keys, bfv.rotate_rows(P, keys, enc(P, keys, v))),
+                          np.concatenate([v[h:], v[:h]]))
+
+
+def test_keys_do_not_depend_on_t():
+    # BFV keys involve only s and Q*P; the same keys serve every t_i.
+    P1, P2 = mkparams(32, t=65537), mkparams(32, t=W.T30[0])
+    k1, k2 = bfv.keygen(P1, 5, rotations=[1]), bfv.keygen(P2, 5, rotations=[1])
+    assert np.array_equal(k1.pk.p0, k2.pk.p0)
+    g = bfv.galois_for_rotation(32, 1)
+    assert np.array_equal(k1.galois[g].b, k2.galois[g].b)
+
+
+def test_key_switch_k0(small):
+    P = mkparams(32, L=3, K=0)
+    keys = bfv.keygen(P, 4, rotations=[3], relin=True)
+    v = np.random.default_rng(4).integers(0, 65537, P.n)
+    c = enc(P, keys, v)
+    assert np.array_equal(dec(P, keys, bfv.rotate(P, keys, c, 3)), row_shift(v, 3))
+    assert np.array_equal(dec(P, keys, bfv.square(P, keys, c)), (v * v) % 65537)
+
+
+def test_moddown_is_exact_division():
+    # (x - x~) / P is an integer for every x mod QP, and equals round(x/P)
+    # up to the choice of representative: check on random bignums.
+    P = mkparams(16)
+    Pm, Q = P.P, P.Q
+    g = np.random.default_rng(5)
+    for _ in range(200):
+        x = int(g.integers(0, 2**62)) * int(g.integers(0, 2**62)) * int(g.integers(1, 2**62)) % (Q * Pm)
+        xt = bfv.centered(x, Pm)
+        assert (x - xt) % Pm == 0
+        y = (x - xt) // Pm
+        assert abs(Fraction(x, Pm) - y) <= Fraction(1, 2)
+
+
+def test_multiply_matches_bruteforce_tensor():
+    # Tiny ring: compute the tensor product over Z by a double loop on Python
+    # integers and round t*d/Q with exact fractions; the oracle's multiply
+    # (CRT-based product over Z) must agree coefficient by coefficient.
+    P = mkparams(8, L=2, K=1)
+    keys = bfv.keygen(P, 6, rotations=[], relin=False)
+    g = np.random.default_rng(6)
+    ca = enc(P, keys, g.integers(0, 65537, 8), 2, 0)
+    cb = enc(P, keys, g.integers(0, 65537, 8), 2, 1)
+    out = bfv.multiply(P, ca, cb)
+    Q, t, n = P.Q, 65537, 8
+    lift = lambda c: [bfv.centered(v, Q) for v in P.qbasis.lift(c)]
+    a0, a1, b0, b1 = lift(ca.c[0]), lift(ca.c[1]), lift(cb.c[0]), lift(cb.c[1])
+
+    def negacyclic(x, y):
+        r = [0] * n
+        for i in range(n):
+            for j in range(n):
+                if i + j < n:
+                    r[i + j] += x[i] * y[j]
+                else:
+                    r[i + j - n] -= x[i] * y[j]
+        return r
+
+    d0 = negacyclic(a0, b0)
+    d1 = [u + v for u, v in zip(negacyclic(a0, b1), negacyclic(a1, b0))]
+    d2 = negacyclic(a1, b1)
+    for k, d in enumerate((d0, d1, d2)):
+        want = []
+        for v in d:
+            f = Fraction(t * v, Q)
+            r = f.numerator // f.denominator
+            if f - r > Fraction(1, 2):
+                r += 1
+            assert f - r != Fraction(1, 2)     # never a tie
+            want.append(r)
+        got = P.qbasis.lift(out.c[k])
+        assert got == [w % Q for w in want]
+
+
+def test_noise_margin_positive_and_shrinks(small):
+    P, keys = small
+    v = np.random.default_rng(7).integers(0, 16, P.n)
+    c = enc(P, keys, v)
+    m = encoding.encode(v, 65537)
+    fresh = bfv.noise_margin_bits(P, keys.sk, c, m)
+    sq = bfv.square(P, keys, c)
+    after = bfv.noise_margin_bits(P, keys.sk, sq, encoding.encode(v * v, 65537))
+    assert fresh > after > 0
+
+
+def test_full_size_rotation_and_square():
+    """n = 16384, L = 5, K = 1: the MNIST-network parameters."""
+    ps = W.params_mnist()
+    P = bfv.Params(ps.n, ps.q, ps.L, ps.K, ps.t)
+    keys = bfv.keygen(P, 8, rotations=[1], relin=True)
+    t = ps.t[0]
+    v = np.random.default_rng(8).integers(0, 16, P.n)
+    c = bfv.encrypt(P, keys.pk, encoding.encode(v, t), t, 3, 0)
+    r = bfv.rotate(P, keys, c, 1)
+    assert np.array_equal(encoding.decode(bfv.decrypt(P, keys.sk, r), t), row_shift(v, 1))
+    s = bfv.square(P, keys, c)
+    assert np.array_equal(encoding.decode(bfv.decrypt(P, keys.sk, s), t), v * v)

@@ -1,0 +1,226 @@
+"""Pins for the oracle's LoLa layers (CPU only).
+
+* the paper's worked footnote examples (tests/golden/*.json);
+* the slot simulator against the integer network over Z (reduced mod t and,
+  for several t_i, recombined by CRT) at the full MNIST / head shapes;
+* operation counts stated in the paper (Table 1, App. C) and derived in the
+  plan;
+* encrypted runs of the oracle whose decryptions equal the integer network,
+  with the measured noise margin.
+"""
+import json
+import os
+from math import prod
+
+import numpy as np
+import pytest
+
+import workloads as W
+from conftest import GOLDEN
+from oracle import bfv, encoding, lola
+
+
+class Counting(lola.SlotEval):
+    def __init__(self, n, t):
+        super().__init__(n, t)
+        self.c = {"rot": 0, "mul_plain": 0, "mul_scalar": 0, "square": 0}
+
+    def rot(self, a, k):
+        self.c["rot"] += 1
+        return super().rot(a, k)
+
+    def rot_rows(self, a):
+        self.c["rot"] += 1
+        return super().rot_rows(a)
+
+    def mul_plain(self, a, s):
+        self.c["mul_plain"] += 1
+        return super().mul_plain(a, s)
+
+    def mul_scalar(self, a, w):
+        self.c["mul_scalar"] += 1
+        return super().mul_scalar(a, w)
+
+    def square(self, a):
+        self.c["square"] += 1
+        return super().square(a)
+
+
+def load(name):
+    return json.load(open(os.path.join(GOLDEN, name)))
+
+
+# ------------------------------------------------------------ golden examples
+
+def test_dot_product_footnote():
+    g = load("dot_product_footnote.json")
+    n, t = 8, 65537          # one row of the 2 x 4 slot matrix holds the 4-vector
+    ev = lola.SlotEval(n, t)
+    tags = [10 ** i for i in range(1, 5)]        # v_i w_i := 10^i, decodable sums
+    x = np.array(tags + [0] * 4, dtype=np.int64) % t
+    x1 = ev.add(x, ev.rot(x, 1))
+    x2 = ev.add(x1, ev.rot(x1, 2))
+
+    def decode(v):
+        return sorted(i for i in range(1, 5) if (v // 10 ** i) % 10)
+
+    assert [decode(int(v)) for v in x1[:4]] == [sorted(s) for s in g["after_rot1_add"]]
+    assert [decode(int(v)) for v in x2[:4]] == [sorted(s) for s in g["after_rot2_add"]]
+
+
+def test_stacked_2x2_footnote():
+    g = load("stacked_2x2_footnote.json")
+    n, t = 8, 65537
+    Wm = g["W"]
+    v = [5, 7]
+    ev = lola.SlotEval(n, t)
+    x, pos = lola.pack_stacked(v, 1, 2, n)
+    st = lola.State([np.array(x, dtype=np.int64)], pos, 2, 2)
+    out = lola.layer_stacked_rowmajor(ev, st, Wm, 1, 2)
+    for entry, terms in g["result_entries_1based"].items():
+        want = sum(Wm[r - 1][c - 1] * v[c - 1] for r, c in terms)
+        assert int(out.msgs[0][int(entry) - 1]) == want
+    assert [s for _, s in out.pos] == [int(e) - 1 for e in g["result_entries_1based"]]
+
+
+def test_conv_representation_footnote():
+    g = load("conv_representation_footnote.json")
+    h, w = g["image_shape"]
+    img = np.array([[10 * (r + 1) + (c + 1) for c in range(w)] for r in range(h)])   # a_{r,c} -> "rc"
+    msgs, pos = lola.pack_convolution(img, *g["kernel"], g["stride"], 16)
+    assert len(msgs) == len(g["messages_1based"]) and len(pos) == 4
+    for m, want in zip(msgs, g["messages_1based"]):
+        assert m[:4] == [10 * r + c for r, c in want]
+
+
+# ------------------------------------------------- plan vs integer network
+
+def mnist_slot_run(n, t, net, img, ev_cls=lola.SlotEval):
+    ev = ev_cls(n, t)
+    msgs, pos = lola.pack_convolution(img, net.kh, net.kw, net.stride, n)
+    st = lola.State([np.array(m, dtype=np.int64) % t for m in msgs], pos)
+    return ev, lola.run_network(ev, W.layers_mnist(net, n), st)
+
+
+def mnist_int(net, img):
+    x = lola.int_conv(img, net.conv_w, net.kh, net.kw, net.stride)
+    x = lola.int_square(x)
+    x = lola.int_dense(x, net.dense1_w)
+    x = lola.int_square(x)
+    return lola.int_dense(x, net.dense2_w)
+
+
+def crt(residues, moduli):
+    T = prod(moduli)
+    x = sum(r * (T // m) * pow(T // m, -1, m) for r, m in zip(residues, moduli)) % T
+    return x - T if x > T // 2 else x
+
+
+def test_mnist_plan_matches_integer_network_with_crt():
+    n = 16384
+    net = W.mnist_net()
+    img = W.image()
+    want = mnist_int(net, img)
+    # no-wrap bound: the largest possible |output| must fit in prod(t_i)/2
+    bound = 100 * 3 * (845 * 3 * (25 * 15 * 3) ** 2) ** 2
+    assert max(abs(v) for v in want) <= bound < prod(W.T30[:3]) // 2
+    per_t = []
+    for t in W.T30[:3]:
+        ev, st = mnist_slot_run(n, t, net, img, Counting)
+        assert ev.c == {"rot": 224, "mul_plain": 24, "mul_scalar": 125, "square": 2}
+        per_t.append([int(st.msgs[m][s]) for m, s in st.pos])
+        # the output is sparse: every slot of message o holds output o
+        assert all(len(set(int(v) for v in msg)) == 1 for msg in st.msgs)
+    got = [crt([r[o] for r in per_t], W.T30[:3]) for o in range(10)]
+    assert got == want
+
+
+def test_table1_operation_counts():
+    # Table 1 / Sec. 4.3: 5 maps combined with 4 rotations; App. C: at
+    # n = 16384 the 845-vector takes 16 stacked copies and 7 rounds.
+    n = 16384
+    L = W.layers_mnist(W.mnist_net(), n)
+    assert L[3]["copies"] == 16 and L[3]["d"] == 10
+    assert -(-100 // L[4]["copies"]) == 7
+    ev = Counting(n, 65537)
+    st = lola.State([np.zeros(n, np.int64) for _ in range(5)], [(m, w) for m in range(5) for w in range(169)])
+    lola.layer_combine(ev, st, 169)
+    assert ev.c["rot"] == 4
+    # Table 1's n = 8192 variant: 8 copies, 13 rounds
+    L8 = W.layers_mnist(W.mnist_net(), 8192)
+    assert L8[3]["copies"] == 8 and -(-100 // L8[4]["copies"]) == 13
+
+
+def test_head_plan_matches_integer_network():
+    n, t = 16384, W.T30[0]
+    Wh = W.head_weights()
+    x = W.feature_vector()
+    want = lola.int_dense(x, Wh)
+    assert max(abs(v) for v in want) < t // 2
+    ev = Counting(n, t)
+    v, pos = lola.pack_dense(x, n)
+    st = lola.run_network(ev, W.layers_head(Wh, n), lola.State([np.array(v, np.int64) % t], pos))
+    assert ev.c["rot"] == 2 + 26 * 12 + 25 and ev.c["mul_plain"] == 26 + 26
+    got = [int(st.msgs[m][s]) for m, s in st.pos]
+    assert [g - t if g > t // 2 else g for g in got] == want
+
+
+def test_dense64_plan_wraps_mod_t():
+    # the square of a 64-term dot product can exceed t = 65537: compare mod t
+    n, t = 4096, 65537
+    Wd, x = W.dense_weights(), W.dense_vector()
+    want = [v % t for v in lola.int_square(lola.int_dense(x, Wd))]
+    ev = Counting(n, t)
+    v, pos = lola.pack_stacked(x, 6, W.dense64_input_copies(Wd), n)
+    st = lola.run_network(ev, W.layers_dense64(Wd, n), lola.State([np.array(v, np.int64)], pos, 64, 16))
+    assert ev.c == {"rot": 6, "mul_plain": 1, "mul_scalar": 0, "square": 1}
+    assert [int(st.msgs[m][s]) for m, s in st.pos] == want
+
+
+# --------------------------------------------------------- encrypted runs
+
+def test_dense64_encrypted_oracle_run():
+    ps = W.params_dense64()
+    P = bfv.Params(ps.n, ps.q, ps.L, ps.K, ps.t)
+    keys = bfv.keygen(P, W.DEFAULT_SEED, rotations=[1, 2, 4, 8, 16, 32], relin=True)
+    t = 65537
+    Wd, x = W.dense_weights(), W.dense_vector()
+    v, pos = lola.pack_stacked(x, 6, 16, ps.n)
+    ct = bfv.encrypt(P, keys.pk, encoding.encode(v, t), t, 1, 0)
+    ev = lola.HEEval(P, keys, t)
+    st = lola.run_network(ev, W.layers_dense64(Wd, ps.n), lola.State([ct], pos, 64, 16))
+    slots = encoding.decode(bfv.decrypt(P, keys.sk, st.msgs[0]), t)
+    want = [v % t for v in lola.int_square(lola.int_dense(x, Wd))]
+    assert [int(slots[s]) for _, s in st.pos] == want
+    # the margin left after the square (recorded in the design notes)
+    sim = lola.run_network(lola.SlotEval(ps.n, t), W.layers_dense64(Wd, ps.n),
+                           lola.State([np.array(v, np.int64)], pos, 64, 16))
+    margin = bfv.noise_margin_bits(P, keys.sk, st.msgs[0], encoding.encode(sim.msgs[0], t))
+    assert margin > 8
+
+
+def mini_mnist():
+    # a reduced MNIST-shaped network: 12x12 image, 3x3 stride-2 conv, 2 maps,
+    # 12 hidden (two stacked rounds, so masks + combine run), 3 outputs
+    net = W.mnist_net(seed=7, maps=2, hidden=12, classes=3, h=12, w=12, k=3, stride=2)
+    return net, W.image(seed=7, h=12, w=12)
+
+
+def test_mini_mnist_encrypted_oracle_run():
+    n = 1024
+    ps = W.params_small(n, L=5, K=1, t=W.T30[:1])
+    P = bfv.Params(ps.n, ps.q, ps.L, ps.K, ps.t)
+    net, img = mini_mnist()
+    layers = W.layers_mnist(net, n)
+    assert layers[3]["copies"] == 8 and -(-12 // 8) == 2
+    steps = sorted({36, 128, 256, 1, 2, 4, 8, 16, 32, 64} | set(1 << j for j in range(9)))
+    keys = bfv.keygen(P, 11, rotations=steps, relin=True, row_swap=True)
+    t = ps.t[0]
+    msgs, pos = lola.pack_convolution(img, net.kh, net.kw, net.stride, n)
+    cts = [bfv.encrypt(P, keys.pk, encoding.encode(m, t), t, 5, i) for i, m in enumerate(msgs)]
+    ev = lola.HEEval(P, keys, t)
+    st = lola.run_network(ev, layers, lola.State(cts, pos))
+    got = [int(encoding.decode(bfv.decrypt(P, keys.sk, st.msgs[m]), t)[s]) for m, s in st.pos]
+    # one ~30-bit modulus: the outputs wrap, so compare mod t
+    assert got == [v % t for v in mnist_int(net, img)]
+    assert ev.counts["rot"] == 1 + 3 + 2 * 7 + 1 + 3 * 10

@@ -1,0 +1,199 @@
+"""Seeded synthetic workloads shared by the tests, the benchmark and the oracle.
+
+This module holds parameter tables (literal prime lists) and seeded input
+generators only: no part of the method's arithmetic.  It is the one module
+that both the CUDA path's callers and the CPU oracle import.
+
+The paper evaluates on MNIST, CIFAR-10 and CalTech-101 features with trained
+weights; none of those are available, so every input here is synthetic with
+the paper's shapes (Sec. 4.3 MNIST network, Sec. 5 transfer-learning head):
+pixel / feature values uniform in [0, 15] and weights uniform in [-3, 3],
+drawn from numpy's Philox generator seeded per purpose.
+
+Prime lists: NTT-friendly primes (= 1 mod 2n), listed in descending order
+below 2^60 (ciphertext primes), 2^36 (n = 4096 set) and 2^30 (plaintext
+CRT moduli).  Each side validates them with its own code.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+DEFAULT_SEED = 20181225
+
+# primes = 1 mod 2^15 below 2^60, descending
+Q60 = [
+    1152921504606748673, 1152921504606683137, 1152921504606584833,
+    1152921504605962241, 1152921504604979201, 1152921504600260609,
+    1152921504599080961, 1152921504598720513, 1152921504597114881,
+    1152921504597016577, 1152921504596525057, 1152921504595968001,
+]
+# primes = 1 mod 2^13 below 2^36, descending
+Q36 = [68719403009, 68719230977, 68719206401, 68719190017]
+# plaintext CRT moduli: primes = 1 mod 2^15 below 2^30, descending
+T30 = [1073643521, 1073479681, 1073184769, 1073053697]
+
+
+@dataclass
+class ParamSet:
+    name: str
+    n: int
+    q: list          # L + K primes, special prime last
+    L: int
+    K: int
+    t: list
+
+    def as_dict(self):
+        return dict(n=self.n, q=list(self.q), L=self.L, K=self.K, t=list(self.t))
+
+
+def params_dense64() -> ParamSet:
+    """Single encrypted dense layer: n = 4096, three ~36-bit primes, no
+    special prime, t = 65537."""
+    return ParamSet("dense64_n4096", 4096, Q36[:3], 3, 0, [65537])
+
+
+def params_mnist(L: int = 5) -> ParamSet:
+    """MNIST-shaped network and transfer-learning head: n = 16384, L
+    ciphertext primes of 60 bits plus one 60-bit special prime, three ~30-bit
+    plaintext CRT moduli."""
+    return ParamSet(f"mnist_n16384_L{L}", 16384, Q60[:L + 1], L, 1, T30[:3])
+
+
+def params_head(L: int = 5) -> ParamSet:
+    """Transfer-learning head: as params_mnist but one plaintext modulus."""
+    return ParamSet(f"head_n16384_L{L}", 16384, Q60[:L + 1], L, 1, T30[:1])
+
+
+def params_sweep(n: int, L: int) -> ParamSet:
+    """Batched primitive sweep: n in {8192, 16384}, L in 4..8 primes of 60
+    bits plus a special prime (security not considered: random residues)."""
+    return ParamSet(f"sweep_n{n}_L{L}", n, Q60[:L + 1], L, 1, T30[:1])
+
+
+def params_small(n: int, L: int = 3, K: int = 1, t=None) -> ParamSet:
+    """Reduced ring sizes for fast parity tests (same 60-bit primes)."""
+    return ParamSet(f"small_n{n}_L{L}_K{K}", n, Q60[:L + K], L, K, list(t or T30[:1]))
+
+
+def rng(seed: int, purpose: int) -> np.random.Generator:
+    return np.random.Generator(np.random.Philox(key=[seed & (2**64 - 1), purpose]))
+
+
+# purposes
+P_IMAGE, P_CONV_W, P_DENSE1_W, P_DENSE2_W, P_FEAT, P_HEAD_W, P_VEC, P_DENSE_W, \
+    P_RESIDUES, P_STEPS, P_ENC, P_KEY = range(1, 13)
+
+
+def image(seed=DEFAULT_SEED, idx: int = 0, h: int = 28, w: int = 28) -> np.ndarray:
+    return rng(seed + idx, P_IMAGE).integers(0, 16, size=(h, w), dtype=np.int64)
+
+
+def int_weights(seed, purpose, shape) -> np.ndarray:
+    return rng(seed, purpose).integers(-3, 4, size=shape, dtype=np.int64)
+
+
+@dataclass
+class MnistNet:
+    conv_w: np.ndarray = field(repr=False)     # (maps, kh*kw)
+    dense1_w: np.ndarray = field(repr=False)   # (hidden, maps*oh*ow)
+    dense2_w: np.ndarray = field(repr=False)   # (classes, hidden)
+    kh: int = 5
+    kw: int = 5
+    stride: int = 2
+    h: int = 28
+    w: int = 28
+
+
+def mnist_net(seed=DEFAULT_SEED, maps=5, hidden=100, classes=10, h=28, w=28, k=5, stride=2) -> MnistNet:
+    oh = -(-(h - k) // stride) + 1
+    ow = -(-(w - k) // stride) + 1
+    return MnistNet(int_weights(seed, P_CONV_W, (maps, k * k)),
+                    int_weights(seed, P_DENSE1_W, (hidden, maps * oh * ow)),
+                    int_weights(seed, P_DENSE2_W, (classes, hidden)), k, k, stride, h, w)
+
+
+def feature_vector(seed=DEFAULT_SEED, idx: int = 0, dim: int = 4096) -> np.ndarray:
+    return rng(seed + idx, P_FEAT).integers(0, 16, size=dim, dtype=np.int64)
+
+
+def head_weights(seed=DEFAULT_SEED, classes: int = 101, dim: int = 4096) -> np.ndarray:
+    return int_weights(seed, P_HEAD_W, (classes, dim))
+
+
+def dense_vector(seed=DEFAULT_SEED, dim: int = 64) -> np.ndarray:
+    return rng(seed, P_VEC).integers(0, 16, size=dim, dtype=np.int64)
+
+
+def dense_weights(seed=DEFAULT_SEED, rows: int = 10, dim: int = 64) -> np.ndarray:
+    return int_weights(seed, P_DENSE_W, (rows, dim))
+
+
+def random_residues(seed, shape_prefix, primes, n) -> np.ndarray:
+    """Uniform residues: array of shape shape_prefix + (len(primes), n), row j mod primes[j]."""
+    g = rng(seed, P_RESIDUES)
+    out = np.empty(tuple(shape_prefix) + (len(primes), n), dtype=np.uint64)
+    for j, p in enumerate(primes):
+        out[..., j, :] = g.integers(0, p, size=tuple(shape_prefix) + (n,), dtype=np.uint64)
+    return out
+
+
+def rotation_steps(seed, count: int, n: int) -> np.ndarray:
+    """Random rotation steps in [1, n/2)."""
+    return rng(seed, P_STEPS).integers(1, n // 2, size=count, dtype=np.int64)
+
+
+# ----------------------------------------------------------- layer lists
+# Network descriptions (weights + representation choices), consumed by both
+# the oracle's plan and the library's layer-list API.
+
+def _ceil_log2(k: int) -> int:
+    return max(0, (k - 1).bit_length())
+
+
+def layers_mnist(net: MnistNet, n: int) -> list:
+    """Sec. 4.3 / Table 1: conv (convolution representation) -> combine maps
+    -> square -> stack -> stacked row-major dense -> square -> interleaved
+    row-major dense."""
+    maps, hidden = net.conv_w.shape[0], net.dense1_w.shape[0]
+    oh = -(-(net.h - net.kh) // net.stride) + 1
+    ow = -(-(net.w - net.kw) // net.stride) + 1
+    k1 = maps * oh * ow
+    d = _ceil_log2(k1)
+    copies = n >> d
+    return [
+        {"op": "conv", "weights": net.conv_w},
+        {"op": "combine", "stride": oh * ow},
+        {"op": "square"},
+        {"op": "stack", "d": d, "copies": copies},
+        {"op": "stacked_rowmajor", "weights": net.dense1_w, "d": d, "copies": copies},
+        {"op": "square"},
+        {"op": "interleaved_rowmajor", "weights": net.dense2_w},
+    ]
+
+
+def layers_head(Wh: np.ndarray, n: int) -> list:
+    """Sec. 5 transfer-learning head as stacked row-major: dense input
+    stacked n / 2^d times, then rounds of stacked row-major products."""
+    d = _ceil_log2(Wh.shape[1])
+    copies = n >> d
+    return [
+        {"op": "stack", "d": d, "copies": copies},
+        {"op": "stacked_rowmajor", "weights": Wh, "d": d, "copies": copies},
+    ]
+
+
+def layers_dense64(Wd: np.ndarray, n: int) -> list:
+    """Single dense layer + square; the input arrives already stacked
+    (one copy per output row) so no server-side stacking rotations."""
+    d = _ceil_log2(Wd.shape[1])
+    copies = 1 << _ceil_log2(Wd.shape[0])
+    return [
+        {"op": "stacked_rowmajor", "weights": Wd, "d": d, "copies": copies},
+        {"op": "square"},
+    ]
+
+
+def dense64_input_copies(Wd: np.ndarray) -> int:
+    return 1 << _ceil_log2(Wd.shape[0])
