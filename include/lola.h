@@ -1,0 +1,257 @@
+/*
+ * lola.h -- C-ABI of the GB300 LoLa library: RNS-BFV ciphertext arithmetic on
+ * one GPU and the LoLa message representations / matrix-vector algorithms on
+ * top of it.
+ *
+ * Problem statement (paper Sec. 1 and Sec. 3.1): a client encrypts its data
+ * with a homomorphic encryption scheme (BFV), a server evaluates a network on
+ * the ciphertexts without the secret key, and the client decrypts the
+ * result.  The network is a layer list; each layer consumes one message
+ * representation and produces another (Sec. 4.2, Tables 1 and 3).
+ *
+ * Conventions for every call:
+ *  - Return value: LOLA_OK (0) or a negative LOLA_E_* code.  Nothing aborts
+ *    the process.  lola_last_error() returns a thread-local message for the
+ *    last failing call on the calling thread.
+ *  - Handles (lola_ctx, lola_keys, lola_ct, lola_net) are created and owned by
+ *    the library and released with the matching *_destroy call.  Destroying
+ *    NULL is a no-op.
+ *  - "host" pointers are caller-owned CPU memory, read or written during the
+ *    call only.  "device" pointers are caller-owned GPU memory on the
+ *    context's device; the library never frees them.
+ *  - Residues are uint64 words holding canonical values in [0, q).  A
+ *    ciphertext in the device layout is [2][L][n] words, limb-major: limb j
+ *    (prime q_j) of each of its two polynomials is n contiguous words.  A
+ *    batch of ciphertexts is those blocks back to back.  Between operations
+ *    ciphertexts are kept in NTT (evaluation) form; import/export calls
+ *    convert from/to coefficient form.
+ *  - A "message" is one plaintext slot vector; the library encrypts each
+ *    message once per plaintext modulus t_i (CRT pipelines, Sec. 4.4), so a
+ *    lola_ct holding m messages holds m * k_t ciphertexts ordered
+ *    [message][t_i].
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *    that take a stream are asynchronous with respect to the host unless
+ *    they read or write host memory.
+ */
+#ifndef LOLA_H
+#define LOLA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LOLA_OK 0
+#define LOLA_E_PARAM (-1)   /* invalid argument or parameter set */
+#define LOLA_E_NOMEM (-2)   /* device or host allocation failed */
+#define LOLA_E_NOKEY (-3)   /* a needed Galois / relinearisation key is missing */
+#define LOLA_E_REPR (-4)    /* a layer's input representation does not match */
+#define LOLA_E_CUDA (-5)    /* a CUDA runtime call failed */
+#define LOLA_E_TIMEOUT (-6) /* a bounded wait expired */
+#define LOLA_E_STATE (-7)   /* object used in the wrong state (e.g. secret key missing) */
+
+typedef struct lola_ctx lola_ctx;
+typedef struct lola_keys lola_keys;
+typedef struct lola_ct lola_ct;
+typedef struct lola_net lola_net;
+
+/* ------------------------------------------------------------------ context
+ * BFV parameters (Sec. 3.1: ring Z_t[x]/(x^n+1), n a power of two, with an
+ * order-2n root of unity mod t for batching).
+ *   n      ring degree, power of two, 16 <= n <= 16384
+ *   L      number of ciphertext primes (Q = q_0 ... q_{L-1}), 1 <= L <= 12
+ *   K      special primes for key switching: 0 or 1 (P = q_L when 1)
+ *   q      L + K distinct primes, each = 1 mod 2n and < 2^61
+ *   k_t    number of plaintext moduli (CRT pipelines), 1 <= k_t <= 4
+ *   t      k_t distinct primes = 1 mod 2n, < 2^31, coprime to all q
+ * The library adds its own auxiliary primes for exact ct x ct scaling.
+ * Errors: LOLA_E_PARAM for an invalid set, LOLA_E_CUDA / LOLA_E_NOMEM. */
+typedef struct {
+  uint32_t n;
+  uint32_t L;
+  uint32_t K;
+  const uint64_t* q; /* host, L + K entries, special prime last */
+  uint32_t k_t;
+  const uint64_t* t; /* host, k_t entries */
+} lola_params;
+
+int lola_ctx_create(const lola_params* params, int device, lola_ctx** out);
+void lola_ctx_destroy(lola_ctx* ctx);
+/* The auxiliary prime basis chosen by the context (count, then primes). */
+int lola_ctx_aux_primes(const lola_ctx* ctx, uint64_t* primes_out, uint32_t* count_out);
+
+/* --------------------------------------------------------------------- keys
+ * Key generation from a seed (secret key ternary, errors discrete Gaussian
+ * sigma = 3.2, uniform masks; Philox4x64-10 streams).  rot_steps lists the
+ * column-rotation steps k (0 < k < n/2, right shift within each row of the
+ * 2 x n/2 slot matrix, Sec. 3.1) that need Galois keys; flags add the
+ * relinearisation key and the row-swap key.  *secret_out receives a handle
+ * holding the secret, public and evaluation keys; *eval_out (may be NULL)
+ * a handle holding only the evaluation keys (what the server gets).
+ * Errors: LOLA_E_PARAM (bad step), LOLA_E_NOMEM, LOLA_E_CUDA. */
+#define LOLA_KEY_RELIN 1u
+#define LOLA_KEY_ROW_SWAP 2u
+int lola_keygen(lola_ctx* ctx, uint64_t seed, const int32_t* rot_steps, size_t n_steps, uint32_t flags,
+                lola_keys** secret_out, lola_keys** eval_out);
+void lola_keys_destroy(lola_keys* keys);
+/* Key material in coefficient form, for parity checks.  what: 0 = secret s
+ * (n int64 words written as uint64 two's complement), 1 = public key
+ * ([2][L][n]), 2 = relinearisation key, 3 = Galois key for rotation `step`
+ * (step = 0 selects the row swap).  Switching keys are [2 (b, a)][L digits]
+ * [L+K primes][n].  words_out receives the size; host may be NULL to query.
+ * Errors: LOLA_E_NOKEY, LOLA_E_STATE (secret missing), LOLA_E_PARAM. */
+int lola_keys_export(lola_ctx* ctx, const lola_keys* keys, int what, int32_t step, uint64_t* host,
+                     size_t* words_out);
+
+/* -------------------------------------------------------------- ciphertexts
+ * Encrypt n_msg slot vectors (host, n_msg x n int64, any sign; reduced mod
+ * each t_i).  Ciphertext c = (Delta m + p0 u + e1, p1 u + e2) mod Q with
+ * Delta = floor(Q / t_i); the randomness of ciphertext (message i, modulus
+ * j) comes from stream id i * k_t + j under `seed`.
+ * Errors: LOLA_E_STATE (no public key), LOLA_E_PARAM, LOLA_E_NOMEM. */
+int lola_encrypt(lola_ctx* ctx, const lola_keys* keys, const int64_t* slots, size_t n_msg, uint64_t seed,
+                 lola_ct** out);
+/* Decrypt and recombine the k_t residues by CRT (Sec. 4.4) into signed
+ * values in (-T/2, T/2], T = prod t_i.  out: host, n_msg x n pairs of int64
+ * (low word, high word) of a signed 128-bit integer.
+ * Errors: LOLA_E_STATE (no secret key). */
+int lola_decrypt(lola_ctx* ctx, const lola_keys* keys, const lola_ct* ct, int64_t* out);
+/* Decrypt without CRT: out host [n_msg][k_t][n], slot values in [0, t_i). */
+int lola_decrypt_residues(lola_ctx* ctx, const lola_keys* keys, const lola_ct* ct, uint64_t* out);
+int lola_ct_create(lola_ctx* ctx, size_t n_msg, lola_ct** out); /* all-zero ciphertexts */
+size_t lola_ct_messages(const lola_ct* ct);
+/* Device pointer to the ciphertext words ([n_msg][k_t][2][L][n], NTT form);
+ * valid until lola_ct_destroy. */
+uint64_t* lola_ct_data(lola_ct* ct);
+/* Coefficient-form exchange, host [n_msg][k_t][2][L][n]. */
+int lola_ct_export(lola_ctx* ctx, const lola_ct* ct, uint64_t* host);
+int lola_ct_import(lola_ctx* ctx, const uint64_t* host, size_t n_msg, lola_ct** out);
+/* Asynchronous host<->device copies of the NTT-form words (pinned host memory
+ * recommended); bytes = lola_ct_messages * k_t * 2 * L * n * 8. */
+int lola_ct_upload(lola_ctx* ctx, lola_ct* ct, const uint64_t* host, void* stream);
+int lola_ct_download(lola_ctx* ctx, const lola_ct* ct, uint64_t* host, void* stream);
+void lola_ct_destroy(lola_ct* ct);
+
+/* ------------------------------------------------------------ primitives
+ * Batched ciphertext primitives on caller-owned device buffers in the
+ * device layout (NTT form).  count = number of ciphertexts.  t_index[i]
+ * (host; NULL = all 0) selects the plaintext modulus of ciphertext i where
+ * the operation depends on it.  Output buffers must not alias inputs.
+ * Errors: LOLA_E_PARAM, LOLA_E_NOKEY, LOLA_E_CUDA, LOLA_E_NOMEM (scratch). */
+
+/* In-place forward / inverse negacyclic NTT of n_polys polynomials of
+ * n_limbs limbs each (limb j uses prime q_j), device layout. */
+int lola_ntt_forward(lola_ctx* ctx, uint64_t* data, size_t n_polys, uint32_t n_limbs, void* stream);
+int lola_ntt_inverse(lola_ctx* ctx, uint64_t* data, size_t n_polys, uint32_t n_limbs, void* stream);
+/* out = a + b (Sec. 3.1 operator (+)). */
+int lola_add(lola_ctx* ctx, const uint64_t* a, const uint64_t* b, uint64_t* out, size_t count, void* stream);
+/* Rotation (Sec. 3.1): out_i = rotate(in_i, steps[i]) with steps host, 0 < step < n/2
+ * a right shift of each slot row, step = 0 the row swap. */
+int lola_rotate(lola_ctx* ctx, const lola_keys* keys, const uint64_t* in, uint64_t* out, size_t count,
+                const int32_t* steps, void* stream);
+/* ct (x) ct with BFV scaling and relinearisation (Sec. 3.1 operator (x)):
+ * out_i = relin(round(t/Q * a_i (x) b_i)).  b may equal a (square). */
+int lola_multiply(lola_ctx* ctx, const lola_keys* keys, const uint64_t* a, const uint64_t* b, uint64_t* out,
+                  size_t count, const uint32_t* t_index, void* stream);
+/* ct x plaintext: out_i = in_i * encode(slots_i) (slots host [count][n]
+ * int64, centered lift mod t). */
+int lola_mul_plain(lola_ctx* ctx, const uint64_t* in, const int64_t* slots, uint64_t* out, size_t count,
+                   const uint32_t* t_index, void* stream);
+
+/* ------------------------------------------------------------ networks
+ * Message representations (Sec. 4.2.1). */
+typedef enum {
+  LOLA_REPR_DENSE = 1,       /* m_i = v_i (message 0) */
+  LOLA_REPR_SPARSE = 2,      /* k messages, message i constant v_i */
+  LOLA_REPR_STACKED = 3,     /* copies of v every 2^d slots */
+  LOLA_REPR_INTERLEAVED = 4, /* m_sigma(i) = v_i */
+  LOLA_REPR_CONVOLUTION = 5  /* r messages, m^j_i = v_sigma_i(j) */
+} lola_repr;
+
+/* Layers (Sec. 4.2.2 matrix-vector algorithms, Sec. 3.2 square, Sec. 4.3
+ * combine).  Weights are host int64, row-major rows x cols, copied. */
+typedef enum {
+  LOLA_LAYER_CONV_ROWMAJOR = 1,        /* convolution -> dense messages (one per row of W) */
+  LOLA_LAYER_COMBINE = 2,              /* k dense messages -> 1: message m rotated by m*stride */
+  LOLA_LAYER_SQUARE = 3,               /* elementwise square (ct (x) ct) */
+  LOLA_LAYER_STACK = 4,                /* dense -> stacked: copies every 2^d slots */
+  LOLA_LAYER_STACKED_ROWMAJOR = 5,     /* stacked -> interleaved (mask + combine rounds) */
+  LOLA_LAYER_INTERLEAVED_ROWMAJOR = 6, /* interleaved/dense -> sparse (one message per row) */
+  LOLA_LAYER_DENSE_ROWMAJOR = 7        /* dense -> sparse */
+} lola_layer_op;
+
+typedef struct {
+  lola_layer_op op;
+  lola_repr in_repr;      /* checked against the running representation */
+  lola_repr out_repr;     /* checked against what the layer produces */
+  uint32_t rows, cols;    /* weight shape (CONV: maps x window size) */
+  const int64_t* weights; /* host, rows * cols, NULL for COMBINE/SQUARE/STACK */
+  uint32_t d;             /* STACK / STACKED_ROWMAJOR: block size 2^d */
+  uint32_t copies;        /* STACK / STACKED_ROWMAJOR: number of copies (power of two) */
+  uint32_t stride;        /* COMBINE: slot offset between consecutive messages */
+} lola_layer;
+
+/* Input description: n_msgs messages per request, n_elems vector elements
+ * (CONVOLUTION: windows per message), element i in slot slot[i] of message 0
+ * (NULL = slot i).  STACKED inputs also give d and copies. */
+typedef struct {
+  lola_repr repr;
+  uint32_t n_msgs;
+  uint32_t n_elems;
+  const uint32_t* slot;
+  uint32_t d, copies;
+} lola_input;
+
+/* Compile a layer list: validates representations, encodes the weight
+ * plaintexts for every t_i and uploads them.  Errors: LOLA_E_REPR,
+ * LOLA_E_PARAM, LOLA_E_NOMEM. */
+int lola_net_create(lola_ctx* ctx, const lola_input* input, const lola_layer* layers, size_t n_layers,
+                    lola_net** out);
+void lola_net_destroy(lola_net* net);
+/* Rotation steps whose Galois keys the network needs (0 = row swap);
+ * steps may be NULL to query the count. */
+int lola_net_rotation_steps(const lola_net* net, int32_t* steps, size_t* count);
+/* Output element o is in output message msg[o] at slot slot[o]. */
+int lola_net_output_map(const lola_net* net, uint32_t* msg, uint32_t* slot, size_t* count);
+/* Messages per request at the input and the output. */
+int lola_net_shape(const lola_net* net, uint32_t* in_msgs, uint32_t* out_msgs);
+/* Evaluate on a batch: `in` holds B * in_msgs messages (request-major), `out`
+ * must hold B * out_msgs.  The first call for a batch size B builds and
+ * caches the executor (scratch + CUDA graph); later calls replay it.
+ * Errors: LOLA_E_NOKEY, LOLA_E_PARAM, LOLA_E_NOMEM, LOLA_E_CUDA. */
+int lola_eval_network(lola_ctx* ctx, const lola_keys* keys, lola_net* net, const lola_ct* in, lola_ct* out,
+                      void* stream);
+/* Same, without CUDA graph capture (plain launches on `stream`). */
+int lola_eval_network_eager(lola_ctx* ctx, const lola_keys* keys, lola_net* net, const lola_ct* in,
+                            lola_ct* out, void* stream);
+
+/* ------------------------------------------------------------ client packing
+ * Convolution representation (Sec. 4.2.1 footnote): image h x w (host int64,
+ * row-major), window kh x kw, stride s; windows with upper-left corner
+ * (s*i, s*j), padded with zeros bottom/right to ceil((h-kh)/s)+1 windows per
+ * axis.  out: host [kh*kw][n]; message r = dr*kw + dc holds pixel
+ * (s*i+dr, s*j+dc) at slot i*ow + j.  *windows_out = oh*ow. */
+int lola_pack_convolution(const int64_t* image, uint32_t h, uint32_t w, uint32_t kh, uint32_t kw, uint32_t s,
+                          uint32_t n, int64_t* out, uint32_t* windows_out);
+/* Stacked representation: `copies` copies of vec (length k <= 2^d) every 2^d slots. */
+int lola_pack_stacked(const int64_t* vec, uint32_t k, uint32_t d, uint32_t copies, uint32_t n, int64_t* out);
+
+/* ------------------------------------------------------------- profiling
+ * Per-kernel device time with CUDA events around every launch of kernel
+ * class `kind` (0 = NTT-family kernels, 1 = key-switch inner product,
+ * 2 = elementwise, 3 = basis conversion) while enabled.  Read returns the
+ * summed milliseconds and launch count since the last reset. */
+int lola_profile_enable(lola_ctx* ctx, int kind, int on);
+int lola_profile_read(lola_ctx* ctx, int kind, double* ms, uint64_t* launches);
+/* Kernel launches issued by the library since context creation. */
+uint64_t lola_launch_count(const lola_ctx* ctx);
+
+const char* lola_last_error(void);
+const char* lola_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LOLA_H */

@@ -1,0 +1,78 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/lola.h"
+#include "modarith.cuh"
+
+namespace lola {
+
+constexpr int MAXP = 40;    // primes per context: Q + P + aux + t
+constexpr int MAXL = 12;    // ciphertext primes
+constexpr int MAXB = 16;    // size bound of either mixed-radix basis (Q or aux)
+constexpr int MAXT = 4;     // plaintext moduli
+
+struct PrimeDev {
+  uint64_t q, qinv, r2, f64;  // modulus, -q^-1 mod 2^64, 2^128 mod q, floor(2^64/q)
+  uint64_t ninv, ninv_s;      // n^-1 and its Shoup companion
+  uint64_t ninvr, ninvr_s;    // n^-1 * 2^64 mod q (undoes one Montgomery factor)
+};
+
+// Constants for exact mixed-radix (Garner) conversion out of a basis
+// b_0..b_{k-1}: x = v_0 + v_1 b_0 + v_2 b_0 b_1 + ..., v_i in [0, b_i).
+struct MrcDev {
+  int k;                           // basis size
+  uint64_t inv[MAXB][MAXB];        // inv[i][j] = b_j^-1 mod b_i (j < i)
+  uint64_t inv_s[MAXB][MAXB];
+  uint64_t half[MAXB];             // mixed-radix digits of (prod b - 1) / 2
+};
+
+struct CtxDev {
+  uint32_t n, logn, L, K, M, kt, np;
+  int iP;                          // index of P (= L) when K = 1
+  int iB;                          // first auxiliary prime index (= L + K)
+  int iT;                          // first plaintext modulus index (= L + K + M)
+  PrimeDev pr[MAXP];
+  const uint64_t* tw_fwd;          // [np][n]
+  const uint64_t* tw_fwd_s;
+  const uint64_t* tw_inv;
+  const uint64_t* tw_inv_s;
+  // --- exact lifts Q -> B and B -> Q ---
+  MrcDev mrcQ;                     // over q_0..q_{L-1}
+  MrcDev mrcB;                     // over the aux primes b_0..b_{M-1}
+  uint64_t wQB[MAXB][MAXB];        // [k][j] prod_{l<k} q_l mod b_j
+  uint64_t wQB_s[MAXB][MAXB];
+  uint64_t QmodB[MAXB];            // Q mod b_j
+  uint64_t wBQ[MAXB][MAXB];        // [k][i] prod_{l<k} b_l mod q_i
+  uint64_t wBQ_s[MAXB][MAXB];
+  uint64_t BmodQ[MAXB];            // prod B mod q_i
+  uint64_t QinvB[MAXB], QinvB_s[MAXB];            // Q^-1 mod b_j
+  uint64_t tQ[MAXT][MAXB], tQ_s[MAXT][MAXB];      // t mod q_i
+  uint64_t tB[MAXT][MAXB], tB_s[MAXT][MAXB];      // t mod b_j
+  // --- decryption ---
+  uint64_t wQT[MAXB][MAXT], wQT_s[MAXB][MAXT];    // prod_{l<k} q_l mod t
+  uint64_t QinvT[MAXT], QinvT_s[MAXT];            // Q^-1 mod t
+  uint64_t deltaQ[MAXT][MAXB];                    // floor(Q/t) mod q_i
+  uint64_t deltaQ_s[MAXT][MAXB];
+  // --- key switching (K = 1) ---
+  uint64_t PmodQ[MAXB];
+  uint64_t PinvQ[MAXB], PinvQ_s[MAXB];            // P^-1 mod q_i
+  uint64_t PmontQ[MAXB];                          // (P mod q_i) 2^64 mod q_i (P = 1 when K = 0)
+};
+
+// host-side error reporting
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+
+#define LOLA_CUDA_TRY(expr)                                                          \
+  do {                                                                               \
+    cudaError_t _e = (expr);                                                         \
+    if (_e != cudaSuccess)                                                           \
+      return ::lola::fail(LOLA_E_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
+  } while (0)
+
+}  // namespace lola

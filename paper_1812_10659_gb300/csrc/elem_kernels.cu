@@ -1,0 +1,523 @@
+// Element-wise kernels (HBM-bound) and exact RNS basis conversions.
+//
+// Ciphertext words are addressed as [ct][comp][limb][n]; the prime of a word
+// is its limb index in the ciphertext basis.  All kernels are grid-stride
+// loops over words (or over coefficient positions for the basis
+// conversions, which need every limb of one coefficient at once).
+#include "internal.h"
+#include "kernels.h"
+
+namespace lola {
+
+static int post(Ctx* c) {
+  c->launches.fetch_add(1, std::memory_order_relaxed);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(LOLA_E_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+  return LOLA_OK;
+}
+
+static unsigned grid_for(size_t items, int threads) {
+  size_t g = (items + threads - 1) / threads;
+  const size_t cap = 152 * 16;   // enough CTAs to fill every SM several times
+  return (unsigned)(g < 1 ? 1 : (g > cap ? cap : g));
+}
+
+// ------------------------------------------------------------- key switching
+// K = 0 output stage: out[comp][j] = sum_i D[i][j] key[comp][i][j]
+//                                    (+ tau_g(c0)_j, + add1_j, + accum)
+__global__ void ke_ks_ip_q(const CtxDev* __restrict__ C, KsDev a) {
+  const int L = C->L, LK = C->L + C->K, logn = C->logn;
+  const size_t n = C->n;
+  const size_t total = a.count * 2 * L * n;
+  for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < total; w += (size_t)gridDim.x * blockDim.x) {
+    const uint32_t k = w & (n - 1);
+    const size_t r = w >> logn;
+    const int j = r % L;
+    const int comp = (r / L) & 1;
+    const size_t ct = r / (2 * L);
+    const PrimeDev& P = C->pr[j];
+    const uint64_t* key = a.d_keys ? a.d_keys[ct / a.gal_div] : a.key;
+    uint64_t acc = 0;
+    for (int i = 0; i < L; ++i) {
+      const uint64_t d = a.D[((ct * L + i) * LK + j) * n + k];
+      const uint64_t kw = key[((size_t)(comp * L + i) * LK + j) * n + k];
+      acc = add_mod(acc, mont_mul(d, kw, P.q, P.qinv), P.q);
+    }
+    if (comp == 0 && a.c0) {
+      const uint32_t g = a.d_gal ? a.d_gal[ct / a.gal_div] : a.gal;
+      acc = add_mod(acc, a.c0[(ct * 2 * L + j) * n + (g == 1 ? k : gal_src(k, g, logn))], P.q);
+    }
+    if (comp == 1 && a.add1) acc = add_mod(acc, a.add1[(ct * 2 * L + L + j) * n + k], P.q);
+    if (a.accum) acc = add_mod(acc, a.accum[w], P.q);
+    a.out[w] = acc;
+  }
+}
+
+// ------------------------------------------------------------- element-wise
+// words of a batch of ciphertexts; limb = (w / n) % L
+__global__ void ke_add(const CtxDev* __restrict__ C, const uint64_t* a, const uint64_t* b, uint64_t* out,
+                       size_t total, int sub) {
+  const int L = C->L, logn = C->logn;
+  for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < total; w += (size_t)gridDim.x * blockDim.x) {
+    const uint64_t q = C->pr[(w >> logn) % L].q;
+    out[w] = sub ? sub_mod(a[w], b[w], q) : add_mod(a[w], b[w], q);
+  }
+}
+
+// x -> x * 2^64 mod q per limb of [poly][limbs][n]
+// (inverse = true: x -> x * 2^-64 mod q)
+__global__ void ke_to_mont(const CtxDev* __restrict__ C, uint64_t* x, size_t total, uint32_t limbs, PrimeMap pm,
+                           int inverse) {
+  const int logn = C->logn;
+  for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < total; w += (size_t)gridDim.x * blockDim.x) {
+    const PrimeDev& P = C->pr[pm.p[(w >> logn) % limbs]];
+    x[w] = mont_mul(x[w], inverse ? 1 : P.r2, P.q, P.qinv);
+  }
+}
+
+// out = a + b * w (w in Montgomery form, one [limbs][n] block broadcast over polys)
+__global__ void ke_axpy_mont(const CtxDev* __restrict__ C, const uint64_t* a, const uint64_t* b, const uint64_t* w,
+                             uint64_t* out, size_t total, uint32_t limbs, PrimeMap pm) {
+  const int logn = C->logn;
+  const size_t blk = (size_t)limbs << logn;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const PrimeDev& P = C->pr[pm.p[(i >> logn) % limbs]];
+    const uint64_t v = mont_mul(b[i], w[i % blk], P.q, P.qinv);
+    out[i] = a ? add_mod(a[i], v, P.q) : v;
+  }
+}
+
+// out = -(a * s + e) per limb (public key): s in Montgomery form
+__global__ void ke_neg_axpe(const CtxDev* __restrict__ C, const uint64_t* a, const uint64_t* s_mont,
+                            const uint64_t* e, uint64_t* out, size_t total) {
+  const int logn = C->logn;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const PrimeDev& P = C->pr[i >> logn];
+    out[i] = neg_mod(add_mod(mont_mul(a[i], s_mont[i], P.q, P.qinv), e[i], P.q), P.q);
+  }
+}
+
+// switching key rows: a, e: [L][LK][n] (e broadcast per digit over primes),
+// out: [2][L][LK][n] Montgomery form of (b, a),
+// b_ij = -a_ij s_j + e_ij + [i == j] (P mod q_j) s'_j
+__global__ void ke_keygen_switch(const CtxDev* __restrict__ C, const uint64_t* a, const uint64_t* e,
+                                 const uint64_t* s_mont, const uint64_t* sfrom, uint64_t* out) {
+  const int L = C->L, LK = C->L + C->K, logn = C->logn;
+  const size_t n = C->n;
+  const size_t total = (size_t)L * LK * n;
+  for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < total; w += (size_t)gridDim.x * blockDim.x) {
+    const size_t k = w & (n - 1);
+    const int j = (w >> logn) % LK;
+    const int i = (int)((w >> logn) / LK);
+    const PrimeDev& P = C->pr[j];
+    uint64_t b = neg_mod(mont_mul(a[w], s_mont[(size_t)j * n + k], P.q, P.qinv), P.q);
+    b = add_mod(b, e[w], P.q);
+    if (i == j) b = add_mod(b, mont_mul(sfrom[(size_t)j * n + k], C->PmontQ[j], P.q, P.qinv), P.q);
+    out[w] = mont_mul(b, P.r2, P.q, P.qinv);
+    out[total + w] = mont_mul(a[w], P.r2, P.q, P.qinv);
+  }
+}
+
+// NTT-domain Galois permutation of [poly][limbs][n]
+__global__ void ke_gal_permute(const CtxDev* __restrict__ C, const uint64_t* in, uint64_t* out, size_t total,
+                               uint32_t g) {
+  const int logn = C->logn;
+  const size_t n = C->n;
+  for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < total; w += (size_t)gridDim.x * blockDim.x) {
+    const size_t base = w & ~(n - 1);
+    out[w] = in[base + gal_src((uint32_t)(w & (n - 1)), g, logn)];
+  }
+}
+
+// ct x plaintext for R plaintexts at once: out[r][b][t] = in[b][t] (.) pt[r][t]
+// in: [B][kt][2][L][n]; pt: [R][kt][L][n] Montgomery; out: [R][B][kt][2][L][n]
+__global__ void ke_mul_plain_multi(const CtxDev* __restrict__ C, const uint64_t* in, const uint64_t* pt,
+                                   uint64_t* out, uint32_t R, uint32_t B) {
+  const int L = C->L, logn = C->logn, kt = C->kt;
+  const size_t n = C->n;
+  const size_t ctw = 2 * (size_t)L * n;
+  const size_t total = (size_t)R * B * kt * ctw;
+  for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < total; w += (size_t)gridDim.x * blockDim.x) {
+    const size_t k = w & (n - 1);
+    const int j = (w >> logn) % L;
+    const size_t ctg = w / ctw;             // r * B * kt + b * kt + t
+    const int t = ctg % kt;
+    const size_t r = ctg / ((size_t)B * kt);
+    const size_t in_ct = ctg % ((size_t)B * kt);
+    const size_t comp = (w / ((size_t)L * n)) & 1;
+    const PrimeDev& P = C->pr[j];
+    const uint64_t x = in[in_ct * ctw + (comp * L + j) * n + k];
+    const uint64_t p = pt[((r * kt + t) * L + j) * n + k];
+    out[w] = mont_mul(x, p, P.q, P.qinv);
+  }
+}
+
+// convolution row-major: out[m][b][t] = sum_r w[m][r][t][j] in[r][b][t]
+// in: [R][B][kt][2][L][n]; w, ws: [maps][R][kt][L] scalars (Shoup)
+__global__ void ke_mac_scalar(const CtxDev* __restrict__ C, const uint64_t* in, uint32_t R, const uint64_t* w,
+                              const uint64_t* ws, uint64_t* out, uint32_t maps, uint32_t B) {
+  const int L = C->L, logn = C->logn, kt = C->kt;
+  const size_t n = C->n;
+  const size_t ctw = 2 * (size_t)L * n;
+  const size_t per_msg = (size_t)B * kt * ctw;
+  const size_t total = (size_t)maps * per_msg;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t m = i / per_msg;
+    const size_t off = i % per_msg;
+    const int j = (off >> logn) % L;
+    const int t = (off / ctw) % kt;
+    const uint64_t q = C->pr[j].q;
+    uint64_t acc = 0;
+    for (uint32_t r = 0; r < R; ++r) {
+      const size_t wi = ((m * R + r) * kt + t) * L + j;
+      acc = add_mod(acc, shoup_mul(in[r * per_msg + off], w[wi], ws[wi], q), q);
+    }
+    out[i] = acc;
+  }
+}
+
+// ------------------------------------------------------ exact basis conversion
+// Mixed-radix digits of x given by residues x_i (i < k) over basis `b` of the
+// MRC table; returns whether x > (prod b - 1) / 2 (the centered lift is x - prod b).
+template <int KMAX>
+__device__ __forceinline__ bool mrc_digits(const CtxDev* C, const MrcDev& T, int first_prime, int k,
+                                           const uint64_t (&x)[KMAX], uint64_t (&v)[KMAX]) {
+#pragma unroll
+  for (int i = 0; i < KMAX; ++i) {
+    if (i < k) {
+      const PrimeDev& P = C->pr[first_prime + i];
+      uint64_t u = x[i];
+#pragma unroll
+      for (int j = 0; j < KMAX; ++j) {
+        if (j < i) {
+          const uint64_t vj = reduce64(v[j], P.q, P.f64);
+          u = shoup_mul(sub_mod(u, vj, P.q), T.inv[i][j], T.inv_s[i][j], P.q);
+        }
+      }
+      v[i] = u;
+    }
+  }
+  bool decided = false, gt = false;
+#pragma unroll
+  for (int i = KMAX - 1; i >= 0; --i) {
+    if (i < k && !decided && v[i] != T.half[i]) {
+      decided = true;
+      gt = v[i] > T.half[i];
+    }
+  }
+  return gt;
+}
+
+// lift centered x in Z_Q (residues over q_0..q_{L-1}) to the aux primes
+// xq: [poly][L][n], xb: [poly][M][n]
+template <int KQ>
+__global__ void ke_lift_q_to_b(const CtxDev* __restrict__ C, const uint64_t* xq, uint64_t* xb, size_t n_polys) {
+  const int L = C->L, M = C->M, logn = C->logn, iB = C->iB;
+  const size_t n = C->n;
+  const size_t total = n_polys * n;
+  for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < total; w += (size_t)gridDim.x * blockDim.x) {
+    const size_t poly = w >> logn, k = w & (n - 1);
+    uint64_t x[KQ], v[KQ];
+#pragma unroll
+    for (int i = 0; i < KQ; ++i) x[i] = i < L ? xq[(poly * L + i) * n + k] : 0;
+    const bool neg = mrc_digits<KQ>(C, C->mrcQ, 0, L, x, v);
+    for (int jb = 0; jb < M; ++jb) {
+      const PrimeDev& P = C->pr[iB + jb];
+      uint64_t acc = 0;
+#pragma unroll
+      for (int i = 0; i < KQ; ++i)
+        if (i < L) acc = add_mod(acc, shoup_mul(reduce64(v[i], P.q, P.f64), C->wQB[i][jb], C->wQB_s[i][jb], P.q), P.q);
+      if (neg) acc = sub_mod(acc, C->QmodB[jb], P.q);
+      xb[(poly * M + jb) * n + k] = acc;
+    }
+  }
+}
+
+// tensor over Q u B (Montgomery products; the inverse transform that follows
+// multiplies by 2^64 to undo the factor).  x/y: NTT form, Q part in
+// ciphertext layout [ct][2][L][n], B part [ct][2][M][n].
+// T: [ct][3][L+M][n]
+__global__ void ke_tensor(const CtxDev* __restrict__ C, const uint64_t* xq, const uint64_t* xb, const uint64_t* yq,
+                          const uint64_t* yb, uint64_t* T, size_t count) {
+  const int L = C->L, M = C->M, LM = C->L + C->M, logn = C->logn, iB = C->iB;
+  const size_t n = C->n;
+  const size_t total = count * LM * n;
+  for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < total; w += (size_t)gridDim.x * blockDim.x) {
+    const size_t k = w & (n - 1);
+    const int l = (w >> logn) % LM;
+    const size_t ct = (w >> logn) / LM;
+    uint64_t x0, x1, y0, y1;
+    int p;
+    if (l < L) {
+      p = l;
+      x0 = xq[(ct * 2 * L + l) * n + k];
+      x1 = xq[(ct * 2 * L + L + l) * n + k];
+      y0 = yq[(ct * 2 * L + l) * n + k];
+      y1 = yq[(ct * 2 * L + L + l) * n + k];
+    } else {
+      const int jb = l - L;
+      p = iB + jb;
+      x0 = xb[(ct * 2 * M + jb) * n + k];
+      x1 = xb[(ct * 2 * M + M + jb) * n + k];
+      y0 = yb[(ct * 2 * M + jb) * n + k];
+      y1 = yb[(ct * 2 * M + M + jb) * n + k];
+    }
+    const PrimeDev& P = C->pr[p];
+    const uint64_t d0 = mont_mul(x0, y0, P.q, P.qinv);
+    const uint64_t d1 = add_mod(mont_mul(x0, y1, P.q, P.qinv), mont_mul(x1, y0, P.q, P.qinv), P.q);
+    const uint64_t d2 = mont_mul(x1, y1, P.q, P.qinv);
+    T[((ct * 3 + 0) * LM + l) * n + k] = d0;
+    T[((ct * 3 + 1) * LM + l) * n + k] = d1;
+    T[((ct * 3 + 2) * LM + l) * n + k] = d2;
+  }
+}
+
+// BFV scaling, exact: for d given mod Q u B (coefficient form),
+// r = [t d]_Q centered, y = (t d - r) / Q computed mod each b, then y lifted
+// exactly from B to Q.  T: [ct][3][L+M][n]; parts 0 and 1 go to E
+// ([ct][2][L][n], ciphertext layout), part 2 to DIG ([ct][L][n]).
+template <int KQ, int KB>
+__global__ void ke_scale_round(const CtxDev* __restrict__ C, const uint64_t* T, const uint32_t* tidx,
+                               uint32_t tidx_div, uint64_t* E, uint64_t* DIG, size_t count) {
+  const int L = C->L, M = C->M, LM = C->L + C->M, logn = C->logn, iB = C->iB;
+  const size_t n = C->n;
+  const size_t total = count * 3 * n;
+  for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < total; w += (size_t)gridDim.x * blockDim.x) {
+    const size_t k = w & (n - 1);
+    const size_t cp = w >> logn;         // ct * 3 + part
+    const size_t ct = cp / 3;
+    const int ti = tidx ? tidx[ct / tidx_div] : 0;
+    const uint64_t* src = T + cp * LM * n + k;
+    uint64_t r[KQ], v[KQ];
+#pragma unroll
+    for (int i = 0; i < KQ; ++i)
+      r[i] = i < L ? shoup_mul(src[(size_t)i * n], C->tQ[ti][i], C->tQ_s[ti][i], C->pr[i].q) : 0;
+    const bool rneg = mrc_digits<KQ>(C, C->mrcQ, 0, L, r, v);
+    uint64_t y[KB], u[KB];
+#pragma unroll
+    for (int jb = 0; jb < KB; ++jb) {
+      if (jb < M) {
+        const PrimeDev& P = C->pr[iB + jb];
+        uint64_t rb = 0;
+#pragma unroll
+        for (int i = 0; i < KQ; ++i)
+          if (i < L) rb = add_mod(rb, shoup_mul(reduce64(v[i], P.q, P.f64), C->wQB[i][jb], C->wQB_s[i][jb], P.q), P.q);
+        if (rneg) rb = sub_mod(rb, C->QmodB[jb], P.q);
+        const uint64_t td = shoup_mul(src[(size_t)(L + jb) * n], C->tB[ti][jb], C->tB_s[ti][jb], P.q);
+        y[jb] = shoup_mul(sub_mod(td, rb, P.q), C->QinvB[jb], C->QinvB_s[jb], P.q);
+      } else {
+        y[jb] = 0;
+      }
+    }
+    const bool yneg = mrc_digits<KB>(C, C->mrcB, iB, M, y, u);
+    const int part = (int)(cp % 3);
+    uint64_t* dst = (part < 2 ? E + (ct * 2 + part) * L * n : DIG + ct * L * n) + k;
+    for (int i = 0; i < L; ++i) {
+      const PrimeDev& P = C->pr[i];
+      uint64_t acc = 0;
+#pragma unroll
+      for (int jb = 0; jb < KB; ++jb)
+        if (jb < M) acc = add_mod(acc, shoup_mul(reduce64(u[jb], P.q, P.f64), C->wBQ[jb][i], C->wBQ_s[jb][i], P.q), P.q);
+      if (yneg) acc = sub_mod(acc, C->BmodQ[i], P.q);
+      dst[(size_t)i * n] = acc;
+    }
+  }
+}
+
+// decryption rounding: x = [c0 + c1 s]_Q (coefficient form, [poly][L][n]) ->
+// m = round(t x / Q) mod t = (-(r mod t) Q^-1 + [r > (Q-1)/2]) mod t, r = [t x]_Q
+template <int KQ>
+__global__ void ke_decrypt_round(const CtxDev* __restrict__ C, const uint64_t* x, const uint32_t* tidx,
+                                 uint64_t* m, size_t n_polys) {
+  const int L = C->L, logn = C->logn, iT = C->iT;
+  const size_t n = C->n;
+  const size_t total = n_polys * n;
+  for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < total; w += (size_t)gridDim.x * blockDim.x) {
+    const size_t poly = w >> logn, k = w & (n - 1);
+    const int ti = tidx[poly];
+    uint64_t r[KQ], v[KQ];
+#pragma unroll
+    for (int i = 0; i < KQ; ++i)
+      r[i] = i < L ? shoup_mul(x[(poly * L + i) * n + k], C->tQ[ti][i], C->tQ_s[ti][i], C->pr[i].q) : 0;
+    const bool gt = mrc_digits<KQ>(C, C->mrcQ, 0, L, r, v);
+    const PrimeDev& T = C->pr[iT + ti];
+    uint64_t rt = 0;
+#pragma unroll
+    for (int i = 0; i < KQ; ++i)
+      if (i < L) rt = add_mod(rt, shoup_mul(reduce64(v[i], T.q, T.f64), C->wQT[i][ti], C->wQT_s[i][ti], T.q), T.q);
+    uint64_t mm = neg_mod(shoup_mul(rt, C->QinvT[ti], C->QinvT_s[ti], T.q), T.q);
+    if (gt) mm = add_mod(mm, 1, T.q);
+    m[w] = mm;
+  }
+}
+
+// encryption combine: out[ct][0][j] = M1[ct][j] + U[ct][j] pk0_j ; out[ct][1][j] = E2[ct][j] + U[ct][j] pk1_j
+__global__ void ke_enc_combine(const CtxDev* __restrict__ C, const uint64_t* M1, const uint64_t* E2,
+                               const uint64_t* U, const uint64_t* pk, uint64_t* out, size_t count) {
+  const int L = C->L, logn = C->logn;
+  const size_t n = C->n;
+  const size_t total = count * 2 * L * n;
+  for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < total; w += (size_t)gridDim.x * blockDim.x) {
+    const size_t k = w & (n - 1);
+    const size_t r = w >> logn;
+    const int j = r % L;
+    const int comp = (r / L) & 1;
+    const size_t ct = r / (2 * L);
+    const PrimeDev& P = C->pr[j];
+    const size_t src = (ct * L + j) * n + k;
+    const uint64_t prod = mont_mul(U[src], pk[((size_t)comp * L + j) * n + k], P.q, P.qinv);
+    out[w] = add_mod(comp ? E2[src] : M1[src], prod, P.q);
+  }
+}
+
+// decryption phase: x = c0 + c1 s (NTT form), out [ct][L][n]
+__global__ void ke_dec_phase(const CtxDev* __restrict__ C, const uint64_t* ct_in, const uint64_t* s_mont,
+                             uint64_t* out, size_t count) {
+  const int L = C->L, logn = C->logn;
+  const size_t n = C->n;
+  const size_t total = count * L * n;
+  for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < total; w += (size_t)gridDim.x * blockDim.x) {
+    const size_t k = w & (n - 1);
+    const int j = (w >> logn) % L;
+    const size_t ct = (w >> logn) / L;
+    const PrimeDev& P = C->pr[j];
+    const uint64_t c0 = ct_in[(ct * 2 * L + j) * n + k];
+    const uint64_t c1 = ct_in[(ct * 2 * L + L + j) * n + k];
+    out[w] = add_mod(c0, mont_mul(c1, s_mont[(size_t)j * n + k], P.q, P.qinv), P.q);
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+namespace k {
+
+#define ELEM_LAUNCH(kind, KERNEL, items, ...)                                       \
+  do {                                                                             \
+    ProfScope ps_(c, kind, s);                                                     \
+    KERNEL<<<grid_for(items, 256), 256, 0, s>>>(__VA_ARGS__);                       \
+  } while (0)
+
+int ks_ip_q(Ctx* c, const KsDev& a, cudaStream_t s) {
+  ELEM_LAUNCH(KK_KSIP, ke_ks_ip_q, a.count * 2 * c->L * c->n, c->dev, a);
+  return post(c);
+}
+
+int add(Ctx* c, const uint64_t* a, const uint64_t* b, uint64_t* out, size_t count, cudaStream_t s) {
+  if (!count) return LOLA_OK;
+  const size_t total = count * c->ct_words();
+  ELEM_LAUNCH(KK_ELEM, ke_add, total, c->dev, a, b, out, total, 0);
+  return post(c);
+}
+
+int sub(Ctx* c, const uint64_t* a, const uint64_t* b, uint64_t* out, size_t count, cudaStream_t s) {
+  if (!count) return LOLA_OK;
+  const size_t total = count * c->ct_words();
+  ELEM_LAUNCH(KK_ELEM, ke_add, total, c->dev, a, b, out, total, 1);
+  return post(c);
+}
+
+int to_mont_map(Ctx* c, uint64_t* data, size_t n_limbpolys, uint32_t limbs, const PrimeMap& pm, cudaStream_t s,
+                bool inverse) {
+  const size_t total = n_limbpolys * c->n;
+  ELEM_LAUNCH(KK_ELEM, ke_to_mont, total, c->dev, data, total, limbs, pm, (int)inverse);
+  return post(c);
+}
+
+int axpy_mont_map(Ctx* c, const uint64_t* a, const uint64_t* b, const uint64_t* w_mont, uint64_t* out,
+                  size_t n_limbpolys, uint32_t limbs, const PrimeMap& pm, cudaStream_t s) {
+  const size_t total = n_limbpolys * c->n;
+  ELEM_LAUNCH(KK_ELEM, ke_axpy_mont, total, c->dev, a, b, w_mont, out, total, limbs, pm);
+  return post(c);
+}
+
+int neg_axpe(Ctx* c, const uint64_t* a, const uint64_t* s_mont, const uint64_t* e, uint64_t* out, uint32_t limbs,
+             cudaStream_t s) {
+  const size_t total = (size_t)limbs * c->n;
+  ELEM_LAUNCH(KK_ELEM, ke_neg_axpe, total, c->dev, a, s_mont, e, out, total);
+  return post(c);
+}
+
+int keygen_switch(Ctx* c, const uint64_t* a, const uint64_t* e, const uint64_t* s_mont, const uint64_t* sfrom,
+                  uint64_t* out, cudaStream_t s) {
+  const size_t total = (size_t)c->L * (c->L + c->K) * c->n;
+  ELEM_LAUNCH(KK_ELEM, ke_keygen_switch, total, c->dev, a, e, s_mont, sfrom, out);
+  return post(c);
+}
+
+int gal_permute(Ctx* c, const uint64_t* in, uint64_t* out, size_t n_limbpolys, uint32_t g, cudaStream_t s) {
+  const size_t total = n_limbpolys * c->n;
+  ELEM_LAUNCH(KK_ELEM, ke_gal_permute, total, c->dev, in, out, total, g);
+  return post(c);
+}
+
+int mul_plain_multi(Ctx* c, const uint64_t* in, const uint64_t* pt, uint64_t* out, uint32_t R, uint32_t B,
+                    cudaStream_t s) {
+  const size_t total = (size_t)R * B * c->kt * c->ct_words();
+  if (!total) return LOLA_OK;
+  ELEM_LAUNCH(KK_ELEM, ke_mul_plain_multi, total, c->dev, in, pt, out, R, B);
+  return post(c);
+}
+
+int mac_scalar(Ctx* c, const uint64_t* in, uint32_t R, const uint64_t* w, const uint64_t* ws, uint64_t* out,
+               uint32_t maps, uint32_t B, cudaStream_t s) {
+  const size_t total = (size_t)maps * B * c->kt * c->ct_words();
+  if (!total) return LOLA_OK;
+  ELEM_LAUNCH(KK_ELEM, ke_mac_scalar, total, c->dev, in, R, w, ws, out, maps, B);
+  return post(c);
+}
+
+template <int KQ>
+static int lift_dispatch(Ctx* c, const uint64_t* xq, uint64_t* xb, size_t n_polys, cudaStream_t s) {
+  ELEM_LAUNCH(KK_BASIS, ke_lift_q_to_b<KQ>, n_polys * c->n, c->dev, xq, xb, n_polys);
+  return post(c);
+}
+
+int lift_q_to_b(Ctx* c, const uint64_t* xq, uint64_t* xb, size_t n_polys, cudaStream_t s) {
+  if (c->L <= 4) return lift_dispatch<4>(c, xq, xb, n_polys, s);
+  if (c->L <= 8) return lift_dispatch<8>(c, xq, xb, n_polys, s);
+  return lift_dispatch<12>(c, xq, xb, n_polys, s);
+}
+
+int tensor(Ctx* c, const uint64_t* xq, const uint64_t* xb, const uint64_t* yq, const uint64_t* yb, uint64_t* T,
+           size_t count, cudaStream_t s) {
+  ELEM_LAUNCH(KK_ELEM, ke_tensor, count * (c->L + c->M) * c->n, c->dev, xq, xb, yq, yb, T, count);
+  return post(c);
+}
+
+template <int KQ, int KB>
+static int scale_dispatch(Ctx* c, const uint64_t* T, const uint32_t* tidx, uint32_t div, uint64_t* E, uint64_t* DIG,
+                          size_t count, cudaStream_t s) {
+  ELEM_LAUNCH(KK_BASIS, (ke_scale_round<KQ, KB>), count * 3 * c->n, c->dev, T, tidx, div, E, DIG, count);
+  return post(c);
+}
+
+int scale_round(Ctx* c, const uint64_t* T, const uint32_t* d_tidx, uint32_t tidx_div, uint64_t* E, uint64_t* DIG,
+                size_t count, cudaStream_t s) {
+  if (c->L <= 4 && c->M <= 4) return scale_dispatch<4, 4>(c, T, d_tidx, tidx_div, E, DIG, count, s);
+  if (c->L <= 8 && c->M <= 8) return scale_dispatch<8, 8>(c, T, d_tidx, tidx_div, E, DIG, count, s);
+  return scale_dispatch<12, 16>(c, T, d_tidx, tidx_div, E, DIG, count, s);
+}
+
+int decrypt_round(Ctx* c, const uint64_t* x, const uint32_t* d_tidx, uint64_t* m, size_t n_polys, cudaStream_t s) {
+  if (c->L <= 4) {
+    ELEM_LAUNCH(KK_BASIS, ke_decrypt_round<4>, n_polys * c->n, c->dev, x, d_tidx, m, n_polys);
+  } else if (c->L <= 8) {
+    ELEM_LAUNCH(KK_BASIS, ke_decrypt_round<8>, n_polys * c->n, c->dev, x, d_tidx, m, n_polys);
+  } else {
+    ELEM_LAUNCH(KK_BASIS, ke_decrypt_round<12>, n_polys * c->n, c->dev, x, d_tidx, m, n_polys);
+  }
+  return post(c);
+}
+
+int enc_combine(Ctx* c, const uint64_t* M1, const uint64_t* E2, const uint64_t* U, const uint64_t* pk, uint64_t* out,
+                size_t count, cudaStream_t s) {
+  ELEM_LAUNCH(KK_ELEM, ke_enc_combine, count * c->ct_words(), c->dev, M1, E2, U, pk, out, count);
+  return post(c);
+}
+
+int dec_phase(Ctx* c, const uint64_t* ct, const uint64_t* s_mont, uint64_t* out, size_t count, cudaStream_t s) {
+  ELEM_LAUNCH(KK_ELEM, ke_dec_phase, count * c->L * c->n, c->dev, ct, s_mont, out, count);
+  return post(c);
+}
+
+}  // namespace k
+}  // namespace lola

@@ -1,0 +1,66 @@
+// BFV operations composed from the kernels (host orchestration).
+#pragma once
+#include "internal.h"
+#include "kernels.h"
+
+namespace lola {
+
+int ctx_create(const lola_params* p, int device, Ctx** out);
+void ctx_destroy(Ctx* c);
+int profile_enable(Ctx* c, int kind, int on);
+int profile_read(Ctx* c, int kind, double* ms, uint64_t* launches);
+const char* last_error();
+
+struct EvalKeys {
+  std::shared_ptr<SwitchKey> relin;
+  std::map<uint32_t, std::shared_ptr<SwitchKey>> galois;   // Galois element -> key
+};
+
+struct KeySet {
+  Ctx* ctx = nullptr;
+  bool has_secret = false, has_public = false;
+  std::vector<int64_t> s_coeff;      // ternary secret (host)
+  DevBuf s_ntt;                      // [L+K][n] NTT form
+  DevBuf s_mont;                     // [L+K][n] NTT form, Montgomery
+  DevBuf pk;                         // [2][L][n] NTT form, Montgomery
+  std::shared_ptr<EvalKeys> ev;
+  const SwitchKey* galois_key(uint32_t g) const {
+    auto it = ev->galois.find(g);
+    return it == ev->galois.end() ? nullptr : it->second.get();
+  }
+};
+
+int keygen(Ctx* c, uint64_t seed, const int32_t* steps, size_t n_steps, uint32_t flags, KeySet** secret,
+           KeySet** eval);
+int keys_export(Ctx* c, const KeySet* ks, int what, int32_t step, uint64_t* host, size_t* words);
+
+int encrypt(Ctx* c, const KeySet* ks, const int64_t* slots, size_t n_msg, uint64_t seed, uint64_t* d_out,
+            cudaStream_t s);
+int decrypt_residues(Ctx* c, const KeySet* ks, const uint64_t* d_ct, size_t n_msg, uint64_t* host_slots,
+                     cudaStream_t s);
+int to_coeff(Ctx* c, const uint64_t* d_ct, uint64_t* d_out, size_t count, cudaStream_t s);
+int from_coeff(Ctx* c, const uint64_t* d_in, uint64_t* d_out, size_t count, cudaStream_t s);
+
+// Rotation / Galois key switch of `count` ciphertexts.  Either a uniform
+// Galois element + key, or per-entry arrays on the device (entry i / div).
+struct RotSpec {
+  const uint32_t* d_gal = nullptr;
+  uint32_t gal = 0;
+  const uint64_t* const* d_keys = nullptr;
+  const uint64_t* key = nullptr;
+  uint32_t div = 1;
+};
+size_t rotate_scratch_words(const Ctx* c, size_t count);
+int rotate(Ctx* c, const uint64_t* in, uint64_t* out, const uint64_t* accum, size_t count, const RotSpec& r,
+           uint64_t* scratch, cudaStream_t s);
+
+size_t multiply_scratch_words(const Ctx* c, size_t count, bool square);
+int multiply(Ctx* c, const uint64_t* x, const uint64_t* y, uint64_t* out, size_t count, const uint32_t* d_tidx,
+             uint32_t tidx_div, const uint64_t* relin_key, uint64_t* scratch, cudaStream_t s);
+
+// encode slot vectors (host int64 [count][n], plaintext modulus index per
+// entry) into NTT-form Montgomery plaintexts [count][L][n] on the device
+int encode_plaintexts(Ctx* c, const int64_t* slots, const uint32_t* tidx, size_t count, uint64_t* d_out,
+                      cudaStream_t s);
+
+}  // namespace lola

@@ -1,0 +1,94 @@
+// Kernel-side argument structs and the launcher API used by the host code.
+#pragma once
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace lola {
+
+__device__ __forceinline__ uint32_t brev_n(uint32_t k, int logn) { return __brev(k) >> (32 - logn); }
+
+// NTT position whose value lands at position k under a(x) -> a(x^g): the
+// forward transform leaves a(psi^(2 brev(k) + 1)) at position k, and
+// tau_g(a)(psi^e) = a(psi^(e g)).
+__device__ __forceinline__ uint32_t gal_src(uint32_t k, uint32_t g, int logn) {
+  const uint32_t e = 2 * brev_n(k, logn) + 1;
+  const uint32_t e2 = (uint32_t)(((uint64_t)e * g) & ((2ull << logn) - 1));
+  return brev_n((e2 - 1) >> 1, logn);
+}
+
+struct PrimeMap {
+  uint8_t p[32];  // limb l of a polynomial uses prime index p[l]
+};
+
+// Arguments of the key-switching kernels (one batch of `count` ciphertexts).
+struct KsDev {
+  const uint64_t* c0;     // comp-0 addend: ciphertext (c0 limbs read through the Galois map) or e0
+  const uint64_t* c1;     // ciphertext whose c1 is switched (rotation), NTT form
+  const uint64_t* add1;   // comp-1 addend (relinearisation: e1 in ciphertext layout) or null
+  const uint64_t* accum;  // optional ciphertext added to the result (rotate-and-sum) or null
+  uint64_t* out;          // [count][2][L][n]
+  uint64_t* dig;          // scratch / input digits [count][L][n] coefficient form
+  uint64_t* D;            // scratch [count][L][L+K][n]
+  uint64_t* xP;           // scratch [count][2][n]
+  size_t count;
+  const uint32_t* d_gal;  // per-entry Galois element or null (use gal)
+  uint32_t gal;
+  const uint64_t* const* d_keys;  // per-entry key base or null (use key)
+  const uint64_t* key;
+  uint32_t gal_div;       // ciphertext i uses entry i / gal_div
+};
+
+namespace k {
+// NTT family (ntt_kernels.cu)
+int ntt_fwd_map(Ctx* c, const uint64_t* in, uint64_t* out, size_t n_limbpolys, uint32_t limbs, const PrimeMap& pm,
+                cudaStream_t s);
+int ntt_inv_map(Ctx* c, const uint64_t* in, uint64_t* out, size_t n_limbpolys, uint32_t limbs, const PrimeMap& pm,
+                bool mont_fix, cudaStream_t s);
+int ntt_fwd(Ctx* c, uint64_t* data, size_t n_polys, uint32_t limbs, uint32_t prime0, cudaStream_t s);
+int ntt_inv(Ctx* c, uint64_t* data, size_t n_polys, uint32_t limbs, uint32_t prime0, bool mont_fix,
+            cudaStream_t s);
+int ntt_fwd_from_signed(Ctx* c, const int64_t* in, uint64_t* out, size_t n_polys, uint32_t limbs, uint32_t prime0,
+                        cudaStream_t s);
+int encode_lift(Ctx* c, const uint64_t* in, const uint32_t* d_tidx, uint64_t* out, size_t n_polys, uint32_t limbs,
+                bool mont, cudaStream_t s);
+int slots_to_coeff(Ctx* c, const uint64_t* slots, const uint32_t* d_tidx, uint64_t* coeff, size_t n_polys,
+                   cudaStream_t s);
+int coeff_to_slots(Ctx* c, const uint64_t* coeff, const uint32_t* d_tidx, uint64_t* slots, size_t n_polys,
+                   cudaStream_t s);
+int enc_msg(Ctx* c, const uint64_t* m, const int64_t* e1, const uint32_t* d_tidx, uint64_t* out, size_t n_polys,
+            cudaStream_t s);
+int ks_decompose(Ctx* c, const KsDev& a, cudaStream_t s);
+int ks_modup(Ctx* c, const KsDev& a, bool skip_diag, cudaStream_t s);
+int ks_ip_p(Ctx* c, const KsDev& a, cudaStream_t s);
+int ks_moddown(Ctx* c, const KsDev& a, cudaStream_t s);
+
+// element-wise / basis conversion (elem_kernels.cu)
+int ks_ip_q(Ctx* c, const KsDev& a, cudaStream_t s);   // K = 0 output stage
+int add(Ctx* c, const uint64_t* a, const uint64_t* b, uint64_t* out, size_t count, cudaStream_t s);
+int sub(Ctx* c, const uint64_t* a, const uint64_t* b, uint64_t* out, size_t count, cudaStream_t s);
+int to_mont_map(Ctx* c, uint64_t* data, size_t n_limbpolys, uint32_t limbs, const PrimeMap& pm, cudaStream_t s,
+                bool inverse = false);
+int axpy_mont_map(Ctx* c, const uint64_t* a, const uint64_t* b, const uint64_t* w_mont, uint64_t* out,
+                  size_t n_limbpolys, uint32_t limbs, const PrimeMap& pm, cudaStream_t s);
+int neg_axpe(Ctx* c, const uint64_t* a, const uint64_t* s_mont, const uint64_t* e, uint64_t* out, uint32_t limbs,
+             cudaStream_t s);
+int keygen_switch(Ctx* c, const uint64_t* a, const uint64_t* e, const uint64_t* s_mont, const uint64_t* sfrom,
+                  uint64_t* out, cudaStream_t s);
+int gal_permute(Ctx* c, const uint64_t* in, uint64_t* out, size_t n_limbpolys, uint32_t g, cudaStream_t s);
+int mul_plain_multi(Ctx* c, const uint64_t* in, const uint64_t* pt, uint64_t* out, uint32_t R, uint32_t B,
+                    cudaStream_t s);
+int mac_scalar(Ctx* c, const uint64_t* in, uint32_t R, const uint64_t* w, const uint64_t* ws, uint64_t* out,
+               uint32_t maps, uint32_t B, cudaStream_t s);
+int lift_q_to_b(Ctx* c, const uint64_t* xq, uint64_t* xb, size_t n_polys, cudaStream_t s);
+int tensor(Ctx* c, const uint64_t* xq, const uint64_t* xb, const uint64_t* yq, const uint64_t* yb, uint64_t* T,
+           size_t count, cudaStream_t s);
+int scale_round(Ctx* c, const uint64_t* T, const uint32_t* d_tidx, uint32_t tidx_div, uint64_t* E, uint64_t* DIG,
+                size_t count, cudaStream_t s);
+int decrypt_round(Ctx* c, const uint64_t* x, const uint32_t* d_tidx, uint64_t* m, size_t n_polys, cudaStream_t s);
+int enc_combine(Ctx* c, const uint64_t* M1, const uint64_t* E2, const uint64_t* U, const uint64_t* pk, uint64_t* out,
+                size_t count, cudaStream_t s);
+int dec_phase(Ctx* c, const uint64_t* ct, const uint64_t* s_mont, uint64_t* out, size_t count, cudaStream_t s);
+}  // namespace k
+
+}  // namespace lola

@@ -1,0 +1,592 @@
+// Compiles a LoLa layer list (paper Sec. 4.2-4.4, Tables 1 and 3) into waves
+// of batched ciphertext operations and runs them.
+//
+// Every layer is expressed with five batched ops: scalar multiply-accumulate
+// (convolution row-major), rotation waves (with an optional fused
+// accumulate: x + rot(x, s) is one key switch + one add in the same
+// kernel), message sums, ct x plaintext and square (ct (x) ct +
+// relinearisation).  Independent rotations of one layer (the rounds of a
+// stacked row-major product, the outputs of an interleaved row-major
+// product, the messages being combined) run in the same wave, so one launch
+// carries many ciphertexts and one key read serves all of them.
+#include <string.h>
+
+#include <algorithm>
+#include <set>
+
+#include "net.h"
+
+namespace lola {
+
+#define TRY(x)                      \
+  do {                              \
+    int _rc = (x);                  \
+    if (_rc != LOLA_OK) return _rc; \
+  } while (0)
+
+// ------------------------------------------------------------ compile state
+struct Repr {
+  lola_repr kind = LOLA_REPR_DENSE;
+  int reg = -1;
+  uint32_t msgs = 0;
+  std::vector<std::pair<uint32_t, uint32_t>> pos;   // element -> (message, slot)
+  uint32_t block = 0, copies = 0;
+};
+
+struct Builder {
+  Ctx* c;
+  Net* net;
+  std::vector<std::vector<int64_t>> pts;   // plaintext slot vectors, in block order
+  std::vector<uint64_t> w, ws;             // MAC tables
+  std::set<int32_t> steps;
+
+  int vreg(uint32_t msgs) {
+    net->vreg_msgs.push_back(msgs);
+    return (int)net->vreg_msgs.size() - 1;
+  }
+  // dst[0..k) = (accum ? accum : 0) + rot(src, step_i)
+  void rot(int dst, int src, int accum, uint32_t msgs, const std::vector<int32_t>& st) {
+    Op o;
+    o.kind = OP_ROT;
+    o.dst = dst;
+    o.src = src;
+    o.aux = accum;
+    o.msgs = msgs;
+    o.steps = st;
+    for (int32_t s : st) steps.insert(s);
+    net->ops.push_back(o);
+  }
+  // x <- x + rot(x, s) for s in shifts, on all `msgs` messages of x
+  int rotate_and_sum(int x, uint32_t msgs, const std::vector<int32_t>& shifts) {
+    for (int32_t s : shifts) {
+      const int y = vreg(msgs);
+      rot(y, x, x, msgs, std::vector<int32_t>(msgs, s));
+      x = y;
+    }
+    return x;
+  }
+  size_t add_plaintexts(const std::vector<std::vector<int64_t>>& v) {
+    const size_t first = pts.size();
+    for (auto& p : v) pts.push_back(p);
+    return first;
+  }
+};
+
+static int layer_conv(Builder& b, const lola_layer& L, Repr& r) {
+  const uint32_t n = b.c->n;
+  if (r.kind != LOLA_REPR_CONVOLUTION) return fail(LOLA_E_REPR, "conv layer needs the convolution representation");
+  if (!L.weights || L.cols != r.msgs || L.rows == 0) return fail(LOLA_E_PARAM, "conv weights must be maps x window");
+  const uint32_t maps = L.rows, R = L.cols;
+  Op o;
+  o.kind = OP_MAC;
+  o.src = r.reg;
+  o.dst = b.vreg(maps);
+  o.msgs = maps;
+  o.R = R;
+  o.w_first = b.w.size();
+  const uint32_t kt = b.c->kt, Lq = b.c->L;
+  for (uint32_t m = 0; m < maps; ++m)
+    for (uint32_t j = 0; j < R; ++j)
+      for (uint32_t ti = 0; ti < kt; ++ti) {
+        const int64_t t = (int64_t)b.c->primes[b.c->iT() + ti];
+        int64_t v = L.weights[(size_t)m * R + j] % t;   // centered lift mod t (Sec. 3.1 scalar)
+        if (v < 0) v += t;
+        if (v > (t - 1) / 2) v -= t;
+        for (uint32_t l = 0; l < Lq; ++l) {
+          const uint64_t q = b.c->primes[l];
+          const uint64_t x = v >= 0 ? (uint64_t)v % q : (q - ((uint64_t)(-v) % q)) % q;
+          b.w.push_back(x);
+          b.ws.push_back(shoup_h(x, q));
+        }
+      }
+  b.net->ops.push_back(o);
+  const uint32_t width = (uint32_t)r.pos.size();
+  Repr out;
+  out.kind = LOLA_REPR_DENSE;
+  out.reg = o.dst;
+  out.msgs = maps;
+  for (uint32_t m = 0; m < maps; ++m)
+    for (uint32_t i = 0; i < width; ++i) out.pos.push_back({m, r.pos[i].second});
+  for (auto& p : out.pos)
+    if (p.second >= n) return fail(LOLA_E_PARAM, "slot out of range");
+  r = out;
+  return LOLA_OK;
+}
+
+static int layer_combine(Builder& b, const lola_layer& L, Repr& r) {
+  const uint32_t h = b.c->n / 2;
+  if (r.kind != LOLA_REPR_DENSE && r.kind != LOLA_REPR_INTERLEAVED)
+    return fail(LOLA_E_REPR, "combine needs dense messages");
+  Repr out = r;
+  out.msgs = 1;
+  std::set<uint32_t> used;
+  for (auto& p : out.pos) {
+    const uint64_t slot = (uint64_t)p.second + (uint64_t)p.first * L.stride;
+    if (p.second >= h || slot >= h) return fail(LOLA_E_PARAM, "combine would wrap a slot row");
+    if (!used.insert((uint32_t)slot).second) return fail(LOLA_E_PARAM, "combine positions collide");
+    p = {0, (uint32_t)slot};
+  }
+  if (r.msgs > 1) {
+    const uint32_t k = r.msgs - 1;
+    const int tmp = b.vreg(k);
+    std::vector<int32_t> st;
+    for (uint32_t m = 1; m <= k; ++m) st.push_back((int32_t)(m * L.stride));
+    Op ro;
+    b.rot(tmp, r.reg, -1, k, st);
+    b.net->ops.back().src_off = 1;
+    Op so;
+    so.kind = OP_SUM;
+    so.dst = b.vreg(1);
+    so.src = tmp;
+    so.msgs = k;
+    so.aux = r.reg;
+    so.aux_off = 0;
+    b.net->ops.push_back(so);
+    out.reg = so.dst;
+  }
+  r = out;
+  return LOLA_OK;
+}
+
+static int layer_square(Builder& b, const lola_layer&, Repr& r) {
+  Op o;
+  o.kind = OP_SQUARE;
+  o.src = r.reg;
+  o.dst = b.vreg(r.msgs);
+  o.msgs = r.msgs;
+  b.net->ops.push_back(o);
+  b.net->needs_relin = true;
+  r.reg = o.dst;
+  return LOLA_OK;
+}
+
+static int layer_stack(Builder& b, const lola_layer& L, Repr& r) {
+  const uint32_t n = b.c->n, h = n / 2, s = 1u << L.d;
+  if (r.msgs != 1 || (r.kind != LOLA_REPR_DENSE && r.kind != LOLA_REPR_INTERLEAVED))
+    return fail(LOLA_E_REPR, "stack needs one dense message");
+  if (L.d > 14 || L.copies == 0 || (L.copies & (L.copies - 1)) || (uint64_t)L.copies * s > n)
+    return fail(LOLA_E_PARAM, "stack: copies must be a power of two with copies * 2^d <= n");
+  for (auto& p : r.pos)
+    if (p.second >= s) return fail(LOLA_E_PARAM, "stack: vector must fit in one block of 2^d slots");
+  const uint32_t per_row = std::min<uint32_t>(L.copies, std::max<uint32_t>(1, h / s));
+  std::vector<int32_t> shifts;
+  for (uint32_t sh = s; sh < per_row * s; sh *= 2) shifts.push_back((int32_t)sh);
+  if (L.copies > per_row) shifts.push_back(0);   // row swap
+  r.reg = b.rotate_and_sum(r.reg, 1, shifts);
+  r.kind = LOLA_REPR_STACKED;
+  r.block = s;
+  r.copies = L.copies;
+  return LOLA_OK;
+}
+
+static uint32_t stacked_out_slot(uint32_t n, uint32_t s, uint32_t blk, uint32_t rnd) {
+  const uint32_t h = n / 2, base = blk * s + s - 1;
+  return (base / h) * h + (base % h + rnd) % h;
+}
+
+static int layer_stacked_rowmajor(Builder& b, const lola_layer& L, Repr& r) {
+  const uint32_t n = b.c->n;
+  if (r.kind != LOLA_REPR_STACKED || r.msgs != 1) return fail(LOLA_E_REPR, "stacked row-major needs a stacked vector");
+  const uint32_t s = 1u << L.d;
+  if (s != r.block || L.copies != r.copies) return fail(LOLA_E_REPR, "stacked layout (d, copies) mismatch");
+  if (!L.weights || L.cols != r.pos.size() || L.rows == 0) return fail(LOLA_E_PARAM, "weights must be rows x vector length");
+  const uint32_t rows = L.rows, c = L.copies;
+  const uint32_t R = (rows + c - 1) / c;
+  if (R > s) return fail(LOLA_E_PARAM, "too many rounds for the block size");
+  std::vector<std::vector<int64_t>> P(R, std::vector<int64_t>(n, 0));
+  for (uint32_t rd = 0; rd < R; ++rd)
+    for (uint32_t blk = 0; blk < c; ++blk) {
+      const uint32_t row = rd * c + blk;
+      if (row >= rows) continue;
+      for (uint32_t i = 0; i < L.cols; ++i) P[rd][(size_t)blk * s + r.pos[i].second] = L.weights[(size_t)row * L.cols + i];
+    }
+  Op mp;
+  mp.kind = OP_MULPT;
+  mp.src = r.reg;
+  mp.src_stride = 0;
+  mp.dst = b.vreg(R);
+  mp.msgs = R;
+  mp.pt_first = b.add_plaintexts(P);
+  b.net->ops.push_back(mp);
+  std::vector<int32_t> shifts;
+  for (uint32_t j = 0; j < L.d; ++j) shifts.push_back((int32_t)(1u << j));
+  int y = b.rotate_and_sum(mp.dst, R, shifts);
+  Repr out;
+  out.kind = LOLA_REPR_INTERLEAVED;
+  out.msgs = 1;
+  if (R == 1) {
+    out.reg = y;
+    for (uint32_t row = 0; row < rows; ++row) out.pos.push_back({0, stacked_out_slot(n, s, row, 0)});
+    r = out;
+    return LOLA_OK;
+  }
+  // mask each round's block ends, rotate round rd right by rd, add
+  std::vector<std::vector<int64_t>> M(R, std::vector<int64_t>(n, 0));
+  for (uint32_t rd = 0; rd < R; ++rd)
+    for (uint32_t blk = 0; blk < c; ++blk)
+      if (rd * c + blk < rows) M[rd][(size_t)blk * s + s - 1] = 1;
+  Op mk;
+  mk.kind = OP_MULPT;
+  mk.src = y;
+  mk.src_stride = 1;
+  mk.dst = b.vreg(R);
+  mk.msgs = R;
+  mk.pt_first = b.add_plaintexts(M);
+  b.net->ops.push_back(mk);
+  const int tmp = b.vreg(R - 1);
+  std::vector<int32_t> st;
+  for (uint32_t rd = 1; rd < R; ++rd) st.push_back((int32_t)rd);
+  b.rot(tmp, mk.dst, -1, R - 1, st);
+  b.net->ops.back().src_off = 1;
+  Op so;
+  so.kind = OP_SUM;
+  so.dst = b.vreg(1);
+  so.src = tmp;
+  so.msgs = R - 1;
+  so.aux = mk.dst;
+  so.aux_off = 0;
+  b.net->ops.push_back(so);
+  out.reg = so.dst;
+  for (uint32_t o = 0; o < rows; ++o) out.pos.push_back({0, stacked_out_slot(n, s, o % c, o / c)});
+  r = out;
+  return LOLA_OK;
+}
+
+static int layer_rowmajor_sparse(Builder& b, const lola_layer& L, Repr& r, bool dense_only) {
+  const uint32_t n = b.c->n;
+  if (r.msgs != 1) return fail(LOLA_E_REPR, "row-major product needs one message");
+  if (dense_only && r.kind != LOLA_REPR_DENSE) return fail(LOLA_E_REPR, "dense row-major needs a dense vector");
+  if (!dense_only && r.kind != LOLA_REPR_INTERLEAVED && r.kind != LOLA_REPR_DENSE)
+    return fail(LOLA_E_REPR, "interleaved row-major needs an interleaved vector");
+  if (!L.weights || L.cols != r.pos.size() || L.rows == 0) return fail(LOLA_E_PARAM, "weights must be rows x vector length");
+  const uint32_t rows = L.rows;
+  std::vector<std::vector<int64_t>> V(rows, std::vector<int64_t>(n, 0));
+  for (uint32_t o = 0; o < rows; ++o)
+    for (uint32_t i = 0; i < L.cols; ++i) V[o][r.pos[i].second] = L.weights[(size_t)o * L.cols + i];
+  Op mp;
+  mp.kind = OP_MULPT;
+  mp.src = r.reg;
+  mp.src_stride = 0;
+  mp.dst = b.vreg(rows);
+  mp.msgs = rows;
+  mp.pt_first = b.add_plaintexts(V);
+  b.net->ops.push_back(mp);
+  std::vector<int32_t> shifts;
+  for (uint32_t sh = 1; sh < n / 2; sh *= 2) shifts.push_back((int32_t)sh);
+  shifts.push_back(0);
+  Repr out;
+  out.kind = LOLA_REPR_SPARSE;
+  out.msgs = rows;
+  out.reg = b.rotate_and_sum(mp.dst, rows, shifts);
+  for (uint32_t o = 0; o < rows; ++o) out.pos.push_back({o, 0});
+  r = out;
+  return LOLA_OK;
+}
+
+Net::~Net() {}
+
+int net_create(Ctx* c, const lola_input* in, const lola_layer* layers, size_t n_layers, Net** out) {
+  if (!in || (!layers && n_layers) || !out) return fail(LOLA_E_PARAM, "null argument");
+  *out = nullptr;
+  std::unique_ptr<Net> net(new Net());
+  net->ctx = c;
+  Builder b{c, net.get(), {}, {}, {}, {}};
+  Repr r;
+  r.kind = in->repr;
+  r.msgs = in->n_msgs;
+  if (in->n_msgs == 0 || in->n_elems == 0) return fail(LOLA_E_PARAM, "empty input");
+  for (uint32_t i = 0; i < in->n_elems; ++i) {
+    const uint32_t slot = in->slot ? in->slot[i] : i;
+    if (slot >= c->n) return fail(LOLA_E_PARAM, "input slot out of range");
+    r.pos.push_back({0, slot});
+  }
+  if (in->repr == LOLA_REPR_STACKED) {
+    r.block = 1u << in->d;
+    r.copies = in->copies;
+  }
+  r.reg = b.vreg(in->n_msgs);
+  net->in_reg = r.reg;
+  net->n_in = in->n_msgs;
+  for (size_t li = 0; li < n_layers; ++li) {
+    const lola_layer& L = layers[li];
+    if (L.in_repr && L.in_repr != r.kind)
+      return fail(LOLA_E_REPR, "layer " + std::to_string(li) + ": input representation mismatch");
+    int rc;
+    switch (L.op) {
+      case LOLA_LAYER_CONV_ROWMAJOR: rc = layer_conv(b, L, r); break;
+      case LOLA_LAYER_COMBINE: rc = layer_combine(b, L, r); break;
+      case LOLA_LAYER_SQUARE: rc = layer_square(b, L, r); break;
+      case LOLA_LAYER_STACK: rc = layer_stack(b, L, r); break;
+      case LOLA_LAYER_STACKED_ROWMAJOR: rc = layer_stacked_rowmajor(b, L, r); break;
+      case LOLA_LAYER_INTERLEAVED_ROWMAJOR: rc = layer_rowmajor_sparse(b, L, r, false); break;
+      case LOLA_LAYER_DENSE_ROWMAJOR: rc = layer_rowmajor_sparse(b, L, r, true); break;
+      default: return fail(LOLA_E_PARAM, "unknown layer op");
+    }
+    if (rc != LOLA_OK) return rc;
+    if (L.out_repr && L.out_repr != r.kind)
+      return fail(LOLA_E_REPR, "layer " + std::to_string(li) + ": output representation mismatch");
+  }
+  net->out_reg = r.reg;
+  net->n_out = r.msgs;
+  for (auto& p : r.pos) {
+    net->out_msg.push_back(p.first);
+    net->out_slot.push_back(p.second);
+  }
+  net->steps_needed.assign(b.steps.begin(), b.steps.end());
+  // encode plaintexts for every t_i: blocks [pt][kt][L][n]
+  const size_t kt = c->kt, n = c->n, Lq = c->L;
+  net->n_pt_blocks = b.pts.size();
+  if (!b.pts.empty()) {
+    TRY(net->pt.alloc(b.pts.size() * kt * Lq * n * 8));
+    std::vector<int64_t> slots;
+    std::vector<uint32_t> tidx;
+    const size_t chunk = 64;
+    for (size_t p0 = 0; p0 < b.pts.size(); p0 += chunk) {
+      const size_t p1 = std::min(b.pts.size(), p0 + chunk);
+      slots.clear();
+      tidx.clear();
+      for (size_t p = p0; p < p1; ++p)
+        for (size_t ti = 0; ti < kt; ++ti) {
+          slots.insert(slots.end(), b.pts[p].begin(), b.pts[p].end());
+          tidx.push_back((uint32_t)ti);
+        }
+      TRY(encode_plaintexts(c, slots.data(), tidx.data(), (p1 - p0) * kt, net->pt.u64() + p0 * kt * Lq * n, nullptr));
+    }
+  }
+  if (!b.w.empty()) {
+    TRY(net->w.alloc(b.w.size() * 8));
+    TRY(net->ws.alloc(b.ws.size() * 8));
+    LOLA_CUDA_TRY(cudaMemcpy(net->w.p, b.w.data(), b.w.size() * 8, cudaMemcpyHostToDevice));
+    LOLA_CUDA_TRY(cudaMemcpy(net->ws.p, b.ws.data(), b.ws.size() * 8, cudaMemcpyHostToDevice));
+  }
+  *out = net.release();
+  return LOLA_OK;
+}
+
+// ------------------------------------------------------------------- executor
+struct Executor {
+  uint32_t B = 0;
+  std::vector<DevBuf> phys;            // physical register buffers
+  std::vector<int> vmap;               // virtual -> physical
+  DevBuf scratch;
+  DevBuf tid_pattern;                  // i % kt
+  const KeySet* keys = nullptr;        // key set the device tables were built for
+  std::vector<DevBuf> op_gal, op_keys; // per-op per-message tables (non-uniform rotations)
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  ~Executor() {
+    if (graph) cudaGraphExecDestroy(graph);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+  }
+};
+
+static int build_executor(Ctx* c, Net* net, uint32_t B, Executor* ex) {
+  ex->B = B;
+  const size_t kt = c->kt, ctw = c->ct_words();
+  const size_t msg_words = (size_t)B * kt * ctw;
+  // liveness: last op index using each vreg
+  const int nv = (int)net->vreg_msgs.size();
+  std::vector<int> last(nv, -1), first(nv, (int)net->ops.size());
+  first[net->in_reg] = -1;
+  for (int i = 0; i < (int)net->ops.size(); ++i) {
+    const Op& o = net->ops[i];
+    for (int v : {o.src, o.aux})
+      if (v >= 0) last[v] = std::max(last[v], i);
+    if (o.dst >= 0) first[o.dst] = std::min(first[o.dst], i);
+  }
+  last[net->out_reg] = (int)net->ops.size();
+  ex->vmap.assign(nv, -1);
+  std::vector<uint32_t> phys_msgs;
+  std::vector<int> phys_free_after;   // op index after which the buffer is free
+  auto assign = [&](int v, int at) {
+    int best = -1;
+    for (int p = 0; p < (int)phys_msgs.size(); ++p)
+      if (phys_free_after[p] < at && phys_msgs[p] >= net->vreg_msgs[v] &&
+          (best < 0 || phys_msgs[p] < phys_msgs[best]))
+        best = p;
+    if (best < 0) {
+      phys_msgs.push_back(net->vreg_msgs[v]);
+      phys_free_after.push_back(0);
+      best = (int)phys_msgs.size() - 1;
+    }
+    ex->vmap[v] = best;
+    phys_free_after[best] = std::max(last[v], at);
+  };
+  assign(net->in_reg, -1);
+  for (int i = 0; i < (int)net->ops.size(); ++i) {
+    const int d = net->ops[i].dst;
+    if (d >= 0 && ex->vmap[d] < 0) assign(d, i);
+  }
+  ex->phys.resize(phys_msgs.size());
+  for (size_t p = 0; p < phys_msgs.size(); ++p) TRY(ex->phys[p].alloc(phys_msgs[p] * msg_words * 8));
+  // scratch: largest op requirement
+  size_t sw = 0, maxcnt = 1;
+  for (const Op& o : net->ops) {
+    const size_t cnt = (size_t)o.msgs * B * kt;
+    maxcnt = std::max(maxcnt, cnt);
+    if (o.kind == OP_ROT) sw = std::max(sw, rotate_scratch_words(c, cnt) + 2 * o.msgs);
+    if (o.kind == OP_SQUARE) sw = std::max(sw, multiply_scratch_words(c, cnt, true));
+  }
+  TRY(ex->scratch.alloc(sw * 8));
+  std::vector<uint32_t> pat(maxcnt);
+  for (size_t i = 0; i < maxcnt; ++i) pat[i] = (uint32_t)(i % kt);
+  TRY(ex->tid_pattern.alloc(maxcnt * 4));
+  LOLA_CUDA_TRY(cudaMemcpy(ex->tid_pattern.p, pat.data(), maxcnt * 4, cudaMemcpyHostToDevice));
+  return LOLA_OK;
+}
+
+static int bind_keys(Ctx* c, Net* net, Executor* ex, const KeySet* ks) {
+  if (ex->keys == ks) return LOLA_OK;
+  if (net->needs_relin && !ks->ev->relin) return fail(LOLA_E_NOKEY, "network squares but no relinearisation key");
+  ex->op_gal.clear();
+  ex->op_keys.clear();
+  ex->op_gal.resize(net->ops.size());
+  ex->op_keys.resize(net->ops.size());
+  for (size_t i = 0; i < net->ops.size(); ++i) {
+    const Op& o = net->ops[i];
+    if (o.kind != OP_ROT) continue;
+    std::vector<uint32_t> g(o.msgs);
+    std::vector<const uint64_t*> kp(o.msgs);
+    for (uint32_t m = 0; m < o.msgs; ++m) {
+      g[m] = galois_for_step(c->n, o.steps[m]);
+      const SwitchKey* key = ks->galois_key(g[m]);
+      if (!key) return fail(LOLA_E_NOKEY, "missing Galois key for rotation step " + std::to_string(o.steps[m]));
+      kp[m] = key->buf.u64();
+    }
+    TRY(ex->op_gal[i].alloc(o.msgs * 4));
+    TRY(ex->op_keys[i].alloc(o.msgs * 8));
+    LOLA_CUDA_TRY(cudaMemcpy(ex->op_gal[i].p, g.data(), o.msgs * 4, cudaMemcpyHostToDevice));
+    LOLA_CUDA_TRY(cudaMemcpy(ex->op_keys[i].p, kp.data(), o.msgs * 8, cudaMemcpyHostToDevice));
+  }
+  if (ex->graph) {
+    cudaGraphExecDestroy(ex->graph);
+    ex->graph = nullptr;
+  }
+  ex->keys = ks;
+  return LOLA_OK;
+}
+
+static int run_ops(Ctx* c, Net* net, Executor* ex, const KeySet* ks, cudaStream_t s) {
+  const size_t kt = c->kt, ctw = c->ct_words();
+  const uint32_t B = ex->B;
+  const size_t msg_words = (size_t)B * kt * ctw;
+  auto reg = [&](int v, uint32_t off) { return ex->phys[ex->vmap[v]].u64() + (size_t)off * msg_words; };
+  for (size_t i = 0; i < net->ops.size(); ++i) {
+    const Op& o = net->ops[i];
+    const size_t cnt = (size_t)o.msgs * B * kt;
+    switch (o.kind) {
+      case OP_MAC:
+        TRY(k::mac_scalar(c, reg(o.src, o.src_off), o.R, net->w.u64() + o.w_first, net->ws.u64() + o.w_first,
+                          reg(o.dst, o.dst_off), o.msgs, B, s));
+        break;
+      case OP_ROT: {
+        RotSpec rs;
+        const bool uniform = std::all_of(o.steps.begin(), o.steps.end(), [&](int32_t x) { return x == o.steps[0]; });
+        if (uniform) {
+          rs.gal = galois_for_step(c->n, o.steps[0]);
+          rs.key = ks->galois_key(rs.gal)->buf.u64();
+        } else {
+          rs.d_gal = (const uint32_t*)ex->op_gal[i].p;
+          rs.d_keys = (const uint64_t* const*)ex->op_keys[i].p;
+          rs.div = (uint32_t)(B * kt);
+        }
+        TRY(rotate(c, reg(o.src, o.src_off), reg(o.dst, o.dst_off), o.aux >= 0 ? reg(o.aux, o.aux_off) : nullptr, cnt,
+                   rs, ex->scratch.u64(), s));
+        break;
+      }
+      case OP_SUM: {
+        uint64_t* d = reg(o.dst, o.dst_off);
+        const size_t per = (size_t)B * kt;
+        if (o.aux >= 0) {
+          TRY(k::add(c, reg(o.aux, o.aux_off), reg(o.src, o.src_off), d, per, s));
+        } else {
+          LOLA_CUDA_TRY(cudaMemcpyAsync(d, reg(o.src, o.src_off), msg_words * 8, cudaMemcpyDeviceToDevice, s));
+        }
+        for (uint32_t m = (o.aux >= 0 ? 1 : 1); m < o.msgs; ++m)
+          TRY(k::add(c, d, reg(o.src, o.src_off + m), d, per, s));
+        break;
+      }
+      case OP_MULPT: {
+        const uint64_t* pt = net->pt.u64() + o.pt_first * kt * c->L * c->n;
+        if (o.src_stride == 0) {
+          TRY(k::mul_plain_multi(c, reg(o.src, o.src_off), pt, reg(o.dst, o.dst_off), o.msgs, B, s));
+        } else {
+          for (uint32_t m = 0; m < o.msgs; ++m)
+            TRY(k::mul_plain_multi(c, reg(o.src, o.src_off + m), pt + (size_t)m * kt * c->L * c->n,
+                                   reg(o.dst, o.dst_off + m), 1, B, s));
+        }
+        break;
+      }
+      case OP_SQUARE:
+        TRY(multiply(c, reg(o.src, o.src_off), reg(o.src, o.src_off), reg(o.dst, o.dst_off), cnt,
+                     (const uint32_t*)ex->tid_pattern.p, 1, ks->ev->relin->buf.u64(), ex->scratch.u64(), s));
+        break;
+    }
+  }
+  return LOLA_OK;
+}
+
+// request-major lola_ct layout [b][g][t] <-> register layout [g][b][t]
+static int transpose_msgs(uint64_t* dst, const uint64_t* src, uint32_t G, uint32_t B, size_t blk_words, bool to_reg,
+                          cudaStream_t s) {
+  if (G == 1 || B == 1) {
+    LOLA_CUDA_TRY(cudaMemcpyAsync(dst, src, (size_t)G * B * blk_words * 8, cudaMemcpyDeviceToDevice, s));
+    return LOLA_OK;
+  }
+  for (uint32_t g = 0; g < G; ++g) {
+    const size_t bytes = blk_words * 8;
+    if (to_reg) {
+      LOLA_CUDA_TRY(cudaMemcpy2DAsync(dst + (size_t)g * B * blk_words, bytes, src + (size_t)g * blk_words,
+                                      (size_t)G * bytes, bytes, B, cudaMemcpyDeviceToDevice, s));
+    } else {
+      LOLA_CUDA_TRY(cudaMemcpy2DAsync(dst + (size_t)g * blk_words, (size_t)G * bytes, src + (size_t)g * B * blk_words,
+                                      bytes, bytes, B, cudaMemcpyDeviceToDevice, s));
+    }
+  }
+  return LOLA_OK;
+}
+
+int net_eval(Ctx* c, const KeySet* ks, Net* net, const uint64_t* d_in, size_t in_msgs, uint64_t* d_out,
+             size_t out_msgs, cudaStream_t s, bool use_graph) {
+  if (in_msgs == 0 || in_msgs % net->n_in) return fail(LOLA_E_PARAM, "input message count is not a multiple of the network input");
+  const uint32_t B = (uint32_t)(in_msgs / net->n_in);
+  if (out_msgs != (size_t)B * net->n_out) return fail(LOLA_E_PARAM, "output ciphertext has the wrong message count");
+  auto& slot = net->exec[B];
+  if (!slot) {
+    std::unique_ptr<Executor> ex(new Executor());
+    TRY(build_executor(c, net, B, ex.get()));
+    slot = std::move(ex);
+  }
+  Executor* ex = slot.get();
+  TRY(bind_keys(c, net, ex, ks));
+  const size_t blk = (size_t)c->kt * c->ct_words();
+  TRY(transpose_msgs(ex->phys[ex->vmap[net->in_reg]].u64(), d_in, net->n_in, B, blk, true, s));
+  const bool profiling = c->prof.on[0] || c->prof.on[1] || c->prof.on[2] || c->prof.on[3];
+  if (use_graph && !profiling) {
+    if (!ex->graph) {
+      if (!ex->cap_stream) LOLA_CUDA_TRY(cudaStreamCreateWithFlags(&ex->cap_stream, cudaStreamNonBlocking));
+      cudaGraph_t g = nullptr;
+      LOLA_CUDA_TRY(cudaStreamBeginCapture(ex->cap_stream, cudaStreamCaptureModeThreadLocal));
+      int rc = run_ops(c, net, ex, ks, ex->cap_stream);
+      cudaError_t e = cudaStreamEndCapture(ex->cap_stream, &g);
+      if (rc != LOLA_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+      }
+      if (e != cudaSuccess) return fail(LOLA_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+      e = cudaGraphInstantiate(&ex->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        ex->graph = nullptr;
+        return fail(LOLA_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+      }
+    }
+    LOLA_CUDA_TRY(cudaGraphLaunch(ex->graph, s));
+  } else {
+    TRY(run_ops(c, net, ex, ks, s));
+  }
+  TRY(transpose_msgs(d_out, ex->phys[ex->vmap[net->out_reg]].u64(), net->n_out, B, blk, false, s));
+  return LOLA_OK;
+}
+
+}  // namespace lola

@@ -1,0 +1,51 @@
+// LoLa network: layer list -> op list over message registers -> executor.
+#pragma once
+#include <map>
+#include <memory>
+#include <vector>
+
+#include "he.h"
+
+namespace lola {
+
+enum OpKind { OP_MAC = 1, OP_ROT = 2, OP_SUM = 3, OP_MULPT = 4, OP_SQUARE = 5 };
+
+// A register holds `msgs` messages for every request of the batch and every
+// plaintext modulus: layout [msg][request][t_i][2][L][n].
+struct Op {
+  OpKind kind;
+  int dst = -1, src = -1, aux = -1;   // virtual registers
+  uint32_t dst_off = 0, src_off = 0, aux_off = 0;
+  uint32_t msgs = 0;                  // messages processed
+  // OP_ROT: per-message rotation step (0 = row swap); aux = accumulator register (or -1)
+  std::vector<int32_t> steps;
+  // OP_MULPT: plaintexts [msgs][kt][L][n] at pt_first (in plaintext blocks); src_stride 0 = broadcast
+  size_t pt_first = 0;
+  uint32_t src_stride = 1;
+  // OP_MAC: R inputs per output, weight table offset (entries [msgs][R][kt][L])
+  uint32_t R = 0;
+  size_t w_first = 0;
+  // OP_SUM: dst = sum of `msgs` messages of src (+ message aux_off of aux if aux >= 0)
+};
+
+struct Net {
+  Ctx* ctx = nullptr;
+  uint32_t n_in = 0, n_out = 0;
+  std::vector<uint32_t> vreg_msgs;    // size of each virtual register (messages)
+  int in_reg = -1, out_reg = -1;
+  std::vector<Op> ops;
+  std::vector<uint32_t> out_msg, out_slot;
+  std::vector<int32_t> steps_needed;  // distinct rotation steps (0 = row swap)
+  bool needs_relin = false;
+  DevBuf pt;                          // encoded plaintexts [blocks][kt][L][n]
+  DevBuf w, ws;                       // MAC scalars and Shoup companions
+  size_t n_pt_blocks = 0;
+  std::map<uint32_t, std::unique_ptr<struct Executor>> exec;   // by batch size
+  ~Net();
+};
+
+int net_create(Ctx* c, const lola_input* in, const lola_layer* layers, size_t n_layers, Net** out);
+int net_eval(Ctx* c, const KeySet* ks, Net* net, const uint64_t* d_in, size_t in_msgs, uint64_t* d_out,
+             size_t out_msgs, cudaStream_t s, bool use_graph);
+
+}  // namespace lola

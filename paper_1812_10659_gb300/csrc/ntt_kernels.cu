@@ -1,0 +1,399 @@
+// NTT-family kernels: every kernel here runs one negacyclic transform per
+// CTA (ntt.cuh) with a kernel-specific loader (what feeds the transform) and
+// storer (what happens to each output word).  Fusing the neighbouring
+// element-wise work into the transform's first load / last store is what
+// keeps each limb to one HBM read and one HBM write.
+#include "internal.h"
+#include "kernels.h"
+#include "ntt.cuh"
+
+namespace lola {
+
+template <int LOGN>
+struct Cfg {
+  static constexpr int LOGE = LOGN >= 14 ? 5 : 4;
+  static constexpr int N = 1 << LOGN;
+  static constexpr int T = N >> LOGE;
+};
+
+#define TW_F(C, p) (C)->tw_fwd + (size_t)(p) * (1u << LOGN), (C)->tw_fwd_s + (size_t)(p) * (1u << LOGN)
+#define TW_I(C, p) (C)->tw_inv + (size_t)(p) * (1u << LOGN), (C)->tw_inv_s + (size_t)(p) * (1u << LOGN)
+
+// ------------------------------------------------------------ plain transforms
+template <int LOGN>
+__global__ void __launch_bounds__(Cfg<LOGN>::T) kn_fwd(const CtxDev* __restrict__ C, const uint64_t* in,
+                                                        uint64_t* out, uint32_t limbs, PrimeMap pm) {
+  extern __shared__ uint64_t sm[];
+  constexpr int N = Cfg<LOGN>::N;
+  const size_t poly = blockIdx.x;
+  const int p = pm.p[poly % limbs];
+  const uint64_t* src = in + poly * N;
+  uint64_t* dst = out + poly * N;
+  ntt_forward<LOGN, Cfg<LOGN>::LOGE>(sm, TW_F(C, p), C->pr[p].q, [&](int i) { return src[i]; },
+                                      [&](int i, uint64_t v) { dst[i] = v; });
+}
+
+template <int LOGN>
+__global__ void __launch_bounds__(Cfg<LOGN>::T) kn_inv(const CtxDev* __restrict__ C, const uint64_t* in,
+                                                        uint64_t* out, uint32_t limbs, PrimeMap pm, int mont_fix) {
+  extern __shared__ uint64_t sm[];
+  constexpr int N = Cfg<LOGN>::N;
+  const size_t poly = blockIdx.x;
+  const int p = pm.p[poly % limbs];
+  const PrimeDev& P = C->pr[p];
+  const uint64_t* src = in + poly * N;
+  uint64_t* dst = out + poly * N;
+  const uint64_t c = mont_fix ? P.ninvr : P.ninv, cs = mont_fix ? P.ninvr_s : P.ninv_s;
+  ntt_inverse<LOGN, Cfg<LOGN>::LOGE>(sm, TW_I(C, p), P.q, c, cs, [&](int i) { return src[i]; },
+                                      [&](int i, uint64_t v) { dst[i] = v; });
+}
+
+// small signed integers (int64 [poly][n]) -> NTT mod each prime of the map
+template <int LOGN>
+__global__ void __launch_bounds__(Cfg<LOGN>::T) kn_fwd_signed(const CtxDev* __restrict__ C, const int64_t* in,
+                                                               uint64_t* out, uint32_t limbs, PrimeMap pm) {
+  extern __shared__ uint64_t sm[];
+  constexpr int N = Cfg<LOGN>::N;
+  const size_t blk = blockIdx.x;
+  const size_t poly = blk / limbs;
+  const int p = pm.p[blk % limbs];
+  const PrimeDev& P = C->pr[p];
+  const int64_t* src = in + poly * N;
+  uint64_t* dst = out + blk * N;
+  ntt_forward<LOGN, Cfg<LOGN>::LOGE>(sm, TW_F(C, p), P.q,
+                                      [&](int i) { return from_signed(src[i], P.q, P.f64); },
+                                      [&](int i, uint64_t v) { dst[i] = v; });
+}
+
+// plaintext polynomial mod t -> centered lift -> mod q_l -> NTT (-> Montgomery)
+template <int LOGN>
+__global__ void __launch_bounds__(Cfg<LOGN>::T) kn_encode_lift(const CtxDev* __restrict__ C, const uint64_t* in,
+                                                                const uint32_t* tidx, uint64_t* out, uint32_t limbs,
+                                                                int mont) {
+  extern __shared__ uint64_t sm[];
+  constexpr int N = Cfg<LOGN>::N;
+  const size_t blk = blockIdx.x;
+  const size_t poly = blk / limbs;
+  const int l = blk % limbs;
+  const PrimeDev& P = C->pr[l];
+  const uint64_t t = C->pr[C->iT + tidx[poly]].q;
+  const uint64_t* src = in + poly * N;
+  uint64_t* dst = out + blk * N;
+  ntt_forward<LOGN, Cfg<LOGN>::LOGE>(
+      sm, TW_F(C, l), P.q,
+      [&](int i) {
+        const uint64_t x = src[i];
+        return x <= (t - 1) / 2 ? reduce64(x, P.q, P.f64) : neg_mod(reduce64(t - x, P.q, P.f64), P.q);
+      },
+      [&](int i, uint64_t v) { dst[i] = mont ? mont_mul(v, P.r2, P.q, P.qinv) : v; });
+}
+
+// slots (mod t) -> plaintext coefficients: inverse transform mod t fed through the slot map
+template <int LOGN>
+__global__ void __launch_bounds__(Cfg<LOGN>::T) kn_slots_to_coeff(const CtxDev* __restrict__ C, const uint64_t* slots,
+                                                                   const uint32_t* tidx, const uint32_t* slot_at_pos,
+                                                                   uint64_t* coeff) {
+  extern __shared__ uint64_t sm[];
+  constexpr int N = Cfg<LOGN>::N;
+  const size_t poly = blockIdx.x;
+  const int p = C->iT + tidx[poly];
+  const PrimeDev& P = C->pr[p];
+  const uint64_t* src = slots + poly * N;
+  uint64_t* dst = coeff + poly * N;
+  ntt_inverse<LOGN, Cfg<LOGN>::LOGE>(sm, TW_I(C, p), P.q, P.ninv, P.ninv_s,
+                                      [&](int i) { return src[slot_at_pos[i]]; },
+                                      [&](int i, uint64_t v) { dst[i] = v; });
+}
+
+template <int LOGN>
+__global__ void __launch_bounds__(Cfg<LOGN>::T) kn_coeff_to_slots(const CtxDev* __restrict__ C, const uint64_t* coeff,
+                                                                   const uint32_t* tidx, const uint32_t* slot_at_pos,
+                                                                   uint64_t* slots) {
+  extern __shared__ uint64_t sm[];
+  constexpr int N = Cfg<LOGN>::N;
+  const size_t poly = blockIdx.x;
+  const int p = C->iT + tidx[poly];
+  const uint64_t* src = coeff + poly * N;
+  uint64_t* dst = slots + poly * N;
+  ntt_forward<LOGN, Cfg<LOGN>::LOGE>(sm, TW_F(C, p), C->pr[p].q, [&](int i) { return src[i]; },
+                                      [&](int i, uint64_t v) { dst[slot_at_pos[i]] = v; });
+}
+
+// encryption: NTT_j(Delta_t * m + e1) per limb (m coefficients mod t, e1 signed)
+template <int LOGN>
+__global__ void __launch_bounds__(Cfg<LOGN>::T) kn_enc_msg(const CtxDev* __restrict__ C, const uint64_t* m,
+                                                            const int64_t* e1, const uint32_t* tidx, uint64_t* out,
+                                                            uint32_t L) {
+  extern __shared__ uint64_t sm[];
+  constexpr int N = Cfg<LOGN>::N;
+  const size_t blk = blockIdx.x;
+  const size_t poly = blk / L;
+  const int j = blk % L;
+  const PrimeDev& P = C->pr[j];
+  const uint32_t ti = tidx[poly];
+  const uint64_t d = C->deltaQ[ti][j], ds = C->deltaQ_s[ti][j];
+  const uint64_t* ms = m + poly * N;
+  const int64_t* es = e1 + poly * N;
+  uint64_t* dst = out + blk * N;
+  ntt_forward<LOGN, Cfg<LOGN>::LOGE>(
+      sm, TW_F(C, j), P.q,
+      [&](int i) { return add_mod(shoup_mul(ms[i], d, ds, P.q), from_signed(es[i], P.q, P.f64), P.q); },
+      [&](int i, uint64_t v) { dst[i] = v; });
+}
+
+// ------------------------------------------------------------- key switching
+// A: permute c1 (NTT form) by the Galois element, keep the permuted limb as
+//    the diagonal block D[i][i], inverse-transform it into digit i.
+template <int LOGN>
+__global__ void __launch_bounds__(Cfg<LOGN>::T) kn_ks_decompose(const CtxDev* __restrict__ C, KsDev a) {
+  extern __shared__ uint64_t sm[];
+  constexpr int N = Cfg<LOGN>::N;
+  const int L = C->L, LK = C->L + C->K;
+  const size_t ct = blockIdx.x / L;
+  const int i = blockIdx.x % L;
+  const uint32_t g = a.d_gal ? a.d_gal[ct / a.gal_div] : a.gal;
+  const uint64_t* src = a.c1 + (ct * 2 * L + L + i) * (size_t)N;
+  uint64_t* diag = a.D + ((ct * L + i) * LK + i) * (size_t)N;
+  uint64_t* dig = a.dig + (ct * L + i) * (size_t)N;
+  const PrimeDev& P = C->pr[i];
+  ntt_inverse<LOGN, Cfg<LOGN>::LOGE>(
+      sm, TW_I(C, i), P.q, P.ninv, P.ninv_s,
+      [&](int k) {
+        const uint64_t v = src[g == 1 ? k : gal_src(k, g, LOGN)];
+        diag[k] = v;
+        return v;
+      },
+      [&](int k, uint64_t v) { dig[k] = v; });
+}
+
+// B: digit i reduced mod prime j, forward transform -> D[i][j]
+template <int LOGN>
+__global__ void __launch_bounds__(Cfg<LOGN>::T) kn_ks_modup(const CtxDev* __restrict__ C, KsDev a, int skip_diag) {
+  extern __shared__ uint64_t sm[];
+  constexpr int N = Cfg<LOGN>::N;
+  const int L = C->L, LK = C->L + C->K;
+  const int per = skip_diag ? L * (LK - 1) : L * LK;
+  const size_t ct = blockIdx.x / per;
+  const int r = blockIdx.x % per;
+  const int i = r / (skip_diag ? LK - 1 : LK);
+  int j = r % (skip_diag ? LK - 1 : LK);
+  if (skip_diag && j >= i) ++j;
+  const uint64_t* dig = a.dig + (ct * L + i) * (size_t)N;
+  uint64_t* dst = a.D + ((ct * L + i) * LK + j) * (size_t)N;
+  const PrimeDev& P = C->pr[j];
+  ntt_forward<LOGN, Cfg<LOGN>::LOGE>(sm, TW_F(C, j), P.q, [&](int k) { return reduce64(dig[k], P.q, P.f64); },
+                                      [&](int k, uint64_t v) { dst[k] = v; });
+}
+
+__device__ __forceinline__ const uint64_t* ks_key(const KsDev& a, size_t ct) {
+  return a.d_keys ? a.d_keys[ct / a.gal_div] : a.key;
+}
+
+// D: inner product over digits for the special prime, then inverse transform mod P
+template <int LOGN>
+__global__ void __launch_bounds__(Cfg<LOGN>::T) kn_ks_ip_p(const CtxDev* __restrict__ C, KsDev a) {
+  extern __shared__ uint64_t sm[];
+  constexpr int N = Cfg<LOGN>::N;
+  const int L = C->L, LK = C->L + C->K, ip = C->iP;
+  const size_t ct = blockIdx.x >> 1;
+  const int comp = blockIdx.x & 1;
+  const uint64_t* key = ks_key(a, ct);
+  const PrimeDev& P = C->pr[ip];
+  uint64_t* dst = a.xP + (ct * 2 + comp) * (size_t)N;
+  ntt_inverse<LOGN, Cfg<LOGN>::LOGE>(
+      sm, TW_I(C, ip), P.q, P.ninv, P.ninv_s,
+      [&](int k) {
+        uint64_t acc = 0;
+        for (int i = 0; i < L; ++i) {
+          const uint64_t d = a.D[((ct * L + i) * LK + ip) * (size_t)N + k];
+          const uint64_t w = key[((size_t)(comp * L + i) * LK + ip) * N + k];
+          acc = add_mod(acc, mont_mul(d, w, P.q, P.qinv), P.q);
+        }
+        return acc;
+      },
+      [&](int k, uint64_t v) { dst[k] = v; });
+}
+
+// E: x~ = centered(x mod P) reduced mod q_j and transformed; output limb
+//    out[comp][j] = (sum_i D[i][j] key[comp][i][j] - NTT(x~)) P^-1
+//                   (+ tau_g(c0)_j for comp 0, + add1_j for comp 1, + accum)
+template <int LOGN>
+__global__ void __launch_bounds__(Cfg<LOGN>::T) kn_ks_moddown(const CtxDev* __restrict__ C, KsDev a) {
+  extern __shared__ uint64_t sm[];
+  constexpr int N = Cfg<LOGN>::N;
+  const int L = C->L, LK = C->L + C->K;
+  const size_t ct = blockIdx.x / (2 * L);
+  const int r = blockIdx.x % (2 * L);
+  const int comp = r / L, j = r % L;
+  const uint32_t g = a.d_gal ? a.d_gal[ct / a.gal_div] : a.gal;
+  const uint64_t* key = ks_key(a, ct);
+  const PrimeDev& P = C->pr[j];
+  const uint64_t Pq = C->pr[C->iP].q;
+  const uint64_t PmodQ = C->PmodQ[j], Pinv = C->PinvQ[j], Pinv_s = C->PinvQ_s[j];
+  const uint64_t* x = a.xP + (ct * 2 + comp) * (size_t)N;
+  const uint64_t* c0 = a.c0 ? a.c0 + (ct * 2 * L + j) * (size_t)N : nullptr;
+  const uint64_t* ad1 = a.add1 ? a.add1 + (ct * 2 * L + L + j) * (size_t)N : nullptr;
+  const uint64_t* acc_in = a.accum ? a.accum + ((ct * 2 + comp) * L + j) * (size_t)N : nullptr;
+  uint64_t* dst = a.out + ((ct * 2 + comp) * L + j) * (size_t)N;
+  ntt_forward<LOGN, Cfg<LOGN>::LOGE>(
+      sm, TW_F(C, j), P.q,
+      [&](int k) {
+        const uint64_t v = x[k];
+        const uint64_t r0 = reduce64(v, P.q, P.f64);
+        return v > (Pq - 1) / 2 ? sub_mod(r0, PmodQ, P.q) : r0;
+      },
+      [&](int k, uint64_t v) {
+        uint64_t acc = 0;
+        for (int i = 0; i < L; ++i) {
+          const uint64_t d = a.D[((ct * L + i) * LK + j) * (size_t)N + k];
+          const uint64_t w = key[((size_t)(comp * L + i) * LK + j) * N + k];
+          acc = add_mod(acc, mont_mul(d, w, P.q, P.qinv), P.q);
+        }
+        uint64_t res = shoup_mul(sub_mod(acc, v, P.q), Pinv, Pinv_s, P.q);
+        if (comp == 0 && c0) res = add_mod(res, c0[g == 1 ? k : gal_src(k, g, LOGN)], P.q);
+        if (comp == 1 && ad1) res = add_mod(res, ad1[k], P.q);
+        if (acc_in) res = add_mod(res, acc_in[k], P.q);
+        dst[k] = res;
+      });
+}
+
+// ------------------------------------------------------------------ dispatch
+#define LOLA_DISPATCH(logn, KERNEL, grid, stream, ...)                                             \
+  do {                                                                                             \
+    switch (logn) {                                                                                \
+      case 4: LOLA_LAUNCH(4, KERNEL, grid, stream, __VA_ARGS__); break;                            \
+      case 5: LOLA_LAUNCH(5, KERNEL, grid, stream, __VA_ARGS__); break;                            \
+      case 6: LOLA_LAUNCH(6, KERNEL, grid, stream, __VA_ARGS__); break;                            \
+      case 7: LOLA_LAUNCH(7, KERNEL, grid, stream, __VA_ARGS__); break;                            \
+      case 8: LOLA_LAUNCH(8, KERNEL, grid, stream, __VA_ARGS__); break;                            \
+      case 9: LOLA_LAUNCH(9, KERNEL, grid, stream, __VA_ARGS__); break;                            \
+      case 10: LOLA_LAUNCH(10, KERNEL, grid, stream, __VA_ARGS__); break;                          \
+      case 11: LOLA_LAUNCH(11, KERNEL, grid, stream, __VA_ARGS__); break;                          \
+      case 12: LOLA_LAUNCH(12, KERNEL, grid, stream, __VA_ARGS__); break;                          \
+      case 13: LOLA_LAUNCH(13, KERNEL, grid, stream, __VA_ARGS__); break;                          \
+      case 14: LOLA_LAUNCH(14, KERNEL, grid, stream, __VA_ARGS__); break;                          \
+      default: return fail(LOLA_E_PARAM, "unsupported ring degree");                                \
+    }                                                                                              \
+  } while (0)
+
+#define LOLA_LAUNCH(LG, KERNEL, grid, stream, ...)                                                 \
+  do {                                                                                             \
+    const size_t smem = sizeof(uint64_t) << (LG);                                                  \
+    static bool attr_done = false;                                                                 \
+    if (!attr_done) {                                                                              \
+      cudaFuncSetAttribute(KERNEL<LG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);    \
+      attr_done = true;                                                                            \
+    }                                                                                              \
+    KERNEL<LG><<<(unsigned)(grid), Cfg<LG>::T, smem, stream>>>(__VA_ARGS__);                       \
+  } while (0)
+
+static int post_launch(Ctx* c, cudaStream_t) {
+  c->launches.fetch_add(1, std::memory_order_relaxed);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(LOLA_E_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+  return LOLA_OK;
+}
+
+namespace k {
+
+static PrimeMap contiguous_map(uint32_t limbs, uint32_t prime0) {
+  PrimeMap m{};
+  for (uint32_t l = 0; l < limbs && l < sizeof(m.p); ++l) m.p[l] = (uint8_t)(prime0 + l);
+  return m;
+}
+
+int ntt_fwd_map(Ctx* c, const uint64_t* in, uint64_t* out, size_t n_polys, uint32_t limbs, const PrimeMap& pm,
+                cudaStream_t s) {
+  if (!n_polys) return LOLA_OK;
+  ProfScope ps(c, KK_NTT, s);
+  LOLA_DISPATCH(c->logn, kn_fwd, n_polys, s, c->dev, in, out, limbs, pm);
+  return post_launch(c, s);
+}
+
+int ntt_inv_map(Ctx* c, const uint64_t* in, uint64_t* out, size_t n_polys, uint32_t limbs, const PrimeMap& pm,
+                bool mont_fix, cudaStream_t s) {
+  if (!n_polys) return LOLA_OK;
+  ProfScope ps(c, KK_NTT, s);
+  LOLA_DISPATCH(c->logn, kn_inv, n_polys, s, c->dev, in, out, limbs, pm, (int)mont_fix);
+  return post_launch(c, s);
+}
+
+int ntt_fwd(Ctx* c, uint64_t* data, size_t n_polys, uint32_t limbs, uint32_t prime0, cudaStream_t s) {
+  return ntt_fwd_map(c, data, data, n_polys * limbs, limbs, contiguous_map(limbs, prime0), s);
+}
+
+int ntt_inv(Ctx* c, uint64_t* data, size_t n_polys, uint32_t limbs, uint32_t prime0, bool mont_fix,
+            cudaStream_t s) {
+  return ntt_inv_map(c, data, data, n_polys * limbs, limbs, contiguous_map(limbs, prime0), mont_fix, s);
+}
+
+int ntt_fwd_from_signed(Ctx* c, const int64_t* in, uint64_t* out, size_t n_polys, uint32_t limbs, uint32_t prime0,
+                        cudaStream_t s) {
+  if (!n_polys) return LOLA_OK;
+  PrimeMap pm = contiguous_map(limbs, prime0);
+  ProfScope ps(c, KK_NTT, s);
+  LOLA_DISPATCH(c->logn, kn_fwd_signed, n_polys * limbs, s, c->dev, in, out, limbs, pm);
+  return post_launch(c, s);
+}
+
+int encode_lift(Ctx* c, const uint64_t* in, const uint32_t* d_tidx, uint64_t* out, size_t n_polys, uint32_t limbs,
+                bool mont, cudaStream_t s) {
+  if (!n_polys) return LOLA_OK;
+  ProfScope ps(c, KK_NTT, s);
+  LOLA_DISPATCH(c->logn, kn_encode_lift, n_polys * limbs, s, c->dev, in, d_tidx, out, limbs, (int)mont);
+  return post_launch(c, s);
+}
+
+int slots_to_coeff(Ctx* c, const uint64_t* slots, const uint32_t* d_tidx, uint64_t* coeff, size_t n_polys,
+                   cudaStream_t s) {
+  if (!n_polys) return LOLA_OK;
+  ProfScope ps(c, KK_NTT, s);
+  LOLA_DISPATCH(c->logn, kn_slots_to_coeff, n_polys, s, c->dev, slots, d_tidx, (const uint32_t*)c->d_slotpos.p, coeff);
+  return post_launch(c, s);
+}
+
+int coeff_to_slots(Ctx* c, const uint64_t* coeff, const uint32_t* d_tidx, uint64_t* slots, size_t n_polys,
+                   cudaStream_t s) {
+  if (!n_polys) return LOLA_OK;
+  ProfScope ps(c, KK_NTT, s);
+  LOLA_DISPATCH(c->logn, kn_coeff_to_slots, n_polys, s, c->dev, coeff, d_tidx, (const uint32_t*)c->d_slotpos.p, slots);
+  return post_launch(c, s);
+}
+
+int enc_msg(Ctx* c, const uint64_t* m, const int64_t* e1, const uint32_t* d_tidx, uint64_t* out, size_t n_polys,
+            cudaStream_t s) {
+  if (!n_polys) return LOLA_OK;
+  ProfScope ps(c, KK_NTT, s);
+  LOLA_DISPATCH(c->logn, kn_enc_msg, n_polys * c->L, s, c->dev, m, e1, d_tidx, out, c->L);
+  return post_launch(c, s);
+}
+
+int ks_decompose(Ctx* c, const KsDev& a, cudaStream_t s) {
+  ProfScope ps(c, KK_NTT, s);
+  LOLA_DISPATCH(c->logn, kn_ks_decompose, a.count * c->L, s, c->dev, a);
+  return post_launch(c, s);
+}
+
+int ks_modup(Ctx* c, const KsDev& a, bool skip_diag, cudaStream_t s) {
+  const uint32_t LK = c->L + c->K;
+  const size_t per = skip_diag ? (size_t)c->L * (LK - 1) : (size_t)c->L * LK;
+  if (!per) return LOLA_OK;
+  ProfScope ps(c, KK_NTT, s);
+  LOLA_DISPATCH(c->logn, kn_ks_modup, a.count * per, s, c->dev, a, (int)skip_diag);
+  return post_launch(c, s);
+}
+
+int ks_ip_p(Ctx* c, const KsDev& a, cudaStream_t s) {
+  ProfScope ps(c, KK_NTT, s);
+  LOLA_DISPATCH(c->logn, kn_ks_ip_p, a.count * 2, s, c->dev, a);
+  return post_launch(c, s);
+}
+
+int ks_moddown(Ctx* c, const KsDev& a, cudaStream_t s) {
+  ProfScope ps(c, KK_NTT, s);
+  LOLA_DISPATCH(c->logn, kn_ks_moddown, a.count * 2 * c->L, s, c->dev, a);
+  return post_launch(c, s);
+}
+
+}  // namespace k
+}  // namespace lola

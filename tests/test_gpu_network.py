@@ -1,0 +1,191 @@
+"""GPU parity of whole LoLa networks.
+
+* single dense layer + square (n = 4096) and a reduced MNIST-shaped network
+  (n = 1024): every output ciphertext bit-exact against the oracle running
+  the same layer list on the same encrypted input with the same keys;
+* the full MNIST-shaped network (n = 16384, three CRT moduli) and the
+  transfer-learning head at full size, batched: decrypted outputs equal the
+  integer network exactly (after CRT), graph replay equal to eager launch.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from gpu_util import ct_stack, lib, make_ctx, need_gpu, oracle_params
+from oracle import bfv, encoding, lola as OL
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_keys(Lb, ctx, net, seed):
+    steps = net.rotation_steps()
+    flags = Lb.LOLA_KEY_RELIN | (Lb.LOLA_KEY_ROW_SWAP if 0 in steps else 0)
+    return Lb.lola_keygen(ctx, seed, [s for s in steps if s], flags)
+
+
+def oracle_keys(P, net, seed):
+    steps = net.rotation_steps()
+    return bfv.keygen(P, seed, rotations=[s for s in steps if s], relin=True, row_swap=0 in steps)
+
+
+def mnist_int(net, img):
+    x = OL.int_conv(img, net.conv_w, net.kh, net.kw, net.stride)
+    x = OL.int_dense(OL.int_square(x), net.dense1_w)
+    return OL.int_dense(OL.int_square(x), net.dense2_w)
+
+
+def test_dense64_bit_exact_vs_oracle():
+    need_gpu()
+    Lb = lib()
+    ps = W.params_dense64()
+    P = oracle_params(ps)
+    n, t = ps.n, ps.t[0]
+    Wd, x = W.dense_weights(), W.dense_vector()
+    copies = W.dense64_input_copies(Wd)
+    layers = W.layers_dense64(Wd, n)
+    ctx = make_ctx(ps)
+    try:
+        net = Lb.lola_net_create(ctx, {"repr": "stacked", "n_msgs": 1, "n_elems": 64, "d": 6, "copies": copies}, layers)
+        sk, ev = gpu_keys(Lb, ctx, net, W.DEFAULT_SEED)
+        packed = Lb.lola_pack_stacked(x, 6, copies, n)
+        ct = Lb.lola_encrypt(ctx, sk, packed[None], 3)
+        out = Lb.lola_ct_create(ctx, 1)
+        Lb.lola_eval_network(ctx, ev, net, ct, out)
+        got = Lb.lola_ct_export(ctx, out, (1, 2, P.L, n))[0, 0]
+        # oracle: same keys, same ciphertext, same layer list
+        ok = oracle_keys(P, net, W.DEFAULT_SEED)
+        oct_ = bfv.encrypt(P, ok.pk, encoding.encode(packed, t), t, 3, 0)
+        st = OL.run_network(OL.HEEval(P, ok, t), layers, OL.State([oct_], [(0, i) for i in range(64)], 64, copies))
+        assert np.array_equal(got[0], st.msgs[0].c[0]) and np.array_equal(got[1], st.msgs[0].c[1])
+        dec = Lb.lola_decrypt_residues(ctx, sk, out, 1, n)[0, 0]
+        want = [v % t for v in OL.int_square(OL.int_dense(x, Wd))]
+        assert [int(dec[s]) for _, s in net.output_map()] == want
+        for h in (ct, out):
+            Lb.lola_ct_destroy(h)
+        Lb.lola_keys_destroy(sk)
+        Lb.lola_keys_destroy(ev)
+        net.destroy()
+    finally:
+        Lb.lola_ctx_destroy(ctx)
+
+
+def test_mini_mnist_bit_exact_vs_oracle():
+    need_gpu()
+    Lb = lib()
+    n = 1024
+    ps = W.params_small(n, L=5, K=1, t=W.T30[:1])
+    P = oracle_params(ps)
+    t = ps.t[0]
+    mnet = W.mnist_net(seed=7, maps=2, hidden=12, classes=3, h=12, w=12, k=3, stride=2)
+    img = W.image(seed=7, h=12, w=12)
+    layers = W.layers_mnist(mnet, n)
+    ctx = make_ctx(ps)
+    try:
+        msgs, win = Lb.lola_pack_convolution(img, 3, 3, 2, n)
+        net = Lb.lola_net_create(ctx, {"repr": "convolution", "n_msgs": 9, "n_elems": win}, layers)
+        sk, ev = gpu_keys(Lb, ctx, net, 11)
+        ct = Lb.lola_encrypt(ctx, sk, msgs, 5)
+        out = Lb.lola_ct_create(ctx, 3)
+        Lb.lola_eval_network(ctx, ev, net, ct, out)
+        got = Lb.lola_ct_export(ctx, out, (1, 2, P.L, n))[:, 0]
+        ok = oracle_keys(P, net, 11)
+        octs = [bfv.encrypt(P, ok.pk, encoding.encode(m, t), t, 5, i) for i, m in enumerate(msgs)]
+        st = OL.run_network(OL.HEEval(P, ok, t), layers, OL.State(octs, [(0, i) for i in range(win)]))
+        for o in range(3):
+            assert np.array_equal(got[o, 0], st.msgs[o].c[0]) and np.array_equal(got[o, 1], st.msgs[o].c[1]), o
+        res = Lb.lola_decrypt_residues(ctx, sk, out, 1, n)
+        assert [int(res[m, 0, s]) for m, s in net.output_map()] == [v % t for v in mnist_int(mnet, img)]
+        for h in (ct, out):
+            Lb.lola_ct_destroy(h)
+        Lb.lola_keys_destroy(sk)
+        Lb.lola_keys_destroy(ev)
+        net.destroy()
+    finally:
+        Lb.lola_ctx_destroy(ctx)
+
+
+def test_full_mnist_batched_decrypts_to_integer_network():
+    need_gpu()
+    Lb = lib()
+    ps = W.params_mnist()
+    n = ps.n
+    mnet = W.mnist_net()
+    layers = W.layers_mnist(mnet, n)
+    ctx = make_ctx(ps)
+    try:
+        B = 2
+        imgs = [W.image(idx=i) for i in range(B)]
+        packed = [Lb.lola_pack_convolution(im, 5, 5, 2, n) for im in imgs]
+        win = packed[0][1]
+        net = Lb.lola_net_create(ctx, {"repr": "convolution", "n_msgs": 25, "n_elems": win}, layers)
+        assert sorted(net.rotation_steps()) == sorted([0, 1, 2, 3, 4, 5, 6, 169, 338, 507, 676] +
+                                                      [1 << j for j in range(3, 13)])
+        sk, ev = gpu_keys(Lb, ctx, net, W.DEFAULT_SEED)
+        ct = Lb.lola_encrypt(ctx, sk, np.concatenate([p[0] for p in packed]), 21)
+        out = Lb.lola_ct_create(ctx, B * 10)
+        out2 = Lb.lola_ct_create(ctx, B * 10)
+        Lb.lola_eval_network(ctx, ev, net, ct, out)                   # first call: eager + capture
+        Lb.lola_eval_network(ctx, ev, net, ct, out2)                  # graph replay
+        a = Lb.lola_ct_export(ctx, out, (3, 2, ps.L, n))
+        b = Lb.lola_ct_export(ctx, out2, (3, 2, ps.L, n))
+        assert np.array_equal(a, b)
+        dec = Lb.lola_decrypt(ctx, sk, out, n)
+        omap = net.output_map()
+        for r in range(B):
+            got = [int(dec[r * 10 + m, s]) for m, s in omap]
+            assert got == mnist_int(mnet, imgs[r]), r
+            # sparse output: every slot of the message holds the value
+            assert all(int(dec[r * 10 + m, 77]) == g for (m, _), g in zip(omap, got))
+        for h in (ct, out, out2):
+            Lb.lola_ct_destroy(h)
+        Lb.lola_keys_destroy(sk)
+        Lb.lola_keys_destroy(ev)
+        net.destroy()
+    finally:
+        Lb.lola_ctx_destroy(ctx)
+
+
+def test_head_batched_decrypts_to_integer_network():
+    need_gpu()
+    Lb = lib()
+    ps = W.params_head()
+    n, t = ps.n, ps.t[0]
+    Wh = W.head_weights()
+    layers = W.layers_head(Wh, n)
+    ctx = make_ctx(ps)
+    try:
+        B = 3
+        xs = [W.feature_vector(idx=i) for i in range(B)]
+        net = Lb.lola_net_create(ctx, {"repr": "dense", "n_msgs": 1, "n_elems": 4096}, layers)
+        sk, ev = gpu_keys(Lb, ctx, net, 99)
+        slots = np.zeros((B, n), dtype=np.int64)
+        for i, x in enumerate(xs):
+            slots[i, :4096] = x
+        ct = Lb.lola_encrypt(ctx, sk, slots, 8)
+        out = Lb.lola_ct_create(ctx, B)
+        Lb.lola_eval_network(ctx, ev, net, ct, out, graph=False)
+        dec = Lb.lola_decrypt(ctx, sk, out, n)
+        for r in range(B):
+            got = [int(dec[r, s]) for _, s in net.output_map()]
+            assert got == OL.int_dense(xs[r], Wh)
+        for h in (ct, out):
+            Lb.lola_ct_destroy(h)
+        Lb.lola_keys_destroy(sk)
+        Lb.lola_keys_destroy(ev)
+        net.destroy()
+    finally:
+        Lb.lola_ctx_destroy(ctx)
+
+
+def test_representation_mismatch_rejected():
+    need_gpu()
+    Lb = lib()
+    ps = W.params_small(1024, L=3)
+    ctx = make_ctx(ps)
+    try:
+        with pytest.raises(Lb.LolaError) as ei:
+            Lb.lola_net_create(ctx, {"repr": "dense", "n_msgs": 1, "n_elems": 10},
+                               [{"op": "stacked_rowmajor", "weights": np.ones((2, 10), np.int64), "d": 4, "copies": 2}])
+        assert ei.value.code == -4
+    finally:
+        Lb.lola_ctx_destroy(ctx)
