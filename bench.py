@@ -1,0 +1,394 @@
+#!/usr/bin/env python
+"""Benchmark: LoLa's MNIST-shaped network on encrypted input, BFV n = 16384.
+
+One step = one batched evaluation of the whole network (conv row-major,
+combine, square, stack, stacked row-major dense, square, interleaved
+row-major dense; 224 rotations and 2 squares per CRT residue, 3 residues)
+on B encrypted synthetic 28x28 images whose ciphertexts are already resident
+in HBM.  Reported beside it:
+
+* plain: the same network for one request at a time (B = 1, eager launches,
+  no CUDA graph), p50 / p99 latency;
+* e2e: the batched step through the public API with host buffers: pinned
+  host -> device copy of the input ciphertexts, evaluation, device -> host
+  copy of the output ciphertexts, all inside the timed region;
+* roofline: the kernel with the largest device time, its algorithmic bytes
+  per launch over its CUDA-event-timed average duration, against the
+  measured HBM copy bandwidth;
+* cpu_baseline: the CPU oracle's per-operation times on the same parameters
+  scaled by the network's operation counts.
+
+`--impl reference` times that CPU oracle as the reference arm.
+Multi-GPU (torchrun): independent replicas, one per GPU, no collective on
+the data path; the barrier and the max over ranks are for timing only.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "p50 latency & inferences/s, batched vs plain, BFV n=16384; NTT HBM GB/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--batch", type=int, default=16, help="requests per batched step (per GPU)")
+    ap.add_argument("--plain", type=int, default=8, help="single-request evaluations for plain latency")
+    ap.add_argument("--L", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-steps", type=int, default=1)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": num(rows[0][2]),
+                "reasons": sorted(reasons), "samples": len(rows),
+                "power_w_max": max((num(r[3]) or 0) for r in rows)}
+
+
+# ------------------------------------------------------------ CPU baseline
+def oracle_sample(n_rot=1, n_sq=1):
+    """Time the CPU oracle's operations on the MNIST parameters (one CRT
+    residue) and scale by the network's operation counts for one inference
+    over all residues.  Returns (seconds per inference, description)."""
+    import numpy as np
+
+    import workloads as W
+    from oracle import bfv, encoding
+    ps = W.params_mnist()
+    P = bfv.Params(ps.n, ps.q, ps.L, ps.K, ps.t)
+    keys = bfv.keygen(P, 5, rotations=[1], relin=True)
+    t = ps.t[0]
+    v = np.random.default_rng(0).integers(0, 16, ps.n)
+    ct = bfv.encrypt(P, keys.pk, encoding.encode(v, t), t, 1, 0)
+    w = encoding.encode(np.random.default_rng(1).integers(-3, 4, ps.n), t)
+
+    def timed(fn, reps):
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        return (time.perf_counter() - t0) / reps
+    t_rot = timed(lambda: bfv.rotate(P, keys, ct, 1), n_rot)
+    t_sq = timed(lambda: bfv.square(P, keys, ct), n_sq)
+    t_pt = timed(lambda: bfv.mul_plain(P, ct, w), 1)
+    t_sc = timed(lambda: bfv.mul_scalar(P, ct, -3), 3)
+    t_add = timed(lambda: bfv.add(P, ct, ct), 3)
+    counts = {"rot": 224, "square": 2, "mul_plain": 24, "mul_scalar": 125, "add": 344}
+    per_residue = (counts["rot"] * t_rot + counts["square"] * t_sq + counts["mul_plain"] * t_pt
+                   + counts["mul_scalar"] * t_sc + counts["add"] * t_add)
+    sec = per_residue * len(ps.t)
+    desc = (f"oracle per-op times on n=16384, L={ps.L}: rotation {t_rot:.3f}s, square+relin {t_sq:.3f}s, "
+            f"ct*pt {t_pt:.3f}s, ct*scalar {t_sc:.4f}s, add {t_add:.4f}s; x op counts of one inference "
+            f"(224 rot, 2 sq, 24 ct*pt, 125 ct*scalar, 344 add) x {len(ps.t)} CRT residues")
+    return sec, desc
+
+
+def cpu_baseline_obj():
+    t0 = time.perf_counter()
+    sec, desc = oracle_sample()
+    return {"value": 1.0 / sec, "unit": "inferences/s", "cores": 1, "kind": "oracle",
+            "sample": desc, "sample_wall_s": round(time.perf_counter() - t0, 1)}
+
+
+# ---------------------------------------------------------------- reference
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample(1, 1)
+    secs = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s, desc = oracle_sample(1, 1)
+        secs.append(s)
+    wall = time.perf_counter() - t0
+    sec = statistics.median(secs)
+    value = 1.0 / sec
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "inferences/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1000,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "mnist_lola_n16384", "n": 16384, "L": args.L, "K": 1, "k_t": 3,
+                       "parallelism": "none (CPU oracle)"},
+            "cpu_baseline": {"value": value, "unit": "inferences/s", "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": "inferences/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------- ours
+KERNEL_BYTES = {
+    # algorithmic bytes per work unit (n = ring degree, L = ciphertext primes)
+    # transform kernels: one unit = one limb-polynomial
+    "ks_modup": lambda n, L: 16 * n,                 # read digit limb, write one mod-up limb
+    "ks_decompose": lambda n, L: 24 * n,             # read c1 limb, write diagonal + digit
+    "ks_moddown": lambda n, L: (2 * L + 5) * 8 * n,  # x_P, L digit limbs, L key limbs, addend, accum in; out
+    "ks_ip_p": lambda n, L: (2 * L + 1) * 8 * n,     # L digit limbs + L key limbs in, one limb out
+    "ntt_fwd": lambda n, L: 16 * n,
+    "ntt_inv": lambda n, L: 16 * n,
+    # element-wise kernels: one unit = one output word
+    "add": lambda n, L: 24,
+    "mul_plain": lambda n, L: 24,
+    "mac_scalar": lambda n, L: 25 * 8 + 8,
+    "tensor": lambda n, L: 4 * 8 + 3 * 8,
+    "lift_q_to_b": lambda n, L: L * 8,
+    "scale_round": lambda n, L: 0,
+}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_1812_10659_gb300 import lola as L
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    ps = W.params_mnist(args.L)
+    n, kt, Lq = ps.n, len(ps.t), ps.L
+    mnet = W.mnist_net()
+    layers = W.layers_mnist(mnet, n)
+    ctx = L.lola_ctx_create(ps.n, ps.q, ps.L, ps.K, ps.t, device=local)
+    B = args.batch
+    net = L.lola_net_create(ctx, {"repr": "convolution", "n_msgs": 25, "n_elems": 169}, layers)
+    steps_needed = net.rotation_steps()
+    sk, ev = L.lola_keygen(ctx, W.DEFAULT_SEED, [s for s in steps_needed if s],
+                           L.LOLA_KEY_RELIN | L.LOLA_KEY_ROW_SWAP)
+    imgs = [W.image(idx=rank * 100000 + i) for i in range(B)]
+    packed = np.concatenate([L.lola_pack_convolution(im, 5, 5, 2, n)[0] for im in imgs])
+    ct_in = L.lola_encrypt(ctx, sk, packed, 1000 + rank)
+    ct_out = L.lola_ct_create(ctx, B * 10)
+    ct_words = 2 * Lq * n
+    in_bytes = B * 25 * kt * ct_words * 8
+    out_bytes = B * 10 * kt * ct_words * 8
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    def step():
+        L.lola_eval_network(ctx, ev, net, ct_in, ct_out, stream)
+
+    # ---- batched, HBM-resident inputs
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    evs[0].record(stream)
+    for i in range(args.steps):
+        step()
+        evs[i + 1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
+    total_ms = evs[0].elapsed_time(evs[-1])
+    tmax = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+    if dist:
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    total_ms_max = float(tmax.item())
+    value = world * B * args.steps / (total_ms_max / 1000.0)
+
+    # correctness spot check of this run's output (first request, decrypted)
+    dec = L.lola_decrypt(ctx, sk, ct_out, n)
+    from oracle import lola as OL  # integer network only (no encryption)
+    x = OL.int_conv(imgs[0], mnet.conv_w, 5, 5, 2)
+    x = OL.int_dense(OL.int_square(x), mnet.dense1_w)
+    want = OL.int_dense(OL.int_square(x), mnet.dense2_w)
+    got = [int(dec[m, s]) for m, s in net.output_map()]
+    correct = got == want
+
+    # ---- e2e through host buffers (pinned)
+    h_in = torch.empty(in_bytes // 8, dtype=torch.int64, pin_memory=True)
+    h_out = torch.empty(out_bytes // 8, dtype=torch.int64, pin_memory=True)
+    L.lola_ct_download(ctx, ct_in, h_in.data_ptr(), stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        L.lola_ct_upload(ctx, ct_in, h_in.data_ptr(), stream)
+        step()
+        L.lola_ct_download(ctx, ct_out, h_out.data_ptr(), stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    t2 = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+    if dist:
+        dist.all_reduce(t2, op=dist.ReduceOp.MAX)
+    e2e_value = world * B * args.steps / (float(t2.item()) / 1000.0)
+
+    # ---- plain: one request at a time, eager, no graph
+    ct1_in = L.lola_encrypt(ctx, sk, packed[:25], 7)
+    ct1_out = L.lola_ct_create(ctx, 10)
+    L.lola_eval_network(ctx, ev, net, ct1_in, ct1_out, stream, graph=False)
+    torch.cuda.synchronize()
+    plain_ms = []
+    for _ in range(args.plain):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        L.lola_eval_network(ctx, ev, net, ct1_in, ct1_out, stream, graph=False)
+        b.record(stream)
+        torch.cuda.synchronize()
+        plain_ms.append(a.elapsed_time(b))
+
+    # ---- per-kernel device time over profiled batched steps (eager, CUDA events)
+    launches0 = L.lola_launch_count(ctx)
+    L.lola_profile_enable(ctx, -1, True)
+    for _ in range(args.profile_steps):
+        step()
+    torch.cuda.synchronize()
+    per_kernel = {}
+    for k in range(L.lola_profile_kinds()):
+        ms, cnt, units = L.lola_profile_read(ctx, k)
+        if cnt:
+            per_kernel[L.lola_profile_name(k)] = {"ms": ms, "launches": cnt, "units": units}
+    L.lola_profile_enable(ctx, -1, False)
+    launches_per_step = (L.lola_launch_count(ctx) - launches0) // max(1, args.profile_steps)
+    kernel_ms_total = sum(v["ms"] for v in per_kernel.values())
+    dom = max(per_kernel, key=lambda k: per_kernel[k]["ms"])
+    d = per_kernel[dom]
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        peaks = json.load(open(pk))
+    hbm_peak = peaks.get("hbm_gbs")
+    peak_src = "measured" if hbm_peak else "fallback"
+    hbm_peak = hbm_peak or 6800.0
+    fn = KERNEL_BYTES.get(dom)
+    achieved = (d["units"] * fn(n, Lq)) / (d["ms"] / 1000.0) / 1e9 if fn else None
+    roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "peak_source": peak_src,
+                "unit": "GB/s", "frac": (achieved / hbm_peak) if achieved else None, "traffic": None,
+                "avg_launch_ms": d["ms"] / d["launches"], "share_of_kernel_time": d["ms"] / kernel_ms_total}
+    ntt_like = {k: v for k, v in per_kernel.items() if k in ("ks_modup", "ks_decompose", "ntt_fwd", "ntt_inv")}
+    ntt_gbs = None
+    if "ks_modup" in per_kernel:
+        v = per_kernel["ks_modup"]
+        ntt_gbs = v["units"] * 16 * n / (v["ms"] / 1000.0) / 1e9
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_obj()
+
+    if rank == 0:
+        srt = sorted(step_ms)
+        line = {
+            "metric": METRIC, "value": value, "unit": "inferences/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "mnist_lola_n16384", "batch_per_gpu": B, "n": n, "L": Lq, "K": 1, "k_t": kt,
+                       "aux_primes": len(L.lola_ctx_aux_primes(ctx)), "parallelism": f"replicas x{world}",
+                       "l2": f"inputs larger than L2 ({in_bytes / 1e6:.0f} MB of input ciphertexts per step)"},
+            "latency_ms": {"batched_p50": statistics.median(step_ms), "batched_p99": srt[min(len(srt) - 1, int(0.99 * len(srt)))],
+                           "plain_p50": statistics.median(plain_ms),
+                           "plain_p99": sorted(plain_ms)[min(len(plain_ms) - 1, int(0.99 * len(plain_ms)))]},
+            "plain": {"value": 1000.0 / statistics.median(plain_ms), "unit": "inferences/s", "batch": 1,
+                      "graph": False},
+            "ntt_gbs": ntt_gbs,
+            "roofline": roofline,
+            "kernels": {k: {"ms_per_step": v["ms"] / args.profile_steps, "launches_per_step": v["launches"] // args.profile_steps}
+                        for k, v in sorted(per_kernel.items(), key=lambda kv: -kv[1]["ms"])},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "inferences/s", "h2d_bytes_per_step": in_bytes,
+                    "d2h_bytes_per_step": out_bytes},
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clk,
+            "correct": correct,
+        }
+        print(json.dumps(line), flush=True)
+    for h in (ct_in, ct_out, ct1_in, ct1_out):
+        L.lola_ct_destroy(h)
+    net.destroy()
+    L.lola_keys_destroy(sk)
+    L.lola_keys_destroy(ev)
+    L.lola_ctx_destroy(ctx)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

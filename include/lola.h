@@ -239,13 +239,19 @@ int lola_pack_convolution(const int64_t* image, uint32_t h, uint32_t w, uint32_t
 int lola_pack_stacked(const int64_t* vec, uint32_t k, uint32_t d, uint32_t copies, uint32_t n, int64_t* out);
 
 /* ------------------------------------------------------------- profiling
- * Per-kernel device time with CUDA events around every launch of kernel
- * class `kind` (0 = NTT-family kernels, 1 = key-switch inner product,
- * 2 = elementwise, 3 = basis conversion) while enabled.  Read returns the
- * summed milliseconds and launch count since the last reset. */
+ * CUDA events around every launch of the enabled kernels (events are
+ * recorded only on eager launches; lola_eval_network runs eagerly while any
+ * kernel is being profiled).  kind = kernel id in [0, lola_profile_kinds()),
+ * or -1 in lola_profile_enable for all of them.  Read returns the summed
+ * device milliseconds, the launch count and the work units processed since
+ * the last enable: limb-polynomials (one n-word limb) for transform kernels,
+ * 64-bit words or coefficient positions for element-wise kernels. */
 int lola_profile_enable(lola_ctx* ctx, int kind, int on);
-int lola_profile_read(lola_ctx* ctx, int kind, double* ms, uint64_t* launches);
-/* Kernel launches issued by the library since context creation. */
+int lola_profile_read(lola_ctx* ctx, int kind, double* ms, uint64_t* launches, uint64_t* units);
+int lola_profile_kinds(void);
+const char* lola_profile_name(int kind);
+/* Kernel launches issued by the library since context creation (launches
+ * inside a replayed CUDA graph are counted once, when captured). */
 uint64_t lola_launch_count(const lola_ctx* ctx);
 
 const char* lola_last_error(void);

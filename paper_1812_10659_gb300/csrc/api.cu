@@ -415,10 +415,13 @@ int lola_profile_enable(lola_ctx* ctx, int kind, int on) {
   return profile_enable(ctx->c, kind, on);
 }
 
-int lola_profile_read(lola_ctx* ctx, int kind, double* ms, uint64_t* launches) {
+int lola_profile_read(lola_ctx* ctx, int kind, double* ms, uint64_t* launches, uint64_t* units) {
   CHECK(ctx, LOLA_E_PARAM, "null context");
-  return profile_read(ctx->c, kind, ms, launches);
+  return profile_read(ctx->c, kind, ms, launches, units);
 }
+
+int lola_profile_kinds(void) { return KI_COUNT; }
+const char* lola_profile_name(int kind) { return kernel_name(kind); }
 
 uint64_t lola_launch_count(const lola_ctx* ctx) { return ctx ? ctx->c->launches.load() : 0; }
 

@@ -123,6 +123,14 @@ int DevBuf::alloc(size_t nbytes) {
 }
 
 // ------------------------------------------------------------- profiling
+const char* kernel_name(int id) {
+  static const char* names[KI_COUNT] = {
+      "ntt_fwd", "ntt_inv", "ntt_fwd_signed", "encode_lift", "slots_to_coeff", "coeff_to_slots", "enc_msg",
+      "ks_decompose", "ks_modup", "ks_ip_p", "ks_moddown", "ks_ip_q",
+      "add", "mul_plain", "mac_scalar", "tensor", "lift_q_to_b", "scale_round", "decrypt_round", "misc"};
+  return (id >= 0 && id < KI_COUNT) ? names[id] : "?";
+}
+
 void prof_begin(Ctx* c, int kind, cudaStream_t s, cudaEvent_t* ev) {
   if (!c->prof.on[kind]) return;
   if (c->prof.pool.empty()) {
@@ -137,20 +145,21 @@ void prof_begin(Ctx* c, int kind, cudaStream_t s, cudaEvent_t* ev) {
   ev[1] = pr.second;
   cudaEventRecord(ev[0], s);
 }
-void prof_end(Ctx* c, int kind, cudaStream_t s, cudaEvent_t* ev) {
+void prof_end(Ctx* c, int kind, cudaStream_t s, cudaEvent_t* ev, uint64_t units) {
   if (!ev[0]) return;
   cudaEventRecord(ev[1], s);
-  c->prof.pending[kind].push_back({ev[0], ev[1]});
+  c->prof.pending[kind].push_back({ev[0], ev[1], units});
 }
 
 static void prof_collect(Ctx* c, int kind) {
   for (auto& pr : c->prof.pending[kind]) {
-    cudaEventSynchronize(pr.second);
+    cudaEventSynchronize(pr.b);
     float ms = 0;
-    cudaEventElapsedTime(&ms, pr.first, pr.second);
+    cudaEventElapsedTime(&ms, pr.a, pr.b);
     c->prof.ms[kind] += ms;
     c->prof.launches[kind] += 1;
-    c->prof.pool.push_back(pr);
+    c->prof.units[kind] += pr.units;
+    c->prof.pool.push_back({pr.a, pr.b});
   }
   c->prof.pending[kind].clear();
 }
@@ -384,7 +393,7 @@ int ctx_create(const lola_params* p, int device, Ctx** out) {
 void ctx_destroy(Ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
-  for (int k2 = 0; k2 < 4; ++k2) prof_collect(c, k2);
+  for (int k2 = 0; k2 < KI_COUNT; ++k2) prof_collect(c, k2);
   for (auto& pr : c->prof.pool) {
     cudaEventDestroy(pr.first);
     cudaEventDestroy(pr.second);
@@ -393,19 +402,23 @@ void ctx_destroy(Ctx* c) {
 }
 
 int profile_enable(Ctx* c, int kind, int on) {
-  if (!c || kind < 0 || kind > 3) return fail(LOLA_E_PARAM, "bad profile kind");
-  prof_collect(c, kind);
-  c->prof.on[kind] = on != 0;
-  c->prof.ms[kind] = 0;
-  c->prof.launches[kind] = 0;
+  if (!c || kind < -1 || kind >= KI_COUNT) return fail(LOLA_E_PARAM, "bad profile kind");
+  for (int k2 = (kind < 0 ? 0 : kind); k2 < (kind < 0 ? KI_COUNT : kind + 1); ++k2) {
+    prof_collect(c, k2);
+    c->prof.on[k2] = on != 0;
+    c->prof.ms[k2] = 0;
+    c->prof.launches[k2] = 0;
+    c->prof.units[k2] = 0;
+  }
   return LOLA_OK;
 }
 
-int profile_read(Ctx* c, int kind, double* ms, uint64_t* launches) {
-  if (!c || kind < 0 || kind > 3) return fail(LOLA_E_PARAM, "bad profile kind");
+int profile_read(Ctx* c, int kind, double* ms, uint64_t* launches, uint64_t* units) {
+  if (!c || kind < 0 || kind >= KI_COUNT) return fail(LOLA_E_PARAM, "bad profile kind");
   prof_collect(c, kind);
   if (ms) *ms = c->prof.ms[kind];
   if (launches) *launches = c->prof.launches[kind];
+  if (units) *units = c->prof.units[kind];
   return LOLA_OK;
 }
 

@@ -392,60 +392,60 @@ namespace k {
 
 #define ELEM_LAUNCH(kind, KERNEL, items, ...)                                       \
   do {                                                                             \
-    ProfScope ps_(c, kind, s);                                                     \
+    ProfScope ps_(c, kind, s, (uint64_t)(items));                                  \
     KERNEL<<<grid_for(items, 256), 256, 0, s>>>(__VA_ARGS__);                       \
   } while (0)
 
 int ks_ip_q(Ctx* c, const KsDev& a, cudaStream_t s) {
-  ELEM_LAUNCH(KK_KSIP, ke_ks_ip_q, a.count * 2 * c->L * c->n, c->dev, a);
+  ELEM_LAUNCH(KI_KS_IP_Q, ke_ks_ip_q, a.count * 2 * c->L * c->n, c->dev, a);
   return post(c);
 }
 
 int add(Ctx* c, const uint64_t* a, const uint64_t* b, uint64_t* out, size_t count, cudaStream_t s) {
   if (!count) return LOLA_OK;
   const size_t total = count * c->ct_words();
-  ELEM_LAUNCH(KK_ELEM, ke_add, total, c->dev, a, b, out, total, 0);
+  ELEM_LAUNCH(KI_ADD, ke_add, total, c->dev, a, b, out, total, 0);
   return post(c);
 }
 
 int sub(Ctx* c, const uint64_t* a, const uint64_t* b, uint64_t* out, size_t count, cudaStream_t s) {
   if (!count) return LOLA_OK;
   const size_t total = count * c->ct_words();
-  ELEM_LAUNCH(KK_ELEM, ke_add, total, c->dev, a, b, out, total, 1);
+  ELEM_LAUNCH(KI_ADD, ke_add, total, c->dev, a, b, out, total, 1);
   return post(c);
 }
 
 int to_mont_map(Ctx* c, uint64_t* data, size_t n_limbpolys, uint32_t limbs, const PrimeMap& pm, cudaStream_t s,
                 bool inverse) {
   const size_t total = n_limbpolys * c->n;
-  ELEM_LAUNCH(KK_ELEM, ke_to_mont, total, c->dev, data, total, limbs, pm, (int)inverse);
+  ELEM_LAUNCH(KI_MISC, ke_to_mont, total, c->dev, data, total, limbs, pm, (int)inverse);
   return post(c);
 }
 
 int axpy_mont_map(Ctx* c, const uint64_t* a, const uint64_t* b, const uint64_t* w_mont, uint64_t* out,
                   size_t n_limbpolys, uint32_t limbs, const PrimeMap& pm, cudaStream_t s) {
   const size_t total = n_limbpolys * c->n;
-  ELEM_LAUNCH(KK_ELEM, ke_axpy_mont, total, c->dev, a, b, w_mont, out, total, limbs, pm);
+  ELEM_LAUNCH(KI_MISC, ke_axpy_mont, total, c->dev, a, b, w_mont, out, total, limbs, pm);
   return post(c);
 }
 
 int neg_axpe(Ctx* c, const uint64_t* a, const uint64_t* s_mont, const uint64_t* e, uint64_t* out, uint32_t limbs,
              cudaStream_t s) {
   const size_t total = (size_t)limbs * c->n;
-  ELEM_LAUNCH(KK_ELEM, ke_neg_axpe, total, c->dev, a, s_mont, e, out, total);
+  ELEM_LAUNCH(KI_MISC, ke_neg_axpe, total, c->dev, a, s_mont, e, out, total);
   return post(c);
 }
 
 int keygen_switch(Ctx* c, const uint64_t* a, const uint64_t* e, const uint64_t* s_mont, const uint64_t* sfrom,
                   uint64_t* out, cudaStream_t s) {
   const size_t total = (size_t)c->L * (c->L + c->K) * c->n;
-  ELEM_LAUNCH(KK_ELEM, ke_keygen_switch, total, c->dev, a, e, s_mont, sfrom, out);
+  ELEM_LAUNCH(KI_MISC, ke_keygen_switch, total, c->dev, a, e, s_mont, sfrom, out);
   return post(c);
 }
 
 int gal_permute(Ctx* c, const uint64_t* in, uint64_t* out, size_t n_limbpolys, uint32_t g, cudaStream_t s) {
   const size_t total = n_limbpolys * c->n;
-  ELEM_LAUNCH(KK_ELEM, ke_gal_permute, total, c->dev, in, out, total, g);
+  ELEM_LAUNCH(KI_MISC, ke_gal_permute, total, c->dev, in, out, total, g);
   return post(c);
 }
 
@@ -453,7 +453,7 @@ int mul_plain_multi(Ctx* c, const uint64_t* in, const uint64_t* pt, uint64_t* ou
                     cudaStream_t s) {
   const size_t total = (size_t)R * B * c->kt * c->ct_words();
   if (!total) return LOLA_OK;
-  ELEM_LAUNCH(KK_ELEM, ke_mul_plain_multi, total, c->dev, in, pt, out, R, B);
+  ELEM_LAUNCH(KI_MUL_PLAIN, ke_mul_plain_multi, total, c->dev, in, pt, out, R, B);
   return post(c);
 }
 
@@ -461,13 +461,13 @@ int mac_scalar(Ctx* c, const uint64_t* in, uint32_t R, const uint64_t* w, const 
                uint32_t maps, uint32_t B, cudaStream_t s) {
   const size_t total = (size_t)maps * B * c->kt * c->ct_words();
   if (!total) return LOLA_OK;
-  ELEM_LAUNCH(KK_ELEM, ke_mac_scalar, total, c->dev, in, R, w, ws, out, maps, B);
+  ELEM_LAUNCH(KI_MAC_SCALAR, ke_mac_scalar, total, c->dev, in, R, w, ws, out, maps, B);
   return post(c);
 }
 
 template <int KQ>
 static int lift_dispatch(Ctx* c, const uint64_t* xq, uint64_t* xb, size_t n_polys, cudaStream_t s) {
-  ELEM_LAUNCH(KK_BASIS, ke_lift_q_to_b<KQ>, n_polys * c->n, c->dev, xq, xb, n_polys);
+  ELEM_LAUNCH(KI_LIFT_Q_TO_B, ke_lift_q_to_b<KQ>, n_polys * c->n, c->dev, xq, xb, n_polys);
   return post(c);
 }
 
@@ -479,14 +479,14 @@ int lift_q_to_b(Ctx* c, const uint64_t* xq, uint64_t* xb, size_t n_polys, cudaSt
 
 int tensor(Ctx* c, const uint64_t* xq, const uint64_t* xb, const uint64_t* yq, const uint64_t* yb, uint64_t* T,
            size_t count, cudaStream_t s) {
-  ELEM_LAUNCH(KK_ELEM, ke_tensor, count * (c->L + c->M) * c->n, c->dev, xq, xb, yq, yb, T, count);
+  ELEM_LAUNCH(KI_TENSOR, ke_tensor, count * (c->L + c->M) * c->n, c->dev, xq, xb, yq, yb, T, count);
   return post(c);
 }
 
 template <int KQ, int KB>
 static int scale_dispatch(Ctx* c, const uint64_t* T, const uint32_t* tidx, uint32_t div, uint64_t* E, uint64_t* DIG,
                           size_t count, cudaStream_t s) {
-  ELEM_LAUNCH(KK_BASIS, (ke_scale_round<KQ, KB>), count * 3 * c->n, c->dev, T, tidx, div, E, DIG, count);
+  ELEM_LAUNCH(KI_SCALE_ROUND, (ke_scale_round<KQ, KB>), count * 3 * c->n, c->dev, T, tidx, div, E, DIG, count);
   return post(c);
 }
 
@@ -499,23 +499,23 @@ int scale_round(Ctx* c, const uint64_t* T, const uint32_t* d_tidx, uint32_t tidx
 
 int decrypt_round(Ctx* c, const uint64_t* x, const uint32_t* d_tidx, uint64_t* m, size_t n_polys, cudaStream_t s) {
   if (c->L <= 4) {
-    ELEM_LAUNCH(KK_BASIS, ke_decrypt_round<4>, n_polys * c->n, c->dev, x, d_tidx, m, n_polys);
+    ELEM_LAUNCH(KI_DECRYPT_ROUND, ke_decrypt_round<4>, n_polys * c->n, c->dev, x, d_tidx, m, n_polys);
   } else if (c->L <= 8) {
-    ELEM_LAUNCH(KK_BASIS, ke_decrypt_round<8>, n_polys * c->n, c->dev, x, d_tidx, m, n_polys);
+    ELEM_LAUNCH(KI_DECRYPT_ROUND, ke_decrypt_round<8>, n_polys * c->n, c->dev, x, d_tidx, m, n_polys);
   } else {
-    ELEM_LAUNCH(KK_BASIS, ke_decrypt_round<12>, n_polys * c->n, c->dev, x, d_tidx, m, n_polys);
+    ELEM_LAUNCH(KI_DECRYPT_ROUND, ke_decrypt_round<12>, n_polys * c->n, c->dev, x, d_tidx, m, n_polys);
   }
   return post(c);
 }
 
 int enc_combine(Ctx* c, const uint64_t* M1, const uint64_t* E2, const uint64_t* U, const uint64_t* pk, uint64_t* out,
                 size_t count, cudaStream_t s) {
-  ELEM_LAUNCH(KK_ELEM, ke_enc_combine, count * c->ct_words(), c->dev, M1, E2, U, pk, out, count);
+  ELEM_LAUNCH(KI_MISC, ke_enc_combine, count * c->ct_words(), c->dev, M1, E2, U, pk, out, count);
   return post(c);
 }
 
 int dec_phase(Ctx* c, const uint64_t* ct, const uint64_t* s_mont, uint64_t* out, size_t count, cudaStream_t s) {
-  ELEM_LAUNCH(KK_ELEM, ke_dec_phase, count * c->L * c->n, c->dev, ct, s_mont, out, count);
+  ELEM_LAUNCH(KI_MISC, ke_dec_phase, count * c->L * c->n, c->dev, ct, s_mont, out, count);
   return post(c);
 }
 

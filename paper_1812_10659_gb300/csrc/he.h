@@ -8,7 +8,7 @@ namespace lola {
 int ctx_create(const lola_params* p, int device, Ctx** out);
 void ctx_destroy(Ctx* c);
 int profile_enable(Ctx* c, int kind, int on);
-int profile_read(Ctx* c, int kind, double* ms, uint64_t* launches);
+int profile_read(Ctx* c, int kind, double* ms, uint64_t* launches, uint64_t* units);
 const char* last_error();
 
 struct EvalKeys {

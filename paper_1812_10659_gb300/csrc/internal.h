@@ -36,16 +36,32 @@ struct DevBuf {
   uint64_t* u64() const { return (uint64_t*)p; }
 };
 
-// Profiling: CUDA events around launches of one kernel class.
-struct Profiler {
-  bool on[4] = {false, false, false, false};
-  double ms[4] = {0, 0, 0, 0};
-  uint64_t launches[4] = {0, 0, 0, 0};
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending[4];
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pool;
+// Kernel identities for profiling (lola_profile_* in the C-ABI).
+enum KernelId {
+  KI_NTT_FWD = 0, KI_NTT_INV, KI_NTT_SIGNED, KI_ENCODE_LIFT, KI_SLOTS_TO_COEFF, KI_COEFF_TO_SLOTS, KI_ENC_MSG,
+  KI_KS_DECOMPOSE, KI_KS_MODUP, KI_KS_IP_P, KI_KS_MODDOWN, KI_KS_IP_Q,
+  KI_ADD, KI_MUL_PLAIN, KI_MAC_SCALAR, KI_TENSOR, KI_LIFT_Q_TO_B, KI_SCALE_ROUND, KI_DECRYPT_ROUND, KI_MISC,
+  KI_COUNT
 };
+const char* kernel_name(int id);
 
-enum KernelKind { KK_NTT = 0, KK_KSIP = 1, KK_ELEM = 2, KK_BASIS = 3 };
+// Profiling: CUDA events around every launch of the enabled kernels, plus
+// the work units each launch processed (limb-polynomials for transform
+// kernels, 64-bit words for element-wise kernels).
+struct Profiler {
+  bool on[KI_COUNT] = {};
+  double ms[KI_COUNT] = {};
+  uint64_t launches[KI_COUNT] = {};
+  uint64_t units[KI_COUNT] = {};
+  struct Pending { cudaEvent_t a, b; uint64_t units; };
+  std::vector<Pending> pending[KI_COUNT];
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pool;
+  bool any() const {
+    for (int i = 0; i < KI_COUNT; ++i)
+      if (on[i]) return true;
+    return false;
+  }
+};
 
 // -------------------------------------------------------------------- context
 struct Ctx {
@@ -63,13 +79,13 @@ struct Ctx {
   size_t ct_words() const { return (size_t)2 * L * n; }
 };
 
-// Launch bookkeeping: call before/after a kernel launch of class `kind`.
-void prof_begin(Ctx* c, int kind, cudaStream_t s, cudaEvent_t* ev_pair);
-void prof_end(Ctx* c, int kind, cudaStream_t s, cudaEvent_t* ev_pair);
+// Launch bookkeeping around one kernel launch.
+void prof_begin(Ctx* c, int id, cudaStream_t s, cudaEvent_t* ev_pair);
+void prof_end(Ctx* c, int id, cudaStream_t s, cudaEvent_t* ev_pair, uint64_t units);
 struct ProfScope {
-  Ctx* c; int kind; cudaStream_t s; cudaEvent_t ev[2] = {nullptr, nullptr};
-  ProfScope(Ctx* c_, int k, cudaStream_t s_) : c(c_), kind(k), s(s_) { prof_begin(c, kind, s, ev); }
-  ~ProfScope() { prof_end(c, kind, s, ev); }
+  Ctx* c; int id; cudaStream_t s; uint64_t units; cudaEvent_t ev[2] = {nullptr, nullptr};
+  ProfScope(Ctx* c_, int id_, cudaStream_t s_, uint64_t u) : c(c_), id(id_), s(s_), units(u) { prof_begin(c, id, s, ev); }
+  ~ProfScope() { prof_end(c, id, s, ev, units); }
 };
 
 // ---------------------------------------------------------------------- keys

@@ -561,7 +561,7 @@ int net_eval(Ctx* c, const KeySet* ks, Net* net, const uint64_t* d_in, size_t in
   TRY(bind_keys(c, net, ex, ks));
   const size_t blk = (size_t)c->kt * c->ct_words();
   TRY(transpose_msgs(ex->phys[ex->vmap[net->in_reg]].u64(), d_in, net->n_in, B, blk, true, s));
-  const bool profiling = c->prof.on[0] || c->prof.on[1] || c->prof.on[2] || c->prof.on[3];
+  const bool profiling = c->prof.any();
   if (use_graph && !profiling) {
     if (!ex->graph) {
       if (!ex->cap_stream) LOLA_CUDA_TRY(cudaStreamCreateWithFlags(&ex->cap_stream, cudaStreamNonBlocking));

@@ -305,7 +305,7 @@ static PrimeMap contiguous_map(uint32_t limbs, uint32_t prime0) {
 int ntt_fwd_map(Ctx* c, const uint64_t* in, uint64_t* out, size_t n_polys, uint32_t limbs, const PrimeMap& pm,
                 cudaStream_t s) {
   if (!n_polys) return LOLA_OK;
-  ProfScope ps(c, KK_NTT, s);
+  ProfScope ps(c, KI_NTT_FWD, s, n_polys);
   LOLA_DISPATCH(c->logn, kn_fwd, n_polys, s, c->dev, in, out, limbs, pm);
   return post_launch(c, s);
 }
@@ -313,7 +313,7 @@ int ntt_fwd_map(Ctx* c, const uint64_t* in, uint64_t* out, size_t n_polys, uint3
 int ntt_inv_map(Ctx* c, const uint64_t* in, uint64_t* out, size_t n_polys, uint32_t limbs, const PrimeMap& pm,
                 bool mont_fix, cudaStream_t s) {
   if (!n_polys) return LOLA_OK;
-  ProfScope ps(c, KK_NTT, s);
+  ProfScope ps(c, KI_NTT_INV, s, n_polys);
   LOLA_DISPATCH(c->logn, kn_inv, n_polys, s, c->dev, in, out, limbs, pm, (int)mont_fix);
   return post_launch(c, s);
 }
@@ -331,7 +331,7 @@ int ntt_fwd_from_signed(Ctx* c, const int64_t* in, uint64_t* out, size_t n_polys
                         cudaStream_t s) {
   if (!n_polys) return LOLA_OK;
   PrimeMap pm = contiguous_map(limbs, prime0);
-  ProfScope ps(c, KK_NTT, s);
+  ProfScope ps(c, KI_NTT_SIGNED, s, n_polys * limbs);
   LOLA_DISPATCH(c->logn, kn_fwd_signed, n_polys * limbs, s, c->dev, in, out, limbs, pm);
   return post_launch(c, s);
 }
@@ -339,7 +339,7 @@ int ntt_fwd_from_signed(Ctx* c, const int64_t* in, uint64_t* out, size_t n_polys
 int encode_lift(Ctx* c, const uint64_t* in, const uint32_t* d_tidx, uint64_t* out, size_t n_polys, uint32_t limbs,
                 bool mont, cudaStream_t s) {
   if (!n_polys) return LOLA_OK;
-  ProfScope ps(c, KK_NTT, s);
+  ProfScope ps(c, KI_ENCODE_LIFT, s, n_polys * limbs);
   LOLA_DISPATCH(c->logn, kn_encode_lift, n_polys * limbs, s, c->dev, in, d_tidx, out, limbs, (int)mont);
   return post_launch(c, s);
 }
@@ -347,7 +347,7 @@ int encode_lift(Ctx* c, const uint64_t* in, const uint32_t* d_tidx, uint64_t* ou
 int slots_to_coeff(Ctx* c, const uint64_t* slots, const uint32_t* d_tidx, uint64_t* coeff, size_t n_polys,
                    cudaStream_t s) {
   if (!n_polys) return LOLA_OK;
-  ProfScope ps(c, KK_NTT, s);
+  ProfScope ps(c, KI_SLOTS_TO_COEFF, s, n_polys);
   LOLA_DISPATCH(c->logn, kn_slots_to_coeff, n_polys, s, c->dev, slots, d_tidx, (const uint32_t*)c->d_slotpos.p, coeff);
   return post_launch(c, s);
 }
@@ -355,7 +355,7 @@ int slots_to_coeff(Ctx* c, const uint64_t* slots, const uint32_t* d_tidx, uint64
 int coeff_to_slots(Ctx* c, const uint64_t* coeff, const uint32_t* d_tidx, uint64_t* slots, size_t n_polys,
                    cudaStream_t s) {
   if (!n_polys) return LOLA_OK;
-  ProfScope ps(c, KK_NTT, s);
+  ProfScope ps(c, KI_COEFF_TO_SLOTS, s, n_polys);
   LOLA_DISPATCH(c->logn, kn_coeff_to_slots, n_polys, s, c->dev, coeff, d_tidx, (const uint32_t*)c->d_slotpos.p, slots);
   return post_launch(c, s);
 }
@@ -363,13 +363,13 @@ int coeff_to_slots(Ctx* c, const uint64_t* coeff, const uint32_t* d_tidx, uint64
 int enc_msg(Ctx* c, const uint64_t* m, const int64_t* e1, const uint32_t* d_tidx, uint64_t* out, size_t n_polys,
             cudaStream_t s) {
   if (!n_polys) return LOLA_OK;
-  ProfScope ps(c, KK_NTT, s);
+  ProfScope ps(c, KI_ENC_MSG, s, n_polys * c->L);
   LOLA_DISPATCH(c->logn, kn_enc_msg, n_polys * c->L, s, c->dev, m, e1, d_tidx, out, c->L);
   return post_launch(c, s);
 }
 
 int ks_decompose(Ctx* c, const KsDev& a, cudaStream_t s) {
-  ProfScope ps(c, KK_NTT, s);
+  ProfScope ps(c, KI_KS_DECOMPOSE, s, a.count * c->L);
   LOLA_DISPATCH(c->logn, kn_ks_decompose, a.count * c->L, s, c->dev, a);
   return post_launch(c, s);
 }
@@ -378,19 +378,19 @@ int ks_modup(Ctx* c, const KsDev& a, bool skip_diag, cudaStream_t s) {
   const uint32_t LK = c->L + c->K;
   const size_t per = skip_diag ? (size_t)c->L * (LK - 1) : (size_t)c->L * LK;
   if (!per) return LOLA_OK;
-  ProfScope ps(c, KK_NTT, s);
+  ProfScope ps(c, KI_KS_MODUP, s, a.count * per);
   LOLA_DISPATCH(c->logn, kn_ks_modup, a.count * per, s, c->dev, a, (int)skip_diag);
   return post_launch(c, s);
 }
 
 int ks_ip_p(Ctx* c, const KsDev& a, cudaStream_t s) {
-  ProfScope ps(c, KK_NTT, s);
+  ProfScope ps(c, KI_KS_IP_P, s, a.count * 2);
   LOLA_DISPATCH(c->logn, kn_ks_ip_p, a.count * 2, s, c->dev, a);
   return post_launch(c, s);
 }
 
 int ks_moddown(Ctx* c, const KsDev& a, cudaStream_t s) {
-  ProfScope ps(c, KK_NTT, s);
+  ProfScope ps(c, KI_KS_MODDOWN, s, a.count * 2 * c->L);
   LOLA_DISPATCH(c->logn, kn_ks_moddown, a.count * 2 * c->L, s, c->dev, a);
   return post_launch(c, s);
 }

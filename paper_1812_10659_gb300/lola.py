@@ -93,7 +93,10 @@ _SIGS = {
                                         C.c_uint32, I64P, U32P]),
     "lola_pack_stacked": (C.c_int, [I64P, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, I64P]),
     "lola_profile_enable": (C.c_int, [P, C.c_int, C.c_int]),
-    "lola_profile_read": (C.c_int, [P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_uint64)]),
+    "lola_profile_read": (C.c_int, [P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_uint64),
+                                    C.POINTER(C.c_uint64)]),
+    "lola_profile_kinds": (C.c_int, []),
+    "lola_profile_name": (C.c_char_p, [C.c_int]),
     "lola_launch_count": (C.c_uint64, [P]),
     "lola_last_error": (C.c_char_p, []),
     "lola_version": (C.c_char_p, []),
@@ -400,9 +403,18 @@ def lola_profile_enable(ctx, kind, on=True):
 
 
 def lola_profile_read(ctx, kind):
-    ms, cnt = C.c_double(), C.c_uint64()
-    _check(load().lola_profile_read(ctx, kind, C.byref(ms), C.byref(cnt)))
-    return ms.value, cnt.value
+    """(milliseconds, launches, work units) since the last enable."""
+    ms, cnt, units = C.c_double(), C.c_uint64(), C.c_uint64()
+    _check(load().lola_profile_read(ctx, kind, C.byref(ms), C.byref(cnt), C.byref(units)))
+    return ms.value, cnt.value, units.value
+
+
+def lola_profile_kinds() -> int:
+    return int(load().lola_profile_kinds())
+
+
+def lola_profile_name(kind) -> str:
+    return load().lola_profile_name(kind).decode()
 
 
 def lola_launch_count(ctx) -> int:
