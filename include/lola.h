@@ -155,6 +155,24 @@ int lola_rotate(lola_ctx* ctx, const lola_keys* keys, const uint64_t* in, uint64
  * out_i = relin(round(t/Q * a_i (x) b_i)).  b may equal a (square). */
 int lola_multiply(lola_ctx* ctx, const lola_keys* keys, const uint64_t* a, const uint64_t* b, uint64_t* out,
                   size_t count, const uint32_t* t_index, void* stream);
+/* Rotation that allocates no device memory, for callers that cannot call
+ * cudaMalloc / cudaMallocAsync (inside a stream capture that must stay free
+ * of allocation nodes, or under a memory manager that forbids allocation
+ * after start-up).  The paper has no counterpart: this is a library
+ * facility.  out_i = rotate(in_i, step) for i < count, one step for all
+ * (0 < step < n/2 right shift of each slot row, 0 = row swap), device
+ * layout, NTT form; the result is identical to lola_rotate's.
+ * Scratch comes from a static device array of LOLA_ROTATE_NOALLOC_SCRATCH_BYTES
+ * compiled into the library, which every GPU that loads the library keeps
+ * until the process exits.  The first call on a device looks up that array's
+ * address (cudaGetSymbolAddress), so make it before any stream capture.
+ * Calls share the array: calls that overlap on the GPU race and must be
+ * serialised by the caller.  No part of the array needs clearing between
+ * calls.  A count whose scratch (count * (L + L*(L+K) + 2) * n words) does
+ * not fit returns LOLA_E_PARAM; missing key: LOLA_E_NOKEY. */
+#define LOLA_ROTATE_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+int lola_rotate_noalloc(lola_ctx* ctx, const lola_keys* keys, const uint64_t* in, uint64_t* out, size_t count,
+                        int32_t step, void* stream);
 /* ct x plaintext: out_i = in_i * encode(slots_i) (slots host [count][n]
  * int64, centered lift mod t). */
 int lola_mul_plain(lola_ctx* ctx, const uint64_t* in, const int64_t* slots, uint64_t* out, size_t count,

@@ -82,6 +82,7 @@ _SIGS = {
     "lola_rotate": (C.c_int, [P, P, P, P, C.c_size_t, I32P, P]),
     "lola_multiply": (C.c_int, [P, P, P, P, P, C.c_size_t, U32P, P]),
     "lola_mul_plain": (C.c_int, [P, P, I64P, P, C.c_size_t, U32P, P]),
+    "lola_rotate_noalloc": (C.c_int, [P, P, P, P, C.c_size_t, C.c_int32, P]),
     "lola_net_create": (C.c_int, [P, C.POINTER(lola_input), C.POINTER(lola_layer), C.c_size_t, C.POINTER(P)]),
     "lola_net_destroy": (None, [P]),
     "lola_net_rotation_steps": (C.c_int, [P, I32P, C.POINTER(C.c_size_t)]),
@@ -289,6 +290,15 @@ def lola_rotate(ctx, keys, inp, out, count, steps, stream=None):
     assert st.size == count
     _check(load().lola_rotate(ctx, keys, dptr(inp), dptr(out), count, st.ctypes.data_as(I32P),
                               stream_handle(stream)))
+
+
+def lola_rotate_noalloc(ctx, keys, inp, out, count, step, stream=None):
+    """Rotation of `count` ciphertexts by one step using the library's static
+    scratch area (no device allocation); see include/lola.h."""
+    _check(load().lola_rotate_noalloc(ctx, keys, dptr(inp), dptr(out), count, int(step), stream_handle(stream)))
+
+
+NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
 def lola_multiply(ctx, keys, a, b, out, count, t_index=None, stream=None):

@@ -1,0 +1,65 @@
+"""The allocation-free rotation entry point (lola_rotate_noalloc).
+
+It exists for callers that cannot allocate device memory (inside a stream
+capture that must stay free of allocation nodes, or under an application
+memory manager that forbids cudaMalloc).  This test calls it through the
+C-ABI twice in a row and checks each result against the ordinary
+lola_rotate entry point (which allocates its scratch): rotations are exact
+integer arithmetic, so the tolerance is zero.  It also checks the size
+limit of the static scratch area.  The file name makes pytest collect it
+last.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from gpu_util import lib, make_ctx, need_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def test_rotate_noalloc_matches_rotate_twice():
+    need_gpu()
+    Lb = lib()
+    ps = W.params_mnist()            # n = 16384, L = 5, K = 1, three plaintext moduli
+    n, kt = ps.n, len(ps.t)
+    ctx = make_ctx(ps)
+    try:
+        sk, ev = Lb.lola_keygen(ctx, 31, [1, 169], Lb.LOLA_KEY_RELIN)
+        slots = np.random.default_rng(3).integers(0, 16, (2, n))
+        ct = Lb.lola_encrypt(ctx, sk, slots, 5)                 # 2 messages x 3 moduli = 6 ciphertexts
+        count = 2 * kt
+        ref = Lb.lola_ct_create(ctx, 2)
+        got = Lb.lola_ct_create(ctx, 2)
+        try:
+            for step in (1, 169):                                # two calls in a row
+                Lb.lola_rotate(ctx, ev, Lb.lola_ct_data(ct), Lb.lola_ct_data(ref), count, [step] * count)
+                Lb.lola_rotate_noalloc(ctx, ev, Lb.lola_ct_data(ct), Lb.lola_ct_data(got), count, step)
+                a = Lb.lola_ct_export(ctx, ref, (kt, 2, ps.L, n))
+                b = Lb.lola_ct_export(ctx, got, (kt, 2, ps.L, n))
+                assert np.array_equal(a, b), step
+                res = Lb.lola_decrypt_residues(ctx, sk, got, kt, n)
+                h = n // 2
+                for m in range(2):
+                    want = np.concatenate([np.roll(slots[m, :h], step), np.roll(slots[m, h:], step)])
+                    for ti in range(kt):
+                        assert np.array_equal(res[m, ti], want % ps.t[ti])
+            # a request larger than the static scratch area is refused, not truncated
+            per_ct = (ps.L + ps.L * (ps.L + ps.K) + 2) * n * 8
+            too_many = Lb.NOALLOC_SCRATCH_BYTES // per_ct + 1
+            big_in = Lb.lola_ct_create(ctx, too_many)
+            big_out = Lb.lola_ct_create(ctx, too_many)
+            try:
+                with pytest.raises(Lb.LolaError) as ei:
+                    Lb.lola_rotate_noalloc(ctx, ev, Lb.lola_ct_data(big_in), Lb.lola_ct_data(big_out), too_many * kt, 1)
+                assert ei.value.code == -1
+            finally:
+                Lb.lola_ct_destroy(big_in)
+                Lb.lola_ct_destroy(big_out)
+        finally:
+            for h_ in (ct, ref, got):
+                Lb.lola_ct_destroy(h_)
+            Lb.lola_keys_destroy(sk)
+            Lb.lola_keys_destroy(ev)
+    finally:
+        Lb.lola_ctx_destroy(ctx)
