@@ -184,8 +184,10 @@ KERNEL_BYTES = {
     # transform kernels: one unit = one limb-polynomial
     "ks_modup": lambda n, L: 16 * n,                 # read digit limb, write one mod-up limb
     "ks_decompose": lambda n, L: 24 * n,             # read c1 limb, write diagonal + digit
-    "ks_moddown": lambda n, L: (2 * L + 5) * 8 * n,  # x_P, L digit limbs, L key limbs, addend, accum in; out
-    "ks_ip_p": lambda n, L: (2 * L + 1) * 8 * n,     # L digit limbs + L key limbs in, one limb out
+    "ks_moddown": lambda n, L: 5 * 8 * n,            # x_P, inner product, addend, accumulator in; out
+    "ks_intt_p": lambda n, L: 16 * n,                # special-prime inner product in, x_P out
+    # inner product: one unit = two coefficients of one (ct, prime): L digit words in, 2 words out, each x2
+    "ks_ip": lambda n, L: 2 * 8 * (L + 2),
     "ntt_fwd": lambda n, L: 16 * n,
     "ntt_inv": lambda n, L: 16 * n,
     # element-wise kernels: one unit = one output word

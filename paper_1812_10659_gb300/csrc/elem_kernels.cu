@@ -23,33 +23,74 @@ static unsigned grid_for(size_t items, int threads) {
 }
 
 // ------------------------------------------------------------- key switching
-// K = 0 output stage: out[comp][j] = sum_i D[i][j] key[comp][i][j]
-//                                    (+ tau_g(c0)_j, + add1_j, + accum)
-__global__ void ke_ks_ip_q(const CtxDev* __restrict__ C, KsDev a) {
+// REDC of a 128-bit sum T < q 2^64: T 2^-64 mod q in [0, q).
+__device__ __forceinline__ uint64_t redc128(unsigned __int128 T, uint64_t q, uint64_t qinv) {
+  const uint64_t lo = (uint64_t)T, hi = (uint64_t)(T >> 64);
+  const uint64_t m = lo * qinv;
+  return csub(hi + mulhi64(m, q) + (lo != 0), q);
+}
+
+// Inner product over the digits, both key components at once:
+//   ACC[comp][j] = sum_i D[i][j] * key[comp][i][j]   (keys are Montgomery-scaled)
+// Products are summed in 128 bits and reduced once (every 8 terms: 8 q^2 < q 2^64
+// for q < 2^61).  Each thread owns two adjacent coefficients of one (ct, j).
+// final_out (K = 0): write the switched ciphertext limb directly, plus addends.
+// Otherwise write ACC; the caller may place ACC over D's digit rows 0 and 1:
+// a thread reads every D word it overwrites before writing it.
+__global__ void ke_ks_ip(const CtxDev* __restrict__ C, KsDev a, int final_out) {
   const int L = C->L, LK = C->L + C->K, logn = C->logn;
-  const size_t n = C->n;
-  const size_t total = a.count * 2 * L * n;
+  const size_t n = C->n, half = n >> 1;
+  const int J = final_out ? L : LK;
+  const size_t total = a.count * J * half;
   for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < total; w += (size_t)gridDim.x * blockDim.x) {
-    const uint32_t k = w & (n - 1);
-    const size_t r = w >> logn;
-    const int j = r % L;
-    const int comp = (r / L) & 1;
-    const size_t ct = r / (2 * L);
+    const size_t k = 2 * (w % half);
+    const size_t r = w / half;
+    const int j = r % J;
+    const size_t ct = r / J;
     const PrimeDev& P = C->pr[j];
     const uint64_t* key = a.d_keys ? a.d_keys[ct / a.gal_div] : a.key;
-    uint64_t acc = 0;
+    uint64_t acc0[2] = {0, 0}, acc1[2] = {0, 0};
+    unsigned __int128 s0[2] = {0, 0}, s1[2] = {0, 0};
     for (int i = 0; i < L; ++i) {
-      const uint64_t d = a.D[((ct * L + i) * LK + j) * n + k];
-      const uint64_t kw = key[((size_t)(comp * L + i) * LK + j) * n + k];
-      acc = add_mod(acc, mont_mul(d, kw, P.q, P.qinv), P.q);
+      const ulonglong2 d = *(const ulonglong2*)(a.D + ((ct * L + i) * LK + j) * n + k);
+      const ulonglong2 k0 = __ldg((const ulonglong2*)(key + ((size_t)i * LK + j) * n + k));
+      const ulonglong2 k1 = __ldg((const ulonglong2*)(key + ((size_t)(L + i) * LK + j) * n + k));
+      s0[0] += (unsigned __int128)d.x * k0.x;
+      s0[1] += (unsigned __int128)d.y * k0.y;
+      s1[0] += (unsigned __int128)d.x * k1.x;
+      s1[1] += (unsigned __int128)d.y * k1.y;
+      if ((i & 7) == 7 || i == L - 1) {
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          acc0[e] = add_mod(acc0[e], redc128(s0[e], P.q, P.qinv), P.q);
+          acc1[e] = add_mod(acc1[e], redc128(s1[e], P.q, P.qinv), P.q);
+          s0[e] = s1[e] = 0;
+        }
+      }
     }
-    if (comp == 0 && a.c0) {
+    if (final_out) {
       const uint32_t g = a.d_gal ? a.d_gal[ct / a.gal_div] : a.gal;
-      acc = add_mod(acc, a.c0[(ct * 2 * L + j) * n + (g == 1 ? k : gal_src(k, g, logn))], P.q);
+      uint64_t* o0 = a.out + ((ct * 2 + 0) * L + j) * n;
+      uint64_t* o1 = a.out + ((ct * 2 + 1) * L + j) * n;
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const size_t kk = k + e;
+        uint64_t v0 = acc0[e], v1 = acc1[e];
+        if (a.c0) v0 = add_mod(v0, a.c0[(ct * 2 * L + j) * n + (g == 1 ? kk : gal_src((uint32_t)kk, g, logn))], P.q);
+        if (a.add1) v1 = add_mod(v1, a.add1[(ct * 2 * L + L + j) * n + kk], P.q);
+        if (a.accum) {
+          v0 = add_mod(v0, a.accum[((ct * 2 + 0) * L + j) * n + kk], P.q);
+          v1 = add_mod(v1, a.accum[((ct * 2 + 1) * L + j) * n + kk], P.q);
+        }
+        o0[kk] = v0;
+        o1[kk] = v1;
+      }
+    } else {
+      uint64_t* A0 = a.acc + ct * a.acc_stride + (size_t)j * n + k;
+      uint64_t* A1 = a.acc + ct * a.acc_stride + (size_t)(LK + j) * n + k;
+      *(ulonglong2*)A0 = make_ulonglong2(acc0[0], acc0[1]);
+      *(ulonglong2*)A1 = make_ulonglong2(acc1[0], acc1[1]);
     }
-    if (comp == 1 && a.add1) acc = add_mod(acc, a.add1[(ct * 2 * L + L + j) * n + k], P.q);
-    if (a.accum) acc = add_mod(acc, a.accum[w], P.q);
-    a.out[w] = acc;
   }
 }
 
@@ -396,8 +437,9 @@ namespace k {
     KERNEL<<<grid_for(items, 256), 256, 0, s>>>(__VA_ARGS__);                       \
   } while (0)
 
-int ks_ip_q(Ctx* c, const KsDev& a, cudaStream_t s) {
-  ELEM_LAUNCH(KI_KS_IP_Q, ke_ks_ip_q, a.count * 2 * c->L * c->n, c->dev, a);
+int ks_ip(Ctx* c, const KsDev& a, bool final_out, cudaStream_t s) {
+  const size_t pairs = a.count * (final_out ? c->L : c->L + c->K) * (c->n / 2);
+  ELEM_LAUNCH(KI_KS_IP_Q, ke_ks_ip, pairs, c->dev, a, (int)final_out);
   return post(c);
 }
 

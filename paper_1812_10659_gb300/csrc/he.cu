@@ -109,9 +109,30 @@ struct AsyncBuf {
   } while (0)
 
 // --------------------------------------------------------------- key switching
+// scratch: digits [count][L][n], mod-up limbs D [count][L][L+K][n], x_P
+// [count][2][n]; the inner products live in place over D's digit rows 0
+// and 1 (a separate [count][2][L+K][n] area when L = 1).
 size_t rotate_scratch_words(const Ctx* c, size_t count) {
   const size_t LK = c->L + c->K;
-  return count * (c->L + c->L * LK + 2) * (size_t)c->n;
+  size_t w = count * (c->L + c->L * LK + 2) * (size_t)c->n;
+  if (c->L < 2) w += count * 2 * LK * (size_t)c->n;
+  return w;
+}
+
+// Inner product + (special prime) mod-down, shared by rotation and relinearisation.
+static int ks_finish(Ctx* c, KsDev& a, uint64_t* extra_acc, cudaStream_t s) {
+  const size_t n = c->n, L = c->L, LK = c->L + c->K;
+  if (!c->K) return k::ks_ip(c, a, true, s);
+  if (L >= 2) {
+    a.acc = a.D;
+    a.acc_stride = L * LK * n;
+  } else {
+    a.acc = extra_acc;
+    a.acc_stride = 2 * LK * n;
+  }
+  TRY(k::ks_ip(c, a, false, s));
+  TRY(k::ks_intt_p(c, a, s));
+  return k::ks_moddown(c, a, s);
 }
 
 int rotate(Ctx* c, const uint64_t* in, uint64_t* out, const uint64_t* accum, size_t count, const RotSpec& r,
@@ -135,13 +156,7 @@ int rotate(Ctx* c, const uint64_t* in, uint64_t* out, const uint64_t* accum, siz
   a.gal_div = r.div ? r.div : 1;
   TRY(k::ks_decompose(c, a, s));
   TRY(k::ks_modup(c, a, true, s));
-  if (c->K) {
-    TRY(k::ks_ip_p(c, a, s));
-    TRY(k::ks_moddown(c, a, s));
-  } else {
-    TRY(k::ks_ip_q(c, a, s));
-  }
-  return LOLA_OK;
+  return ks_finish(c, a, a.xP + count * 2 * n, s);
 }
 
 // ---------------------------------------------------------- ct x ct (Sec. 3.1 (x))
@@ -152,6 +167,7 @@ size_t multiply_scratch_words(const Ctx* c, size_t count, bool square) {
   w += count * 3 * (L + M) * n;                        // T
   w += count * 2 * L * n + count * L * n;              // E, DIG
   w += count * L * LK * n + count * 2 * n;             // D, xP
+  if (L < 2) w += count * 2 * LK * n;                  // inner products (L = 1)
   return w;
 }
 
@@ -206,13 +222,7 @@ int multiply(Ctx* c, const uint64_t* x, const uint64_t* y, uint64_t* out, size_t
   a.key = relin_key;
   a.gal_div = 1;
   TRY(k::ks_modup(c, a, false, s));
-  if (c->K) {
-    TRY(k::ks_ip_p(c, a, s));
-    TRY(k::ks_moddown(c, a, s));
-  } else {
-    TRY(k::ks_ip_q(c, a, s));
-  }
-  return LOLA_OK;
+  return ks_finish(c, a, xP + count * 2 * n, s);
 }
 
 // --------------------------------------------------------------------- keys

@@ -31,6 +31,8 @@ struct KsDev {
   uint64_t* dig;          // scratch / input digits [count][L][n] coefficient form
   uint64_t* D;            // scratch [count][L][L+K][n]
   uint64_t* xP;           // scratch [count][2][n]
+  uint64_t* acc;          // inner products: ACC(ct, comp, j) = acc + ct * acc_stride + (comp * (L+K) + j) * n
+  size_t acc_stride;      // (in place over D's first two digit rows when L >= 2)
   size_t count;
   const uint32_t* d_gal;  // per-entry Galois element or null (use gal)
   uint32_t gal;
@@ -60,11 +62,11 @@ int enc_msg(Ctx* c, const uint64_t* m, const int64_t* e1, const uint32_t* d_tidx
             cudaStream_t s);
 int ks_decompose(Ctx* c, const KsDev& a, cudaStream_t s);
 int ks_modup(Ctx* c, const KsDev& a, bool skip_diag, cudaStream_t s);
-int ks_ip_p(Ctx* c, const KsDev& a, cudaStream_t s);
+int ks_intt_p(Ctx* c, const KsDev& a, cudaStream_t s);
 int ks_moddown(Ctx* c, const KsDev& a, cudaStream_t s);
 
 // element-wise / basis conversion (elem_kernels.cu)
-int ks_ip_q(Ctx* c, const KsDev& a, cudaStream_t s);   // K = 0 output stage
+int ks_ip(Ctx* c, const KsDev& a, bool final_out, cudaStream_t s);   // inner product over digits
 int add(Ctx* c, const uint64_t* a, const uint64_t* b, uint64_t* out, size_t count, cudaStream_t s);
 int sub(Ctx* c, const uint64_t* a, const uint64_t* b, uint64_t* out, size_t count, cudaStream_t s);
 int to_mont_map(Ctx* c, uint64_t* data, size_t n_limbpolys, uint32_t limbs, const PrimeMap& pm, cudaStream_t s,

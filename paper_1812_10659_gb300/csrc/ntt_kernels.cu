@@ -185,37 +185,23 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T) kn_ks_modup(const CtxDev* __rest
                                       [&](int k, uint64_t v) { dst[k] = v; });
 }
 
-__device__ __forceinline__ const uint64_t* ks_key(const KsDev& a, size_t ct) {
-  return a.d_keys ? a.d_keys[ct / a.gal_div] : a.key;
-}
-
-// D: inner product over digits for the special prime, then inverse transform mod P
+// D: inverse transform of the special-prime inner products (both components)
 template <int LOGN>
-__global__ void __launch_bounds__(Cfg<LOGN>::T) kn_ks_ip_p(const CtxDev* __restrict__ C, KsDev a) {
+__global__ void __launch_bounds__(Cfg<LOGN>::T) kn_ks_intt_p(const CtxDev* __restrict__ C, KsDev a) {
   extern __shared__ uint64_t sm[];
   constexpr int N = Cfg<LOGN>::N;
-  const int L = C->L, LK = C->L + C->K, ip = C->iP;
+  const int LK = C->L + C->K, ip = C->iP;
   const size_t ct = blockIdx.x >> 1;
   const int comp = blockIdx.x & 1;
-  const uint64_t* key = ks_key(a, ct);
   const PrimeDev& P = C->pr[ip];
+  const uint64_t* src = a.acc + ct * a.acc_stride + (size_t)(comp * LK + ip) * N;
   uint64_t* dst = a.xP + (ct * 2 + comp) * (size_t)N;
-  ntt_inverse<LOGN, Cfg<LOGN>::LOGE>(
-      sm, TW_I(C, ip), P.q, P.ninv, P.ninv_s,
-      [&](int k) {
-        uint64_t acc = 0;
-        for (int i = 0; i < L; ++i) {
-          const uint64_t d = a.D[((ct * L + i) * LK + ip) * (size_t)N + k];
-          const uint64_t w = key[((size_t)(comp * L + i) * LK + ip) * N + k];
-          acc = add_mod(acc, mont_mul(d, w, P.q, P.qinv), P.q);
-        }
-        return acc;
-      },
-      [&](int k, uint64_t v) { dst[k] = v; });
+  ntt_inverse<LOGN, Cfg<LOGN>::LOGE>(sm, TW_I(C, ip), P.q, P.ninv, P.ninv_s, [&](int k) { return src[k]; },
+                                      [&](int k, uint64_t v) { dst[k] = v; });
 }
 
 // E: x~ = centered(x mod P) reduced mod q_j and transformed; output limb
-//    out[comp][j] = (sum_i D[i][j] key[comp][i][j] - NTT(x~)) P^-1
+//    out[comp][j] = (ACC[comp][j] - NTT(x~)) P^-1
 //                   (+ tau_g(c0)_j for comp 0, + add1_j for comp 1, + accum)
 template <int LOGN>
 __global__ void __launch_bounds__(Cfg<LOGN>::T) kn_ks_moddown(const CtxDev* __restrict__ C, KsDev a) {
@@ -226,7 +212,7 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T) kn_ks_moddown(const CtxDev* __re
   const int r = blockIdx.x % (2 * L);
   const int comp = r / L, j = r % L;
   const uint32_t g = a.d_gal ? a.d_gal[ct / a.gal_div] : a.gal;
-  const uint64_t* key = ks_key(a, ct);
+  const uint64_t* accp = a.acc + ct * a.acc_stride + (size_t)(comp * LK + j) * N;
   const PrimeDev& P = C->pr[j];
   const uint64_t Pq = C->pr[C->iP].q;
   const uint64_t PmodQ = C->PmodQ[j], Pinv = C->PinvQ[j], Pinv_s = C->PinvQ_s[j];
@@ -243,13 +229,7 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T) kn_ks_moddown(const CtxDev* __re
         return v > (Pq - 1) / 2 ? sub_mod(r0, PmodQ, P.q) : r0;
       },
       [&](int k, uint64_t v) {
-        uint64_t acc = 0;
-        for (int i = 0; i < L; ++i) {
-          const uint64_t d = a.D[((ct * L + i) * LK + j) * (size_t)N + k];
-          const uint64_t w = key[((size_t)(comp * L + i) * LK + j) * N + k];
-          acc = add_mod(acc, mont_mul(d, w, P.q, P.qinv), P.q);
-        }
-        uint64_t res = shoup_mul(sub_mod(acc, v, P.q), Pinv, Pinv_s, P.q);
+        uint64_t res = shoup_mul(sub_mod(accp[k], v, P.q), Pinv, Pinv_s, P.q);
         if (comp == 0 && c0) res = add_mod(res, c0[g == 1 ? k : gal_src(k, g, LOGN)], P.q);
         if (comp == 1 && ad1) res = add_mod(res, ad1[k], P.q);
         if (acc_in) res = add_mod(res, acc_in[k], P.q);
@@ -383,9 +363,9 @@ int ks_modup(Ctx* c, const KsDev& a, bool skip_diag, cudaStream_t s) {
   return post_launch(c, s);
 }
 
-int ks_ip_p(Ctx* c, const KsDev& a, cudaStream_t s) {
+int ks_intt_p(Ctx* c, const KsDev& a, cudaStream_t s) {
   ProfScope ps(c, KI_KS_IP_P, s, a.count * 2);
-  LOLA_DISPATCH(c->logn, kn_ks_ip_p, a.count * 2, s, c->dev, a);
+  LOLA_DISPATCH(c->logn, kn_ks_intt_p, a.count * 2, s, c->dev, a);
   return post_launch(c, s);
 }
 
