@@ -41,6 +41,7 @@ def _newest_input() -> float:
 
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     os.makedirs(OUT, exist_ok=True)
+    extra = tuple(extra) + tuple(f for f in os.environ.get("LOLA_NVCC_DEFINES", "").split() if f.startswith("-D"))
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _newest_input():
         return LIB
     cc = nvcc()

@@ -37,10 +37,8 @@ struct CtxDev {
   int iB;                          // first auxiliary prime index (= L + K)
   int iT;                          // first plaintext modulus index (= L + K + M)
   PrimeDev pr[MAXP];
-  const uint64_t* tw_fwd;          // [np][n]
-  const uint64_t* tw_fwd_s;
-  const uint64_t* tw_inv;
-  const uint64_t* tw_inv_s;
+  const uint64_t* tw_fwd;          // [np][n] pairs (w, floor(w 2^64 / q))
+  const uint64_t* tw_inv;          // [np][n] pairs for psi^-1
   // --- exact lifts Q -> B and B -> Q ---
   MrcDev mrcQ;                     // over q_0..q_{L-1}
   MrcDev mrcB;                     // over the aux primes b_0..b_{M-1}
@@ -59,7 +57,7 @@ struct CtxDev {
   uint64_t deltaQ[MAXT][MAXB];                    // floor(Q/t) mod q_i
   uint64_t deltaQ_s[MAXT][MAXB];
   // --- key switching (K = 1) ---
-  uint64_t PmodQ[MAXB];
+  uint64_t PmodQ[MAXB], PmodQ_s[MAXB];
   uint64_t PinvQ[MAXB], PinvQ_s[MAXB];            // P^-1 mod q_i
   uint64_t PmontQ[MAXB];                          // (P mod q_i) 2^64 mod q_i (P = 1 when K = 0)
 };

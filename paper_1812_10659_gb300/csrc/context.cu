@@ -253,10 +253,8 @@ static int build_ctx(Ctx* c, const lola_params* p) {
   H.iT = c->iT();
   const uint64_t n = c->n;
   std::vector<uint64_t> tw((size_t)4 * np * n);
-  uint64_t* twf = tw.data();
-  uint64_t* twfs = twf + (size_t)np * n;
-  uint64_t* twi = twfs + (size_t)np * n;
-  uint64_t* twis = twi + (size_t)np * n;
+  uint64_t* twf = tw.data();                  // [np][n][2]: (w, w')
+  uint64_t* twi = twf + (size_t)2 * np * n;
   for (uint32_t pi = 0; pi < np; ++pi) {
     const uint64_t q = c->primes[pi];
     PrimeDev& P = H.pr[pi];
@@ -282,10 +280,10 @@ static int build_ctx(Ctx* c, const lola_params* p) {
     for (uint32_t i = 0; i < n; ++i) {
       const uint32_t e = brev_h(i, c->logn);
       const uint64_t w = pw[e], wi = ipw[e];
-      twf[(size_t)pi * n + i] = w;
-      twfs[(size_t)pi * n + i] = shoup_h(w, q);
-      twi[(size_t)pi * n + i] = wi;
-      twis[(size_t)pi * n + i] = shoup_h(wi, q);
+      twf[((size_t)pi * n + i) * 2] = w;
+      twf[((size_t)pi * n + i) * 2 + 1] = shoup_h(w, q);
+      twi[((size_t)pi * n + i) * 2] = wi;
+      twi[((size_t)pi * n + i) * 2 + 1] = shoup_h(wi, q);
     }
   }
   // exact conversion constants
@@ -336,6 +334,7 @@ static int build_ctx(Ctx* c, const lola_params* p) {
   for (uint32_t i = 0; i < c->L; ++i) {
     const uint64_t q = Qb[i];
     H.PmodQ[i] = P % q;
+    H.PmodQ_s[i] = shoup_h(H.PmodQ[i], q);
     H.PinvQ[i] = c->K ? invmod_h(P % q, q) : 1;
     H.PinvQ_s[i] = shoup_h(H.PinvQ[i], q);
     const uint64_t r1 = (uint64_t)(((u128)1 << 64) % q);
@@ -358,9 +357,7 @@ static int build_ctx(Ctx* c, const lola_params* p) {
   if ((rc = c->d_tw.alloc(tw.size() * 8)) != LOLA_OK) return rc;
   LOLA_CUDA_TRY(cudaMemcpy(c->d_tw.p, tw.data(), tw.size() * 8, cudaMemcpyHostToDevice));
   H.tw_fwd = c->d_tw.u64();
-  H.tw_fwd_s = H.tw_fwd + (size_t)np * n;
-  H.tw_inv = H.tw_fwd_s + (size_t)np * n;
-  H.tw_inv_s = H.tw_inv + (size_t)np * n;
+  H.tw_inv = H.tw_fwd + (size_t)2 * np * n;
   if ((rc = c->d_slotpos.alloc(n * 4)) != LOLA_OK) return rc;
   LOLA_CUDA_TRY(cudaMemcpy(c->d_slotpos.p, slot_at_pos.data(), n * 4, cudaMemcpyHostToDevice));
   if ((rc = c->d_const.alloc(sizeof(CtxDev))) != LOLA_OK) return rc;

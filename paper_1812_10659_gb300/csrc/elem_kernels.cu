@@ -69,14 +69,14 @@ __global__ void ke_ks_ip(const CtxDev* __restrict__ C, KsDev a, int final_out) {
       }
     }
     if (final_out) {
-      const uint32_t g = a.d_gal ? a.d_gal[ct / a.gal_div] : a.gal;
       uint64_t* o0 = a.out + ((ct * 2 + 0) * L + j) * n;
       uint64_t* o1 = a.out + ((ct * 2 + 1) * L + j) * n;
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
         const size_t kk = k + e;
         uint64_t v0 = acc0[e], v1 = acc1[e];
-        if (a.c0) v0 = add_mod(v0, a.c0[(ct * 2 * L + j) * n + (g == 1 ? kk : gal_src((uint32_t)kk, g, logn))], P.q);
+        if (a.c0p) v0 = add_mod(v0, a.c0p[(ct * L + j) * n + kk], P.q);
+        else if (a.c0) v0 = add_mod(v0, a.c0[(ct * 2 * L + j) * n + kk], P.q);
         if (a.add1) v1 = add_mod(v1, a.add1[(ct * 2 * L + L + j) * n + kk], P.q);
         if (a.accum) {
           v0 = add_mod(v0, a.accum[((ct * 2 + 0) * L + j) * n + kk], P.q);
@@ -86,6 +86,25 @@ __global__ void ke_ks_ip(const CtxDev* __restrict__ C, KsDev a, int final_out) {
         o1[kk] = v1;
       }
     } else {
+      if (j < L) {
+        // fold the addends: out = (ACC + (addend + accum) P - NTT(x~)) P^-1
+        //                       = (ACC - NTT(x~)) P^-1 + addend + accum
+        const uint64_t Pm = C->PmodQ[j], Pms = C->PmodQ_s[j];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const size_t kk = k + e;
+          uint64_t s0v = 0, s1v = 0;
+          if (a.c0p) s0v = a.c0p[(ct * L + j) * n + kk];
+          else if (a.c0) s0v = a.c0[(ct * 2 * L + j) * n + kk];
+          if (a.add1) s1v = a.add1[(ct * 2 * L + L + j) * n + kk];
+          if (a.accum) {
+            s0v = add_mod(s0v, a.accum[((ct * 2 + 0) * L + j) * n + kk], P.q);
+            s1v = add_mod(s1v, a.accum[((ct * 2 + 1) * L + j) * n + kk], P.q);
+          }
+          acc0[e] = add_mod(acc0[e], shoup_mul(s0v, Pm, Pms, P.q), P.q);
+          acc1[e] = add_mod(acc1[e], shoup_mul(s1v, Pm, Pms, P.q), P.q);
+        }
+      }
       uint64_t* A0 = a.acc + ct * a.acc_stride + (size_t)j * n + k;
       uint64_t* A1 = a.acc + ct * a.acc_stride + (size_t)(LK + j) * n + k;
       *(ulonglong2*)A0 = make_ulonglong2(acc0[0], acc0[1]);

@@ -17,13 +17,24 @@ __device__ __forceinline__ uint32_t gal_src(uint32_t k, uint32_t g, int logn) {
   return brev_n((e2 - 1) >> 1, logn);
 }
 
+// Inverse of the map above: the position k whose gal_src is i (ginv = g^-1 mod 2n).
+__device__ __forceinline__ uint32_t gal_dst(uint32_t i, uint32_t ginv, int logn) { return gal_src(i, ginv, logn); }
+
+// g^-1 mod 2^32 for odd g (Newton iteration), reduced mod 2n by the caller's mask
+__device__ __forceinline__ uint32_t inv_odd32(uint32_t g) {
+  uint32_t x = g;
+  for (int i = 0; i < 5; ++i) x *= 2u - g * x;
+  return x;
+}
+
 struct PrimeMap {
   uint8_t p[32];  // limb l of a polynomial uses prime index p[l]
 };
 
 // Arguments of the key-switching kernels (one batch of `count` ciphertexts).
 struct KsDev {
-  const uint64_t* c0;     // comp-0 addend: ciphertext (c0 limbs read through the Galois map) or e0
+  const uint64_t* c0;     // comp-0 addend in ciphertext layout, not permuted (relinearisation: e0)
+  uint64_t* c0p;          // rotation: tau_g(c0) written by the decompose kernel, [count][L][n]
   const uint64_t* c1;     // ciphertext whose c1 is switched (rotation), NTT form
   const uint64_t* add1;   // comp-1 addend (relinearisation: e1 in ciphertext layout) or null
   const uint64_t* accum;  // optional ciphertext added to the result (rotate-and-sum) or null

@@ -52,6 +52,12 @@ struct NttGeom {
   static constexpr int idone(int p) { return p == 0 ? 0 : ilb(p - 1) + LOGE; }
 };
 
+// Twiddle tables hold (w, floor(w 2^64 / q)) pairs so one 16-byte load
+// fetches both; `tw` points at the pair array of one prime, `tws` is unused.
+__device__ __forceinline__ ulonglong2 tw_pair(const uint64_t* __restrict__ tw, int ti) {
+  return __ldg(reinterpret_cast<const ulonglong2*>(tw) + ti);
+}
+
 template <int LOGN, int LOGE, int P>
 __device__ __forceinline__ void fwd_stages(uint64_t (&x)[1 << LOGE], const uint64_t* __restrict__ tw,
                                            const uint64_t* __restrict__ tws, uint64_t q, int tid) {
@@ -67,7 +73,8 @@ __device__ __forceinline__ void fwd_stages(uint64_t (&x)[1 << LOGE], const uint6
       if (k & (1 << lbit)) continue;
       const int j = win_index(tid, k, hb, lb);
       const int ti = (1 << s) + (j >> (bp + 1));
-      const uint64_t w = __ldg(tw + ti), wp = __ldg(tws + ti);
+      const ulonglong2 wq = tw_pair(tw, ti);
+      const uint64_t w = wq.x, wp = wq.y;
       uint64_t a = x[k];
       a = a >= q2 ? a - q2 : a;
       const uint64_t t = shoup_mul_lazy(x[k | (1 << lbit)], w, wp, q);
@@ -141,7 +148,8 @@ __device__ __forceinline__ void inv_stages(uint64_t (&x)[1 << LOGE], const uint6
       if (k & (1 << lbit)) continue;
       const int j = win_index(tid, k, hb, lb);
       const int ti = (1 << s) + (j >> (bp + 1));
-      const uint64_t w = __ldg(tw + ti), wp = __ldg(tws + ti);
+      const ulonglong2 wq = tw_pair(tw, ti);
+      const uint64_t w = wq.x, wp = wq.y;
       const uint64_t a = x[k], b = x[k | (1 << lbit)];
       uint64_t u = a + b;
       u = u >= q2 ? u - q2 : u;
@@ -187,6 +195,17 @@ __device__ __forceinline__ void ntt_inverse(uint64_t* sm, const uint64_t* __rest
   }
   uint64_t x[1 << LOGE];
   inv_pass<LOGN, LOGE, 0>(sm, x, tw, tws, q, c, cs, st, tid);
+}
+
+// Inverse transform of data the caller has already placed in shared memory
+// (element i at sm[swz<LOGE>(i)], canonical).  The first pass synchronises
+// before reading.
+template <int LOGN, int LOGE, class Storer>
+__device__ __forceinline__ void ntt_inverse_smem(uint64_t* sm, const uint64_t* __restrict__ tw,
+                                                 const uint64_t* __restrict__ tws, uint64_t q, uint64_t c,
+                                                 uint64_t cs, const Storer& st) {
+  uint64_t x[1 << LOGE];
+  inv_pass<LOGN, LOGE, 0>(sm, x, tw, tws, q, c, cs, st, (int)threadIdx.x);
 }
 
 }  // namespace lola

@@ -9,15 +9,21 @@
 
 namespace lola {
 
+// words per thread per pass at n = 16384 (2^5: 512 threads; 2^4: 1024 threads)
+#ifndef LOLA_NTT14_LOGE
+#define LOLA_NTT14_LOGE 4
+#endif
+
 template <int LOGN>
 struct Cfg {
-  static constexpr int LOGE = LOGN >= 14 ? 5 : 4;
+  static constexpr int LOGE = LOGN >= 14 ? LOLA_NTT14_LOGE : 4;
   static constexpr int N = 1 << LOGN;
   static constexpr int T = N >> LOGE;
 };
 
-#define TW_F(C, p) (C)->tw_fwd + (size_t)(p) * (1u << LOGN), (C)->tw_fwd_s + (size_t)(p) * (1u << LOGN)
-#define TW_I(C, p) (C)->tw_inv + (size_t)(p) * (1u << LOGN), (C)->tw_inv_s + (size_t)(p) * (1u << LOGN)
+// (w, w') pair tables, 2n words per prime
+#define TW_F(C, p) (C)->tw_fwd + (size_t)(p) * (2u << LOGN), nullptr
+#define TW_I(C, p) (C)->tw_inv + (size_t)(p) * (2u << LOGN), nullptr
 
 // ------------------------------------------------------------ plain transforms
 template <int LOGN>
@@ -142,28 +148,53 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T) kn_enc_msg(const CtxDev* __restr
 }
 
 // ------------------------------------------------------------- key switching
-// A: permute c1 (NTT form) by the Galois element, keep the permuted limb as
-//    the diagonal block D[i][i], inverse-transform it into digit i.
+// A: the Galois automorphism in NTT form is a permutation of positions.
+//    Load c0 limb i and c1 limb i coalesced and scatter them through the
+//    inverse permutation into shared memory; write tau_g(c0) and the permuted
+//    c1 limb (the diagonal block D[i][i]) back coalesced; inverse-transform the
+//    permuted c1 limb into digit i.
 template <int LOGN>
 __global__ void __launch_bounds__(Cfg<LOGN>::T) kn_ks_decompose(const CtxDev* __restrict__ C, KsDev a) {
   extern __shared__ uint64_t sm[];
-  constexpr int N = Cfg<LOGN>::N;
+  constexpr int N = Cfg<LOGN>::N, T = Cfg<LOGN>::T, LOGE = Cfg<LOGN>::LOGE;
   const int L = C->L, LK = C->L + C->K;
   const size_t ct = blockIdx.x / L;
   const int i = blockIdx.x % L;
   const uint32_t g = a.d_gal ? a.d_gal[ct / a.gal_div] : a.gal;
-  const uint64_t* src = a.c1 + (ct * 2 * L + L + i) * (size_t)N;
+  const uint32_t ginv = inv_odd32(g) & ((2u << LOGN) - 1);
+  const int tid = threadIdx.x;
+  const uint64_t* src0 = a.c1 + (ct * 2 * L + i) * (size_t)N;
+  const uint64_t* src1 = a.c1 + (ct * 2 * L + L + i) * (size_t)N;
+  uint64_t* c0p = a.c0p + (ct * L + i) * (size_t)N;
   uint64_t* diag = a.D + ((ct * L + i) * LK + i) * (size_t)N;
   uint64_t* dig = a.dig + (ct * L + i) * (size_t)N;
   const PrimeDev& P = C->pr[i];
-  ntt_inverse<LOGN, Cfg<LOGN>::LOGE>(
-      sm, TW_I(C, i), P.q, P.ninv, P.ninv_s,
-      [&](int k) {
-        const uint64_t v = src[g == 1 ? k : gal_src(k, g, LOGN)];
-        diag[k] = v;
-        return v;
-      },
-      [&](int k, uint64_t v) { dig[k] = v; });
+  // tau_g(c0)
+#pragma unroll 4
+  for (int k = 0; k < N / T; ++k) {
+    const int idx = tid + k * T;
+    sm[swz<LOGE>(gal_dst(idx, ginv, LOGN))] = src0[idx];
+  }
+  __syncthreads();
+#pragma unroll 4
+  for (int k = 0; k < N / T; ++k) {
+    const int idx = tid + k * T;
+    c0p[idx] = sm[swz<LOGE>(idx)];
+  }
+  __syncthreads();
+  // tau_g(c1): diagonal block, then digit
+#pragma unroll 4
+  for (int k = 0; k < N / T; ++k) {
+    const int idx = tid + k * T;
+    sm[swz<LOGE>(gal_dst(idx, ginv, LOGN))] = src1[idx];
+  }
+  __syncthreads();
+#pragma unroll 4
+  for (int k = 0; k < N / T; ++k) {
+    const int idx = tid + k * T;
+    diag[idx] = sm[swz<LOGE>(idx)];
+  }
+  ntt_inverse_smem<LOGN, LOGE>(sm, TW_I(C, i), P.q, P.ninv, P.ninv_s, [&](int k2, uint64_t v) { dig[k2] = v; });
 }
 
 // B: digit i reduced mod prime j, forward transform -> D[i][j]
@@ -201,8 +232,8 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T) kn_ks_intt_p(const CtxDev* __res
 }
 
 // E: x~ = centered(x mod P) reduced mod q_j and transformed; output limb
-//    out[comp][j] = (ACC[comp][j] - NTT(x~)) P^-1
-//                   (+ tau_g(c0)_j for comp 0, + add1_j for comp 1, + accum)
+//    out[comp][j] = (ACC'[comp][j] - NTT(x~)) P^-1, where the inner-product
+//    kernel already added (addend + accumulator) * P to ACC'.
 template <int LOGN>
 __global__ void __launch_bounds__(Cfg<LOGN>::T) kn_ks_moddown(const CtxDev* __restrict__ C, KsDev a) {
   extern __shared__ uint64_t sm[];
@@ -217,9 +248,6 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T) kn_ks_moddown(const CtxDev* __re
   const uint64_t Pq = C->pr[C->iP].q;
   const uint64_t PmodQ = C->PmodQ[j], Pinv = C->PinvQ[j], Pinv_s = C->PinvQ_s[j];
   const uint64_t* x = a.xP + (ct * 2 + comp) * (size_t)N;
-  const uint64_t* c0 = a.c0 ? a.c0 + (ct * 2 * L + j) * (size_t)N : nullptr;
-  const uint64_t* ad1 = a.add1 ? a.add1 + (ct * 2 * L + L + j) * (size_t)N : nullptr;
-  const uint64_t* acc_in = a.accum ? a.accum + ((ct * 2 + comp) * L + j) * (size_t)N : nullptr;
   uint64_t* dst = a.out + ((ct * 2 + comp) * L + j) * (size_t)N;
   ntt_forward<LOGN, Cfg<LOGN>::LOGE>(
       sm, TW_F(C, j), P.q,
@@ -228,13 +256,7 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T) kn_ks_moddown(const CtxDev* __re
         const uint64_t r0 = reduce64(v, P.q, P.f64);
         return v > (Pq - 1) / 2 ? sub_mod(r0, PmodQ, P.q) : r0;
       },
-      [&](int k, uint64_t v) {
-        uint64_t res = shoup_mul(sub_mod(accp[k], v, P.q), Pinv, Pinv_s, P.q);
-        if (comp == 0 && c0) res = add_mod(res, c0[g == 1 ? k : gal_src(k, g, LOGN)], P.q);
-        if (comp == 1 && ad1) res = add_mod(res, ad1[k], P.q);
-        if (acc_in) res = add_mod(res, acc_in[k], P.q);
-        dst[k] = res;
-      });
+      [&](int k, uint64_t v) { dst[k] = shoup_mul(sub_mod(accp[k], v, P.q), Pinv, Pinv_s, P.q); });
 }
 
 // ------------------------------------------------------------------ dispatch
