@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--L", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=1)
+    ap.add_argument("--mode", choices=["network", "serve"], default="network")
+    ap.add_argument("--rates", default="25,100,200", help="serve mode: Poisson arrival rates (requests/s)")
+    ap.add_argument("--duration", type=float, default=10.0, help="serve mode: seconds of arrivals per rate")
     return ap.parse_args()
 
 
@@ -384,10 +387,120 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------------- serving
+def run_serve(args):
+    """Serving mix: Poisson arrivals, 70 % MNIST-shaped networks and 30 %
+    transfer-learning heads, keys resident, memory-based admission; the
+    continuous-batching server against one-request-at-a-time evaluation."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from oracle import lola as OL
+    from paper_1812_10659_gb300 import lola as L, serve
+
+    ps2, ps4 = W.params_mnist(args.L), W.params_head(args.L)
+    n = ps2.n
+    ctx2 = L.lola_ctx_create(ps2.n, ps2.q, ps2.L, ps2.K, ps2.t)
+    ctx4 = L.lola_ctx_create(ps4.n, ps4.q, ps4.L, ps4.K, ps4.t)
+    mnet, Wh = W.mnist_net(), W.head_weights()
+    d2, l2 = {"repr": "convolution", "n_msgs": 25, "n_elems": 169}, W.layers_mnist(mnet, n)
+    d4, l4 = {"repr": "dense", "n_msgs": 1, "n_elems": 4096}, W.layers_head(Wh, n)
+    keys = {}
+    for name, ctx, d, layers in (("mnist", ctx2, d2, l2), ("head", ctx4, d4, l4)):
+        h = L.lola_net_create(ctx, d, layers)
+        st = h.rotation_steps()
+        h.destroy()
+        keys[name] = L.lola_keygen(ctx, W.DEFAULT_SEED, [x for x in st if x], L.LOLA_KEY_RELIN | L.LOLA_KEY_ROW_SWAP)
+    nets = {"mnist": (d2, l2, ctx2, keys["mnist"][1]), "head": (d4, l4, ctx4, keys["head"][1])}
+    pool = {"mnist": [], "head": []}
+    want = {"mnist": [], "head": []}
+    for i in range(8):
+        img = W.image(idx=5000 + i)
+        pool["mnist"].append(L.lola_encrypt(ctx2, keys["mnist"][0], L.lola_pack_convolution(img, 5, 5, 2, n)[0], 300 + i))
+        x = OL.int_conv(img, mnet.conv_w, 5, 5, 2)
+        x = OL.int_dense(OL.int_square(x), mnet.dense1_w)
+        want["mnist"].append(OL.int_dense(OL.int_square(x), mnet.dense2_w))
+        f = W.feature_vector(idx=5000 + i)
+        v = np.zeros((1, n), np.int64)
+        v[0, :4096] = f
+        pool["head"].append(L.lola_encrypt(ctx4, keys["head"][0], v, 400 + i))
+        want["head"].append(OL.int_dense(f, Wh))
+    omap = {}
+    for name, (d, layers, ctx, _) in nets.items():
+        h = L.lola_net_create(ctx, d, layers)
+        omap[name] = h.output_map()
+        h.destroy()
+
+    def run(rate, slots, max_batch, graph):
+        rng = np.random.default_rng(int(rate * 1000) + 7)
+        arr, t = [], 0.0
+        while True:
+            t += rng.exponential(1.0 / rate)
+            if t > args.duration:
+                break
+            arr.append((t, "mnist" if rng.random() < 0.7 else "head", int(rng.integers(0, 8))))
+        srv = serve.Server(None, None, nets, slots=slots, max_batch=max_batch, graph=graph)
+        srv.warm()
+        checked, ok = {"mnist": 0, "head": 0}, True
+        t0 = time.perf_counter()
+        i = seen = 0
+        while i < len(arr) or srv.pending():
+            now = time.perf_counter() - t0
+            while i < len(arr) and arr[i][0] <= now:
+                ta, kind, idx = arr[i]
+                rid = srv.submit(kind, pool[kind][idx], t_arrival=t0 + ta)
+                srv.requests[rid].pool_idx = idx
+                i += 1
+            srv.step()
+            fin = srv.done[seen:]
+            seen = len(srv.done)
+            for r in fin:
+                if checked[r.kind] < 2:
+                    ctx, sk = (ctx2, keys["mnist"][0]) if r.kind == "mnist" else (ctx4, keys["head"][0])
+                    dec = L.lola_decrypt(ctx, sk, r.ct_out, n)
+                    got = [int(dec[m, sl]) for m, sl in omap[r.kind]]
+                    ok = ok and got == want[r.kind][r.pool_idx]
+                    checked[r.kind] += 1
+                srv.release(r.rid)
+            time.sleep(1e-4)
+        t_end = max(r.t_done for r in srv.done)
+        st = srv.stats()
+        st["throughput"] = len(srv.done) / (t_end - t0)
+        st["offered"] = len(arr) / args.duration
+        srv.close()
+        return st, ok
+
+    rates = [float(x) for x in args.rates.split(",") if x]
+    results, correct = [], True
+    for rate in rates:
+        b, ok1 = run(rate, 2, {"mnist": 8, "head": 8}, True)
+        p, ok2 = run(rate, 1, {"mnist": 1, "head": 1}, False)
+        correct = correct and ok1 and ok2
+        results.append({"rate": rate, "batched": b, "plain": p})
+    top = results[-1]
+    line = {"mode": "serve", "metric": METRIC, "value": top["batched"]["throughput"], "unit": "inferences/s",
+            "n_gpus": 1, "higher_is_better": True, "data": "synthetic", "dtype": "u64",
+            "config": {"workload": "serving mix 70% mnist_lola_n16384 (k_t=3) + 30% transfer head (k_t=1)",
+                       "duration_s_per_rate": args.duration, "slots": 2, "max_batch": 8},
+            "rates": results, "correct": correct}
+    print(json.dumps(line), flush=True)
+    for name in keys:
+        L.lola_keys_destroy(keys[name][0])
+        L.lola_keys_destroy(keys[name][1])
+    for lst in pool.values():
+        for h in lst:
+            L.lola_ct_destroy(h)
+    L.lola_ctx_destroy(ctx2)
+    L.lola_ctx_destroy(ctx4)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.mode == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

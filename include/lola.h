@@ -125,6 +125,11 @@ size_t lola_ct_messages(const lola_ct* ct);
 /* Device pointer to the ciphertext words ([n_msg][k_t][2][L][n], NTT form);
  * valid until lola_ct_destroy. */
 uint64_t* lola_ct_data(lola_ct* ct);
+/* Copy n messages (all k_t residues) from src starting at message src_off
+ * to dst starting at dst_off, device to device on `stream` (batch assembly
+ * and result scatter for request batching).  Errors: LOLA_E_PARAM (range). */
+int lola_ct_copy_messages(lola_ctx* ctx, lola_ct* dst, size_t dst_off, const lola_ct* src, size_t src_off,
+                          size_t n, void* stream);
 /* Coefficient-form exchange, host [n_msg][k_t][2][L][n]. */
 int lola_ct_export(lola_ctx* ctx, const lola_ct* ct, uint64_t* host);
 int lola_ct_import(lola_ctx* ctx, const uint64_t* host, size_t n_msg, lola_ct** out);

@@ -196,6 +196,17 @@ int lola_ct_import(lola_ctx* ctx, const uint64_t* host, size_t n_msg, lola_ct** 
   return LOLA_OK;
 }
 
+int lola_ct_copy_messages(lola_ctx* ctx, lola_ct* dst, size_t dst_off, const lola_ct* src, size_t src_off,
+                          size_t n, void* stream) {
+  CHECK(ctx && dst && src, LOLA_E_PARAM, "null argument");
+  CHECK(dst_off + n <= dst->ct.n_msg && src_off + n <= src->ct.n_msg, LOLA_E_PARAM, "message range out of bounds");
+  if (!n) return LOLA_OK;
+  const size_t w = ctx->c->kt * ctx->c->ct_words();
+  LOLA_CUDA_TRY(cudaMemcpyAsync(dst->ct.buf.u64() + dst_off * w, src->ct.buf.u64() + src_off * w, n * w * 8,
+                                cudaMemcpyDeviceToDevice, to_stream(stream)));
+  return LOLA_OK;
+}
+
 int lola_ct_upload(lola_ctx* ctx, lola_ct* ct, const uint64_t* host, void* stream) {
   CHECK(ctx && ct && host, LOLA_E_PARAM, "null argument");
   LOLA_CUDA_TRY(cudaMemcpyAsync(ct->ct.buf.p, host, ct->ct.buf.bytes, cudaMemcpyHostToDevice, to_stream(stream)));

@@ -73,6 +73,7 @@ _SIGS = {
     "lola_ct_data": (P, [P]),
     "lola_ct_export": (C.c_int, [P, P, U64P]),
     "lola_ct_import": (C.c_int, [P, U64P, C.c_size_t, C.POINTER(P)]),
+    "lola_ct_copy_messages": (C.c_int, [P, P, C.c_size_t, P, C.c_size_t, C.c_size_t, P]),
     "lola_ct_upload": (C.c_int, [P, P, P, P]),
     "lola_ct_download": (C.c_int, [P, P, P, P]),
     "lola_ct_destroy": (None, [P]),
@@ -244,6 +245,10 @@ def lola_ct_import(ctx, host):
     out = P()
     _check(load().lola_ct_import(ctx, ap, a.shape[0], C.byref(out)))
     return out
+
+
+def lola_ct_copy_messages(ctx, dst, dst_off, src, src_off, n, stream=None):
+    _check(load().lola_ct_copy_messages(ctx, dst, dst_off, src, src_off, n, stream_handle(stream)))
 
 
 def lola_ct_upload(ctx, ct, host_ptr: int, stream=None):
