@@ -202,7 +202,8 @@ typedef enum {
   LOLA_LAYER_STACK = 4,                /* dense -> stacked: copies every 2^d slots */
   LOLA_LAYER_STACKED_ROWMAJOR = 5,     /* stacked -> interleaved (mask + combine rounds) */
   LOLA_LAYER_INTERLEAVED_ROWMAJOR = 6, /* interleaved/dense -> sparse (one message per row) */
-  LOLA_LAYER_DENSE_ROWMAJOR = 7        /* dense -> sparse */
+  LOLA_LAYER_DENSE_ROWMAJOR = 7,       /* dense -> sparse */
+  LOLA_LAYER_SPARSE_COLMAJOR = 8       /* sparse (one message per element) -> dense: sum_i v_i * column_i */
 } lola_layer_op;
 
 typedef struct {

@@ -20,6 +20,7 @@ Layer list entries (dicts):
                                                         Sec. 4.2.2 stacked vector - row major
   {"op": "interleaved_rowmajor", "weights": W}          Sec. 4.2.2 interleaved vector - row major
   {"op": "dense_rowmajor", "weights": W}                Sec. 4.2.2 dense vector - row major
+  {"op": "sparse_colmajor", "weights": W}               Sec. 4.2.2 sparse vector - column major
 """
 from __future__ import annotations
 
@@ -235,6 +236,24 @@ def layer_interleaved_rowmajor(ev, st: State, W) -> State:
     return State(outs, [(o, 0) for o in range(len(W))])
 
 
+def layer_sparse_colmajor(ev, st: State, W) -> State:
+    """Sparse vector - column major (Sec. 4.2.2): W v = sum_i v_i c^i.
+    Message i holds v_i in every slot (sparse representation); multiply it
+    by column i of W laid out densely and add the products in order i = 0,
+    1, ...; the result is dense (output o at slot o)."""
+    n = ev.n
+    k, rows = len(st.msgs), len(W)
+    assert len(W[0]) == k and rows <= n
+    acc = None
+    for i in range(k):
+        col = [0] * n
+        for o in range(rows):
+            col[o] = int(W[o][i])
+        y = ev.mul_plain(st.msgs[i], col)
+        acc = y if acc is None else ev.add(acc, y)
+    return State([acc], [(0, o) for o in range(rows)])
+
+
 def run_network(ev, layers, st: State) -> State:
     for L in layers:
         op = L["op"]
@@ -250,6 +269,8 @@ def run_network(ev, layers, st: State) -> State:
             st = layer_stacked_rowmajor(ev, st, L["weights"], L["d"], L["copies"])
         elif op in ("interleaved_rowmajor", "dense_rowmajor"):
             st = layer_interleaved_rowmajor(ev, st, L["weights"])
+        elif op == "sparse_colmajor":
+            st = layer_sparse_colmajor(ev, st, L["weights"])
         else:
             raise ValueError(op)
     return st

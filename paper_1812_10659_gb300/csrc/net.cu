@@ -283,6 +283,44 @@ static int layer_rowmajor_sparse(Builder& b, const lola_layer& L, Repr& r, bool 
   return LOLA_OK;
 }
 
+// Sparse vector - column major (Sec. 4.2.2): W v = sum_i v_i c^i.  Message i
+// holds v_i in every slot; multiply it by column i of W laid out densely
+// (slot o = W[o][i]) and add the products.  No rotations; dense result.
+static int layer_sparse_colmajor(Builder& b, const lola_layer& L, Repr& r) {
+  const uint32_t n = b.c->n;
+  if (r.kind != LOLA_REPR_SPARSE) return fail(LOLA_E_REPR, "column-major product needs a sparse vector");
+  if (!L.weights || L.cols != r.msgs || L.rows == 0 || L.rows > n)
+    return fail(LOLA_E_PARAM, "weights must be rows x (number of sparse messages), rows <= n");
+  const uint32_t k = L.cols, rows = L.rows;
+  std::vector<std::vector<int64_t>> Cc(k, std::vector<int64_t>(n, 0));
+  for (uint32_t i = 0; i < k; ++i)
+    for (uint32_t o = 0; o < rows; ++o) Cc[i][o] = L.weights[(size_t)o * k + i];
+  Op mp;
+  mp.kind = OP_MULPT;
+  mp.src = r.reg;
+  mp.src_stride = 1;
+  mp.dst = b.vreg(k);
+  mp.msgs = k;
+  mp.pt_first = b.add_plaintexts(Cc);
+  b.net->ops.push_back(mp);
+  Repr out;
+  out.kind = LOLA_REPR_DENSE;
+  out.msgs = 1;
+  out.reg = mp.dst;
+  if (k > 1) {
+    Op so;
+    so.kind = OP_SUM;
+    so.dst = b.vreg(1);
+    so.src = mp.dst;
+    so.msgs = k;
+    b.net->ops.push_back(so);
+    out.reg = so.dst;
+  }
+  for (uint32_t o = 0; o < rows; ++o) out.pos.push_back({0, o});
+  r = out;
+  return LOLA_OK;
+}
+
 Net::~Net() {}
 
 int net_create(Ctx* c, const lola_input* in, const lola_layer* layers, size_t n_layers, Net** out) {
@@ -320,6 +358,7 @@ int net_create(Ctx* c, const lola_input* in, const lola_layer* layers, size_t n_
       case LOLA_LAYER_STACKED_ROWMAJOR: rc = layer_stacked_rowmajor(b, L, r); break;
       case LOLA_LAYER_INTERLEAVED_ROWMAJOR: rc = layer_rowmajor_sparse(b, L, r, false); break;
       case LOLA_LAYER_DENSE_ROWMAJOR: rc = layer_rowmajor_sparse(b, L, r, true); break;
+      case LOLA_LAYER_SPARSE_COLMAJOR: rc = layer_sparse_colmajor(b, L, r); break;
       default: return fail(LOLA_E_PARAM, "unknown layer op");
     }
     if (rc != LOLA_OK) return rc;

@@ -149,9 +149,13 @@ class Server:
             if not self.step():
                 time.sleep(poll_s)
 
-    def warm(self, sizes=None):
+    def warm(self, sizes=None, outputs: int = 0):
         """Build executors (scratch + CUDA graph) for every slot, network and
-        power-of-two batch size up to the cap, outside any timed region."""
+        power-of-two batch size up to the cap, and `outputs` pooled output
+        handles per network, outside any timed region."""
+        for k in self.kinds:
+            while len(self.free_outputs[k]) < outputs:
+                self.free_outputs[k].append(L.lola_ct_create(self.kctx[k], self.shape[k][1]))
         for s in self.slots:
             for k in self.kinds:
                 B = 1

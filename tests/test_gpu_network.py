@@ -189,3 +189,43 @@ def test_representation_mismatch_rejected():
         assert ei.value.code == -4
     finally:
         Lb.lola_ctx_destroy(ctx)
+
+
+def test_dense_rowmajor_sparse_colmajor_bit_exact_vs_oracle():
+    """Dense vector - row major (Sec. 4.2.2, the transfer-learning head's
+    variant) followed by sparse vector - column major, on the GPU and on the
+    oracle with the same keys and ciphertext."""
+    need_gpu()
+    Lb = lib()
+    n = 256
+    ps = W.params_small(n, L=3, K=1, t=W.T30[:1])
+    P = oracle_params(ps)
+    t = ps.t[0]
+    g = np.random.default_rng(4)
+    x = g.integers(0, 16, 40)
+    W1 = g.integers(-3, 4, (6, 40))
+    W2 = g.integers(-3, 4, (9, 6))
+    layers = [{"op": "dense_rowmajor", "weights": W1}, {"op": "sparse_colmajor", "weights": W2}]
+    ctx = make_ctx(ps)
+    try:
+        net = Lb.lola_net_create(ctx, {"repr": "dense", "n_msgs": 1, "n_elems": 40}, layers)
+        sk, ev = gpu_keys(Lb, ctx, net, 21)
+        v = np.zeros((1, n), np.int64)
+        v[0, :40] = x
+        ct = Lb.lola_encrypt(ctx, sk, v, 4)
+        out = Lb.lola_ct_create(ctx, 1)
+        Lb.lola_eval_network(ctx, ev, net, ct, out)
+        got = Lb.lola_ct_export(ctx, out, (1, 2, P.L, n))[0, 0]
+        ok = oracle_keys(P, net, 21)
+        oct_ = bfv.encrypt(P, ok.pk, encoding.encode(v[0], t), t, 4, 0)
+        st = OL.run_network(OL.HEEval(P, ok, t), layers, OL.State([oct_], [(0, i) for i in range(40)]))
+        assert np.array_equal(got[0], st.msgs[0].c[0]) and np.array_equal(got[1], st.msgs[0].c[1])
+        dec = Lb.lola_decrypt(ctx, sk, out, n)
+        assert [int(dec[m, s]) for m, s in net.output_map()] == OL.int_dense(OL.int_dense(x, W1), W2)
+        for h in (ct, out):
+            Lb.lola_ct_destroy(h)
+        Lb.lola_keys_destroy(sk)
+        Lb.lola_keys_destroy(ev)
+        net.destroy()
+    finally:
+        Lb.lola_ctx_destroy(ctx)

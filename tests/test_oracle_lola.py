@@ -224,3 +224,22 @@ def test_mini_mnist_encrypted_oracle_run():
     # one ~30-bit modulus: the outputs wrap, so compare mod t
     assert got == [v % t for v in mnist_int(net, img)]
     assert ev.counts["rot"] == 1 + 3 + 2 * 7 + 1 + 3 * 10
+
+
+def test_dense_rowmajor_then_sparse_colmajor_chain():
+    # M1 (dense -> sparse) then M2 (sparse -> dense), checked against the
+    # integer product W2 (W1 x) on the slot simulator
+    n, t = 256, W.T30[0]
+    g = np.random.default_rng(4)
+    x = g.integers(0, 16, 40)
+    W1 = g.integers(-3, 4, (6, 40))
+    W2 = g.integers(-3, 4, (9, 6))
+    layers = [{"op": "dense_rowmajor", "weights": W1}, {"op": "sparse_colmajor", "weights": W2}]
+    ev = Counting(n, t)
+    v, pos = lola.pack_dense(x, n)
+    st = lola.run_network(ev, layers, lola.State([np.array(v, np.int64)], pos))
+    want = lola.int_dense(lola.int_dense(x, W1), W2)
+    got = [int(st.msgs[m][s]) for m, s in st.pos]
+    assert [v2 - t if v2 > t // 2 else v2 for v2 in got] == want
+    # M1: log2(n) rotations per output (7 within a row of 128, then the row swap); M2: none
+    assert ev.c["rot"] == 6 * 8 and ev.c["mul_plain"] == 6 + 6
