@@ -68,12 +68,13 @@ __device__ __forceinline__ void fwd_stages(uint64_t (&x)[1 << LOGE], const uint6
   for (int bp = top; bp >= lb; --bp) {
     const int s = LOGN - 1 - bp;
     const int lbit = bp - lb;
+    // twiddle index (1 << s) + (j >> (bp + 1)) splits into a per-stage,
+    // per-thread base and the compile-time k >> (lbit + 1)
+    const ulonglong2* twb = reinterpret_cast<const ulonglong2*>(tw) + (1 << s) + ((tid >> lb) << (hb - bp));
 #pragma unroll
     for (int k = 0; k < G::E; ++k) {
       if (k & (1 << lbit)) continue;
-      const int j = win_index(tid, k, hb, lb);
-      const int ti = (1 << s) + (j >> (bp + 1));
-      const ulonglong2 wq = tw_pair(tw, ti);
+      const ulonglong2 wq = __ldg(twb + (k >> (lbit + 1)));
       const uint64_t w = wq.x, wp = wq.y;
       uint64_t a = x[k];
       a = a >= q2 ? a - q2 : a;
@@ -143,12 +144,11 @@ __device__ __forceinline__ void inv_stages(uint64_t (&x)[1 << LOGE], const uint6
   for (int bp = first; bp <= hb; ++bp) {
     const int s = LOGN - 1 - bp;
     const int lbit = bp - lb;
+    const ulonglong2* twb = reinterpret_cast<const ulonglong2*>(tw) + (1 << s) + ((tid >> lb) << (hb - bp));
 #pragma unroll
     for (int k = 0; k < G::E; ++k) {
       if (k & (1 << lbit)) continue;
-      const int j = win_index(tid, k, hb, lb);
-      const int ti = (1 << s) + (j >> (bp + 1));
-      const ulonglong2 wq = tw_pair(tw, ti);
+      const ulonglong2 wq = __ldg(twb + (k >> (lbit + 1)));
       const uint64_t w = wq.x, wp = wq.y;
       const uint64_t a = x[k], b = x[k | (1 << lbit)];
       uint64_t u = a + b;
