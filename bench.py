@@ -217,6 +217,29 @@ KERNEL_BYTES = {
 }
 
 
+TRANSFORM_KERNELS = {"ks_modup", "ks_decompose", "ks_moddown", "ks_intt_p", "ntt_fwd", "ntt_inv"}
+OPS_PER_BUTTERFLY = 22
+
+
+def committed_traffic(kernel: str, units_per_launch: float):
+    """DRAM bytes (read + write) per launch from the committed ncu capture of
+    this kernel (profiles/ncu_traffic.json), scaled to this launch size; None
+    when there is no capture or the kernel sources changed since it was taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path)).get(kernel)
+    if not rec:
+        return None
+    h = hashlib.sha256()
+    for f in rec.get("sources", []):
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    if h.hexdigest() != rec.get("sources_sha256"):
+        return None
+    return rec["dram_bytes_per_unit"] * units_per_launch
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -346,11 +369,28 @@ def run_ours(args):
     peak_src = "measured" if hbm_peak else "fallback"
     hbm_peak = hbm_peak or 6800.0
     fn = KERNEL_BYTES.get(dom)
-    achieved = (d["units"] * fn(n, Lq)) / (d["ms"] / 1000.0) / 1e9 if fn else None
-    roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "peak_source": peak_src,
-                "unit": "GB/s", "frac": (achieved / hbm_peak) if achieved else None, "traffic": None,
-                "avg_launch_ms": d["ms"] / d["launches"], "share_of_kernel_time": d["ms"] / kernel_ms_total}
-    ntt_like = {k: v for k, v in per_kernel.items() if k in ("ks_modup", "ks_decompose", "ntt_fwd", "ntt_inv")}
+    hbm_achieved = (d["units"] * fn(n, Lq)) / (d["ms"] / 1000.0) / 1e9 if fn else None
+    traffic = committed_traffic(dom, d["units"] / d["launches"])
+    roofline = {"kernel": dom, "avg_launch_ms": d["ms"] / d["launches"], "share_of_kernel_time": d["ms"] / kernel_ms_total,
+                "hbm": {"achieved": hbm_achieved, "peak": hbm_peak, "peak_source": peak_src, "unit": "GB/s",
+                        "frac": (hbm_achieved / hbm_peak) if hbm_achieved else None}}
+    if dom in TRANSFORM_KERNELS:
+        # integer-ALU bound: algorithmic modular butterflies per second against
+        # the issue-rate peak (SMs x 4 schedulers x 32 lanes x max clock)
+        # divided by the 32-bit operations of one 64-bit Shoup butterfly
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        clk = peaks.get("sm_max_mhz", 2070.0) * 1e6
+        peak_bf = sms * 128 * clk / OPS_PER_BUTTERFLY / 1e9
+        bf_per_unit = (n // 2) * (n.bit_length() - 1)
+        achieved = d["units"] * bf_per_unit / (d["ms"] / 1000.0) / 1e9
+        roofline.update({"bound": "alu", "achieved": achieved, "peak": peak_bf, "unit": "Gbutterfly/s",
+                         "frac": achieved / peak_bf,
+                         "peak_source": f"derived: {sms} SMs x 128 lanes x {clk / 1e9:.2f} GHz / {OPS_PER_BUTTERFLY} "
+                                        "32-bit ops per 64-bit Shoup butterfly"})
+    else:
+        roofline.update({"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": (hbm_achieved / hbm_peak) if hbm_achieved else None, "peak_source": peak_src})
+    roofline["traffic"] = traffic
     ntt_gbs = None
     if "ks_modup" in per_kernel:
         v = per_kernel["ks_modup"]

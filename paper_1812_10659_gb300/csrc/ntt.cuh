@@ -8,9 +8,12 @@
 // twiddles (tw[2^s + i] = psi^brev(2^s + i)), natural-order input, output
 // position k holds a(psi^(2 brev(k) + 1)).  Inverse: the Gentleman-Sande
 // mirror image with psi^-1, scaled at the end by a caller-given constant
-// (n^-1, possibly times an extra factor).  Harvey's lazy reduction keeps
-// values in [0, 4q) (forward) / [0, 2q) (inverse) between stages; what the
-// loader supplies and what the storer receives is canonical [0, q).
+// (n^-1, possibly times an extra factor).  Lazy reduction (Harvey) between
+// stages: forward values stay below 4q + 2^32 (the "a" operand of each
+// butterfly is brought below 2q + 2^32 by comparing only its high 32 bits
+// with those of 2q), inverse values below 2q; q < 2^61 keeps every
+// intermediate below 2^64.  What the loader supplies and what the storer
+// receives is canonical [0, q).
 //
 // Layout: the CTA holds the whole limb (n words) in shared memory.  Each
 // thread owns E = 2^LOGE words per pass and runs up to LOGE radix-2 stages
@@ -53,17 +56,18 @@ struct NttGeom {
 };
 
 // Twiddle tables hold (w, floor(w 2^64 / q)) pairs so one 16-byte load
-// fetches both; `tw` points at the pair array of one prime, `tws` is unused.
+// fetches both; `tw` points at the pair array of one prime.
 __device__ __forceinline__ ulonglong2 tw_pair(const uint64_t* __restrict__ tw, int ti) {
   return __ldg(reinterpret_cast<const ulonglong2*>(tw) + ti);
 }
 
 template <int LOGN, int LOGE, int P>
-__device__ __forceinline__ void fwd_stages(uint64_t (&x)[1 << LOGE], const uint64_t* __restrict__ tw,
-                                           const uint64_t* __restrict__ tws, uint64_t q, int tid) {
+__device__ __forceinline__ void fwd_stages(uint64_t (&x)[1 << LOGE], const uint64_t* __restrict__ tw, uint64_t q,
+                                           int tid) {
   using G = NttGeom<LOGN, LOGE>;
   constexpr int hb = G::fhb(P), lb = G::flb(P), top = G::fdone(P) - 1;
   const uint64_t q2 = 2 * q;
+  const uint32_t q2hi = (uint32_t)(q2 >> 32);
 #pragma unroll
   for (int bp = top; bp >= lb; --bp) {
     const int s = LOGN - 1 - bp;
@@ -77,7 +81,7 @@ __device__ __forceinline__ void fwd_stages(uint64_t (&x)[1 << LOGE], const uint6
       const ulonglong2 wq = __ldg(twb + (k >> (lbit + 1)));
       const uint64_t w = wq.x, wp = wq.y;
       uint64_t a = x[k];
-      a = a >= q2 ? a - q2 : a;
+      if ((uint32_t)(a >> 32) > q2hi) a -= q2;
       const uint64_t t = shoup_mul_lazy(x[k | (1 << lbit)], w, wp, q);
       x[k] = a + t;
       x[k | (1 << lbit)] = a - t + q2;
@@ -87,8 +91,7 @@ __device__ __forceinline__ void fwd_stages(uint64_t (&x)[1 << LOGE], const uint6
 
 template <int LOGN, int LOGE, int P, class Loader, class Storer>
 __device__ __forceinline__ void fwd_pass(uint64_t* sm, uint64_t (&x)[1 << LOGE], const uint64_t* __restrict__ tw,
-                                         const uint64_t* __restrict__ tws, uint64_t q, const Loader& ld,
-                                         const Storer& st, int tid) {
+                                         uint64_t q, uint64_t qf, const Loader& ld, const Storer& st, int tid) {
   using G = NttGeom<LOGN, LOGE>;
   constexpr int hb = G::fhb(P), lb = G::flb(P);
   if constexpr (P == 0) {
@@ -99,21 +102,15 @@ __device__ __forceinline__ void fwd_pass(uint64_t* sm, uint64_t (&x)[1 << LOGE],
 #pragma unroll
     for (int k = 0; k < G::E; ++k) x[k] = sm[swz<LOGE>(win_index(tid, k, hb, lb))];
   }
-  fwd_stages<LOGN, LOGE, P>(x, tw, tws, q, tid);
+  fwd_stages<LOGN, LOGE, P>(x, tw, q, tid);
   __syncthreads();
   if constexpr (P + 1 < G::NPASS) {
 #pragma unroll
     for (int k = 0; k < G::E; ++k) sm[swz<LOGE>(win_index(tid, k, hb, lb))] = x[k];
-    fwd_pass<LOGN, LOGE, P + 1>(sm, x, tw, tws, q, ld, st, tid);
+    fwd_pass<LOGN, LOGE, P + 1>(sm, x, tw, q, qf, ld, st, tid);
   } else {
-    const uint64_t q2 = 2 * q;
 #pragma unroll
-    for (int k = 0; k < G::E; ++k) {
-      uint64_t v = x[k];
-      v = v >= q2 ? v - q2 : v;
-      v = v >= q ? v - q : v;
-      sm[swz<LOGE>(win_index(tid, k, hb, lb))] = v;
-    }
+    for (int k = 0; k < G::E; ++k) sm[swz<LOGE>(win_index(tid, k, hb, lb))] = reduce64(x[k], q, qf);
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < G::E; ++k) {
@@ -125,18 +122,18 @@ __device__ __forceinline__ void fwd_pass(uint64_t* sm, uint64_t (&x)[1 << LOGE],
 
 // Forward transform.  ld(i) returns input coefficient i (canonical);
 // st(i, v) receives output position i (canonical), called once per i.
+// tw: the prime's (w, w') twiddle pairs; qf = floor(2^64 / q).
 // Every thread of the CTA must call this (it synchronises).
 template <int LOGN, int LOGE, class Loader, class Storer>
-__device__ __forceinline__ void ntt_forward(uint64_t* sm, const uint64_t* __restrict__ tw,
-                                            const uint64_t* __restrict__ tws, uint64_t q,
+__device__ __forceinline__ void ntt_forward(uint64_t* sm, const uint64_t* __restrict__ tw, uint64_t q, uint64_t qf,
                                             const Loader& ld, const Storer& st) {
   uint64_t x[1 << LOGE];
-  fwd_pass<LOGN, LOGE, 0>(sm, x, tw, tws, q, ld, st, (int)threadIdx.x);
+  fwd_pass<LOGN, LOGE, 0>(sm, x, tw, q, qf, ld, st, (int)threadIdx.x);
 }
 
 template <int LOGN, int LOGE, int P>
-__device__ __forceinline__ void inv_stages(uint64_t (&x)[1 << LOGE], const uint64_t* __restrict__ tw,
-                                           const uint64_t* __restrict__ tws, uint64_t q, int tid) {
+__device__ __forceinline__ void inv_stages(uint64_t (&x)[1 << LOGE], const uint64_t* __restrict__ tw, uint64_t q,
+                                           int tid) {
   using G = NttGeom<LOGN, LOGE>;
   constexpr int lb = G::ilb(P), hb = lb + LOGE - 1, first = G::idone(P);
   const uint64_t q2 = 2 * q;
@@ -161,19 +158,18 @@ __device__ __forceinline__ void inv_stages(uint64_t (&x)[1 << LOGE], const uint6
 
 template <int LOGN, int LOGE, int P, class Storer>
 __device__ __forceinline__ void inv_pass(uint64_t* sm, uint64_t (&x)[1 << LOGE], const uint64_t* __restrict__ tw,
-                                         const uint64_t* __restrict__ tws, uint64_t q, uint64_t c, uint64_t cs,
-                                         const Storer& st, int tid) {
+                                         uint64_t q, uint64_t c, uint64_t cs, const Storer& st, int tid) {
   using G = NttGeom<LOGN, LOGE>;
   constexpr int lb = G::ilb(P), hb = lb + LOGE - 1;
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < G::E; ++k) x[k] = sm[swz<LOGE>(win_index(tid, k, hb, lb))];
-  inv_stages<LOGN, LOGE, P>(x, tw, tws, q, tid);
+  inv_stages<LOGN, LOGE, P>(x, tw, q, tid);
   if constexpr (P + 1 < G::NPASS) {
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < G::E; ++k) sm[swz<LOGE>(win_index(tid, k, hb, lb))] = x[k];
-    inv_pass<LOGN, LOGE, P + 1>(sm, x, tw, tws, q, c, cs, st, tid);
+    inv_pass<LOGN, LOGE, P + 1>(sm, x, tw, q, c, cs, st, tid);
   } else {
 #pragma unroll
     for (int k = 0; k < G::E; ++k) st(win_index(tid, k, hb, lb), shoup_mul(x[k], c, cs, q));
@@ -183,8 +179,7 @@ __device__ __forceinline__ void inv_pass(uint64_t* sm, uint64_t (&x)[1 << LOGE],
 // Inverse transform, output scaled by c (n^-1, possibly times an extra
 // factor), cs = floor(c 2^64 / q).  ld(i) is read once per i.
 template <int LOGN, int LOGE, class Loader, class Storer>
-__device__ __forceinline__ void ntt_inverse(uint64_t* sm, const uint64_t* __restrict__ tw,
-                                            const uint64_t* __restrict__ tws, uint64_t q, uint64_t c,
+__device__ __forceinline__ void ntt_inverse(uint64_t* sm, const uint64_t* __restrict__ tw, uint64_t q, uint64_t c,
                                             uint64_t cs, const Loader& ld, const Storer& st) {
   using G = NttGeom<LOGN, LOGE>;
   const int tid = threadIdx.x;
@@ -194,18 +189,17 @@ __device__ __forceinline__ void ntt_inverse(uint64_t* sm, const uint64_t* __rest
     sm[swz<LOGE>(i)] = ld(i);
   }
   uint64_t x[1 << LOGE];
-  inv_pass<LOGN, LOGE, 0>(sm, x, tw, tws, q, c, cs, st, tid);
+  inv_pass<LOGN, LOGE, 0>(sm, x, tw, q, c, cs, st, tid);
 }
 
 // Inverse transform of data the caller has already placed in shared memory
 // (element i at sm[swz<LOGE>(i)], canonical).  The first pass synchronises
 // before reading.
 template <int LOGN, int LOGE, class Storer>
-__device__ __forceinline__ void ntt_inverse_smem(uint64_t* sm, const uint64_t* __restrict__ tw,
-                                                 const uint64_t* __restrict__ tws, uint64_t q, uint64_t c,
-                                                 uint64_t cs, const Storer& st) {
+__device__ __forceinline__ void ntt_inverse_smem(uint64_t* sm, const uint64_t* __restrict__ tw, uint64_t q,
+                                                 uint64_t c, uint64_t cs, const Storer& st) {
   uint64_t x[1 << LOGE];
-  inv_pass<LOGN, LOGE, 0>(sm, x, tw, tws, q, c, cs, st, (int)threadIdx.x);
+  inv_pass<LOGN, LOGE, 0>(sm, x, tw, q, c, cs, st, (int)threadIdx.x);
 }
 
 }  // namespace lola

@@ -9,21 +9,31 @@
 
 namespace lola {
 
-// words per thread per pass at n = 16384 (2^5: 512 threads; 2^4: 1024 threads)
+// Words per thread per pass.  At n = 16384 a CTA holds the whole limb in
+// 128 KiB of shared memory, so one CTA runs per SM: 2^4 words (1024 threads,
+// at most 64 registers) hides more latency, 2^5 words (512 threads, up to 128
+// registers) avoids register spills in the forward transforms that read their
+// input straight from global memory.  Measured per kernel: the mod-up
+// transform is faster with 512 threads, the others with 1024.
 #ifndef LOLA_NTT14_LOGE
 #define LOLA_NTT14_LOGE 4
 #endif
+#ifndef LOLA_NTT14_LOGE_MODUP
+#define LOLA_NTT14_LOGE_MODUP 5
+#endif
 
-template <int LOGN>
+template <int LOGN, int LOGE14 = LOLA_NTT14_LOGE>
 struct Cfg {
-  static constexpr int LOGE = LOGN >= 14 ? LOLA_NTT14_LOGE : 4;
+  static constexpr int LOGE = LOGN >= 14 ? LOGE14 : 4;
   static constexpr int N = 1 << LOGN;
   static constexpr int T = N >> LOGE;
 };
+template <int LOGN>
+using CfgM = Cfg<LOGN, LOLA_NTT14_LOGE_MODUP>;
 
 // (w, w') pair tables, 2n words per prime
-#define TW_F(C, p) (C)->tw_fwd + (size_t)(p) * (2u << LOGN), nullptr
-#define TW_I(C, p) (C)->tw_inv + (size_t)(p) * (2u << LOGN), nullptr
+#define TW_F(C, p) (C)->tw_fwd + (size_t)(p) * (2u << LOGN)
+#define TW_I(C, p) (C)->tw_inv + (size_t)(p) * (2u << LOGN)
 
 // ------------------------------------------------------------ plain transforms
 template <int LOGN>
@@ -35,7 +45,7 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T) kn_fwd(const CtxDev* __restrict_
   const int p = pm.p[poly % limbs];
   const uint64_t* src = in + poly * N;
   uint64_t* dst = out + poly * N;
-  ntt_forward<LOGN, Cfg<LOGN>::LOGE>(sm, TW_F(C, p), C->pr[p].q, [&](int i) { return src[i]; },
+  ntt_forward<LOGN, Cfg<LOGN>::LOGE>(sm, TW_F(C, p), C->pr[p].q, C->pr[p].f64, [&](int i) { return src[i]; },
                                       [&](int i, uint64_t v) { dst[i] = v; });
 }
 
@@ -66,7 +76,7 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T) kn_fwd_signed(const CtxDev* __re
   const PrimeDev& P = C->pr[p];
   const int64_t* src = in + poly * N;
   uint64_t* dst = out + blk * N;
-  ntt_forward<LOGN, Cfg<LOGN>::LOGE>(sm, TW_F(C, p), P.q,
+  ntt_forward<LOGN, Cfg<LOGN>::LOGE>(sm, TW_F(C, p), P.q, P.f64,
                                       [&](int i) { return from_signed(src[i], P.q, P.f64); },
                                       [&](int i, uint64_t v) { dst[i] = v; });
 }
@@ -86,7 +96,7 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T) kn_encode_lift(const CtxDev* __r
   const uint64_t* src = in + poly * N;
   uint64_t* dst = out + blk * N;
   ntt_forward<LOGN, Cfg<LOGN>::LOGE>(
-      sm, TW_F(C, l), P.q,
+      sm, TW_F(C, l), P.q, P.f64,
       [&](int i) {
         const uint64_t x = src[i];
         return x <= (t - 1) / 2 ? reduce64(x, P.q, P.f64) : neg_mod(reduce64(t - x, P.q, P.f64), P.q);
@@ -121,7 +131,7 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T) kn_coeff_to_slots(const CtxDev* 
   const int p = C->iT + tidx[poly];
   const uint64_t* src = coeff + poly * N;
   uint64_t* dst = slots + poly * N;
-  ntt_forward<LOGN, Cfg<LOGN>::LOGE>(sm, TW_F(C, p), C->pr[p].q, [&](int i) { return src[i]; },
+  ntt_forward<LOGN, Cfg<LOGN>::LOGE>(sm, TW_F(C, p), C->pr[p].q, C->pr[p].f64, [&](int i) { return src[i]; },
                                       [&](int i, uint64_t v) { dst[slot_at_pos[i]] = v; });
 }
 
@@ -142,7 +152,7 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T) kn_enc_msg(const CtxDev* __restr
   const int64_t* es = e1 + poly * N;
   uint64_t* dst = out + blk * N;
   ntt_forward<LOGN, Cfg<LOGN>::LOGE>(
-      sm, TW_F(C, j), P.q,
+      sm, TW_F(C, j), P.q, P.f64,
       [&](int i) { return add_mod(shoup_mul(ms[i], d, ds, P.q), from_signed(es[i], P.q, P.f64), P.q); },
       [&](int i, uint64_t v) { dst[i] = v; });
 }
@@ -199,9 +209,9 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T) kn_ks_decompose(const CtxDev* __
 
 // B: digit i reduced mod prime j, forward transform -> D[i][j]
 template <int LOGN>
-__global__ void __launch_bounds__(Cfg<LOGN>::T) kn_ks_modup(const CtxDev* __restrict__ C, KsDev a, int skip_diag) {
+__global__ void __launch_bounds__(CfgM<LOGN>::T) kn_ks_modup(const CtxDev* __restrict__ C, KsDev a, int skip_diag) {
   extern __shared__ uint64_t sm[];
-  constexpr int N = Cfg<LOGN>::N;
+  constexpr int N = CfgM<LOGN>::N;
   const int L = C->L, LK = C->L + C->K;
   const int per = skip_diag ? L * (LK - 1) : L * LK;
   const size_t ct = blockIdx.x / per;
@@ -212,7 +222,7 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T) kn_ks_modup(const CtxDev* __rest
   const uint64_t* dig = a.dig + (ct * L + i) * (size_t)N;
   uint64_t* dst = a.D + ((ct * L + i) * LK + j) * (size_t)N;
   const PrimeDev& P = C->pr[j];
-  ntt_forward<LOGN, Cfg<LOGN>::LOGE>(sm, TW_F(C, j), P.q, [&](int k) { return reduce64(dig[k], P.q, P.f64); },
+  ntt_forward<LOGN, CfgM<LOGN>::LOGE>(sm, TW_F(C, j), P.q, P.f64, [&](int k) { return reduce64(dig[k], P.q, P.f64); },
                                       [&](int k, uint64_t v) { dst[k] = v; });
 }
 
@@ -250,7 +260,7 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T) kn_ks_moddown(const CtxDev* __re
   const uint64_t* x = a.xP + (ct * 2 + comp) * (size_t)N;
   uint64_t* dst = a.out + ((ct * 2 + comp) * L + j) * (size_t)N;
   ntt_forward<LOGN, Cfg<LOGN>::LOGE>(
-      sm, TW_F(C, j), P.q,
+      sm, TW_F(C, j), P.q, P.f64,
       [&](int k) {
         const uint64_t v = x[k];
         const uint64_t r0 = reduce64(v, P.q, P.f64);
@@ -260,25 +270,26 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T) kn_ks_moddown(const CtxDev* __re
 }
 
 // ------------------------------------------------------------------ dispatch
-#define LOLA_DISPATCH(logn, KERNEL, grid, stream, ...)                                             \
+#define LOLA_DISPATCH(logn, KERNEL, grid, stream, ...) LOLA_DISPATCH_CFG(Cfg, logn, KERNEL, grid, stream, __VA_ARGS__)
+#define LOLA_DISPATCH_CFG(CFG, logn, KERNEL, grid, stream, ...)                                     \
   do {                                                                                             \
     switch (logn) {                                                                                \
-      case 4: LOLA_LAUNCH(4, KERNEL, grid, stream, __VA_ARGS__); break;                            \
-      case 5: LOLA_LAUNCH(5, KERNEL, grid, stream, __VA_ARGS__); break;                            \
-      case 6: LOLA_LAUNCH(6, KERNEL, grid, stream, __VA_ARGS__); break;                            \
-      case 7: LOLA_LAUNCH(7, KERNEL, grid, stream, __VA_ARGS__); break;                            \
-      case 8: LOLA_LAUNCH(8, KERNEL, grid, stream, __VA_ARGS__); break;                            \
-      case 9: LOLA_LAUNCH(9, KERNEL, grid, stream, __VA_ARGS__); break;                            \
-      case 10: LOLA_LAUNCH(10, KERNEL, grid, stream, __VA_ARGS__); break;                          \
-      case 11: LOLA_LAUNCH(11, KERNEL, grid, stream, __VA_ARGS__); break;                          \
-      case 12: LOLA_LAUNCH(12, KERNEL, grid, stream, __VA_ARGS__); break;                          \
-      case 13: LOLA_LAUNCH(13, KERNEL, grid, stream, __VA_ARGS__); break;                          \
-      case 14: LOLA_LAUNCH(14, KERNEL, grid, stream, __VA_ARGS__); break;                          \
+      case 4: LOLA_LAUNCH(CFG, 4, KERNEL, grid, stream, __VA_ARGS__); break;                       \
+      case 5: LOLA_LAUNCH(CFG, 5, KERNEL, grid, stream, __VA_ARGS__); break;                            \
+      case 6: LOLA_LAUNCH(CFG, 6, KERNEL, grid, stream, __VA_ARGS__); break;                            \
+      case 7: LOLA_LAUNCH(CFG, 7, KERNEL, grid, stream, __VA_ARGS__); break;                            \
+      case 8: LOLA_LAUNCH(CFG, 8, KERNEL, grid, stream, __VA_ARGS__); break;                            \
+      case 9: LOLA_LAUNCH(CFG, 9, KERNEL, grid, stream, __VA_ARGS__); break;                            \
+      case 10: LOLA_LAUNCH(CFG, 10, KERNEL, grid, stream, __VA_ARGS__); break;                          \
+      case 11: LOLA_LAUNCH(CFG, 11, KERNEL, grid, stream, __VA_ARGS__); break;                          \
+      case 12: LOLA_LAUNCH(CFG, 12, KERNEL, grid, stream, __VA_ARGS__); break;                          \
+      case 13: LOLA_LAUNCH(CFG, 13, KERNEL, grid, stream, __VA_ARGS__); break;                          \
+      case 14: LOLA_LAUNCH(CFG, 14, KERNEL, grid, stream, __VA_ARGS__); break;                          \
       default: return fail(LOLA_E_PARAM, "unsupported ring degree");                                \
     }                                                                                              \
   } while (0)
 
-#define LOLA_LAUNCH(LG, KERNEL, grid, stream, ...)                                                 \
+#define LOLA_LAUNCH(CFG, LG, KERNEL, grid, stream, ...)                                            \
   do {                                                                                             \
     const size_t smem = sizeof(uint64_t) << (LG);                                                  \
     static bool attr_done = false;                                                                 \
@@ -286,7 +297,7 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T) kn_ks_moddown(const CtxDev* __re
       cudaFuncSetAttribute(KERNEL<LG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);    \
       attr_done = true;                                                                            \
     }                                                                                              \
-    KERNEL<LG><<<(unsigned)(grid), Cfg<LG>::T, smem, stream>>>(__VA_ARGS__);                       \
+    KERNEL<LG><<<(unsigned)(grid), CFG<LG>::T, smem, stream>>>(__VA_ARGS__);                       \
   } while (0)
 
 static int post_launch(Ctx* c, cudaStream_t) {
@@ -381,7 +392,7 @@ int ks_modup(Ctx* c, const KsDev& a, bool skip_diag, cudaStream_t s) {
   const size_t per = skip_diag ? (size_t)c->L * (LK - 1) : (size_t)c->L * LK;
   if (!per) return LOLA_OK;
   ProfScope ps(c, KI_KS_MODUP, s, a.count * per);
-  LOLA_DISPATCH(c->logn, kn_ks_modup, a.count * per, s, c->dev, a, (int)skip_diag);
+  LOLA_DISPATCH_CFG(CfgM, c->logn, kn_ks_modup, a.count * per, s, c->dev, a, (int)skip_diag);
   return post_launch(c, s);
 }
 
