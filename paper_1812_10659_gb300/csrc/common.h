@@ -60,6 +60,11 @@ struct CtxDev {
   uint64_t PmodQ[MAXB], PmodQ_s[MAXB];
   uint64_t PinvQ[MAXB], PinvQ_s[MAXB];            // P^-1 mod q_i
   uint64_t PmontQ[MAXB];                          // (P mod q_i) 2^64 mod q_i (P = 1 when K = 0)
+  // switching keys are stored as k * P^-1 * 2^64 mod q_j on the L ciphertext
+  // primes (k * 2^64 on the special prime), so the inner product already
+  // carries the ModDown factor P^-1:
+  uint64_t KskR2[MAXB];                           // 2^128 P^-1 mod q_j; 2^128 mod P on P
+  uint64_t KskOut[MAXB];                          // P mod q_j; 1 on P (Montgomery factor back to k)
 };
 
 // host-side error reporting

@@ -339,6 +339,12 @@ static int build_ctx(Ctx* c, const lola_params* p) {
     H.PinvQ_s[i] = shoup_h(H.PinvQ[i], q);
     const uint64_t r1 = (uint64_t)(((u128)1 << 64) % q);
     H.PmontQ[i] = mulmod_h(P % q, r1, q);
+    H.KskR2[i] = mulmod_h(H.pr[i].r2, H.PinvQ[i], q);
+    H.KskOut[i] = H.PmodQ[i];
+  }
+  for (uint32_t i = c->L; i < c->L + c->K; ++i) {
+    H.KskR2[i] = H.pr[i].r2;
+    H.KskOut[i] = 1;
   }
   // slot map for the plaintext transform mod t: NTT position k holds the
   // value at psi^(2 brev(k) + 1); slot j sits at psi^(3^j), slot n/2 + j at psi^(-3^j)

@@ -87,9 +87,9 @@ __global__ void ke_ks_ip(const CtxDev* __restrict__ C, KsDev a, int final_out) {
       }
     } else {
       if (j < L) {
-        // fold the addends: out = (ACC + (addend + accum) P - NTT(x~)) P^-1
-        //                       = (ACC - NTT(x~)) P^-1 + addend + accum
-        const uint64_t Pm = C->PmodQ[j], Pms = C->PmodQ_s[j];
+        // the keys carry P^-1 on these primes, so ACC here is already the
+        // inner product times P^-1; fold the addends:
+        //   out = ACC P^-1 + addend + accum - NTT(x~) P^-1
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
           const size_t kk = k + e;
@@ -101,8 +101,8 @@ __global__ void ke_ks_ip(const CtxDev* __restrict__ C, KsDev a, int final_out) {
             s0v = add_mod(s0v, a.accum[((ct * 2 + 0) * L + j) * n + kk], P.q);
             s1v = add_mod(s1v, a.accum[((ct * 2 + 1) * L + j) * n + kk], P.q);
           }
-          acc0[e] = add_mod(acc0[e], shoup_mul(s0v, Pm, Pms, P.q), P.q);
-          acc1[e] = add_mod(acc1[e], shoup_mul(s1v, Pm, Pms, P.q), P.q);
+          acc0[e] = add_mod(acc0[e], s0v, P.q);
+          acc1[e] = add_mod(acc1[e], s1v, P.q);
         }
       }
       uint64_t* A0 = a.acc + ct * a.acc_stride + (size_t)j * n + k;
@@ -127,11 +127,12 @@ __global__ void ke_add(const CtxDev* __restrict__ C, const uint64_t* a, const ui
 // x -> x * 2^64 mod q per limb of [poly][limbs][n]
 // (inverse = true: x -> x * 2^-64 mod q)
 __global__ void ke_to_mont(const CtxDev* __restrict__ C, uint64_t* x, size_t total, uint32_t limbs, PrimeMap pm,
-                           int inverse) {
+                           int mode) {
   const int logn = C->logn;
   for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < total; w += (size_t)gridDim.x * blockDim.x) {
-    const PrimeDev& P = C->pr[pm.p[(w >> logn) % limbs]];
-    x[w] = mont_mul(x[w], inverse ? 1 : P.r2, P.q, P.qinv);
+    const int pi = pm.p[(w >> logn) % limbs];
+    const PrimeDev& P = C->pr[pi];
+    x[w] = mont_mul(x[w], mode == k::MONT_TO ? P.r2 : mode == k::MONT_FROM ? 1 : C->KskOut[pi], P.q, P.qinv);
   }
 }
 
@@ -158,7 +159,7 @@ __global__ void ke_neg_axpe(const CtxDev* __restrict__ C, const uint64_t* a, con
 }
 
 // switching key rows: a, e: [L][LK][n] (e broadcast per digit over primes),
-// out: [2][L][LK][n] Montgomery form of (b, a),
+// out: [2][L][LK][n] Montgomery form of (b, a) times P^-1 on the ciphertext primes,
 // b_ij = -a_ij s_j + e_ij + [i == j] (P mod q_j) s'_j
 __global__ void ke_keygen_switch(const CtxDev* __restrict__ C, const uint64_t* a, const uint64_t* e,
                                  const uint64_t* s_mont, const uint64_t* sfrom, uint64_t* out) {
@@ -173,8 +174,8 @@ __global__ void ke_keygen_switch(const CtxDev* __restrict__ C, const uint64_t* a
     uint64_t b = neg_mod(mont_mul(a[w], s_mont[(size_t)j * n + k], P.q, P.qinv), P.q);
     b = add_mod(b, e[w], P.q);
     if (i == j) b = add_mod(b, mont_mul(sfrom[(size_t)j * n + k], C->PmontQ[j], P.q, P.qinv), P.q);
-    out[w] = mont_mul(b, P.r2, P.q, P.qinv);
-    out[total + w] = mont_mul(a[w], P.r2, P.q, P.qinv);
+    out[w] = mont_mul(b, C->KskR2[j], P.q, P.qinv);
+    out[total + w] = mont_mul(a[w], C->KskR2[j], P.q, P.qinv);
   }
 }
 
@@ -477,9 +478,9 @@ int sub(Ctx* c, const uint64_t* a, const uint64_t* b, uint64_t* out, size_t coun
 }
 
 int to_mont_map(Ctx* c, uint64_t* data, size_t n_limbpolys, uint32_t limbs, const PrimeMap& pm, cudaStream_t s,
-                bool inverse) {
+                int mode) {
   const size_t total = n_limbpolys * c->n;
-  ELEM_LAUNCH(KI_MISC, ke_to_mont, total, c->dev, data, total, limbs, pm, (int)inverse);
+  ELEM_LAUNCH(KI_MISC, ke_to_mont, total, c->dev, data, total, limbs, pm, mode);
   return post(c);
 }
 

@@ -382,7 +382,7 @@ int keys_export(Ctx* c, const KeySet* ks, int what, int32_t step, uint64_t* host
   TRY(tmp.alloc(need * 8));
   LOLA_CUDA_TRY(cudaMemcpy(tmp.p, src, need * 8, cudaMemcpyDeviceToDevice));
   PrimeMap pm = prime_map(limbs);
-  TRY(k::to_mont_map(c, tmp.u64(), need / n, limbs, pm, s, true));
+  TRY(k::to_mont_map(c, tmp.u64(), need / n, limbs, pm, s, what == 1 ? k::MONT_FROM : k::MONT_FROM_KSK));
   TRY(k::ntt_inv_map(c, tmp.u64(), tmp.u64(), need / n, limbs, pm, false, s));
   LOLA_CUDA_TRY(cudaMemcpy(host, tmp.p, need * 8, cudaMemcpyDeviceToHost));
   return LOLA_OK;

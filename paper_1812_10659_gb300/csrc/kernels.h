@@ -80,8 +80,11 @@ int ks_moddown(Ctx* c, const KsDev& a, cudaStream_t s);
 int ks_ip(Ctx* c, const KsDev& a, bool final_out, cudaStream_t s);   // inner product over digits
 int add(Ctx* c, const uint64_t* a, const uint64_t* b, uint64_t* out, size_t count, cudaStream_t s);
 int sub(Ctx* c, const uint64_t* a, const uint64_t* b, uint64_t* out, size_t count, cudaStream_t s);
+// mode: MONT_TO x -> x 2^64; MONT_FROM x -> x 2^-64; MONT_FROM_KSK a stored
+// switching key back to its plain value (undoes the 2^64 P^-1 factor)
+enum { MONT_TO = 0, MONT_FROM = 1, MONT_FROM_KSK = 2 };
 int to_mont_map(Ctx* c, uint64_t* data, size_t n_limbpolys, uint32_t limbs, const PrimeMap& pm, cudaStream_t s,
-                bool inverse = false);
+                int mode = MONT_TO);
 int axpy_mont_map(Ctx* c, const uint64_t* a, const uint64_t* b, const uint64_t* w_mont, uint64_t* out,
                   size_t n_limbpolys, uint32_t limbs, const PrimeMap& pm, cudaStream_t s);
 int neg_axpe(Ctx* c, const uint64_t* a, const uint64_t* s_mont, const uint64_t* e, uint64_t* out, uint32_t limbs,

@@ -241,13 +241,16 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T) kn_ks_intt_p(const CtxDev* __res
                                       [&](int k, uint64_t v) { dst[k] = v; });
 }
 
-// E: x~ = centered(x mod P) reduced mod q_j and transformed; output limb
-//    out[comp][j] = (ACC'[comp][j] - NTT(x~)) P^-1, where the inner-product
-//    kernel already added (addend + accumulator) * P to ACC'.
+// E: output limb out[comp][j] = ACC'[comp][j] - NTT(x~ P^-1 mod q_j), with
+//    x~ = centered(x mod P); the inner-product kernel left ACC' = ACC P^-1 +
+//    addend + accumulator (the keys carry P^-1).  The loader multiplies the
+//    raw residue x in [0, P) by P^-1 mod q_j (Shoup, any 64-bit input) and
+//    subtracts 1 = P P^-1 where x~ = x - P; its value stays below 4q, which
+//    the forward butterflies accept.
 template <int LOGN>
-__global__ void __launch_bounds__(Cfg<LOGN>::T) kn_ks_moddown(const CtxDev* __restrict__ C, KsDev a) {
+__global__ void __launch_bounds__(CfgM<LOGN>::T) kn_ks_moddown(const CtxDev* __restrict__ C, KsDev a) {
   extern __shared__ uint64_t sm[];
-  constexpr int N = Cfg<LOGN>::N;
+  constexpr int N = CfgM<LOGN>::N;
   const int L = C->L, LK = C->L + C->K;
   const size_t ct = blockIdx.x / (2 * L);
   const int r = blockIdx.x % (2 * L);
@@ -255,19 +258,150 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T) kn_ks_moddown(const CtxDev* __re
   const uint32_t g = a.d_gal ? a.d_gal[ct / a.gal_div] : a.gal;
   const uint64_t* accp = a.acc + ct * a.acc_stride + (size_t)(comp * LK + j) * N;
   const PrimeDev& P = C->pr[j];
-  const uint64_t Pq = C->pr[C->iP].q;
-  const uint64_t PmodQ = C->PmodQ[j], Pinv = C->PinvQ[j], Pinv_s = C->PinvQ_s[j];
+  const uint64_t Phalf = (C->pr[C->iP].q - 1) / 2, q2m1 = 2 * P.q - 1;
+  const uint64_t Pinv = C->PinvQ[j], Pinv_s = C->PinvQ_s[j];
   const uint64_t* x = a.xP + (ct * 2 + comp) * (size_t)N;
   uint64_t* dst = a.out + ((ct * 2 + comp) * L + j) * (size_t)N;
-  ntt_forward<LOGN, Cfg<LOGN>::LOGE>(
+  ntt_forward<LOGN, CfgM<LOGN>::LOGE>(
       sm, TW_F(C, j), P.q, P.f64,
       [&](int k) {
         const uint64_t v = x[k];
-        const uint64_t r0 = reduce64(v, P.q, P.f64);
-        return v > (Pq - 1) / 2 ? sub_mod(r0, PmodQ, P.q) : r0;
+        return shoup_mul_lazy(v, Pinv, Pinv_s, P.q) + (v > Phalf ? q2m1 : 0);
       },
-      [&](int k, uint64_t v) { dst[k] = shoup_mul(sub_mod(accp[k], v, P.q), Pinv, Pinv_s, P.q); });
+      [&](int k, uint64_t v) { dst[k] = sub_mod(accp[k], v, P.q); });
 }
+
+// ------------------------------------------- n = 16384: 2-CTA cluster versions
+// Each limb transform is split over a cluster of two CTAs (half the limb each,
+// 64 KiB of shared memory), so a launch with few limbs still keeps twice as
+// many SMs busy and each dependent step of a rotation takes half as long.
+constexpr int CL_LOGN = 14, CL_LOGC = 1;
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 2)
+    kc_ks_modup(const CtxDev* __restrict__ C, KsDev a, int skip_diag) {
+  extern __shared__ uint64_t sm[];
+  constexpr int N = 1 << CL_LOGN;
+  const int L = C->L, LK = C->L + C->K;
+  const int per = skip_diag ? L * (LK - 1) : L * LK;
+  const size_t unit = blockIdx.x >> 1;
+  const size_t ct = unit / per;
+  const int r = unit % per;
+  const int i = r / (skip_diag ? LK - 1 : LK);
+  int j = r % (skip_diag ? LK - 1 : LK);
+  if (skip_diag && j >= i) ++j;
+  const uint64_t* dig = a.dig + (ct * L + i) * (size_t)N;
+  uint64_t* dst = a.D + ((ct * L + i) * LK + j) * (size_t)N;
+  const PrimeDev& P = C->pr[j];
+  ncl::ntt_forward_cluster<CL_LOGN, 5, CL_LOGC>(sm, C->tw_fwd + (size_t)j * (2u << CL_LOGN), P.q, P.f64,
+                                                [&](int k) { return reduce64(dig[k], P.q, P.f64); },
+                                                [&](int k, uint64_t v) { dst[k] = v; });
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 2) kc_ks_intt_p(const CtxDev* __restrict__ C, KsDev a) {
+  extern __shared__ uint64_t sm[];
+  constexpr int N = 1 << CL_LOGN;
+  const int LK = C->L + C->K, ip = C->iP;
+  const size_t unit = blockIdx.x >> 1;
+  const size_t ct = unit >> 1;
+  const int comp = unit & 1;
+  const PrimeDev& P = C->pr[ip];
+  const uint64_t* src = a.acc + ct * a.acc_stride + (size_t)(comp * LK + ip) * N;
+  uint64_t* dst = a.xP + (ct * 2 + comp) * (size_t)N;
+  ncl::ntt_inverse_cluster<CL_LOGN, 5, CL_LOGC>(sm, C->tw_inv + (size_t)ip * (2u << CL_LOGN), P.q, P.ninv, P.ninv_s,
+                                                [&](int k) { return src[k]; },
+                                                [&](int k, uint64_t v) { dst[k] = v; });
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 2) kc_ks_moddown(const CtxDev* __restrict__ C, KsDev a) {
+  extern __shared__ uint64_t sm[];
+  constexpr int N = 1 << CL_LOGN;
+  const int L = C->L, LK = C->L + C->K;
+  const size_t unit = blockIdx.x >> 1;
+  const size_t ct = unit / (2 * L);
+  const int r = unit % (2 * L);
+  const int comp = r / L, j = r % L;
+  const uint64_t* accp = a.acc + ct * a.acc_stride + (size_t)(comp * LK + j) * N;
+  const PrimeDev& P = C->pr[j];
+  const uint64_t Phalf = (C->pr[C->iP].q - 1) / 2, q2m1 = 2 * P.q - 1;
+  const uint64_t Pinv = C->PinvQ[j], Pinv_s = C->PinvQ_s[j];
+  const uint64_t* x = a.xP + (ct * 2 + comp) * (size_t)N;
+  uint64_t* dst = a.out + ((ct * 2 + comp) * L + j) * (size_t)N;
+  ncl::ntt_forward_cluster<CL_LOGN, 5, CL_LOGC>(
+      sm, C->tw_fwd + (size_t)j * (2u << CL_LOGN), P.q, P.f64,
+      [&](int k) {
+        const uint64_t v = x[k];
+        return shoup_mul_lazy(v, Pinv, Pinv_s, P.q) + (v > Phalf ? q2m1 : 0);
+      },
+      [&](int k, uint64_t v) { dst[k] = sub_mod(accp[k], v, P.q); });
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 2) kc_ks_decompose(const CtxDev* __restrict__ C, KsDev a) {
+  extern __shared__ uint64_t sm[];
+  namespace cg = cooperative_groups;
+  constexpr int N = 1 << CL_LOGN, LOGE = 5, LOGNL = CL_LOGN - CL_LOGC, NC = 1 << LOGNL;
+  constexpr int T = N >> (LOGE + CL_LOGC);
+  cg::cluster_group cl = cg::this_cluster();
+  const int h = (int)cl.block_rank();
+  const int L = C->L, LK = C->L + C->K;
+  const size_t unit = blockIdx.x >> 1;
+  const size_t ct = unit / L;
+  const int i = unit % L;
+  const uint32_t g = a.d_gal ? a.d_gal[ct / a.gal_div] : a.gal;
+  const uint32_t ginv = inv_odd32(g) & ((2u << CL_LOGN) - 1);
+  const int tid = threadIdx.x;
+  const uint64_t* src0 = a.c1 + (ct * 2 * L + i) * (size_t)N;
+  const uint64_t* src1 = a.c1 + (ct * 2 * L + L + i) * (size_t)N;
+  uint64_t* c0p = a.c0p + (ct * L + i) * (size_t)N;
+  uint64_t* diag = a.D + ((ct * L + i) * LK + i) * (size_t)N;
+  uint64_t* dig = a.dig + (ct * L + i) * (size_t)N;
+  const PrimeDev& P = C->pr[i];
+  // tau_g(c0): this CTA reads its chunk of c0 and scatters through the inverse
+  // permutation; the peers must have started before their shared memory is
+  // written, a barrier overlapped with the loads
+  cl.barrier_arrive();
+  uint64_t v[NC / T];
+#pragma unroll
+  for (int k = 0; k < NC / T; ++k) v[k] = src0[(h << LOGNL) + tid + k * T];
+  cl.barrier_wait();
+#pragma unroll
+  for (int k = 0; k < NC / T; ++k) {
+    const uint32_t d = gal_dst((h << LOGNL) + tid + k * T, ginv, CL_LOGN);
+    cl.map_shared_rank(sm, (int)(d >> LOGNL))[swz<LOGE>(d & (NC - 1))] = v[k];
+  }
+  cl.sync();
+#pragma unroll 4
+  for (int k = 0; k < NC / T; ++k) {
+    const int li = tid + k * T;
+    c0p[(h << LOGNL) + li] = sm[swz<LOGE>(li)];
+  }
+  cl.sync();
+  // tau_g(c1): diagonal block, then the digit
+#pragma unroll 4
+  for (int k = 0; k < NC / T; ++k) {
+    const int idx = (h << LOGNL) + tid + k * T;
+    const uint32_t d = gal_dst(idx, ginv, CL_LOGN);
+    cl.map_shared_rank(sm, (int)(d >> LOGNL))[swz<LOGE>(d & (NC - 1))] = src1[idx];
+  }
+  cl.sync();
+#pragma unroll 4
+  for (int k = 0; k < NC / T; ++k) {
+    const int li = tid + k * T;
+    diag[(h << LOGNL) + li] = sm[swz<LOGE>(li)];
+  }
+  ncl::ntt_inverse_cluster_smem<CL_LOGN, LOGE, CL_LOGC>(sm, C->tw_inv + (size_t)i * (2u << CL_LOGN), P.q, P.ninv,
+                                                        P.ninv_s, [&](int k2, uint64_t v) { dig[k2] = v; });
+}
+
+#define LOLA_LAUNCH_CLUSTER(KERNEL, units, threads, stream, ...)                                    \
+  do {                                                                                             \
+    const size_t smem = sizeof(uint64_t) << (CL_LOGN - CL_LOGC);                                    \
+    static bool attr_done = false;                                                                 \
+    if (!attr_done) {                                                                              \
+      cudaFuncSetAttribute(KERNEL, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);        \
+      attr_done = true;                                                                            \
+    }                                                                                              \
+    KERNEL<<<(unsigned)((units) << CL_LOGC), threads, smem, stream>>>(__VA_ARGS__);                 \
+  } while (0)
 
 // ------------------------------------------------------------------ dispatch
 #define LOLA_DISPATCH(logn, KERNEL, grid, stream, ...) LOLA_DISPATCH_CFG(Cfg, logn, KERNEL, grid, stream, __VA_ARGS__)
@@ -381,8 +515,19 @@ int enc_msg(Ctx* c, const uint64_t* m, const int64_t* e1, const uint32_t* d_tidx
   return post_launch(c, s);
 }
 
+// which key-switch transforms run as 2-CTA clusters at n = 16384 (bit 0
+// decompose, 1 mod-up, 2 INTT mod P, 3 mod-down)
+#ifndef LOLA_CLUSTER_MASK
+#define LOLA_CLUSTER_MASK 0xE
+#endif
+static constexpr unsigned kClusterMask = LOLA_CLUSTER_MASK;
+
 int ks_decompose(Ctx* c, const KsDev& a, cudaStream_t s) {
   ProfScope ps(c, KI_KS_DECOMPOSE, s, a.count * c->L);
+  if ((kClusterMask & 1u) && c->logn == CL_LOGN) {
+    LOLA_LAUNCH_CLUSTER(kc_ks_decompose, a.count * c->L, 256, s, c->dev, a);
+    return post_launch(c, s);
+  }
   LOLA_DISPATCH(c->logn, kn_ks_decompose, a.count * c->L, s, c->dev, a);
   return post_launch(c, s);
 }
@@ -392,19 +537,31 @@ int ks_modup(Ctx* c, const KsDev& a, bool skip_diag, cudaStream_t s) {
   const size_t per = skip_diag ? (size_t)c->L * (LK - 1) : (size_t)c->L * LK;
   if (!per) return LOLA_OK;
   ProfScope ps(c, KI_KS_MODUP, s, a.count * per);
+  if ((kClusterMask & 2u) && c->logn == CL_LOGN) {
+    LOLA_LAUNCH_CLUSTER(kc_ks_modup, a.count * per, 256, s, c->dev, a, (int)skip_diag);
+    return post_launch(c, s);
+  }
   LOLA_DISPATCH_CFG(CfgM, c->logn, kn_ks_modup, a.count * per, s, c->dev, a, (int)skip_diag);
   return post_launch(c, s);
 }
 
 int ks_intt_p(Ctx* c, const KsDev& a, cudaStream_t s) {
   ProfScope ps(c, KI_KS_IP_P, s, a.count * 2);
+  if ((kClusterMask & 4u) && c->logn == CL_LOGN) {
+    LOLA_LAUNCH_CLUSTER(kc_ks_intt_p, a.count * 2, 256, s, c->dev, a);
+    return post_launch(c, s);
+  }
   LOLA_DISPATCH(c->logn, kn_ks_intt_p, a.count * 2, s, c->dev, a);
   return post_launch(c, s);
 }
 
 int ks_moddown(Ctx* c, const KsDev& a, cudaStream_t s) {
   ProfScope ps(c, KI_KS_MODDOWN, s, a.count * 2 * c->L);
-  LOLA_DISPATCH(c->logn, kn_ks_moddown, a.count * 2 * c->L, s, c->dev, a);
+  if ((kClusterMask & 8u) && c->logn == CL_LOGN) {
+    LOLA_LAUNCH_CLUSTER(kc_ks_moddown, a.count * 2 * c->L, 256, s, c->dev, a);
+    return post_launch(c, s);
+  }
+  LOLA_DISPATCH_CFG(CfgM, c->logn, kn_ks_moddown, a.count * 2 * c->L, s, c->dev, a);
   return post_launch(c, s);
 }
 
