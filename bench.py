@@ -50,7 +50,8 @@ def parse():
     ap.add_argument("--L", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=1)
-    ap.add_argument("--mode", choices=["network", "serve"], default="network")
+    ap.add_argument("--mode", choices=["network", "serve", "primitives"], default="network")
+    ap.add_argument("--n", type=int, default=16384, help="primitives mode: ring degree")
     ap.add_argument("--rates", default="25,100,200", help="serve mode: Poisson arrival rates (requests/s)")
     ap.add_argument("--duration", type=float, default=10.0, help="serve mode: seconds of arrivals per rate")
     return ap.parse_args()
@@ -195,13 +196,41 @@ def aggregate(local_ms: float, local_units: int, dist=None, device=None):
     return float(t.item()), int(u.item())
 
 
+# ----------------------------------------------------- plaintext expectations
+def plain_conv(img, conv_w, k: int = 5, stride: int = 2):
+    """The MNIST-shaped convolution over Z (numpy, exact in int64): the
+    image zero-padded bottom/right so that ceil((28 - 5) / 2) + 1 = 13
+    windows fit per axis; outputs map-major, windows row-major."""
+    import numpy as np
+    img = np.asarray(img, dtype=np.int64)
+    h, w = img.shape
+    oh, ow = -(-(h - k) // stride) + 1, -(-(w - k) // stride) + 1
+    pad = np.zeros((stride * (oh - 1) + k, stride * (ow - 1) + k), np.int64)
+    pad[:h, :w] = img
+    win = np.stack([pad[stride * i:stride * i + k, stride * j:stride * j + k].reshape(-1)
+                    for i in range(oh) for j in range(ow)])           # [windows][k*k]
+    return (np.asarray(conv_w, dtype=np.int64) @ win.T).reshape(-1)
+
+
+def plain_mnist(img, mnet):
+    """Expected decrypted outputs: conv, square, dense, square, dense over Z
+    (Python ints after the first dense layer: the last values exceed int64)."""
+    x = [int(v) ** 2 for v in plain_conv(img, mnet.conv_w)]
+    x = [sum(int(wi) * xi for wi, xi in zip(row, x)) ** 2 for row in mnet.dense1_w]
+    return [sum(int(wi) * xi for wi, xi in zip(row, x)) for row in mnet.dense2_w]
+
+
+def plain_dense(x, W):
+    return [sum(int(wi) * int(xi) for wi, xi in zip(row, x)) for row in W]
+
+
 # --------------------------------------------------------------------- ours
 KERNEL_BYTES = {
     # algorithmic bytes per work unit (n = ring degree, L = ciphertext primes)
     # transform kernels: one unit = one limb-polynomial
     "ks_modup": lambda n, L: 16 * n,                 # read digit limb, write one mod-up limb
-    "ks_decompose": lambda n, L: 24 * n,             # read c1 limb, write diagonal + digit
-    "ks_moddown": lambda n, L: 5 * 8 * n,            # x_P, inner product, addend, accumulator in; out
+    "ks_decompose": lambda n, L: 40 * n,             # read c0, c1 limbs; write permuted c0, diagonal, digit
+    "ks_moddown": lambda n, L: 24 * n,               # x_P and inner-product limb in (addends folded in ks_ip); out
     "ks_intt_p": lambda n, L: 16 * n,                # special-prime inner product in, x_P out
     # inner product: one unit = two coefficients of one (ct, prime): L digit words in, 2 words out, each x2
     "ks_ip": lambda n, L: 2 * 8 * (L + 2),
@@ -306,10 +335,7 @@ def run_ours(args):
 
     # correctness spot check of this run's output (first request, decrypted)
     dec = L.lola_decrypt(ctx, sk, ct_out, n)
-    from oracle import lola as OL  # integer network only (no encryption)
-    x = OL.int_conv(imgs[0], mnet.conv_w, 5, 5, 2)
-    x = OL.int_dense(OL.int_square(x), mnet.dense1_w)
-    want = OL.int_dense(OL.int_square(x), mnet.dense2_w)
+    want = plain_mnist(imgs[0], mnet)
     got = [int(dec[m, s]) for m, s in net.output_map()]
     correct = got == want
 
@@ -379,13 +405,13 @@ def run_ours(args):
         # the issue-rate peak (SMs x 4 schedulers x 32 lanes x max clock)
         # divided by the 32-bit operations of one 64-bit Shoup butterfly
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
-        clk = peaks.get("sm_max_mhz", 2070.0) * 1e6
-        peak_bf = sms * 128 * clk / OPS_PER_BUTTERFLY / 1e9
+        sm_hz = peaks.get("sm_max_mhz", 2070.0) * 1e6
+        peak_bf = sms * 128 * sm_hz / OPS_PER_BUTTERFLY / 1e9
         bf_per_unit = (n // 2) * (n.bit_length() - 1)
         achieved = d["units"] * bf_per_unit / (d["ms"] / 1000.0) / 1e9
         roofline.update({"bound": "alu", "achieved": achieved, "peak": peak_bf, "unit": "Gbutterfly/s",
                          "frac": achieved / peak_bf,
-                         "peak_source": f"derived: {sms} SMs x 128 lanes x {clk / 1e9:.2f} GHz / {OPS_PER_BUTTERFLY} "
+                         "peak_source": f"derived: {sms} SMs x 128 lanes x {sm_hz / 1e9:.2f} GHz / {OPS_PER_BUTTERFLY} "
                                         "32-bit ops per 64-bit Shoup butterfly"})
     else:
         roofline.update({"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
@@ -436,6 +462,79 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------- primitives
+def run_primitives(args):
+    """One launch per operation on a batch of `--batch` ciphertexts of
+    uniform random residues (n = `--n`, `--L` 60-bit primes + a special
+    prime): forward NTT and inverse NTT of all 2 B L limb-polynomials, B
+    rotations by random steps in [1, n/2) (one Galois key per distinct
+    step), B/2 ct x ct products with relinearisation.  Per operation: device
+    time per launch (CUDA events), per ciphertext, and the transform rate
+    against the derived integer-ALU peak."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_1812_10659_gb300 import lola as L
+
+    ps = W.params_sweep(args.n, args.L)
+    n, Lq, B = ps.n, ps.L, args.batch
+    ctx = L.lola_ctx_create(ps.n, ps.q, ps.L, ps.K, ps.t)
+    stream = torch.cuda.current_stream()
+    host = W.random_residues(11, (B, 2), ps.q[:Lq], n)
+    steps = [int(s) for s in W.rotation_steps(11, B, n)]
+    sk, ev = L.lola_keygen(ctx, 11, sorted(set(steps)), L.LOLA_KEY_RELIN)
+    src = L.lola_ct_import(ctx, host[:, None])
+    dst = L.lola_ct_create(ctx, B)
+    half = max(1, B // 2)
+    prod = L.lola_ct_create(ctx, half)
+    work = torch.from_numpy(host.view(np.int64).copy()).cuda()
+    ps_src, ps_dst, ps_prod = L.lola_ct_data(src), L.lola_ct_data(dst), L.lola_ct_data(prod)
+    ct_bytes = 2 * Lq * n * 8
+    ops = {
+        "ntt_fwd": (lambda: L.lola_ntt_forward(ctx, work, 2 * B, Lq, stream), B),
+        "ntt_inv": (lambda: L.lola_ntt_inverse(ctx, work, 2 * B, Lq, stream), B),
+        "rotate": (lambda: L.lola_rotate(ctx, ev, ps_src, ps_dst, B, steps, stream), B),
+        "multiply_relin": (lambda: L.lola_multiply(ctx, ev, ps_src, ps_src + (half * ct_bytes if B > 1 else 0),
+                                                   ps_prod, half, stream=stream), half),
+    }
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        peaks = json.load(open(pk))
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    clk = peaks.get("sm_max_mhz", 2070.0) * 1e6
+    peak_bf = sms * 128 * clk / OPS_PER_BUTTERFLY / 1e9
+    bf_limb = (n // 2) * (n.bit_length() - 1)
+    res = {}
+    for name, (fn, cts) in ops.items():
+        for _ in range(max(args.warmup, 3)):
+            fn()
+        torch.cuda.synchronize()
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        evs[0].record(stream)
+        for i in range(args.steps):
+            fn()
+            evs[i + 1].record(stream)
+        torch.cuda.synchronize()
+        ms = sorted(evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps))
+        med = statistics.median(ms)
+        r = {"ms_per_launch": med, "us_per_ct": med * 1000 / cts, "cts_per_launch": cts}
+        if name.startswith("ntt"):
+            limbs = 2 * B * Lq
+            r["GB/s"] = limbs * 16 * n / (med / 1000) / 1e9
+            r["alu_frac"] = limbs * bf_limb / (med / 1000) / 1e9 / peak_bf
+        res[name] = r
+    print(json.dumps({"mode": "primitives", "n": n, "L": Lq, "K": ps.K, "batch": B, "steps": args.steps,
+                      "data": "synthetic uniform residues, random rotation steps",
+                      "alu_peak_gbutterfly_s": peak_bf, "ops": res}), flush=True)
+    for h in (src, dst, prod):
+        L.lola_ct_destroy(h)
+    L.lola_keys_destroy(sk)
+    L.lola_keys_destroy(ev)
+    L.lola_ctx_destroy(ctx)
+
+
 # ------------------------------------------------------------------- serving
 def run_serve(args):
     """Serving mix: Poisson arrivals, 70 % MNIST-shaped networks and 30 %
@@ -445,7 +544,6 @@ def run_serve(args):
     import torch
 
     import workloads as W
-    from oracle import lola as OL
     from paper_1812_10659_gb300 import lola as L, serve
 
     ps2, ps4 = W.params_mnist(args.L), W.params_head(args.L)
@@ -467,14 +565,12 @@ def run_serve(args):
     for i in range(8):
         img = W.image(idx=5000 + i)
         pool["mnist"].append(L.lola_encrypt(ctx2, keys["mnist"][0], L.lola_pack_convolution(img, 5, 5, 2, n)[0], 300 + i))
-        x = OL.int_conv(img, mnet.conv_w, 5, 5, 2)
-        x = OL.int_dense(OL.int_square(x), mnet.dense1_w)
-        want["mnist"].append(OL.int_dense(OL.int_square(x), mnet.dense2_w))
+        want["mnist"].append(plain_mnist(img, mnet))
         f = W.feature_vector(idx=5000 + i)
         v = np.zeros((1, n), np.int64)
         v[0, :4096] = f
         pool["head"].append(L.lola_encrypt(ctx4, keys["head"][0], v, 400 + i))
-        want["head"].append(OL.int_dense(f, Wh))
+        want["head"].append(plain_dense(f, Wh))
     omap = {}
     for name, (d, layers, ctx, _) in nets.items():
         h = L.lola_net_create(ctx, d, layers)
@@ -554,6 +650,8 @@ def main():
         run_reference(args)
     elif args.mode == "serve":
         run_serve(args)
+    elif args.mode == "primitives":
+        run_primitives(args)
     else:
         run_ours(args)
 
