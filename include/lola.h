@@ -63,7 +63,7 @@ typedef struct lola_net lola_net;
  *   n      ring degree, power of two, 16 <= n <= 16384
  *   L      number of ciphertext primes (Q = q_0 ... q_{L-1}), 1 <= L <= 12
  *   K      special primes for key switching: 0 or 1 (P = q_L when 1)
- *   q      L + K distinct primes, each = 1 mod 2n and < 2^61
+ *   q      L + K distinct primes, each = 1 mod 2n and < 2^61 - 2^30
  *   k_t    number of plaintext moduli (CRT pipelines), 1 <= k_t <= 4
  *   t      k_t distinct primes = 1 mod 2n, < 2^31, coprime to all q
  * The library adds its own auxiliary primes for exact ct x ct scaling.

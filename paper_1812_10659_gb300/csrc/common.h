@@ -36,6 +36,9 @@ struct CtxDev {
   int iP;                          // index of P (= L) when K = 1
   int iB;                          // first auxiliary prime index (= L + K)
   int iT;                          // first plaintext modulus index (= L + K + M)
+  // 1 when every prime of Q and P is below 8x the smallest one: a digit
+  // (< q_i) is then a valid forward-transform input for every q_j as it is
+  uint32_t modup_raw;
   PrimeDev pr[MAXP];
   const uint64_t* tw_fwd;          // [np][n] pairs (w, floor(w 2^64 / q))
   const uint64_t* tw_inv;          // [np][n] pairs for psi^-1

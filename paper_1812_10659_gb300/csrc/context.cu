@@ -208,8 +208,11 @@ static int build_ctx(Ctx* c, const lola_params* p) {
   if (!p->q || !p->t) return fail(LOLA_E_PARAM, "null prime list");
   const uint64_t two_n = 2ull * p->n;
   std::vector<uint64_t> qp(p->q, p->q + p->L + p->K), ts(p->t, p->t + p->k_t);
+  // the forward transforms' lazy bound (values below 8q + 2^32) needs q < 2^61 - 2^30
+  const uint64_t qmax = (1ull << 61) - (1ull << 30);
   for (uint64_t q : qp)
-    if (q >= (1ull << 61) || q % two_n != 1 || !is_prime_h(q)) return fail(LOLA_E_PARAM, "ciphertext prime must be prime, = 1 mod 2n, < 2^61");
+    if (q >= qmax || q % two_n != 1 || !is_prime_h(q))
+      return fail(LOLA_E_PARAM, "ciphertext prime must be prime, = 1 mod 2n, < 2^61 - 2^30");
   for (uint64_t t : ts)
     if (t >= (1ull << 31) || t % two_n != 1 || !is_prime_h(t)) return fail(LOLA_E_PARAM, "plaintext modulus must be prime, = 1 mod 2n, < 2^31");
   std::vector<uint64_t> all = qp;
@@ -225,8 +228,8 @@ static int build_ctx(Ctx* c, const lola_params* p) {
   need += tmax;
   std::vector<uint64_t> aux;
   double have = 0;
-  for (uint64_t x = ((1ull << 61) - 1) / two_n * two_n + 1; have < need; x -= two_n) {
-    if (x >= (1ull << 61) || !is_prime_h(x)) continue;
+  for (uint64_t x = (qmax - 1) / two_n * two_n + 1; have < need; x -= two_n) {
+    if (x >= qmax || !is_prime_h(x)) continue;
     if (std::find(qp.begin(), qp.end(), x) != qp.end()) continue;
     aux.push_back(x);
     have += std::log2((double)x);
@@ -249,6 +252,10 @@ static int build_ctx(Ctx* c, const lola_params* p) {
   H.kt = c->kt;
   H.np = np;
   H.iP = c->iP();
+  {
+    const uint64_t qlo = *std::min_element(qp.begin(), qp.end()), qhi = *std::max_element(qp.begin(), qp.end());
+    H.modup_raw = qhi / 8 < qlo ? 1u : 0u;
+  }
   H.iB = c->iB();
   H.iT = c->iT();
   const uint64_t n = c->n;

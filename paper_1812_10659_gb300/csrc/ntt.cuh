@@ -9,11 +9,13 @@
 // position k holds a(psi^(2 brev(k) + 1)).  Inverse: the Gentleman-Sande
 // mirror image with psi^-1, scaled at the end by a caller-given constant
 // (n^-1, possibly times an extra factor).  Lazy reduction (Harvey) between
-// stages: forward values stay below 4q + 2^32 (the "a" operand of each
-// butterfly is brought below 2q + 2^32 by comparing only its high 32 bits
-// with those of 2q), inverse values below 2q; q < 2^61 keeps every
-// intermediate below 2^64.  The loader may supply any value below 4q; what
-// the storer receives is canonical [0, q).
+// stages.  Forward: on even stages the "a" operand of each butterfly is
+// brought below 4q + 2^32 by comparing only its high 32 bits with those of
+// 4q; odd stages skip that step, so values stay below 6q + 2^32 after an
+// even stage and below 8q + 2^32 after an odd one (twiddle products are in
+// [0, 2q)).  Inverse values stay below 2q.  q < 2^61 - 2^30 keeps every
+// intermediate below 2^64.  The forward loader may supply any value below
+// 8q + 2^32; what the storer receives is canonical [0, q).
 //
 // Layout: the CTA holds the whole limb (n words) in shared memory.  Each
 // thread owns E = 2^LOGE words per pass and runs up to LOGE radix-2 stages
@@ -24,6 +26,8 @@
 #pragma once
 #include <stdint.h>
 
+#include <type_traits>
+
 #include <cooperative_groups.h>
 
 #include "modarith.cuh"
@@ -33,6 +37,39 @@ namespace lola {
 template <int LOGE>
 __device__ __forceinline__ int swz(int idx) {
   return idx ^ ((idx >> LOGE) & 15);
+}
+
+// A forward storer is either a callable st(i, v) or an object with
+// fetch(i) -> f and operator()(i, v, f): the final phase then issues the
+// fetches of a group of outputs before their stores (the fetch is a global
+// load the store may alias, so the compiler would not hoist it itself).
+template <class S, class = void>
+struct has_fetch : std::false_type {};
+template <class S>
+struct has_fetch<S, std::void_t<decltype(std::declval<const S&>().fetch(0))>> : std::true_type {};
+
+template <int LOGE, int E, int T, class Storer>
+__device__ __forceinline__ void store_outputs(const uint64_t* sm, const Storer& st, int tid, int base) {
+  if constexpr (has_fetch<Storer>::value) {
+    constexpr int GRP = 8 < E ? 8 : E;
+#pragma unroll
+    for (int k0 = 0; k0 < E; k0 += GRP) {
+      uint64_t f[GRP];
+#pragma unroll
+      for (int j = 0; j < GRP; ++j) f[j] = st.fetch(base + tid + (k0 + j) * T);
+#pragma unroll
+      for (int j = 0; j < GRP; ++j) {
+        const int i = tid + (k0 + j) * T;
+        st(base + i, sm[swz<LOGE>(i)], f[j]);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+      const int i = tid + k * T;
+      st(base + i, sm[swz<LOGE>(i)]);
+    }
+  }
 }
 
 // global index of local element k for thread tid in the bit window [hb .. lb]
@@ -68,8 +105,8 @@ __device__ __forceinline__ void fwd_stages(uint64_t (&x)[1 << LOGE], const uint6
                                            int tid) {
   using G = NttGeom<LOGN, LOGE>;
   constexpr int hb = G::fhb(P), lb = G::flb(P), top = G::fdone(P) - 1;
-  const uint64_t q2 = 2 * q;
-  const uint32_t q2hi = (uint32_t)(q2 >> 32);
+  const uint64_t q2 = 2 * q, q4 = 4 * q;
+  const uint32_t q4hi = (uint32_t)(q4 >> 32);
 #pragma unroll
   for (int bp = top; bp >= lb; --bp) {
     const int s = LOGN - 1 - bp;
@@ -83,7 +120,7 @@ __device__ __forceinline__ void fwd_stages(uint64_t (&x)[1 << LOGE], const uint6
       const ulonglong2 wq = __ldg(twb + (k >> (lbit + 1)));
       const uint64_t w = wq.x, wp = wq.y;
       uint64_t a = x[k];
-      if ((uint32_t)(a >> 32) > q2hi) a -= q2;
+      if ((s & 1) == 0 && (uint32_t)(a >> 32) > q4hi) a -= q4;
       const uint64_t t = shoup_mul_lazy(x[k | (1 << lbit)], w, wp, q);
       x[k] = a + t;
       x[k | (1 << lbit)] = a - t + q2;
@@ -114,15 +151,11 @@ __device__ __forceinline__ void fwd_pass(uint64_t* sm, uint64_t (&x)[1 << LOGE],
 #pragma unroll
     for (int k = 0; k < G::E; ++k) sm[swz<LOGE>(win_index(tid, k, hb, lb))] = reduce64(x[k], q, qf);
     __syncthreads();
-#pragma unroll
-    for (int k = 0; k < G::E; ++k) {
-      const int i = tid + k * G::T;
-      st(i, sm[swz<LOGE>(i)]);
-    }
+    store_outputs<LOGE, G::E, G::T>(sm, st, tid, 0);
   }
 }
 
-// Forward transform.  ld(i) returns input coefficient i (below 4q);
+// Forward transform.  ld(i) returns input coefficient i (below 8q + 2^32);
 // st(i, v) receives output position i (canonical), called once per i.
 // tw: the prime's (w, w') twiddle pairs; qf = floor(2^64 / q).
 // Every thread of the CTA must call this (it synchronises).
@@ -235,8 +268,8 @@ __device__ __forceinline__ void fwd_stages_c(uint64_t (&x)[1 << LOGE], const uin
                                              int tid, int h, int lognl) {
   using G = NttGeom<LOGN, LOGE>;
   constexpr int hb = G::fhb(P), lb = G::flb(P), top = G::fdone(P) - 1;
-  const uint64_t q2 = 2 * q;
-  const uint32_t q2hi = (uint32_t)(q2 >> 32);
+  const uint64_t q2 = 2 * q, q4 = 4 * q;
+  const uint32_t q4hi = (uint32_t)(q4 >> 32);
 #pragma unroll
   for (int bp = top; bp >= lb; --bp) {
     const int s = LOGN - 1 - bp;
@@ -248,7 +281,7 @@ __device__ __forceinline__ void fwd_stages_c(uint64_t (&x)[1 << LOGE], const uin
       if (k & (1 << lbit)) continue;
       const ulonglong2 wq = __ldg(twb + (k >> (lbit + 1)));
       uint64_t a = x[k];
-      if ((uint32_t)(a >> 32) > q2hi) a -= q2;
+      if ((s & 1) == 0 && (uint32_t)(a >> 32) > q4hi) a -= q4;
       const uint64_t t = shoup_mul_lazy(x[k | (1 << lbit)], wq.x, wq.y, q);
       x[k] = a + t;
       x[k | (1 << lbit)] = a - t + q2;
@@ -300,11 +333,7 @@ __device__ __forceinline__ void fwd_local_pass(uint64_t* sm, uint64_t (&x)[1 << 
 #pragma unroll
     for (int k = 0; k < G::E; ++k) sm[swz<LOGE>(win_index(tid, k, hb, lb))] = reduce64(x[k], q, qf);
     __syncthreads();
-#pragma unroll
-    for (int k = 0; k < G::E; ++k) {
-      const int i = tid + k * GC::T;
-      st((h << GC::LOGNL) + i, sm[swz<LOGE>(i)]);
-    }
+    store_outputs<LOGE, G::E, GC::T>(sm, st, tid, h << GC::LOGNL);
   }
 }
 

@@ -13,8 +13,9 @@ namespace lola {
 // 128 KiB of shared memory, so one CTA runs per SM: 2^4 words (1024 threads,
 // at most 64 registers) hides more latency, 2^5 words (512 threads, up to 128
 // registers) avoids register spills in the forward transforms that read their
-// input straight from global memory.  Measured per kernel: the mod-up
-// transform is faster with 512 threads, the others with 1024.
+// input straight from global memory.  Measured per kernel: the mod-up,
+// mod-down and plain forward / inverse transforms are faster with 512
+// threads, decompose with 1024.
 #ifndef LOLA_NTT14_LOGE
 #define LOLA_NTT14_LOGE 4
 #endif
@@ -37,30 +38,30 @@ using CfgM = Cfg<LOGN, LOLA_NTT14_LOGE_MODUP>;
 
 // ------------------------------------------------------------ plain transforms
 template <int LOGN>
-__global__ void __launch_bounds__(Cfg<LOGN>::T) kn_fwd(const CtxDev* __restrict__ C, const uint64_t* in,
+__global__ void __launch_bounds__(CfgM<LOGN>::T) kn_fwd(const CtxDev* __restrict__ C, const uint64_t* in,
                                                         uint64_t* out, uint32_t limbs, PrimeMap pm) {
   extern __shared__ uint64_t sm[];
-  constexpr int N = Cfg<LOGN>::N;
+  constexpr int N = CfgM<LOGN>::N;
   const size_t poly = blockIdx.x;
   const int p = pm.p[poly % limbs];
   const uint64_t* src = in + poly * N;
   uint64_t* dst = out + poly * N;
-  ntt_forward<LOGN, Cfg<LOGN>::LOGE>(sm, TW_F(C, p), C->pr[p].q, C->pr[p].f64, [&](int i) { return src[i]; },
+  ntt_forward<LOGN, CfgM<LOGN>::LOGE>(sm, TW_F(C, p), C->pr[p].q, C->pr[p].f64, [&](int i) { return src[i]; },
                                       [&](int i, uint64_t v) { dst[i] = v; });
 }
 
 template <int LOGN>
-__global__ void __launch_bounds__(Cfg<LOGN>::T) kn_inv(const CtxDev* __restrict__ C, const uint64_t* in,
+__global__ void __launch_bounds__(CfgM<LOGN>::T) kn_inv(const CtxDev* __restrict__ C, const uint64_t* in,
                                                         uint64_t* out, uint32_t limbs, PrimeMap pm, int mont_fix) {
   extern __shared__ uint64_t sm[];
-  constexpr int N = Cfg<LOGN>::N;
+  constexpr int N = CfgM<LOGN>::N;
   const size_t poly = blockIdx.x;
   const int p = pm.p[poly % limbs];
   const PrimeDev& P = C->pr[p];
   const uint64_t* src = in + poly * N;
   uint64_t* dst = out + poly * N;
   const uint64_t c = mont_fix ? P.ninvr : P.ninv, cs = mont_fix ? P.ninvr_s : P.ninv_s;
-  ntt_inverse<LOGN, Cfg<LOGN>::LOGE>(sm, TW_I(C, p), P.q, c, cs, [&](int i) { return src[i]; },
+  ntt_inverse<LOGN, CfgM<LOGN>::LOGE>(sm, TW_I(C, p), P.q, c, cs, [&](int i) { return src[i]; },
                                       [&](int i, uint64_t v) { dst[i] = v; });
 }
 
@@ -179,12 +180,13 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T) kn_ks_decompose(const CtxDev* __
   uint64_t* diag = a.D + ((ct * L + i) * LK + i) * (size_t)N;
   uint64_t* dig = a.dig + (ct * L + i) * (size_t)N;
   const PrimeDev& P = C->pr[i];
-  // tau_g(c0)
-#pragma unroll 4
-  for (int k = 0; k < N / T; ++k) {
-    const int idx = tid + k * T;
-    sm[swz<LOGE>(gal_dst(idx, ginv, LOGN))] = src0[idx];
-  }
+  // tau_g(c0): all loads of the thread first (the compiler may not move a
+  // global load above a shared store through a generic pointer)
+  uint64_t v[N / T];
+#pragma unroll
+  for (int k = 0; k < N / T; ++k) v[k] = src0[tid + k * T];
+#pragma unroll
+  for (int k = 0; k < N / T; ++k) sm[swz<LOGE>(gal_dst(tid + k * T, ginv, LOGN))] = v[k];
   __syncthreads();
 #pragma unroll 4
   for (int k = 0; k < N / T; ++k) {
@@ -193,11 +195,10 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T) kn_ks_decompose(const CtxDev* __
   }
   __syncthreads();
   // tau_g(c1): diagonal block, then digit
-#pragma unroll 4
-  for (int k = 0; k < N / T; ++k) {
-    const int idx = tid + k * T;
-    sm[swz<LOGE>(gal_dst(idx, ginv, LOGN))] = src1[idx];
-  }
+#pragma unroll
+  for (int k = 0; k < N / T; ++k) v[k] = src1[tid + k * T];
+#pragma unroll
+  for (int k = 0; k < N / T; ++k) sm[swz<LOGE>(gal_dst(tid + k * T, ginv, LOGN))] = v[k];
   __syncthreads();
 #pragma unroll 4
   for (int k = 0; k < N / T; ++k) {
@@ -222,7 +223,8 @@ __global__ void __launch_bounds__(CfgM<LOGN>::T) kn_ks_modup(const CtxDev* __res
   const uint64_t* dig = a.dig + (ct * L + i) * (size_t)N;
   uint64_t* dst = a.D + ((ct * L + i) * LK + j) * (size_t)N;
   const PrimeDev& P = C->pr[j];
-  ntt_forward<LOGN, CfgM<LOGN>::LOGE>(sm, TW_F(C, j), P.q, P.f64, [&](int k) { return reduce64(dig[k], P.q, P.f64); },
+  const bool raw = C->modup_raw != 0;
+  ntt_forward<LOGN, CfgM<LOGN>::LOGE>(sm, TW_F(C, j), P.q, P.f64, [&](int k) { return raw ? dig[k] : reduce64(dig[k], P.q, P.f64); },
                                       [&](int k, uint64_t v) { dst[k] = v; });
 }
 
@@ -240,6 +242,15 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T) kn_ks_intt_p(const CtxDev* __res
   ntt_inverse<LOGN, Cfg<LOGN>::LOGE>(sm, TW_I(C, ip), P.q, P.ninv, P.ninv_s, [&](int k) { return src[k]; },
                                       [&](int k, uint64_t v) { dst[k] = v; });
 }
+
+// mod-down epilogue: the inner-product limb is fetched ahead of the stores
+struct ModDownStore {
+  const uint64_t* acc;
+  uint64_t* dst;
+  uint64_t q;
+  __device__ __forceinline__ uint64_t fetch(int k) const { return acc[k]; }
+  __device__ __forceinline__ void operator()(int k, uint64_t v, uint64_t f) const { dst[k] = sub_mod(f, v, q); }
+};
 
 // E: output limb out[comp][j] = ACC'[comp][j] - NTT(x~ P^-1 mod q_j), with
 //    x~ = centered(x mod P); the inner-product kernel left ACC' = ACC P^-1 +
@@ -268,7 +279,7 @@ __global__ void __launch_bounds__(CfgM<LOGN>::T) kn_ks_moddown(const CtxDev* __r
         const uint64_t v = x[k];
         return shoup_mul_lazy(v, Pinv, Pinv_s, P.q) + (v > Phalf ? q2m1 : 0);
       },
-      [&](int k, uint64_t v) { dst[k] = sub_mod(accp[k], v, P.q); });
+      ModDownStore{accp, dst, P.q});
 }
 
 // ------------------------------------------- n = 16384: 2-CTA cluster versions
@@ -292,8 +303,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 2)
   const uint64_t* dig = a.dig + (ct * L + i) * (size_t)N;
   uint64_t* dst = a.D + ((ct * L + i) * LK + j) * (size_t)N;
   const PrimeDev& P = C->pr[j];
+  const bool raw = C->modup_raw != 0;
   ncl::ntt_forward_cluster<CL_LOGN, 5, CL_LOGC>(sm, C->tw_fwd + (size_t)j * (2u << CL_LOGN), P.q, P.f64,
-                                                [&](int k) { return reduce64(dig[k], P.q, P.f64); },
+                                                [&](int k) { return raw ? dig[k] : reduce64(dig[k], P.q, P.f64); },
                                                 [&](int k, uint64_t v) { dst[k] = v; });
 }
 
@@ -332,7 +344,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 2) kc_ks_moddow
         const uint64_t v = x[k];
         return shoup_mul_lazy(v, Pinv, Pinv_s, P.q) + (v > Phalf ? q2m1 : 0);
       },
-      [&](int k, uint64_t v) { dst[k] = sub_mod(accp[k], v, P.q); });
+      ModDownStore{accp, dst, P.q});
 }
 
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 2) kc_ks_decompose(const CtxDev* __restrict__ C, KsDev a) {
@@ -453,7 +465,7 @@ int ntt_fwd_map(Ctx* c, const uint64_t* in, uint64_t* out, size_t n_polys, uint3
                 cudaStream_t s) {
   if (!n_polys) return LOLA_OK;
   ProfScope ps(c, KI_NTT_FWD, s, n_polys);
-  LOLA_DISPATCH(c->logn, kn_fwd, n_polys, s, c->dev, in, out, limbs, pm);
+  LOLA_DISPATCH_CFG(CfgM, c->logn, kn_fwd, n_polys, s, c->dev, in, out, limbs, pm);
   return post_launch(c, s);
 }
 
@@ -461,7 +473,7 @@ int ntt_inv_map(Ctx* c, const uint64_t* in, uint64_t* out, size_t n_polys, uint3
                 bool mont_fix, cudaStream_t s) {
   if (!n_polys) return LOLA_OK;
   ProfScope ps(c, KI_NTT_INV, s, n_polys);
-  LOLA_DISPATCH(c->logn, kn_inv, n_polys, s, c->dev, in, out, limbs, pm, (int)mont_fix);
+  LOLA_DISPATCH_CFG(CfgM, c->logn, kn_inv, n_polys, s, c->dev, in, out, limbs, pm, (int)mont_fix);
   return post_launch(c, s);
 }
 
