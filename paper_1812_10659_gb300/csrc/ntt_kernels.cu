@@ -286,9 +286,20 @@ __global__ void __launch_bounds__(CfgM<LOGN>::T) kn_ks_moddown(const CtxDev* __r
 // Each limb transform is split over a cluster of two CTAs (half the limb each,
 // 64 KiB of shared memory), so a launch with few limbs still keeps twice as
 // many SMs busy and each dependent step of a rotation takes half as long.
+// Two geometries: 2^5 words per thread (256 threads per CTA, up to 128
+// registers) for launches of many limbs, where per-thread ILP and three
+// passes win; 2^4 words (512 threads, 64 registers, four passes) for small
+// launches, where more threads per transform shorten its latency.
 constexpr int CL_LOGN = 14, CL_LOGC = 1;
+template <int LOGE>
+constexpr int cl_threads() { return (1 << CL_LOGN) >> (LOGE + CL_LOGC); }
+// launches with fewer limb transforms than this use the 2^4 geometry
+#ifndef LOLA_CL_SMALL_UNITS
+#define LOLA_CL_SMALL_UNITS 400
+#endif
 
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 2)
+template <int CL_LOGE>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(cl_threads<CL_LOGE>(), 2)
     kc_ks_modup(const CtxDev* __restrict__ C, KsDev a, int skip_diag) {
   extern __shared__ uint64_t sm[];
   constexpr int N = 1 << CL_LOGN;
@@ -304,12 +315,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 2)
   uint64_t* dst = a.D + ((ct * L + i) * LK + j) * (size_t)N;
   const PrimeDev& P = C->pr[j];
   const bool raw = C->modup_raw != 0;
-  ncl::ntt_forward_cluster<CL_LOGN, 5, CL_LOGC>(sm, C->tw_fwd + (size_t)j * (2u << CL_LOGN), P.q, P.f64,
+  ncl::ntt_forward_cluster<CL_LOGN, CL_LOGE, CL_LOGC>(sm, C->tw_fwd + (size_t)j * (2u << CL_LOGN), P.q, P.f64,
                                                 [&](int k) { return raw ? dig[k] : reduce64(dig[k], P.q, P.f64); },
                                                 [&](int k, uint64_t v) { dst[k] = v; });
 }
 
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 2) kc_ks_intt_p(const CtxDev* __restrict__ C, KsDev a) {
+template <int CL_LOGE>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(cl_threads<CL_LOGE>(), 2) kc_ks_intt_p(const CtxDev* __restrict__ C, KsDev a) {
   extern __shared__ uint64_t sm[];
   constexpr int N = 1 << CL_LOGN;
   const int LK = C->L + C->K, ip = C->iP;
@@ -319,12 +331,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 2) kc_ks_intt_p
   const PrimeDev& P = C->pr[ip];
   const uint64_t* src = a.acc + ct * a.acc_stride + (size_t)(comp * LK + ip) * N;
   uint64_t* dst = a.xP + (ct * 2 + comp) * (size_t)N;
-  ncl::ntt_inverse_cluster<CL_LOGN, 5, CL_LOGC>(sm, C->tw_inv + (size_t)ip * (2u << CL_LOGN), P.q, P.ninv, P.ninv_s,
+  ncl::ntt_inverse_cluster<CL_LOGN, CL_LOGE, CL_LOGC>(sm, C->tw_inv + (size_t)ip * (2u << CL_LOGN), P.q, P.ninv, P.ninv_s,
                                                 [&](int k) { return src[k]; },
                                                 [&](int k, uint64_t v) { dst[k] = v; });
 }
 
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 2) kc_ks_moddown(const CtxDev* __restrict__ C, KsDev a) {
+template <int CL_LOGE>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(cl_threads<CL_LOGE>(), 2) kc_ks_moddown(const CtxDev* __restrict__ C, KsDev a) {
   extern __shared__ uint64_t sm[];
   constexpr int N = 1 << CL_LOGN;
   const int L = C->L, LK = C->L + C->K;
@@ -338,7 +351,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 2) kc_ks_moddow
   const uint64_t Pinv = C->PinvQ[j], Pinv_s = C->PinvQ_s[j];
   const uint64_t* x = a.xP + (ct * 2 + comp) * (size_t)N;
   uint64_t* dst = a.out + ((ct * 2 + comp) * L + j) * (size_t)N;
-  ncl::ntt_forward_cluster<CL_LOGN, 5, CL_LOGC>(
+  ncl::ntt_forward_cluster<CL_LOGN, CL_LOGE, CL_LOGC>(
       sm, C->tw_fwd + (size_t)j * (2u << CL_LOGN), P.q, P.f64,
       [&](int k) {
         const uint64_t v = x[k];
@@ -347,10 +360,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 2) kc_ks_moddow
       ModDownStore{accp, dst, P.q});
 }
 
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 2) kc_ks_decompose(const CtxDev* __restrict__ C, KsDev a) {
+template <int CL_LOGE>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(cl_threads<CL_LOGE>(), 2) kc_ks_decompose(const CtxDev* __restrict__ C, KsDev a) {
   extern __shared__ uint64_t sm[];
   namespace cg = cooperative_groups;
-  constexpr int N = 1 << CL_LOGN, LOGE = 5, LOGNL = CL_LOGN - CL_LOGC, NC = 1 << LOGNL;
+  constexpr int N = 1 << CL_LOGN, LOGE = CL_LOGE, LOGNL = CL_LOGN - CL_LOGC, NC = 1 << LOGNL;
   constexpr int T = N >> (LOGE + CL_LOGC);
   cg::cluster_group cl = cg::this_cluster();
   const int h = (int)cl.block_rank();
@@ -537,7 +551,10 @@ static constexpr unsigned kClusterMask = LOLA_CLUSTER_MASK;
 int ks_decompose(Ctx* c, const KsDev& a, cudaStream_t s) {
   ProfScope ps(c, KI_KS_DECOMPOSE, s, a.count * c->L);
   if ((kClusterMask & 1u) && c->logn == CL_LOGN) {
-    LOLA_LAUNCH_CLUSTER(kc_ks_decompose, a.count * c->L, 256, s, c->dev, a);
+    if (a.count * c->L < LOLA_CL_SMALL_UNITS)
+      LOLA_LAUNCH_CLUSTER(kc_ks_decompose<4>, a.count * c->L, cl_threads<4>(), s, c->dev, a);
+    else
+      LOLA_LAUNCH_CLUSTER(kc_ks_decompose<5>, a.count * c->L, cl_threads<5>(), s, c->dev, a);
     return post_launch(c, s);
   }
   LOLA_DISPATCH(c->logn, kn_ks_decompose, a.count * c->L, s, c->dev, a);
@@ -550,7 +567,10 @@ int ks_modup(Ctx* c, const KsDev& a, bool skip_diag, cudaStream_t s) {
   if (!per) return LOLA_OK;
   ProfScope ps(c, KI_KS_MODUP, s, a.count * per);
   if ((kClusterMask & 2u) && c->logn == CL_LOGN) {
-    LOLA_LAUNCH_CLUSTER(kc_ks_modup, a.count * per, 256, s, c->dev, a, (int)skip_diag);
+    if (a.count * per < LOLA_CL_SMALL_UNITS)
+      LOLA_LAUNCH_CLUSTER(kc_ks_modup<4>, a.count * per, cl_threads<4>(), s, c->dev, a, (int)skip_diag);
+    else
+      LOLA_LAUNCH_CLUSTER(kc_ks_modup<5>, a.count * per, cl_threads<5>(), s, c->dev, a, (int)skip_diag);
     return post_launch(c, s);
   }
   LOLA_DISPATCH_CFG(CfgM, c->logn, kn_ks_modup, a.count * per, s, c->dev, a, (int)skip_diag);
@@ -560,7 +580,10 @@ int ks_modup(Ctx* c, const KsDev& a, bool skip_diag, cudaStream_t s) {
 int ks_intt_p(Ctx* c, const KsDev& a, cudaStream_t s) {
   ProfScope ps(c, KI_KS_IP_P, s, a.count * 2);
   if ((kClusterMask & 4u) && c->logn == CL_LOGN) {
-    LOLA_LAUNCH_CLUSTER(kc_ks_intt_p, a.count * 2, 256, s, c->dev, a);
+    if (a.count * 2 < LOLA_CL_SMALL_UNITS)
+      LOLA_LAUNCH_CLUSTER(kc_ks_intt_p<4>, a.count * 2, cl_threads<4>(), s, c->dev, a);
+    else
+      LOLA_LAUNCH_CLUSTER(kc_ks_intt_p<5>, a.count * 2, cl_threads<5>(), s, c->dev, a);
     return post_launch(c, s);
   }
   LOLA_DISPATCH(c->logn, kn_ks_intt_p, a.count * 2, s, c->dev, a);
@@ -570,7 +593,10 @@ int ks_intt_p(Ctx* c, const KsDev& a, cudaStream_t s) {
 int ks_moddown(Ctx* c, const KsDev& a, cudaStream_t s) {
   ProfScope ps(c, KI_KS_MODDOWN, s, a.count * 2 * c->L);
   if ((kClusterMask & 8u) && c->logn == CL_LOGN) {
-    LOLA_LAUNCH_CLUSTER(kc_ks_moddown, a.count * 2 * c->L, 256, s, c->dev, a);
+    if (a.count * 2 * c->L < LOLA_CL_SMALL_UNITS)
+      LOLA_LAUNCH_CLUSTER(kc_ks_moddown<4>, a.count * 2 * c->L, cl_threads<4>(), s, c->dev, a);
+    else
+      LOLA_LAUNCH_CLUSTER(kc_ks_moddown<5>, a.count * 2 * c->L, cl_threads<5>(), s, c->dev, a);
     return post_launch(c, s);
   }
   LOLA_DISPATCH_CFG(CfgM, c->logn, kn_ks_moddown, a.count * 2 * c->L, s, c->dev, a);
