@@ -18,6 +18,9 @@ in HBM.  Reported beside it:
 * cpu_baseline: the CPU oracle's per-operation times on the same parameters
   scaled by the network's operation counts.
 
+`--workload lola_dense` runs LoLa-Dense instead (App. C: one dense image
+message per request, masked into the convolution representation on the
+server; 326 rotations per residue, six ciphertext primes).
 `--impl reference` times that CPU oracle as the reference arm.
 Multi-GPU (torchrun): independent replicas, one per GPU, no collective on
 the data path; the barrier and the max over ranks are for timing only.
@@ -47,14 +50,27 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--batch", type=int, default=16, help="requests per batched step (per GPU)")
     ap.add_argument("--plain", type=int, default=8, help="single-request evaluations for plain latency")
-    ap.add_argument("--L", type=int, default=5)
+    ap.add_argument("--L", type=int, default=None,
+                    help="ciphertext primes (default: 5 for mnist, 6 for lola_dense)")
+    ap.add_argument("--workload", choices=["mnist", "lola_dense"], default="mnist",
+                    help="mnist: convolution-representation input (Sec. 4.3); lola_dense: dense input "
+                         "masked on the server (App. C)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=1)
     ap.add_argument("--mode", choices=["network", "serve", "primitives"], default="network")
     ap.add_argument("--n", type=int, default=16384, help="primitives mode: ring degree")
     ap.add_argument("--rates", default="25,100,200", help="serve mode: Poisson arrival rates (requests/s)")
     ap.add_argument("--duration", type=float, default=10.0, help="serve mode: seconds of arrivals per rate")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.L is None:
+        args.L = 6 if args.workload == "lola_dense" else 5
+    return args
+
+
+# per-residue operation counts of one inference (the plan's, checked by the CPU tests)
+OP_COUNTS = {"mnist": {"rot": 224, "square": 2, "mul_plain": 24, "mul_scalar": 125, "add": 344},
+             "lola_dense": {"rot": 326, "square": 2, "mul_plain": 61, "mul_scalar": 125, "add": 422}}
+WORKLOAD_NAME = {"mnist": "mnist_lola_n16384", "lola_dense": "lola_dense_n16384"}
 
 
 # ------------------------------------------------------------------ clocks
@@ -114,15 +130,15 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ CPU baseline
-def oracle_sample(n_rot=1, n_sq=1):
-    """Time the CPU oracle's operations on the MNIST parameters (one CRT
+def oracle_sample(n_rot=1, n_sq=1, workload="mnist", L=5):
+    """Time the CPU oracle's operations on the network's parameters (one CRT
     residue) and scale by the network's operation counts for one inference
     over all residues.  Returns (seconds per inference, description)."""
     import numpy as np
 
     import workloads as W
     from oracle import bfv, encoding
-    ps = W.params_mnist()
+    ps = W.params_mnist(L)
     P = bfv.Params(ps.n, ps.q, ps.L, ps.K, ps.t)
     keys = bfv.keygen(P, 5, rotations=[1], relin=True)
     t = ps.t[0]
@@ -140,19 +156,20 @@ def oracle_sample(n_rot=1, n_sq=1):
     t_pt = timed(lambda: bfv.mul_plain(P, ct, w), 1)
     t_sc = timed(lambda: bfv.mul_scalar(P, ct, -3), 3)
     t_add = timed(lambda: bfv.add(P, ct, ct), 3)
-    counts = {"rot": 224, "square": 2, "mul_plain": 24, "mul_scalar": 125, "add": 344}
+    counts = OP_COUNTS[workload]
     per_residue = (counts["rot"] * t_rot + counts["square"] * t_sq + counts["mul_plain"] * t_pt
                    + counts["mul_scalar"] * t_sc + counts["add"] * t_add)
     sec = per_residue * len(ps.t)
     desc = (f"oracle per-op times on n=16384, L={ps.L}: rotation {t_rot:.3f}s, square+relin {t_sq:.3f}s, "
             f"ct*pt {t_pt:.3f}s, ct*scalar {t_sc:.4f}s, add {t_add:.4f}s; x op counts of one inference "
-            f"(224 rot, 2 sq, 24 ct*pt, 125 ct*scalar, 344 add) x {len(ps.t)} CRT residues")
+            f"({counts['rot']} rot, {counts['square']} sq, {counts['mul_plain']} ct*pt, {counts['mul_scalar']} ct*scalar, "
+            f"{counts['add']} add) x {len(ps.t)} CRT residues")
     return sec, desc
 
 
-def cpu_baseline_obj():
+def cpu_baseline_obj(workload="mnist", L=5):
     t0 = time.perf_counter()
-    sec, desc = oracle_sample()
+    sec, desc = oracle_sample(workload=workload, L=L)
     return {"value": 1.0 / sec, "unit": "inferences/s", "cores": 1, "kind": "oracle",
             "sample": desc, "sample_wall_s": round(time.perf_counter() - t0, 1)}
 
@@ -163,11 +180,11 @@ def run_reference(args):
     if rank != 0:
         return
     for _ in range(args.warmup):
-        oracle_sample(1, 1)
+        oracle_sample(1, 1, args.workload, args.L)
     secs = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        s, desc = oracle_sample(1, 1)
+        s, desc = oracle_sample(1, 1, args.workload, args.L)
         secs.append(s)
     wall = time.perf_counter() - t0
     sec = statistics.median(secs)
@@ -175,7 +192,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "inferences/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1000,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": "mnist_lola_n16384", "n": 16384, "L": args.L, "K": 1, "k_t": 3,
+            "config": {"workload": WORKLOAD_NAME[args.workload], "n": 16384, "L": args.L, "K": 1, "k_t": 3,
                        "parallelism": "none (CPU oracle)"},
             "cpu_baseline": {"value": value, "unit": "inferences/s", "cores": 1, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": "inferences/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -290,19 +307,31 @@ def run_ours(args):
     ps = W.params_mnist(args.L)
     n, kt, Lq = ps.n, len(ps.t), ps.L
     mnet = W.mnist_net()
-    layers = W.layers_mnist(mnet, n)
     ctx = L.lola_ctx_create(ps.n, ps.q, ps.L, ps.K, ps.t, device=local)
     B = args.batch
-    net = L.lola_net_create(ctx, {"repr": "convolution", "n_msgs": 25, "n_elems": 169}, layers)
+    if args.workload == "lola_dense":
+        layers = W.layers_lola_dense(mnet, n)
+        img_slots = np.asarray(W.dense_image_slots(), dtype=np.int64)
+        net = L.lola_net_create(ctx, {"repr": "dense", "n_msgs": 1, "n_elems": 784, "slot": img_slots}, layers)
+    else:
+        layers = W.layers_mnist(mnet, n)
+        net = L.lola_net_create(ctx, {"repr": "convolution", "n_msgs": 25, "n_elems": 169}, layers)
+    n_in = net.shape()[0]
     steps_needed = net.rotation_steps()
     sk, ev = L.lola_keygen(ctx, W.DEFAULT_SEED, [s for s in steps_needed if s],
                            L.LOLA_KEY_RELIN | L.LOLA_KEY_ROW_SWAP)
     imgs = [W.image(idx=rank * 100000 + i) for i in range(B)]
-    packed = np.concatenate([L.lola_pack_convolution(im, 5, 5, 2, n)[0] for im in imgs])
+    if args.workload == "lola_dense":
+        # one dense message per image, line after line (29-slot lines)
+        packed = np.zeros((B, n), np.int64)
+        for i, im in enumerate(imgs):
+            packed[i, img_slots] = np.asarray(im, dtype=np.int64).reshape(-1)
+    else:
+        packed = np.concatenate([L.lola_pack_convolution(im, 5, 5, 2, n)[0] for im in imgs])
     ct_in = L.lola_encrypt(ctx, sk, packed, 1000 + rank)
     ct_out = L.lola_ct_create(ctx, B * 10)
     ct_words = 2 * Lq * n
-    in_bytes = B * 25 * kt * ct_words * 8
+    in_bytes = B * n_in * kt * ct_words * 8
     out_bytes = B * 10 * kt * ct_words * 8
 
     def barrier():
@@ -316,20 +345,27 @@ def run_ours(args):
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
-    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    # inputs below twice the L2 (129 MB): flush it between timed steps by
+    # writing a 256 MB buffer outside each step's event pair
+    L2_BYTES = 129 * 2**20
+    flush = torch.empty(256 * 2**20, dtype=torch.uint8, device=dev) if in_bytes < 2 * L2_BYTES else None
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     clocks = ClockSampler(local)
     clocks.start()
     barrier()
     torch.cuda.synchronize()
-    evs[0].record(stream)
     for i in range(args.steps):
+        if flush is not None:
+            flush.fill_(i & 0xFF)
+        ev0[i].record(stream)
         step()
-        evs[i + 1].record(stream)
+        ev1[i].record(stream)
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
-    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
-    total_ms = evs[0].elapsed_time(evs[-1])
+    step_ms = [ev0[i].elapsed_time(ev1[i]) for i in range(args.steps)]
+    total_ms = sum(step_ms)
     total_ms_max, units = aggregate(total_ms, B * args.steps, dist, dev)
     value = units / (total_ms_max / 1000.0)
 
@@ -358,7 +394,7 @@ def run_ours(args):
     e2e_value = e2e_units / (e2e_ms_max / 1000.0)
 
     # ---- plain: one request at a time, eager, no graph
-    ct1_in = L.lola_encrypt(ctx, sk, packed[:25], 7)
+    ct1_in = L.lola_encrypt(ctx, sk, packed[:n_in], 7)
     ct1_out = L.lola_ct_create(ctx, 10)
     L.lola_eval_network(ctx, ev, net, ct1_in, ct1_out, stream, graph=False)
     torch.cuda.synchronize()
@@ -424,7 +460,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline_obj()
+        cpu = cpu_baseline_obj(args.workload, args.L)
 
     if rank == 0:
         srt = sorted(step_ms)
@@ -432,9 +468,11 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "inferences/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": "mnist_lola_n16384", "batch_per_gpu": B, "n": n, "L": Lq, "K": 1, "k_t": kt,
+            "config": {"workload": WORKLOAD_NAME[args.workload], "batch_per_gpu": B, "n": n, "L": Lq, "K": 1, "k_t": kt,
                        "aux_primes": len(L.lola_ctx_aux_primes(ctx)), "parallelism": f"replicas x{world}",
-                       "l2": f"inputs larger than L2 ({in_bytes / 1e6:.0f} MB of input ciphertexts per step)"},
+                       "l2": (f"L2 flushed between timed steps (256 MB write; {in_bytes / 1e6:.0f} MB of input "
+                              "ciphertexts per step)") if flush is not None else
+                             f"inputs larger than L2 ({in_bytes / 1e6:.0f} MB of input ciphertexts per step)"},
             "latency_ms": {"batched_p50": statistics.median(step_ms), "batched_p99": srt[min(len(srt) - 1, int(0.99 * len(srt)))],
                            "plain_p50": statistics.median(plain_ms),
                            "plain_p99": sorted(plain_ms)[min(len(plain_ms) - 1, int(0.99 * len(plain_ms)))]},

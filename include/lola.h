@@ -197,13 +197,18 @@ typedef enum {
  * combine).  Weights are host int64, row-major rows x cols, copied. */
 typedef enum {
   LOLA_LAYER_CONV_ROWMAJOR = 1,        /* convolution -> dense messages (one per row of W) */
-  LOLA_LAYER_COMBINE = 2,              /* k dense messages -> 1: message m rotated by m*stride */
+  LOLA_LAYER_COMBINE = 2,              /* k dense messages -> 1: message m rotated by m*stride, or by
+                                          weights[m] (1 x k, weights[0] = 0) when weights is given */
   LOLA_LAYER_SQUARE = 3,               /* elementwise square (ct (x) ct) */
   LOLA_LAYER_STACK = 4,                /* dense -> stacked: copies every 2^d slots */
   LOLA_LAYER_STACKED_ROWMAJOR = 5,     /* stacked -> interleaved (mask + combine rounds) */
   LOLA_LAYER_INTERLEAVED_ROWMAJOR = 6, /* interleaved/dense -> sparse (one message per row) */
   LOLA_LAYER_DENSE_ROWMAJOR = 7,       /* dense -> sparse */
-  LOLA_LAYER_SPARSE_COLMAJOR = 8       /* sparse (one message per element) -> dense: sum_i v_i * column_i */
+  LOLA_LAYER_SPARSE_COLMAJOR = 8,      /* sparse (one message per element) -> dense: sum_i v_i * column_i */
+  LOLA_LAYER_MASKED_SHIFTS = 9         /* dense -> convolution by masking (App. C, LoLa-Dense): weights
+                                          rows x cols = messages x elements, entry = input element index
+                                          held by message r at element e (-1 = zero); message r must be a
+                                          single shift off_r of message 0 (x * mask_r, rotated left by off_r) */
 } lola_layer_op;
 
 typedef struct {
@@ -211,7 +216,7 @@ typedef struct {
   lola_repr in_repr;      /* checked against the running representation */
   lola_repr out_repr;     /* checked against what the layer produces */
   uint32_t rows, cols;    /* weight shape (CONV: maps x window size) */
-  const int64_t* weights; /* host, rows * cols, NULL for COMBINE/SQUARE/STACK */
+  const int64_t* weights; /* host, rows * cols; NULL for SQUARE/STACK, optional for COMBINE */
   uint32_t d;             /* STACK / STACKED_ROWMAJOR: block size 2^d */
   uint32_t copies;        /* STACK / STACKED_ROWMAJOR: number of copies (power of two) */
   uint32_t stride;        /* COMBINE: slot offset between consecutive messages */

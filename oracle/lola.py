@@ -114,7 +114,8 @@ def rotate_and_sum(ev, x, shifts):
 def layer_conv(ev, st: State, W) -> State:
     """Convolution vector - row major (Sec. 4.2.2): map m = sum_j W[m][j] * M^j,
     scalar weights (sparse representation of w).  Output: one dense message
-    per map; element (m, w) sits at slot w of message m."""
+    per map; element (m, w) sits at message m, in the slot window w has in
+    the input messages."""
     R = len(st.msgs)
     out = []
     for m in range(len(W)):
@@ -122,23 +123,73 @@ def layer_conv(ev, st: State, W) -> State:
         for j in range(1, R):
             acc = ev.add(acc, ev.mul_scalar(st.msgs[j], W[m][j]))
         out.append(acc)
-    width = len(st.pos)
-    pos = [(m, w) for m in range(len(W)) for w in range(width)]
+    pos = [(m, slot) for m in range(len(W)) for (_, slot) in st.pos]
     return State(out, pos)
 
 
-def layer_combine(ev, st: State, stride: int) -> State:
+def layer_combine(ev, st: State, stride: int = 0, shifts=None) -> State:
     """Combine k messages into one (Sec. 4.3, App. C): message m is rotated
-    right by m * stride so active slots do not collide, then all are added."""
+    right by shifts[m] (default m * stride; shifts[0] = 0) so active slots do
+    not collide, then all are added."""
     h = ev.n // 2
+    k = len(st.msgs)
+    if shifts is None:
+        shifts = [m * stride for m in range(k)]
+    assert len(shifts) == k and shifts[0] == 0 and all(0 < s < h for s in shifts[1:])
     acc = st.msgs[0]
-    for m in range(1, len(st.msgs)):
-        acc = ev.add(acc, ev.rot(st.msgs[m], m * stride))
+    for m in range(1, k):
+        acc = ev.add(acc, ev.rot(st.msgs[m], shifts[m]))
     pos = []
     for (m, slot) in st.pos:
-        assert slot + m * stride < h, "combine must not wrap a row"
-        pos.append((0, slot + m * stride))
+        assert slot + shifts[m] < h, "combine must not wrap a row"
+        pos.append((0, slot + shifts[m]))
+    assert len(set(pos)) == len(pos), "combine positions collide"
     return State([acc], pos)
+
+
+def masked_shift_plan(st: State, G, n: int):
+    """Slots S_e of the output elements and the offset of each message for
+    layer_masked_shifts; checks that every message is one shift of message 0."""
+    h = n // 2
+    slot_of = [slot for (_, slot) in st.pos]
+    assert all(m == 0 for (m, _) in st.pos)
+    R, E = len(G), len(G[0])
+    assert all(int(G[0][e]) >= 0 for e in range(E)), "message 0 must hold every element"
+    S = [slot_of[int(G[0][e])] for e in range(E)]
+    offs = []
+    for r in range(R):
+        d = {slot_of[int(G[r][e])] - S[e] for e in range(E) if int(G[r][e]) >= 0}
+        assert len(d) == 1, "message %d is not a single shift of message 0" % r
+        off = d.pop()
+        assert 0 <= off < h and (r == 0) == (off == 0)
+        assert all(S[e] + off < h for e in range(E))
+        offs.append(off)
+    assert len(set(offs)) == R
+    return S, offs
+
+
+def layer_masked_shifts(ev, st: State, G) -> State:
+    """Dense -> convolution representation by masking (App. C, LoLa-Dense;
+    Table 3: mask the input to create 25 messages).  G[r][e] is the input
+    element that message r holds at element e (-1: zero padding).  Reading:
+    message 0 keeps element G[0][e] at its input slot S_e; message r is the
+    input times the 0/1 mask of the slots S_e + off_r of its elements, then
+    rotated left by off_r (right by n/2 - off_r) so its elements line up
+    with S_e (the masks are shifts of each other)."""
+    n, h = ev.n, ev.n // 2
+    S, offs = masked_shift_plan(st, G, n)
+    x = st.msgs[0]
+    out = []
+    for r, off in enumerate(offs):
+        mask = [0] * n
+        for e in range(len(S)):
+            if int(G[r][e]) >= 0:
+                mask[S[e] + off] = 1
+        y = ev.mul_plain(x, mask)
+        if off:
+            y = ev.rot(y, h - off)
+        out.append(y)
+    return State(out, [(0, s) for s in S])
 
 
 def layer_square(ev, st: State) -> State:
@@ -259,8 +310,10 @@ def run_network(ev, layers, st: State) -> State:
         op = L["op"]
         if op == "conv":
             st = layer_conv(ev, st, L["weights"])
+        elif op == "masked_shifts":
+            st = layer_masked_shifts(ev, st, L["weights"])
         elif op == "combine":
-            st = layer_combine(ev, st, L["stride"])
+            st = layer_combine(ev, st, L.get("stride", 0), L.get("shifts"))
         elif op == "square":
             st = layer_square(ev, st)
         elif op == "stack":
@@ -311,6 +364,22 @@ def pack_dense(vec, n: int):
     for i, x in enumerate(vec):
         v[i] = int(x)
     return v, [(0, i) for i in range(len(vec))]
+
+
+def pack_image_rows(img, width: int, n: int):
+    """Dense message of an image, line after line (App. C): pixel (r, c) at
+    slot r * width + c; width > the image width leaves zero columns (the
+    convolution's right padding)."""
+    img = np.asarray(img)
+    h, w = img.shape
+    assert width >= w and h * width <= n // 2
+    v = [0] * n
+    pos = []
+    for r in range(h):
+        for c in range(w):
+            v[r * width + c] = int(img[r, c])
+            pos.append((0, r * width + c))
+    return v, pos
 
 
 def pack_stacked(vec, d: int, copies: int, n: int):

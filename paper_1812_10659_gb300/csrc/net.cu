@@ -113,15 +113,105 @@ static int layer_conv(Builder& b, const lola_layer& L, Repr& r) {
   return LOLA_OK;
 }
 
+// Dense -> convolution representation by masking (App. C, LoLa-Dense):
+// weights[r][e] = input element that message r holds at element e (-1 =
+// zero padding).  Message 0 keeps its elements at their input slots S_e;
+// message r must be one shift off_r of message 0.  All R products
+// x * mask_r run as one ct x plaintext launch (mask_r: ones at S_e + off_r),
+// then messages 1..R-1 are rotated left by off_r in one rotation wave.
+static int layer_masked_shifts(Builder& b, const lola_layer& L, Repr& r) {
+  const uint32_t n = b.c->n, h = n / 2;
+  if (r.kind != LOLA_REPR_DENSE || r.msgs != 1) return fail(LOLA_E_REPR, "masked shifts need one dense message");
+  for (auto& p : r.pos)
+    if (p.first != 0) return fail(LOLA_E_REPR, "masked shifts need one dense message");
+  const uint32_t R = L.rows, E = L.cols;
+  if (!L.weights || R == 0 || E == 0) return fail(LOLA_E_PARAM, "masked shifts need a messages x elements gather");
+  auto G = [&](uint32_t m, uint32_t e) { return L.weights[(size_t)m * E + e]; };
+  std::vector<uint32_t> S(E);
+  for (uint32_t e = 0; e < E; ++e) {
+    const int64_t g = G(0, e);
+    if (g < 0 || (uint64_t)g >= r.pos.size()) return fail(LOLA_E_PARAM, "message 0 must hold every element");
+    S[e] = r.pos[(size_t)g].second;
+    if (S[e] >= h) return fail(LOLA_E_PARAM, "masked shifts: elements must sit in slot row 0");
+  }
+  std::vector<uint32_t> off(R, 0);
+  std::set<uint32_t> seen;
+  for (uint32_t m = 0; m < R; ++m) {
+    bool have = false;
+    int64_t o = 0;
+    for (uint32_t e = 0; e < E; ++e) {
+      const int64_t g = G(m, e);
+      if (g < 0) continue;
+      if ((uint64_t)g >= r.pos.size()) return fail(LOLA_E_PARAM, "gather index out of range");
+      const int64_t d = (int64_t)r.pos[(size_t)g].second - (int64_t)S[e];
+      if (have && d != o) return fail(LOLA_E_PARAM, "message is not one shift of message 0");
+      o = d;
+      have = true;
+    }
+    if (!have || o < 0 || o >= (int64_t)h || ((m == 0) != (o == 0)))
+      return fail(LOLA_E_PARAM, "masked shifts: offsets must be 0 for message 0, else in (0, n/2)");
+    off[m] = (uint32_t)o;
+    if (!seen.insert(off[m]).second) return fail(LOLA_E_PARAM, "masked shifts: offsets must be distinct");
+    for (uint32_t e = 0; e < E; ++e)
+      if (S[e] + off[m] >= h) return fail(LOLA_E_PARAM, "masked shifts would wrap a slot row");
+  }
+  std::vector<std::vector<int64_t>> M(R, std::vector<int64_t>(n, 0));
+  for (uint32_t m = 0; m < R; ++m)
+    for (uint32_t e = 0; e < E; ++e)
+      if (G(m, e) >= 0) M[m][S[e] + off[m]] = 1;
+  const int outr = b.vreg(R);
+  const size_t pt0 = b.add_plaintexts(M);
+  Op m0;                                    // message 0: x * mask_0, straight into the output
+  m0.kind = OP_MULPT;
+  m0.src = r.reg;
+  m0.src_stride = 0;
+  m0.dst = outr;
+  m0.msgs = 1;
+  m0.pt_first = pt0;
+  b.net->ops.push_back(m0);
+  if (R > 1) {
+    Op mr;                                  // messages 1..R-1: x * mask_r
+    mr.kind = OP_MULPT;
+    mr.src = r.reg;
+    mr.src_stride = 0;
+    mr.dst = b.vreg(R - 1);
+    mr.msgs = R - 1;
+    mr.pt_first = pt0 + 1;
+    b.net->ops.push_back(mr);
+    std::vector<int32_t> st;
+    for (uint32_t m = 1; m < R; ++m) st.push_back((int32_t)(h - off[m]));   // left by off = right by h - off
+    b.rot(outr, mr.dst, -1, R - 1, st);
+    b.net->ops.back().dst_off = 1;
+  }
+  Repr out;
+  out.kind = LOLA_REPR_CONVOLUTION;
+  out.reg = outr;
+  out.msgs = R;
+  for (uint32_t e = 0; e < E; ++e) out.pos.push_back({0, S[e]});
+  r = out;
+  return LOLA_OK;
+}
+
 static int layer_combine(Builder& b, const lola_layer& L, Repr& r) {
   const uint32_t h = b.c->n / 2;
   if (r.kind != LOLA_REPR_DENSE && r.kind != LOLA_REPR_INTERLEAVED)
     return fail(LOLA_E_REPR, "combine needs dense messages");
+  // shifts: weights (1 x messages, shift[0] = 0) or m * stride
+  std::vector<uint64_t> shift(r.msgs);
+  if (L.weights) {
+    if (L.rows != 1 || L.cols != r.msgs || L.weights[0] != 0) return fail(LOLA_E_PARAM, "combine shifts: 1 x messages, first 0");
+    for (uint32_t m = 1; m < r.msgs; ++m) {
+      if (L.weights[m] <= 0 || L.weights[m] >= (int64_t)h) return fail(LOLA_E_PARAM, "combine shifts must be in (0, n/2)");
+      shift[m] = (uint64_t)L.weights[m];
+    }
+  } else {
+    for (uint32_t m = 0; m < r.msgs; ++m) shift[m] = (uint64_t)m * L.stride;
+  }
   Repr out = r;
   out.msgs = 1;
   std::set<uint32_t> used;
   for (auto& p : out.pos) {
-    const uint64_t slot = (uint64_t)p.second + (uint64_t)p.first * L.stride;
+    const uint64_t slot = (uint64_t)p.second + shift[p.first];
     if (p.second >= h || slot >= h) return fail(LOLA_E_PARAM, "combine would wrap a slot row");
     if (!used.insert((uint32_t)slot).second) return fail(LOLA_E_PARAM, "combine positions collide");
     p = {0, (uint32_t)slot};
@@ -130,7 +220,7 @@ static int layer_combine(Builder& b, const lola_layer& L, Repr& r) {
     const uint32_t k = r.msgs - 1;
     const int tmp = b.vreg(k);
     std::vector<int32_t> st;
-    for (uint32_t m = 1; m <= k; ++m) st.push_back((int32_t)(m * L.stride));
+    for (uint32_t m = 1; m <= k; ++m) st.push_back((int32_t)shift[m]);
     Op ro;
     b.rot(tmp, r.reg, -1, k, st);
     b.net->ops.back().src_off = 1;
@@ -353,6 +443,7 @@ int net_create(Ctx* c, const lola_input* in, const lola_layer* layers, size_t n_
     switch (L.op) {
       case LOLA_LAYER_CONV_ROWMAJOR: rc = layer_conv(b, L, r); break;
       case LOLA_LAYER_COMBINE: rc = layer_combine(b, L, r); break;
+      case LOLA_LAYER_MASKED_SHIFTS: rc = layer_masked_shifts(b, L, r); break;
       case LOLA_LAYER_SQUARE: rc = layer_square(b, L, r); break;
       case LOLA_LAYER_STACK: rc = layer_stack(b, L, r); break;
       case LOLA_LAYER_STACKED_ROWMAJOR: rc = layer_stacked_rowmajor(b, L, r); break;

@@ -23,11 +23,11 @@ LOLA_KEY_ROW_SWAP = 2
 
 REPR = {"dense": 1, "sparse": 2, "stacked": 3, "interleaved": 4, "convolution": 5}
 LAYER = {"conv": 1, "combine": 2, "square": 3, "stack": 4, "stacked_rowmajor": 5,
-         "interleaved_rowmajor": 6, "dense_rowmajor": 7, "sparse_colmajor": 8}
+         "interleaved_rowmajor": 6, "dense_rowmajor": 7, "sparse_colmajor": 8, "masked_shifts": 9}
 # representation each layer consumes / produces (0 = not checked)
 LAYER_REPR = {"conv": (5, 1), "combine": (1, 1), "square": (0, 0), "stack": (1, 3),
               "stacked_rowmajor": (3, 4), "interleaved_rowmajor": (4, 2), "dense_rowmajor": (1, 2),
-              "sparse_colmajor": (2, 1)}
+              "sparse_colmajor": (2, 1), "masked_shifts": (1, 5)}
 
 
 class LolaError(RuntimeError):
@@ -378,6 +378,8 @@ def lola_net_create(ctx, input_desc: dict, layers: list) -> Network:
     for i, Ld in enumerate(layers):
         op = Ld["op"]
         w = Ld.get("weights")
+        if op == "combine" and Ld.get("shifts") is not None:
+            w = [list(Ld["shifts"])]
         rows = cols = 0
         wp = None
         if w is not None:

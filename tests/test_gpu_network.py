@@ -229,3 +229,90 @@ def test_dense_rowmajor_sparse_colmajor_bit_exact_vs_oracle():
         net.destroy()
     finally:
         Lb.lola_ctx_destroy(ctx)
+
+
+def lola_dense_input(net, width):
+    return {"repr": "dense", "n_msgs": 1, "n_elems": net.h * net.w,
+            "slot": W.dense_image_slots(net.h, net.w, width)}
+
+
+def test_mini_lola_dense_bit_exact_vs_oracle():
+    """LoLa-Dense (App. C) on a reduced network: the dense image message is
+    masked into the convolution representation on the server; every output
+    ciphertext bit-exact against the oracle with the same keys and input."""
+    need_gpu()
+    Lb = lib()
+    n = 1024
+    ps = W.params_small(n, L=5, K=1, t=W.T30[:1])
+    P = oracle_params(ps)
+    t = ps.t[0]
+    mnet = W.mnist_net(seed=7, maps=2, hidden=12, classes=3, h=12, w=12, k=3, stride=2)
+    img = W.image(seed=7, h=12, w=12)
+    width = 13
+    layers = W.layers_lola_dense(mnet, n, width)
+    ctx = make_ctx(ps)
+    try:
+        net = Lb.lola_net_create(ctx, lola_dense_input(mnet, width), layers)
+        sk, ev = gpu_keys(Lb, ctx, net, 13)
+        v, _ = OL.pack_image_rows(img, width, n)
+        ct = Lb.lola_encrypt(ctx, sk, np.array([v], np.int64), 6)
+        out = Lb.lola_ct_create(ctx, 3)
+        Lb.lola_eval_network(ctx, ev, net, ct, out)
+        got = Lb.lola_ct_export(ctx, out, (1, 2, P.L, n))[:, 0]
+        ok = oracle_keys(P, net, 13)
+        oct_ = bfv.encrypt(P, ok.pk, encoding.encode(v, t), t, 6, 0)
+        st = OL.run_network(OL.HEEval(P, ok, t), layers, OL.State([oct_], OL.pack_image_rows(img, width, n)[1]))
+        for o in range(3):
+            assert np.array_equal(got[o, 0], st.msgs[o].c[0]) and np.array_equal(got[o, 1], st.msgs[o].c[1]), o
+        res = Lb.lola_decrypt_residues(ctx, sk, out, 1, n)
+        assert [int(res[m, 0, s]) for m, s in net.output_map()] == [x % t for x in mnist_int(mnet, img)]
+        for h in (ct, out):
+            Lb.lola_ct_destroy(h)
+        Lb.lola_keys_destroy(sk)
+        Lb.lola_keys_destroy(ev)
+        net.destroy()
+    finally:
+        Lb.lola_ctx_destroy(ctx)
+
+
+def test_full_lola_dense_batched_decrypts_to_integer_network():
+    need_gpu()
+    Lb = lib()
+    ps = W.params_mnist(6)
+    n = ps.n
+    mnet = W.mnist_net()
+    layers = W.layers_lola_dense(mnet, n)
+    ctx = make_ctx(ps)
+    try:
+        B = 2
+        imgs = [W.image(idx=10 + i) for i in range(B)]
+        net = Lb.lola_net_create(ctx, lola_dense_input(mnet, W.DENSE_IMAGE_WIDTH), layers)
+        sk, ev = gpu_keys(Lb, ctx, net, W.DEFAULT_SEED)
+        slots = np.array([OL.pack_image_rows(im, W.DENSE_IMAGE_WIDTH, n)[0] for im in imgs], np.int64)
+        ct = Lb.lola_encrypt(ctx, sk, slots, 31)
+        out = Lb.lola_ct_create(ctx, B * 10)
+        Lb.lola_eval_network(ctx, ev, net, ct, out)
+        dec = Lb.lola_decrypt(ctx, sk, out, n)
+        for r in range(B):
+            assert [int(dec[r * 10 + m, s]) for m, s in net.output_map()] == mnist_int(mnet, imgs[r]), r
+        for h in (ct, out):
+            Lb.lola_ct_destroy(h)
+        Lb.lola_keys_destroy(sk)
+        Lb.lola_keys_destroy(ev)
+        net.destroy()
+    finally:
+        Lb.lola_ctx_destroy(ctx)
+
+
+def test_masked_shifts_rejects_a_non_shift_gather():
+    need_gpu()
+    Lb = lib()
+    ps = W.params_small(256, L=3)
+    ctx = make_ctx(ps)
+    try:
+        with pytest.raises(Lb.LolaError) as ei:
+            Lb.lola_net_create(ctx, {"repr": "dense", "n_msgs": 1, "n_elems": 8},
+                               [{"op": "masked_shifts", "weights": np.array([[0, 1], [2, 4]])}])
+        assert ei.value.code == -1
+    finally:
+        Lb.lola_ctx_destroy(ctx)

@@ -243,3 +243,99 @@ def test_dense_rowmajor_then_sparse_colmajor_chain():
     assert [v2 - t if v2 > t // 2 else v2 for v2 in got] == want
     # M1: log2(n) rotations per output (7 within a row of 128, then the row swap); M2: none
     assert ev.c["rot"] == 6 * 8 and ev.c["mul_plain"] == 6 + 6
+
+
+# ------------------------------------------------------------- LoLa-Dense (App. C)
+
+def lola_dense_slot_run(n, t, net, img, ev_cls=lola.SlotEval, width=W.DENSE_IMAGE_WIDTH):
+    ev = ev_cls(n, t)
+    v, pos = lola.pack_image_rows(img, width, n)
+    st = lola.State([np.array(v, dtype=np.int64) % t], pos)
+    return ev, lola.run_network(ev, W.layers_lola_dense(net, n, width), st)
+
+
+def test_masked_shifts_equal_convolution_representation():
+    # App. C: masking the dense image gives the convolution representation;
+    # message r = dr*kw + dc holds pixel (2i+dr, 2j+dc) of window (i, j),
+    # zero in the padding, brute-forced from the image itself.
+    n, t = 4096, 65537
+    net = W.mnist_net()
+    img = W.image(idx=4)
+    v, pos = lola.pack_image_rows(img, W.DENSE_IMAGE_WIDTH, n)
+    ev = lola.SlotEval(n, t)
+    st = lola.layer_masked_shifts(ev, lola.State([np.array(v, np.int64)], pos), W.conv_gather(net))
+    assert len(st.msgs) == 25 and len(st.pos) == 169
+    for r in range(25):
+        dr, dc = divmod(r, 5)
+        for e, (_, slot) in enumerate(st.pos):
+            i, j = divmod(e, 13)
+            assert slot == 2 * W.DENSE_IMAGE_WIDTH * i + 2 * j
+            rr, cc = 2 * i + dr, 2 * j + dc
+            want = int(img[rr, cc]) if rr < 28 and cc < 28 else 0
+            assert int(st.msgs[r][slot]) == want, (r, e)
+    # and only those slots of each message are nonzero
+    live = {slot for _, slot in st.pos}
+    for m in st.msgs:
+        assert all(int(x) == 0 for s, x in enumerate(m) if s not in live)
+
+
+def test_masked_shifts_rejects_a_non_shift_gather():
+    n = 256
+    st = lola.State([np.zeros(n, np.int64)], [(0, s) for s in range(8)])
+    with pytest.raises(AssertionError):
+        lola.layer_masked_shifts(lola.SlotEval(n, 17), st, [[0, 1], [2, 4]])
+
+
+def test_lola_dense_plan_matches_integer_network_with_crt():
+    n = 16384
+    net = W.mnist_net()
+    img = W.image(idx=1)
+    want = mnist_int(net, img)
+    layers = W.layers_lola_dense(net, n)
+    # 845 values combined by shifts [0, 1, 26, 27, 748] span 1469 slots, so
+    # 2048-slot blocks: 8 copies, 13 rounds (the paper's 16 copies need a
+    # span below 1024, which no placement of 5 shifted corner grids reaches)
+    assert layers[2]["shifts"] == [0, 1, 26, 27, 748]
+    assert layers[4]["d"] == 11 and layers[4]["copies"] == 8
+    per_t = []
+    for t in W.T30[:3]:
+        ev, st = lola_dense_slot_run(n, t, net, img, Counting)
+        # 24 alignment + 4 combine + 3 stack + 13*11 + 12 stacked + 10*14 interleaved
+        assert ev.c == {"rot": 24 + 4 + 3 + 13 * 11 + 12 + 140, "mul_plain": 25 + 13 + 13 + 10,
+                        "mul_scalar": 125, "square": 2}
+        per_t.append([int(st.msgs[m][s]) for m, s in st.pos])
+    assert [crt([r[o] for r in per_t], W.T30[:3]) for o in range(10)] == want
+
+
+def mini_lola_dense_layers(n):
+    net, img = mini_mnist()
+    width = 13                                   # 12 pixels per line + 1 padding column
+    return net, img, width, W.layers_lola_dense(net, n, width)
+
+
+def test_mini_lola_dense_encrypted_oracle_run():
+    n = 1024
+    ps = W.params_small(n, L=5, K=1, t=W.T30[:1])
+    P = bfv.Params(ps.n, ps.q, ps.L, ps.K, ps.t)
+    net, img, width, layers = mini_lola_dense_layers(n)
+    t = ps.t[0]
+
+    class Rec(lola.SlotEval):
+        def __init__(self, n, t):
+            super().__init__(n, t)
+            self.steps = set()
+
+        def rot(self, a, k):
+            self.steps.add(k)
+            return super().rot(a, k)
+
+    v, pos = lola.pack_image_rows(img, width, n)
+    rec = Rec(n, t)
+    sim = lola.run_network(rec, layers, lola.State([np.array(v, np.int64) % t], pos))
+    keys = bfv.keygen(P, 13, rotations=sorted(rec.steps), relin=True, row_swap=True)
+    ct = bfv.encrypt(P, keys.pk, encoding.encode(v, t), t, 6, 0)
+    ev = lola.HEEval(P, keys, t)
+    st = lola.run_network(ev, layers, lola.State([ct], pos))
+    got = [int(encoding.decode(bfv.decrypt(P, keys.sk, st.msgs[m]), t)[s]) for m, s in st.pos]
+    assert got == [int(sim.msgs[m][s]) for m, s in sim.pos] == [x % t for x in mnist_int(net, img)]
+    assert min(bfv.noise_margin_bits(P, keys.sk, c, encoding.encode(s, t)) for c, s in zip(st.msgs, sim.msgs)) > 4

@@ -173,6 +173,69 @@ def layers_mnist(net: MnistNet, n: int) -> list:
     ]
 
 
+DENSE_IMAGE_WIDTH = 29   # line length of the dense image message: 28 pixels + 1 padding column
+
+
+def dense_image_slots(h: int = 28, w: int = 28, width: int = DENSE_IMAGE_WIDTH) -> list:
+    """Slots of the pixels of a dense image message, line after line (App. C)."""
+    return [r * width + c for r in range(h) for c in range(w)]
+
+
+def conv_gather(net: MnistNet) -> np.ndarray:
+    """[kh*kw][windows] pixel index (row-major) that window offset r = dr*kw
+    + dc reads at window (i, j); -1 in the zero padding."""
+    oh = -(-(net.h - net.kh) // net.stride) + 1
+    ow = -(-(net.w - net.kw) // net.stride) + 1
+    G = np.full((net.kh * net.kw, oh * ow), -1, dtype=np.int64)
+    for dr in range(net.kh):
+        for dc in range(net.kw):
+            for i in range(oh):
+                for j in range(ow):
+                    r, c = net.stride * i + dr, net.stride * j + dc
+                    if r < net.h and c < net.w:
+                        G[dr * net.kw + dc, i * ow + j] = r * net.w + c
+    return G
+
+
+def combine_shifts(slots, k: int) -> list:
+    """Smallest right shifts, message by message, that place k copies of the
+    slot pattern `slots` without collisions (shift 0 for message 0)."""
+    base = sorted(slots)
+    placed, shifts = set(base), [0]
+    for _ in range(1, k):
+        s = 1
+        while any(p + s in placed for p in base):
+            s += 1
+        shifts.append(s)
+        placed |= {p + s for p in base}
+    return shifts
+
+
+def layers_lola_dense(net: MnistNet, n: int, width: int = DENSE_IMAGE_WIDTH) -> list:
+    """LoLa-Dense (App. C, Table 3): one dense image message masked into the
+    convolution representation (window (i, j) at the slot of its upper-left
+    pixel), convolution row-major, maps combined by collision-free shifts,
+    square, stack, stacked row-major, square, interleaved row-major."""
+    G = conv_gather(net)
+    slots = dense_image_slots(net.h, net.w, width)
+    corner = [slots[int(g)] for g in G[0]]
+    maps, hidden = net.conv_w.shape[0], net.dense1_w.shape[0]
+    shifts = combine_shifts(corner, maps)
+    span = max(corner) + shifts[-1] + 1
+    d = _ceil_log2(span)
+    copies = n >> d
+    return [
+        {"op": "masked_shifts", "weights": G},
+        {"op": "conv", "weights": net.conv_w},
+        {"op": "combine", "shifts": shifts},
+        {"op": "square"},
+        {"op": "stack", "d": d, "copies": copies},
+        {"op": "stacked_rowmajor", "weights": net.dense1_w, "d": d, "copies": copies},
+        {"op": "square"},
+        {"op": "interleaved_rowmajor", "weights": net.dense2_w},
+    ]
+
+
 def layers_head(Wh: np.ndarray, n: int) -> list:
     """Sec. 5 transfer-learning head as stacked row-major: dense input
     stacked n / 2^d times, then rounds of stacked row-major products."""
