@@ -48,13 +48,14 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--batch", type=int, default=16, help="requests per batched step (per GPU)")
+    ap.add_argument("--batch", type=int, default=None,
+                    help="requests per batched step (per GPU; default 16, 2 for cifar)")
     ap.add_argument("--plain", type=int, default=8, help="single-request evaluations for plain latency")
     ap.add_argument("--L", type=int, default=None,
                     help="ciphertext primes (default: 5 for mnist, 6 for lola_dense)")
-    ap.add_argument("--workload", choices=["mnist", "lola_dense"], default="mnist",
+    ap.add_argument("--workload", choices=["mnist", "lola_dense", "cifar"], default="mnist",
                     help="mnist: convolution-representation input (Sec. 4.3); lola_dense: dense input "
-                         "masked on the server (App. C)")
+                         "masked on the server (App. C); cifar: the CIFAR-shaped network (Sec. 6.2)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=1)
     ap.add_argument("--mode", choices=["network", "serve", "primitives"], default="network")
@@ -63,14 +64,17 @@ def parse():
     ap.add_argument("--duration", type=float, default=10.0, help="serve mode: seconds of arrivals per rate")
     args = ap.parse_args()
     if args.L is None:
-        args.L = 6 if args.workload == "lola_dense" else 5
+        args.L = 5 if args.workload == "mnist" else 6
+    if args.batch is None:
+        args.batch = 2 if args.workload == "cifar" else 16
     return args
 
 
 # per-residue operation counts of one inference (the plan's, checked by the CPU tests)
 OP_COUNTS = {"mnist": {"rot": 224, "square": 2, "mul_plain": 24, "mul_scalar": 125, "add": 344},
-             "lola_dense": {"rot": 326, "square": 2, "mul_plain": 61, "mul_scalar": 125, "add": 422}}
-WORKLOAD_NAME = {"mnist": "mnist_lola_n16384", "lola_dense": "lola_dense_n16384"}
+             "lola_dense": {"rot": 326, "square": 2, "mul_plain": 61, "mul_scalar": 125, "add": 422},
+             "cifar": {"rot": 57273, "square": 2, "mul_plain": 8162, "mul_scalar": 15936, "add": 77200}}
+WORKLOAD_NAME = {"mnist": "mnist_lola_n16384", "lola_dense": "lola_dense_n16384", "cifar": "cifar_lola_n16384"}
 
 
 # ------------------------------------------------------------------ clocks
@@ -237,6 +241,21 @@ def plain_mnist(img, mnet):
     return [sum(int(wi) * xi for wi, xi in zip(row, x)) for row in mnet.dense2_w]
 
 
+def plain_cifar(img, cnet):
+    """Expected outputs of the CIFAR-shaped network over Z: convolution of
+    the padded image (windows row-major, weight order channel, row, column),
+    square, the second convolution as its dense matrix, square, dense."""
+    import numpy as np
+
+    import workloads as W
+    x = np.asarray(W.cifar_padded(np.asarray(img), cnet.pad), dtype=np.int64)
+    k, s, o1 = cnet.k1, cnet.stride, cnet.o1
+    win = np.stack([x[:, s * i:s * i + k, s * j:s * j + k].reshape(-1) for i in range(o1) for j in range(o1)])
+    h1 = (np.asarray(cnet.w1, dtype=np.int64) @ win.T).reshape(-1) ** 2
+    h2 = [int(v) ** 2 for v in W.cifar_dense2(cnet) @ h1]
+    return [sum(int(wi) * xi for wi, xi in zip(row, h2)) for row in cnet.w3]
+
+
 def plain_dense(x, W):
     return [sum(int(wi) * int(xi) for wi, xi in zip(row, x)) for row in W]
 
@@ -304,12 +323,17 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
 
-    ps = W.params_mnist(args.L)
+    ps = W.params_cifar(args.L) if args.workload == "cifar" else W.params_mnist(args.L)
     n, kt, Lq = ps.n, len(ps.t), ps.L
     mnet = W.mnist_net()
     ctx = L.lola_ctx_create(ps.n, ps.q, ps.L, ps.K, ps.t, device=local)
     B = args.batch
-    if args.workload == "lola_dense":
+    if args.workload == "cifar":
+        cnet = W.cifar_net()
+        layers = W.layers_cifar(cnet, n)
+        net = L.lola_net_create(ctx, {"repr": "convolution", "n_msgs": 3 * cnet.k1 * cnet.k1,
+                                      "n_elems": cnet.o1 * cnet.o1}, layers)
+    elif args.workload == "lola_dense":
         layers = W.layers_lola_dense(mnet, n)
         img_slots = np.asarray(W.dense_image_slots(), dtype=np.int64)
         net = L.lola_net_create(ctx, {"repr": "dense", "n_msgs": 1, "n_elems": 784, "slot": img_slots}, layers)
@@ -320,8 +344,15 @@ def run_ours(args):
     steps_needed = net.rotation_steps()
     sk, ev = L.lola_keygen(ctx, W.DEFAULT_SEED, [s for s in steps_needed if s],
                            L.LOLA_KEY_RELIN | L.LOLA_KEY_ROW_SWAP)
-    imgs = [W.image(idx=rank * 100000 + i) for i in range(B)]
-    if args.workload == "lola_dense":
+    if args.workload == "cifar":
+        imgs = [W.cifar_image(idx=rank * 100000 + i) for i in range(B)]
+        packed = np.concatenate([L.lola_pack_convolution_channels(W.cifar_padded(im, cnet.pad), cnet.k1, cnet.k1,
+                                                                  cnet.stride, n)[0] for im in imgs])
+    else:
+        imgs = [W.image(idx=rank * 100000 + i) for i in range(B)]
+    if args.workload == "cifar":
+        pass
+    elif args.workload == "lola_dense":
         # one dense message per image, line after line (29-slot lines)
         packed = np.zeros((B, n), np.int64)
         for i, im in enumerate(imgs):
@@ -370,10 +401,17 @@ def run_ours(args):
     value = units / (total_ms_max / 1000.0)
 
     # correctness spot check of this run's output (first request, decrypted)
-    dec = L.lola_decrypt(ctx, sk, ct_out, n)
-    want = plain_mnist(imgs[0], mnet)
-    got = [int(dec[m, s]) for m, s in net.output_map()]
-    correct = got == want
+    if args.workload == "cifar":
+        # outputs may exceed prod(t_i) / 2: compare residue by residue
+        res = L.lola_decrypt_residues(ctx, sk, ct_out, kt, n)
+        want = plain_cifar(imgs[0], cnet)
+        correct = all([int(res[m, ti, s]) for m, s in net.output_map()] == [v % t for v in want]
+                      for ti, t in enumerate(ps.t))
+    else:
+        dec = L.lola_decrypt(ctx, sk, ct_out, n)
+        want = plain_mnist(imgs[0], mnet)
+        got = [int(dec[m, s]) for m, s in net.output_map()]
+        correct = got == want
 
     # ---- e2e through host buffers (pinned)
     h_in = torch.empty(in_bytes // 8, dtype=torch.int64, pin_memory=True)

@@ -205,10 +205,13 @@ typedef enum {
   LOLA_LAYER_INTERLEAVED_ROWMAJOR = 6, /* interleaved/dense -> sparse (one message per row) */
   LOLA_LAYER_DENSE_ROWMAJOR = 7,       /* dense -> sparse */
   LOLA_LAYER_SPARSE_COLMAJOR = 8,      /* sparse (one message per element) -> dense: sum_i v_i * column_i */
-  LOLA_LAYER_MASKED_SHIFTS = 9         /* dense -> convolution by masking (App. C, LoLa-Dense): weights
+  LOLA_LAYER_MASKED_SHIFTS = 9,        /* dense -> convolution by masking (App. C, LoLa-Dense): weights
                                           rows x cols = messages x elements, entry = input element index
                                           held by message r at element e (-1 = zero); message r must be a
                                           single shift off_r of message 0 (x * mask_r, rotated left by off_r) */
+  LOLA_LAYER_PLACE = 10                /* k dense messages -> 1 with element e at slot weights[e] (one target
+                                          per element, both slot rows; Sec. 6.2 combine of 83 maps); the
+                                          messages must hold zeros outside their elements' slots */
 } lola_layer_op;
 
 typedef struct {

@@ -192,6 +192,50 @@ def layer_masked_shifts(ev, st: State, G) -> State:
     return State(out, [(0, s) for s in S])
 
 
+def place_groups(st: State, T, n: int):
+    """For layer_place: per message, its elements grouped by the within-row
+    right shift and the row change that carry them from their slot to T[e]."""
+    h = n // 2
+    assert len(T) == len(st.pos) and len(set(T)) == len(T) and all(0 <= t < n for t in T)
+    groups = {}
+    for e, ((m, s), t) in enumerate(zip(st.pos, T)):
+        k = (t % h - s % h) % h
+        swap = (s // h) != (t // h)
+        groups.setdefault(m, {}).setdefault((swap, k), []).append(e)
+    return groups
+
+
+def layer_place(ev, st: State, T) -> State:
+    """Combine k messages into one with element e at slot T[e], over both
+    slot rows (Sec. 6.2: the 83 convolution maps of the CIFAR-shaped network
+    combined into one message of 16268 values, more than one row holds).
+    Each message's elements are grouped by the right shift within a row and
+    by whether they change row; a message with several groups is multiplied
+    by the 0/1 mask of each group's slots; every group is rotated right by
+    its shift; the groups that change row are summed and row-swapped once.
+    The messages must hold zeros outside their elements' slots."""
+    n = ev.n
+    groups = place_groups(st, T, n)
+    acc = {False: None, True: None}
+    for m in sorted(groups):
+        gs = groups[m]
+        for (swap, k) in sorted(gs):
+            y = st.msgs[m]
+            if len(gs) > 1:
+                mask = [0] * n
+                for e in gs[(swap, k)]:
+                    mask[st.pos[e][1]] = 1
+                y = ev.mul_plain(y, mask)
+            if k:
+                y = ev.rot(y, k)
+            acc[swap] = y if acc[swap] is None else ev.add(acc[swap], y)
+    out = acc[False]
+    if acc[True] is not None:
+        z = ev.rot_rows(acc[True])
+        out = z if out is None else ev.add(out, z)
+    return State([out], [(0, t) for t in T])
+
+
 def layer_square(ev, st: State) -> State:
     return State([ev.square(x) for x in st.msgs], st.pos, st.block, st.copies)
 
@@ -276,10 +320,10 @@ def layer_interleaved_rowmajor(ev, st: State, W) -> State:
     assert len(st.msgs) == 1 and len(W[0]) == len(st.pos)
     shifts = [1 << j for j in range((n // 2).bit_length() - 1)]
     outs = []
+    slots = np.array([slot for (_, slot) in st.pos], dtype=np.int64)
     for o in range(len(W)):
-        V = [0] * n
-        for i, (_, slot) in enumerate(st.pos):
-            V[slot] = int(W[o][i])
+        V = np.zeros(n, dtype=np.int64)
+        V[slots] = np.asarray(W[o], dtype=np.int64)     # column i of W at element i's slot
         y = ev.mul_plain(st.msgs[0], V)
         y = rotate_and_sum(ev, y, shifts)
         y = ev.add(y, ev.rot_rows(y))
@@ -296,10 +340,10 @@ def layer_sparse_colmajor(ev, st: State, W) -> State:
     k, rows = len(st.msgs), len(W)
     assert len(W[0]) == k and rows <= n
     acc = None
+    Wa = np.asarray(W, dtype=np.int64)
     for i in range(k):
-        col = [0] * n
-        for o in range(rows):
-            col[o] = int(W[o][i])
+        col = np.zeros(n, dtype=np.int64)
+        col[:rows] = Wa[:, i]                             # column i, output o at slot o
         y = ev.mul_plain(st.msgs[i], col)
         acc = y if acc is None else ev.add(acc, y)
     return State([acc], [(0, o) for o in range(rows)])
@@ -312,6 +356,8 @@ def run_network(ev, layers, st: State) -> State:
             st = layer_conv(ev, st, L["weights"])
         elif op == "masked_shifts":
             st = layer_masked_shifts(ev, st, L["weights"])
+        elif op == "place":
+            st = layer_place(ev, st, [int(t) for t in np.asarray(L["weights"]).reshape(-1)])
         elif op == "combine":
             st = layer_combine(ev, st, L.get("stride", 0), L.get("shifts"))
         elif op == "square":
@@ -343,19 +389,23 @@ def conv_windows(h: int, w: int, kh: int, kw: int, stride: int):
 def pack_convolution(img, kh: int, kw: int, stride: int, n: int):
     """Convolution representation (Sec. 4.2.1 and its footnote): message
     r = dr*kw + dc (window offset, row-major) holds, at slot i*ow + j, the
-    pixel at (stride*i + dr, stride*j + dc) (zero in the padding)."""
+    pixel at (stride*i + dr, stride*j + dc) (zero in the padding).  A
+    multi-channel image (channels, h, w) gives messages r = ch*kh*kw +
+    dr*kw + dc (Sec. 6.2: 3 x 8 x 8 = 192 messages)."""
     img = np.asarray(img)
-    h, w = img.shape
+    chans = img[None] if img.ndim == 2 else img
+    _, h, w = chans.shape
     oh, ow = conv_windows(h, w, kh, kw, stride)
     msgs = []
-    for dr in range(kh):
-        for dc in range(kw):
-            v = [0] * n
-            for i in range(oh):
-                for j in range(ow):
-                    r, c = stride * i + dr, stride * j + dc
-                    v[i * ow + j] = int(img[r, c]) if (r < h and c < w) else 0
-            msgs.append(v)
+    for ch in range(chans.shape[0]):
+        for dr in range(kh):
+            for dc in range(kw):
+                v = [0] * n
+                for i in range(oh):
+                    for j in range(ow):
+                        r, c = stride * i + dr, stride * j + dc
+                        v[i * ow + j] = int(chans[ch, r, c]) if (r < h and c < w) else 0
+                msgs.append(v)
     return msgs, [(0, i) for i in range(oh * ow)]
 
 
@@ -394,19 +444,24 @@ def pack_stacked(vec, d: int, copies: int, n: int):
 # ------------------------------------------------------- integer network
 
 def int_conv(img, W, kh: int, kw: int, stride: int):
+    """Convolution over Z with bottom/right zero padding; a multi-channel
+    image (channels, h, w) pairs weight index ch*kh*kw + dr*kw + dc with
+    channel ch.  Output map-major, windows row-major."""
     img = np.asarray(img)
-    h, w = img.shape
+    chans = img[None] if img.ndim == 2 else img
+    C, h, w = chans.shape
     oh, ow = conv_windows(h, w, kh, kw, stride)
     out = []
     for m in range(len(W)):
         for i in range(oh):
             for j in range(ow):
                 acc = 0
-                for dr in range(kh):
-                    for dc in range(kw):
-                        r, c = stride * i + dr, stride * j + dc
-                        if r < h and c < w:
-                            acc += int(W[m][dr * kw + dc]) * int(img[r, c])
+                for ch in range(C):
+                    for dr in range(kh):
+                        for dc in range(kw):
+                            r, c = stride * i + dr, stride * j + dc
+                            if r < h and c < w:
+                                acc += int(W[m][(ch * kh + dr) * kw + dc]) * int(chans[ch, r, c])
                 out.append(acc)
     return out
 

@@ -12,6 +12,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
 #include <set>
 
 #include "net.h"
@@ -238,6 +239,137 @@ static int layer_combine(Builder& b, const lola_layer& L, Repr& r) {
   return LOLA_OK;
 }
 
+// Combine k dense messages into one with element e at slot T[e], over both
+// slot rows (Sec. 6.2: 83 maps of 196 values, more than one row holds).
+// Each message's elements are grouped by the in-row right shift and by
+// whether they change row; a message with several groups is masked per
+// group (one ct x plaintext each); shifted groups rotate in waves of
+// consecutive messages; the groups that change row are summed and
+// row-swapped once, fused with the final addition.  Messages must hold
+// zeros outside their elements' slots.
+static int layer_place(Builder& b, const lola_layer& L, Repr& r) {
+  const uint32_t n = b.c->n, h = n / 2;
+  if (r.kind != LOLA_REPR_DENSE && r.kind != LOLA_REPR_INTERLEAVED)
+    return fail(LOLA_E_REPR, "place needs dense messages");
+  const size_t E = r.pos.size();
+  if (!L.weights || (size_t)L.rows * L.cols != E) return fail(LOLA_E_PARAM, "place needs one target slot per element");
+  std::set<uint32_t> used;
+  std::map<uint32_t, std::map<std::pair<int, uint32_t>, std::vector<uint32_t>>> groups;
+  for (size_t e = 0; e < E; ++e) {
+    const int64_t t = L.weights[e];
+    if (t < 0 || t >= (int64_t)n) return fail(LOLA_E_PARAM, "place target out of range");
+    if (!used.insert((uint32_t)t).second) return fail(LOLA_E_PARAM, "place targets collide");
+    const uint32_t m = r.pos[e].first, s = r.pos[e].second;
+    const uint32_t k = ((uint32_t)t % h + h - s % h) % h;
+    const int swap = (s / h) != ((uint32_t)t / h) ? 1 : 0;
+    groups[m][{swap, k}].push_back((uint32_t)e);
+  }
+  struct Term {
+    int reg;
+    uint32_t off;
+    uint32_t k;
+    int swap;
+  };
+  std::vector<Term> terms;
+  for (auto& mg : groups) {
+    const uint32_t m = mg.first;
+    for (auto& g : mg.second) {
+      Term tm{r.reg, m, g.first.second, g.first.first};
+      if (mg.second.size() > 1) {
+        std::vector<std::vector<int64_t>> M(1, std::vector<int64_t>(n, 0));
+        for (uint32_t e : g.second) M[0][r.pos[e].second] = 1;
+        Op mp;
+        mp.kind = OP_MULPT;
+        mp.src = r.reg;
+        mp.src_off = m;
+        mp.src_stride = 1;
+        mp.dst = b.vreg(1);
+        mp.msgs = 1;
+        mp.pt_first = b.add_plaintexts(M);
+        b.net->ops.push_back(mp);
+        tm.reg = mp.dst;
+        tm.off = 0;
+      }
+      terms.push_back(tm);
+    }
+  }
+  // rotation waves over runs of consecutive source messages
+  for (size_t i = 0; i < terms.size();) {
+    if (terms[i].k == 0) {
+      ++i;
+      continue;
+    }
+    size_t j = i + 1;
+    while (j < terms.size() && terms[j].k != 0 && terms[j].reg == terms[i].reg &&
+           terms[j].off == terms[i].off + (uint32_t)(j - i))
+      ++j;
+    const uint32_t cnt = (uint32_t)(j - i);
+    const int dst = b.vreg(cnt);
+    std::vector<int32_t> st;
+    for (size_t x = i; x < j; ++x) st.push_back((int32_t)terms[x].k);
+    b.rot(dst, terms[i].reg, -1, cnt, st);
+    b.net->ops.back().src_off = terms[i].off;
+    for (size_t x = i; x < j; ++x) {
+      terms[x].reg = dst;
+      terms[x].off = (uint32_t)(x - i);
+    }
+    i = j;
+  }
+  // sums per row class, runs of consecutive messages per OP_SUM
+  int acc[2] = {-1, -1};
+  uint32_t acc_off[2] = {0, 0};
+  for (int cls = 0; cls < 2; ++cls) {
+    std::vector<Term> ts;
+    for (auto& tm : terms)
+      if (tm.swap == cls) ts.push_back(tm);
+    for (size_t i = 0; i < ts.size();) {
+      size_t j = i + 1;
+      while (j < ts.size() && ts[j].reg == ts[i].reg && ts[j].off == ts[i].off + (uint32_t)(j - i)) ++j;
+      if (acc[cls] < 0 && j - i == 1) {
+        acc[cls] = ts[i].reg;                 // a lone first term is the accumulator as it is
+        acc_off[cls] = ts[i].off;
+      } else {
+        Op so;
+        so.kind = OP_SUM;
+        so.dst = b.vreg(1);
+        so.src = ts[i].reg;
+        so.src_off = ts[i].off;
+        so.msgs = (uint32_t)(j - i);
+        so.aux = acc[cls];
+        so.aux_off = acc_off[cls];
+        b.net->ops.push_back(so);
+        acc[cls] = so.dst;
+        acc_off[cls] = 0;
+      }
+      i = j;
+    }
+  }
+  Repr out;
+  out.kind = r.kind;
+  out.msgs = 1;
+  if (acc[1] >= 0) {
+    const int dst = b.vreg(1);
+    b.rot(dst, acc[1], acc[0], 1, std::vector<int32_t>(1, 0));
+    b.net->ops.back().src_off = acc_off[1];
+    b.net->ops.back().aux_off = acc_off[0];
+    out.reg = dst;
+  } else if (acc_off[0] != 0) {
+    Op so;                                    // move the lone term into a register of its own
+    so.kind = OP_SUM;
+    so.dst = b.vreg(1);
+    so.src = acc[0];
+    so.src_off = acc_off[0];
+    so.msgs = 1;
+    b.net->ops.push_back(so);
+    out.reg = so.dst;
+  } else {
+    out.reg = acc[0];
+  }
+  for (size_t e = 0; e < E; ++e) out.pos.push_back({0, (uint32_t)L.weights[e]});
+  r = out;
+  return LOLA_OK;
+}
+
 static int layer_square(Builder& b, const lola_layer&, Repr& r) {
   Op o;
   o.kind = OP_SQUARE;
@@ -444,6 +576,7 @@ int net_create(Ctx* c, const lola_input* in, const lola_layer* layers, size_t n_
       case LOLA_LAYER_CONV_ROWMAJOR: rc = layer_conv(b, L, r); break;
       case LOLA_LAYER_COMBINE: rc = layer_combine(b, L, r); break;
       case LOLA_LAYER_MASKED_SHIFTS: rc = layer_masked_shifts(b, L, r); break;
+      case LOLA_LAYER_PLACE: rc = layer_place(b, L, r); break;
       case LOLA_LAYER_SQUARE: rc = layer_square(b, L, r); break;
       case LOLA_LAYER_STACK: rc = layer_stack(b, L, r); break;
       case LOLA_LAYER_STACKED_ROWMAJOR: rc = layer_stacked_rowmajor(b, L, r); break;
@@ -494,6 +627,10 @@ int net_create(Ctx* c, const lola_input* in, const lola_layer* layers, size_t n_
 }
 
 // ------------------------------------------------------------------- executor
+// largest rotation wave (ciphertexts) per launch sequence; at n = 16384, L = 6
+// its key-switch scratch is about 7.5 GB
+static constexpr uint32_t kMaxRotCts = 1024;
+
 struct Executor {
   uint32_t B = 0;
   std::vector<DevBuf> phys;            // physical register buffers
@@ -554,7 +691,12 @@ static int build_executor(Ctx* c, Net* net, uint32_t B, Executor* ex) {
   for (const Op& o : net->ops) {
     const size_t cnt = (size_t)o.msgs * B * kt;
     maxcnt = std::max(maxcnt, cnt);
-    if (o.kind == OP_ROT) sw = std::max(sw, rotate_scratch_words(c, cnt) + 2 * o.msgs);
+    if (o.kind == OP_ROT) {
+      const size_t per_msg = (size_t)B * kt;
+      const size_t chunk_msgs = std::max<size_t>(1, kMaxRotCts / per_msg);
+      const size_t mc = std::min<size_t>(o.msgs, chunk_msgs);
+      sw = std::max(sw, rotate_scratch_words(c, mc * per_msg) + 2 * mc);
+    }
     if (o.kind == OP_SQUARE) sw = std::max(sw, multiply_scratch_words(c, cnt, true));
   }
   TRY(ex->scratch.alloc(sw * 8));
@@ -610,18 +752,26 @@ static int run_ops(Ctx* c, Net* net, Executor* ex, const KeySet* ks, cudaStream_
                           reg(o.dst, o.dst_off), o.msgs, B, s));
         break;
       case OP_ROT: {
-        RotSpec rs;
         const bool uniform = std::all_of(o.steps.begin(), o.steps.end(), [&](int32_t x) { return x == o.steps[0]; });
-        if (uniform) {
-          rs.gal = galois_for_step(c->n, o.steps[0]);
-          rs.key = ks->galois_key(rs.gal)->buf.u64();
-        } else {
-          rs.d_gal = (const uint32_t*)ex->op_gal[i].p;
-          rs.d_keys = (const uint64_t* const*)ex->op_keys[i].p;
-          rs.div = (uint32_t)(B * kt);
+        // waves larger than kMaxRotCts ciphertexts run in chunks of whole
+        // messages, which bounds the key-switch scratch
+        const uint32_t per_msg = (uint32_t)(B * kt);
+        const uint32_t chunk = std::max<uint32_t>(1, kMaxRotCts / per_msg);
+        for (uint32_t m0 = 0; m0 < o.msgs; m0 += chunk) {
+          const uint32_t mc = std::min(chunk, o.msgs - m0);
+          RotSpec rs;
+          if (uniform) {
+            rs.gal = galois_for_step(c->n, o.steps[0]);
+            rs.key = ks->galois_key(rs.gal)->buf.u64();
+          } else {
+            rs.d_gal = (const uint32_t*)ex->op_gal[i].p + m0;
+            rs.d_keys = (const uint64_t* const*)ex->op_keys[i].p + m0;
+            rs.div = per_msg;
+          }
+          TRY(rotate(c, reg(o.src, o.src_off + m0), reg(o.dst, o.dst_off + m0),
+                     o.aux >= 0 ? reg(o.aux, o.aux_off + m0) : nullptr, (size_t)mc * per_msg, rs, ex->scratch.u64(),
+                     s));
         }
-        TRY(rotate(c, reg(o.src, o.src_off), reg(o.dst, o.dst_off), o.aux >= 0 ? reg(o.aux, o.aux_off) : nullptr, cnt,
-                   rs, ex->scratch.u64(), s));
         break;
       }
       case OP_SUM: {

@@ -23,11 +23,11 @@ LOLA_KEY_ROW_SWAP = 2
 
 REPR = {"dense": 1, "sparse": 2, "stacked": 3, "interleaved": 4, "convolution": 5}
 LAYER = {"conv": 1, "combine": 2, "square": 3, "stack": 4, "stacked_rowmajor": 5,
-         "interleaved_rowmajor": 6, "dense_rowmajor": 7, "sparse_colmajor": 8, "masked_shifts": 9}
+         "interleaved_rowmajor": 6, "dense_rowmajor": 7, "sparse_colmajor": 8, "masked_shifts": 9, "place": 10}
 # representation each layer consumes / produces (0 = not checked)
 LAYER_REPR = {"conv": (5, 1), "combine": (1, 1), "square": (0, 0), "stack": (1, 3),
               "stacked_rowmajor": (3, 4), "interleaved_rowmajor": (4, 2), "dense_rowmajor": (1, 2),
-              "sparse_colmajor": (2, 1), "masked_shifts": (1, 5)}
+              "sparse_colmajor": (2, 1), "masked_shifts": (1, 5), "place": (1, 1)}
 
 
 class LolaError(RuntimeError):
@@ -407,6 +407,15 @@ def lola_pack_convolution(image, kh, kw, stride, n):
     win = C.c_uint32()
     _check(load().lola_pack_convolution(ip, h, w, kh, kw, stride, n, out.ctypes.data_as(I64P), C.byref(win)))
     return out, win.value
+
+
+def lola_pack_convolution_channels(image, kh, kw, stride, n):
+    """Multi-channel image (channels, h, w): the convolution representation
+    of each channel, concatenated channel by channel (message ch*kh*kw +
+    dr*kw + dc), through lola_pack_convolution."""
+    img = np.asarray(image)
+    parts = [lola_pack_convolution(img[ch], kh, kw, stride, n) for ch in range(img.shape[0])]
+    return np.concatenate([p[0] for p in parts]), parts[0][1]
 
 
 def lola_pack_stacked(vec, d, copies, n):

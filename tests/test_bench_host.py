@@ -26,3 +26,12 @@ def test_plain_dense_matches_oracle():
     Wh = W.head_weights()
     f = W.feature_vector(idx=1)
     assert bench.plain_dense(f, Wh) == OL.int_dense(f, Wh)
+
+
+def test_plain_cifar_matches_oracle_integer_network():
+    net = W.cifar_net()
+    img = W.cifar_image(idx=5)
+    x = OL.int_conv(W.cifar_padded(img, net.pad), net.w1, net.k1, net.k1, net.stride)
+    x = OL.int_square(x)
+    x = OL.int_square(OL.int_dense(x, W.cifar_dense2(net)))
+    assert bench.plain_cifar(img, net) == OL.int_dense(x, net.w3)

@@ -316,3 +316,119 @@ def test_masked_shifts_rejects_a_non_shift_gather():
         assert ei.value.code == -1
     finally:
         Lb.lola_ctx_destroy(ctx)
+
+
+# ------------------------------------------------------ CIFAR-shaped (Sec. 6.2)
+
+def test_place_layer_bit_exact_vs_oracle():
+    """Three dense messages combined over both slot rows (in-row shifts, a
+    row change, a message split by masks): bit-exact against the oracle."""
+    need_gpu()
+    Lb = lib()
+    n = 256
+    ps = W.params_small(n, L=3, K=1, t=W.T30[:1])
+    P = oracle_params(ps)
+    t = ps.t[0]
+    h = n // 2
+    T = list(range(9)) + [h + e for e in range(9)] + [20 + e for e in range(4)] + [h + 40 + e for e in range(5)]
+    layers = [{"op": "conv", "weights": np.eye(3, dtype=np.int64)},
+              {"op": "place", "weights": np.array([T], dtype=np.int64)}]
+    g = np.random.default_rng(5)
+    msgs = np.zeros((3, n), np.int64)
+    msgs[:, :9] = g.integers(0, 1000, (3, 9))
+    ctx = make_ctx(ps)
+    try:
+        net = Lb.lola_net_create(ctx, {"repr": "convolution", "n_msgs": 3, "n_elems": 9}, layers)
+        sk, ev = gpu_keys(Lb, ctx, net, 23)
+        ct = Lb.lola_encrypt(ctx, sk, msgs, 2)
+        out = Lb.lola_ct_create(ctx, 1)
+        Lb.lola_eval_network(ctx, ev, net, ct, out)
+        got = Lb.lola_ct_export(ctx, out, (1, 2, P.L, n))[0, 0]
+        ok = oracle_keys(P, net, 23)
+        octs = [bfv.encrypt(P, ok.pk, encoding.encode(m, t), t, 2, i) for i, m in enumerate(msgs)]
+        st = OL.run_network(OL.HEEval(P, ok, t), layers, OL.State(octs, [(0, e) for e in range(9)]))
+        assert np.array_equal(got[0], st.msgs[0].c[0]) and np.array_equal(got[1], st.msgs[0].c[1])
+        dec = Lb.lola_decrypt_residues(ctx, sk, out, 1, n)[0, 0]
+        assert [int(dec[s]) for _, s in net.output_map()] == [int(msgs[m, e]) for m in range(3) for e in range(9)]
+        for hdl in (ct, out):
+            Lb.lola_ct_destroy(hdl)
+        Lb.lola_keys_destroy(sk)
+        Lb.lola_keys_destroy(ev)
+        net.destroy()
+    finally:
+        Lb.lola_ctx_destroy(ctx)
+
+
+def cifar_int(net, img):
+    x = OL.int_conv(W.cifar_padded(img, net.pad), net.w1, net.k1, net.k1, net.stride)
+    x = np.array(OL.int_square(x), dtype=np.int64)
+    x = W.cifar_dense2(net) @ x
+    x = OL.int_square([int(v) for v in x])
+    return OL.int_dense(x, net.w3)
+
+
+def test_mini_cifar_bit_exact_vs_oracle():
+    need_gpu()
+    Lb = lib()
+    n = 1024
+    ps = W.params_small(n, L=5, K=1, t=W.T30[:1])
+    P = oracle_params(ps)
+    t = ps.t[0]
+    net_ = W.cifar_net(seed=9, C=2, h=8, w=8, pad=2, k1=4, maps1=6, k2=2, maps2=3, classes=2)
+    img = W.cifar_image(seed=9, C=2, h=8, w=8)
+    layers = W.layers_cifar(net_, n)
+    msgs, pos = OL.pack_convolution(W.cifar_padded(img, net_.pad), net_.k1, net_.k1, net_.stride, n)
+    ctx = make_ctx(ps)
+    try:
+        net = Lb.lola_net_create(ctx, {"repr": "convolution", "n_msgs": len(msgs), "n_elems": len(pos)}, layers)
+        sk, ev = gpu_keys(Lb, ctx, net, 17)
+        ct = Lb.lola_encrypt(ctx, sk, np.array(msgs, np.int64), 8)
+        out = Lb.lola_ct_create(ctx, 2)
+        Lb.lola_eval_network(ctx, ev, net, ct, out)
+        got = Lb.lola_ct_export(ctx, out, (1, 2, P.L, n))[:, 0]
+        ok = oracle_keys(P, net, 17)
+        octs = [bfv.encrypt(P, ok.pk, encoding.encode(m, t), t, 8, i) for i, m in enumerate(msgs)]
+        st = OL.run_network(OL.HEEval(P, ok, t), layers, OL.State(octs, pos))
+        for o in range(2):
+            assert np.array_equal(got[o, 0], st.msgs[o].c[0]) and np.array_equal(got[o, 1], st.msgs[o].c[1]), o
+        res = Lb.lola_decrypt_residues(ctx, sk, out, 1, n)
+        assert [int(res[m, 0, s]) for m, s in net.output_map()] == [x % t for x in cifar_int(net_, img)]
+        for hdl in (ct, out):
+            Lb.lola_ct_destroy(hdl)
+        Lb.lola_keys_destroy(sk)
+        Lb.lola_keys_destroy(ev)
+        net.destroy()
+    finally:
+        Lb.lola_ctx_destroy(ctx)
+
+
+@pytest.mark.slow
+def test_full_cifar_decrypts_to_integer_network():
+    """The CIFAR-shaped network at full size (n = 16384, three ~30-bit t_i):
+    the decrypted outputs equal the integer network modulo each t_i."""
+    need_gpu()
+    Lb = lib()
+    ps = W.params_cifar()
+    n = ps.n
+    net_ = W.cifar_net()
+    img = W.cifar_image(idx=3)
+    layers = W.layers_cifar(net_, n)
+    msgs, win = Lb.lola_pack_convolution_channels(W.cifar_padded(img, net_.pad), net_.k1, net_.k1, net_.stride, n)
+    ctx = make_ctx(ps)
+    try:
+        net = Lb.lola_net_create(ctx, {"repr": "convolution", "n_msgs": len(msgs), "n_elems": win}, layers)
+        sk, ev = gpu_keys(Lb, ctx, net, W.DEFAULT_SEED)
+        ct = Lb.lola_encrypt(ctx, sk, msgs, 41)
+        out = Lb.lola_ct_create(ctx, 10)
+        Lb.lola_eval_network(ctx, ev, net, ct, out)
+        res = Lb.lola_decrypt_residues(ctx, sk, out, len(ps.t), n)
+        want = cifar_int(net_, img)
+        for ti, t in enumerate(ps.t):
+            assert [int(res[m, ti, s]) for m, s in net.output_map()] == [x % t for x in want], ti
+        for hdl in (ct, out):
+            Lb.lola_ct_destroy(hdl)
+        Lb.lola_keys_destroy(sk)
+        Lb.lola_keys_destroy(ev)
+        net.destroy()
+    finally:
+        Lb.lola_ctx_destroy(ctx)

@@ -339,3 +339,91 @@ def test_mini_lola_dense_encrypted_oracle_run():
     got = [int(encoding.decode(bfv.decrypt(P, keys.sk, st.msgs[m]), t)[s]) for m, s in st.pos]
     assert got == [int(sim.msgs[m][s]) for m, s in sim.pos] == [x % t for x in mnist_int(net, img)]
     assert min(bfv.noise_margin_bits(P, keys.sk, c, encoding.encode(s, t)) for c, s in zip(st.msgs, sim.msgs)) > 4
+
+
+# ------------------------------------------------------ CIFAR-shaped (Sec. 6.2)
+
+def place_case(n):
+    """Three messages of 9 values at slots 0..8; targets exercise no move, an
+    in-row shift, a row change without shift, and a message split over both rows."""
+    h = n // 2
+    T = [e for e in range(9)]                                  # message 0 stays
+    T += [h + e for e in range(9)]                             # message 1: row swap only
+    T += [20 + e for e in range(4)] + [h + 40 + e for e in range(5)]   # message 2: split
+    return T
+
+
+def test_place_layer_puts_every_element_at_its_target():
+    n, t = 256, 257
+    rng = np.random.default_rng(3)
+    vals = rng.integers(0, t, size=(3, 9))
+    msgs = [np.zeros(n, np.int64) for _ in range(3)]
+    for m in range(3):
+        msgs[m][:9] = vals[m]
+    st = lola.State(msgs, [(m, e) for m in range(3) for e in range(9)])
+    T = place_case(n)
+    ev = Counting(n, t)
+    out = lola.layer_place(ev, st, T)
+    want = np.zeros(n, np.int64)
+    for idx, (m, e) in enumerate(st.pos):
+        want[T[idx]] = vals[m][e]
+    assert np.array_equal(out.msgs[0] % t, want) and out.pos == [(0, x) for x in T]
+    # message 2 has two groups (masked); groups: m1 swap k=0, m2 (k=20, k=40 swap); one row swap
+    assert ev.c["mul_plain"] == 2 and ev.c["rot"] == 2 + 1
+
+
+def cifar_int(net, img):
+    """Integer network: conv (padded image), square, second conv as its dense
+    matrix, square, dense; exact over Z (Python ints after the first square)."""
+    x = lola.int_conv(W.cifar_padded(img, net.pad), net.w1, net.k1, net.k1, net.stride)
+    x = np.array(lola.int_square(x), dtype=np.int64)
+    x = W.cifar_dense2(net) @ x                                 # |x| < 2^43: exact in int64
+    x = lola.int_square([int(v) for v in x])
+    return lola.int_dense(x, net.w3)
+
+
+def mini_cifar():
+    net = W.cifar_net(seed=9, C=2, h=8, w=8, pad=2, k1=4, maps1=6, k2=2, maps2=3, classes=2)
+    return net, W.cifar_image(seed=9, C=2, h=8, w=8)
+
+
+def test_mini_cifar_encrypted_oracle_run():
+    n = 1024
+    ps = W.params_small(n, L=5, K=1, t=W.T30[:1])
+    P = bfv.Params(ps.n, ps.q, ps.L, ps.K, ps.t)
+    net, img = mini_cifar()
+    layers = W.layers_cifar(net, n)
+    t = ps.t[0]
+    msgs, pos = lola.pack_convolution(W.cifar_padded(img, net.pad), net.k1, net.k1, net.stride, n)
+    assert len(msgs) == 2 * 16 and len(pos) == 16
+    rec = Counting(n, t)
+    sim = lola.run_network(rec, layers, lola.State([np.array(m, np.int64) % t for m in msgs], pos))
+    want = [x % t for x in cifar_int(net, img)]
+    assert [int(sim.msgs[m][s]) for m, s in sim.pos] == want
+    steps = set()
+
+    class Rec(lola.SlotEval):
+        def rot(self, a, k):
+            steps.add(k)
+            return super().rot(a, k)
+    lola.run_network(Rec(n, t), layers, lola.State([np.array(m, np.int64) % t for m in msgs], pos))
+    keys = bfv.keygen(P, 17, rotations=sorted(steps), relin=True, row_swap=True)
+    cts = [bfv.encrypt(P, keys.pk, encoding.encode(m, t), t, 8, i) for i, m in enumerate(msgs)]
+    st = lola.run_network(lola.HEEval(P, keys, t), layers, lola.State(cts, pos))
+    got = [int(encoding.decode(bfv.decrypt(P, keys.sk, st.msgs[m]), t)[s]) for m, s in st.pos]
+    assert got == want
+
+
+def test_cifar_plan_matches_integer_network():
+    n, t = 16384, W.T30[0]
+    net = W.cifar_net()
+    img = W.cifar_image(idx=2)
+    layers = W.layers_cifar(net, n)
+    msgs, pos = lola.pack_convolution(W.cifar_padded(img, net.pad), net.k1, net.k1, net.stride, n)
+    assert len(msgs) == 192 and len(pos) == 196          # Sec. 6.2: 3 x 8 x 8 messages
+    ev = Counting(n, t)
+    st = lola.run_network(ev, layers, lola.State([np.array(m, np.int64) % t for m in msgs], pos))
+    assert [int(st.msgs[m][s]) for m, s in st.pos] == [x % t for x in cifar_int(net, img)]
+    # place: 40 + 40 + 2 shifted groups + 1 row swap; 4075 + 10 outputs x 14 rotations
+    assert ev.c == {"rot": 83 + 4085 * 14, "mul_plain": 2 + 4075 + 4075 + 10, "mul_scalar": 83 * 192,
+                    "square": 2}

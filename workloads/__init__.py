@@ -61,6 +61,12 @@ def params_mnist(L: int = 5) -> ParamSet:
     return ParamSet(f"mnist_n16384_L{L}", 16384, Q60[:L + 1], L, 1, T30[:3])
 
 
+def params_cifar(L: int = 6) -> ParamSet:
+    """CIFAR-shaped network (Sec. 6.2): n = 16384, L 60-bit primes plus a
+    60-bit special prime, three ~30-bit plaintext CRT moduli."""
+    return ParamSet(f"cifar_n16384_L{L}", 16384, Q60[:L + 1], L, 1, T30[:3])
+
+
 def params_head(L: int = 5) -> ParamSet:
     """Transfer-learning head: as params_mnist but one plaintext modulus."""
     return ParamSet(f"head_n16384_L{L}", 16384, Q60[:L + 1], L, 1, T30[:1])
@@ -83,7 +89,7 @@ def rng(seed: int, purpose: int) -> np.random.Generator:
 
 # purposes
 P_IMAGE, P_CONV_W, P_DENSE1_W, P_DENSE2_W, P_FEAT, P_HEAD_W, P_VEC, P_DENSE_W, \
-    P_RESIDUES, P_STEPS, P_ENC, P_KEY = range(1, 13)
+    P_RESIDUES, P_STEPS, P_ENC, P_KEY, P_CIFAR_IMG, P_CIFAR_W1, P_CIFAR_W2, P_CIFAR_W3 = range(1, 17)
 
 
 def image(seed=DEFAULT_SEED, idx: int = 0, h: int = 28, w: int = 28) -> np.ndarray:
@@ -112,6 +118,72 @@ def mnist_net(seed=DEFAULT_SEED, maps=5, hidden=100, classes=10, h=28, w=28, k=5
     return MnistNet(int_weights(seed, P_CONV_W, (maps, k * k)),
                     int_weights(seed, P_DENSE1_W, (hidden, maps * oh * ow)),
                     int_weights(seed, P_DENSE2_W, (classes, hidden)), k, k, stride, h, w)
+
+
+@dataclass
+class CifarNet:
+    """Sec. 6.2 / App. D, after collapsing adjacent linear layers: k1 x k1 x C
+    convolution, stride 2, maps1 maps; square; k2 x k2 x maps1 convolution,
+    stride 2, maps2 maps (evaluated as a dense layer); square; dense layer
+    with `classes` outputs.  The image is zero-padded bottom/right by `pad`
+    (34 x 34 from 32 x 32 gives the paper's 14 x 14 windows: 83 * 196 = 16268
+    first-layer nodes, 163 * 25 = 4075 second-layer nodes)."""
+    w1: np.ndarray = field(repr=False)     # (maps1, C*k1*k1)
+    w2: np.ndarray = field(repr=False)     # (maps2, maps1*k2*k2)
+    w3: np.ndarray = field(repr=False)     # (classes, maps2*o2*o2)
+    C: int = 3
+    h: int = 32
+    w: int = 32
+    pad: int = 2
+    k1: int = 8
+    k2: int = 6
+    stride: int = 2
+
+    @property
+    def o1(self) -> int:
+        return -(-(self.h + self.pad - self.k1) // self.stride) + 1
+
+    @property
+    def o2(self) -> int:
+        return (self.o1 - self.k2) // self.stride + 1
+
+
+def cifar_net(seed=DEFAULT_SEED, C=3, h=32, w=32, pad=2, k1=8, maps1=83, k2=6, maps2=163, classes=10,
+              stride=2) -> CifarNet:
+    o1 = -(-(h + pad - k1) // stride) + 1
+    o2 = (o1 - k2) // stride + 1
+    return CifarNet(int_weights(seed, P_CIFAR_W1, (maps1, C * k1 * k1)),
+                    int_weights(seed, P_CIFAR_W2, (maps2, maps1 * k2 * k2)),
+                    int_weights(seed, P_CIFAR_W3, (classes, maps2 * o2 * o2)), C, h, w, pad, k1, k2, stride)
+
+
+def cifar_image(seed=DEFAULT_SEED, idx: int = 0, C=3, h=32, w=32) -> np.ndarray:
+    return rng(seed + idx, P_CIFAR_IMG).integers(0, 16, size=(C, h, w), dtype=np.int64)
+
+
+def cifar_padded(img: np.ndarray, pad: int) -> np.ndarray:
+    """Zero rows and columns appended bottom/right (the client pads before packing)."""
+    C, h, w = img.shape
+    out = np.zeros((C, h + pad, w + pad), dtype=np.int64)
+    out[:, :h, :w] = img
+    return out
+
+
+def cifar_dense2(net: CifarNet) -> np.ndarray:
+    """The second convolution as the dense matrix it is evaluated as: row
+    (o, i, j) (map-major, windows row-major) over the first layer's outputs
+    (map-major, windows row-major)."""
+    maps2, maps1 = net.w2.shape[0], net.w1.shape[0]
+    o1, o2, k2, s = net.o1, net.o2, net.k2, net.stride
+    M = np.zeros((maps2 * o2 * o2, maps1 * o1 * o1), dtype=np.int64)
+    # column of kernel entry (ch, dr, dc), in the kernel's own order, for window (0, 0)
+    ch, dr, dc = np.meshgrid(np.arange(maps1), np.arange(k2), np.arange(k2), indexing="ij")
+    off = (ch * o1 * o1 + dr * o1 + dc).reshape(-1)
+    for o in range(maps2):
+        for i in range(o2):
+            for j in range(o2):
+                M[(o * o2 + i) * o2 + j, s * i * o1 + s * j + off] = net.w2[o]
+    return M
 
 
 def feature_vector(seed=DEFAULT_SEED, idx: int = 0, dim: int = 4096) -> np.ndarray:
@@ -233,6 +305,51 @@ def layers_lola_dense(net: MnistNet, n: int, width: int = DENSE_IMAGE_WIDTH) -> 
         {"op": "stacked_rowmajor", "weights": net.dense1_w, "d": d, "copies": copies},
         {"op": "square"},
         {"op": "interleaved_rowmajor", "weights": net.dense2_w},
+    ]
+
+
+def cifar_place_targets(maps: int, per_map: int, n: int) -> list:
+    """Target slots for combining `maps` messages of `per_map` values (at
+    slots 0..per_map-1) into one message over both slot rows: whole maps fill
+    row 0 then row 1, a map that does not fit in what is left of row 0 is split
+    between the tail of row 0 and the tail of row 1."""
+    h = n // 2
+    per_row = h // per_map
+    assert maps * per_map <= n
+    T = []
+    for m in range(maps):
+        for e in range(per_map):
+            if m < per_row:
+                t = m * per_map + e
+            elif m < 2 * per_row:
+                t = h + (m - per_row) * per_map + e
+            else:                                   # split maps: row 0 tail, then row 1 tail
+                k = (m - 2 * per_row) * per_map + e
+                tail0 = h - per_row * per_map
+                t = per_row * per_map + k if k < tail0 else h + per_row * per_map + (k - tail0)
+            T.append(t)
+    assert len(set(T)) == len(T) and max(T) < n
+    return T
+
+
+def layers_cifar(net: CifarNet, n: int, dense2: np.ndarray | None = None) -> list:
+    """Sec. 6.2: convolution row-major on the convolution representation
+    (C*k1*k1 messages), the maps combined into one message, square, the
+    second convolution as dense row-major (sparse output), sparse -> dense by
+    masks and additions (column-major with the identity), square, dense
+    row-major."""
+    maps1 = net.w1.shape[0]
+    per = net.o1 * net.o1
+    D2 = cifar_dense2(net) if dense2 is None else dense2
+    k2 = D2.shape[0]
+    return [
+        {"op": "conv", "weights": net.w1},
+        {"op": "place", "weights": np.array([cifar_place_targets(maps1, per, n)], dtype=np.int64)},
+        {"op": "square"},
+        {"op": "dense_rowmajor", "weights": D2},
+        {"op": "sparse_colmajor", "weights": np.eye(k2, dtype=np.int64)},
+        {"op": "square"},
+        {"op": "dense_rowmajor", "weights": net.w3},
     ]
 
 
