@@ -546,7 +546,8 @@ def run_primitives(args):
     rotations by random steps in [1, n/2) (one Galois key per distinct
     step), B/2 ct x ct products with relinearisation.  Per operation: device
     time per launch (CUDA events), per ciphertext, and the transform rate
-    against the derived integer-ALU peak."""
+    against the derived integer-ALU peak.  rotate_hoisted_x8: every
+    ciphertext rotated by 8 of those steps sharing one decomposition."""
     import numpy as np
     import torch
 
@@ -567,10 +568,13 @@ def run_primitives(args):
     work = torch.from_numpy(host.view(np.int64).copy()).cuda()
     ps_src, ps_dst, ps_prod = L.lola_ct_data(src), L.lola_ct_data(dst), L.lola_ct_data(prod)
     ct_bytes = 2 * Lq * n * 8
+    hsteps = sorted(set(steps))[:8]                   # 8 rotations of every ciphertext, one decomposition
+    hout = torch.empty(len(hsteps) * B * 2 * Lq * n, dtype=torch.int64, device="cuda")
     ops = {
         "ntt_fwd": (lambda: L.lola_ntt_forward(ctx, work, 2 * B, Lq, stream), B),
         "ntt_inv": (lambda: L.lola_ntt_inverse(ctx, work, 2 * B, Lq, stream), B),
         "rotate": (lambda: L.lola_rotate(ctx, ev, ps_src, ps_dst, B, steps, stream), B),
+        "rotate_hoisted_x8": (lambda: L.lola_rotate_hoisted(ctx, ev, ps_src, hout, B, hsteps, stream), B * len(hsteps)),
         "multiply_relin": (lambda: L.lola_multiply(ctx, ev, ps_src, ps_src + (half * ct_bytes if B > 1 else 0),
                                                    ps_prod, half, stream=stream), half),
     }

@@ -178,6 +178,18 @@ int lola_multiply(lola_ctx* ctx, const lola_keys* keys, const uint64_t* a, const
 #define LOLA_ROTATE_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
 int lola_rotate_noalloc(lola_ctx* ctx, const lola_keys* keys, const uint64_t* in, uint64_t* out, size_t count,
                         int32_t step, void* stream);
+/* Hoisted rotations (several rotations of the same ciphertexts, Sec. 3.1
+ * rot; a batching of the rotate-and-sum building block of Sec. 4.1): every
+ * one of `count` ciphertexts in `in` (device, [count][2][L][n]) is rotated
+ * by each of the n_steps steps (0 = row swap); out (device, caller-owned,
+ * [n_steps][count][2][L][n], must not overlap in) receives step-major
+ * results.  The digits [c1]_{q_i} are computed and raised to Q*P once; the
+ * rotation by g uses the digits tau_g([c1]_{q_i}) taken over Z (congruent
+ * to tau_g(c1) mod q_i), so results decrypt like lola_rotate's but differ
+ * from them in the key-switching noise.  Errors: LOLA_E_NOKEY,
+ * LOLA_E_PARAM, LOLA_E_CUDA, LOLA_E_NOMEM (scratch is allocated per call). */
+int lola_rotate_hoisted(lola_ctx* ctx, const lola_keys* keys, const uint64_t* in, uint64_t* out, size_t count,
+                        const int32_t* steps, size_t n_steps, void* stream);
 /* ct x plaintext: out_i = in_i * encode(slots_i) (slots host [count][n]
  * int64, centered lift mod t). */
 int lola_mul_plain(lola_ctx* ctx, const uint64_t* in, const int64_t* slots, uint64_t* out, size_t count,

@@ -285,16 +285,23 @@ def mul_scalar(params: Params, ct: Ciphertext, w: int) -> Ciphertext:
 
 
 def key_switch(params: Params, d: np.ndarray, ksk: KeySwitchKey):
-    """Switch d (shape (L, n), mod Q) from s' to s; returns (u0, u1) mod Q."""
+    """Switch d (shape (L, n), mod Q) from s' to s; returns (u0, u1) mod Q.
+    Digits: [d]_{q_i} in [0, q_i), lifted unchanged to every other prime."""
+    return key_switch_digits(params, [d[i].astype(np.int64) for i in range(params.L)], ksk)
+
+
+def key_switch_digits(params: Params, digits, ksk: KeySwitchKey):
+    """The key-switch inner product sum_i digit_i * ksk_i over Q * P and the
+    ModDown, for digits given as integer polynomials (digit i must be
+    congruent mod q_i to the polynomial being switched)."""
     L, K, primes = params.L, params.K, params.q
-    digits = [d[i] for i in range(L)]          # [d]_{q_i} in [0, q_i)
     u = []
     for comp in (ksk.b, ksk.a):
         acc = []
         for j, pj in enumerate(primes):
             s = np.zeros(params.n, dtype=np.uint64)
             for i in range(L):
-                di = ring.u64(digits[i] % np.uint64(pj))
+                di = np.mod(digits[i], np.int64(pj)).astype(np.uint64)   # digit i lifted to Z, mod p_j
                 s = ring.vec_add(s, ring.poly_mul(di, comp[i, j], pj), pj)
             acc.append(s)
         u.append(np.stack(acc))
@@ -325,6 +332,26 @@ def apply_galois(params: Params, ct: Ciphertext, g: int, ksk: KeySwitchKey) -> C
 def rotate(params: Params, keys: Keys, ct: Ciphertext, k: int) -> Ciphertext:
     g = galois_for_rotation(params.n, k)
     return apply_galois(params, ct, g, keys.galois[g])
+
+
+def rotate_hoisted(params: Params, keys: Keys, ct: Ciphertext, steps) -> list:
+    """Rotations of one ciphertext by several steps sharing one digit
+    decomposition (hoisting; step 0 = row swap).  The digits of c1 are
+    d_i = [c1]_{q_i} as integer polynomials with coefficients in [0, q_i),
+    computed once; rotation g switches tau_g(c1) with the digits tau_g(d_i)
+    taken over Z (coefficients in (-q_i, q_i)), which are congruent to
+    tau_g(c1) mod q_i, then adds tau_g(c0).  At g = 1 the digits are those of
+    key_switch; for other g the result differs from apply_galois by a
+    different (equally valid) key-switching noise."""
+    qs = params.q[:params.L]
+    d = [ct.c[1][i].astype(np.int64) for i in range(params.L)]
+    out = []
+    for k in steps:
+        g = galois_row_swap(params.n) if k == 0 else galois_for_rotation(params.n, k)
+        c0 = _auto_rns(ct.c[0], g, qs)
+        u0, u1 = key_switch_digits(params, [ring.automorphism_int(di, g) for di in d], keys.galois[g])
+        out.append(Ciphertext([_add_rns(c0, u0, qs), u1], ct.t))
+    return out
 
 
 def rotate_rows(params: Params, keys: Keys, ct: Ciphertext) -> Ciphertext:

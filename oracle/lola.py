@@ -47,6 +47,10 @@ class SlotEval:
         h = self.n // 2
         return np.concatenate([np.roll(a[:h], k), np.roll(a[h:], k)])
 
+    def rot_hoisted(self, a, steps):
+        """Several rotations of one message (slot semantics of rot / rot_rows)."""
+        return [self.rot_rows(a) if k == 0 else self.rot(a, k) for k in steps]
+
     def rot_rows(self, a):
         h = self.n // 2
         return np.concatenate([a[h:], a[:h]])
@@ -80,6 +84,10 @@ class HEEval:
     def rot_rows(self, a):
         self.counts["rot"] += 1
         return bfv.rotate_rows(self.p, self.keys, a)
+
+    def rot_hoisted(self, a, steps):
+        self.counts["rot"] += len(steps)
+        return bfv.rotate_hoisted(self.p, self.keys, a, steps)
 
     def mul_plain(self, a, slots):
         self.counts["mul_plain"] += 1
@@ -173,22 +181,21 @@ def layer_masked_shifts(ev, st: State, G) -> State:
     Table 3: mask the input to create 25 messages).  G[r][e] is the input
     element that message r holds at element e (-1: zero padding).  Reading:
     message 0 keeps element G[0][e] at its input slot S_e; message r is the
-    input times the 0/1 mask of the slots S_e + off_r of its elements, then
-    rotated left by off_r (right by n/2 - off_r) so its elements line up
-    with S_e (the masks are shifts of each other)."""
+    input rotated left by off_r (right by n/2 - off_r; the masks are shifts
+    of each other, so one rotation per message aligns it), then multiplied
+    by the 0/1 mask of the slots S_e of its elements.  The R - 1 rotations
+    all rotate the one input, so they share one decomposition (hoisted)."""
     n, h = ev.n, ev.n // 2
     S, offs = masked_shift_plan(st, G, n)
     x = st.msgs[0]
+    ys = [x] + ev.rot_hoisted(x, [h - off for off in offs[1:]])
     out = []
-    for r, off in enumerate(offs):
+    for r, y in enumerate(ys):
         mask = [0] * n
         for e in range(len(S)):
             if int(G[r][e]) >= 0:
-                mask[S[e] + off] = 1
-        y = ev.mul_plain(x, mask)
-        if off:
-            y = ev.rot(y, h - off)
-        out.append(y)
+                mask[S[e]] = 1
+        out.append(ev.mul_plain(y, mask))
     return State(out, [(0, s) for s in S])
 
 

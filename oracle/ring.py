@@ -138,6 +138,17 @@ def inverse_transform(a: np.ndarray, q: int, psi: int) -> np.ndarray:
     return a
 
 
+def automorphism_int(a: np.ndarray, g: int) -> np.ndarray:
+    """tau_g over Z: a(x) -> a(x^g) mod x^n + 1 for an integer polynomial
+    (int64 coefficients, |a_i| < 2^62); x^(n+r) = -x^r."""
+    a = np.asarray(a, dtype=np.int64)
+    n = a.shape[-1]
+    e = (np.arange(n, dtype=np.int64) * g) % (2 * n)
+    out = np.zeros(n, dtype=np.int64)
+    out[e % n] = np.where(e >= n, -a, a)
+    return out
+
+
 def automorphism(a: np.ndarray, g: int, q: int) -> np.ndarray:
     """tau_g: a(x) -> a(x^g) in Z_q[x]/(x^n+1), g odd.
 

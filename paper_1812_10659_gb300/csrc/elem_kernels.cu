@@ -37,6 +37,11 @@ __device__ __forceinline__ uint64_t redc128(unsigned __int128 T, uint64_t q, uin
 // final_out (K = 0): write the switched ciphertext limb directly, plus addends.
 // Otherwise write ACC; the caller may place ACC over D's digit rows 0 and 1:
 // a thread reads every D word it overwrites before writing it.
+// Hoisted rotations (ip_gather): D and c0 are those of the unrotated source
+// ciphertext ct % src_mod; position k of tau_g(D) is D[gal_src(k)], and the
+// pair (k, k+1) maps to the aligned pair holding gal_src(k) and
+// gal_src(k) ^ 1, so each pair is still one 16-byte load (swapped when
+// gal_src(k) is odd).
 __global__ void ke_ks_ip(const CtxDev* __restrict__ C, KsDev a, int final_out) {
   const int L = C->L, LK = C->L + C->K, logn = C->logn;
   const size_t n = C->n, half = n >> 1;
@@ -49,10 +54,20 @@ __global__ void ke_ks_ip(const CtxDev* __restrict__ C, KsDev a, int final_out) {
     const size_t ct = r / J;
     const PrimeDev& P = C->pr[j];
     const uint64_t* key = a.d_keys ? a.d_keys[ct / a.gal_div] : a.key;
+    const size_t src = a.src_mod ? ct % a.src_mod : ct;
+    size_t kd = k;
+    bool swp = false;
+    if (a.ip_gather) {
+      const uint32_t g = a.d_gal ? a.d_gal[ct / a.gal_div] : a.gal;
+      const uint32_t m = gal_src((uint32_t)k, g, logn);
+      kd = m & ~1u;
+      swp = (m & 1u) != 0;
+    }
     uint64_t acc0[2] = {0, 0}, acc1[2] = {0, 0};
     unsigned __int128 s0[2] = {0, 0}, s1[2] = {0, 0};
     for (int i = 0; i < L; ++i) {
-      const ulonglong2 d = *(const ulonglong2*)(a.D + ((ct * L + i) * LK + j) * n + k);
+      ulonglong2 d = *(const ulonglong2*)(a.D + ((src * L + i) * LK + j) * n + kd);
+      if (swp) d = make_ulonglong2(d.y, d.x);
       const ulonglong2 k0 = __ldg((const ulonglong2*)(key + ((size_t)i * LK + j) * n + k));
       const ulonglong2 k1 = __ldg((const ulonglong2*)(key + ((size_t)(L + i) * LK + j) * n + k));
       s0[0] += (unsigned __int128)d.x * k0.x;
@@ -76,6 +91,7 @@ __global__ void ke_ks_ip(const CtxDev* __restrict__ C, KsDev a, int final_out) {
         const size_t kk = k + e;
         uint64_t v0 = acc0[e], v1 = acc1[e];
         if (a.c0p) v0 = add_mod(v0, a.c0p[(ct * L + j) * n + kk], P.q);
+        else if (a.ip_gather) v0 = add_mod(v0, a.c0[(src * 2 * L + j) * n + (kd + (e ^ (int)swp))], P.q);
         else if (a.c0) v0 = add_mod(v0, a.c0[(ct * 2 * L + j) * n + kk], P.q);
         if (a.add1) v1 = add_mod(v1, a.add1[(ct * 2 * L + L + j) * n + kk], P.q);
         if (a.accum) {
@@ -95,6 +111,7 @@ __global__ void ke_ks_ip(const CtxDev* __restrict__ C, KsDev a, int final_out) {
           const size_t kk = k + e;
           uint64_t s0v = 0, s1v = 0;
           if (a.c0p) s0v = a.c0p[(ct * L + j) * n + kk];
+          else if (a.ip_gather) s0v = a.c0[(src * 2 * L + j) * n + (kd + (e ^ (int)swp))];
           else if (a.c0) s0v = a.c0[(ct * 2 * L + j) * n + kk];
           if (a.add1) s1v = a.add1[(ct * 2 * L + L + j) * n + kk];
           if (a.accum) {

@@ -160,6 +160,61 @@ int rotate(Ctx* c, const uint64_t* in, uint64_t* out, const uint64_t* accum, siz
   return ks_finish(c, a, a.c0p + count * L * n, s);
 }
 
+// Hoisted rotations: every one of `count` ciphertexts rotated by each of
+// S steps, out = [S][count] ciphertexts.  The digits of c1 are decomposed
+// and raised to Q * P once (decompose with the identity, mod-up); each
+// step then gathers tau_g(D) and tau_g(c0) inside the inner product and
+// runs INTT mod P and mod-down for all S * count outputs in one launch each.
+// steps per inner-product launch: at most ~1024 outputs, at least one step
+static size_t hoisted_chunk(size_t count, size_t S) { return std::min(S, std::max<size_t>(1, 1024 / count)); }
+
+size_t rotate_hoisted_scratch_words(const Ctx* c, size_t count, size_t S) {
+  const size_t n = c->n, L = c->L, LK = c->L + c->K;
+  return count * (2 * L + L * LK) * n + hoisted_chunk(count, S) * count * (2 * LK + 2) * n;
+}
+
+int rotate_hoisted(Ctx* c, const uint64_t* in, uint64_t* out, size_t count, size_t S, const uint32_t* d_gal,
+                   const uint64_t* const* d_keys, uint64_t* scratch, cudaStream_t s) {
+  if (!count || !S) return LOLA_OK;
+  const size_t chunk = hoisted_chunk(count, S);
+  const size_t n = c->n, L = c->L, LK = c->L + c->K;
+  KsDev a{};
+  a.c0 = in;
+  a.c1 = in;
+  a.dig = scratch;
+  a.D = a.dig + count * L * n;
+  a.c0p = a.D + count * L * LK * n;          // written by decompose (identity), not read
+  a.count = count;
+  a.gal = 1;
+  a.gal_div = 1;
+  TRY(k::ks_decompose(c, a, s));
+  TRY(k::ks_modup(c, a, true, s));
+  for (size_t s0 = 0; s0 < S; s0 += chunk) {
+    const size_t sc = std::min(chunk, S - s0);
+    KsDev b{};
+    b.c0 = in;
+    b.out = out + s0 * count * c->ct_words();
+    b.D = a.D;
+    b.acc = a.c0p + count * L * n;
+    b.acc_stride = 2 * LK * n;
+    b.xP = b.acc + sc * count * 2 * LK * n;
+    b.count = sc * count;
+    b.d_gal = d_gal + s0;
+    b.d_keys = d_keys + s0;
+    b.gal_div = (uint32_t)count;
+    b.src_mod = (uint32_t)count;
+    b.ip_gather = 1;
+    if (!c->K) {
+      TRY(k::ks_ip(c, b, true, s));
+      continue;
+    }
+    TRY(k::ks_ip(c, b, false, s));
+    TRY(k::ks_intt_p(c, b, s));
+    TRY(k::ks_moddown(c, b, s));
+  }
+  return LOLA_OK;
+}
+
 // ---------------------------------------------------------- ct x ct (Sec. 3.1 (x))
 size_t multiply_scratch_words(const Ctx* c, size_t count, bool square) {
   const size_t n = c->n, L = c->L, M = c->M, LK = c->L + c->K;

@@ -51,6 +51,9 @@ struct RotSpec {
   uint32_t div = 1;
 };
 size_t rotate_scratch_words(const Ctx* c, size_t count);
+size_t rotate_hoisted_scratch_words(const Ctx* c, size_t count, size_t S);
+int rotate_hoisted(Ctx* c, const uint64_t* in, uint64_t* out, size_t count, size_t S, const uint32_t* d_gal,
+                   const uint64_t* const* d_keys, uint64_t* scratch, cudaStream_t s);
 int rotate(Ctx* c, const uint64_t* in, uint64_t* out, const uint64_t* accum, size_t count, const RotSpec& r,
            uint64_t* scratch, cudaStream_t s);
 

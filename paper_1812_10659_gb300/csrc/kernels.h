@@ -50,6 +50,10 @@ struct KsDev {
   const uint64_t* const* d_keys;  // per-entry key base or null (use key)
   const uint64_t* key;
   uint32_t gal_div;       // ciphertext i uses entry i / gal_div
+  // hoisted rotations: entry i reads D and c0 of source ciphertext i % src_mod
+  // (0: i) through tau_g in the NTT domain (D and c0 not permuted beforehand)
+  uint32_t src_mod;
+  uint32_t ip_gather;
 };
 
 namespace k {

@@ -117,9 +117,9 @@ static int layer_conv(Builder& b, const lola_layer& L, Repr& r) {
 // Dense -> convolution representation by masking (App. C, LoLa-Dense):
 // weights[r][e] = input element that message r holds at element e (-1 =
 // zero padding).  Message 0 keeps its elements at their input slots S_e;
-// message r must be one shift off_r of message 0.  All R products
-// x * mask_r run as one ct x plaintext launch (mask_r: ones at S_e + off_r),
-// then messages 1..R-1 are rotated left by off_r in one rotation wave.
+// message r must be one shift off_r of message 0.  The input is rotated
+// left by every off_r in one hoisted rotation (one decomposition for all),
+// then each message is multiplied by the 0/1 mask of its elements' slots.
 static int layer_masked_shifts(Builder& b, const lola_layer& L, Repr& r) {
   const uint32_t n = b.c->n, h = n / 2;
   if (r.kind != LOLA_REPR_DENSE || r.msgs != 1) return fail(LOLA_E_REPR, "masked shifts need one dense message");
@@ -159,7 +159,7 @@ static int layer_masked_shifts(Builder& b, const lola_layer& L, Repr& r) {
   std::vector<std::vector<int64_t>> M(R, std::vector<int64_t>(n, 0));
   for (uint32_t m = 0; m < R; ++m)
     for (uint32_t e = 0; e < E; ++e)
-      if (G(m, e) >= 0) M[m][S[e] + off[m]] = 1;
+      if (G(m, e) >= 0) M[m][S[e]] = 1;
   const int outr = b.vreg(R);
   const size_t pt0 = b.add_plaintexts(M);
   Op m0;                                    // message 0: x * mask_0, straight into the output
@@ -171,18 +171,23 @@ static int layer_masked_shifts(Builder& b, const lola_layer& L, Repr& r) {
   m0.pt_first = pt0;
   b.net->ops.push_back(m0);
   if (R > 1) {
-    Op mr;                                  // messages 1..R-1: x * mask_r
+    Op ro;                                  // messages 1..R-1: x rotated left by off_r, hoisted
+    ro.kind = OP_ROT_HOISTED;
+    ro.src = r.reg;
+    ro.dst = b.vreg(R - 1);
+    ro.msgs = R - 1;
+    for (uint32_t m = 1; m < R; ++m) ro.steps.push_back((int32_t)(h - off[m]));   // left by off = right by h - off
+    for (int32_t s : ro.steps) b.steps.insert(s);
+    b.net->ops.push_back(ro);
+    Op mr;                                  // then times mask_r
     mr.kind = OP_MULPT;
-    mr.src = r.reg;
-    mr.src_stride = 0;
-    mr.dst = b.vreg(R - 1);
+    mr.src = ro.dst;
+    mr.src_stride = 1;
+    mr.dst = outr;
+    mr.dst_off = 1;
     mr.msgs = R - 1;
     mr.pt_first = pt0 + 1;
     b.net->ops.push_back(mr);
-    std::vector<int32_t> st;
-    for (uint32_t m = 1; m < R; ++m) st.push_back((int32_t)(h - off[m]));   // left by off = right by h - off
-    b.rot(outr, mr.dst, -1, R - 1, st);
-    b.net->ops.back().dst_off = 1;
   }
   Repr out;
   out.kind = LOLA_REPR_CONVOLUTION;
@@ -698,6 +703,7 @@ static int build_executor(Ctx* c, Net* net, uint32_t B, Executor* ex) {
       sw = std::max(sw, rotate_scratch_words(c, mc * per_msg) + 2 * mc);
     }
     if (o.kind == OP_SQUARE) sw = std::max(sw, multiply_scratch_words(c, cnt, true));
+    if (o.kind == OP_ROT_HOISTED) sw = std::max(sw, rotate_hoisted_scratch_words(c, (size_t)B * kt, o.msgs));
   }
   TRY(ex->scratch.alloc(sw * 8));
   std::vector<uint32_t> pat(maxcnt);
@@ -716,7 +722,7 @@ static int bind_keys(Ctx* c, Net* net, Executor* ex, const KeySet* ks) {
   ex->op_keys.resize(net->ops.size());
   for (size_t i = 0; i < net->ops.size(); ++i) {
     const Op& o = net->ops[i];
-    if (o.kind != OP_ROT) continue;
+    if (o.kind != OP_ROT && o.kind != OP_ROT_HOISTED) continue;
     std::vector<uint32_t> g(o.msgs);
     std::vector<const uint64_t*> kp(o.msgs);
     for (uint32_t m = 0; m < o.msgs; ++m) {
@@ -774,6 +780,11 @@ static int run_ops(Ctx* c, Net* net, Executor* ex, const KeySet* ks, cudaStream_
         }
         break;
       }
+      case OP_ROT_HOISTED:
+        TRY(rotate_hoisted(c, reg(o.src, o.src_off), reg(o.dst, o.dst_off), (size_t)B * kt, o.msgs,
+                           (const uint32_t*)ex->op_gal[i].p, (const uint64_t* const*)ex->op_keys[i].p,
+                           ex->scratch.u64(), s));
+        break;
       case OP_SUM: {
         uint64_t* d = reg(o.dst, o.dst_off);
         const size_t per = (size_t)B * kt;

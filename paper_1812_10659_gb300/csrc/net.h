@@ -8,7 +8,7 @@
 
 namespace lola {
 
-enum OpKind { OP_MAC = 1, OP_ROT = 2, OP_SUM = 3, OP_MULPT = 4, OP_SQUARE = 5 };
+enum OpKind { OP_MAC = 1, OP_ROT = 2, OP_SUM = 3, OP_MULPT = 4, OP_SQUARE = 5, OP_ROT_HOISTED = 6 };
 
 // A register holds `msgs` messages for every request of the batch and every
 // plaintext modulus: layout [msg][request][t_i][2][L][n].
@@ -18,6 +18,7 @@ struct Op {
   uint32_t dst_off = 0, src_off = 0, aux_off = 0;
   uint32_t msgs = 0;                  // messages processed
   // OP_ROT: per-message rotation step (0 = row swap); aux = accumulator register (or -1)
+  // OP_ROT_HOISTED: message src_off of src rotated by steps[m] into message m of dst
   std::vector<int32_t> steps;
   // OP_MULPT: plaintexts [msgs][kt][L][n] at pt_first (in plaintext blocks); src_stride 0 = broadcast
   size_t pt_first = 0;

@@ -85,6 +85,7 @@ _SIGS = {
     "lola_multiply": (C.c_int, [P, P, P, P, P, C.c_size_t, U32P, P]),
     "lola_mul_plain": (C.c_int, [P, P, I64P, P, C.c_size_t, U32P, P]),
     "lola_rotate_noalloc": (C.c_int, [P, P, P, P, C.c_size_t, C.c_int32, P]),
+    "lola_rotate_hoisted": (C.c_int, [P, P, P, P, C.c_size_t, I32P, C.c_size_t, P]),
     "lola_net_create": (C.c_int, [P, C.POINTER(lola_input), C.POINTER(lola_layer), C.c_size_t, C.POINTER(P)]),
     "lola_net_destroy": (None, [P]),
     "lola_net_rotation_steps": (C.c_int, [P, I32P, C.POINTER(C.c_size_t)]),
@@ -296,6 +297,14 @@ def lola_rotate(ctx, keys, inp, out, count, steps, stream=None):
     assert st.size == count
     _check(load().lola_rotate(ctx, keys, dptr(inp), dptr(out), count, st.ctypes.data_as(I32P),
                               stream_handle(stream)))
+
+
+def lola_rotate_hoisted(ctx, keys, inp, out, count, steps, stream=None):
+    """Rotate each of `count` ciphertexts by every step in `steps` (one
+    shared decomposition); out holds len(steps) * count ciphertexts, step-major."""
+    st = np.ascontiguousarray(np.asarray(steps, dtype=np.int32))
+    _check(load().lola_rotate_hoisted(ctx, keys, dptr(inp), dptr(out), count, st.ctypes.data_as(I32P), st.size,
+                                      stream_handle(stream)))
 
 
 def lola_rotate_noalloc(ctx, keys, inp, out, count, step, stream=None):

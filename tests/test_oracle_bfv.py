@@ -137,6 +137,51 @@ def test_row_swap(small):
                           np.concatenate([v[h:], v[:h]]))
 
 
+def test_hoisted_rotations_decrypt_to_rotated_slots(small):
+    P, keys = small
+    v = np.random.default_rng(11).integers(0, 65537, P.n)
+    ct = enc(P, keys, v)
+    h = P.n // 2
+    outs = bfv.rotate_hoisted(P, keys, ct, [1, 7, 0, 4])
+    for k, o in zip([1, 7, 0, 4], outs):
+        want = np.concatenate([v[h:], v[:h]]) if k == 0 else row_shift(v, k)
+        assert np.array_equal(dec(P, keys, o), want), k
+        # a different, equally small key-switching noise than the plain rotation
+        plain = bfv.rotate_rows(P, keys, ct) if k == 0 else bfv.rotate(P, keys, ct, k)
+        m = encoding.encode(want, 65537)
+        assert abs(bfv.noise_margin_bits(P, keys.sk, o, m) - bfv.noise_margin_bits(P, keys.sk, plain, m)) < 3
+
+
+def test_hoisted_digits_are_congruent_to_the_rotated_polynomial(small):
+    # tau_g over Z of the digit [c1]_{q_i} reduces mod q_i to tau_g(c1) mod q_i
+    P, keys = small
+    c1 = enc(P, keys, np.arange(P.n) % 65537).c[1]
+    for g in (bfv.galois_for_rotation(P.n, 3), bfv.galois_row_swap(P.n)):
+        for i, qi in enumerate(P.q[:P.L]):
+            e = ring.automorphism_int(c1[i].astype(np.int64), g)
+            assert all(-qi < int(x) < qi for x in e)
+            assert np.array_equal(np.mod(e, qi).astype(np.uint64), ring.automorphism(c1[i], g, qi))
+
+
+def test_hoisted_equals_plain_rotation_when_no_coefficient_changes_sign(small):
+    # With c1 zero at every position tau_g maps past x^n, the integer digits
+    # tau_g(d_i) are the plain digits [tau_g(c1)]_{q_i}: both definitions agree.
+    P, keys = small
+    n, k = P.n, 2
+    g = bfv.galois_for_rotation(n, k)
+    ct = enc(P, keys, np.random.default_rng(5).integers(0, 65537, n))
+    keep = np.array([(a * g) % (2 * n) < n for a in range(n)])
+    c1 = ct.c[1].copy()
+    c1[:, ~keep] = 0
+    ct2 = bfv.Ciphertext([ct.c[0], c1], ct.t)
+    hz = bfv.rotate_hoisted(P, keys, ct2, [k])[0]
+    pl = bfv.rotate(P, keys, ct2, k)
+    assert np.array_equal(hz.c[0], pl.c[0]) and np.array_equal(hz.c[1], pl.c[1])
+    # and they differ on a generic ciphertext (the definitions are not the same)
+    hz2 = bfv.rotate_hoisted(P, keys, ct, [k])[0]
+    assert not np.array_equal(hz2.c[1], bfv.rotate(P, keys, ct, k).c[1])
+
+
 def test_keys_do_not_depend_on_t():
     # BFV keys involve only s and Q*P; the same keys serve every t_i.
     P1, P2 = mkparams(32, t=65537), mkparams(32, t=W.T30[0])
