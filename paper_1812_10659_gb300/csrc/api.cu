@@ -316,9 +316,9 @@ int lola_rotate_hoisted(lola_ctx* ctx, const lola_keys* keys, const uint64_t* in
 int lola_multiply(lola_ctx* ctx, const lola_keys* keys, const uint64_t* a, const uint64_t* b, uint64_t* out,
                   size_t count, const uint32_t* t_index, void* stream) {
   CHECK(ctx && keys && ((a && b && out) || !count), LOLA_E_PARAM, "null argument");
-  CHECK(out != a && out != b, LOLA_E_PARAM, "output must not alias an input");
   Ctx* c = ctx->c;
   if (!count) return LOLA_OK;
+  CHECK(out != a && out != b, LOLA_E_PARAM, "output must not alias an input");
   CHECK(keys->k->ev->relin, LOLA_E_NOKEY, "no relinearisation key");
   cudaStream_t s = to_stream(stream);
   std::vector<uint32_t> ti(count, 0);
