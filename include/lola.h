@@ -173,7 +173,7 @@ int lola_multiply(lola_ctx* ctx, const lola_keys* keys, const uint64_t* a, const
  * address (cudaGetSymbolAddress), so make it before any stream capture.
  * Calls share the array: calls that overlap on the GPU race and must be
  * serialised by the caller.  No part of the array needs clearing between
- * calls.  A count whose scratch (count * (2L + L*(L+K) + 2) * n words) does
+ * calls.  A count whose scratch (count * (L + L*(L+K) + 2) * n words) does
  * not fit returns LOLA_E_PARAM; missing key: LOLA_E_NOKEY. */
 #define LOLA_ROTATE_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
 int lola_rotate_noalloc(lola_ctx* ctx, const lola_keys* keys, const uint64_t* in, uint64_t* out, size_t count,

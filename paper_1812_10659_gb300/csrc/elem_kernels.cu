@@ -55,19 +55,22 @@ __global__ void ke_ks_ip(const CtxDev* __restrict__ C, KsDev a, int final_out) {
     const PrimeDev& P = C->pr[j];
     const uint64_t* key = a.d_keys ? a.d_keys[ct / a.gal_div] : a.key;
     const size_t src = a.src_mod ? ct % a.src_mod : ct;
-    size_t kd = k;
+    size_t kd = k;                                // gathered pair of tau_g (D and/or c0)
     bool swp = false;
-    if (a.ip_gather) {
+    const bool gather_c0 = a.ip_gather || a.c0_gather;
+    if (gather_c0) {
       const uint32_t g = a.d_gal ? a.d_gal[ct / a.gal_div] : a.gal;
       const uint32_t m = gal_src((uint32_t)k, g, logn);
       kd = m & ~1u;
       swp = (m & 1u) != 0;
     }
+    const size_t kD = a.ip_gather ? kd : k;
+    const bool swpD = a.ip_gather && swp;
     uint64_t acc0[2] = {0, 0}, acc1[2] = {0, 0};
     unsigned __int128 s0[2] = {0, 0}, s1[2] = {0, 0};
     for (int i = 0; i < L; ++i) {
-      ulonglong2 d = *(const ulonglong2*)(a.D + ((src * L + i) * LK + j) * n + kd);
-      if (swp) d = make_ulonglong2(d.y, d.x);
+      ulonglong2 d = *(const ulonglong2*)(a.D + ((src * L + i) * LK + j) * n + kD);
+      if (swpD) d = make_ulonglong2(d.y, d.x);
       const ulonglong2 k0 = __ldg((const ulonglong2*)(key + ((size_t)i * LK + j) * n + k));
       const ulonglong2 k1 = __ldg((const ulonglong2*)(key + ((size_t)(L + i) * LK + j) * n + k));
       s0[0] += (unsigned __int128)d.x * k0.x;
@@ -91,7 +94,7 @@ __global__ void ke_ks_ip(const CtxDev* __restrict__ C, KsDev a, int final_out) {
         const size_t kk = k + e;
         uint64_t v0 = acc0[e], v1 = acc1[e];
         if (a.c0p) v0 = add_mod(v0, a.c0p[(ct * L + j) * n + kk], P.q);
-        else if (a.ip_gather) v0 = add_mod(v0, a.c0[(src * 2 * L + j) * n + (kd + (e ^ (int)swp))], P.q);
+        else if (gather_c0) v0 = add_mod(v0, a.c0[(src * 2 * L + j) * n + (kd + (e ^ (int)swp))], P.q);
         else if (a.c0) v0 = add_mod(v0, a.c0[(ct * 2 * L + j) * n + kk], P.q);
         if (a.add1) v1 = add_mod(v1, a.add1[(ct * 2 * L + L + j) * n + kk], P.q);
         if (a.accum) {
@@ -111,7 +114,7 @@ __global__ void ke_ks_ip(const CtxDev* __restrict__ C, KsDev a, int final_out) {
           const size_t kk = k + e;
           uint64_t s0v = 0, s1v = 0;
           if (a.c0p) s0v = a.c0p[(ct * L + j) * n + kk];
-          else if (a.ip_gather) s0v = a.c0[(src * 2 * L + j) * n + (kd + (e ^ (int)swp))];
+          else if (gather_c0) s0v = a.c0[(src * 2 * L + j) * n + (kd + (e ^ (int)swp))];
           else if (a.c0) s0v = a.c0[(ct * 2 * L + j) * n + kk];
           if (a.add1) s1v = a.add1[(ct * 2 * L + L + j) * n + kk];
           if (a.accum) {

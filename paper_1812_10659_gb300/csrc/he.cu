@@ -114,7 +114,7 @@ struct AsyncBuf {
 // over D's digit rows 0 and 1 (a separate [count][2][L+K][n] area when L = 1).
 size_t rotate_scratch_words(const Ctx* c, size_t count) {
   const size_t LK = c->L + c->K;
-  size_t w = count * (2 * c->L + c->L * LK + 2) * (size_t)c->n;
+  size_t w = count * (c->L + c->L * LK + 2) * (size_t)c->n;   // digits, D, x_P
   if (c->L < 2) w += count * 2 * LK * (size_t)c->n;
   return w;
 }
@@ -148,7 +148,8 @@ int rotate(Ctx* c, const uint64_t* in, uint64_t* out, const uint64_t* accum, siz
   a.dig = scratch;
   a.D = a.dig + count * L * n;
   a.xP = a.D + count * L * LK * n;
-  a.c0p = a.xP + count * 2 * n;
+  a.c0p = nullptr;                            // the inner product gathers tau_g(c0)
+  a.c0_gather = 1;
   a.count = count;
   a.d_gal = r.d_gal;
   a.gal = r.gal;
@@ -157,7 +158,7 @@ int rotate(Ctx* c, const uint64_t* in, uint64_t* out, const uint64_t* accum, siz
   a.gal_div = r.div ? r.div : 1;
   TRY(k::ks_decompose(c, a, s));
   TRY(k::ks_modup(c, a, true, s));
-  return ks_finish(c, a, a.c0p + count * L * n, s);
+  return ks_finish(c, a, a.xP + count * 2 * n, s);
 }
 
 // Hoisted rotations: every one of `count` ciphertexts rotated by each of

@@ -54,6 +54,9 @@ struct KsDev {
   // (0: i) through tau_g in the NTT domain (D and c0 not permuted beforehand)
   uint32_t src_mod;
   uint32_t ip_gather;
+  // rotation: the inner product adds tau_g(c0) by gathering c0 itself (the
+  // decompose kernel then writes no c0p)
+  uint32_t c0_gather;
 };
 
 namespace k {

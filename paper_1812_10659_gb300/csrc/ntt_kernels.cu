@@ -160,10 +160,11 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T) kn_enc_msg(const CtxDev* __restr
 
 // ------------------------------------------------------------- key switching
 // A: the Galois automorphism in NTT form is a permutation of positions.
-//    Load c0 limb i and c1 limb i coalesced and scatter them through the
-//    inverse permutation into shared memory; write tau_g(c0) and the permuted
-//    c1 limb (the diagonal block D[i][i]) back coalesced; inverse-transform the
-//    permuted c1 limb into digit i.
+//    Load c1 limb i coalesced and scatter it through the inverse permutation
+//    into shared memory; write the permuted limb (the diagonal block D[i][i])
+//    back coalesced; inverse-transform it into digit i.  When c0p is given,
+//    tau_g(c0) is written the same way first (otherwise the inner product
+//    gathers it).
 template <int LOGN>
 __global__ void __launch_bounds__(Cfg<LOGN>::T) kn_ks_decompose(const CtxDev* __restrict__ C, KsDev a) {
   extern __shared__ uint64_t sm[];
@@ -176,24 +177,26 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T) kn_ks_decompose(const CtxDev* __
   const int tid = threadIdx.x;
   const uint64_t* src0 = a.c1 + (ct * 2 * L + i) * (size_t)N;
   const uint64_t* src1 = a.c1 + (ct * 2 * L + L + i) * (size_t)N;
-  uint64_t* c0p = a.c0p + (ct * L + i) * (size_t)N;
   uint64_t* diag = a.D + ((ct * L + i) * LK + i) * (size_t)N;
   uint64_t* dig = a.dig + (ct * L + i) * (size_t)N;
   const PrimeDev& P = C->pr[i];
-  // tau_g(c0): all loads of the thread first (the compiler may not move a
-  // global load above a shared store through a generic pointer)
   uint64_t v[N / T];
+  if (a.c0p) {
+    // tau_g(c0): all loads of the thread first (the compiler may not move a
+    // global load above a shared store through a generic pointer)
+    uint64_t* c0p = a.c0p + (ct * L + i) * (size_t)N;
 #pragma unroll
-  for (int k = 0; k < N / T; ++k) v[k] = src0[tid + k * T];
+    for (int k = 0; k < N / T; ++k) v[k] = src0[tid + k * T];
 #pragma unroll
-  for (int k = 0; k < N / T; ++k) sm[swz<LOGE>(gal_dst(tid + k * T, ginv, LOGN))] = v[k];
-  __syncthreads();
+    for (int k = 0; k < N / T; ++k) sm[swz<LOGE>(gal_dst(tid + k * T, ginv, LOGN))] = v[k];
+    __syncthreads();
 #pragma unroll 4
-  for (int k = 0; k < N / T; ++k) {
-    const int idx = tid + k * T;
-    c0p[idx] = sm[swz<LOGE>(idx)];
+    for (int k = 0; k < N / T; ++k) {
+      const int idx = tid + k * T;
+      c0p[idx] = sm[swz<LOGE>(idx)];
+    }
+    __syncthreads();
   }
-  __syncthreads();
   // tau_g(c1): diagonal block, then digit
 #pragma unroll
   for (int k = 0; k < N / T; ++k) v[k] = src1[tid + k * T];
@@ -377,30 +380,35 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(cl_threads<CL_LOGE>(
   const int tid = threadIdx.x;
   const uint64_t* src0 = a.c1 + (ct * 2 * L + i) * (size_t)N;
   const uint64_t* src1 = a.c1 + (ct * 2 * L + L + i) * (size_t)N;
-  uint64_t* c0p = a.c0p + (ct * L + i) * (size_t)N;
   uint64_t* diag = a.D + ((ct * L + i) * LK + i) * (size_t)N;
   uint64_t* dig = a.dig + (ct * L + i) * (size_t)N;
   const PrimeDev& P = C->pr[i];
-  // tau_g(c0): this CTA reads its chunk of c0 and scatters through the inverse
-  // permutation; the peers must have started before their shared memory is
-  // written, a barrier overlapped with the loads
+  // the peers must have started before their shared memory is written: a
+  // cluster barrier, overlapped with the first loads
   cl.barrier_arrive();
-  uint64_t v[NC / T];
+  if (a.c0p) {
+    // tau_g(c0): this CTA reads its chunk of c0 and scatters through the
+    // inverse permutation (c0p is the same for the whole cluster)
+    uint64_t* c0p = a.c0p + (ct * L + i) * (size_t)N;
+    uint64_t v[NC / T];
 #pragma unroll
-  for (int k = 0; k < NC / T; ++k) v[k] = src0[(h << LOGNL) + tid + k * T];
-  cl.barrier_wait();
+    for (int k = 0; k < NC / T; ++k) v[k] = src0[(h << LOGNL) + tid + k * T];
+    cl.barrier_wait();
 #pragma unroll
-  for (int k = 0; k < NC / T; ++k) {
-    const uint32_t d = gal_dst((h << LOGNL) + tid + k * T, ginv, CL_LOGN);
-    cl.map_shared_rank(sm, (int)(d >> LOGNL))[swz<LOGE>(d & (NC - 1))] = v[k];
-  }
-  cl.sync();
+    for (int k = 0; k < NC / T; ++k) {
+      const uint32_t d = gal_dst((h << LOGNL) + tid + k * T, ginv, CL_LOGN);
+      cl.map_shared_rank(sm, (int)(d >> LOGNL))[swz<LOGE>(d & (NC - 1))] = v[k];
+    }
+    cl.sync();
 #pragma unroll 4
-  for (int k = 0; k < NC / T; ++k) {
-    const int li = tid + k * T;
-    c0p[(h << LOGNL) + li] = sm[swz<LOGE>(li)];
+    for (int k = 0; k < NC / T; ++k) {
+      const int li = tid + k * T;
+      c0p[(h << LOGNL) + li] = sm[swz<LOGE>(li)];
+    }
+    cl.sync();
+  } else {
+    cl.barrier_wait();
   }
-  cl.sync();
   // tau_g(c1): diagonal block, then the digit
 #pragma unroll 4
   for (int k = 0; k < NC / T; ++k) {

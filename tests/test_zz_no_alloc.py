@@ -45,7 +45,7 @@ def test_rotate_noalloc_matches_rotate_twice():
                     for ti in range(kt):
                         assert np.array_equal(res[m, ti], want % ps.t[ti])
             # a request larger than the static scratch area is refused, not truncated
-            per_ct = (2 * ps.L + ps.L * (ps.L + ps.K) + 2) * n * 8
+            per_ct = (ps.L + ps.L * (ps.L + ps.K) + 2) * n * 8
             too_many = Lb.NOALLOC_SCRATCH_BYTES // per_ct + 1
             big_in = Lb.lola_ct_create(ctx, too_many)
             big_out = Lb.lola_ct_create(ctx, too_many)
