@@ -1,0 +1,167 @@
+// 2-CTA thread-block cluster versions of the key-switching transforms at
+// n = 16384 (geometry and launch macro in ntt_common.cuh).
+#include "ntt_common.cuh"
+
+namespace lola {
+
+template <int CL_LOGE>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(cl_threads<CL_LOGE>(), 2)
+    kc_ks_modup(const CtxDev* __restrict__ C, KsDev a, int skip_diag) {
+  extern __shared__ uint64_t sm[];
+  constexpr int N = 1 << CL_LOGN;
+  const int L = C->L, LK = C->L + C->K;
+  const int per = skip_diag ? L * (LK - 1) : L * LK;
+  const size_t unit = blockIdx.x >> 1;
+  const size_t ct = unit / per;
+  const int r = unit % per;
+  const int i = r / (skip_diag ? LK - 1 : LK);
+  int j = r % (skip_diag ? LK - 1 : LK);
+  if (skip_diag && j >= i) ++j;
+  const uint64_t* dig = a.dig + (ct * L + i) * (size_t)N;
+  uint64_t* dst = a.D + ((ct * L + i) * LK + j) * (size_t)N;
+  const PrimeDev& P = C->pr[j];
+  const bool raw = C->modup_raw != 0;
+  ncl::ntt_forward_cluster<CL_LOGN, CL_LOGE, CL_LOGC>(sm, C->tw_fwd + (size_t)j * (2u << CL_LOGN), P.q, P.f64,
+                                                [&](int k) { return raw ? dig[k] : reduce64(dig[k], P.q, P.f64); },
+                                                [&](int k, uint64_t v) { dst[k] = v; });
+}
+
+template <int CL_LOGE>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(cl_threads<CL_LOGE>(), 2) kc_ks_intt_p(const CtxDev* __restrict__ C, KsDev a) {
+  extern __shared__ uint64_t sm[];
+  constexpr int N = 1 << CL_LOGN;
+  const int LK = C->L + C->K, ip = C->iP;
+  const size_t unit = blockIdx.x >> 1;
+  const size_t ct = unit >> 1;
+  const int comp = unit & 1;
+  const PrimeDev& P = C->pr[ip];
+  const uint64_t* src = a.acc + ct * a.acc_stride + (size_t)(comp * LK + ip) * N;
+  uint64_t* dst = a.xP + (ct * 2 + comp) * (size_t)N;
+  ncl::ntt_inverse_cluster<CL_LOGN, CL_LOGE, CL_LOGC>(sm, C->tw_inv + (size_t)ip * (2u << CL_LOGN), P.q, P.ninv, P.ninv_s,
+                                                [&](int k) { return src[k]; },
+                                                [&](int k, uint64_t v) { dst[k] = v; });
+}
+
+template <int CL_LOGE>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(cl_threads<CL_LOGE>(), 2) kc_ks_moddown(const CtxDev* __restrict__ C, KsDev a) {
+  extern __shared__ uint64_t sm[];
+  constexpr int N = 1 << CL_LOGN;
+  const int L = C->L, LK = C->L + C->K;
+  const size_t unit = blockIdx.x >> 1;
+  const size_t ct = unit / (2 * L);
+  const int r = unit % (2 * L);
+  const int comp = r / L, j = r % L;
+  const uint64_t* accp = a.acc + ct * a.acc_stride + (size_t)(comp * LK + j) * N;
+  const PrimeDev& P = C->pr[j];
+  const uint64_t Phalf = (C->pr[C->iP].q - 1) / 2, q2m1 = 2 * P.q - 1;
+  const uint64_t Pinv = C->PinvQ[j], Pinv_s = C->PinvQ_s[j];
+  const uint64_t* x = a.xP + (ct * 2 + comp) * (size_t)N;
+  uint64_t* dst = a.out + ((ct * 2 + comp) * L + j) * (size_t)N;
+  ncl::ntt_forward_cluster<CL_LOGN, CL_LOGE, CL_LOGC>(
+      sm, C->tw_fwd + (size_t)j * (2u << CL_LOGN), P.q, P.f64,
+      [&](int k) {
+        const uint64_t v = x[k];
+        return shoup_mul_lazy(v, Pinv, Pinv_s, P.q) + (v > Phalf ? q2m1 : 0);
+      },
+      ModDownStore{accp, dst, P.q});
+}
+
+template <int CL_LOGE>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(cl_threads<CL_LOGE>(), 2) kc_ks_decompose(const CtxDev* __restrict__ C, KsDev a) {
+  extern __shared__ uint64_t sm[];
+  namespace cg = cooperative_groups;
+  constexpr int N = 1 << CL_LOGN, LOGE = CL_LOGE, LOGNL = CL_LOGN - CL_LOGC, NC = 1 << LOGNL;
+  constexpr int T = N >> (LOGE + CL_LOGC);
+  cg::cluster_group cl = cg::this_cluster();
+  const int h = (int)cl.block_rank();
+  const int L = C->L, LK = C->L + C->K;
+  const size_t unit = blockIdx.x >> 1;
+  const size_t ct = unit / L;
+  const int i = unit % L;
+  const uint32_t g = a.d_gal ? a.d_gal[ct / a.gal_div] : a.gal;
+  const uint32_t ginv = inv_odd32(g) & ((2u << CL_LOGN) - 1);
+  const int tid = threadIdx.x;
+  const uint64_t* src0 = a.c1 + (ct * 2 * L + i) * (size_t)N;
+  const uint64_t* src1 = a.c1 + (ct * 2 * L + L + i) * (size_t)N;
+  uint64_t* diag = a.D + ((ct * L + i) * LK + i) * (size_t)N;
+  uint64_t* dig = a.dig + (ct * L + i) * (size_t)N;
+  const PrimeDev& P = C->pr[i];
+  // the peers must have started before their shared memory is written: a
+  // cluster barrier, overlapped with the first loads
+  cl.barrier_arrive();
+  if (a.c0p) {
+    // tau_g(c0): this CTA reads its chunk of c0 and scatters through the
+    // inverse permutation (c0p is the same for the whole cluster)
+    uint64_t* c0p = a.c0p + (ct * L + i) * (size_t)N;
+    uint64_t v[NC / T];
+#pragma unroll
+    for (int k = 0; k < NC / T; ++k) v[k] = src0[(h << LOGNL) + tid + k * T];
+    cl.barrier_wait();
+#pragma unroll
+    for (int k = 0; k < NC / T; ++k) {
+      const uint32_t d = gal_dst((h << LOGNL) + tid + k * T, ginv, CL_LOGN);
+      cl.map_shared_rank(sm, (int)(d >> LOGNL))[swz<LOGE>(d & (NC - 1))] = v[k];
+    }
+    cl.sync();
+#pragma unroll 4
+    for (int k = 0; k < NC / T; ++k) {
+      const int li = tid + k * T;
+      c0p[(h << LOGNL) + li] = sm[swz<LOGE>(li)];
+    }
+    cl.sync();
+  } else {
+    cl.barrier_wait();
+  }
+  // tau_g(c1): diagonal block, then the digit
+#pragma unroll 4
+  for (int k = 0; k < NC / T; ++k) {
+    const int idx = (h << LOGNL) + tid + k * T;
+    const uint32_t d = gal_dst(idx, ginv, CL_LOGN);
+    cl.map_shared_rank(sm, (int)(d >> LOGNL))[swz<LOGE>(d & (NC - 1))] = src1[idx];
+  }
+  cl.sync();
+#pragma unroll 4
+  for (int k = 0; k < NC / T; ++k) {
+    const int li = tid + k * T;
+    diag[(h << LOGNL) + li] = sm[swz<LOGE>(li)];
+  }
+  ncl::ntt_inverse_cluster_smem<CL_LOGN, LOGE, CL_LOGC>(sm, C->tw_inv + (size_t)i * (2u << CL_LOGN), P.q, P.ninv,
+                                                        P.ninv_s, [&](int k2, uint64_t v) { dig[k2] = v; });
+}
+
+namespace k {
+int ks_decompose_cluster(Ctx* c, const KsDev& a, cudaStream_t s, bool small) {
+  if (small)
+    LOLA_LAUNCH_CLUSTER(kc_ks_decompose<4>, a.count * c->L, cl_threads<4>(), s, c->dev, a);
+  else
+    LOLA_LAUNCH_CLUSTER(kc_ks_decompose<5>, a.count * c->L, cl_threads<5>(), s, c->dev, a);
+  return post_launch(c, s);
+}
+
+int ks_modup_cluster(Ctx* c, const KsDev& a, bool skip_diag, cudaStream_t s, bool small) {
+  const uint32_t LK = c->L + c->K;
+  const size_t per = skip_diag ? (size_t)c->L * (LK - 1) : (size_t)c->L * LK;
+  if (small)
+    LOLA_LAUNCH_CLUSTER(kc_ks_modup<4>, a.count * per, cl_threads<4>(), s, c->dev, a, (int)skip_diag);
+  else
+    LOLA_LAUNCH_CLUSTER(kc_ks_modup<5>, a.count * per, cl_threads<5>(), s, c->dev, a, (int)skip_diag);
+  return post_launch(c, s);
+}
+
+int ks_intt_p_cluster(Ctx* c, const KsDev& a, cudaStream_t s, bool small) {
+  if (small)
+    LOLA_LAUNCH_CLUSTER(kc_ks_intt_p<4>, a.count * 2, cl_threads<4>(), s, c->dev, a);
+  else
+    LOLA_LAUNCH_CLUSTER(kc_ks_intt_p<5>, a.count * 2, cl_threads<5>(), s, c->dev, a);
+  return post_launch(c, s);
+}
+
+int ks_moddown_cluster(Ctx* c, const KsDev& a, cudaStream_t s, bool small) {
+  if (small)
+    LOLA_LAUNCH_CLUSTER(kc_ks_moddown<4>, a.count * 2 * c->L, cl_threads<4>(), s, c->dev, a);
+  else
+    LOLA_LAUNCH_CLUSTER(kc_ks_moddown<5>, a.count * 2 * c->L, cl_threads<5>(), s, c->dev, a);
+  return post_launch(c, s);
+}
+}  // namespace k
+}  // namespace lola
