@@ -427,3 +427,19 @@ def test_cifar_plan_matches_integer_network():
     # place: 40 + 40 + 2 shifted groups + 1 row swap; 4075 + 10 outputs x 14 rotations
     assert ev.c == {"rot": 83 + 4085 * 14, "mul_plain": 2 + 4075 + 4075 + 10, "mul_scalar": 83 * 192,
                     "square": 2}
+
+
+def test_cifar_second_convolution_matrix_is_the_convolution():
+    # the dense matrix the second layer is evaluated as equals a direct
+    # 6x6x83 stride-2 convolution of the 14x14x83 first-layer output
+    net = W.cifar_net()
+    D = W.cifar_dense2(net)
+    maps1, o1, o2, k2, s = net.w1.shape[0], net.o1, net.o2, net.k2, net.stride
+    h1 = np.random.default_rng(6).integers(-50, 50, size=(maps1, o1, o1))
+    direct = []
+    for o in range(net.w2.shape[0]):
+        K = net.w2[o].reshape(maps1, k2, k2)
+        for i in range(o2):
+            for j in range(o2):
+                direct.append(int((K * h1[:, s * i:s * i + k2, s * j:s * j + k2]).sum()))
+    assert [int(v) for v in D @ h1.reshape(-1)] == direct
