@@ -444,6 +444,16 @@ def run_ours(args):
         b.record(stream)
         torch.cuda.synchronize()
         plain_ms.append(a.elapsed_time(b))
+    # one more plain evaluation with per-kernel CUDA-event timing (not in the latency figures)
+    L.lola_profile_enable(ctx, -1, True)
+    L.lola_eval_network(ctx, ev, net, ct1_in, ct1_out, stream, graph=False)
+    torch.cuda.synchronize()
+    plain_kernels = {}
+    for k in range(L.lola_profile_kinds()):
+        ms, cnt, _ = L.lola_profile_read(ctx, k)
+        if cnt:
+            plain_kernels[L.lola_profile_name(k)] = {"ms": ms, "launches": cnt}
+    L.lola_profile_enable(ctx, -1, False)
 
     # ---- per-kernel device time over profiled batched steps (eager, CUDA events)
     launches0 = L.lola_launch_count(ctx)
@@ -515,6 +525,8 @@ def run_ours(args):
                            "plain_p50": statistics.median(plain_ms),
                            "plain_p99": sorted(plain_ms)[min(len(plain_ms) - 1, int(0.99 * len(plain_ms)))]},
             "plain": {"value": 1000.0 / statistics.median(plain_ms), "unit": "inferences/s", "batch": 1,
+                      "kernels_ms": {k: round(v["ms"], 3) for k, v in sorted(plain_kernels.items(), key=lambda kv: -kv[1]["ms"])},
+                      "launches": sum(v["launches"] for v in plain_kernels.values()),
                       "graph": False},
             "ntt_gbs": ntt_gbs,
             "roofline": roofline,

@@ -171,7 +171,7 @@ static size_t hoisted_chunk(size_t count, size_t S) { return std::min(S, std::ma
 
 size_t rotate_hoisted_scratch_words(const Ctx* c, size_t count, size_t S) {
   const size_t n = c->n, L = c->L, LK = c->L + c->K;
-  return count * (2 * L + L * LK) * n + hoisted_chunk(count, S) * count * (2 * LK + 2) * n;
+  return count * (L + L * LK) * n + hoisted_chunk(count, S) * count * (2 * LK + 2) * n;
 }
 
 int rotate_hoisted(Ctx* c, const uint64_t* in, uint64_t* out, size_t count, size_t S, const uint32_t* d_gal,
@@ -184,7 +184,7 @@ int rotate_hoisted(Ctx* c, const uint64_t* in, uint64_t* out, size_t count, size
   a.c1 = in;
   a.dig = scratch;
   a.D = a.dig + count * L * n;
-  a.c0p = a.D + count * L * LK * n;          // written by decompose (identity), not read
+  a.c0p = nullptr;                            // the inner product gathers tau_g(c0)
   a.count = count;
   a.gal = 1;
   a.gal_div = 1;
@@ -196,7 +196,7 @@ int rotate_hoisted(Ctx* c, const uint64_t* in, uint64_t* out, size_t count, size
     b.c0 = in;
     b.out = out + s0 * count * c->ct_words();
     b.D = a.D;
-    b.acc = a.c0p + count * L * n;
+    b.acc = a.D + count * L * LK * n;
     b.acc_stride = 2 * LK * n;
     b.xP = b.acc + sc * count * 2 * LK * n;
     b.count = sc * count;
