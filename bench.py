@@ -413,21 +413,47 @@ def run_ours(args):
         got = [int(dec[m, s]) for m, s in net.output_map()]
         correct = got == want
 
-    # ---- e2e through host buffers (pinned)
-    h_in = torch.empty(in_bytes // 8, dtype=torch.int64, pin_memory=True)
-    h_out = torch.empty(out_bytes // 8, dtype=torch.int64, pin_memory=True)
-    L.lola_ct_download(ctx, ct_in, h_in.data_ptr(), stream)
+    # ---- e2e through host buffers (pinned): every step uploads its input
+    # ciphertexts from pinned host memory and downloads its outputs; two
+    # buffer pairs and two copy streams let the copies of neighbouring steps
+    # overlap a step's evaluation (upload i+1 and download i-1 during step i)
+    h_in = [torch.empty(in_bytes // 8, dtype=torch.int64, pin_memory=True) for _ in range(2)]
+    h_out = [torch.empty(out_bytes // 8, dtype=torch.int64, pin_memory=True) for _ in range(2)]
+    ins = [ct_in, L.lola_ct_create(ctx, B * n_in)]
+    outs = [ct_out, L.lola_ct_create(ctx, B * 10)]
+    for hb in h_in:
+        L.lola_ct_download(ctx, ct_in, hb.data_ptr(), stream)
+    L.lola_eval_network(ctx, ev, net, ins[1], outs[1], stream)
     torch.cuda.synchronize()
+    up_s, down_s = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    up_done = [torch.cuda.Event() for _ in range(2)]
+    comp_done = [torch.cuda.Event() for _ in range(2)]
+    down_done = [torch.cuda.Event() for _ in range(2)]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     e0.record(stream)
-    for _ in range(args.steps):
-        L.lola_ct_upload(ctx, ct_in, h_in.data_ptr(), stream)
-        step()
-        L.lola_ct_download(ctx, ct_out, h_out.data_ptr(), stream)
+    up_s.wait_event(e0)
+    for i in range(args.steps):
+        b = i % 2
+        if i >= 2:
+            up_s.wait_event(comp_done[b])              # step i-2 has consumed ins[b]
+        L.lola_ct_upload(ctx, ins[b], h_in[b].data_ptr(), up_s)
+        up_done[b].record(up_s)
+        stream.wait_event(up_done[b])
+        if i >= 2:
+            stream.wait_event(down_done[b])            # outs[b] of step i-2 is on the host
+        L.lola_eval_network(ctx, ev, net, ins[b], outs[b], stream)
+        comp_done[b].record(stream)
+        down_s.wait_event(comp_done[b])
+        L.lola_ct_download(ctx, outs[b], h_out[b].data_ptr(), down_s)
+        down_done[b].record(down_s)
+    for ev_ in down_done[:min(2, args.steps)]:
+        stream.wait_event(ev_)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
+    L.lola_ct_destroy(ins[1])
+    L.lola_ct_destroy(outs[1])
     e2e_ms_max, e2e_units = aggregate(e2e_ms, B * args.steps, dist, dev)
     e2e_value = e2e_units / (e2e_ms_max / 1000.0)
 
