@@ -42,8 +42,11 @@ __device__ __forceinline__ uint64_t redc128(unsigned __int128 T, uint64_t q, uin
 // pair (k, k+1) maps to the aligned pair holding gal_src(k) and
 // gal_src(k) ^ 1, so each pair is still one 16-byte load (swapped when
 // gal_src(k) is odd).
+// LT > 0: the digit count as a compile-time constant (fully unrolled digit
+// loop, all loads of a thread issued together); 0: read it from the context.
+template <int LT>
 __global__ void ke_ks_ip(const CtxDev* __restrict__ C, KsDev a, int final_out) {
-  const int L = C->L, LK = C->L + C->K, logn = C->logn;
+  const int L = LT > 0 ? LT : C->L, LK = L + C->K, logn = C->logn;
   const size_t n = C->n, half = n >> 1;
   const int J = final_out ? L : LK;
   const size_t total = a.count * J * half;
@@ -68,7 +71,8 @@ __global__ void ke_ks_ip(const CtxDev* __restrict__ C, KsDev a, int final_out) {
     const bool swpD = a.ip_gather && swp;
     uint64_t acc0[2] = {0, 0}, acc1[2] = {0, 0};
     unsigned __int128 s0[2] = {0, 0}, s1[2] = {0, 0};
-    for (int i = 0; i < L; ++i) {
+#pragma unroll
+    for (int i = 0; i < (LT > 0 ? LT : L); ++i) {
       ulonglong2 d = *(const ulonglong2*)(a.D + ((src * L + i) * LK + j) * n + kD);
       if (swpD) d = make_ulonglong2(d.y, d.x);
       const ulonglong2 k0 = __ldg((const ulonglong2*)(key + ((size_t)i * LK + j) * n + k));
@@ -479,7 +483,15 @@ namespace k {
 
 int ks_ip(Ctx* c, const KsDev& a, bool final_out, cudaStream_t s) {
   const size_t pairs = a.count * (final_out ? c->L : c->L + c->K) * (c->n / 2);
-  ELEM_LAUNCH(KI_KS_IP_Q, ke_ks_ip, pairs, c->dev, a, (int)final_out);
+  switch (c->L) {
+    case 3: ELEM_LAUNCH(KI_KS_IP_Q, ke_ks_ip<3>, pairs, c->dev, a, (int)final_out); break;
+    case 4: ELEM_LAUNCH(KI_KS_IP_Q, ke_ks_ip<4>, pairs, c->dev, a, (int)final_out); break;
+    case 5: ELEM_LAUNCH(KI_KS_IP_Q, ke_ks_ip<5>, pairs, c->dev, a, (int)final_out); break;
+    case 6: ELEM_LAUNCH(KI_KS_IP_Q, ke_ks_ip<6>, pairs, c->dev, a, (int)final_out); break;
+    case 7: ELEM_LAUNCH(KI_KS_IP_Q, ke_ks_ip<7>, pairs, c->dev, a, (int)final_out); break;
+    case 8: ELEM_LAUNCH(KI_KS_IP_Q, ke_ks_ip<8>, pairs, c->dev, a, (int)final_out); break;
+    default: ELEM_LAUNCH(KI_KS_IP_Q, ke_ks_ip<0>, pairs, c->dev, a, (int)final_out); break;
+  }
   return post(c);
 }
 
