@@ -432,3 +432,50 @@ def test_full_cifar_decrypts_to_integer_network():
         net.destroy()
     finally:
         Lb.lola_ctx_destroy(ctx)
+
+
+def test_large_nonuniform_rotation_wave_is_chunked_exactly():
+    """A combine of 9 messages rotates 8 of them by different steps; at 200
+    requests the wave holds 1600 ciphertexts, more than one launch takes, so
+    it runs in chunks of whole messages.  Every request's output must equal
+    its single-request evaluation bit for bit and decrypt to the combined
+    vector."""
+    need_gpu()
+    Lb = lib()
+    n = 256
+    ps = W.params_small(n, L=3, K=1, t=W.T30[:1])
+    t = ps.t[0]
+    layers = [{"op": "conv", "weights": np.eye(9, dtype=np.int64)},
+              {"op": "combine", "stride": 10}]
+    g = np.random.default_rng(8)
+    B = 200
+    msgs = np.zeros((B, 9, n), np.int64)
+    msgs[:, :, :10] = g.integers(0, 1000, (B, 9, 10))
+    ctx = make_ctx(ps)
+    try:
+        net = Lb.lola_net_create(ctx, {"repr": "convolution", "n_msgs": 9, "n_elems": 10}, layers)
+        sk, ev = gpu_keys(Lb, ctx, net, 29)
+        ct = Lb.lola_encrypt(ctx, sk, msgs.reshape(B * 9, n), 4)
+        out = Lb.lola_ct_create(ctx, B)
+        Lb.lola_eval_network(ctx, ev, net, ct, out)
+        allw = Lb.lola_ct_export(ctx, out, (1, 2, ps.L, n))
+        for r in (0, 57, B - 1):
+            one_in = Lb.lola_ct_create(ctx, 9)
+            Lb.lola_ct_copy_messages(ctx, one_in, 0, ct, r * 9, 9)
+            one_out = Lb.lola_ct_create(ctx, 1)
+            Lb.lola_eval_network(ctx, ev, net, one_in, one_out)
+            single = Lb.lola_ct_export(ctx, one_out, (1, 2, ps.L, n))
+            assert np.array_equal(allw[r], single[0]), r
+            Lb.lola_ct_destroy(one_in)
+            Lb.lola_ct_destroy(one_out)
+        dec = Lb.lola_decrypt_residues(ctx, sk, out, 1, n)
+        omap = net.output_map()
+        for r in (0, B - 1):
+            assert [int(dec[r, 0, s]) for _, s in omap] == [int(msgs[r, m, e]) % t for m in range(9) for e in range(10)]
+        for h in (ct, out):
+            Lb.lola_ct_destroy(h)
+        Lb.lola_keys_destroy(sk)
+        Lb.lola_keys_destroy(ev)
+        net.destroy()
+    finally:
+        Lb.lola_ctx_destroy(ctx)
