@@ -111,3 +111,47 @@ def test_ragged_batch():
     g = np.random.default_rng(7)
     slots = [g.integers(0, 1 << 12, n) for _ in range(7)]
     run_primitives_vs_oracle(ps, slots, [1, 2, 3, 0, 100, 2047, 5], 41)
+
+
+def test_single_ciphertext_prime():
+    # L = 1: the key switch's inner products live in scratch of their own
+    need_gpu()
+    n = 1024
+    ps = W.ParamSet("L1", n, W.Q60[:2], 1, 1, [65537])
+    g = np.random.default_rng(3)
+    slots = [g.integers(0, 256, n), g.integers(0, 256, n)]
+    run_primitives_vs_oracle(ps, slots, [1, 0], 43)
+
+
+def test_hoisted_rotation_in_step_chunks():
+    """150 ciphertexts x 12 steps: the inner product runs in chunks of
+    floor(1024 / 150) = 6 steps; every output equals the oracle's hoisted
+    rotation."""
+    need_gpu()
+    Lb = lib()
+    n = 256
+    ps = W.params_small(n, L=3, K=1, t=W.T30[:1])
+    P = oracle_params(ps)
+    t = ps.t[0]
+    steps = list(range(1, 12)) + [0]
+    okeys = bfv.keygen(P, 47, rotations=steps[:-1], relin=False, row_swap=True)
+    ctx = make_ctx(ps)
+    try:
+        sk, ev = Lb.lola_keygen(ctx, 47, steps[:-1], Lb.LOLA_KEY_ROW_SWAP)
+        count = 150
+        slots = np.random.default_rng(9).integers(0, 1000, (count, n))
+        ct = Lb.lola_encrypt(ctx, sk, slots, 48)
+        out = Lb.lola_ct_create(ctx, count * len(steps))
+        Lb.lola_rotate_hoisted(ctx, ev, Lb.lola_ct_data(ct), Lb.lola_ct_data(out), count, steps)
+        got = Lb.lola_ct_export(ctx, out, (1, 2, ps.L, n)).reshape(len(steps), count, 2, ps.L, n)
+        for i in (0, 77, count - 1):
+            c = bfv.encrypt(P, okeys.pk, encoding.encode(slots[i], t), t, 48, i)
+            refs = bfv.rotate_hoisted(P, okeys, c, steps)
+            for si in (0, 5, 6, len(steps) - 1):                  # both sides of the chunk boundary
+                assert np.array_equal(got[si, i, 0], refs[si].c[0]) and np.array_equal(got[si, i, 1], refs[si].c[1]), (i, si)
+        for h in (ct, out):
+            Lb.lola_ct_destroy(h)
+        Lb.lola_keys_destroy(sk)
+        Lb.lola_keys_destroy(ev)
+    finally:
+        Lb.lola_ctx_destroy(ctx)
