@@ -28,6 +28,11 @@ row/column rotations) but not SEAL's internals.  The readings used here:
   g = 3^(n/2 - k) mod 2n followed by a key switch from tau_g(s) to s; it
   shifts each row of the 2 x n/2 slot matrix right by k (Sec. 3.1).  The row
   swap uses g = 2n - 1.
+* Modulus switching (not in the paper, which does not say how SEAL's
+  modulus is managed; it leaves every decrypted value unchanged): drop the
+  last prime q_l of Q, c' = round(c / q_l) mod Q / q_l, one prime at a
+  time.  Later operations use the first primes of Q, the same special prime
+  and the key entries of the kept digits and primes.
 """
 from __future__ import annotations
 
@@ -357,6 +362,64 @@ def rotate_hoisted(params: Params, keys: Keys, ct: Ciphertext, steps) -> list:
 def rotate_rows(params: Params, keys: Keys, ct: Ciphertext) -> Ciphertext:
     g = galois_row_swap(params.n)
     return apply_galois(params, ct, g, keys.galois[g])
+
+
+# ------------------------------------------------------ modulus switching
+
+def params_at_level(params: Params, Lv: int) -> Params:
+    """Parameters of a ciphertext that keeps the first Lv primes of Q (after
+    modulus switching); the special prime and the plaintext moduli stay."""
+    assert 1 <= Lv <= params.L
+    return Params(params.n, params.q[:Lv] + params.q[params.L:], Lv, params.K, params.t)
+
+
+def keys_at_level(keys: Keys, Lv: int) -> Keys:
+    """The key set restricted to level Lv: public key on q_0..q_{Lv-1};
+    switching keys on digits i < Lv and primes q_0..q_{Lv-1} plus the special
+    prime.  Every kept entry is unchanged, and it is what gen_switch_key
+    defines for those digits and primes (b_i = -a_i s + e_i + [P]_{q_i} s' on
+    prime i), so the restriction is a key set of params_at_level."""
+    full = keys.params
+    sel = list(range(Lv)) + list(range(full.L, full.L + full.K))
+
+    def cut(k):
+        return None if k is None else KeySwitchKey(k.b[:Lv][:, sel], k.a[:Lv][:, sel])
+
+    return Keys(params_at_level(full, Lv), keys.sk, PublicKey(keys.pk.p0[:Lv], keys.pk.p1[:Lv]),
+                cut(keys.relin), {g: cut(k) for g, k in keys.galois.items()})
+
+
+def mod_switch(params: Params, ct: Ciphertext) -> Ciphertext:
+    """Modulus switching from Q to Q' = Q / q_l, q_l the last prime of Q:
+    every coefficient x mod Q becomes round(x / q_l) mod Q'.  In RNS this is
+    exact: x - x~ is divisible by q_l when x~ is the centered residue of x
+    mod q_l, so c'_j = (c_j - x~) q_l^-1 mod q_j for every other prime.  The
+    result decrypts under params_at_level(params, L - 1) to the same message
+    (Delta' = floor(Q'/t); the noise is divided by q_l and gains a rounding
+    term below (1 + n) / 2 + t)."""
+    L = params.L
+    assert L >= 2 and all(x.shape[0] == L for x in ct.c)
+    ql = params.q[L - 1]
+    out = []
+    for x in ct.c:
+        top = x[L - 1].astype(np.int64)
+        xt = np.where(top > ql // 2, top - ql, top)            # centered residue mod q_l
+        limbs = []
+        for j in range(L - 1):
+            qj = params.q[j]
+            v = np.mod(x[j].astype(np.int64) - xt, np.int64(qj)).astype(np.uint64)
+            limbs.append(ring.vec_scalar_mul(v, pow(ql, -1, qj), qj))
+        out.append(np.stack(limbs))
+    return Ciphertext(out, ct.t)
+
+
+def mod_switch_to(params: Params, ct: Ciphertext, Lv: int) -> Ciphertext:
+    """Drop primes from the top one at a time until Lv remain."""
+    p = params
+    while p.L > Lv:
+        ct = mod_switch(p, ct)
+        p = params_at_level(p, p.L - 1)
+    return ct
 
 
 @lru_cache(maxsize=None)

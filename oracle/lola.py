@@ -21,6 +21,8 @@ Layer list entries (dicts):
   {"op": "interleaved_rowmajor", "weights": W}          Sec. 4.2.2 interleaved vector - row major
   {"op": "dense_rowmajor", "weights": W}                Sec. 4.2.2 dense vector - row major
   {"op": "sparse_colmajor", "weights": W}               Sec. 4.2.2 sparse vector - column major
+  {"op": "mod_switch", "L": Lv}                         keep the first Lv primes of Q (modulus
+                                                        switching; no change to any slot value)
 """
 from __future__ import annotations
 
@@ -64,12 +66,16 @@ class SlotEval:
     def square(self, a):
         return (a * a) % self.t
 
+    def mod_switch(self, msgs, Lv):
+        return msgs
+
 
 class HEEval:
     """The same steps on oracle ciphertexts."""
 
     def __init__(self, params: bfv.Params, keys: bfv.Keys, t: int):
         self.p, self.keys, self.t = params, keys, t
+        self.full_keys = keys
         self.n = params.n
         self.counts = {"rot": 0, "mul_plain": 0, "mul_scalar": 0, "square": 0, "add": 0}
 
@@ -100,6 +106,13 @@ class HEEval:
     def square(self, a):
         self.counts["square"] += 1
         return bfv.square(self.p, self.keys, a)
+
+    def mod_switch(self, msgs, Lv):
+        """Every message to level Lv; later steps run at that level."""
+        out = [bfv.mod_switch_to(self.p, m, Lv) for m in msgs]
+        self.p = bfv.params_at_level(self.p, Lv)
+        self.keys = bfv.keys_at_level(self.full_keys, Lv)
+        return out
 
 
 # ------------------------------------------------------------------ the plan
@@ -247,6 +260,12 @@ def layer_square(ev, st: State) -> State:
     return State([ev.square(x) for x in st.msgs], st.pos, st.block, st.copies)
 
 
+def layer_mod_switch(ev, st: State, Lv: int) -> State:
+    """Modulus switching of every message to the first Lv primes of Q: the
+    same slots, less work for every later step (not in the paper)."""
+    return State(ev.mod_switch(st.msgs, Lv), st.pos, st.block, st.copies)
+
+
 def layer_stack(ev, st: State, d: int, copies: int) -> State:
     """Stacked representation (Sec. 4.2.1): copies of the vector every 2^d
     slots.  Built by x <- x + rot(x, s) for s = 2^d, 2^(d+1), ... within a
@@ -377,6 +396,8 @@ def run_network(ev, layers, st: State) -> State:
             st = layer_interleaved_rowmajor(ev, st, L["weights"])
         elif op == "sparse_colmajor":
             st = layer_sparse_colmajor(ev, st, L["weights"])
+        elif op == "mod_switch":
+            st = layer_mod_switch(ev, st, L["L"])
         else:
             raise ValueError(op)
     return st

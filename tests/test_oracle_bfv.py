@@ -277,3 +277,71 @@ def test_full_size_rotation_and_square():
     assert np.array_equal(encoding.decode(bfv.decrypt(P, keys.sk, r), t), row_shift(v, 1))
     s = bfv.square(P, keys, c)
     assert np.array_equal(encoding.decode(bfv.decrypt(P, keys.sk, s), t), v * v)
+
+
+# --------------------------------------------------------- modulus switching
+
+def test_mod_switch_is_rounded_division_by_the_dropped_prime():
+    # Each coefficient x mod Q must become round(x / q_l) mod Q / q_l,
+    # checked with bignums on the CRT lift (random residues, and the two
+    # residues next to the rounding boundary q_l / 2)
+    P = mkparams(16, L=3)
+    ql = P.q[P.L - 1]
+    g = np.random.default_rng(11)
+    res = np.stack([g.integers(0, q, 16, dtype=np.uint64) for q in P.q[:P.L]])
+    res[2, 0], res[2, 1] = (ql - 1) // 2, (ql + 1) // 2
+    ct = bfv.Ciphertext([res, res.copy()], P.t[0])
+    out = bfv.mod_switch(P, ct)
+    P2 = bfv.params_at_level(P, 2)
+    assert out.c[0].shape == (2, 16) and P2.Q * ql == P.Q
+    for x, y in zip(P.qbasis.lift(res), P2.qbasis.lift(out.c[0])):
+        assert y == ((2 * x + ql) // (2 * ql)) % P2.Q
+
+
+def test_mod_switch_keeps_the_message_and_lower_levels_compute(small):
+    # decryption is unchanged at every level; at level 2 and 1 the restricted
+    # keys still rotate and relinearise correctly (Sec. 3.1 semantics)
+    P, keys = small
+    v = np.random.default_rng(12).integers(0, 16, P.n)
+    c = enc(P, keys, v)
+    for Lv in (2, 1):
+        cl = bfv.mod_switch_to(P, c, Lv)
+        Pl, kl = bfv.params_at_level(P, Lv), bfv.keys_at_level(keys, Lv)
+        assert np.array_equal(dec(Pl, kl, cl), v)
+        assert np.array_equal(dec(Pl, kl, bfv.rotate(Pl, kl, cl, 7)), row_shift(v, 7))
+        assert np.array_equal(dec(Pl, kl, bfv.rotate_rows(Pl, kl, cl)), np.concatenate([v[16:], v[:16]]))
+    Pl, kl = bfv.params_at_level(P, 2), bfv.keys_at_level(keys, 2)
+    sq = bfv.square(Pl, kl, bfv.mod_switch_to(P, c, 2))
+    assert np.array_equal(dec(Pl, kl, sq), (v * v) % 65537)
+
+
+def test_mod_switch_keeps_the_noise_budget(small):
+    # the noise is divided by q_l along with Q, plus a rounding term below
+    # (1 + n) / 2 + t: with noise far above q_l n (an error of ~2^100 added to
+    # c0) the budget in bits stays; with a fresh ciphertext the rounding term
+    # sets the new noise, which still decrypts
+    P, keys = small
+    g = np.random.default_rng(13)
+    v = g.integers(0, 16, P.n)
+    m = encoding.encode(v, 65537)
+    c = enc(P, keys, v)
+    big = [int(x) << 80 for x in g.integers(-2**20, 2**20, P.n)]
+    noisy = bfv.Ciphertext([bfv.add(P, c, bfv.Ciphertext([P.qbasis.reduce(big), np.zeros_like(c.c[1])], c.t)).c[0],
+                            c.c[1]], c.t)
+    before = bfv.noise_margin_bits(P, keys.sk, noisy, m)
+    P2 = bfv.params_at_level(P, 2)
+    after = bfv.noise_margin_bits(P2, keys.sk, bfv.mod_switch(P, noisy), m)
+    assert 30 < before < 70 and abs(before - after) < 0.1
+    fresh = bfv.noise_margin_bits(P2, keys.sk, bfv.mod_switch(P, c), m)
+    assert fresh > 90        # Q' / 2t ~ 2^103 against a rounding term of a few bits
+
+
+def test_level_keys_are_restrictions_of_the_full_keys(small):
+    P, keys = small
+    kl = bfv.keys_at_level(keys, 2)
+    g = bfv.galois_for_rotation(P.n, 1)
+    kf, kr = keys.galois[g], kl.galois[g]
+    assert kr.b.shape == (2, 3, P.n)
+    for i in range(2):
+        for jl, jf in enumerate([0, 1, P.L]):
+            assert np.array_equal(kr.b[i, jl], kf.b[i, jf]) and np.array_equal(kr.a[i, jl], kf.a[i, jf])
