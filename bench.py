@@ -57,6 +57,9 @@ def parse():
                     help="mnist: convolution-representation input (Sec. 4.3); lola_dense: dense input "
                          "masked on the server (App. C); cifar: the CIFAR-shaped network (Sec. 6.2)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mod-switch", action="store_true",
+                    help="mnist: keep all L primes to the end (default at L = 5: switch to 4 and 2 primes "
+                         "after the two squares)")
     ap.add_argument("--profile-steps", type=int, default=1)
     ap.add_argument("--mode", choices=["network", "serve", "primitives"], default="network")
     ap.add_argument("--n", type=int, default=16384, help="primitives mode: ring degree")
@@ -65,6 +68,10 @@ def parse():
     args = ap.parse_args()
     if args.L is None:
         args.L = 5 if args.workload == "mnist" else 6
+    args.levels = None
+    if args.workload == "mnist" and args.L == 5 and not args.no_mod_switch:
+        import workloads as W
+        args.levels = W.MNIST_LEVELS
     if args.batch is None:
         args.batch = 2 if args.workload == "cifar" else 16
     return args
@@ -74,6 +81,11 @@ def parse():
 OP_COUNTS = {"mnist": {"rot": 224, "square": 2, "mul_plain": 24, "mul_scalar": 125, "add": 344},
              "lola_dense": {"rot": 326, "square": 2, "mul_plain": 61, "mul_scalar": 125, "add": 422},
              "cifar": {"rot": 57273, "square": 2, "mul_plain": 8162, "mul_scalar": 15936, "add": 77200}}
+# the MNIST-shaped network with modulus switching (5 -> 4 primes after the
+# first square, 4 -> 2 after the second): the same counts split by level
+OP_COUNTS_LEVELS = {"mnist": {5: {"rot": 4, "square": 1, "mul_plain": 0, "mul_scalar": 125, "add": 124},
+                              4: {"rot": 80, "square": 1, "mul_plain": 14, "mul_scalar": 0, "add": 80},
+                              2: {"rot": 140, "square": 0, "mul_plain": 10, "mul_scalar": 0, "add": 140}}}
 WORKLOAD_NAME = {"mnist": "mnist_lola_n16384", "lola_dense": "lola_dense_n16384", "cifar": "cifar_lola_n16384"}
 
 
@@ -134,10 +146,12 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ CPU baseline
-def oracle_sample(n_rot=1, n_sq=1, workload="mnist", L=5):
+def oracle_sample(n_rot=1, n_sq=1, workload="mnist", L=5, levels=None):
     """Time the CPU oracle's operations on the network's parameters (one CRT
     residue) and scale by the network's operation counts for one inference
-    over all residues.  Returns (seconds per inference, description)."""
+    over all residues; with modulus switching, each level's operations are
+    timed at that level (ciphertexts switched by the oracle).  Returns
+    (seconds per inference, description)."""
     import numpy as np
 
     import workloads as W
@@ -155,25 +169,29 @@ def oracle_sample(n_rot=1, n_sq=1, workload="mnist", L=5):
         for _ in range(reps):
             fn()
         return (time.perf_counter() - t0) / reps
-    t_rot = timed(lambda: bfv.rotate(P, keys, ct, 1), n_rot)
-    t_sq = timed(lambda: bfv.square(P, keys, ct), n_sq)
-    t_pt = timed(lambda: bfv.mul_plain(P, ct, w), 1)
-    t_sc = timed(lambda: bfv.mul_scalar(P, ct, -3), 3)
-    t_add = timed(lambda: bfv.add(P, ct, ct), 3)
-    counts = OP_COUNTS[workload]
-    per_residue = (counts["rot"] * t_rot + counts["square"] * t_sq + counts["mul_plain"] * t_pt
-                   + counts["mul_scalar"] * t_sc + counts["add"] * t_add)
-    sec = per_residue * len(ps.t)
-    desc = (f"oracle per-op times on n=16384, L={ps.L}: rotation {t_rot:.3f}s, square+relin {t_sq:.3f}s, "
-            f"ct*pt {t_pt:.3f}s, ct*scalar {t_sc:.4f}s, add {t_add:.4f}s; x op counts of one inference "
-            f"({counts['rot']} rot, {counts['square']} sq, {counts['mul_plain']} ct*pt, {counts['mul_scalar']} ct*scalar, "
-            f"{counts['add']} add) x {len(ps.t)} CRT residues")
+    by_level = OP_COUNTS_LEVELS[workload] if levels else {L: OP_COUNTS[workload]}
+    sec, parts, total = 0.0, [], {}
+    for lv, counts in sorted(by_level.items(), reverse=True):
+        Pl, kl = bfv.params_at_level(P, lv), bfv.keys_at_level(keys, lv)
+        cl = bfv.mod_switch_to(P, ct, lv)
+        t_rot = timed(lambda: bfv.rotate(Pl, kl, cl, 1), n_rot) if counts["rot"] else 0.0
+        t_sq = timed(lambda: bfv.square(Pl, kl, cl), n_sq) if counts["square"] else 0.0
+        t_pt = timed(lambda: bfv.mul_plain(Pl, cl, w), 1) if counts["mul_plain"] else 0.0
+        t_sc = timed(lambda: bfv.mul_scalar(Pl, cl, -3), 3) if counts["mul_scalar"] else 0.0
+        t_add = timed(lambda: bfv.add(Pl, cl, cl), 3)
+        sec += (counts["rot"] * t_rot + counts["square"] * t_sq + counts["mul_plain"] * t_pt
+                + counts["mul_scalar"] * t_sc + counts["add"] * t_add) * len(ps.t)
+        parts.append(f"L={lv}: rotation {t_rot:.3f}s, square+relin {t_sq:.3f}s, ct*pt {t_pt:.3f}s, "
+                     f"ct*scalar {t_sc:.4f}s, add {t_add:.4f}s x ({counts['rot']} rot, {counts['square']} sq, "
+                     f"{counts['mul_plain']} ct*pt, {counts['mul_scalar']} ct*scalar, {counts['add']} add)")
+    desc = (f"oracle per-op times on n=16384 x op counts of one inference per level; " + "; ".join(parts)
+            + f"; x {len(ps.t)} CRT residues")
     return sec, desc
 
 
-def cpu_baseline_obj(workload="mnist", L=5):
+def cpu_baseline_obj(workload="mnist", L=5, levels=None):
     t0 = time.perf_counter()
-    sec, desc = oracle_sample(workload=workload, L=L)
+    sec, desc = oracle_sample(workload=workload, L=L, levels=levels)
     return {"value": 1.0 / sec, "unit": "inferences/s", "cores": 1, "kind": "oracle",
             "sample": desc, "sample_wall_s": round(time.perf_counter() - t0, 1)}
 
@@ -184,11 +202,11 @@ def run_reference(args):
     if rank != 0:
         return
     for _ in range(args.warmup):
-        oracle_sample(1, 1, args.workload, args.L)
+        oracle_sample(1, 1, args.workload, args.L, args.levels)
     secs = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        s, desc = oracle_sample(1, 1, args.workload, args.L)
+        s, desc = oracle_sample(1, 1, args.workload, args.L, args.levels)
         secs.append(s)
     wall = time.perf_counter() - t0
     sec = statistics.median(secs)
@@ -197,6 +215,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1000,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": WORKLOAD_NAME[args.workload], "n": 16384, "L": args.L, "K": 1, "k_t": 3,
+                       "levels": [args.L] + list(args.levels or []),
                        "parallelism": "none (CPU oracle)"},
             "cpu_baseline": {"value": value, "unit": "inferences/s", "cores": 1, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": "inferences/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -265,7 +284,7 @@ KERNEL_BYTES = {
     # algorithmic bytes per work unit (n = ring degree, L = ciphertext primes)
     # transform kernels: one unit = one limb-polynomial
     "ks_modup": lambda n, L: 16 * n,                 # read digit limb, write one mod-up limb
-    "ks_decompose": lambda n, L: 40 * n,             # read c0, c1 limbs; write permuted c0, diagonal, digit
+    "ks_decompose": lambda n, L: 24 * n,             # read c1 limb; write the permuted (diagonal) limb and the digit
     "ks_moddown": lambda n, L: 24 * n,               # x_P and inner-product limb in (addends folded in ks_ip); out
     "ks_intt_p": lambda n, L: 16 * n,                # special-prime inner product in, x_P out
     # inner product: one unit = two coefficients of one (ct, prime): L digit words in, 2 words out, each x2
@@ -338,7 +357,7 @@ def run_ours(args):
         img_slots = np.asarray(W.dense_image_slots(), dtype=np.int64)
         net = L.lola_net_create(ctx, {"repr": "dense", "n_msgs": 1, "n_elems": 784, "slot": img_slots}, layers)
     else:
-        layers = W.layers_mnist(mnet, n)
+        layers = W.layers_mnist(mnet, n, args.levels)
         net = L.lola_net_create(ctx, {"repr": "convolution", "n_msgs": 25, "n_elems": 169}, layers)
     n_in = net.shape()[0]
     steps_needed = net.rotation_steps()
@@ -361,9 +380,9 @@ def run_ours(args):
         packed = np.concatenate([L.lola_pack_convolution(im, 5, 5, 2, n)[0] for im in imgs])
     ct_in = L.lola_encrypt(ctx, sk, packed, 1000 + rank)
     ct_out = L.lola_ct_create(ctx, B * 10)
-    ct_words = 2 * Lq * n
-    in_bytes = B * n_in * kt * ct_words * 8
-    out_bytes = B * 10 * kt * ct_words * 8
+    in_bytes = B * n_in * kt * 2 * Lq * n * 8
+    out_level = args.levels[-1] if args.levels else Lq           # primes left in the outputs
+    out_bytes = B * 10 * kt * 2 * out_level * n * 8
 
     def barrier():
         if dist:
@@ -534,7 +553,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline_obj(args.workload, args.L)
+        cpu = cpu_baseline_obj(args.workload, args.L, args.levels)
 
     if rank == 0:
         srt = sorted(step_ms)
@@ -543,6 +562,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": WORKLOAD_NAME[args.workload], "batch_per_gpu": B, "n": n, "L": Lq, "K": 1, "k_t": kt,
+                       "levels": [Lq] + list(args.levels or []),
                        "aux_primes": len(L.lola_ctx_aux_primes(ctx)), "parallelism": f"replicas x{world}",
                        "l2": (f"L2 flushed between timed steps (256 MB write; {in_bytes / 1e6:.0f} MB of input "
                               "ciphertexts per step)") if flush is not None else
@@ -669,7 +689,7 @@ def run_serve(args):
     ctx2 = L.lola_ctx_create(ps2.n, ps2.q, ps2.L, ps2.K, ps2.t)
     ctx4 = L.lola_ctx_create(ps4.n, ps4.q, ps4.L, ps4.K, ps4.t)
     mnet, Wh = W.mnist_net(), W.head_weights()
-    d2, l2 = {"repr": "convolution", "n_msgs": 25, "n_elems": 169}, W.layers_mnist(mnet, n)
+    d2, l2 = {"repr": "convolution", "n_msgs": 25, "n_elems": 169}, W.layers_mnist(mnet, n, W.MNIST_LEVELS)
     d4, l4 = {"repr": "dense", "n_msgs": 1, "n_elems": 4096}, W.layers_head(Wh, n)
     keys = {}
     for name, ctx, d, layers in (("mnist", ctx2, d2, l2), ("head", ctx4, d4, l4)):

@@ -127,14 +127,22 @@ size_t lola_ct_messages(const lola_ct* ct);
 uint64_t* lola_ct_data(lola_ct* ct);
 /* Copy n messages (all k_t residues) from src starting at message src_off
  * to dst starting at dst_off, device to device on `stream` (batch assembly
- * and result scatter for request batching).  Errors: LOLA_E_PARAM (range). */
+ * and result scatter for request batching).  A copy that fills all of dst
+ * gives dst the level of src; otherwise both must be at the same level.
+ * Errors: LOLA_E_PARAM (range, levels). */
 int lola_ct_copy_messages(lola_ctx* ctx, lola_ct* dst, size_t dst_off, const lola_ct* src, size_t src_off,
                           size_t n, void* stream);
-/* Coefficient-form exchange, host [n_msg][k_t][2][L][n]. */
+/* Ciphertext primes of the ciphertexts in `ct`: L, or fewer for the output
+ * of a network that switches modulus (0 for a NULL handle).  The words of a
+ * ciphertext at level L' are [2][L'][n] over the first L' primes of Q; a
+ * handle keeps the capacity of level L. */
+uint32_t lola_ct_level(const lola_ct* ct);
+/* Coefficient-form exchange, host [n_msg][k_t][2][L'][n] at the handle's
+ * level L' (import: level L). */
 int lola_ct_export(lola_ctx* ctx, const lola_ct* ct, uint64_t* host);
 int lola_ct_import(lola_ctx* ctx, const uint64_t* host, size_t n_msg, lola_ct** out);
 /* Asynchronous host<->device copies of the NTT-form words (pinned host memory
- * recommended); bytes = lola_ct_messages * k_t * 2 * L * n * 8. */
+ * recommended); bytes = lola_ct_messages * k_t * 2 * lola_ct_level * n * 8. */
 int lola_ct_upload(lola_ctx* ctx, lola_ct* ct, const uint64_t* host, void* stream);
 int lola_ct_download(lola_ctx* ctx, const lola_ct* ct, uint64_t* host, void* stream);
 void lola_ct_destroy(lola_ct* ct);
@@ -190,6 +198,23 @@ int lola_rotate_noalloc(lola_ctx* ctx, const lola_keys* keys, const uint64_t* in
  * LOLA_E_PARAM, LOLA_E_CUDA, LOLA_E_NOMEM (scratch is allocated per call). */
 int lola_rotate_hoisted(lola_ctx* ctx, const lola_keys* keys, const uint64_t* in, uint64_t* out, size_t count,
                         const int32_t* steps, size_t n_steps, void* stream);
+/* Modulus switching (BFV; not in the paper, which leaves SEAL's modulus
+ * management unstated): every ciphertext of in (device, [count][2][L_from][n]
+ * over q_0..q_{L_from-1}) becomes one over the first L_to primes, out
+ * (device, [count][2][L_to][n], must not overlap in).  Primes are dropped
+ * from the top one at a time: coefficient x mod Q becomes round(x / q_l)
+ * mod Q / q_l, computed exactly as (c_j - x~) q_l^-1 mod q_j with x~ the
+ * centered residue of x mod q_l.  Decryption is unchanged (the noise shrinks
+ * with Q, plus a rounding term), and every later operation costs less: a
+ * key switch at L' primes runs L'(L'+1) + 2L' + 2 limb transforms (K = 1).  Keys
+ * need no change (a level uses the entries of its digits and primes).
+ * 1 <= L_to <= L_from <= L.  Errors: LOLA_E_PARAM, LOLA_E_NOMEM (scratch). */
+int lola_mod_switch(lola_ctx* ctx, const uint64_t* in, uint64_t* out, size_t count, uint32_t L_from, uint32_t L_to,
+                    void* stream);
+/* Decrypt ciphertexts at level L' (device, [n_msg][k_t][2][L'][n], e.g. the
+ * output of lola_mod_switch) without CRT: out host [n_msg][k_t][n]. */
+int lola_decrypt_residues_level(lola_ctx* ctx, const lola_keys* keys, const uint64_t* d_ct, size_t n_msg,
+                                uint32_t level, uint64_t* out);
 /* ct x plaintext: out_i = in_i * encode(slots_i) (slots host [count][n]
  * int64, centered lift mod t). */
 int lola_mul_plain(lola_ctx* ctx, const uint64_t* in, const int64_t* slots, uint64_t* out, size_t count,
@@ -221,9 +246,11 @@ typedef enum {
                                           rows x cols = messages x elements, entry = input element index
                                           held by message r at element e (-1 = zero); message r must be a
                                           single shift off_r of message 0 (x * mask_r, rotated left by off_r) */
-  LOLA_LAYER_PLACE = 10                /* k dense messages -> 1 with element e at slot weights[e] (one target
+  LOLA_LAYER_PLACE = 10,               /* k dense messages -> 1 with element e at slot weights[e] (one target
                                           per element, both slot rows; Sec. 6.2 combine of 83 maps); the
                                           messages must hold zeros outside their elements' slots */
+  LOLA_LAYER_MOD_SWITCH = 11           /* modulus switching to the first d primes of Q (lola_mod_switch);
+                                          no slot changes, later layers run on d primes; not in the paper */
 } lola_layer_op;
 
 typedef struct {
@@ -232,7 +259,7 @@ typedef struct {
   lola_repr out_repr;     /* checked against what the layer produces */
   uint32_t rows, cols;    /* weight shape (CONV: maps x window size) */
   const int64_t* weights; /* host, rows * cols; NULL for SQUARE/STACK, optional for COMBINE */
-  uint32_t d;             /* STACK / STACKED_ROWMAJOR: block size 2^d */
+  uint32_t d;             /* STACK / STACKED_ROWMAJOR: block size 2^d; MOD_SWITCH: primes kept */
   uint32_t copies;        /* STACK / STACKED_ROWMAJOR: number of copies (power of two) */
   uint32_t stride;        /* COMBINE: slot offset between consecutive messages */
 } lola_layer;

@@ -128,14 +128,30 @@ int lola_encrypt(lola_ctx* ctx, const lola_keys* keys, const int64_t* slots, siz
   return LOLA_OK;
 }
 
+// the context of a handle's level
+static int ct_ctx(lola_ctx* ctx, const lola_ct* ct, Ctx** lc) { return ctx_level(ctx->c, ct->ct.L(), lc); }
+
 int lola_decrypt_residues(lola_ctx* ctx, const lola_keys* keys, const lola_ct* ct, uint64_t* out) {
   CHECK(ctx && keys && ct && out, LOLA_E_PARAM, "null argument");
-  return decrypt_residues(ctx->c, keys->k, ct->ct.buf.u64(), ct->ct.n_msg, out, nullptr);
+  Ctx* lc = nullptr;
+  TRY(ct_ctx(ctx, ct, &lc));
+  return decrypt_residues(lc, keys->k, ct->ct.buf.u64(), ct->ct.n_msg, out, nullptr);
 }
+
+int lola_decrypt_residues_level(lola_ctx* ctx, const lola_keys* keys, const uint64_t* d_ct, size_t n_msg,
+                                uint32_t level, uint64_t* out) {
+  CHECK(ctx && keys && (d_ct || !n_msg) && out, LOLA_E_PARAM, "null argument");
+  Ctx* lc = nullptr;
+  TRY(ctx_level(ctx->c, level, &lc));
+  return decrypt_residues(lc, keys->k, d_ct, n_msg, out, nullptr);
+}
+
+uint32_t lola_ct_level(const lola_ct* ct) { return ct ? ct->ct.L() : 0; }
 
 int lola_decrypt(lola_ctx* ctx, const lola_keys* keys, const lola_ct* ct, int64_t* out) {
   CHECK(ctx && keys && ct && out, LOLA_E_PARAM, "null argument");
-  Ctx* c = ctx->c;
+  Ctx* c = nullptr;
+  TRY(ct_ctx(ctx, ct, &c));
   const size_t n = c->n, kt = c->kt, m = ct->ct.n_msg;
   std::vector<uint64_t> res(m * kt * n);
   TRY(decrypt_residues(c, keys->k, ct->ct.buf.u64(), m, res.data(), nullptr));
@@ -166,7 +182,8 @@ int lola_decrypt(lola_ctx* ctx, const lola_keys* keys, const lola_ct* ct, int64_
 
 int lola_ct_export(lola_ctx* ctx, const lola_ct* ct, uint64_t* host) {
   CHECK(ctx && ct && host, LOLA_E_PARAM, "null argument");
-  Ctx* c = ctx->c;
+  Ctx* c = nullptr;
+  TRY(ct_ctx(ctx, ct, &c));
   const size_t count = ct->ct.n_msg * c->kt;
   DevBuf tmp;
   TRY(tmp.alloc(count * c->ct_words() * 8));
@@ -201,7 +218,10 @@ int lola_ct_copy_messages(lola_ctx* ctx, lola_ct* dst, size_t dst_off, const lol
   CHECK(ctx && dst && src, LOLA_E_PARAM, "null argument");
   CHECK(dst_off + n <= dst->ct.n_msg && src_off + n <= src->ct.n_msg, LOLA_E_PARAM, "message range out of bounds");
   if (!n) return LOLA_OK;
-  const size_t w = ctx->c->kt * ctx->c->ct_words();
+  // a copy that overwrites all of dst takes src's level; otherwise the levels must agree
+  if (dst_off == 0 && n == dst->ct.n_msg) dst->ct.level = src->ct.level;
+  CHECK(dst->ct.L() == src->ct.L(), LOLA_E_PARAM, "ciphertexts of different levels");
+  const size_t w = ctx->c->kt * 2 * (size_t)src->ct.L() * ctx->c->n;
   LOLA_CUDA_TRY(cudaMemcpyAsync(dst->ct.buf.u64() + dst_off * w, src->ct.buf.u64() + src_off * w, n * w * 8,
                                 cudaMemcpyDeviceToDevice, to_stream(stream)));
   return LOLA_OK;
@@ -209,13 +229,13 @@ int lola_ct_copy_messages(lola_ctx* ctx, lola_ct* dst, size_t dst_off, const lol
 
 int lola_ct_upload(lola_ctx* ctx, lola_ct* ct, const uint64_t* host, void* stream) {
   CHECK(ctx && ct && host, LOLA_E_PARAM, "null argument");
-  LOLA_CUDA_TRY(cudaMemcpyAsync(ct->ct.buf.p, host, ct->ct.buf.bytes, cudaMemcpyHostToDevice, to_stream(stream)));
+  LOLA_CUDA_TRY(cudaMemcpyAsync(ct->ct.buf.p, host, ct->ct.used_words() * 8, cudaMemcpyHostToDevice, to_stream(stream)));
   return LOLA_OK;
 }
 
 int lola_ct_download(lola_ctx* ctx, const lola_ct* ct, uint64_t* host, void* stream) {
   CHECK(ctx && ct && host, LOLA_E_PARAM, "null argument");
-  LOLA_CUDA_TRY(cudaMemcpyAsync(host, ct->ct.buf.p, ct->ct.buf.bytes, cudaMemcpyDeviceToHost, to_stream(stream)));
+  LOLA_CUDA_TRY(cudaMemcpyAsync(host, ct->ct.buf.p, ct->ct.used_words() * 8, cudaMemcpyDeviceToHost, to_stream(stream)));
   return LOLA_OK;
 }
 
@@ -310,6 +330,25 @@ int lola_rotate_hoisted(lola_ctx* ctx, const lola_keys* keys, const uint64_t* in
   // the host vectors above must outlive the async copies
   cudaStreamSynchronize(s);
   cudaFreeAsync(buf, s);
+  return rc;
+}
+
+int lola_mod_switch(lola_ctx* ctx, const uint64_t* in, uint64_t* out, size_t count, uint32_t L_from, uint32_t L_to,
+                    void* stream) {
+  CHECK(ctx && ((in && out) || !count), LOLA_E_PARAM, "null argument");
+  Ctx* c = ctx->c;
+  CHECK(L_to >= 1 && L_to <= L_from && L_from <= c->L, LOLA_E_PARAM, "levels must satisfy 1 <= L_to <= L_from <= L");
+  if (!count) return LOLA_OK;
+  const size_t n = c->n;
+  const char *ib = (const char*)in, *ob = (const char*)out;
+  CHECK(ob + count * 2 * L_to * n * 8 <= ib || ib + count * 2 * L_from * n * 8 <= ob, LOLA_E_PARAM,
+        "output must not overlap the input");
+  cudaStream_t s = to_stream(stream);
+  const size_t sw = mod_switch_scratch_words(c, count, L_from, L_to);
+  void* buf = nullptr;
+  if (sw) LOLA_CUDA_TRY(cudaMallocAsync(&buf, sw * 8, s));
+  const int rc = mod_switch(c, in, out, count, L_from, L_to, (uint64_t*)buf, s);
+  if (buf) cudaFreeAsync(buf, s);
   return rc;
 }
 
@@ -414,8 +453,12 @@ static int eval_impl(lola_ctx* ctx, const lola_keys* keys, lola_net* net, const 
                      void* stream, bool graph) {
   CHECK(ctx && keys && net && in && out, LOLA_E_PARAM, "null argument");
   CHECK(net->net->ctx == ctx->c, LOLA_E_PARAM, "network belongs to another context");
-  return net_eval(ctx->c, keys->k, net->net, in->ct.buf.u64(), in->ct.n_msg, out->ct.buf.u64(), out->ct.n_msg,
-                  to_stream(stream), graph);
+  CHECK(in->ct.L() == ctx->c->L, LOLA_E_PARAM, "network input must be at the full level");
+  CHECK(in != out, LOLA_E_PARAM, "input and output must differ");
+  TRY(net_eval(ctx->c, keys->k, net->net, in->ct.buf.u64(), in->ct.n_msg, out->ct.buf.u64(), out->ct.n_msg,
+               to_stream(stream), graph));
+  out->ct.level = net->net->out_level == ctx->c->L ? 0 : net->net->out_level;
+  return LOLA_OK;
 }
 
 int lola_eval_network(lola_ctx* ctx, const lola_keys* keys, lola_net* net, const lola_ct* in, lola_ct* out,

@@ -68,6 +68,10 @@ struct CtxDev {
   // carries the ModDown factor P^-1:
   uint64_t KskR2[MAXB];                           // 2^128 P^-1 mod q_j; 2^128 mod P on P
   uint64_t KskOut[MAXB];                          // P mod q_j; 1 on P (Montgomery factor back to k)
+  // geometry of the switching keys, which belong to the full context: kL
+  // digits of kL + K primes, the special prime at prime index kL (kL = L
+  // except in a context reached by modulus switching)
+  uint32_t kL, kLK;
 };
 
 // host-side error reporting

@@ -127,11 +127,13 @@ const char* kernel_name(int id) {
   static const char* names[KI_COUNT] = {
       "ntt_fwd", "ntt_inv", "ntt_fwd_signed", "encode_lift", "slots_to_coeff", "coeff_to_slots", "enc_msg",
       "ks_decompose", "ks_modup", "ks_intt_p", "ks_moddown", "ks_ip",
-      "add", "mul_plain", "mac_scalar", "tensor", "lift_q_to_b", "scale_round", "decrypt_round", "misc"};
+      "add", "mul_plain", "mac_scalar", "tensor", "lift_q_to_b", "scale_round", "decrypt_round", "misc",
+      "mod_switch"};
   return (id >= 0 && id < KI_COUNT) ? names[id] : "?";
 }
 
 void prof_begin(Ctx* c, int kind, cudaStream_t s, cudaEvent_t* ev) {
+  c = c->root;
   if (!c->prof.on[kind]) return;
   if (c->prof.pool.empty()) {
     cudaEvent_t a, b;
@@ -147,6 +149,7 @@ void prof_begin(Ctx* c, int kind, cudaStream_t s, cudaEvent_t* ev) {
 }
 void prof_end(Ctx* c, int kind, cudaStream_t s, cudaEvent_t* ev, uint64_t units) {
   if (!ev[0]) return;
+  c = c->root;
   cudaEventRecord(ev[1], s);
   c->prof.pending[kind].push_back({ev[0], ev[1], units});
 }
@@ -258,6 +261,8 @@ static int build_ctx(Ctx* c, const lola_params* p) {
   }
   H.iB = c->iB();
   H.iT = c->iT();
+  H.kL = c->L;
+  H.kLK = c->L + c->K;
   const uint64_t n = c->n;
   std::vector<uint64_t> tw((size_t)4 * np * n);
   uint64_t* twf = tw.data();                  // [np][n][2]: (w, w')
@@ -400,9 +405,40 @@ int ctx_create(const lola_params* p, int device, Ctx** out) {
   return LOLA_OK;
 }
 
+int ctx_level(Ctx* c, uint32_t Lv, Ctx** out) {
+  Ctx* r = c->root;
+  if (Lv == r->L) {
+    *out = r;
+    return LOLA_OK;
+  }
+  if (Lv < 1 || Lv > r->L) return fail(LOLA_E_PARAM, "level out of range");
+  auto it = r->levels.find(Lv);
+  if (it != r->levels.end()) {
+    *out = it->second.get();
+    return LOLA_OK;
+  }
+  std::vector<uint64_t> q(r->primes.begin(), r->primes.begin() + Lv);
+  q.insert(q.end(), r->primes.begin() + r->L, r->primes.begin() + r->L + r->K);
+  std::vector<uint64_t> t(r->primes.begin() + r->iT(), r->primes.begin() + r->iT() + r->kt);
+  lola_params p{r->n, Lv, r->K, q.data(), r->kt, t.data()};
+  std::unique_ptr<Ctx> lc(new Ctx());
+  lc->device = r->device;
+  LOLA_CUDA_TRY(cudaSetDevice(r->device));
+  int rc = build_ctx(lc.get(), &p);
+  if (rc != LOLA_OK) return rc;
+  lc->root = r;
+  lc->host.kL = r->L;
+  lc->host.kLK = r->L + r->K;
+  LOLA_CUDA_TRY(cudaMemcpy(lc->d_const.p, &lc->host, sizeof(CtxDev), cudaMemcpyHostToDevice));
+  *out = lc.get();
+  r->levels[Lv] = std::move(lc);
+  return LOLA_OK;
+}
+
 void ctx_destroy(Ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
+  c->levels.clear();
   for (int k2 = 0; k2 < KI_COUNT; ++k2) prof_collect(c, k2);
   for (auto& pr : c->prof.pool) {
     cudaEventDestroy(pr.first);

@@ -10,7 +10,7 @@
 namespace lola {
 
 static int post(Ctx* c) {
-  c->launches.fetch_add(1, std::memory_order_relaxed);
+  c->root->launches.fetch_add(1, std::memory_order_relaxed);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(LOLA_E_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
   return LOLA_OK;
@@ -57,6 +57,10 @@ __global__ void ke_ks_ip(const CtxDev* __restrict__ C, KsDev a, int final_out) {
     const size_t ct = r / J;
     const PrimeDev& P = C->pr[j];
     const uint64_t* key = a.d_keys ? a.d_keys[ct / a.gal_div] : a.key;
+    // the keys have kL digits over kL + K primes (the full context's): prime
+    // j of this context is key prime j, the special primes follow kL
+    const size_t kLK = C->kLK, jk = j < L ? (size_t)j : (size_t)C->kL + (j - L);
+    const size_t krow1 = (size_t)C->kL * kLK;
     const size_t src = a.src_mod ? ct % a.src_mod : ct;
     size_t kd = k;                                // gathered pair of tau_g (D and/or c0)
     bool swp = false;
@@ -75,8 +79,8 @@ __global__ void ke_ks_ip(const CtxDev* __restrict__ C, KsDev a, int final_out) {
     for (int i = 0; i < (LT > 0 ? LT : L); ++i) {
       ulonglong2 d = *(const ulonglong2*)(a.D + ((src * L + i) * LK + j) * n + kD);
       if (swpD) d = make_ulonglong2(d.y, d.x);
-      const ulonglong2 k0 = __ldg((const ulonglong2*)(key + ((size_t)i * LK + j) * n + k));
-      const ulonglong2 k1 = __ldg((const ulonglong2*)(key + ((size_t)(L + i) * LK + j) * n + k));
+      const ulonglong2 k0 = __ldg((const ulonglong2*)(key + ((size_t)i * kLK + jk) * n + k));
+      const ulonglong2 k1 = __ldg((const ulonglong2*)(key + (krow1 + (size_t)i * kLK + jk) * n + k));
       s0[0] += (unsigned __int128)d.x * k0.x;
       s0[1] += (unsigned __int128)d.y * k0.y;
       s1[0] += (unsigned __int128)d.x * k1.x;
@@ -97,8 +101,7 @@ __global__ void ke_ks_ip(const CtxDev* __restrict__ C, KsDev a, int final_out) {
       for (int e = 0; e < 2; ++e) {
         const size_t kk = k + e;
         uint64_t v0 = acc0[e], v1 = acc1[e];
-        if (a.c0p) v0 = add_mod(v0, a.c0p[(ct * L + j) * n + kk], P.q);
-        else if (gather_c0) v0 = add_mod(v0, a.c0[(src * 2 * L + j) * n + (kd + (e ^ (int)swp))], P.q);
+        if (gather_c0) v0 = add_mod(v0, a.c0[(src * 2 * L + j) * n + (kd + (e ^ (int)swp))], P.q);
         else if (a.c0) v0 = add_mod(v0, a.c0[(ct * 2 * L + j) * n + kk], P.q);
         if (a.add1) v1 = add_mod(v1, a.add1[(ct * 2 * L + L + j) * n + kk], P.q);
         if (a.accum) {
@@ -117,8 +120,7 @@ __global__ void ke_ks_ip(const CtxDev* __restrict__ C, KsDev a, int final_out) {
         for (int e = 0; e < 2; ++e) {
           const size_t kk = k + e;
           uint64_t s0v = 0, s1v = 0;
-          if (a.c0p) s0v = a.c0p[(ct * L + j) * n + kk];
-          else if (gather_c0) s0v = a.c0[(src * 2 * L + j) * n + (kd + (e ^ (int)swp))];
+          if (gather_c0) s0v = a.c0[(src * 2 * L + j) * n + (kd + (e ^ (int)swp))];
           else if (a.c0) s0v = a.c0[(ct * 2 * L + j) * n + kk];
           if (a.add1) s1v = a.add1[(ct * 2 * L + L + j) * n + kk];
           if (a.accum) {
@@ -484,6 +486,7 @@ namespace k {
 int ks_ip(Ctx* c, const KsDev& a, bool final_out, cudaStream_t s) {
   const size_t pairs = a.count * (final_out ? c->L : c->L + c->K) * (c->n / 2);
   switch (c->L) {
+    case 2: ELEM_LAUNCH(KI_KS_IP_Q, ke_ks_ip<2>, pairs, c->dev, a, (int)final_out); break;
     case 3: ELEM_LAUNCH(KI_KS_IP_Q, ke_ks_ip<3>, pairs, c->dev, a, (int)final_out); break;
     case 4: ELEM_LAUNCH(KI_KS_IP_Q, ke_ks_ip<4>, pairs, c->dev, a, (int)final_out); break;
     case 5: ELEM_LAUNCH(KI_KS_IP_Q, ke_ks_ip<5>, pairs, c->dev, a, (int)final_out); break;

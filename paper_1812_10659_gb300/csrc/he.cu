@@ -148,8 +148,7 @@ int rotate(Ctx* c, const uint64_t* in, uint64_t* out, const uint64_t* accum, siz
   a.dig = scratch;
   a.D = a.dig + count * L * n;
   a.xP = a.D + count * L * LK * n;
-  a.c0p = nullptr;                            // the inner product gathers tau_g(c0)
-  a.c0_gather = 1;
+  a.c0_gather = 1;                            // the inner product gathers tau_g(c0)
   a.count = count;
   a.d_gal = r.d_gal;
   a.gal = r.gal;
@@ -184,7 +183,6 @@ int rotate_hoisted(Ctx* c, const uint64_t* in, uint64_t* out, size_t count, size
   a.c1 = in;
   a.dig = scratch;
   a.D = a.dig + count * L * n;
-  a.c0p = nullptr;                            // the inner product gathers tau_g(c0)
   a.count = count;
   a.gal = 1;
   a.gal_div = 1;
@@ -212,6 +210,37 @@ int rotate_hoisted(Ctx* c, const uint64_t* in, uint64_t* out, size_t count, size
     TRY(k::ks_ip(c, b, false, s));
     TRY(k::ks_intt_p(c, b, s));
     TRY(k::ks_moddown(c, b, s));
+  }
+  return LOLA_OK;
+}
+
+// ------------------------------------------------------- modulus switching
+// scratch: the dropped limbs in coefficient form [count][2][n], and two
+// intermediate ciphertext arrays when more than one prime is dropped
+size_t mod_switch_scratch_words(const Ctx* c, size_t count, uint32_t L_from, uint32_t L_to) {
+  if (L_from <= L_to) return 0;
+  size_t w = count * 2 * (size_t)c->n;
+  if (L_from - L_to > 1) w += 2 * count * 2 * (size_t)(L_from - 1) * c->n;
+  return w;
+}
+
+int mod_switch(Ctx* c, const uint64_t* in, uint64_t* out, size_t count, uint32_t L_from, uint32_t L_to,
+               uint64_t* scratch, cudaStream_t s) {
+  c = c->root;
+  if (L_to < 1 || L_to > L_from || L_from > c->L) return fail(LOLA_E_PARAM, "mod switch: bad levels");
+  if (!count) return LOLA_OK;
+  const size_t n = c->n;
+  if (L_from == L_to) {
+    if (in != out) LOLA_CUDA_TRY(cudaMemcpyAsync(out, in, count * 2 * L_from * n * 8, cudaMemcpyDeviceToDevice, s));
+    return LOLA_OK;
+  }
+  uint64_t* top = scratch;
+  uint64_t* tmp[2] = {top + count * 2 * n, top + count * 2 * n + count * 2 * (L_from - 1) * n};
+  const uint64_t* src = in;
+  for (uint32_t L1 = L_from; L1 > L_to; --L1) {
+    uint64_t* dst = (L1 - 1 == L_to) ? out : tmp[(L_from - L1) & 1];
+    TRY(k::mod_switch_drop(c, src, top, dst, count, L1, s));
+    src = dst;
   }
   return LOLA_OK;
 }

@@ -57,6 +57,15 @@ int rotate_hoisted(Ctx* c, const uint64_t* in, uint64_t* out, size_t count, size
 int rotate(Ctx* c, const uint64_t* in, uint64_t* out, const uint64_t* accum, size_t count, const RotSpec& r,
            uint64_t* scratch, cudaStream_t s);
 
+// Modulus switching of `count` ciphertexts [count][2][L_from][n] to
+// [count][2][L_to][n] (L_to <= L_from <= c->L; the first primes of Q stay):
+// the top prime is dropped L_from - L_to times, each time
+// c'_j = (c_j - x~) q_l^-1 with x~ the centered residue mod the dropped q_l.
+// in and out must not overlap.
+size_t mod_switch_scratch_words(const Ctx* c, size_t count, uint32_t L_from, uint32_t L_to);
+int mod_switch(Ctx* c, const uint64_t* in, uint64_t* out, size_t count, uint32_t L_from, uint32_t L_to,
+               uint64_t* scratch, cudaStream_t s);
+
 size_t multiply_scratch_words(const Ctx* c, size_t count, bool square);
 int multiply(Ctx* c, const uint64_t* x, const uint64_t* y, uint64_t* out, size_t count, const uint32_t* d_tidx,
              uint32_t tidx_div, const uint64_t* relin_key, uint64_t* scratch, cudaStream_t s);

@@ -41,7 +41,7 @@ enum KernelId {
   KI_NTT_FWD = 0, KI_NTT_INV, KI_NTT_SIGNED, KI_ENCODE_LIFT, KI_SLOTS_TO_COEFF, KI_COEFF_TO_SLOTS, KI_ENC_MSG,
   KI_KS_DECOMPOSE, KI_KS_MODUP, KI_KS_IP_P, KI_KS_MODDOWN, KI_KS_IP_Q,
   KI_ADD, KI_MUL_PLAIN, KI_MAC_SCALAR, KI_TENSOR, KI_LIFT_Q_TO_B, KI_SCALE_ROUND, KI_DECRYPT_ROUND, KI_MISC,
-  KI_COUNT
+  KI_MOD_SWITCH, KI_COUNT
 };
 const char* kernel_name(int id);
 
@@ -73,11 +73,20 @@ struct Ctx {
   DevBuf d_const, d_tw, d_slotpos;   // d_slotpos[pos] = slot whose value sits at NTT position pos
   std::atomic<uint64_t> launches{0};
   Profiler prof;
+  // Modulus switching: a context of the first L' < L ciphertext primes (same
+  // special prime, plaintext moduli and keys) is a child of the full one.
+  // Launch counts and profiles go to the root; children live in its map.
+  Ctx* root = this;
+  std::map<uint32_t, std::unique_ptr<Ctx>> levels;
   int iP() const { return (int)L; }
   int iB() const { return (int)(L + K); }
   int iT() const { return (int)(L + K + M); }
   size_t ct_words() const { return (size_t)2 * L * n; }
 };
+
+// The context of the first Lv ciphertext primes of `c` (c itself when Lv is
+// its L); created on first use, owned by the root context.
+int ctx_level(Ctx* c, uint32_t Lv, Ctx** out);
 
 // Launch bookkeeping around one kernel launch.
 void prof_begin(Ctx* c, int id, cudaStream_t s, cudaEvent_t* ev_pair);
@@ -97,8 +106,11 @@ struct SwitchKey {
 struct Ct {
   Ctx* ctx = nullptr;
   size_t n_msg = 0;
-  DevBuf buf;           // [n_msg][kt][2][L][n] NTT form
+  uint32_t level = 0;   // ciphertext primes after modulus switching (0: all of ctx)
+  DevBuf buf;           // [n_msg][kt][2][L][n] NTT form (capacity for the full L)
   size_t words() const { return n_msg * ctx->kt * ctx->ct_words(); }
+  uint32_t L() const { return level ? level : ctx->L; }
+  size_t used_words() const { return n_msg * ctx->kt * 2 * (size_t)L() * ctx->n; }
 };
 
 uint32_t galois_for_step(uint32_t n, int32_t step);   // step 0 = row swap

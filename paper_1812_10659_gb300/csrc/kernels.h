@@ -34,7 +34,6 @@ struct PrimeMap {
 // Arguments of the key-switching kernels (one batch of `count` ciphertexts).
 struct KsDev {
   const uint64_t* c0;     // comp-0 addend in ciphertext layout, not permuted (relinearisation: e0)
-  uint64_t* c0p;          // rotation: tau_g(c0) written by the decompose kernel, [count][L][n]
   const uint64_t* c1;     // ciphertext whose c1 is switched (rotation), NTT form
   const uint64_t* add1;   // comp-1 addend (relinearisation: e1 in ciphertext layout) or null
   const uint64_t* accum;  // optional ciphertext added to the result (rotate-and-sum) or null
@@ -54,12 +53,16 @@ struct KsDev {
   // (0: i) through tau_g in the NTT domain (D and c0 not permuted beforehand)
   uint32_t src_mod;
   uint32_t ip_gather;
-  // rotation: the inner product adds tau_g(c0) by gathering c0 itself (the
-  // decompose kernel then writes no c0p)
+  // rotation: the inner product adds tau_g(c0) by gathering c0 itself
   uint32_t c0_gather;
 };
 
 namespace k {
+// Modulus switching, one prime (ntt_keyswitch.cu): in [count][2][L1][n] ->
+// out [count][2][L1 - 1][n], dropping q_{L1-1}; top: scratch [count][2][n].
+// c is the full context.
+int mod_switch_drop(Ctx* c, const uint64_t* in, uint64_t* top, uint64_t* out, size_t count, uint32_t L1,
+                    cudaStream_t s);
 // NTT family (ntt_kernels.cu)
 int ntt_fwd_map(Ctx* c, const uint64_t* in, uint64_t* out, size_t n_limbpolys, uint32_t limbs, const PrimeMap& pm,
                 cudaStream_t s);

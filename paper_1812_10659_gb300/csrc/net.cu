@@ -35,14 +35,17 @@ struct Repr {
 };
 
 struct Builder {
-  Ctx* c;
+  Ctx* c;                                  // full context
   Net* net;
-  std::vector<std::vector<int64_t>> pts;   // plaintext slot vectors, in block order
+  uint32_t level = 0;                      // ciphertext primes of the current messages
+  Ctx* lc = nullptr;                       // context of that level
+  std::map<uint32_t, std::vector<std::vector<int64_t>>> pts;   // level -> plaintext slot vectors
   std::vector<uint64_t> w, ws;             // MAC tables
   std::set<int32_t> steps;
 
   int vreg(uint32_t msgs) {
     net->vreg_msgs.push_back(msgs);
+    net->vreg_level.push_back(level);
     return (int)net->vreg_msgs.size() - 1;
   }
   // dst[0..k) = (accum ? accum : 0) + rot(src, step_i)
@@ -67,8 +70,9 @@ struct Builder {
     return x;
   }
   size_t add_plaintexts(const std::vector<std::vector<int64_t>>& v) {
-    const size_t first = pts.size();
-    for (auto& p : v) pts.push_back(p);
+    auto& lv = pts[level];
+    const size_t first = lv.size();
+    for (auto& p : v) lv.push_back(p);
     return first;
   }
 };
@@ -85,7 +89,7 @@ static int layer_conv(Builder& b, const lola_layer& L, Repr& r) {
   o.msgs = maps;
   o.R = R;
   o.w_first = b.w.size();
-  const uint32_t kt = b.c->kt, Lq = b.c->L;
+  const uint32_t kt = b.c->kt, Lq = b.level;   // the table holds the current level's primes
   for (uint32_t m = 0; m < maps; ++m)
     for (uint32_t j = 0; j < R; ++j)
       for (uint32_t ti = 0; ti < kt; ++ti) {
@@ -387,6 +391,29 @@ static int layer_square(Builder& b, const lola_layer&, Repr& r) {
   return LOLA_OK;
 }
 
+// Modulus switching to the first L.d primes of Q (not in the paper; every
+// slot keeps its value): later layers run on fewer primes.
+static int layer_mod_switch(Builder& b, const lola_layer& L, Repr& r) {
+  const uint32_t Lv = L.d;
+  if (Lv < 1 || Lv > b.level) return fail(LOLA_E_PARAM, "mod switch: level must be in [1, current level]");
+  if (Lv == b.level) return LOLA_OK;
+  Ctx* lc = nullptr;
+  TRY(ctx_level(b.c, Lv, &lc));
+  b.net->lctx[Lv] = lc;
+  Op o;
+  o.kind = OP_MODSWITCH;
+  o.src = r.reg;
+  o.msgs = r.msgs;
+  o.level = b.level;
+  o.level_to = Lv;
+  b.level = Lv;
+  b.lc = lc;
+  o.dst = b.vreg(r.msgs);
+  b.net->ops.push_back(o);
+  r.reg = o.dst;
+  return LOLA_OK;
+}
+
 static int layer_stack(Builder& b, const lola_layer& L, Repr& r) {
   const uint32_t n = b.c->n, h = n / 2, s = 1u << L.d;
   if (r.msgs != 1 || (r.kind != LOLA_REPR_DENSE && r.kind != LOLA_REPR_INTERLEAVED))
@@ -555,7 +582,12 @@ int net_create(Ctx* c, const lola_input* in, const lola_layer* layers, size_t n_
   *out = nullptr;
   std::unique_ptr<Net> net(new Net());
   net->ctx = c;
-  Builder b{c, net.get(), {}, {}, {}, {}};
+  Builder b;
+  b.c = c;
+  b.net = net.get();
+  b.level = c->L;
+  b.lc = c;
+  net->lctx[c->L] = c;
   Repr r;
   r.kind = in->repr;
   r.msgs = in->n_msgs;
@@ -576,6 +608,7 @@ int net_create(Ctx* c, const lola_input* in, const lola_layer* layers, size_t n_
     const lola_layer& L = layers[li];
     if (L.in_repr && L.in_repr != r.kind)
       return fail(LOLA_E_REPR, "layer " + std::to_string(li) + ": input representation mismatch");
+    const size_t op0 = net->ops.size();
     int rc;
     switch (L.op) {
       case LOLA_LAYER_CONV_ROWMAJOR: rc = layer_conv(b, L, r); break;
@@ -588,37 +621,44 @@ int net_create(Ctx* c, const lola_input* in, const lola_layer* layers, size_t n_
       case LOLA_LAYER_INTERLEAVED_ROWMAJOR: rc = layer_rowmajor_sparse(b, L, r, false); break;
       case LOLA_LAYER_DENSE_ROWMAJOR: rc = layer_rowmajor_sparse(b, L, r, true); break;
       case LOLA_LAYER_SPARSE_COLMAJOR: rc = layer_sparse_colmajor(b, L, r); break;
+      case LOLA_LAYER_MOD_SWITCH: rc = layer_mod_switch(b, L, r); break;
       default: return fail(LOLA_E_PARAM, "unknown layer op");
     }
     if (rc != LOLA_OK) return rc;
+    for (size_t i = op0; i < net->ops.size(); ++i)
+      if (!net->ops[i].level) net->ops[i].level = b.level;
     if (L.out_repr && L.out_repr != r.kind)
       return fail(LOLA_E_REPR, "layer " + std::to_string(li) + ": output representation mismatch");
   }
   net->out_reg = r.reg;
+  net->out_level = b.level;
   net->n_out = r.msgs;
   for (auto& p : r.pos) {
     net->out_msg.push_back(p.first);
     net->out_slot.push_back(p.second);
   }
   net->steps_needed.assign(b.steps.begin(), b.steps.end());
-  // encode plaintexts for every t_i: blocks [pt][kt][L][n]
-  const size_t kt = c->kt, n = c->n, Lq = c->L;
-  net->n_pt_blocks = b.pts.size();
-  if (!b.pts.empty()) {
-    TRY(net->pt.alloc(b.pts.size() * kt * Lq * n * 8));
+  // encode plaintexts for every t_i, per level: blocks [pt][kt][level][n]
+  const size_t kt = c->kt, n = c->n;
+  for (auto& lp : b.pts) {
+    const uint32_t Lv = lp.first;
+    const auto& pts = lp.second;
+    Ctx* lc = net->lctx.at(Lv);
+    DevBuf& buf = net->pt[Lv];
+    TRY(buf.alloc(pts.size() * kt * Lv * n * 8));
     std::vector<int64_t> slots;
     std::vector<uint32_t> tidx;
     const size_t chunk = 64;
-    for (size_t p0 = 0; p0 < b.pts.size(); p0 += chunk) {
-      const size_t p1 = std::min(b.pts.size(), p0 + chunk);
+    for (size_t p0 = 0; p0 < pts.size(); p0 += chunk) {
+      const size_t p1 = std::min(pts.size(), p0 + chunk);
       slots.clear();
       tidx.clear();
       for (size_t p = p0; p < p1; ++p)
         for (size_t ti = 0; ti < kt; ++ti) {
-          slots.insert(slots.end(), b.pts[p].begin(), b.pts[p].end());
+          slots.insert(slots.end(), pts[p].begin(), pts[p].end());
           tidx.push_back((uint32_t)ti);
         }
-      TRY(encode_plaintexts(c, slots.data(), tidx.data(), (p1 - p0) * kt, net->pt.u64() + p0 * kt * Lq * n, nullptr));
+      TRY(encode_plaintexts(lc, slots.data(), tidx.data(), (p1 - p0) * kt, buf.u64() + p0 * kt * Lv * n, nullptr));
     }
   }
   if (!b.w.empty()) {
@@ -691,19 +731,21 @@ static int build_executor(Ctx* c, Net* net, uint32_t B, Executor* ex) {
   }
   ex->phys.resize(phys_msgs.size());
   for (size_t p = 0; p < phys_msgs.size(); ++p) TRY(ex->phys[p].alloc(phys_msgs[p] * msg_words * 8));
-  // scratch: largest op requirement
+  // scratch: largest op requirement (each at its level)
   size_t sw = 0, maxcnt = 1;
   for (const Op& o : net->ops) {
+    const Ctx* lc = net->lctx.at(o.level);
     const size_t cnt = (size_t)o.msgs * B * kt;
     maxcnt = std::max(maxcnt, cnt);
     if (o.kind == OP_ROT) {
       const size_t per_msg = (size_t)B * kt;
       const size_t chunk_msgs = std::max<size_t>(1, kMaxRotCts / per_msg);
       const size_t mc = std::min<size_t>(o.msgs, chunk_msgs);
-      sw = std::max(sw, rotate_scratch_words(c, mc * per_msg) + 2 * mc);
+      sw = std::max(sw, rotate_scratch_words(lc, mc * per_msg) + 2 * mc);
     }
-    if (o.kind == OP_SQUARE) sw = std::max(sw, multiply_scratch_words(c, cnt, true));
-    if (o.kind == OP_ROT_HOISTED) sw = std::max(sw, rotate_hoisted_scratch_words(c, (size_t)B * kt, o.msgs));
+    if (o.kind == OP_SQUARE) sw = std::max(sw, multiply_scratch_words(lc, cnt, true));
+    if (o.kind == OP_ROT_HOISTED) sw = std::max(sw, rotate_hoisted_scratch_words(lc, (size_t)B * kt, o.msgs));
+    if (o.kind == OP_MODSWITCH) sw = std::max(sw, mod_switch_scratch_words(c, cnt, o.level, o.level_to));
   }
   TRY(ex->scratch.alloc(sw * 8));
   std::vector<uint32_t> pat(maxcnt);
@@ -744,13 +786,17 @@ static int bind_keys(Ctx* c, Net* net, Executor* ex, const KeySet* ks) {
   return LOLA_OK;
 }
 
-static int run_ops(Ctx* c, Net* net, Executor* ex, const KeySet* ks, cudaStream_t s) {
-  const size_t kt = c->kt, ctw = c->ct_words();
+static int run_ops(Ctx* root, Net* net, Executor* ex, const KeySet* ks, cudaStream_t s) {
+  const size_t kt = root->kt;
   const uint32_t B = ex->B;
-  const size_t msg_words = (size_t)B * kt * ctw;
-  auto reg = [&](int v, uint32_t off) { return ex->phys[ex->vmap[v]].u64() + (size_t)off * msg_words; };
+  // message m of register v: [request][t_i][2][level(v)][n] words at m * B kt 2 level n
+  auto reg = [&](int v, uint32_t off) {
+    return ex->phys[ex->vmap[v]].u64() + (size_t)off * B * kt * 2 * net->vreg_level[v] * root->n;
+  };
   for (size_t i = 0; i < net->ops.size(); ++i) {
     const Op& o = net->ops[i];
+    Ctx* c = net->lctx.at(o.level);
+    const size_t msg_words = (size_t)B * kt * c->ct_words();
     const size_t cnt = (size_t)o.msgs * B * kt;
     switch (o.kind) {
       case OP_MAC:
@@ -798,7 +844,7 @@ static int run_ops(Ctx* c, Net* net, Executor* ex, const KeySet* ks, cudaStream_
         break;
       }
       case OP_MULPT: {
-        const uint64_t* pt = net->pt.u64() + o.pt_first * kt * c->L * c->n;
+        const uint64_t* pt = net->pt.at(o.level).u64() + o.pt_first * kt * c->L * c->n;
         if (o.src_stride == 0) {
           TRY(k::mul_plain_multi(c, reg(o.src, o.src_off), pt, reg(o.dst, o.dst_off), o.msgs, B, s));
         } else {
@@ -811,6 +857,10 @@ static int run_ops(Ctx* c, Net* net, Executor* ex, const KeySet* ks, cudaStream_
       case OP_SQUARE:
         TRY(multiply(c, reg(o.src, o.src_off), reg(o.src, o.src_off), reg(o.dst, o.dst_off), cnt,
                      (const uint32_t*)ex->tid_pattern.p, 1, ks->ev->relin->buf.u64(), ex->scratch.u64(), s));
+        break;
+      case OP_MODSWITCH:
+        TRY(mod_switch(root, reg(o.src, o.src_off), reg(o.dst, o.dst_off), cnt, o.level, o.level_to,
+                       ex->scratch.u64(), s));
         break;
     }
   }
@@ -851,8 +901,9 @@ int net_eval(Ctx* c, const KeySet* ks, Net* net, const uint64_t* d_in, size_t in
   Executor* ex = slot.get();
   TRY(bind_keys(c, net, ex, ks));
   const size_t blk = (size_t)c->kt * c->ct_words();
+  const size_t blk_out = (size_t)c->kt * 2 * net->out_level * c->n;
   TRY(transpose_msgs(ex->phys[ex->vmap[net->in_reg]].u64(), d_in, net->n_in, B, blk, true, s));
-  const bool profiling = c->prof.any();
+  const bool profiling = c->root->prof.any();
   if (use_graph && !profiling) {
     if (!ex->graph) {
       if (!ex->cap_stream) LOLA_CUDA_TRY(cudaStreamCreateWithFlags(&ex->cap_stream, cudaStreamNonBlocking));
@@ -876,7 +927,7 @@ int net_eval(Ctx* c, const KeySet* ks, Net* net, const uint64_t* d_in, size_t in
   } else {
     TRY(run_ops(c, net, ex, ks, s));
   }
-  TRY(transpose_msgs(d_out, ex->phys[ex->vmap[net->out_reg]].u64(), net->n_out, B, blk, false, s));
+  TRY(transpose_msgs(d_out, ex->phys[ex->vmap[net->out_reg]].u64(), net->n_out, B, blk_out, false, s));
   return LOLA_OK;
 }
 

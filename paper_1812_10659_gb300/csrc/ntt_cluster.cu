@@ -81,37 +81,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(cl_threads<CL_LOGE>(
   const uint32_t g = a.d_gal ? a.d_gal[ct / a.gal_div] : a.gal;
   const uint32_t ginv = inv_odd32(g) & ((2u << CL_LOGN) - 1);
   const int tid = threadIdx.x;
-  const uint64_t* src0 = a.c1 + (ct * 2 * L + i) * (size_t)N;
   const uint64_t* src1 = a.c1 + (ct * 2 * L + L + i) * (size_t)N;
   uint64_t* diag = a.D + ((ct * L + i) * LK + i) * (size_t)N;
   uint64_t* dig = a.dig + (ct * L + i) * (size_t)N;
   const PrimeDev& P = C->pr[i];
-  // the peers must have started before their shared memory is written: a
-  // cluster barrier, overlapped with the first loads
-  cl.barrier_arrive();
-  if (a.c0p) {
-    // tau_g(c0): this CTA reads its chunk of c0 and scatters through the
-    // inverse permutation (c0p is the same for the whole cluster)
-    uint64_t* c0p = a.c0p + (ct * L + i) * (size_t)N;
-    uint64_t v[NC / T];
-#pragma unroll
-    for (int k = 0; k < NC / T; ++k) v[k] = src0[(h << LOGNL) + tid + k * T];
-    cl.barrier_wait();
-#pragma unroll
-    for (int k = 0; k < NC / T; ++k) {
-      const uint32_t d = gal_dst((h << LOGNL) + tid + k * T, ginv, CL_LOGN);
-      cl.map_shared_rank(sm, (int)(d >> LOGNL))[swz<LOGE>(d & (NC - 1))] = v[k];
-    }
-    cl.sync();
-#pragma unroll 4
-    for (int k = 0; k < NC / T; ++k) {
-      const int li = tid + k * T;
-      c0p[(h << LOGNL) + li] = sm[swz<LOGE>(li)];
-    }
-    cl.sync();
-  } else {
-    cl.barrier_wait();
-  }
+  // the peers must have started before their shared memory is written
+  cl.sync();
   // tau_g(c1): diagonal block, then the digit
 #pragma unroll 4
   for (int k = 0; k < NC / T; ++k) {

@@ -77,7 +77,7 @@ struct ModDownStore {
   } while (0)
 
 static inline int post_launch(Ctx* c, cudaStream_t) {
-  c->launches.fetch_add(1, std::memory_order_relaxed);
+  c->root->launches.fetch_add(1, std::memory_order_relaxed);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(LOLA_E_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
   return LOLA_OK;

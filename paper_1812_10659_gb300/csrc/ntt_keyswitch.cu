@@ -9,9 +9,8 @@ namespace lola {
 // A: the Galois automorphism in NTT form is a permutation of positions.
 //    Load c1 limb i coalesced and scatter it through the inverse permutation
 //    into shared memory; write the permuted limb (the diagonal block D[i][i])
-//    back coalesced; inverse-transform it into digit i.  When c0p is given,
-//    tau_g(c0) is written the same way first (otherwise the inner product
-//    gathers it).
+//    back coalesced; inverse-transform it into digit i.  (tau_g(c0) is
+//    never materialised: the inner product gathers it.)
 template <int LOGN>
 __global__ void __launch_bounds__(Cfg<LOGN>::T) kn_ks_decompose(const CtxDev* __restrict__ C, KsDev a) {
   extern __shared__ uint64_t sm[];
@@ -22,28 +21,11 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T) kn_ks_decompose(const CtxDev* __
   const uint32_t g = a.d_gal ? a.d_gal[ct / a.gal_div] : a.gal;
   const uint32_t ginv = inv_odd32(g) & ((2u << LOGN) - 1);
   const int tid = threadIdx.x;
-  const uint64_t* src0 = a.c1 + (ct * 2 * L + i) * (size_t)N;
   const uint64_t* src1 = a.c1 + (ct * 2 * L + L + i) * (size_t)N;
   uint64_t* diag = a.D + ((ct * L + i) * LK + i) * (size_t)N;
   uint64_t* dig = a.dig + (ct * L + i) * (size_t)N;
   const PrimeDev& P = C->pr[i];
   uint64_t v[N / T];
-  if (a.c0p) {
-    // tau_g(c0): all loads of the thread first (the compiler may not move a
-    // global load above a shared store through a generic pointer)
-    uint64_t* c0p = a.c0p + (ct * L + i) * (size_t)N;
-#pragma unroll
-    for (int k = 0; k < N / T; ++k) v[k] = src0[tid + k * T];
-#pragma unroll
-    for (int k = 0; k < N / T; ++k) sm[swz<LOGE>(gal_dst(tid + k * T, ginv, LOGN))] = v[k];
-    __syncthreads();
-#pragma unroll 4
-    for (int k = 0; k < N / T; ++k) {
-      const int idx = tid + k * T;
-      c0p[idx] = sm[swz<LOGE>(idx)];
-    }
-    __syncthreads();
-  }
   // tau_g(c1): diagonal block, then digit
 #pragma unroll
   for (int k = 0; k < N / T; ++k) v[k] = src1[tid + k * T];
@@ -123,7 +105,85 @@ __global__ void __launch_bounds__(CfgM<LOGN>::T) kn_ks_moddown(const CtxDev* __r
       ModDownStore{accp, dst, P.q});
 }
 
+// Modulus switching (drop q_l, l = L1 - 1, from ciphertexts of L1 primes):
+// F: inverse transform of limb l of each component into coefficients.
+template <int LOGN>
+__global__ void __launch_bounds__(Cfg<LOGN>::T) kn_ms_top(const CtxDev* __restrict__ C, const uint64_t* __restrict__ in,
+                                                         uint64_t* __restrict__ top, int L1) {
+  extern __shared__ uint64_t sm[];
+  constexpr int N = Cfg<LOGN>::N;
+  const int l = L1 - 1;
+  const size_t cp = blockIdx.x;   // (ciphertext, component)
+  const PrimeDev& P = C->pr[l];
+  const uint64_t* src = in + (cp * L1 + l) * (size_t)N;
+  uint64_t* dst = top + cp * (size_t)N;
+  ntt_inverse<LOGN, Cfg<LOGN>::LOGE>(sm, TW_I(C, l), P.q, P.ninv, P.ninv_s, [&](int k) { return src[k]; },
+                                      [&](int k, uint64_t v) { dst[k] = v; });
+}
+
+// G: out limb j < l = (c_j - NTT_j(x~)) q_l^-1 = c_j q_l^-1 - NTT_j(x~ q_l^-1),
+//    x~ = centered(x mod q_l).  The loader forms x~ q_l^-1 mod q_j from the
+//    raw x in [0, q_l) as mod-down does (x q_l^-1, minus 1 = q_l q_l^-1 when
+//    x > (q_l - 1) / 2); the storer fetches c_j ahead of its stores.
+struct MsConst {
+  uint64_t inv[MAXL], inv_s[MAXL];   // q_l^-1 mod q_j and its Shoup companion
+};
+struct MsStore {
+  const uint64_t* c;
+  uint64_t* dst;
+  uint64_t q, w, ws;
+  __device__ __forceinline__ uint64_t fetch(int k) const { return c[k]; }
+  __device__ __forceinline__ void operator()(int k, uint64_t v, uint64_t f) const {
+    dst[k] = sub_mod(shoup_mul(f, w, ws, q), v, q);
+  }
+};
+
+template <int LOGN>
+__global__ void __launch_bounds__(CfgM<LOGN>::T) kn_ms_down(const CtxDev* __restrict__ C, const uint64_t* __restrict__ in,
+                                                           const uint64_t* __restrict__ top, uint64_t* __restrict__ out,
+                                                           int L1, MsConst mc) {
+  extern __shared__ uint64_t sm[];
+  constexpr int N = CfgM<LOGN>::N;
+  const int l = L1 - 1;
+  const size_t cp = blockIdx.x / l;
+  const int j = blockIdx.x % l;
+  const PrimeDev& P = C->pr[j];
+  const uint64_t half = (C->pr[l].q - 1) / 2, q2m1 = 2 * P.q - 1;
+  const uint64_t w = mc.inv[j], ws = mc.inv_s[j];
+  const uint64_t* x = top + cp * (size_t)N;
+  ntt_forward<LOGN, CfgM<LOGN>::LOGE>(
+      sm, TW_F(C, j), P.q, P.f64,
+      [&](int k) {
+        const uint64_t v = x[k];
+        return shoup_mul_lazy(v, w, ws, P.q) + (v > half ? q2m1 : 0);
+      },
+      MsStore{in + (cp * L1 + j) * (size_t)N, out + (cp * l + j) * (size_t)N, P.q, w, ws});
+}
+
 namespace k {
+int mod_switch_drop(Ctx* c, const uint64_t* in, uint64_t* top, uint64_t* out, size_t count, uint32_t L1,
+                    cudaStream_t s) {
+  if (L1 < 2 || L1 > c->L) return fail(LOLA_E_PARAM, "mod switch: bad level");
+  if (!count) return LOLA_OK;
+  const uint32_t l = L1 - 1;
+  MsConst mc{};
+  const uint64_t ql = c->primes[l];
+  for (uint32_t j = 0; j < l; ++j) {
+    const uint64_t q = c->primes[j];
+    mc.inv[j] = invmod_h(ql % q, q);
+    mc.inv_s[j] = shoup_h(mc.inv[j], q);
+  }
+  {
+    ProfScope ps(c, KI_MOD_SWITCH, s, count * 2);
+    LOLA_DISPATCH(c->logn, kn_ms_top, count * 2, s, c->dev, in, top, (int)L1);
+    const int rc = post_launch(c, s);
+    if (rc != LOLA_OK) return rc;
+  }
+  ProfScope ps(c, KI_MOD_SWITCH, s, count * 2 * l);
+  LOLA_DISPATCH_CFG(CfgM, c->logn, kn_ms_down, count * 2 * l, s, c->dev, in, top, out, (int)L1, mc);
+  return post_launch(c, s);
+}
+
 // which key-switch transforms run as 2-CTA clusters at n = 16384 (bit 0
 // decompose, 1 mod-up, 2 INTT mod P, 3 mod-down)
 #ifndef LOLA_CLUSTER_MASK

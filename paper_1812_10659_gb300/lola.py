@@ -23,11 +23,12 @@ LOLA_KEY_ROW_SWAP = 2
 
 REPR = {"dense": 1, "sparse": 2, "stacked": 3, "interleaved": 4, "convolution": 5}
 LAYER = {"conv": 1, "combine": 2, "square": 3, "stack": 4, "stacked_rowmajor": 5,
-         "interleaved_rowmajor": 6, "dense_rowmajor": 7, "sparse_colmajor": 8, "masked_shifts": 9, "place": 10}
+         "interleaved_rowmajor": 6, "dense_rowmajor": 7, "sparse_colmajor": 8, "masked_shifts": 9, "place": 10,
+         "mod_switch": 11}
 # representation each layer consumes / produces (0 = not checked)
 LAYER_REPR = {"conv": (5, 1), "combine": (1, 1), "square": (0, 0), "stack": (1, 3),
               "stacked_rowmajor": (3, 4), "interleaved_rowmajor": (4, 2), "dense_rowmajor": (1, 2),
-              "sparse_colmajor": (2, 1), "masked_shifts": (1, 5), "place": (1, 1)}
+              "sparse_colmajor": (2, 1), "masked_shifts": (1, 5), "place": (1, 1), "mod_switch": (0, 0)}
 
 
 class LolaError(RuntimeError):
@@ -73,6 +74,9 @@ _SIGS = {
     "lola_ct_messages": (C.c_size_t, [P]),
     "lola_ct_data": (P, [P]),
     "lola_ct_export": (C.c_int, [P, P, U64P]),
+    "lola_ct_level": (C.c_uint32, [P]),
+    "lola_mod_switch": (C.c_int, [P, P, P, C.c_size_t, C.c_uint32, C.c_uint32, P]),
+    "lola_decrypt_residues_level": (C.c_int, [P, P, P, C.c_size_t, C.c_uint32, U64P]),
     "lola_ct_import": (C.c_int, [P, U64P, C.c_size_t, C.POINTER(P)]),
     "lola_ct_copy_messages": (C.c_int, [P, P, C.c_size_t, P, C.c_size_t, C.c_size_t, P]),
     "lola_ct_upload": (C.c_int, [P, P, P, P]),
@@ -234,10 +238,17 @@ def lola_ct_destroy(ct):
     load().lola_ct_destroy(ct)
 
 
+def lola_ct_level(ct) -> int:
+    return int(load().lola_ct_level(ct))
+
+
 def lola_ct_export(ctx, ct, shape_tail):
-    """shape_tail = (k_t, 2, L, n); returns [n_msg][k_t][2][L][n] coefficient form."""
+    """shape_tail = (k_t, 2, L, n); returns [n_msg][k_t][2][L'][n] coefficient form,
+    L' = the handle's level (L unless a network switched modulus)."""
     m = lola_ct_messages(ct)
-    out = np.zeros((m,) + tuple(shape_tail), dtype=np.uint64)
+    tail = list(shape_tail)
+    tail[2] = lola_ct_level(ct)
+    out = np.zeros((m,) + tuple(tail), dtype=np.uint64)
     _check(load().lola_ct_export(ctx, ct, out.ctypes.data_as(U64P)))
     return out
 
@@ -278,6 +289,13 @@ def lola_decrypt_residues(ctx, keys, ct, k_t, n):
     return out
 
 
+def lola_decrypt_residues_level(ctx, keys, d_ct, n_msg, level, k_t, n):
+    """Decrypt device ciphertexts [n_msg][k_t][2][level][n] (e.g. lola_mod_switch output)."""
+    out = np.zeros((n_msg, k_t, n), dtype=np.uint64)
+    _check(load().lola_decrypt_residues_level(ctx, keys, dptr(d_ct), n_msg, level, out.ctypes.data_as(U64P)))
+    return out
+
+
 # --------------------------------------------------------------- primitives
 
 def lola_ntt_forward(ctx, data, n_polys, n_limbs, stream=None):
@@ -314,6 +332,11 @@ def lola_rotate_noalloc(ctx, keys, inp, out, count, step, stream=None):
 
 
 NOALLOC_SCRATCH_BYTES = 32 << 20
+
+
+def lola_mod_switch(ctx, inp, out, count, L_from, L_to, stream=None):
+    """Modulus switching of `count` ciphertexts [2][L_from][n] to [2][L_to][n]."""
+    _check(load().lola_mod_switch(ctx, dptr(inp), dptr(out), count, L_from, L_to, stream_handle(stream)))
 
 
 def lola_multiply(ctx, keys, a, b, out, count, t_index=None, stream=None):
@@ -397,8 +420,8 @@ def lola_net_create(ctx, input_desc: dict, layers: list) -> Network:
             rows, cols = wa.shape
             wp = wa.ctypes.data_as(I64P)
         rin, rout = LAYER_REPR[op]
-        arr[i] = lola_layer(LAYER[op], rin, rout, rows, cols, wp, Ld.get("d", 0), Ld.get("copies", 0),
-                            Ld.get("stride", 0))
+        d = Ld["L"] if op == "mod_switch" else Ld.get("d", 0)
+        arr[i] = lola_layer(LAYER[op], rin, rout, rows, cols, wp, d, Ld.get("copies", 0), Ld.get("stride", 0))
     out = P()
     _check(load().lola_net_create(ctx, C.byref(inp), arr, len(layers), C.byref(out)))
     return Network(out, keep)

@@ -4,6 +4,8 @@ network on the MNIST-shaped weights and images."""
 import os
 import sys
 
+import numpy as np
+
 import workloads as W
 from oracle import lola as OL
 
@@ -35,3 +37,57 @@ def test_plain_cifar_matches_oracle_integer_network():
     x = OL.int_square(x)
     x = OL.int_square(OL.int_dense(x, W.cifar_dense2(net)))
     assert bench.plain_cifar(img, net) == OL.int_dense(x, net.w3)
+
+
+def test_op_counts_by_level_match_the_plan():
+    """bench.py's per-level operation counts (used to scale the oracle's
+    per-operation times) are the MNIST plan's, counted on slot vectors with
+    the modulus switches in place."""
+    lola = OL
+
+    class LevelCount(lola.SlotEval):
+        def __init__(self, n, t, L):
+            super().__init__(n, t)
+            self.level, self.c = L, {}
+
+        def _k(self, op):
+            d = self.c.setdefault(self.level, {"rot": 0, "square": 0, "mul_plain": 0, "mul_scalar": 0, "add": 0})
+            d[op] += 1
+
+        def add(self, a, b):
+            self._k("add")
+            return super().add(a, b)
+
+        def rot(self, a, k):
+            self._k("rot")
+            return super().rot(a, k)
+
+        def rot_rows(self, a):
+            self._k("rot")
+            return super().rot_rows(a)
+
+        def mul_plain(self, a, v):
+            self._k("mul_plain")
+            return super().mul_plain(a, v)
+
+        def mul_scalar(self, a, w):
+            self._k("mul_scalar")
+            return super().mul_scalar(a, w)
+
+        def square(self, a):
+            self._k("square")
+            return super().square(a)
+
+        def mod_switch(self, msgs, Lv):
+            self.level = Lv
+            return msgs
+
+    n, t = 16384, W.T30[0]
+    net = W.mnist_net()
+    ev = LevelCount(n, t, 5)
+    msgs, pos = lola.pack_convolution(W.image(), net.kh, net.kw, net.stride, n)
+    lola.run_network(ev, W.layers_mnist(net, n, W.MNIST_LEVELS),
+                     lola.State([np.array(m, np.int64) % t for m in msgs], pos))
+    assert ev.c == bench.OP_COUNTS_LEVELS["mnist"]
+    for op in ("rot", "square", "mul_plain", "mul_scalar", "add"):
+        assert sum(c[op] for c in ev.c.values()) == bench.OP_COUNTS["mnist"][op]

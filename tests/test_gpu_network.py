@@ -69,7 +69,10 @@ def test_dense64_bit_exact_vs_oracle():
         Lb.lola_ctx_destroy(ctx)
 
 
-def test_mini_mnist_bit_exact_vs_oracle():
+@pytest.mark.parametrize("levels", [None, (4, 2), (3, 1)])
+def test_mini_mnist_bit_exact_vs_oracle(levels):
+    # levels: modulus switching after each square (every later ciphertext,
+    # including the relinearisation at level 4 or 3, compared word for word)
     need_gpu()
     Lb = lib()
     n = 1024
@@ -78,7 +81,7 @@ def test_mini_mnist_bit_exact_vs_oracle():
     t = ps.t[0]
     mnet = W.mnist_net(seed=7, maps=2, hidden=12, classes=3, h=12, w=12, k=3, stride=2)
     img = W.image(seed=7, h=12, w=12)
-    layers = W.layers_mnist(mnet, n)
+    layers = W.layers_mnist(mnet, n, levels)
     ctx = make_ctx(ps)
     try:
         msgs, win = Lb.lola_pack_convolution(img, 3, 3, 2, n)
@@ -88,13 +91,15 @@ def test_mini_mnist_bit_exact_vs_oracle():
         out = Lb.lola_ct_create(ctx, 3)
         Lb.lola_eval_network(ctx, ev, net, ct, out)
         got = Lb.lola_ct_export(ctx, out, (1, 2, P.L, n))[:, 0]
+        assert Lb.lola_ct_level(out) == (levels[1] if levels else P.L)
         ok = oracle_keys(P, net, 11)
         octs = [bfv.encrypt(P, ok.pk, encoding.encode(m, t), t, 5, i) for i, m in enumerate(msgs)]
         st = OL.run_network(OL.HEEval(P, ok, t), layers, OL.State(octs, [(0, i) for i in range(win)]))
         for o in range(3):
             assert np.array_equal(got[o, 0], st.msgs[o].c[0]) and np.array_equal(got[o, 1], st.msgs[o].c[1]), o
-        res = Lb.lola_decrypt_residues(ctx, sk, out, 1, n)
-        assert [int(res[m, 0, s]) for m, s in net.output_map()] == [v % t for v in mnist_int(mnet, img)]
+        if levels != (3, 1):     # one 60-bit prime leaves no noise budget for the last layer (oracle: -15 bits)
+            res = Lb.lola_decrypt_residues(ctx, sk, out, 1, n)
+            assert [int(res[m, 0, s]) for m, s in net.output_map()] == [v % t for v in mnist_int(mnet, img)]
         for h in (ct, out):
             Lb.lola_ct_destroy(h)
         Lb.lola_keys_destroy(sk)
@@ -110,7 +115,7 @@ def test_full_mnist_batched_decrypts_to_integer_network():
     ps = W.params_mnist()
     n = ps.n
     mnet = W.mnist_net()
-    layers = W.layers_mnist(mnet, n)
+    layers = W.layers_mnist(mnet, n, W.MNIST_LEVELS)
     ctx = make_ctx(ps)
     try:
         B = 2
@@ -128,7 +133,7 @@ def test_full_mnist_batched_decrypts_to_integer_network():
         Lb.lola_eval_network(ctx, ev, net, ct, out2)                  # graph replay
         a = Lb.lola_ct_export(ctx, out, (3, 2, ps.L, n))
         b = Lb.lola_ct_export(ctx, out2, (3, 2, ps.L, n))
-        assert np.array_equal(a, b)
+        assert a.shape[3] == W.MNIST_LEVELS[1] and np.array_equal(a, b)
         dec = Lb.lola_decrypt(ctx, sk, out, n)
         omap = net.output_map()
         for r in range(B):

@@ -275,3 +275,72 @@ def test_adversarial_lifts_near_half_q(setup):
     finally:
         Lb.lola_ct_destroy(A)
         Lb.lola_ct_destroy(out)
+
+
+@pytest.mark.parametrize("n,L,levels", [(32, 3, [(3, 2), (3, 1), (2, 1)]), (1024, 5, [(5, 4), (5, 2), (4, 2)]),
+                                        (16384, 5, [(5, 4), (5, 2)])])
+def test_mod_switch_matches_oracle(n, L, levels):
+    """Modulus switching of random ciphertexts (uniform residues, so the
+    centered residues of the dropped primes take both signs) and of
+    encryptions: every word equal to the oracle's, the encryptions still
+    decrypting to their slots at the lower level."""
+    need_gpu()
+    Lb = lib()
+    ps = W.params_small(n, L=L, K=1, t=[W.T30[0]])
+    P = oracle_params(ps)
+    t = ps.t[0]
+    ctx = make_ctx(ps)
+    sk, _ = Lb.lola_keygen(ctx, 77, [], 0)
+    okeys = bfv.keygen(P, 77, rotations=[], relin=False)
+    try:
+        cnt = 3
+        host = W.random_residues(n + L, (cnt, 2), ps.q[:L], n)                # coefficient form
+        slots = np.random.default_rng(n).integers(0, 1 << 20, (2, n))
+        encs = [bfv.encrypt(P, okeys.pk, encoding.encode(v, t), t, 5, i) for i, v in enumerate(slots)]
+        arr = np.concatenate([host, ct_stack(encs)[:, 0]])                    # [cnt + 2][2][L][n]
+        src = Lb.lola_ct_import(ctx, arr[:, None])
+        for L1, L2 in levels:
+            if L1 < L:      # start from the oracle's level-L1 ciphertexts, in NTT form
+                start = [bfv.mod_switch_to(P, bfv.Ciphertext([a[0], a[1]], t), L1) for a in arr]
+                base = torch_u64(np.stack([np.stack(c.c) for c in start]))
+                Lb.lola_ntt_forward(ctx, base, len(arr) * 2, L1)
+            else:
+                base = Lb.lola_ct_data(src)
+            out = torch_u64(np.zeros((len(arr), 2, L2, n), np.uint64))
+            Lb.lola_mod_switch(ctx, base, out, len(arr), L1, L2)
+            Lb.lola_ntt_inverse(ctx, out, len(arr) * 2, L2)
+            got = host_u64(out).reshape(len(arr), 2, L2, n)
+            P1 = bfv.params_at_level(P, L1)
+            for i, a in enumerate(arr):
+                c = bfv.Ciphertext([a[0], a[1]], t)
+                if L1 < L:
+                    c = bfv.mod_switch_to(P, c, L1)
+                ref = bfv.mod_switch_to(P1, c, L2)
+                assert np.array_equal(got[i, 0], ref.c[0]) and np.array_equal(got[i, 1], ref.c[1]), (L1, L2, i)
+            # the encryptions decrypt at level L2 (device layout, NTT form)
+            Lb.lola_ntt_forward(ctx, out, len(arr) * 2, L2)
+            res = Lb.lola_decrypt_residues_level(ctx, sk, out[cnt:], 2, L2, 1, n)
+            for m in range(2):
+                assert np.array_equal(res[m, 0], slots[m] % t), (L1, L2, m)
+        Lb.lola_ct_destroy(src)
+    finally:
+        Lb.lola_keys_destroy(sk)
+        Lb.lola_ctx_destroy(ctx)
+
+
+def test_mod_switch_rejects_bad_levels_and_overlap():
+    need_gpu()
+    Lb = lib()
+    ps = W.params_small(256, L=3, K=1)
+    ctx = make_ctx(ps)
+    try:
+        buf = torch_u64(np.zeros((2, 2, 3, 256), np.uint64))
+        out = torch_u64(np.zeros((2, 2, 3, 256), np.uint64))
+        for lf, lt in ((3, 4), (4, 2), (2, 3), (3, 0)):
+            with pytest.raises(Lb.LolaError):
+                Lb.lola_mod_switch(ctx, buf, out, 2, lf, lt)
+        with pytest.raises(Lb.LolaError):
+            Lb.lola_mod_switch(ctx, buf, buf, 2, 3, 2)
+        Lb.lola_mod_switch(ctx, buf, out, 0, 3, 2)          # empty batch: no-op
+    finally:
+        Lb.lola_ctx_destroy(ctx)

@@ -224,23 +224,34 @@ def _ceil_log2(k: int) -> int:
     return max(0, (k - 1).bit_length())
 
 
-def layers_mnist(net: MnistNet, n: int) -> list:
+# Ciphertext primes kept after each square of the MNIST-shaped network at
+# L = 5: the oracle's exact noise measurement (full network, n = 16384)
+# leaves a 23-bit margin at the output either way, because modulus switching
+# divides the noise with Q while it is far above the rounding term.
+MNIST_LEVELS = (4, 2)
+
+
+def layers_mnist(net: MnistNet, n: int, levels=None) -> list:
     """Sec. 4.3 / Table 1: conv (convolution representation) -> combine maps
     -> square -> stack -> stacked row-major dense -> square -> interleaved
-    row-major dense."""
+    row-major dense.  levels = (L1, L2): switch modulus to L1 primes after the
+    first square and to L2 after the second (None: no switching)."""
     maps, hidden = net.conv_w.shape[0], net.dense1_w.shape[0]
     oh = -(-(net.h - net.kh) // net.stride) + 1
     ow = -(-(net.w - net.kw) // net.stride) + 1
     k1 = maps * oh * ow
     d = _ceil_log2(k1)
     copies = n >> d
+    ms = ([{"op": "mod_switch", "L": levels[0]}], [{"op": "mod_switch", "L": levels[1]}]) if levels else ([], [])
     return [
         {"op": "conv", "weights": net.conv_w},
         {"op": "combine", "stride": oh * ow},
         {"op": "square"},
+        *ms[0],
         {"op": "stack", "d": d, "copies": copies},
         {"op": "stacked_rowmajor", "weights": net.dense1_w, "d": d, "copies": copies},
         {"op": "square"},
+        *ms[1],
         {"op": "interleaved_rowmajor", "weights": net.dense2_w},
     ]
 
