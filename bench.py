@@ -5,7 +5,9 @@ One step = one batched evaluation of the whole network (conv row-major,
 combine, square, stack, stacked row-major dense, square, interleaved
 row-major dense; 224 rotations and 2 squares per CRT residue, 3 residues)
 on B encrypted synthetic 28x28 images whose ciphertexts are already resident
-in HBM.  Reported beside it:
+in HBM.  The ciphertexts start with five primes and are modulus-switched to
+four after the first square and to two after the second (the same decrypted
+outputs; --no-mod-switch keeps five throughout).  Reported beside it:
 
 * plain: the same network for one request at a time (B = 1, eager launches,
   no CUDA graph), p50 / p99 latency;
@@ -58,8 +60,8 @@ def parse():
                          "masked on the server (App. C); cifar: the CIFAR-shaped network (Sec. 6.2)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mod-switch", action="store_true",
-                    help="mnist: keep all L primes to the end (default at L = 5: switch to 4 and 2 primes "
-                         "after the two squares)")
+                    help="keep all L primes to the end (default: switch to 4 and 2 primes after the two "
+                         "squares, at L = 5 for mnist and L = 6 for lola_dense and cifar)")
     ap.add_argument("--profile-steps", type=int, default=1)
     ap.add_argument("--mode", choices=["network", "serve", "primitives"], default="network")
     ap.add_argument("--n", type=int, default=16384, help="primitives mode: ring degree")
@@ -68,10 +70,15 @@ def parse():
     args = ap.parse_args()
     if args.L is None:
         args.L = 5 if args.workload == "mnist" else 6
+    import workloads as W
     args.levels = None
-    if args.workload == "mnist" and args.L == 5 and not args.no_mod_switch:
-        import workloads as W
-        args.levels = W.MNIST_LEVELS
+    if not args.no_mod_switch:
+        if args.workload == "mnist" and args.L == 5:
+            args.levels = W.MNIST_LEVELS
+        elif args.workload == "lola_dense" and args.L == 6:
+            args.levels = W.LOLA_DENSE_LEVELS
+        elif args.workload == "cifar" and args.L == 6:
+            args.levels = W.CIFAR_LEVELS
     if args.batch is None:
         args.batch = 2 if args.workload == "cifar" else 16
     return args
@@ -81,10 +88,16 @@ def parse():
 OP_COUNTS = {"mnist": {"rot": 224, "square": 2, "mul_plain": 24, "mul_scalar": 125, "add": 344},
              "lola_dense": {"rot": 326, "square": 2, "mul_plain": 61, "mul_scalar": 125, "add": 422},
              "cifar": {"rot": 57273, "square": 2, "mul_plain": 8162, "mul_scalar": 15936, "add": 77200}}
-# the MNIST-shaped network with modulus switching (5 -> 4 primes after the
-# first square, 4 -> 2 after the second): the same counts split by level
+# the networks with modulus switching (to 4 primes after the first square,
+# to 2 after the second): the same counts split by level
 OP_COUNTS_LEVELS = {"mnist": {5: {"rot": 4, "square": 1, "mul_plain": 0, "mul_scalar": 125, "add": 124},
                               4: {"rot": 80, "square": 1, "mul_plain": 14, "mul_scalar": 0, "add": 80},
+                              2: {"rot": 140, "square": 0, "mul_plain": 10, "mul_scalar": 0, "add": 140}},
+                    "lola_dense": {6: {"rot": 28, "square": 1, "mul_plain": 25, "mul_scalar": 125, "add": 124},
+                                   4: {"rot": 158, "square": 1, "mul_plain": 26, "mul_scalar": 0, "add": 158},
+                                   2: {"rot": 140, "square": 0, "mul_plain": 10, "mul_scalar": 0, "add": 140}},
+                    "cifar": {6: {"rot": 83, "square": 1, "mul_plain": 2, "mul_scalar": 15936, "add": 15936},
+                              4: {"rot": 57050, "square": 1, "mul_plain": 8150, "mul_scalar": 0, "add": 61124},
                               2: {"rot": 140, "square": 0, "mul_plain": 10, "mul_scalar": 0, "add": 140}}}
 WORKLOAD_NAME = {"mnist": "mnist_lola_n16384", "lola_dense": "lola_dense_n16384", "cifar": "cifar_lola_n16384"}
 
@@ -349,11 +362,11 @@ def run_ours(args):
     B = args.batch
     if args.workload == "cifar":
         cnet = W.cifar_net()
-        layers = W.layers_cifar(cnet, n)
+        layers = W.layers_cifar(cnet, n, levels=args.levels)
         net = L.lola_net_create(ctx, {"repr": "convolution", "n_msgs": 3 * cnet.k1 * cnet.k1,
                                       "n_elems": cnet.o1 * cnet.o1}, layers)
     elif args.workload == "lola_dense":
-        layers = W.layers_lola_dense(mnet, n)
+        layers = W.layers_lola_dense(mnet, n, levels=args.levels)
         img_slots = np.asarray(W.dense_image_slots(), dtype=np.int64)
         net = L.lola_net_create(ctx, {"repr": "dense", "n_msgs": 1, "n_elems": 784, "slot": img_slots}, layers)
     else:

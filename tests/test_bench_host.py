@@ -5,6 +5,7 @@ import os
 import sys
 
 import numpy as np
+import pytest
 
 import workloads as W
 from oracle import lola as OL
@@ -39,10 +40,11 @@ def test_plain_cifar_matches_oracle_integer_network():
     assert bench.plain_cifar(img, net) == OL.int_dense(x, net.w3)
 
 
-def test_op_counts_by_level_match_the_plan():
+@pytest.mark.parametrize("workload", ["mnist", "lola_dense", "cifar"])
+def test_op_counts_by_level_match_the_plan(workload):
     """bench.py's per-level operation counts (used to scale the oracle's
-    per-operation times) are the MNIST plan's, counted on slot vectors with
-    the modulus switches in place."""
+    per-operation times) are the plan's, counted on slot vectors with the
+    modulus switches in place."""
     lola = OL
 
     class LevelCount(lola.SlotEval):
@@ -66,6 +68,9 @@ def test_op_counts_by_level_match_the_plan():
             self._k("rot")
             return super().rot_rows(a)
 
+        def rot_hoisted(self, a, steps):
+            return [self.rot_rows(a) if k == 0 else self.rot(a, k) for k in steps]
+
         def mul_plain(self, a, v):
             self._k("mul_plain")
             return super().mul_plain(a, v)
@@ -84,10 +89,21 @@ def test_op_counts_by_level_match_the_plan():
 
     n, t = 16384, W.T30[0]
     net = W.mnist_net()
-    ev = LevelCount(n, t, 5)
-    msgs, pos = lola.pack_convolution(W.image(), net.kh, net.kw, net.stride, n)
-    lola.run_network(ev, W.layers_mnist(net, n, W.MNIST_LEVELS),
-                     lola.State([np.array(m, np.int64) % t for m in msgs], pos))
-    assert ev.c == bench.OP_COUNTS_LEVELS["mnist"]
+    if workload == "mnist":
+        ev = LevelCount(n, t, 5)
+        msgs, pos = lola.pack_convolution(W.image(), net.kh, net.kw, net.stride, n)
+        layers = W.layers_mnist(net, n, W.MNIST_LEVELS)
+    elif workload == "lola_dense":
+        ev = LevelCount(n, t, 6)
+        v, pos = lola.pack_image_rows(W.image(), W.DENSE_IMAGE_WIDTH, n)
+        msgs = [v]
+        layers = W.layers_lola_dense(net, n, levels=W.LOLA_DENSE_LEVELS)
+    else:
+        ev = LevelCount(n, t, 6)
+        cnet = W.cifar_net()
+        msgs, pos = lola.pack_convolution(W.cifar_padded(W.cifar_image(), cnet.pad), cnet.k1, cnet.k1, cnet.stride, n)
+        layers = W.layers_cifar(cnet, n, levels=W.CIFAR_LEVELS)
+    lola.run_network(ev, layers, lola.State([np.array(m, np.int64) % t for m in msgs], pos))
+    assert ev.c == bench.OP_COUNTS_LEVELS[workload]
     for op in ("rot", "square", "mul_plain", "mul_scalar", "add"):
-        assert sum(c[op] for c in ev.c.values()) == bench.OP_COUNTS["mnist"][op]
+        assert sum(c[op] for c in ev.c.values()) == bench.OP_COUNTS[workload][op]

@@ -241,10 +241,12 @@ def lola_dense_input(net, width):
             "slot": W.dense_image_slots(net.h, net.w, width)}
 
 
-def test_mini_lola_dense_bit_exact_vs_oracle():
+@pytest.mark.parametrize("levels", [None, (4, 2)])
+def test_mini_lola_dense_bit_exact_vs_oracle(levels):
     """LoLa-Dense (App. C) on a reduced network: the dense image message is
     masked into the convolution representation on the server; every output
-    ciphertext bit-exact against the oracle with the same keys and input."""
+    ciphertext bit-exact against the oracle with the same keys and input
+    (levels: modulus switching after the squares)."""
     need_gpu()
     Lb = lib()
     n = 1024
@@ -254,7 +256,7 @@ def test_mini_lola_dense_bit_exact_vs_oracle():
     mnet = W.mnist_net(seed=7, maps=2, hidden=12, classes=3, h=12, w=12, k=3, stride=2)
     img = W.image(seed=7, h=12, w=12)
     width = 13
-    layers = W.layers_lola_dense(mnet, n, width)
+    layers = W.layers_lola_dense(mnet, n, width, levels)
     ctx = make_ctx(ps)
     try:
         net = Lb.lola_net_create(ctx, lola_dense_input(mnet, width), layers)
@@ -286,7 +288,7 @@ def test_full_lola_dense_batched_decrypts_to_integer_network():
     ps = W.params_mnist(6)
     n = ps.n
     mnet = W.mnist_net()
-    layers = W.layers_lola_dense(mnet, n)
+    layers = W.layers_lola_dense(mnet, n, levels=W.LOLA_DENSE_LEVELS)
     ctx = make_ctx(ps)
     try:
         B = 2
@@ -372,7 +374,8 @@ def cifar_int(net, img):
     return OL.int_dense(x, net.w3)
 
 
-def test_mini_cifar_bit_exact_vs_oracle():
+@pytest.mark.parametrize("levels", [None, (4, 2)])
+def test_mini_cifar_bit_exact_vs_oracle(levels):
     need_gpu()
     Lb = lib()
     n = 1024
@@ -381,7 +384,7 @@ def test_mini_cifar_bit_exact_vs_oracle():
     t = ps.t[0]
     net_ = W.cifar_net(seed=9, C=2, h=8, w=8, pad=2, k1=4, maps1=6, k2=2, maps2=3, classes=2)
     img = W.cifar_image(seed=9, C=2, h=8, w=8)
-    layers = W.layers_cifar(net_, n)
+    layers = W.layers_cifar(net_, n, levels=levels)
     msgs, pos = OL.pack_convolution(W.cifar_padded(img, net_.pad), net_.k1, net_.k1, net_.stride, n)
     ctx = make_ctx(ps)
     try:
@@ -417,7 +420,7 @@ def test_full_cifar_decrypts_to_integer_network():
     n = ps.n
     net_ = W.cifar_net()
     img = W.cifar_image(idx=3)
-    layers = W.layers_cifar(net_, n)
+    layers = W.layers_cifar(net_, n, levels=W.CIFAR_LEVELS)
     msgs, win = Lb.lola_pack_convolution_channels(W.cifar_padded(img, net_.pad), net_.k1, net_.k1, net_.stride, n)
     ctx = make_ctx(ps)
     try:

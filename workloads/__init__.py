@@ -294,11 +294,33 @@ def combine_shifts(slots, k: int) -> list:
     return shifts
 
 
-def layers_lola_dense(net: MnistNet, n: int, width: int = DENSE_IMAGE_WIDTH) -> list:
+# LoLa-Dense and the CIFAR-shaped network at L = 6: primes kept after each
+# square (oracle's exact noise measurement at n = 16384: +30.3 bits at the
+# LoLa-Dense output, +32.7 at the CIFAR output of the 8-output reduction;
+# the switch to 4 primes costs 17.5 bits because the noise falls to the
+# rounding term there).
+LOLA_DENSE_LEVELS = (4, 2)
+CIFAR_LEVELS = (4, 2)
+
+
+def _with_levels(layers: list, after_squares, levels) -> list:
+    """Insert a modulus switch after the given layer indices (the squares)."""
+    if not levels:
+        return layers
+    out = []
+    for i, Ly in enumerate(layers):
+        out.append(Ly)
+        if i in after_squares:
+            out.append({"op": "mod_switch", "L": levels[after_squares.index(i)]})
+    return out
+
+
+def layers_lola_dense(net: MnistNet, n: int, width: int = DENSE_IMAGE_WIDTH, levels=None) -> list:
     """LoLa-Dense (App. C, Table 3): one dense image message masked into the
     convolution representation (window (i, j) at the slot of its upper-left
     pixel), convolution row-major, maps combined by collision-free shifts,
-    square, stack, stacked row-major, square, interleaved row-major."""
+    square, stack, stacked row-major, square, interleaved row-major.
+    levels = (L1, L2): modulus switching after the two squares."""
     G = conv_gather(net)
     slots = dense_image_slots(net.h, net.w, width)
     corner = [slots[int(g)] for g in G[0]]
@@ -307,7 +329,7 @@ def layers_lola_dense(net: MnistNet, n: int, width: int = DENSE_IMAGE_WIDTH) -> 
     span = max(corner) + shifts[-1] + 1
     d = _ceil_log2(span)
     copies = n >> d
-    return [
+    return _with_levels([
         {"op": "masked_shifts", "weights": G},
         {"op": "conv", "weights": net.conv_w},
         {"op": "combine", "shifts": shifts},
@@ -316,7 +338,7 @@ def layers_lola_dense(net: MnistNet, n: int, width: int = DENSE_IMAGE_WIDTH) -> 
         {"op": "stacked_rowmajor", "weights": net.dense1_w, "d": d, "copies": copies},
         {"op": "square"},
         {"op": "interleaved_rowmajor", "weights": net.dense2_w},
-    ]
+    ], [3, 6], levels)
 
 
 def cifar_place_targets(maps: int, per_map: int, n: int) -> list:
@@ -343,17 +365,17 @@ def cifar_place_targets(maps: int, per_map: int, n: int) -> list:
     return T
 
 
-def layers_cifar(net: CifarNet, n: int, dense2: np.ndarray | None = None) -> list:
+def layers_cifar(net: CifarNet, n: int, dense2: np.ndarray | None = None, levels=None) -> list:
     """Sec. 6.2: convolution row-major on the convolution representation
     (C*k1*k1 messages), the maps combined into one message, square, the
     second convolution as dense row-major (sparse output), sparse -> dense by
     masks and additions (column-major with the identity), square, dense
-    row-major."""
+    row-major.  levels = (L1, L2): modulus switching after the two squares."""
     maps1 = net.w1.shape[0]
     per = net.o1 * net.o1
     D2 = cifar_dense2(net) if dense2 is None else dense2
     k2 = D2.shape[0]
-    return [
+    return _with_levels([
         {"op": "conv", "weights": net.w1},
         {"op": "place", "weights": np.array([cifar_place_targets(maps1, per, n)], dtype=np.int64)},
         {"op": "square"},
@@ -361,7 +383,7 @@ def layers_cifar(net: CifarNet, n: int, dense2: np.ndarray | None = None) -> lis
         {"op": "sparse_colmajor", "weights": np.eye(k2, dtype=np.int64)},
         {"op": "square"},
         {"op": "dense_rowmajor", "weights": net.w3},
-    ]
+    ], [2, 5], levels)
 
 
 def layers_head(Wh: np.ndarray, n: int) -> list:
