@@ -59,6 +59,7 @@ def parse():
                     help="mnist: convolution-representation input (Sec. 4.3); lola_dense: dense input "
                          "masked on the server (App. C); cifar: the CIFAR-shaped network (Sec. 6.2)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the library's default launch geometry")
     ap.add_argument("--no-mod-switch", action="store_true",
                     help="keep all L primes to the end (default: switch to 4 and 2 primes after the two "
                          "squares, at L = 5 for mnist and L = 6 for lola_dense and cifar)")
@@ -359,6 +360,9 @@ def run_ours(args):
     n, kt, Lq = ps.n, len(ps.t), ps.L
     mnet = W.mnist_net()
     ctx = L.lola_ctx_create(ps.n, ps.q, ps.L, ps.K, ps.t, device=local)
+    t_tune = time.perf_counter()
+    tune = L.lola_autotune(ctx, stream) if not args.no_autotune else None   # key-switch launch geometry
+    t_tune = time.perf_counter() - t_tune
     B = args.batch
     if args.workload == "cifar":
         cnet = W.cifar_net()
@@ -576,6 +580,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": WORKLOAD_NAME[args.workload], "batch_per_gpu": B, "n": n, "L": Lq, "K": 1, "k_t": kt,
                        "levels": [Lq] + list(args.levels or []),
+                       "autotune": ({"table": tune["table"], "seconds": round(t_tune, 2)} if tune else "defaults"),
                        "aux_primes": len(L.lola_ctx_aux_primes(ctx)), "parallelism": f"replicas x{world}",
                        "l2": (f"L2 flushed between timed steps (256 MB write; {in_bytes / 1e6:.0f} MB of input "
                               "ciphertexts per step)") if flush is not None else
@@ -628,6 +633,8 @@ def run_primitives(args):
     ps = W.params_sweep(args.n, args.L)
     n, Lq, B = ps.n, ps.L, args.batch
     ctx = L.lola_ctx_create(ps.n, ps.q, ps.L, ps.K, ps.t)
+    if not args.no_autotune:
+        L.lola_autotune(ctx)
     stream = torch.cuda.current_stream()
     host = W.random_residues(11, (B, 2), ps.q[:Lq], n)
     steps = [int(s) for s in W.rotation_steps(11, B, n)]
@@ -701,6 +708,9 @@ def run_serve(args):
     n = ps2.n
     ctx2 = L.lola_ctx_create(ps2.n, ps2.q, ps2.L, ps2.K, ps2.t)
     ctx4 = L.lola_ctx_create(ps4.n, ps4.q, ps4.L, ps4.K, ps4.t)
+    if not args.no_autotune:
+        L.lola_autotune(ctx2)
+        L.lola_autotune(ctx4)
     mnet, Wh = W.mnist_net(), W.head_weights()
     d2, l2 = {"repr": "convolution", "n_msgs": 25, "n_elems": 169}, W.layers_mnist(mnet, n, W.MNIST_LEVELS)
     d4, l4 = {"repr": "dense", "n_msgs": 1, "n_elems": 4096}, W.layers_head(Wh, n)

@@ -220,6 +220,32 @@ int lola_decrypt_residues_level(lola_ctx* ctx, const lola_keys* keys, const uint
 int lola_mul_plain(lola_ctx* ctx, const uint64_t* in, const int64_t* slots, uint64_t* out, size_t count,
                    const uint32_t* t_index, void* stream);
 
+/* ---------------------------------------------------------------- tuning
+ * Launch geometry of the key-switch transforms (kernel 0 decompose, 1 mod-up,
+ * 2 INTT mod P, 3 mod-down) for each of LOLA_TUNE_BUCKETS launch sizes
+ * (limb transforms per launch: < 64, < 256, < 1024, < 4096, < 16384, more):
+ * 0 = one CTA per limb, 1 = a 2-CTA cluster per limb with 16 words per
+ * thread, 2 = a cluster with 32 words per thread (1 and 2 at n = 16384
+ * only).  Every geometry computes the same words.  Without tuning the
+ * library uses clusters for kernels 1-3 at n = 16384 (16 words below 400
+ * limb transforms, else 32) and one CTA for decompose.
+ * lola_autotune times whole rotations (CUDA events, zero-filled buffers
+ * and key, 1 to 256 ciphertexts: about 1.9 GB at n = 16384, L = 5, freed on
+ * return) with each kernel's entry for the bucket its launch falls in set
+ * to each geometry in turn, keeps a geometry other than the default only
+ * when the rotations get more than 3 % faster, and installs the table for
+ * the context and all of its modulus-switching levels (a fraction of a
+ * second); run it while nothing else uses the context.  lola_tune_get copies the table (4 x 6 bytes, kernel-major) and,
+ * if us is not NULL, the measured microseconds per launch (4 x 6 x 3 floats,
+ * 0 where not run); LOLA_E_STATE when no table is installed.  lola_tune_set
+ * installs a table (e.g. from a cache file); NULL restores the defaults.
+ * Errors: LOLA_E_PARAM (bad entry), LOLA_E_NOMEM, LOLA_E_CUDA. */
+#define LOLA_TUNE_KERNELS 4
+#define LOLA_TUNE_BUCKETS 6
+int lola_autotune(lola_ctx* ctx, void* stream);
+int lola_tune_get(const lola_ctx* ctx, uint8_t* table, float* us);
+int lola_tune_set(lola_ctx* ctx, const uint8_t* table);
+
 /* ------------------------------------------------------------ networks
  * Message representations (Sec. 4.2.1). */
 typedef enum {

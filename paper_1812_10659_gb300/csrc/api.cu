@@ -352,6 +352,36 @@ int lola_mod_switch(lola_ctx* ctx, const uint64_t* in, uint64_t* out, size_t cou
   return rc;
 }
 
+int lola_autotune(lola_ctx* ctx, void* stream) {
+  CHECK(ctx, LOLA_E_PARAM, "null argument");
+  LOLA_CUDA_TRY(cudaSetDevice(ctx->c->device));
+  return autotune(ctx->c, to_stream(stream));
+}
+
+int lola_tune_get(const lola_ctx* ctx, uint8_t* table, float* us) {
+  CHECK(ctx && table, LOLA_E_PARAM, "null argument");
+  const Tune& t = ctx->c->tune;
+  CHECK(t.on, LOLA_E_STATE, "no tuning table installed");
+  memcpy(table, t.v, sizeof(t.v));
+  if (us) memcpy(us, t.us, sizeof(t.us));
+  return LOLA_OK;
+}
+
+int lola_tune_set(lola_ctx* ctx, const uint8_t* table) {
+  CHECK(ctx, LOLA_E_PARAM, "null argument");
+  Tune t;
+  if (table) {
+    for (int i = 0; i < TUNE_KERNELS * TUNE_BUCKETS; ++i) {
+      CHECK(table[i] < TV_COUNT, LOLA_E_PARAM, "tuning entry out of range");
+      CHECK(table[i] == TV_CTA || ctx->c->logn == 14, LOLA_E_PARAM, "cluster geometries exist at n = 16384 only");
+    }
+    memcpy(t.v, table, sizeof(t.v));
+    t.on = true;
+  }
+  ctx->c->tune = t;
+  return LOLA_OK;
+}
+
 int lola_multiply(lola_ctx* ctx, const lola_keys* keys, const uint64_t* a, const uint64_t* b, uint64_t* out,
                   size_t count, const uint32_t* t_index, void* stream) {
   CHECK(ctx && keys && ((a && b && out) || !count), LOLA_E_PARAM, "null argument");

@@ -67,6 +67,10 @@ int mod_switch(Ctx* c, const uint64_t* in, uint64_t* out, size_t count, uint32_t
                uint64_t* scratch, cudaStream_t s);
 
 size_t multiply_scratch_words(const Ctx* c, size_t count, bool square);
+
+// Time every launch geometry of the key-switch transforms per launch-size
+// bucket on synthetic buffers and install the fastest in the root context.
+int autotune(Ctx* c, cudaStream_t s);
 int multiply(Ctx* c, const uint64_t* x, const uint64_t* y, uint64_t* out, size_t count, const uint32_t* d_tidx,
              uint32_t tidx_div, const uint64_t* relin_key, uint64_t* scratch, cudaStream_t s);
 

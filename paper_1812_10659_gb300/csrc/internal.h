@@ -63,6 +63,20 @@ struct Profiler {
   }
 };
 
+// Launch geometry of the key-switch transforms (decompose, mod-up, INTT mod
+// P, mod-down) per launch-size bucket: one CTA per limb, or (n = 16384) a
+// 2-CTA cluster per limb with 16 or 32 words per thread.  Chosen by timing
+// (autotune) or by the built-in defaults when `on` is false.
+constexpr int TUNE_KERNELS = 4;
+constexpr int TUNE_BUCKETS = 6;     // limb transforms per launch: <64, <256, <1024, <4096, <16384, more
+enum TuneVariant : uint8_t { TV_CTA = 0, TV_CLUSTER16 = 1, TV_CLUSTER32 = 2, TV_COUNT = 3 };
+struct Tune {
+  bool on = false;
+  uint8_t v[TUNE_KERNELS][TUNE_BUCKETS] = {};
+  float us[TUNE_KERNELS][TUNE_BUCKETS][TV_COUNT] = {};   // measured microseconds per launch (0: not run)
+};
+int tune_bucket(size_t units);
+
 // -------------------------------------------------------------------- context
 struct Ctx {
   int device = 0;
@@ -73,6 +87,7 @@ struct Ctx {
   DevBuf d_const, d_tw, d_slotpos;   // d_slotpos[pos] = slot whose value sits at NTT position pos
   std::atomic<uint64_t> launches{0};
   Profiler prof;
+  Tune tune;                      // root context's table applies to every level
   // Modulus switching: a context of the first L' < L ciphertext primes (same
   // special prime, plaintext moduli and keys) is a child of the full one.
   // Launch counts and profiles go to the root; children live in its map.

@@ -63,6 +63,10 @@ namespace k {
 // c is the full context.
 int mod_switch_drop(Ctx* c, const uint64_t* in, uint64_t* top, uint64_t* out, size_t count, uint32_t L1,
                     cudaStream_t s);
+// launch geometry (TuneVariant) the key-switch transform `kernel` (0 decompose,
+// 1 mod-up, 2 INTT mod P, 3 mod-down) uses for `units` limb transforms
+// without a tuning table (ntt_keyswitch.cu)
+int default_geometry(const Ctx* c, int kernel, size_t units);
 // NTT family (ntt_kernels.cu)
 int ntt_fwd_map(Ctx* c, const uint64_t* in, uint64_t* out, size_t n_limbpolys, uint32_t limbs, const PrimeMap& pm,
                 cudaStream_t s);

@@ -191,12 +191,27 @@ int mod_switch_drop(Ctx* c, const uint64_t* in, uint64_t* top, uint64_t* out, si
 #endif
 static constexpr unsigned kClusterMask = LOLA_CLUSTER_MASK;
 
+// the library's default geometry: clusters at n = 16384 for the kernels in
+// kClusterMask, with 16 words per thread below LOLA_CL_SMALL_UNITS
+int default_geometry(const Ctx* c, int kernel, size_t units) {
+  if (c->logn != CL_LOGN || !(kClusterMask & (1u << kernel))) return TV_CTA;
+  return units < LOLA_CL_SMALL_UNITS ? TV_CLUSTER16 : TV_CLUSTER32;
+}
+
+// geometry of one launch: the tuned table, else the default
+static int geometry(const Ctx* c, int kernel, size_t units) {
+  if (c->logn != CL_LOGN) return TV_CTA;
+  const Tune& t = c->root->tune;
+  if (t.on) return t.v[kernel][tune_bucket(units)];
+  return default_geometry(c, kernel, units);
+}
+
 int ks_decompose(Ctx* c, const KsDev& a, cudaStream_t s) {
-  ProfScope ps(c, KI_KS_DECOMPOSE, s, a.count * c->L);
-  if ((kClusterMask & 1u) && c->logn == CL_LOGN) {
-    return ks_decompose_cluster(c, a, s, a.count * c->L < LOLA_CL_SMALL_UNITS);
-  }
-  LOLA_DISPATCH(c->logn, kn_ks_decompose, a.count * c->L, s, c->dev, a);
+  const size_t units = a.count * c->L;
+  ProfScope ps(c, KI_KS_DECOMPOSE, s, units);
+  const int g = geometry(c, 0, units);
+  if (g != TV_CTA) return ks_decompose_cluster(c, a, s, g == TV_CLUSTER16);
+  LOLA_DISPATCH(c->logn, kn_ks_decompose, units, s, c->dev, a);
   return post_launch(c, s);
 }
 
@@ -204,29 +219,29 @@ int ks_modup(Ctx* c, const KsDev& a, bool skip_diag, cudaStream_t s) {
   const uint32_t LK = c->L + c->K;
   const size_t per = skip_diag ? (size_t)c->L * (LK - 1) : (size_t)c->L * LK;
   if (!per) return LOLA_OK;
-  ProfScope ps(c, KI_KS_MODUP, s, a.count * per);
-  if ((kClusterMask & 2u) && c->logn == CL_LOGN) {
-    return ks_modup_cluster(c, a, skip_diag, s, a.count * per < LOLA_CL_SMALL_UNITS);
-  }
-  LOLA_DISPATCH_CFG(CfgM, c->logn, kn_ks_modup, a.count * per, s, c->dev, a, (int)skip_diag);
+  const size_t units = a.count * per;
+  ProfScope ps(c, KI_KS_MODUP, s, units);
+  const int g = geometry(c, 1, units);
+  if (g != TV_CTA) return ks_modup_cluster(c, a, skip_diag, s, g == TV_CLUSTER16);
+  LOLA_DISPATCH_CFG(CfgM, c->logn, kn_ks_modup, units, s, c->dev, a, (int)skip_diag);
   return post_launch(c, s);
 }
 
 int ks_intt_p(Ctx* c, const KsDev& a, cudaStream_t s) {
-  ProfScope ps(c, KI_KS_IP_P, s, a.count * 2);
-  if ((kClusterMask & 4u) && c->logn == CL_LOGN) {
-    return ks_intt_p_cluster(c, a, s, a.count * 2 < LOLA_CL_SMALL_UNITS);
-  }
-  LOLA_DISPATCH(c->logn, kn_ks_intt_p, a.count * 2, s, c->dev, a);
+  const size_t units = a.count * 2;
+  ProfScope ps(c, KI_KS_IP_P, s, units);
+  const int g = geometry(c, 2, units);
+  if (g != TV_CTA) return ks_intt_p_cluster(c, a, s, g == TV_CLUSTER16);
+  LOLA_DISPATCH(c->logn, kn_ks_intt_p, units, s, c->dev, a);
   return post_launch(c, s);
 }
 
 int ks_moddown(Ctx* c, const KsDev& a, cudaStream_t s) {
-  ProfScope ps(c, KI_KS_MODDOWN, s, a.count * 2 * c->L);
-  if ((kClusterMask & 8u) && c->logn == CL_LOGN) {
-    return ks_moddown_cluster(c, a, s, a.count * 2 * c->L < LOLA_CL_SMALL_UNITS);
-  }
-  LOLA_DISPATCH_CFG(CfgM, c->logn, kn_ks_moddown, a.count * 2 * c->L, s, c->dev, a);
+  const size_t units = a.count * 2 * c->L;
+  ProfScope ps(c, KI_KS_MODDOWN, s, units);
+  const int g = geometry(c, 3, units);
+  if (g != TV_CTA) return ks_moddown_cluster(c, a, s, g == TV_CLUSTER16);
+  LOLA_DISPATCH_CFG(CfgM, c->logn, kn_ks_moddown, units, s, c->dev, a);
   return post_launch(c, s);
 }
 

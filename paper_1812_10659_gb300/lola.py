@@ -75,6 +75,9 @@ _SIGS = {
     "lola_ct_data": (P, [P]),
     "lola_ct_export": (C.c_int, [P, P, U64P]),
     "lola_ct_level": (C.c_uint32, [P]),
+    "lola_autotune": (C.c_int, [P, P]),
+    "lola_tune_get": (C.c_int, [P, C.POINTER(C.c_uint8), C.POINTER(C.c_float)]),
+    "lola_tune_set": (C.c_int, [P, C.POINTER(C.c_uint8)]),
     "lola_mod_switch": (C.c_int, [P, P, P, C.c_size_t, C.c_uint32, C.c_uint32, P]),
     "lola_decrypt_residues_level": (C.c_int, [P, P, P, C.c_size_t, C.c_uint32, U64P]),
     "lola_ct_import": (C.c_int, [P, U64P, C.c_size_t, C.POINTER(P)]),
@@ -332,6 +335,63 @@ def lola_rotate_noalloc(ctx, keys, inp, out, count, step, stream=None):
 
 
 NOALLOC_SCRATCH_BYTES = 32 << 20
+
+
+TUNE_KERNELS, TUNE_BUCKETS = 4, 6
+TUNE_NAMES = ("ks_decompose", "ks_modup", "ks_intt_p", "ks_moddown")
+TUNE_GEOMETRY = ("cta", "cluster16", "cluster32")
+
+
+def lola_autotune(ctx, stream=None) -> dict:
+    """Time the key-switch transforms' launch geometries on this device and
+    install the fastest per kernel and launch-size bucket; returns the table."""
+    _check(load().lola_autotune(ctx, stream_handle(stream)))
+    return lola_tune_get(ctx)
+
+
+def lola_tune_get(ctx) -> dict:
+    """{"table": [[geometry per bucket] per kernel], "us": [[[us per geometry]]]}"""
+    t = (C.c_uint8 * (TUNE_KERNELS * TUNE_BUCKETS))()
+    us = (C.c_float * (TUNE_KERNELS * TUNE_BUCKETS * 3))()
+    _check(load().lola_tune_get(ctx, t, us))
+    tab = [[int(t[k * TUNE_BUCKETS + b]) for b in range(TUNE_BUCKETS)] for k in range(TUNE_KERNELS)]
+    tim = [[[round(float(us[(k * TUNE_BUCKETS + b) * 3 + v]), 2) for v in range(3)] for b in range(TUNE_BUCKETS)]
+           for k in range(TUNE_KERNELS)]
+    return {"table": tab, "us": tim}
+
+
+def lola_tune_set(ctx, table=None):
+    """Install a table (list of 4 lists of 6 geometry ids), or None for the defaults."""
+    if table is None:
+        _check(load().lola_tune_set(ctx, None))
+        return
+    flat = [int(x) for row in table for x in row]
+    assert len(flat) == TUNE_KERNELS * TUNE_BUCKETS
+    arr = (C.c_uint8 * len(flat))(*flat)
+    _check(load().lola_tune_set(ctx, arr))
+
+
+def autotune_cached(ctx, path, key: dict, stream=None) -> dict:
+    """Load the table for `key` (device name and parameters) from the JSON
+    cache at `path`, or run lola_autotune and store its result there."""
+    import json
+    cache = {}
+    if os.path.exists(path):
+        try:
+            cache = json.load(open(path))
+        except (OSError, ValueError):
+            cache = {}
+    k = json.dumps(key, sort_keys=True)
+    if k in cache:
+        lola_tune_set(ctx, cache[k]["table"])
+        return dict(cache[k], cached=True)
+    res = lola_autotune(ctx, stream)
+    cache[k] = res
+    tmp = path + ".tmp"
+    with open(tmp, "w") as f:
+        json.dump(cache, f)
+    os.replace(tmp, path)
+    return dict(res, cached=False)
 
 
 def lola_mod_switch(ctx, inp, out, count, L_from, L_to, stream=None):
