@@ -563,6 +563,7 @@ def run_ours(args):
         roofline.update({"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": (hbm_achieved / hbm_peak) if hbm_achieved else None, "peak_source": peak_src})
     roofline["traffic"] = traffic
+    # NTT rate of the mod-up transforms as limb bytes (read + write, 16 n) per second
     ntt_gbs = None
     if "ks_modup" in per_kernel:
         v = per_kernel["ks_modup"]

@@ -119,10 +119,15 @@ size_t rotate_scratch_words(const Ctx* c, size_t count) {
   return w;
 }
 
-// Inner product + (special prime) mod-down, shared by rotation and relinearisation.
-static int ks_finish(Ctx* c, KsDev& a, uint64_t* extra_acc, cudaStream_t s) {
+// Mod-up, inner product and (special prime) mod-down, shared by rotation
+// (have_diag: decompose wrote the diagonal limbs D[i][i]) and
+// relinearisation.
+static int ks_switch(Ctx* c, KsDev& a, uint64_t* extra_acc, bool have_diag, cudaStream_t s) {
   const size_t n = c->n, L = c->L, LK = c->L + c->K;
-  if (!c->K) return k::ks_ip(c, a, true, s);
+  if (!c->K) {
+    TRY(k::ks_modup(c, a, have_diag, s));
+    return k::ks_ip(c, a, true, s);
+  }
   if (L >= 2) {
     a.acc = a.D;
     a.acc_stride = L * LK * n;
@@ -130,6 +135,7 @@ static int ks_finish(Ctx* c, KsDev& a, uint64_t* extra_acc, cudaStream_t s) {
     a.acc = extra_acc;
     a.acc_stride = 2 * LK * n;
   }
+  TRY(k::ks_modup(c, a, have_diag, s));
   TRY(k::ks_ip(c, a, false, s));
   TRY(k::ks_intt_p(c, a, s));
   return k::ks_moddown(c, a, s);
@@ -156,8 +162,7 @@ int rotate(Ctx* c, const uint64_t* in, uint64_t* out, const uint64_t* accum, siz
   a.key = r.key;
   a.gal_div = r.div ? r.div : 1;
   TRY(k::ks_decompose(c, a, s));
-  TRY(k::ks_modup(c, a, true, s));
-  return ks_finish(c, a, a.xP + count * 2 * n, s);
+  return ks_switch(c, a, a.xP + count * 2 * n, true, s);
 }
 
 // Hoisted rotations: every one of `count` ciphertexts rotated by each of
@@ -307,8 +312,7 @@ int multiply(Ctx* c, const uint64_t* x, const uint64_t* y, uint64_t* out, size_t
   a.gal = 1;
   a.key = relin_key;
   a.gal_div = 1;
-  TRY(k::ks_modup(c, a, false, s));
-  return ks_finish(c, a, xP + count * 2 * n, s);
+  return ks_switch(c, a, xP + count * 2 * n, false, s);
 }
 
 // --------------------------------------------------------------------- keys
