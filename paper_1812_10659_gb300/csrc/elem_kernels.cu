@@ -44,8 +44,9 @@ __device__ __forceinline__ uint64_t redc128(unsigned __int128 T, uint64_t q, uin
 // gal_src(k) is odd).
 // LT > 0: the digit count as a compile-time constant (fully unrolled digit
 // loop, all loads of a thread issued together); 0: read it from the context.
+// At most 64 registers, so that 32 warps per SM keep loads in flight.
 template <int LT>
-__global__ void ke_ks_ip(const CtxDev* __restrict__ C, KsDev a, int final_out) {
+__global__ void __launch_bounds__(256, 4) ke_ks_ip(const CtxDev* __restrict__ C, KsDev a, int final_out) {
   const int L = LT > 0 ? LT : C->L, LK = L + C->K, logn = C->logn;
   const size_t n = C->n, half = n >> 1;
   const int J = final_out ? L : LK;
