@@ -55,9 +55,10 @@ def parse():
     ap.add_argument("--plain", type=int, default=8, help="single-request evaluations for plain latency")
     ap.add_argument("--L", type=int, default=None,
                     help="ciphertext primes (default: 5 for mnist, 6 for lola_dense)")
-    ap.add_argument("--workload", choices=["mnist", "lola_dense", "cifar"], default="mnist",
+    ap.add_argument("--workload", choices=["mnist", "lola_dense", "cifar", "head"], default="mnist",
                     help="mnist: convolution-representation input (Sec. 4.3); lola_dense: dense input "
-                         "masked on the server (App. C); cifar: the CIFAR-shaped network (Sec. 6.2)")
+                         "masked on the server (App. C); cifar: the CIFAR-shaped network (Sec. 6.2); "
+                         "head: the transfer-learning head (Sec. 5), 4096 -> 101, one plaintext modulus")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's default launch geometry")
     ap.add_argument("--no-mod-switch", action="store_true",
@@ -70,7 +71,7 @@ def parse():
     ap.add_argument("--duration", type=float, default=10.0, help="serve mode: seconds of arrivals per rate")
     args = ap.parse_args()
     if args.L is None:
-        args.L = 5 if args.workload == "mnist" else 6
+        args.L = {"mnist": 5, "head": HEAD_L}.get(args.workload, 6)
     import workloads as W
     args.levels = None
     if not args.no_mod_switch:
@@ -81,14 +82,18 @@ def parse():
         elif args.workload == "cifar" and args.L == 6:
             args.levels = W.CIFAR_LEVELS
     if args.batch is None:
-        args.batch = 2 if args.workload == "cifar" else 16
+        args.batch = {"cifar": 2, "head": 64}.get(args.workload, 16)
     return args
 
+
+# ciphertext primes of the transfer-learning head (workloads.params_head)
+HEAD_L = 3
 
 # per-residue operation counts of one inference (the plan's, checked by the CPU tests)
 OP_COUNTS = {"mnist": {"rot": 224, "square": 2, "mul_plain": 24, "mul_scalar": 125, "add": 344},
              "lola_dense": {"rot": 326, "square": 2, "mul_plain": 61, "mul_scalar": 125, "add": 422},
-             "cifar": {"rot": 57273, "square": 2, "mul_plain": 8162, "mul_scalar": 15936, "add": 77200}}
+             "cifar": {"rot": 57273, "square": 2, "mul_plain": 8162, "mul_scalar": 15936, "add": 77200},
+             "head": {"rot": 339, "square": 0, "mul_plain": 52, "mul_scalar": 0, "add": 339}}
 # the networks with modulus switching (to 4 primes after the first square,
 # to 2 after the second): the same counts split by level
 OP_COUNTS_LEVELS = {"mnist": {5: {"rot": 4, "square": 1, "mul_plain": 0, "mul_scalar": 125, "add": 124},
@@ -100,7 +105,8 @@ OP_COUNTS_LEVELS = {"mnist": {5: {"rot": 4, "square": 1, "mul_plain": 0, "mul_sc
                     "cifar": {6: {"rot": 83, "square": 1, "mul_plain": 2, "mul_scalar": 15936, "add": 15936},
                               4: {"rot": 57050, "square": 1, "mul_plain": 8150, "mul_scalar": 0, "add": 61124},
                               2: {"rot": 140, "square": 0, "mul_plain": 10, "mul_scalar": 0, "add": 140}}}
-WORKLOAD_NAME = {"mnist": "mnist_lola_n16384", "lola_dense": "lola_dense_n16384", "cifar": "cifar_lola_n16384"}
+WORKLOAD_NAME = {"mnist": "mnist_lola_n16384", "lola_dense": "lola_dense_n16384", "cifar": "cifar_lola_n16384",
+                 "head": "transfer_head_n16384"}
 
 
 # ------------------------------------------------------------------ clocks
@@ -160,6 +166,11 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ CPU baseline
+def workload_params(workload, L):
+    import workloads as W
+    return {"cifar": W.params_cifar, "head": W.params_head}.get(workload, W.params_mnist)(L)
+
+
 def oracle_sample(n_rot=1, n_sq=1, workload="mnist", L=5, levels=None):
     """Time the CPU oracle's operations on the network's parameters (one CRT
     residue) and scale by the network's operation counts for one inference
@@ -170,7 +181,7 @@ def oracle_sample(n_rot=1, n_sq=1, workload="mnist", L=5, levels=None):
 
     import workloads as W
     from oracle import bfv, encoding
-    ps = W.params_mnist(L)
+    ps = workload_params(workload, L)
     P = bfv.Params(ps.n, ps.q, ps.L, ps.K, ps.t)
     keys = bfv.keygen(P, 5, rotations=[1], relin=True)
     t = ps.t[0]
@@ -228,7 +239,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "inferences/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1000,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": WORKLOAD_NAME[args.workload], "n": 16384, "L": args.L, "K": 1, "k_t": 3,
+            "config": {"workload": WORKLOAD_NAME[args.workload], "n": 16384, "L": args.L, "K": 1,
+                       "k_t": len(workload_params(args.workload, args.L).t),
                        "levels": [args.L] + list(args.levels or []),
                        "parallelism": "none (CPU oracle)"},
             "cpu_baseline": {"value": value, "unit": "inferences/s", "cores": 1, "kind": "oracle", "sample": desc},
@@ -356,7 +368,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
 
-    ps = W.params_cifar(args.L) if args.workload == "cifar" else W.params_mnist(args.L)
+    ps = workload_params(args.workload, args.L)
     n, kt, Lq = ps.n, len(ps.t), ps.L
     mnet = W.mnist_net()
     ctx = L.lola_ctx_create(ps.n, ps.q, ps.L, ps.K, ps.t, device=local)
@@ -373,10 +385,14 @@ def run_ours(args):
         layers = W.layers_lola_dense(mnet, n, levels=args.levels)
         img_slots = np.asarray(W.dense_image_slots(), dtype=np.int64)
         net = L.lola_net_create(ctx, {"repr": "dense", "n_msgs": 1, "n_elems": 784, "slot": img_slots}, layers)
+    elif args.workload == "head":
+        Wh = W.head_weights()
+        layers = W.layers_head(Wh, n)
+        net = L.lola_net_create(ctx, {"repr": "dense", "n_msgs": 1, "n_elems": Wh.shape[1]}, layers)
     else:
         layers = W.layers_mnist(mnet, n, args.levels)
         net = L.lola_net_create(ctx, {"repr": "convolution", "n_msgs": 25, "n_elems": 169}, layers)
-    n_in = net.shape()[0]
+    n_in, n_out = net.shape()
     steps_needed = net.rotation_steps()
     sk, ev = L.lola_keygen(ctx, W.DEFAULT_SEED, [s for s in steps_needed if s],
                            L.LOLA_KEY_RELIN | L.LOLA_KEY_ROW_SWAP)
@@ -384,9 +400,14 @@ def run_ours(args):
         imgs = [W.cifar_image(idx=rank * 100000 + i) for i in range(B)]
         packed = np.concatenate([L.lola_pack_convolution_channels(W.cifar_padded(im, cnet.pad), cnet.k1, cnet.k1,
                                                                   cnet.stride, n)[0] for im in imgs])
+    elif args.workload == "head":
+        imgs = [W.feature_vector(idx=rank * 100000 + i) for i in range(B)]
+        packed = np.zeros((B, n), np.int64)
+        for i, x in enumerate(imgs):
+            packed[i, :len(x)] = x
     else:
         imgs = [W.image(idx=rank * 100000 + i) for i in range(B)]
-    if args.workload == "cifar":
+    if args.workload in ("cifar", "head"):
         pass
     elif args.workload == "lola_dense":
         # one dense message per image, line after line (29-slot lines)
@@ -396,10 +417,10 @@ def run_ours(args):
     else:
         packed = np.concatenate([L.lola_pack_convolution(im, 5, 5, 2, n)[0] for im in imgs])
     ct_in = L.lola_encrypt(ctx, sk, packed, 1000 + rank)
-    ct_out = L.lola_ct_create(ctx, B * 10)
+    ct_out = L.lola_ct_create(ctx, B * n_out)
     in_bytes = B * n_in * kt * 2 * Lq * n * 8
     out_level = args.levels[-1] if args.levels else Lq           # primes left in the outputs
-    out_bytes = B * 10 * kt * 2 * out_level * n * 8
+    out_bytes = B * n_out * kt * 2 * out_level * n * 8
 
     def barrier():
         if dist:
@@ -445,7 +466,7 @@ def run_ours(args):
                       for ti, t in enumerate(ps.t))
     else:
         dec = L.lola_decrypt(ctx, sk, ct_out, n)
-        want = plain_mnist(imgs[0], mnet)
+        want = plain_dense(imgs[0], Wh) if args.workload == "head" else plain_mnist(imgs[0], mnet)
         got = [int(dec[m, s]) for m, s in net.output_map()]
         correct = got == want
 
@@ -456,7 +477,7 @@ def run_ours(args):
     h_in = [torch.empty(in_bytes // 8, dtype=torch.int64, pin_memory=True) for _ in range(2)]
     h_out = [torch.empty(out_bytes // 8, dtype=torch.int64, pin_memory=True) for _ in range(2)]
     ins = [ct_in, L.lola_ct_create(ctx, B * n_in)]
-    outs = [ct_out, L.lola_ct_create(ctx, B * 10)]
+    outs = [ct_out, L.lola_ct_create(ctx, B * n_out)]
     for hb in h_in:
         L.lola_ct_download(ctx, ct_in, hb.data_ptr(), stream)
     L.lola_eval_network(ctx, ev, net, ins[1], outs[1], stream)
@@ -495,7 +516,7 @@ def run_ours(args):
 
     # ---- plain: one request at a time, eager, no graph
     ct1_in = L.lola_encrypt(ctx, sk, packed[:n_in], 7)
-    ct1_out = L.lola_ct_create(ctx, 10)
+    ct1_out = L.lola_ct_create(ctx, n_out)
     L.lola_eval_network(ctx, ev, net, ct1_in, ct1_out, stream, graph=False)
     torch.cuda.synchronize()
     plain_ms = []
@@ -705,7 +726,7 @@ def run_serve(args):
     import workloads as W
     from paper_1812_10659_gb300 import lola as L, serve
 
-    ps2, ps4 = W.params_mnist(args.L), W.params_head(args.L)
+    ps2, ps4 = W.params_mnist(args.L), W.params_head()
     n = ps2.n
     ctx2 = L.lola_ctx_create(ps2.n, ps2.q, ps2.L, ps2.K, ps2.t)
     ctx4 = L.lola_ctx_create(ps4.n, ps4.q, ps4.L, ps4.K, ps4.t)
@@ -792,7 +813,7 @@ def run_serve(args):
     top = results[-1]
     line = {"mode": "serve", "metric": METRIC, "value": top["batched"]["throughput"], "unit": "inferences/s",
             "n_gpus": 1, "higher_is_better": True, "data": "synthetic", "dtype": "u64",
-            "config": {"workload": "serving mix 70% mnist_lola_n16384 (k_t=3) + 30% transfer head (k_t=1)",
+            "config": {"workload": "serving mix 70% mnist_lola_n16384 (k_t=3, L=5 -> 4 -> 2) + 30% transfer head (k_t=1, L=3)",
                        "duration_s_per_rate": args.duration, "slots": 2, "max_batch": 8},
             "rates": results, "correct": correct}
     print(json.dumps(line), flush=True)

@@ -40,7 +40,7 @@ def test_plain_cifar_matches_oracle_integer_network():
     assert bench.plain_cifar(img, net) == OL.int_dense(x, net.w3)
 
 
-@pytest.mark.parametrize("workload", ["mnist", "lola_dense", "cifar"])
+@pytest.mark.parametrize("workload", ["mnist", "lola_dense", "cifar", "head"])
 def test_op_counts_by_level_match_the_plan(workload):
     """bench.py's per-level operation counts (used to scale the oracle's
     per-operation times) are the plan's, counted on slot vectors with the
@@ -98,12 +98,19 @@ def test_op_counts_by_level_match_the_plan(workload):
         v, pos = lola.pack_image_rows(W.image(), W.DENSE_IMAGE_WIDTH, n)
         msgs = [v]
         layers = W.layers_lola_dense(net, n, levels=W.LOLA_DENSE_LEVELS)
+    elif workload == "head":
+        ev = LevelCount(n, t, 3)
+        Wh = W.head_weights()
+        v = np.zeros(n, np.int64)
+        v[:Wh.shape[1]] = W.feature_vector()
+        msgs, pos = [v], [(0, i) for i in range(Wh.shape[1])]
+        layers = W.layers_head(Wh, n)
     else:
         ev = LevelCount(n, t, 6)
         cnet = W.cifar_net()
         msgs, pos = lola.pack_convolution(W.cifar_padded(W.cifar_image(), cnet.pad), cnet.k1, cnet.k1, cnet.stride, n)
         layers = W.layers_cifar(cnet, n, levels=W.CIFAR_LEVELS)
     lola.run_network(ev, layers, lola.State([np.array(m, np.int64) % t for m in msgs], pos))
-    assert ev.c == bench.OP_COUNTS_LEVELS[workload]
+    assert ev.c == bench.OP_COUNTS_LEVELS.get(workload, {3: bench.OP_COUNTS[workload]})
     for op in ("rot", "square", "mul_plain", "mul_scalar", "add"):
         assert sum(c[op] for c in ev.c.values()) == bench.OP_COUNTS[workload][op]
