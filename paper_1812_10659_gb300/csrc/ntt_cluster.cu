@@ -66,14 +66,19 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(cl_threads<CL_LOGE>(
       ModDownStore{accp, dst, P.q});
 }
 
+// Decompose (Galois permutation of c1 limb i, diagonal limb, inverse
+// transform into digit i) over a cluster.  tau_g maps each half of the limb
+// onto one half: the top bit of an NTT position is bit 1 of its odd
+// exponent, and e g keeps or flips that bit with bit 1 of g (both odd).  So
+// CTA h loads the source half h ^ bit1(g) and scatters into its own shared
+// memory only; the transform's last pass is the one exchange.
 template <int CL_LOGE>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(cl_threads<CL_LOGE>(), 2) kc_ks_decompose(const CtxDev* __restrict__ C, KsDev a) {
   extern __shared__ uint64_t sm[];
   namespace cg = cooperative_groups;
   constexpr int N = 1 << CL_LOGN, LOGE = CL_LOGE, LOGNL = CL_LOGN - CL_LOGC, NC = 1 << LOGNL;
   constexpr int T = N >> (LOGE + CL_LOGC);
-  cg::cluster_group cl = cg::this_cluster();
-  const int h = (int)cl.block_rank();
+  const int h = (int)cg::this_cluster().block_rank();
   const int L = C->L, LK = C->L + C->K;
   const size_t unit = blockIdx.x >> 1;
   const size_t ct = unit / L;
@@ -85,23 +90,23 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(cl_threads<CL_LOGE>(
   uint64_t* diag = a.D + ((ct * L + i) * LK + i) * (size_t)N;
   uint64_t* dig = a.dig + (ct * L + i) * (size_t)N;
   const PrimeDev& P = C->pr[i];
-  // the peers must have started before their shared memory is written
-  cl.sync();
-  // tau_g(c1): diagonal block, then the digit
-#pragma unroll 4
+  const int src_half = h ^ (int)((g >> 1) & 1u);
+  uint64_t v[NC / T];
+#pragma unroll
+  for (int k = 0; k < NC / T; ++k) v[k] = src1[(src_half << LOGNL) + tid + k * T];
+#pragma unroll
   for (int k = 0; k < NC / T; ++k) {
-    const int idx = (h << LOGNL) + tid + k * T;
-    const uint32_t d = gal_dst(idx, ginv, CL_LOGN);
-    cl.map_shared_rank(sm, (int)(d >> LOGNL))[swz<LOGE>(d & (NC - 1))] = src1[idx];
+    const uint32_t d = gal_dst((uint32_t)((src_half << LOGNL) + tid + k * T), ginv, CL_LOGN);   // in half h
+    sm[swz<LOGE>(d & (NC - 1))] = v[k];
   }
-  cl.sync();
+  __syncthreads();
 #pragma unroll 4
   for (int k = 0; k < NC / T; ++k) {
     const int li = tid + k * T;
     diag[(h << LOGNL) + li] = sm[swz<LOGE>(li)];
   }
   ncl::ntt_inverse_cluster_smem<CL_LOGN, LOGE, CL_LOGC>(sm, C->tw_inv + (size_t)i * (2u << CL_LOGN), P.q, P.ninv,
-                                                        P.ninv_s, [&](int k2, uint64_t v) { dig[k2] = v; });
+                                                        P.ninv_s, [&](int k2, uint64_t v2) { dig[k2] = v2; });
 }
 
 namespace k {
