@@ -320,7 +320,7 @@ KERNEL_BYTES = {
     # element-wise kernels: one unit = one output word
     "add": lambda n, L: 24,
     "mul_plain": lambda n, L: 24,
-    "mac_scalar": lambda n, L: 25 * 8 + 8,
+    "mac_scalar": lambda n, L: 25 * 8 / 5 + 8,      # MNIST conv: 25 inputs read once for 5 maps, one output word
     "tensor": lambda n, L: 4 * 8 + 3 * 8,
     "lift_q_to_b": lambda n, L: L * 8,
     "scale_round": lambda n, L: 0,

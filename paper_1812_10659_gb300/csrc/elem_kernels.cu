@@ -240,27 +240,37 @@ __global__ void ke_mul_plain_multi(const CtxDev* __restrict__ C, const uint64_t*
   }
 }
 
-// convolution row-major: out[m][b][t] = sum_r w[m][r][t][j] in[r][b][t]
-// in: [R][B][kt][2][L][n]; w, ws: [maps][R][kt][L] scalars (Shoup)
+// convolution row-major: out[m][b][t] = sum_r w[r][t][j][m] in[r][b][t]
+// in: [R][B][kt][2][L][n]; w, ws: [R][kt][L][maps] scalars (Shoup).  A
+// thread accumulates MB maps for one input word, so every input word is
+// read once per block of MB maps.
+template <int MB>
 __global__ void ke_mac_scalar(const CtxDev* __restrict__ C, const uint64_t* in, uint32_t R, const uint64_t* w,
                               const uint64_t* ws, uint64_t* out, uint32_t maps, uint32_t B) {
   const int L = C->L, logn = C->logn, kt = C->kt;
   const size_t n = C->n;
   const size_t ctw = 2 * (size_t)L * n;
   const size_t per_msg = (size_t)B * kt * ctw;
-  const size_t total = (size_t)maps * per_msg;
+  const size_t total = (size_t)((maps + MB - 1) / MB) * per_msg;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-    const size_t m = i / per_msg;
+    const uint32_t m0 = (uint32_t)(i / per_msg) * MB;
     const size_t off = i % per_msg;
     const int j = (off >> logn) % L;
     const int t = (off / ctw) % kt;
     const uint64_t q = C->pr[j].q;
-    uint64_t acc = 0;
+    uint64_t acc[MB];
+#pragma unroll
+    for (int mm = 0; mm < MB; ++mm) acc[mm] = 0;
     for (uint32_t r = 0; r < R; ++r) {
-      const size_t wi = ((m * R + r) * kt + t) * L + j;
-      acc = add_mod(acc, shoup_mul(in[r * per_msg + off], w[wi], ws[wi], q), q);
+      const uint64_t x = in[r * per_msg + off];
+      const size_t wb = (((size_t)r * kt + t) * L + j) * maps + m0;
+#pragma unroll
+      for (int mm = 0; mm < MB; ++mm)
+        if (m0 + mm < maps) acc[mm] = add_mod(acc[mm], shoup_mul(x, __ldg(w + wb + mm), __ldg(ws + wb + mm), q), q);
     }
-    out[i] = acc;
+#pragma unroll
+    for (int mm = 0; mm < MB; ++mm)
+      if (m0 + mm < maps) out[(m0 + mm) * per_msg + off] = acc[mm];
   }
 }
 
@@ -557,9 +567,16 @@ int mul_plain_multi(Ctx* c, const uint64_t* in, const uint64_t* pt, uint64_t* ou
 
 int mac_scalar(Ctx* c, const uint64_t* in, uint32_t R, const uint64_t* w, const uint64_t* ws, uint64_t* out,
                uint32_t maps, uint32_t B, cudaStream_t s) {
-  const size_t total = (size_t)maps * B * c->kt * c->ct_words();
-  if (!total) return LOLA_OK;
-  ELEM_LAUNCH(KI_MAC_SCALAR, ke_mac_scalar, total, c->dev, in, R, w, ws, out, maps, B);
+  const size_t per_msg = (size_t)B * c->kt * c->ct_words();
+  if (!maps || !per_msg) return LOLA_OK;
+  ProfScope ps_(c, KI_MAC_SCALAR, s, (uint64_t)maps * per_msg);   // units: output words
+  if (maps <= 4) {
+    const size_t items = per_msg * ((maps + 3) / 4);
+    ke_mac_scalar<4><<<grid_for(items, 256), 256, 0, s>>>(c->dev, in, R, w, ws, out, maps, B);
+  } else {
+    const size_t items = per_msg * ((maps + 7) / 8);
+    ke_mac_scalar<8><<<grid_for(items, 256), 256, 0, s>>>(c->dev, in, R, w, ws, out, maps, B);
+  }
   return post(c);
 }
 

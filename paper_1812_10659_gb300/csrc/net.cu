@@ -90,20 +90,22 @@ static int layer_conv(Builder& b, const lola_layer& L, Repr& r) {
   o.R = R;
   o.w_first = b.w.size();
   const uint32_t kt = b.c->kt, Lq = b.level;   // the table holds the current level's primes
-  for (uint32_t m = 0; m < maps; ++m)
-    for (uint32_t j = 0; j < R; ++j)
-      for (uint32_t ti = 0; ti < kt; ++ti) {
-        const int64_t t = (int64_t)b.c->primes[b.c->iT() + ti];
-        int64_t v = L.weights[(size_t)m * R + j] % t;   // centered lift mod t (Sec. 3.1 scalar)
-        if (v < 0) v += t;
-        if (v > (t - 1) / 2) v -= t;
-        for (uint32_t l = 0; l < Lq; ++l) {
-          const uint64_t q = b.c->primes[l];
+  // table order [R][kt][L][maps]: the maps a thread accumulates sit together
+  for (uint32_t j = 0; j < R; ++j)
+    for (uint32_t ti = 0; ti < kt; ++ti) {
+      const int64_t t = (int64_t)b.c->primes[b.c->iT() + ti];
+      for (uint32_t l = 0; l < Lq; ++l) {
+        const uint64_t q = b.c->primes[l];
+        for (uint32_t m = 0; m < maps; ++m) {
+          int64_t v = L.weights[(size_t)m * R + j] % t;   // centered lift mod t (Sec. 3.1 scalar)
+          if (v < 0) v += t;
+          if (v > (t - 1) / 2) v -= t;
           const uint64_t x = v >= 0 ? (uint64_t)v % q : (q - ((uint64_t)(-v) % q)) % q;
           b.w.push_back(x);
           b.ws.push_back(shoup_h(x, q));
         }
       }
+    }
   b.net->ops.push_back(o);
   const uint32_t width = (uint32_t)r.pos.size();
   Repr out;

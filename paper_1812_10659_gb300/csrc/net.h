@@ -27,7 +27,7 @@ struct Op {
   // of the op's level); src_stride 0 = broadcast
   size_t pt_first = 0;
   uint32_t src_stride = 1;
-  // OP_MAC: R inputs per output, weight table offset (entries [msgs][R][kt][L])
+  // OP_MAC: R inputs per output, weight table offset (entries [R][kt][L][msgs])
   uint32_t R = 0;
   size_t w_first = 0;
   // OP_SUM: dst = sum of `msgs` messages of src (+ message aux_off of aux if aux >= 0)
