@@ -142,6 +142,18 @@ __global__ void __launch_bounds__(256, 4) ke_ks_ip(const CtxDev* __restrict__ C,
 
 // ------------------------------------------------------------- element-wise
 // words of a batch of ciphertexts; limb = (w / n) % L
+// out = (aux ? aux : 0) + sum of `msgs` blocks of `total` words at src, src + total, ...
+__global__ void ke_sum_msgs(const CtxDev* __restrict__ C, const uint64_t* src, uint32_t msgs, const uint64_t* aux,
+                            uint64_t* out, size_t total) {
+  const int L = C->L, logn = C->logn;
+  for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < total; w += (size_t)gridDim.x * blockDim.x) {
+    const uint64_t q = C->pr[(w >> logn) % L].q;
+    uint64_t acc = aux ? aux[w] : 0;
+    for (uint32_t m = 0; m < msgs; ++m) acc = add_mod(acc, src[(size_t)m * total + w], q);
+    out[w] = acc;
+  }
+}
+
 __global__ void ke_add(const CtxDev* __restrict__ C, const uint64_t* a, const uint64_t* b, uint64_t* out,
                        size_t total, int sub) {
   const int L = C->L, logn = C->logn;
@@ -218,9 +230,10 @@ __global__ void ke_gal_permute(const CtxDev* __restrict__ C, const uint64_t* in,
 }
 
 // ct x plaintext for R plaintexts at once: out[r][b][t] = in[b][t] (.) pt[r][t]
-// in: [B][kt][2][L][n]; pt: [R][kt][L][n] Montgomery; out: [R][B][kt][2][L][n]
+// in: [B][kt][2][L][n] (per_msg_in: [R][B][kt][2][L][n], message r times
+// plaintext r); pt: [R][kt][L][n] Montgomery; out: [R][B][kt][2][L][n]
 __global__ void ke_mul_plain_multi(const CtxDev* __restrict__ C, const uint64_t* in, const uint64_t* pt,
-                                   uint64_t* out, uint32_t R, uint32_t B) {
+                                   uint64_t* out, uint32_t R, uint32_t B, int per_msg_in) {
   const int L = C->L, logn = C->logn, kt = C->kt;
   const size_t n = C->n;
   const size_t ctw = 2 * (size_t)L * n;
@@ -231,7 +244,7 @@ __global__ void ke_mul_plain_multi(const CtxDev* __restrict__ C, const uint64_t*
     const size_t ctg = w / ctw;             // r * B * kt + b * kt + t
     const int t = ctg % kt;
     const size_t r = ctg / ((size_t)B * kt);
-    const size_t in_ct = ctg % ((size_t)B * kt);
+    const size_t in_ct = per_msg_in ? ctg : ctg % ((size_t)B * kt);
     const size_t comp = (w / ((size_t)L * n)) & 1;
     const PrimeDev& P = C->pr[j];
     const uint64_t x = in[in_ct * ctw + (comp * L + j) * n + k];
@@ -558,10 +571,18 @@ int gal_permute(Ctx* c, const uint64_t* in, uint64_t* out, size_t n_limbpolys, u
 }
 
 int mul_plain_multi(Ctx* c, const uint64_t* in, const uint64_t* pt, uint64_t* out, uint32_t R, uint32_t B,
-                    cudaStream_t s) {
+                    cudaStream_t s, bool per_msg_in) {
   const size_t total = (size_t)R * B * c->kt * c->ct_words();
   if (!total) return LOLA_OK;
-  ELEM_LAUNCH(KI_MUL_PLAIN, ke_mul_plain_multi, total, c->dev, in, pt, out, R, B);
+  ELEM_LAUNCH(KI_MUL_PLAIN, ke_mul_plain_multi, total, c->dev, in, pt, out, R, B, (int)per_msg_in);
+  return post(c);
+}
+
+int sum_msgs(Ctx* c, const uint64_t* src, uint32_t msgs, const uint64_t* aux, uint64_t* out, size_t per,
+             cudaStream_t s) {
+  const size_t total = per * c->ct_words();
+  if (!total) return LOLA_OK;
+  ELEM_LAUNCH(KI_ADD, ke_sum_msgs, total, c->dev, src, msgs, aux, out, total);
   return post(c);
 }
 

@@ -106,8 +106,12 @@ int neg_axpe(Ctx* c, const uint64_t* a, const uint64_t* s_mont, const uint64_t* 
 int keygen_switch(Ctx* c, const uint64_t* a, const uint64_t* e, const uint64_t* s_mont, const uint64_t* sfrom,
                   uint64_t* out, cudaStream_t s);
 int gal_permute(Ctx* c, const uint64_t* in, uint64_t* out, size_t n_limbpolys, uint32_t g, cudaStream_t s);
+// per_msg_in: message r of `in` times plaintext r (else one input for all r)
 int mul_plain_multi(Ctx* c, const uint64_t* in, const uint64_t* pt, uint64_t* out, uint32_t R, uint32_t B,
-                    cudaStream_t s);
+                    cudaStream_t s, bool per_msg_in = false);
+// out = (aux or 0) + sum of `msgs` messages of `per` ciphertexts each at src
+int sum_msgs(Ctx* c, const uint64_t* src, uint32_t msgs, const uint64_t* aux, uint64_t* out, size_t per,
+             cudaStream_t s);
 int mac_scalar(Ctx* c, const uint64_t* in, uint32_t R, const uint64_t* w, const uint64_t* ws, uint64_t* out,
                uint32_t maps, uint32_t B, cudaStream_t s);
 int lift_q_to_b(Ctx* c, const uint64_t* xq, uint64_t* xb, size_t n_polys, cudaStream_t s);

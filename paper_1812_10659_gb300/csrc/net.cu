@@ -836,24 +836,18 @@ static int run_ops(Ctx* root, Net* net, Executor* ex, const KeySet* ks, cudaStre
       case OP_SUM: {
         uint64_t* d = reg(o.dst, o.dst_off);
         const size_t per = (size_t)B * kt;
-        if (o.aux >= 0) {
-          TRY(k::add(c, reg(o.aux, o.aux_off), reg(o.src, o.src_off), d, per, s));
-        } else {
+        if (o.aux < 0 && o.msgs == 1) {
           LOLA_CUDA_TRY(cudaMemcpyAsync(d, reg(o.src, o.src_off), msg_words * 8, cudaMemcpyDeviceToDevice, s));
+        } else {
+          // one launch for the whole sum (the messages of a register are contiguous)
+          TRY(k::sum_msgs(c, reg(o.src, o.src_off), o.msgs, o.aux >= 0 ? reg(o.aux, o.aux_off) : nullptr, d, per, s));
         }
-        for (uint32_t m = (o.aux >= 0 ? 1 : 1); m < o.msgs; ++m)
-          TRY(k::add(c, d, reg(o.src, o.src_off + m), d, per, s));
         break;
       }
       case OP_MULPT: {
         const uint64_t* pt = net->pt.at(o.level).u64() + o.pt_first * kt * c->L * c->n;
-        if (o.src_stride == 0) {
-          TRY(k::mul_plain_multi(c, reg(o.src, o.src_off), pt, reg(o.dst, o.dst_off), o.msgs, B, s));
-        } else {
-          for (uint32_t m = 0; m < o.msgs; ++m)
-            TRY(k::mul_plain_multi(c, reg(o.src, o.src_off + m), pt + (size_t)m * kt * c->L * c->n,
-                                   reg(o.dst, o.dst_off + m), 1, B, s));
-        }
+        // src_stride 0: one input message times every plaintext; 1: message m times plaintext m
+        TRY(k::mul_plain_multi(c, reg(o.src, o.src_off), pt, reg(o.dst, o.dst_off), o.msgs, B, s, o.src_stride != 0));
         break;
       }
       case OP_SQUARE:
