@@ -82,3 +82,23 @@ def test_tune_table_checks():
             Lb.lola_tune_get(ctx)
     finally:
         Lb.lola_ctx_destroy(ctx)
+
+
+def test_autotune_cache_file(tmp_path):
+    """autotune_cached runs the tuner once per key and then installs the
+    stored table from the JSON file."""
+    need_gpu()
+    Lb = lib()
+    ps = W.params_small(16384, L=2, K=1)
+    ctx = make_ctx(ps)
+    try:
+        path = str(tmp_path / "tune.json")
+        key = {"n": ps.n, "L": ps.L, "device": "test"}
+        first = Lb.autotune_cached(ctx, path, key)
+        assert first["cached"] is False
+        Lb.lola_tune_set(ctx, None)
+        second = Lb.autotune_cached(ctx, path, key)
+        assert second["cached"] is True and second["table"] == first["table"]
+        assert Lb.lola_tune_get(ctx)["table"] == first["table"]
+    finally:
+        Lb.lola_ctx_destroy(ctx)
