@@ -443,3 +443,33 @@ def test_cifar_second_convolution_matrix_is_the_convolution():
             for j in range(o2):
                 direct.append(int((K * h1[:, s * i:s * i + k2, s * j:s * j + k2]).sum()))
     assert [int(v) for v in D @ h1.reshape(-1)] == direct
+
+
+@pytest.mark.slow
+def test_full_mnist_with_modulus_switching_keeps_its_noise_margin():
+    """The MNIST-shaped network at full size (n = 16384, L = 5) with the
+    modulus switches of workloads.MNIST_LEVELS (4 primes after the first
+    square, 2 after the second), encrypted in the oracle for one CRT
+    residue: the output decrypts to the integer network mod t with more than
+    20 bits of noise margin (about a minute on one core)."""
+    n = 16384
+    ps = W.params_mnist()
+    P = bfv.Params(ps.n, ps.q, ps.L, ps.K, ps.t)
+    t = ps.t[0]
+    net, img = W.mnist_net(), W.image()
+    layers = W.layers_mnist(net, n, W.MNIST_LEVELS)
+    steps = sorted({169, 338, 507, 676} | {1 << j for j in range(13)} | set(range(1, 7)))
+    keys = bfv.keygen(P, W.DEFAULT_SEED, rotations=steps, relin=True, row_swap=True)
+    msgs, pos = lola.pack_convolution(img, net.kh, net.kw, net.stride, n)
+    cts = [bfv.encrypt(P, keys.pk, encoding.encode(m, t), t, 5, i) for i, m in enumerate(msgs)]
+    ev = lola.HEEval(P, keys, t)
+    st = lola.run_network(ev, layers, lola.State(cts, pos))
+    assert ev.p.L == W.MNIST_LEVELS[1] and all(len(c.c[0]) == ev.p.L for c in st.msgs)
+    want = [v % t for v in mnist_int(net, img)]
+    got = [int(encoding.decode(bfv.decrypt(ev.p, keys.sk, st.msgs[m]), t)[s]) for m, s in st.pos]
+    assert got == want
+    for m in range(2):
+        vals = np.zeros(n, dtype=np.int64)
+        vals[:] = want[m]                       # sparse output: the value in every slot
+        margin = bfv.noise_margin_bits(ev.p, keys.sk, st.msgs[m], encoding.encode(vals, t))
+        assert margin > 20, margin
