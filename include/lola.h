@@ -24,7 +24,9 @@
  *    (prime q_j) of each of its two polynomials is n contiguous words.  A
  *    batch of ciphertexts is those blocks back to back.  Between operations
  *    ciphertexts are kept in NTT (evaluation) form; import/export calls
- *    convert from/to coefficient form.
+ *    convert from/to coefficient form.  After modulus switching a
+ *    ciphertext keeps the first L' primes: [2][L'][n] (lola_mod_switch,
+ *    lola_ct_level).
  *  - A "message" is one plaintext slot vector; the library encrypts each
  *    message once per plaintext modulus t_i (CRT pipelines, Sec. 4.4), so a
  *    lola_ct holding m messages holds m * k_t ciphertexts ordered
