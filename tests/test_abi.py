@@ -73,3 +73,26 @@ def test_bad_parameters_rejected_before_device_use():
     from paper_1812_10659_gb300 import lola as L
     with pytest.raises(L.LolaError):
         L.lola_pack_convolution([[1, 2], [3, 4]], 3, 3, 1, 16)
+
+
+def test_autotune_cache_helper_runs_the_tuner_once_per_key(tmp_path, monkeypatch):
+    """Host logic of lola.autotune_cached (the device calls replaced by
+    recorders): the first call for a key tunes and stores the table, the
+    next installs the stored one, another key tunes again."""
+    from paper_1812_10659_gb300 import lola as L
+    calls = {"tune": 0, "set": []}
+    table = [[1, 0, 0, 0, 0, 0], [1, 1, 1, 2, 2, 2], [1, 1, 1, 2, 2, 2], [1, 1, 1, 2, 2, 2]]
+
+    def fake_autotune(ctx, stream=None):
+        calls["tune"] += 1
+        return {"table": table, "us": []}
+
+    monkeypatch.setattr(L, "lola_autotune", fake_autotune)
+    monkeypatch.setattr(L, "lola_tune_set", lambda ctx, t=None: calls["set"].append(t))
+    path = str(tmp_path / "tune.json")
+    a = L.autotune_cached(None, path, {"n": 16384, "L": 5})
+    b = L.autotune_cached(None, path, {"n": 16384, "L": 5})
+    c = L.autotune_cached(None, path, {"n": 16384, "L": 6})
+    assert (a["cached"], b["cached"], c["cached"]) == (False, True, False)
+    assert calls["tune"] == 2 and calls["set"] == [table]
+    assert b["table"] == table
