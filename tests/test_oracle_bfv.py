@@ -7,6 +7,7 @@ polynomial, and a brute-force tensor product over Z with exact rational
 rounding on tiny rings.
 """
 from fractions import Fraction
+import math
 
 import numpy as np
 import pytest
@@ -345,3 +346,111 @@ def test_level_keys_are_restrictions_of_the_full_keys(small):
     for i in range(2):
         for jl, jf in enumerate([0, 1, P.L]):
             assert np.array_equal(kr.b[i, jl], kf.b[i, jf]) and np.array_equal(kr.a[i, jl], kf.a[i, jf])
+
+
+# ------------------------------------------- exact pins of the noise margin
+#
+# For a ciphertext whose phase is [c0 + c1 s]_Q = [Delta m + e]_Q with a
+# known error e, the BFV decryption error is t x - Q m = t e - r m (mod tQ),
+# r = Q mod t = Q - t Delta, and decryption is right exactly while
+# |t e - r m| < Q / 2.  The tests below build such ciphertexts with their
+# own schoolbook negacyclic products over Z (no oracle ring code) and check
+# noise_margin_bits against log2(Q / 2) - log2(max |t e - r m|).
+
+def schoolbook_negacyclic(a, b):
+    n = len(a)
+    out = [0] * n
+    for i, ai in enumerate(a):
+        if not ai:
+            continue
+        for j, bj in enumerate(b):
+            k = i + j
+            if k < n:
+                out[k] += ai * bj
+            else:
+                out[k - n] -= ai * bj
+    return out
+
+
+def with_error(P, s, m, e, t, rng):
+    """(c0, c1) over Q with c1 uniform and c0 = -c1 s + Delta m + e."""
+    Q = P.Q
+    a = [int(x) for x in rng.integers(0, 2**62, P.n)]
+    a = [x % Q for x in a]
+    D = Q // t
+    as_ = schoolbook_negacyclic(a, [int(x) for x in s])
+    c0 = [(-v + D * int(mi) + int(ei)) % Q for v, mi, ei in zip(as_, m, e)]
+    res = lambda xs: np.array([[x % q for x in xs] for q in P.q[:P.L]], dtype=np.uint64)
+    return bfv.Ciphertext([res(c0), res(a)], t)
+
+
+def closed_form_margin(P, t, m, e):
+    r = P.Q % t
+    worst = max(abs(t * int(ei) - r * int(mi)) for mi, ei in zip(m, e))
+    return math.log2(P.Q) - 1 - math.log2(worst)
+
+
+@pytest.mark.parametrize("t", [65537, W.T30[0]])
+@pytest.mark.parametrize("ebits", [3, 40, 90])
+def test_noise_margin_equals_closed_form_bfv_error(small, t, ebits):
+    P0, keys = small
+    P = bfv.Params(P0.n, P0.q, P0.L, P0.K, [t])
+    rng = np.random.default_rng(ebits + t % 97)
+    m = rng.integers(0, t, P.n)
+    e = [(int(x) << max(0, ebits - 40)) + int(y) for x, y in
+         zip(rng.integers(-2**min(ebits, 40), 2**min(ebits, 40), P.n), rng.integers(-8, 8, P.n))]
+    ct = with_error(P, keys.sk.s, m, e, t, rng)
+    got = bfv.noise_margin_bits(P, keys.sk, ct, m)
+    assert got == pytest.approx(closed_form_margin(P, t, m, e), abs=1e-9)
+    assert np.array_equal(bfv.decrypt(P, keys.sk, ct), m)
+
+
+def test_noise_margin_sign_is_decryption_correctness(small):
+    # one coefficient's error at the decryption boundary |t e - r m| = Q / 2:
+    # decryption of that coefficient flips exactly there (exact integers),
+    # and the margin (a float of ~2^-20 relative resolution here) is
+    # positive a hair inside and negative a hair outside
+    P, keys = small
+    t = P.t[0]
+    Q, r = P.Q, P.Q % t
+    rng = np.random.default_rng(21)
+    m = rng.integers(0, t, P.n)
+    e = [int(x) for x in rng.integers(-8, 8, P.n)]
+    for m5 in (0, t - 1):
+        m[5] = m5
+        hi = (Q // 2 + r * m5) // t            # largest e with t e - r m < Q / 2
+        lo = -((Q // 2 - r * m5) // t)         # smallest e with t e - r m > -Q / 2
+        eps = hi >> 20
+        for e5, ok in ((hi, True), (hi + 1, False), (lo, True), (lo - 1, False),
+                       (hi - eps, True), (hi + eps, False), (lo + eps, True), (lo - eps, False)):
+            e[5] = e5
+            ct = with_error(P, keys.sk.s, m, e, t, rng)
+            got = bfv.decrypt(P, keys.sk, ct)
+            assert bool(got[5] == m[5]) == ok, (m5, e5)
+            assert np.array_equal(np.delete(got, 5), np.delete(m, 5))
+            margin = bfv.noise_margin_bits(P, keys.sk, ct, m)
+            assert margin == pytest.approx(closed_form_margin(P, t, m, e), abs=1e-9)
+            if abs(abs(e5) - abs(hi if e5 > 0 else lo)) > 1:
+                assert (margin > 0) == ok, (m5, e5, margin)
+
+
+def test_fresh_encryption_margin_is_the_public_key_error_term():
+    # c = (Delta m + p0 u + e1, p1 u + e2) with p0 = -(a s + e), p1 = a has the
+    # phase Delta m + e1 + e2 s - e u: recompute that error from the sampled
+    # streams with schoolbook products and compare the margins exactly
+    from oracle import sampling
+    P = mkparams(32)
+    keys = bfv.keygen(P, 3)
+    t = P.t[0]
+    v = np.random.default_rng(22).integers(0, 16, P.n)
+    m = encoding.encode(v, t)
+    ct = bfv.encrypt(P, keys.pk, m, t, 9, 4)
+    u = sampling.sample_ternary(9, sampling.TAG_ENC_U, 4, 0, P.n)
+    e1 = sampling.sample_gaussian(9, sampling.TAG_ENC_E1, 4, 0, P.n)
+    e2 = sampling.sample_gaussian(9, sampling.TAG_ENC_E2, 4, 0, P.n)
+    epk = sampling.sample_gaussian(3, sampling.TAG_PK_E, 0, 0, P.n)
+    s = [int(x) for x in keys.sk.s]
+    e2s = schoolbook_negacyclic([int(x) for x in e2], s)
+    eu = schoolbook_negacyclic([int(x) for x in epk], [int(x) for x in u])
+    err = [int(a) + b - c for a, b, c in zip(e1, e2s, eu)]
+    assert bfv.noise_margin_bits(P, keys.sk, ct, m) == pytest.approx(closed_form_margin(P, t, m, err), abs=1e-9)
