@@ -110,8 +110,10 @@ struct AsyncBuf {
 
 // --------------------------------------------------------------- key switching
 // scratch: digits [count][L][n], mod-up limbs D [count][L][L+K][n], x_P
-// [count][2][n], tau_g(c0) [count][L][n]; the inner products live in place
-// over D's digit rows 0 and 1 (a separate [count][2][L+K][n] area when L = 1).
+// [count][2][n]; the inner products live in place over D's digit rows 0 and
+// 1 (a separate [count][2][L+K][n] area when L = 1).  tau_g(c0) has no area:
+// rotate() always has the inner product gather it from the input (c0_gather),
+// and lola_rotate_noalloc's size check relies on this count.
 size_t rotate_scratch_words(const Ctx* c, size_t count) {
   const size_t LK = c->L + c->K;
   size_t w = count * (c->L + c->L * LK + 2) * (size_t)c->n;   // digits, D, x_P

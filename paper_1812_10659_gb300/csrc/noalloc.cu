@@ -1,9 +1,10 @@
 // Rotation without any device allocation.
 //
-// Some callers cannot allocate device memory: code running inside a CUDA
-// stream capture that must not create allocation nodes, applications whose
-// memory manager forbids cudaMalloc / cudaMallocAsync after start-up, or
-// hosts that budget every byte of device memory up front.  For them
+// Some callers cannot allocate device memory: applications whose memory
+// manager owns the whole device and forbids cudaMalloc / cudaMallocAsync
+// after start-up, hosts that budget every byte of device memory up front,
+// and latency-critical loops where an allocation's cost or its possible
+// implicit synchronisation is not acceptable.  For them
 // lola_rotate_noalloc rotates ciphertexts using a scratch area that is part
 // of the library image itself: a file-scope __device__ array that every GPU
 // loading the library holds until the process exits.
@@ -14,6 +15,8 @@
 // has to be cleared between calls.  Calls whose work overlaps on the GPU
 // (different streams, or different threads without ordering) race on the
 // array; callers must serialise them.
+#include <mutex>
+
 #include "he.h"
 
 namespace lola {
@@ -22,22 +25,31 @@ namespace lola {
 constexpr size_t kNoAllocWords = (size_t)LOLA_ROTATE_NOALLOC_SCRATCH_BYTES / 8;
 static __device__ __align__(256) uint64_t g_noalloc_scratch[kNoAllocWords];
 
-constexpr int kMaxDevices = 64;
-static uint64_t* g_noalloc_ptr[kMaxDevices];   // device address per device, set on first use
+static std::mutex g_noalloc_lookup;
 
 // Host code must not pass g_noalloc_scratch itself to a kernel: in host code
 // that name is only a stand-in for the symbol.  The device address comes from
-// cudaGetSymbolAddress with the device current.
-static int noalloc_scratch(int device, uint64_t** out) {
-  if (device < 0 || device >= kMaxDevices) return fail(LOLA_E_PARAM, "device index out of range");
-  if (!g_noalloc_ptr[device]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p)
-      return fail(LOLA_E_CUDA, std::string("cudaGetSymbolAddress(no-alloc scratch): ") + cudaGetErrorString(e));
-    g_noalloc_ptr[device] = (uint64_t*)p;
+// cudaGetSymbolAddress with the context's device current (the caller makes
+// it current).  It is looked up once per context and kept in the context, so
+// a context created after the device was reset (cudaDeviceReset, a new
+// primary context) looks it up again instead of reusing a stale address.
+// The lock serialises first calls from several threads.
+static int noalloc_scratch(Ctx* c, uint64_t** out) {
+  Ctx* r = c->root;
+  uint64_t* p = r->noalloc_scratch.load(std::memory_order_acquire);
+  if (!p) {
+    std::lock_guard<std::mutex> lk(g_noalloc_lookup);
+    p = r->noalloc_scratch.load(std::memory_order_relaxed);
+    if (!p) {
+      void* a = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&a, g_noalloc_scratch);
+      if (e != cudaSuccess || !a)
+        return fail(LOLA_E_CUDA, std::string("cudaGetSymbolAddress(no-alloc scratch): ") + cudaGetErrorString(e));
+      p = (uint64_t*)a;
+      r->noalloc_scratch.store(p, std::memory_order_release);
+    }
   }
-  *out = g_noalloc_ptr[device];
+  *out = p;
   return LOLA_OK;
 }
 
@@ -75,7 +87,7 @@ extern "C" int lola_rotate_noalloc(lola_ctx* ctx, const lola_keys* keys, const u
     if (e != cudaSuccess) return fail(LOLA_E_CUDA, cudaGetErrorString(e));
   }
   uint64_t* scratch = nullptr;
-  int rc = noalloc_scratch(c->device, &scratch);
+  int rc = noalloc_scratch(c, &scratch);
   if (rc == LOLA_OK) {
     RotSpec rs;
     rs.gal = g;

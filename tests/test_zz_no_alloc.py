@@ -1,12 +1,13 @@
 """The allocation-free rotation entry point (lola_rotate_noalloc).
 
-It exists for callers that cannot allocate device memory (inside a stream
-capture that must stay free of allocation nodes, or under an application
-memory manager that forbids cudaMalloc).  This test calls it through the
+It exists for callers that cannot allocate device memory (an application
+memory manager that owns the device and forbids cudaMalloc after start-up,
+a host that budgets device memory up front, a latency-critical loop that
+cannot afford an allocation).  This test calls it through the
 C-ABI twice in a row and checks each result against the ordinary
 lola_rotate entry point (which allocates its scratch): rotations are exact
 integer arithmetic, so the tolerance is zero.  It also checks the size
-limit of the static scratch area.  The file name makes pytest collect it
+limit of the static scratch area at its exact boundary.  The file name makes pytest collect it
 last.
 """
 import numpy as np
@@ -44,14 +45,17 @@ def test_rotate_noalloc_matches_rotate_twice():
                     want = np.concatenate([np.roll(slots[m, :h], step), np.roll(slots[m, h:], step)])
                     for ti in range(kt):
                         assert np.array_equal(res[m, ti], want % ps.t[ti])
-            # a request larger than the static scratch area is refused, not truncated
+            # the largest count that fits is the one rotated above; one
+            # ciphertext more is refused, not truncated
             per_ct = (ps.L + ps.L * (ps.L + ps.K) + 2) * n * 8
-            too_many = Lb.NOALLOC_SCRATCH_BYTES // per_ct + 1
-            big_in = Lb.lola_ct_create(ctx, too_many)
-            big_out = Lb.lola_ct_create(ctx, too_many)
+            max_ok = Lb.NOALLOC_SCRATCH_BYTES // per_ct
+            assert max_ok == count
+            msgs = (max_ok + 1 + kt - 1) // kt
+            big_in = Lb.lola_ct_create(ctx, msgs)
+            big_out = Lb.lola_ct_create(ctx, msgs)
             try:
                 with pytest.raises(Lb.LolaError) as ei:
-                    Lb.lola_rotate_noalloc(ctx, ev, Lb.lola_ct_data(big_in), Lb.lola_ct_data(big_out), too_many * kt, 1)
+                    Lb.lola_rotate_noalloc(ctx, ev, Lb.lola_ct_data(big_in), Lb.lola_ct_data(big_out), max_ok + 1, 1)
                 assert ei.value.code == -1
             finally:
                 Lb.lola_ct_destroy(big_in)
