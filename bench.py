@@ -214,15 +214,121 @@ def oracle_sample(n_rot=1, n_sq=1, workload="mnist", L=5, levels=None):
     return sec, desc
 
 
+def _slot_rotation_steps(layers, n, t, st):
+    """Rotation steps a layer list uses (0 = row swap), from a slot-level run."""
+    from oracle import lola as OL
+    seen = set()
+
+    class Rec(OL.SlotEval):
+        def rot(self, a, k):
+            seen.add(k)
+            return super().rot(a, k)
+
+        def rot_rows(self, a):
+            seen.add(0)
+            return super().rot_rows(a)
+
+        def rot_hoisted(self, a, steps):
+            seen.update(steps)
+            return super().rot_hoisted(a, steps)
+
+    OL.run_network(Rec(n, t), layers, st)
+    return sorted(seen)
+
+
+def oracle_residue_inference(workload, L, levels, ti):
+    """One CRT residue of one end-to-end oracle inference (run in a spawned
+    worker): key generation, encryption of one synthetic request, the whole
+    layer list on ciphertexts, decryption, and a check against the integer
+    network.  Returns the seconds of each phase."""
+    import numpy as np
+
+    import workloads as W
+    from oracle import bfv, encoding, lola as OL
+    ps = workload_params(workload, L)
+    P = bfv.Params(ps.n, ps.q, ps.L, ps.K, ps.t)
+    n, t, kt = ps.n, ps.t[ti], len(ps.t)
+    if workload == "mnist":
+        mnet, img = W.mnist_net(), W.image()
+        layers = W.layers_mnist(mnet, n, levels)
+        msgs, pos = OL.pack_convolution(img, mnet.kh, mnet.kw, mnet.stride, n)
+        want = plain_mnist(img, mnet)
+    else:
+        Wh = W.head_weights()
+        layers = W.layers_head(Wh, n)
+        v = np.zeros(n, np.int64)
+        x = W.feature_vector()
+        v[:len(x)] = x
+        msgs, pos = [v], [(0, i) for i in range(len(x))]
+        want = plain_dense(x, Wh)
+    steps = _slot_rotation_steps(layers, n, t, OL.State([np.asarray(m, np.int64) % t for m in msgs], pos))
+    t0 = time.perf_counter()
+    keys = bfv.keygen(P, W.DEFAULT_SEED, rotations=[s for s in steps if s], relin=True, row_swap=0 in steps)
+    t1 = time.perf_counter()
+    cts = [bfv.encrypt(P, keys.pk, encoding.encode(m, t), t, 5, i * kt + ti) for i, m in enumerate(msgs)]
+    t2 = time.perf_counter()
+    ev = OL.HEEval(P, keys, t)
+    st = OL.run_network(ev, layers, OL.State(cts, pos))
+    t3 = time.perf_counter()
+    got = {}
+    for m, s in st.pos:
+        if m not in got:
+            got[m] = encoding.decode(bfv.decrypt(ev.p, keys.sk, st.msgs[m]), t)
+    out = [int(got[m][s]) for m, s in st.pos]
+    t4 = time.perf_counter()
+    return {"keygen_s": t1 - t0, "encrypt_s": t2 - t1, "eval_s": t3 - t2, "decrypt_s": t4 - t3,
+            "ok": out == [w % t for w in want], "ops": dict(ev.counts)}
+
+
+def oracle_e2e_inference(workload="mnist", L=5, levels=None) -> dict:
+    """One whole inference on the CPU oracle, its CRT residues in parallel
+    spawned processes (one core each).  Seconds per phase are the slowest
+    residue's; `eval_s` (the layer list on ciphertexts) is the figure the
+    GPU's evaluation rate compares with."""
+    import multiprocessing
+    from concurrent.futures import ProcessPoolExecutor
+    kt = len(workload_params(workload, L).t)
+    t0 = time.perf_counter()
+    with ProcessPoolExecutor(max_workers=kt, mp_context=multiprocessing.get_context("spawn")) as ex:
+        res = list(ex.map(oracle_residue_inference, [workload] * kt, [L] * kt, [levels] * kt, range(kt)))
+    wall = time.perf_counter() - t0
+    agg = {k: max(r[k] for r in res) for k in ("keygen_s", "encrypt_s", "eval_s", "decrypt_s")}
+    agg.update({"ok": all(r["ok"] for r in res), "residues": kt, "wall_s": wall, "ops_per_residue": res[0]["ops"]})
+    return agg
+
+
+E2E_WORKLOADS = ("mnist", "head")
+
+
 def cpu_baseline_obj(workload="mnist", L=5, levels=None):
+    """The oracle timed on this host: for the MNIST-shaped network and the
+    head, one whole inference end to end (residues in parallel processes);
+    for the larger networks, per-operation samples scaled by the plan's
+    operation counts."""
+    if workload in E2E_WORKLOADS:
+        r = oracle_e2e_inference(workload, L, levels)
+        return {"value": 1.0 / r["eval_s"], "unit": "inferences/s", "cores": r["residues"],
+                "kind": "oracle end-to-end",
+                "sample": (f"one whole inference of one synthetic request: the layer list on ciphertexts for all "
+                           f"{r['residues']} CRT residues, one spawned process (core) per residue, value = 1 / the "
+                           f"slowest residue's evaluation time; decrypted outputs equal the integer network: {r['ok']}"),
+                "eval_s": r["eval_s"], "keygen_s": r["keygen_s"], "encrypt_s": r["encrypt_s"],
+                "decrypt_s": r["decrypt_s"], "ops_per_residue": r["ops_per_residue"],
+                "sample_wall_s": round(r["wall_s"], 1)}
     t0 = time.perf_counter()
     sec, desc = oracle_sample(workload=workload, L=L, levels=levels)
-    return {"value": 1.0 / sec, "unit": "inferences/s", "cores": 1, "kind": "oracle",
+    return {"value": 1.0 / sec, "unit": "inferences/s", "cores": 1, "kind": "oracle (per-op samples x op counts)",
             "sample": desc, "sample_wall_s": round(time.perf_counter() - t0, 1)}
 
 
 # ---------------------------------------------------------------- reference
 def run_reference(args):
+    """The reference arm: the CPU oracle.  Each step times one sample of
+    every operation kind at each level on one core and scales it by the
+    plan's per-level operation counts (a whole inference takes minutes, so a
+    step is a bounded sample of it); for the MNIST-shaped network and the
+    head one whole inference is also run end to end after the timed steps
+    (residues in parallel processes) and reported beside the samples."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -236,6 +342,11 @@ def run_reference(args):
     wall = time.perf_counter() - t0
     sec = statistics.median(secs)
     value = 1.0 / sec
+    e2e_run = None
+    if args.workload in E2E_WORKLOADS and not args.no_cpu_baseline:
+        r = oracle_e2e_inference(args.workload, args.L, args.levels)
+        e2e_run = {"value": 1.0 / r["eval_s"], "unit": "inferences/s", "cores": r["residues"],
+                   "eval_s": r["eval_s"], "correct": r["ok"], "wall_s": round(r["wall_s"], 1)}
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "inferences/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1000,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
@@ -243,7 +354,9 @@ def run_reference(args):
                        "k_t": len(workload_params(args.workload, args.L).t),
                        "levels": [args.L] + list(args.levels or []),
                        "parallelism": "none (CPU oracle)"},
-            "cpu_baseline": {"value": value, "unit": "inferences/s", "cores": 1, "kind": "oracle", "sample": desc},
+            "cpu_baseline": {"value": value, "unit": "inferences/s", "cores": 1,
+                             "kind": "oracle (per-op samples x op counts)", "sample": desc},
+            "oracle_end_to_end": e2e_run,
             "e2e": {"value": value, "unit": "inferences/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -328,7 +441,15 @@ KERNEL_BYTES = {
 
 
 TRANSFORM_KERNELS = {"ks_modup", "ks_decompose", "ks_moddown", "ks_intt_p", "ntt_fwd", "ntt_inv"}
+INVERSE_KERNELS = {"ks_decompose", "ks_intt_p", "ntt_inv"}
 OPS_PER_BUTTERFLY = 22
+
+
+def measured_alu_peaks(L, ctx) -> dict:
+    """Integer-unit rates measured on this GPU by the library's
+    microbenchmarks (operations per second; butterflies for the butterfly
+    kinds, int8 operations for mma_s8)."""
+    return {k: L.lola_alu_rate(ctx, k)[0] for k in L.ALU_KINDS}
 
 
 def committed_traffic(kernel: str, units_per_launch: float):
@@ -567,19 +688,26 @@ def run_ours(args):
     roofline = {"kernel": dom, "avg_launch_ms": d["ms"] / d["launches"], "share_of_kernel_time": d["ms"] / kernel_ms_total,
                 "hbm": {"achieved": hbm_achieved, "peak": hbm_peak, "peak_source": peak_src, "unit": "GB/s",
                         "frac": (hbm_achieved / hbm_peak) if hbm_achieved else None}}
+    alu = measured_alu_peaks(L, ctx)
     if dom in TRANSFORM_KERNELS:
         # integer-ALU bound: algorithmic modular butterflies per second against
-        # the issue-rate peak (SMs x 4 schedulers x 32 lanes x max clock)
-        # divided by the 32-bit operations of one 64-bit Shoup butterfly
+        # the measured rate of the same butterfly on register data (the
+        # lola_alu_rate microbenchmark on this GPU, timed just before); the
+        # unit-count derivation is kept beside it for reference
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         sm_hz = peaks.get("sm_max_mhz", 2070.0) * 1e6
-        peak_bf = sms * 128 * sm_hz / OPS_PER_BUTTERFLY / 1e9
+        derived = sms * 128 * sm_hz / OPS_PER_BUTTERFLY / 1e9
+        kind = "inv_butterfly" if dom in INVERSE_KERNELS else "fwd_butterfly"
+        peak_bf = alu[kind] / 1e9
         bf_per_unit = (n // 2) * (n.bit_length() - 1)
         achieved = d["units"] * bf_per_unit / (d["ms"] / 1000.0) / 1e9
         roofline.update({"bound": "alu", "achieved": achieved, "peak": peak_bf, "unit": "Gbutterfly/s",
                          "frac": achieved / peak_bf,
-                         "peak_source": f"derived: {sms} SMs x 128 lanes x {sm_hz / 1e9:.2f} GHz / {OPS_PER_BUTTERFLY} "
-                                        "32-bit ops per 64-bit Shoup butterfly"})
+                         "peak_source": f"measured: lola_alu_rate {kind} (the kernel's butterfly on register data, "
+                                        f"{sms} SMs x 8 CTAs x 256 threads, CUDA events)",
+                         "derived_peak": derived,
+                         "derived_peak_source": f"{sms} SMs x 128 lanes x {sm_hz / 1e9:.2f} GHz / "
+                                                f"{OPS_PER_BUTTERFLY} 32-bit ops per butterfly"})
     else:
         roofline.update({"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": (hbm_achieved / hbm_peak) if hbm_achieved else None, "peak_source": peak_src})
@@ -616,6 +744,7 @@ def run_ours(args):
                       "graph": False},
             "ntt_gbs": ntt_gbs,
             "roofline": roofline,
+            "alu_peaks": {k: v for k, v in alu.items()},
             "kernels": {k: {"ms_per_step": v["ms"] / args.profile_steps, "launches_per_step": v["launches"] // args.profile_steps}
                         for k, v in sorted(per_kernel.items(), key=lambda kv: -kv[1]["ms"])},
             "cpu_baseline": cpu,
@@ -682,9 +811,8 @@ def run_primitives(args):
     pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pk):
         peaks = json.load(open(pk))
-    sms = torch.cuda.get_device_properties(0).multi_processor_count
-    clk = peaks.get("sm_max_mhz", 2070.0) * 1e6
-    peak_bf = sms * 128 * clk / OPS_PER_BUTTERFLY / 1e9
+    alu = measured_alu_peaks(L, ctx)
+    peak_fwd, peak_inv = alu["fwd_butterfly"] / 1e9, alu["inv_butterfly"] / 1e9
     bf_limb = (n // 2) * (n.bit_length() - 1)
     res = {}
     for name, (fn, cts) in ops.items():
@@ -703,11 +831,12 @@ def run_primitives(args):
         if name.startswith("ntt"):
             limbs = 2 * B * Lq
             r["GB/s"] = limbs * 16 * n / (med / 1000) / 1e9
-            r["alu_frac"] = limbs * bf_limb / (med / 1000) / 1e9 / peak_bf
+            r["alu_frac"] = limbs * bf_limb / (med / 1000) / 1e9 / (peak_fwd if name == "ntt_fwd" else peak_inv)
         res[name] = r
     print(json.dumps({"mode": "primitives", "n": n, "L": Lq, "K": ps.K, "batch": B, "steps": args.steps,
                       "data": "synthetic uniform residues, random rotation steps",
-                      "alu_peak_gbutterfly_s": peak_bf, "ops": res}), flush=True)
+                      "alu_peak_gbutterfly_s": {"fwd": peak_fwd, "inv": peak_inv, "source": "measured (lola_alu_rate)"},
+                      "ops": res}), flush=True)
     for h in (src, dst, prod):
         L.lola_ct_destroy(h)
     L.lola_keys_destroy(sk)

@@ -171,20 +171,24 @@ int lola_rotate(lola_ctx* ctx, const lola_keys* keys, const uint64_t* in, uint64
 int lola_multiply(lola_ctx* ctx, const lola_keys* keys, const uint64_t* a, const uint64_t* b, uint64_t* out,
                   size_t count, const uint32_t* t_index, void* stream);
 /* Rotation that allocates no device memory, for callers that cannot call
- * cudaMalloc / cudaMallocAsync (inside a stream capture that must stay free
- * of allocation nodes, or under a memory manager that forbids allocation
- * after start-up).  The paper has no counterpart: this is a library
- * facility.  out_i = rotate(in_i, step) for i < count, one step for all
- * (0 < step < n/2 right shift of each slot row, 0 = row swap), device
- * layout, NTT form; the result is identical to lola_rotate's.
- * Scratch comes from a static device array of LOLA_ROTATE_NOALLOC_SCRATCH_BYTES
- * compiled into the library, which every GPU that loads the library keeps
- * until the process exits.  The first call on a device looks up that array's
- * address (cudaGetSymbolAddress), so make it before any stream capture.
- * Calls share the array: calls that overlap on the GPU race and must be
- * serialised by the caller.  No part of the array needs clearing between
- * calls.  A count whose scratch (count * (L + L*(L+K) + 2) * n words) does
- * not fit returns LOLA_E_PARAM; missing key: LOLA_E_NOKEY. */
+ * cudaMalloc / cudaMallocAsync: applications whose memory manager owns the
+ * device and forbids allocation after start-up, hosts that budget every byte
+ * of device memory up front, latency-critical loops that cannot afford an
+ * allocation or its possible implicit synchronisation.  The paper has no
+ * counterpart: this is a library facility.  out_i = rotate(in_i, step) for
+ * i < count, one step for all (0 < step < n/2 right shift of each slot row,
+ * 0 = row swap), device layout, NTT form; the result is identical to
+ * lola_rotate's.  Scratch comes from a static device array of
+ * LOLA_ROTATE_NOALLOC_SCRATCH_BYTES compiled into the library, which every
+ * GPU that loads the library keeps until the process exits.  The first call
+ * with a context looks up that array's address on the context's device
+ * (cudaGetSymbolAddress) and keeps it in the context, so make that first
+ * call before any stream capture.  Calls share the array: calls that overlap
+ * on the GPU race and must be serialised by the caller.  No part of the
+ * array needs clearing between calls.  A count whose scratch does not fit
+ * returns LOLA_E_PARAM; the scratch is count * (L + L*(L+K) + 2) * n words,
+ * plus count * 2 * (L+K) * n words when L = 1 (a separate inner-product
+ * area); missing key: LOLA_E_NOKEY. */
 #define LOLA_ROTATE_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
 int lola_rotate_noalloc(lola_ctx* ctx, const lola_keys* keys, const uint64_t* in, uint64_t* out, size_t count,
                         int32_t step, void* stream);
@@ -349,6 +353,30 @@ int lola_profile_enable(lola_ctx* ctx, int kind, int on);
 int lola_profile_read(lola_ctx* ctx, int kind, double* ms, uint64_t* launches, uint64_t* units);
 int lola_profile_kinds(void);
 const char* lola_profile_name(int kind);
+/* Integer-unit microbenchmarks on the context's device, the measured peaks
+ * the transforms' rates are stated against (the paper has no counterpart:
+ * its transforms ran on a CPU).  Each kernel runs a fixed count of operations
+ * per thread on register data, 8 CTAs of 256 threads per SM, timed with CUDA
+ * events (best of three after one warm-up; about 0.1 s each).  kind:
+ *   LOLA_ALU_FWD_BUTTERFLY   forward butterflies of the transforms (lazy,
+ *                            32-bit-halves Shoup product) per second
+ *   LOLA_ALU_INV_BUTTERFLY   inverse butterflies per second
+ *   LOLA_ALU_FWD_BUTTERFLY_C forward butterflies with the product in the
+ *                            compiler's 64-bit arithmetic, per second
+ *   LOLA_ALU_MAD_LO_U32, LOLA_ALU_MAD_WIDE_U32, LOLA_ALU_MUL_HI_U32
+ *                            instructions per second
+ *   LOLA_ALU_MMA_S8          int8 tensor-core operations (mma.sync m16n8k32,
+ *                            2 * 16 * 8 * 32 per instruction) per second
+ * per_second and ms (best kernel time) may be NULL.  Errors: LOLA_E_PARAM
+ * (unknown kind), LOLA_E_CUDA, LOLA_E_NOMEM. */
+#define LOLA_ALU_FWD_BUTTERFLY 0
+#define LOLA_ALU_INV_BUTTERFLY 1
+#define LOLA_ALU_FWD_BUTTERFLY_C 2
+#define LOLA_ALU_MAD_LO_U32 3
+#define LOLA_ALU_MAD_WIDE_U32 4
+#define LOLA_ALU_MUL_HI_U32 5
+#define LOLA_ALU_MMA_S8 6
+int lola_alu_rate(lola_ctx* ctx, int kind, double* per_second, double* ms);
 /* Kernel launches issued by the library since context creation (launches
  * inside a replayed CUDA graph are counted once, when captured). */
 uint64_t lola_launch_count(const lola_ctx* ctx);

@@ -545,4 +545,9 @@ const char* lola_profile_name(int kind) { return kernel_name(kind); }
 
 uint64_t lola_launch_count(const lola_ctx* ctx) { return ctx ? ctx->c->launches.load() : 0; }
 
+int lola_alu_rate(lola_ctx* ctx, int kind, double* per_second, double* ms) {
+  CHECK(ctx, LOLA_E_PARAM, "null context");
+  return alu_rate(ctx->c, kind, per_second, ms);
+}
+
 }  // extern "C"

@@ -88,6 +88,9 @@ struct Ctx {
   std::atomic<uint64_t> launches{0};
   Profiler prof;
   Tune tune;                      // root context's table applies to every level
+  // device address of the library's static rotation scratch array (looked
+  // up on the first lola_rotate_noalloc call with this context)
+  std::atomic<uint64_t*> noalloc_scratch{nullptr};
   // Modulus switching: a context of the first L' < L ciphertext primes (same
   // special prime, plaintext moduli and keys) is a child of the full one.
   // Launch counts and profiles go to the root; children live in its map.
@@ -129,5 +132,9 @@ struct Ct {
 };
 
 uint32_t galois_for_step(uint32_t n, int32_t step);   // step 0 = row swap
+
+// Integer-unit microbenchmark `kind` (lola_alu_rate) on the context's device:
+// operations per second and the best kernel time in ms (peak.cu).
+int alu_rate(Ctx* c, int kind, double* per_second, double* ms);
 
 }  // namespace lola

@@ -1,0 +1,233 @@
+// Microbenchmarks of the integer units the transforms are bound by, so that
+// a transform kernel's rate can be stated as a fraction of a measured peak
+// instead of one derived from unit counts.
+//
+// Each kernel runs a fixed number of operations per thread on register data
+// (no memory traffic inside the loop), on 8 CTAs of 256 threads per SM; the
+// host times it with CUDA events (best of three after a warm-up run).
+//  * forward / inverse butterflies: the transforms' own butterflies (lazy
+//    Harvey butterflies with the Shoup product, the forward one correcting
+//    its "a" operand on even stages), 16 words and 8 twiddle pairs per thread
+//    in registers, stages of decreasing distance as in one pass;
+//  * the same forward butterfly with the product left to the compiler's
+//    64-bit arithmetic (for comparison with the 32-bit-halves product);
+//  * mad.lo.u32, mad.wide.u32, mul.hi.u32: eight independent chains per
+//    thread;
+//  * mma.sync m16n8k32 s8 x s8 -> s32 (the integer tensor-core path an
+//    int8-split matrix transform would use): four independent accumulators
+//    per warp, 2 * 16 * 8 * 32 integer operations per instruction.
+#include <cuda_runtime.h>
+
+#include "internal.h"
+#include "modarith.cuh"
+
+namespace lola {
+
+#define TRY_OK(x)                   \
+  do {                              \
+    int _rc = (x);                  \
+    if (_rc != LOLA_OK) return _rc; \
+  } while (0)
+
+namespace {
+
+constexpr int kThreads = 256, kCtasPerSm = 8;
+
+template <bool PTX>
+__device__ __forceinline__ uint64_t prod(uint64_t x, uint64_t w, uint64_t wp, uint64_t q, uint64_t nq) {
+  if constexpr (PTX) return shoup_mul_lazy_ptx(x, w, wp, nq);
+  else return x * w - __umul64hi(x, wp) * q;
+}
+
+template <bool PTX>
+__global__ void __launch_bounds__(kThreads) kb_fwd_butterfly(const uint64_t* __restrict__ tw, uint64_t q, int iters,
+                                                             uint64_t* __restrict__ sink) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  uint64_t x[16], w[8], wp[8];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) x[k] = (uint64_t)(tid * 16 + k) % q;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    w[k] = tw[2 * k];
+    wp[k] = tw[2 * k + 1];
+  }
+  const uint64_t q2 = 2 * q, q4 = 4 * q, nq = 0ull - q;
+  const uint32_t q4hi = (uint32_t)(q4 >> 32);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int lbit = 3; lbit >= 0; --lbit) {
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        if (k & (1 << lbit)) continue;
+        const int ti = (k >> (lbit + 1)) & 7;
+        uint64_t a = x[k];
+        if ((lbit & 1) == 1 && (uint32_t)(a >> 32) > q4hi) a -= q4;   // every other stage
+        const uint64_t t = prod<PTX>(x[k | (1 << lbit)], w[ti], wp[ti], q, nq);
+        x[k] = a + t;
+        x[k | (1 << lbit)] = a - t + q2;
+      }
+    }
+  }
+  uint64_t acc = 0;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) acc ^= x[k];
+  sink[tid] = acc;
+}
+
+__global__ void __launch_bounds__(kThreads) kb_inv_butterfly(const uint64_t* __restrict__ tw, uint64_t q, int iters,
+                                                             uint64_t* __restrict__ sink) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  uint64_t x[16], w[8], wp[8];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) x[k] = (uint64_t)(tid * 16 + k) % q;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    w[k] = tw[2 * k];
+    wp[k] = tw[2 * k + 1];
+  }
+  const uint64_t q2 = 2 * q;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int lbit = 0; lbit < 4; ++lbit) {
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        if (k & (1 << lbit)) continue;
+        const int ti = (k >> (lbit + 1)) & 7;
+        const uint64_t a = x[k], b = x[k | (1 << lbit)];
+        uint64_t u = a + b;
+        u = u >= q2 ? u - q2 : u;
+        x[k] = u;
+        x[k | (1 << lbit)] = shoup_mul_lazy(a - b + q2, w[ti], wp[ti], q);
+      }
+    }
+  }
+  uint64_t acc = 0;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) acc ^= x[k];
+  sink[tid] = acc;
+}
+
+// OP 0: mad.lo.u32, 1: mad.wide.u32, 2: mul.hi.u32 (eight chains per thread)
+template <int OP>
+__global__ void __launch_bounds__(kThreads) kb_imad(uint32_t c, int iters, uint64_t* __restrict__ sink) {
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t v[8];
+  uint64_t v64[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    v[k] = tid * 8 + k + 1;
+    v64[k] = v[k];
+  }
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        if constexpr (OP == 0) {
+          asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(v[k]) : "r"(c), "r"(v[(k + 1) & 7]));
+        } else if constexpr (OP == 1) {
+          asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(v64[k]) : "r"((uint32_t)v64[k]), "r"(c));
+        } else {
+          asm volatile("mul.hi.u32 %0, %0, %1;" : "+r"(v[k]) : "r"(c | 0x80000000u));
+        }
+      }
+    }
+  }
+  uint64_t acc = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) acc += v[k] + v64[k];
+  sink[tid] = acc;
+}
+
+__global__ void __launch_bounds__(kThreads) kb_mma_s8(int iters, uint64_t* __restrict__ sink) {
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t a[4], b[2];
+  int32_t d[4][4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) a[k] = 0x01010101u * ((tid + k) & 3);
+  b[0] = 0x01020102u;
+  b[1] = 0x02010201u;
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) d[j][k] = 0;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      asm volatile(
+          "mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+          "{%0, %1, %2, %3};"
+          : "+r"(d[j][0]), "+r"(d[j][1]), "+r"(d[j][2]), "+r"(d[j][3])
+          : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+    }
+  }
+  uint64_t acc = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc += (uint32_t)d[j][k];
+  sink[tid] = acc;
+}
+
+}  // namespace
+
+// operations per thread per loop iteration of each kind
+static double ops_per_iter(int kind) {
+  switch (kind) {
+    case 0: case 1: case 2: return 32;         // butterflies (4 stages x 8)
+    case 3: case 4: case 5: return 64;         // instructions (8 rounds x 8 chains)
+    case 6: return 4.0 * 2 * 16 * 8 * 32 / 32; // int8 operations per thread (4 mma per warp)
+    default: return 0;
+  }
+}
+
+int alu_rate(Ctx* c, int kind, double* per_second, double* ms_out) {
+  if (kind < 0 || kind > 6) return fail(LOLA_E_PARAM, "unknown ALU benchmark kind");
+  LOLA_CUDA_TRY(cudaSetDevice(c->device));
+  int sms = 0;
+  LOLA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+  const int blocks = sms * kCtasPerSm;
+  const int iters = kind <= 2 ? 2048 : (kind <= 5 ? 16384 : 8192);
+  DevBuf sink, tw;
+  TRY_OK(sink.alloc((size_t)blocks * kThreads * 8));
+  TRY_OK(tw.alloc(16 * 8));
+  // twiddles of the first ciphertext prime: the first 8 (w, w') pairs of its forward table
+  LOLA_CUDA_TRY(cudaMemcpy(tw.p, c->host.tw_fwd + 2 * 8, 16 * 8, cudaMemcpyDeviceToDevice));
+  const uint64_t q = c->primes[0];
+  cudaEvent_t e0, e1;
+  LOLA_CUDA_TRY(cudaEventCreate(&e0));
+  LOLA_CUDA_TRY(cudaEventCreate(&e1));
+  float best = 0;
+  for (int rep = 0; rep < 4; ++rep) {
+    cudaEventRecord(e0, nullptr);
+    switch (kind) {
+      case 0: kb_fwd_butterfly<true><<<blocks, kThreads>>>(tw.u64(), q, iters, sink.u64()); break;
+      case 1: kb_inv_butterfly<<<blocks, kThreads>>>(tw.u64(), q, iters, sink.u64()); break;
+      case 2: kb_fwd_butterfly<false><<<blocks, kThreads>>>(tw.u64(), q, iters, sink.u64()); break;
+      case 3: kb_imad<0><<<blocks, kThreads>>>(0x9E3779B9u, iters, sink.u64()); break;
+      case 4: kb_imad<1><<<blocks, kThreads>>>(0x9E3779B9u, iters, sink.u64()); break;
+      case 5: kb_imad<2><<<blocks, kThreads>>>(0x9E3779B9u, iters, sink.u64()); break;
+      case 6: kb_mma_s8<<<blocks, kThreads>>>(iters, sink.u64()); break;
+    }
+    cudaEventRecord(e1, nullptr);
+    cudaError_t err = cudaEventSynchronize(e1);
+    if (err == cudaSuccess) err = cudaGetLastError();
+    if (err != cudaSuccess) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return fail(LOLA_E_CUDA, std::string("ALU benchmark: ") + cudaGetErrorString(err));
+    }
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0 && (best == 0 || ms < best)) best = ms;   // rep 0 is the warm-up
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->root->launches.fetch_add(4, std::memory_order_relaxed);
+  const double ops = (double)blocks * kThreads * iters * ops_per_iter(kind);
+  if (per_second) *per_second = ops / (best * 1e-3);
+  if (ms_out) *ms_out = best;
+  return LOLA_OK;
+}
+
+}  // namespace lola

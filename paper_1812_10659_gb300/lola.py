@@ -107,6 +107,7 @@ _SIGS = {
     "lola_profile_read": (C.c_int, [P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_uint64),
                                     C.POINTER(C.c_uint64)]),
     "lola_profile_kinds": (C.c_int, []),
+    "lola_alu_rate": (C.c_int, [P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "lola_profile_name": (C.c_char_p, [C.c_int]),
     "lola_launch_count": (C.c_uint64, [P]),
     "lola_last_error": (C.c_char_p, []),
@@ -526,6 +527,19 @@ def lola_profile_read(ctx, kind):
     ms, cnt, units = C.c_double(), C.c_uint64(), C.c_uint64()
     _check(load().lola_profile_read(ctx, kind, C.byref(ms), C.byref(cnt), C.byref(units)))
     return ms.value, cnt.value, units.value
+
+
+ALU_KINDS = {"fwd_butterfly": 0, "inv_butterfly": 1, "fwd_butterfly_c": 2, "mad_lo_u32": 3,
+             "mad_wide_u32": 4, "mul_hi_u32": 5, "mma_s8": 6}
+
+
+def lola_alu_rate(ctx, kind) -> tuple:
+    """(operations per second, best kernel ms) of integer-unit microbenchmark
+    `kind` (a name of ALU_KINDS or its number) on the context's device."""
+    k = ALU_KINDS[kind] if isinstance(kind, str) else int(kind)
+    rate, ms = C.c_double(), C.c_double()
+    _check(load().lola_alu_rate(ctx, k, C.byref(rate), C.byref(ms)))
+    return rate.value, ms.value
 
 
 def lola_profile_kinds() -> int:

@@ -102,3 +102,22 @@ def test_autotune_cache_file(tmp_path):
         assert Lb.lola_tune_get(ctx)["table"] == first["table"]
     finally:
         Lb.lola_ctx_destroy(ctx)
+
+
+def test_alu_microbenchmarks_report_positive_rates():
+    # the measured integer peaks the transforms' roofline is stated against:
+    # every kind runs and returns a positive rate; unknown kinds are refused
+    need_gpu()
+    Lb = lib()
+    ctx = make_ctx(W.params_small(1024, L=2))
+    try:
+        rates = {k: Lb.lola_alu_rate(ctx, k) for k in Lb.ALU_KINDS}
+        for k, (r, ms) in rates.items():
+            assert r > 0 and ms > 0, k
+        # a butterfly needs about a dozen 32-bit multiply-class instructions:
+        # its rate must sit far below the mad.lo.u32 instruction rate
+        assert rates["fwd_butterfly"][0] < rates["mad_lo_u32"][0] / 4
+        with pytest.raises(Lb.LolaError):
+            Lb.lola_alu_rate(ctx, 99)
+    finally:
+        Lb.lola_ctx_destroy(ctx)
