@@ -55,10 +55,12 @@ def parse():
     ap.add_argument("--plain", type=int, default=8, help="single-request evaluations for plain latency")
     ap.add_argument("--L", type=int, default=None,
                     help="ciphertext primes (default: 5 for mnist, 6 for lola_dense)")
-    ap.add_argument("--workload", choices=["mnist", "lola_dense", "cifar", "head"], default="mnist",
+    ap.add_argument("--workload", choices=["mnist", "lola_dense", "cifar", "head", "dense64"], default="mnist",
                     help="mnist: convolution-representation input (Sec. 4.3); lola_dense: dense input "
                          "masked on the server (App. C); cifar: the CIFAR-shaped network (Sec. 6.2); "
-                         "head: the transfer-learning head (Sec. 5), 4096 -> 101, one plaintext modulus")
+                         "head: the transfer-learning head (Sec. 5), 4096 -> 101, one plaintext modulus; "
+                         "dense64: one stacked dense layer 64 -> 10 + square at n = 4096 (Sec. 4.1's linear "
+                         "classifier shape), three 36-bit primes, t = 65537")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's default launch geometry")
     ap.add_argument("--no-mod-switch", action="store_true",
@@ -67,11 +69,16 @@ def parse():
     ap.add_argument("--profile-steps", type=int, default=1)
     ap.add_argument("--mode", choices=["network", "serve", "primitives"], default="network")
     ap.add_argument("--n", type=int, default=16384, help="primitives mode: ring degree")
+    ap.add_argument("--sweep", action="store_true",
+                    help="primitives mode: the grid B = 1..256 x n in {8192, 16384} x L = 4..8")
     ap.add_argument("--rates", default="25,100,200", help="serve mode: Poisson arrival rates (requests/s)")
     ap.add_argument("--duration", type=float, default=10.0, help="serve mode: seconds of arrivals per rate")
+    ap.add_argument("--drain", type=float, default=15.0,
+                    help="serve mode: seconds after the arrivals end to finish queued requests (a saturated "
+                         "server's backlog beyond that is reported as unfinished)")
     args = ap.parse_args()
     if args.L is None:
-        args.L = {"mnist": 5, "head": HEAD_L}.get(args.workload, 6)
+        args.L = {"mnist": 5, "head": HEAD_L, "dense64": 3}.get(args.workload, 6)
     import workloads as W
     args.levels = None
     if not args.no_mod_switch:
@@ -82,7 +89,7 @@ def parse():
         elif args.workload == "cifar" and args.L == 6:
             args.levels = W.CIFAR_LEVELS
     if args.batch is None:
-        args.batch = {"cifar": 2, "head": 64}.get(args.workload, 16)
+        args.batch = {"cifar": 2, "head": 64, "dense64": 256}.get(args.workload, 16)
     return args
 
 
@@ -93,7 +100,8 @@ HEAD_L = 3
 OP_COUNTS = {"mnist": {"rot": 224, "square": 2, "mul_plain": 24, "mul_scalar": 125, "add": 344},
              "lola_dense": {"rot": 326, "square": 2, "mul_plain": 61, "mul_scalar": 125, "add": 422},
              "cifar": {"rot": 57273, "square": 2, "mul_plain": 8162, "mul_scalar": 15936, "add": 77200},
-             "head": {"rot": 339, "square": 0, "mul_plain": 52, "mul_scalar": 0, "add": 339}}
+             "head": {"rot": 339, "square": 0, "mul_plain": 52, "mul_scalar": 0, "add": 339},
+             "dense64": {"rot": 6, "square": 1, "mul_plain": 1, "mul_scalar": 0, "add": 6}}
 # the networks with modulus switching (to 4 primes after the first square,
 # to 2 after the second): the same counts split by level
 OP_COUNTS_LEVELS = {"mnist": {5: {"rot": 4, "square": 1, "mul_plain": 0, "mul_scalar": 125, "add": 124},
@@ -106,7 +114,7 @@ OP_COUNTS_LEVELS = {"mnist": {5: {"rot": 4, "square": 1, "mul_plain": 0, "mul_sc
                               4: {"rot": 57050, "square": 1, "mul_plain": 8150, "mul_scalar": 0, "add": 61124},
                               2: {"rot": 140, "square": 0, "mul_plain": 10, "mul_scalar": 0, "add": 140}}}
 WORKLOAD_NAME = {"mnist": "mnist_lola_n16384", "lola_dense": "lola_dense_n16384", "cifar": "cifar_lola_n16384",
-                 "head": "transfer_head_n16384"}
+                 "head": "transfer_head_n16384", "dense64": "dense64_n4096"}
 
 
 # ------------------------------------------------------------------ clocks
@@ -168,6 +176,8 @@ class ClockSampler:
 # ------------------------------------------------------------ CPU baseline
 def workload_params(workload, L):
     import workloads as W
+    if workload == "dense64":
+        return W.params_dense64()
     return {"cifar": W.params_cifar, "head": W.params_head}.get(workload, W.params_mnist)(L)
 
 
@@ -209,7 +219,7 @@ def oracle_sample(n_rot=1, n_sq=1, workload="mnist", L=5, levels=None):
         parts.append(f"L={lv}: rotation {t_rot:.3f}s, square+relin {t_sq:.3f}s, ct*pt {t_pt:.3f}s, "
                      f"ct*scalar {t_sc:.4f}s, add {t_add:.4f}s x ({counts['rot']} rot, {counts['square']} sq, "
                      f"{counts['mul_plain']} ct*pt, {counts['mul_scalar']} ct*scalar, {counts['add']} add)")
-    desc = (f"oracle per-op times on n=16384 x op counts of one inference per level; " + "; ".join(parts)
+    desc = (f"oracle per-op times on n={ps.n} x op counts of one inference per level; " + "; ".join(parts)
             + f"; x {len(ps.t)} CRT residues")
     return sec, desc
 
@@ -253,6 +263,13 @@ def oracle_residue_inference(workload, L, levels, ti):
         layers = W.layers_mnist(mnet, n, levels)
         msgs, pos = OL.pack_convolution(img, mnet.kh, mnet.kw, mnet.stride, n)
         want = plain_mnist(img, mnet)
+    elif workload == "dense64":
+        Wd, x = W.dense_weights(), W.dense_vector()
+        copies = W.dense64_input_copies(Wd)
+        layers = W.layers_dense64(Wd, n)
+        v, pos = OL.pack_stacked(x, 6, copies, n)
+        msgs = [np.asarray(v, np.int64)]
+        want = [v * v for v in plain_dense(x, Wd)]
     else:
         Wh = W.head_weights()
         layers = W.layers_head(Wh, n)
@@ -261,14 +278,15 @@ def oracle_residue_inference(workload, L, levels, ti):
         v[:len(x)] = x
         msgs, pos = [v], [(0, i) for i in range(len(x))]
         want = plain_dense(x, Wh)
-    steps = _slot_rotation_steps(layers, n, t, OL.State([np.asarray(m, np.int64) % t for m in msgs], pos))
+    stacked = {"block": 64, "copies": W.dense64_input_copies(W.dense_weights())} if workload == "dense64" else {}
+    steps = _slot_rotation_steps(layers, n, t, OL.State([np.asarray(m, np.int64) % t for m in msgs], pos, **stacked))
     t0 = time.perf_counter()
     keys = bfv.keygen(P, W.DEFAULT_SEED, rotations=[s for s in steps if s], relin=True, row_swap=0 in steps)
     t1 = time.perf_counter()
     cts = [bfv.encrypt(P, keys.pk, encoding.encode(m, t), t, 5, i * kt + ti) for i, m in enumerate(msgs)]
     t2 = time.perf_counter()
     ev = OL.HEEval(P, keys, t)
-    st = OL.run_network(ev, layers, OL.State(cts, pos))
+    st = OL.run_network(ev, layers, OL.State(cts, pos, **stacked))
     t3 = time.perf_counter()
     got = {}
     for m, s in st.pos:
@@ -297,7 +315,7 @@ def oracle_e2e_inference(workload="mnist", L=5, levels=None) -> dict:
     return agg
 
 
-E2E_WORKLOADS = ("mnist", "head")
+E2E_WORKLOADS = ("mnist", "head", "dense64")
 
 
 def cpu_baseline_obj(workload="mnist", L=5, levels=None):
@@ -350,7 +368,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "inferences/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1000,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": WORKLOAD_NAME[args.workload], "n": 16384, "L": args.L, "K": 1,
+            "config": {"workload": WORKLOAD_NAME[args.workload], "n": workload_params(args.workload, args.L).n,
+                       "L": args.L, "K": workload_params(args.workload, args.L).K,
                        "k_t": len(workload_params(args.workload, args.L).t),
                        "levels": [args.L] + list(args.levels or []),
                        "parallelism": "none (CPU oracle)"},
@@ -510,6 +529,12 @@ def run_ours(args):
         Wh = W.head_weights()
         layers = W.layers_head(Wh, n)
         net = L.lola_net_create(ctx, {"repr": "dense", "n_msgs": 1, "n_elems": Wh.shape[1]}, layers)
+    elif args.workload == "dense64":
+        Wd = W.dense_weights()
+        copies = W.dense64_input_copies(Wd)
+        layers = W.layers_dense64(Wd, n)
+        net = L.lola_net_create(ctx, {"repr": "stacked", "n_msgs": 1, "n_elems": Wd.shape[1], "d": 6,
+                                      "copies": copies}, layers)
     else:
         layers = W.layers_mnist(mnet, n, args.levels)
         net = L.lola_net_create(ctx, {"repr": "convolution", "n_msgs": 25, "n_elems": 169}, layers)
@@ -526,9 +551,12 @@ def run_ours(args):
         packed = np.zeros((B, n), np.int64)
         for i, x in enumerate(imgs):
             packed[i, :len(x)] = x
+    elif args.workload == "dense64":
+        imgs = [W.dense_vector(seed=W.DEFAULT_SEED + rank * 100000 + i) for i in range(B)]
+        packed = np.stack([L.lola_pack_stacked(x, 6, copies, n) for x in imgs])
     else:
         imgs = [W.image(idx=rank * 100000 + i) for i in range(B)]
-    if args.workload in ("cifar", "head"):
+    if args.workload in ("cifar", "head", "dense64"):
         pass
     elif args.workload == "lola_dense":
         # one dense message per image, line after line (29-slot lines)
@@ -585,6 +613,12 @@ def run_ours(args):
         want = plain_cifar(imgs[0], cnet)
         correct = all([int(res[m, ti, s]) for m, s in net.output_map()] == [v % t for v in want]
                       for ti, t in enumerate(ps.t))
+    elif args.workload == "dense64":
+        # the square wraps mod t = 65537 (Sec. 4.1 shape at n = 4096): compare mod t
+        dec = L.lola_decrypt(ctx, sk, ct_out, n)
+        t = ps.t[0]
+        want = [v * v for v in plain_dense(imgs[0], Wd)]
+        correct = [int(dec[m, s]) % t for m, s in net.output_map()] == [v % t for v in want]
     else:
         dec = L.lola_decrypt(ctx, sk, ct_out, n)
         want = plain_dense(imgs[0], Wh) if args.workload == "head" else plain_mnist(imgs[0], mnet)
@@ -728,7 +762,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "inferences/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": WORKLOAD_NAME[args.workload], "batch_per_gpu": B, "n": n, "L": Lq, "K": 1, "k_t": kt,
+            "config": {"workload": WORKLOAD_NAME[args.workload], "batch_per_gpu": B, "n": n, "L": Lq, "K": ps.K, "k_t": kt,
                        "levels": [Lq] + list(args.levels or []),
                        "autotune": ({"table": tune["table"], "seconds": round(t_tune, 2)} if tune else "defaults"),
                        "aux_primes": len(L.lola_ctx_aux_primes(ctx)), "parallelism": f"replicas x{world}",
@@ -766,30 +800,24 @@ def run_ours(args):
 
 
 # ---------------------------------------------------------------- primitives
-def run_primitives(args):
-    """One launch per operation on a batch of `--batch` ciphertexts of
-    uniform random residues (n = `--n`, `--L` 60-bit primes + a special
-    prime): forward NTT and inverse NTT of all 2 B L limb-polynomials, B
-    rotations by random steps in [1, n/2) (one Galois key per distinct
-    step), B/2 ct x ct products with relinearisation.  Per operation: device
-    time per launch (CUDA events), per ciphertext, and the transform rate
-    against the derived integer-ALU peak.  rotate_hoisted_x8: every
-    ciphertext rotated by 8 of those steps sharing one decomposition."""
+SWEEP_N = (8192, 16384)
+SWEEP_L = (4, 5, 6, 7, 8)
+SWEEP_B = (1, 2, 4, 8, 16, 32, 64, 128, 256)
+KEY_POOL = 32          # distinct random rotation steps (Galois keys) per context
+
+
+def primitives_case(L, ctx, ps, ev, pool, B, args, alu):
+    """One (n, L, B) case: one launch per operation on B ciphertexts of
+    uniform random residues; returns the per-operation results."""
     import numpy as np
     import torch
 
     import workloads as W
-    from paper_1812_10659_gb300 import lola as L
-
-    ps = W.params_sweep(args.n, args.L)
-    n, Lq, B = ps.n, ps.L, args.batch
-    ctx = L.lola_ctx_create(ps.n, ps.q, ps.L, ps.K, ps.t)
-    if not args.no_autotune:
-        L.lola_autotune(ctx)
+    n, Lq = ps.n, ps.L
     stream = torch.cuda.current_stream()
-    host = W.random_residues(11, (B, 2), ps.q[:Lq], n)
-    steps = [int(s) for s in W.rotation_steps(11, B, n)]
-    sk, ev = L.lola_keygen(ctx, 11, sorted(set(steps)), L.LOLA_KEY_RELIN)
+    host = W.random_residues(11 + B, (B, 2), ps.q[:Lq], n)
+    order = np.random.default_rng(B).permutation(max(B, len(pool)))
+    steps = [int(pool[order[i] % len(pool)]) for i in range(B)]
     src = L.lola_ct_import(ctx, host[:, None])
     dst = L.lola_ct_create(ctx, B)
     half = max(1, B // 2)
@@ -797,7 +825,7 @@ def run_primitives(args):
     work = torch.from_numpy(host.view(np.int64).copy()).cuda()
     ps_src, ps_dst, ps_prod = L.lola_ct_data(src), L.lola_ct_data(dst), L.lola_ct_data(prod)
     ct_bytes = 2 * Lq * n * 8
-    hsteps = sorted(set(steps))[:8]                   # 8 rotations of every ciphertext, one decomposition
+    hsteps = [int(x) for x in pool[:8]]               # 8 rotations of every ciphertext, one decomposition
     hout = torch.empty(len(hsteps) * B * 2 * Lq * n, dtype=torch.int64, device="cuda")
     ops = {
         "ntt_fwd": (lambda: L.lola_ntt_forward(ctx, work, 2 * B, Lq, stream), B),
@@ -807,11 +835,6 @@ def run_primitives(args):
         "multiply_relin": (lambda: L.lola_multiply(ctx, ev, ps_src, ps_src + (half * ct_bytes if B > 1 else 0),
                                                    ps_prod, half, stream=stream), half),
     }
-    peaks = {}
-    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(pk):
-        peaks = json.load(open(pk))
-    alu = measured_alu_peaks(L, ctx)
     peak_fwd, peak_inv = alu["fwd_butterfly"] / 1e9, alu["inv_butterfly"] / 1e9
     bf_limb = (n // 2) * (n.bit_length() - 1)
     res = {}
@@ -833,15 +856,63 @@ def run_primitives(args):
             r["GB/s"] = limbs * 16 * n / (med / 1000) / 1e9
             r["alu_frac"] = limbs * bf_limb / (med / 1000) / 1e9 / (peak_fwd if name == "ntt_fwd" else peak_inv)
         res[name] = r
-    print(json.dumps({"mode": "primitives", "n": n, "L": Lq, "K": ps.K, "batch": B, "steps": args.steps,
-                      "data": "synthetic uniform residues, random rotation steps",
-                      "alu_peak_gbutterfly_s": {"fwd": peak_fwd, "inv": peak_inv, "source": "measured (lola_alu_rate)"},
-                      "ops": res}), flush=True)
     for h in (src, dst, prod):
         L.lola_ct_destroy(h)
-    L.lola_keys_destroy(sk)
-    L.lola_keys_destroy(ev)
-    L.lola_ctx_destroy(ctx)
+    del hout, work
+    return res
+
+
+def run_primitives(args):
+    """Batched primitives on ciphertexts of uniform random residues (n =
+    `--n`, `--L` 60-bit primes + a special prime, `--batch` ciphertexts):
+    forward NTT and inverse NTT of all 2 B L limb-polynomials, B rotations by
+    random steps in [1, n/2) (drawn from a pool of up to 32 distinct steps,
+    one Galois key each), B/2 ct x ct products with relinearisation, and
+    rotate_hoisted_x8 (every ciphertext rotated by 8 of the steps sharing one
+    decomposition); one launch per operation.  Per operation: device time
+    per launch (CUDA events), per ciphertext, and the transforms' rate
+    against the measured butterfly rate (lola_alu_rate).  `--sweep` runs the
+    whole grid B in {1, 2, 4, ..., 256} x n in {8192, 16384} x L in 4..8 (the
+    key-switch launch geometry autotuned per (n, L)) and prints one line per
+    case and a summary line; n = 8192 with more than 3 primes is below
+    128-bit security (flagged; the kernels do not depend on it)."""
+    import torch
+
+    import workloads as W
+    from paper_1812_10659_gb300 import lola as L
+
+    grid = ([(n, Lq, SWEEP_B) for n in SWEEP_N for Lq in SWEEP_L] if args.sweep
+            else [(args.n, args.L, (args.batch,))])
+    summary = []
+    alu = None
+    for n, Lq, batches in grid:
+        ps = W.params_sweep(n, Lq)
+        ctx = L.lola_ctx_create(ps.n, ps.q, ps.L, ps.K, ps.t)
+        if not args.no_autotune:
+            L.lola_autotune(ctx)
+        if alu is None:
+            alu = measured_alu_peaks(L, ctx)
+        pool = sorted(set(int(s) for s in W.rotation_steps(11, KEY_POOL, n)))
+        sk, ev = L.lola_keygen(ctx, 11, pool, L.LOLA_KEY_RELIN)
+        for B in batches:
+            res = primitives_case(L, ctx, ps, ev, pool, B, args, alu)
+            line = {"mode": "primitives", "n": n, "L": Lq, "K": ps.K, "batch": B, "steps": args.steps,
+                    "data": "synthetic uniform residues, random rotation steps",
+                    "security": ("128-bit (HE standard: log2 QP <= 218 at n = 8192, 438 at n = 16384)"
+                                 if (Lq + 1) * 60 <= {8192: 218, 16384: 438}.get(n, 0) else
+                                 "below 128-bit (kernel sweep only)"),
+                    "alu_peak_gbutterfly_s": {"fwd": alu["fwd_butterfly"] / 1e9, "inv": alu["inv_butterfly"] / 1e9,
+                                              "source": "measured (lola_alu_rate)"},
+                    "ops": res}
+            print(json.dumps(line), flush=True)
+            summary.append({"n": n, "L": Lq, "B": B, **{k: round(v["us_per_ct"], 3) for k, v in res.items()}})
+        L.lola_keys_destroy(sk)
+        L.lola_keys_destroy(ev)
+        L.lola_ctx_destroy(ctx)
+        torch.cuda.empty_cache()
+    if args.sweep:
+        print(json.dumps({"mode": "primitives_sweep", "unit": "us per ciphertext (per product for multiply_relin)",
+                          "cases": summary}), flush=True)
 
 
 # ------------------------------------------------------------------- serving
@@ -903,8 +974,12 @@ def run_serve(args):
         to_check = []
         t0 = time.perf_counter()
         i = seen = 0
+        host_s = 0.0                             # time spent in the server's host calls
         while i < len(arr) or srv.pending():
             now = time.perf_counter() - t0
+            if now > args.duration + args.drain:
+                break                            # saturated: stop draining, report the backlog
+            h0 = time.perf_counter()
             while i < len(arr) and arr[i][0] <= now:
                 ta, kind, idx = arr[i]
                 rid = srv.submit(kind, pool[kind][idx], t_arrival=t0 + ta)
@@ -919,7 +994,10 @@ def run_serve(args):
                     to_check.append((r.kind, r.pool_idx, r.ct_out))
                     r.ct_out = None
                 srv.release(r.rid)
+            host_s += time.perf_counter() - h0
             time.sleep(1e-4)
+        srv.settle()                             # running batches end; a saturated run's backlog stays queued
+        unfinished = len(arr) - len(srv.done)
         t_end = max(r.t_done for r in srv.done)
         for kind, idx, h in to_check:
             ctx, sk = (ctx2, keys["mnist"][0]) if kind == "mnist" else (ctx4, keys["head"][0])
@@ -929,6 +1007,8 @@ def run_serve(args):
         st = srv.stats()
         st["throughput"] = len(srv.done) / (t_end - t0)
         st["offered"] = len(arr) / args.duration
+        st["unfinished"] = unfinished
+        st["host_ms_per_request"] = 1000.0 * host_s / max(1, len(srv.done))
         srv.close()
         return st, ok
 

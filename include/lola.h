@@ -231,8 +231,8 @@ int lola_mul_plain(lola_ctx* ctx, const uint64_t* in, const int64_t* slots, uint
  * 2 INTT mod P, 3 mod-down) for each of LOLA_TUNE_BUCKETS launch sizes
  * (limb transforms per launch: < 64, < 256, < 1024, < 4096, < 16384, more):
  * 0 = one CTA per limb, 1 = a 2-CTA cluster per limb with 16 words per
- * thread, 2 = a cluster with 32 words per thread (1 and 2 at n = 16384
- * only).  Every geometry computes the same words.  Without tuning the
+ * thread, 2 = a 2-CTA cluster with 32 words per thread, 3 = a 4-CTA cluster
+ * with 16 words per thread (1-3 at n = 16384 only).  Every geometry computes the same words.  Without tuning the
  * library uses clusters for kernels 1-3 at n = 16384 (16 words below 400
  * limb transforms, else 32) and one CTA for decompose.
  * lola_autotune times whole rotations (CUDA events, zero-filled buffers
@@ -242,12 +242,13 @@ int lola_mul_plain(lola_ctx* ctx, const uint64_t* in, const int64_t* slots, uint
  * when the rotations get more than 3 % faster, and installs the table for
  * the context and all of its modulus-switching levels (a fraction of a
  * second); run it while nothing else uses the context.  lola_tune_get copies the table (4 x 6 bytes, kernel-major) and,
- * if us is not NULL, the measured microseconds per launch (4 x 6 x 3 floats,
+ * if us is not NULL, the measured microseconds per launch (4 x 6 x 4 floats,
  * 0 where not run); LOLA_E_STATE when no table is installed.  lola_tune_set
  * installs a table (e.g. from a cache file); NULL restores the defaults.
  * Errors: LOLA_E_PARAM (bad entry), LOLA_E_NOMEM, LOLA_E_CUDA. */
 #define LOLA_TUNE_KERNELS 4
 #define LOLA_TUNE_BUCKETS 6
+#define LOLA_TUNE_VARIANTS 4
 int lola_autotune(lola_ctx* ctx, void* stream);
 int lola_tune_get(const lola_ctx* ctx, uint8_t* table, float* us);
 int lola_tune_set(lola_ctx* ctx, const uint8_t* table);
@@ -367,6 +368,9 @@ const char* lola_profile_name(int kind);
  *                            instructions per second
  *   LOLA_ALU_MMA_S8          int8 tensor-core operations (mma.sync m16n8k32,
  *                            2 * 16 * 8 * 32 per instruction) per second
+ *   LOLA_ALU_FWD_BUTTERFLY_SPARSE  forward butterflies for a prime of the
+ *                            form 2^60 - c 2^32 + 1, whose product qh q
+ *                            needs one 32-bit multiply, per second
  * per_second and ms (best kernel time) may be NULL.  Errors: LOLA_E_PARAM
  * (unknown kind), LOLA_E_CUDA, LOLA_E_NOMEM. */
 #define LOLA_ALU_FWD_BUTTERFLY 0
@@ -376,6 +380,7 @@ const char* lola_profile_name(int kind);
 #define LOLA_ALU_MAD_WIDE_U32 4
 #define LOLA_ALU_MUL_HI_U32 5
 #define LOLA_ALU_MMA_S8 6
+#define LOLA_ALU_FWD_BUTTERFLY_SPARSE 7
 int lola_alu_rate(lola_ctx* ctx, int kind, double* per_second, double* ms);
 /* Kernel launches issued by the library since context creation (launches
  * inside a replayed CUDA graph are counted once, when captured). */

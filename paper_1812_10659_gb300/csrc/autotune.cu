@@ -1,6 +1,7 @@
 // Autotuning of the key-switch transforms' launch geometry (decompose,
 // mod-up, INTT mod P, mod-down; one CTA per limb, or at n = 16384 a 2-CTA
-// cluster per limb with 16 or 32 words per thread) per launch-size bucket.
+// cluster per limb with 16 or 32 words per thread or a 4-CTA cluster with 16)
+// per launch-size bucket.
 //
 // What is timed is the chain the geometry serves: whole rotations (decompose
 // -> mod-up -> inner product -> INTT mod P -> mod-down) of 1, 4, 16, 64 and

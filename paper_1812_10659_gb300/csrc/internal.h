@@ -65,11 +65,12 @@ struct Profiler {
 
 // Launch geometry of the key-switch transforms (decompose, mod-up, INTT mod
 // P, mod-down) per launch-size bucket: one CTA per limb, or (n = 16384) a
-// 2-CTA cluster per limb with 16 or 32 words per thread.  Chosen by timing
-// (autotune) or by the built-in defaults when `on` is false.
+// 2-CTA cluster per limb with 16 or 32 words per thread, or a 4-CTA cluster
+// with 16 words per thread.  Chosen by timing (autotune) or by the built-in
+// defaults when `on` is false.
 constexpr int TUNE_KERNELS = 4;
 constexpr int TUNE_BUCKETS = 6;     // limb transforms per launch: <64, <256, <1024, <4096, <16384, more
-enum TuneVariant : uint8_t { TV_CTA = 0, TV_CLUSTER16 = 1, TV_CLUSTER32 = 2, TV_COUNT = 3 };
+enum TuneVariant : uint8_t { TV_CTA = 0, TV_CLUSTER16 = 1, TV_CLUSTER32 = 2, TV_CLUSTER4_16 = 3, TV_COUNT = 4 };
 struct Tune {
   bool on = false;
   uint8_t v[TUNE_KERNELS][TUNE_BUCKETS] = {};

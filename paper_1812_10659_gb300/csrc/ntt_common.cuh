@@ -83,38 +83,41 @@ static inline int post_launch(Ctx* c, cudaStream_t) {
   return LOLA_OK;
 }
 
-// ------------------------------------------- n = 16384: 2-CTA cluster versions
-// Each limb transform is split over a cluster of two CTAs (half the limb each,
-// 64 KiB of shared memory), so a launch with few limbs still keeps twice as
-// many SMs busy and each dependent step of a rotation takes half as long.
-// Two geometries: 2^5 words per thread (256 threads per CTA, up to 128
-// registers) for launches of many limbs, where per-thread ILP and three
-// passes win; 2^4 words (512 threads, 64 registers, four passes) for small
-// launches, where more threads per transform shorten its latency.
+// ------------------------------------------- n = 16384: cluster versions
+// Each limb transform is split over a cluster of 2 or 4 CTAs (1/C of the
+// limb each in shared memory), so a launch with few limbs still keeps more
+// SMs busy and each dependent step of a rotation takes less time.
+// Geometries: 2 CTAs with 2^5 words per thread (256 threads per CTA, up to
+// 128 registers) for launches of many limbs, where per-thread ILP and three
+// passes win; 2 CTAs with 2^4 words (512 threads, 64 registers, four passes)
+// for small launches, where more threads per transform shorten its latency;
+// 4 CTAs with 2^4 words (256 threads and 32 KiB per CTA) for the smallest
+// launches (single-request evaluation), where a transform's latency is the
+// step's.
 constexpr int CL_LOGN = 14, CL_LOGC = 1;
-template <int LOGE>
-constexpr int cl_threads() { return (1 << CL_LOGN) >> (LOGE + CL_LOGC); }
+template <int LOGE, int LOGC = CL_LOGC>
+constexpr int cl_threads() { return (1 << CL_LOGN) >> (LOGE + LOGC); }
 // launches with fewer limb transforms than this use the 2^4 geometry
 #ifndef LOLA_CL_SMALL_UNITS
 #define LOLA_CL_SMALL_UNITS 400
 #endif
 
-#define LOLA_LAUNCH_CLUSTER(KERNEL, units, threads, stream, ...)                                    \
+#define LOLA_LAUNCH_CLUSTER(KERNEL, LOGC, units, threads, stream, ...)                              \
   do {                                                                                             \
-    const size_t smem = sizeof(uint64_t) << (CL_LOGN - CL_LOGC);                                    \
+    const size_t smem = sizeof(uint64_t) << (CL_LOGN - (LOGC));                                     \
     static bool attr_done = false;                                                                 \
     if (!attr_done) {                                                                              \
       cudaFuncSetAttribute(KERNEL, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);        \
       attr_done = true;                                                                            \
     }                                                                                              \
-    KERNEL<<<(unsigned)((units) << CL_LOGC), threads, smem, stream>>>(__VA_ARGS__);                 \
+    KERNEL<<<(unsigned)((units) << (LOGC)), threads, smem, stream>>>(__VA_ARGS__);                  \
   } while (0)
 
 namespace k {
-// 2-CTA cluster launches (ntt_cluster.cu); `small` selects 2^4 words per thread
-int ks_decompose_cluster(Ctx* c, const KsDev& a, cudaStream_t s, bool small);
-int ks_modup_cluster(Ctx* c, const KsDev& a, bool skip_diag, cudaStream_t s, bool small);
-int ks_intt_p_cluster(Ctx* c, const KsDev& a, cudaStream_t s, bool small);
-int ks_moddown_cluster(Ctx* c, const KsDev& a, cudaStream_t s, bool small);
+// cluster launches (ntt_cluster.cu); `variant` is a TuneVariant other than TV_CTA
+int ks_decompose_cluster(Ctx* c, const KsDev& a, cudaStream_t s, int variant);
+int ks_modup_cluster(Ctx* c, const KsDev& a, bool skip_diag, cudaStream_t s, int variant);
+int ks_intt_p_cluster(Ctx* c, const KsDev& a, cudaStream_t s, int variant);
+int ks_moddown_cluster(Ctx* c, const KsDev& a, cudaStream_t s, int variant);
 }  // namespace k
 }  // namespace lola

@@ -210,7 +210,7 @@ int ks_decompose(Ctx* c, const KsDev& a, cudaStream_t s) {
   const size_t units = a.count * c->L;
   ProfScope ps(c, KI_KS_DECOMPOSE, s, units);
   const int g = geometry(c, 0, units);
-  if (g != TV_CTA) return ks_decompose_cluster(c, a, s, g == TV_CLUSTER16);
+  if (g != TV_CTA) return ks_decompose_cluster(c, a, s, g);
   LOLA_DISPATCH(c->logn, kn_ks_decompose, units, s, c->dev, a);
   return post_launch(c, s);
 }
@@ -222,7 +222,7 @@ int ks_modup(Ctx* c, const KsDev& a, bool skip_diag, cudaStream_t s) {
   const size_t units = a.count * per;
   ProfScope ps(c, KI_KS_MODUP, s, units);
   const int g = geometry(c, 1, units);
-  if (g != TV_CTA) return ks_modup_cluster(c, a, skip_diag, s, g == TV_CLUSTER16);
+  if (g != TV_CTA) return ks_modup_cluster(c, a, skip_diag, s, g);
   LOLA_DISPATCH_CFG(CfgM, c->logn, kn_ks_modup, units, s, c->dev, a, (int)skip_diag);
   return post_launch(c, s);
 }
@@ -231,7 +231,7 @@ int ks_intt_p(Ctx* c, const KsDev& a, cudaStream_t s) {
   const size_t units = a.count * 2;
   ProfScope ps(c, KI_KS_IP_P, s, units);
   const int g = geometry(c, 2, units);
-  if (g != TV_CTA) return ks_intt_p_cluster(c, a, s, g == TV_CLUSTER16);
+  if (g != TV_CTA) return ks_intt_p_cluster(c, a, s, g);
   LOLA_DISPATCH(c->logn, kn_ks_intt_p, units, s, c->dev, a);
   return post_launch(c, s);
 }
@@ -240,7 +240,7 @@ int ks_moddown(Ctx* c, const KsDev& a, cudaStream_t s) {
   const size_t units = a.count * 2 * c->L;
   ProfScope ps(c, KI_KS_MODDOWN, s, units);
   const int g = geometry(c, 3, units);
-  if (g != TV_CTA) return ks_moddown_cluster(c, a, s, g == TV_CLUSTER16);
+  if (g != TV_CTA) return ks_moddown_cluster(c, a, s, g);
   LOLA_DISPATCH_CFG(CfgM, c->logn, kn_ks_moddown, units, s, c->dev, a);
   return post_launch(c, s);
 }

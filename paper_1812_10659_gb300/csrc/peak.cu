@@ -33,15 +33,56 @@ namespace {
 
 constexpr int kThreads = 256, kCtasPerSm = 8;
 
-template <bool PTX>
-__device__ __forceinline__ uint64_t prod(uint64_t x, uint64_t w, uint64_t wp, uint64_t q, uint64_t nq) {
-  if constexpr (PTX) return shoup_mul_lazy_ptx(x, w, wp, nq);
+// Shoup product for a prime of the form q = 2^60 - c 2^32 + 1 (c < 2^28):
+// lo64(qh q) = ((h1 + (h0 << 28) - lo32(h0 c)) << 32) + h0 needs one 32-bit
+// product instead of three.
+__device__ __forceinline__ uint64_t shoup_mul_lazy_sparse(uint64_t x, uint64_t w, uint64_t wp, uint32_t c) {
+  uint64_t r;
+  asm("{\n\t"
+      ".reg .u32 x0, x1, p0, p1, w0, w1, t, al, ah, bl, bh, h0, h1, l0, l1, s;\n\t"
+      ".reg .u64 a, b, d, lo;\n\t"
+      "mov.b64 {x0, x1}, %1;\n\t"
+      "mov.b64 {w0, w1}, %2;\n\t"
+      "mov.b64 {p0, p1}, %3;\n\t"
+      "mul.hi.u32 t, x0, p0;\n\t"
+      "cvt.u64.u32 d, t;\n\t"
+      "mad.wide.u32 a, x0, p1, d;\n\t"
+      "mov.b64 {al, ah}, a;\n\t"
+      "cvt.u64.u32 d, al;\n\t"
+      "mad.wide.u32 b, x1, p0, d;\n\t"
+      "mov.b64 {bl, bh}, b;\n\t"
+      "cvt.u64.u32 d, bh;\n\t"
+      "mad.wide.u32 d, x1, p1, d;\n\t"
+      "mov.b64 {h0, h1}, d;\n\t"
+      "add.cc.u32 h0, h0, ah;\n\t"
+      "addc.u32 h1, h1, 0;\n\t"
+      "mul.wide.u32 lo, x0, w0;\n\t"
+      "mov.b64 {l0, l1}, lo;\n\t"
+      "mad.lo.u32 l1, x0, w1, l1;\n\t"
+      "mad.lo.u32 l1, x1, w0, l1;\n\t"
+      "mad.lo.u32 l1, h0, %4, l1;\n\t"
+      "shl.b32 s, h0, 28;\n\t"
+      "sub.cc.u32 l0, l0, h0;\n\t"
+      "subc.u32 l1, l1, h1;\n\t"
+      "sub.u32 l1, l1, s;\n\t"
+      "mov.b64 %0, {l0, l1};\n\t"
+      "}"
+      : "=l"(r)
+      : "l"(x), "l"(w), "l"(wp), "r"(c));
+  return r;
+}
+
+// PR 0: compiler 64-bit; 1: 32-bit halves; 2: sparse prime (c = nq's high word use)
+template <int PR>
+__device__ __forceinline__ uint64_t prod(uint64_t x, uint64_t w, uint64_t wp, uint64_t q, uint64_t nq, uint32_t c) {
+  if constexpr (PR == 1) return shoup_mul_lazy_ptx(x, w, wp, nq);
+  else if constexpr (PR == 2) return shoup_mul_lazy_sparse(x, w, wp, c);
   else return x * w - __umul64hi(x, wp) * q;
 }
 
-template <bool PTX>
+template <int PR>
 __global__ void __launch_bounds__(kThreads) kb_fwd_butterfly(const uint64_t* __restrict__ tw, uint64_t q, int iters,
-                                                             uint64_t* __restrict__ sink) {
+                                                             uint64_t* __restrict__ sink, uint32_t c) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   uint64_t x[16], w[8], wp[8];
 #pragma unroll
@@ -62,7 +103,7 @@ __global__ void __launch_bounds__(kThreads) kb_fwd_butterfly(const uint64_t* __r
         const int ti = (k >> (lbit + 1)) & 7;
         uint64_t a = x[k];
         if ((lbit & 1) == 1 && (uint32_t)(a >> 32) > q4hi) a -= q4;   // every other stage
-        const uint64_t t = prod<PTX>(x[k | (1 << lbit)], w[ti], wp[ti], q, nq);
+        const uint64_t t = prod<PR>(x[k | (1 << lbit)], w[ti], wp[ti], q, nq, c);
         x[k] = a + t;
         x[k | (1 << lbit)] = a - t + q2;
       }
@@ -174,7 +215,7 @@ __global__ void __launch_bounds__(kThreads) kb_mma_s8(int iters, uint64_t* __res
 // operations per thread per loop iteration of each kind
 static double ops_per_iter(int kind) {
   switch (kind) {
-    case 0: case 1: case 2: return 32;         // butterflies (4 stages x 8)
+    case 0: case 1: case 2: case 7: return 32; // butterflies (4 stages x 8)
     case 3: case 4: case 5: return 64;         // instructions (8 rounds x 8 chains)
     case 6: return 4.0 * 2 * 16 * 8 * 32 / 32; // int8 operations per thread (4 mma per warp)
     default: return 0;
@@ -182,18 +223,32 @@ static double ops_per_iter(int kind) {
 }
 
 int alu_rate(Ctx* c, int kind, double* per_second, double* ms_out) {
-  if (kind < 0 || kind > 6) return fail(LOLA_E_PARAM, "unknown ALU benchmark kind");
+  if (kind < 0 || kind > 7) return fail(LOLA_E_PARAM, "unknown ALU benchmark kind");
   LOLA_CUDA_TRY(cudaSetDevice(c->device));
   int sms = 0;
   LOLA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
   const int blocks = sms * kCtasPerSm;
-  const int iters = kind <= 2 ? 2048 : (kind <= 5 ? 16384 : 8192);
+  const int iters = (kind <= 2 || kind == 7) ? 2048 : (kind <= 5 ? 16384 : 8192);
   DevBuf sink, tw;
   TRY_OK(sink.alloc((size_t)blocks * kThreads * 8));
   TRY_OK(tw.alloc(16 * 8));
-  // twiddles of the first ciphertext prime: the first 8 (w, w') pairs of its forward table
-  LOLA_CUDA_TRY(cudaMemcpy(tw.p, c->host.tw_fwd + 2 * 8, 16 * 8, cudaMemcpyDeviceToDevice));
-  const uint64_t q = c->primes[0];
+  // twiddles of the first ciphertext prime: the first 8 (w, w') pairs of its
+  // forward table; kind 7 uses the prime 2^60 - 96 2^32 + 1 and twiddles 3^k
+  // below it, whatever the context's primes
+  const uint32_t sparse_c = 96;
+  uint64_t q = c->primes[0];
+  if (kind == 7) {
+    q = (1ull << 60) - ((uint64_t)sparse_c << 32) + 1;
+    uint64_t h[16], w = 1;
+    for (int k = 0; k < 8; ++k) {
+      w = mulmod_h(w, 3, q);
+      h[2 * k] = w;
+      h[2 * k + 1] = shoup_h(w, q);
+    }
+    LOLA_CUDA_TRY(cudaMemcpy(tw.p, h, 16 * 8, cudaMemcpyHostToDevice));
+  } else {
+    LOLA_CUDA_TRY(cudaMemcpy(tw.p, c->host.tw_fwd + 2 * 8, 16 * 8, cudaMemcpyDeviceToDevice));
+  }
   cudaEvent_t e0, e1;
   LOLA_CUDA_TRY(cudaEventCreate(&e0));
   LOLA_CUDA_TRY(cudaEventCreate(&e1));
@@ -201,9 +256,10 @@ int alu_rate(Ctx* c, int kind, double* per_second, double* ms_out) {
   for (int rep = 0; rep < 4; ++rep) {
     cudaEventRecord(e0, nullptr);
     switch (kind) {
-      case 0: kb_fwd_butterfly<true><<<blocks, kThreads>>>(tw.u64(), q, iters, sink.u64()); break;
+      case 0: kb_fwd_butterfly<1><<<blocks, kThreads>>>(tw.u64(), q, iters, sink.u64(), 0); break;
       case 1: kb_inv_butterfly<<<blocks, kThreads>>>(tw.u64(), q, iters, sink.u64()); break;
-      case 2: kb_fwd_butterfly<false><<<blocks, kThreads>>>(tw.u64(), q, iters, sink.u64()); break;
+      case 2: kb_fwd_butterfly<0><<<blocks, kThreads>>>(tw.u64(), q, iters, sink.u64(), 0); break;
+      case 7: kb_fwd_butterfly<2><<<blocks, kThreads>>>(tw.u64(), q, iters, sink.u64(), sparse_c); break;
       case 3: kb_imad<0><<<blocks, kThreads>>>(0x9E3779B9u, iters, sink.u64()); break;
       case 4: kb_imad<1><<<blocks, kThreads>>>(0x9E3779B9u, iters, sink.u64()); break;
       case 5: kb_imad<2><<<blocks, kThreads>>>(0x9E3779B9u, iters, sink.u64()); break;

@@ -338,7 +338,7 @@ def lola_rotate_noalloc(ctx, keys, inp, out, count, step, stream=None):
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
-TUNE_KERNELS, TUNE_BUCKETS = 4, 6
+TUNE_KERNELS, TUNE_BUCKETS, TUNE_VARIANTS = 4, 6, 4
 TUNE_NAMES = ("ks_decompose", "ks_modup", "ks_intt_p", "ks_moddown")
 TUNE_GEOMETRY = ("cta", "cluster16", "cluster32")
 
@@ -353,10 +353,11 @@ def lola_autotune(ctx, stream=None) -> dict:
 def lola_tune_get(ctx) -> dict:
     """{"table": [[geometry per bucket] per kernel], "us": [[[us per geometry]]]}"""
     t = (C.c_uint8 * (TUNE_KERNELS * TUNE_BUCKETS))()
-    us = (C.c_float * (TUNE_KERNELS * TUNE_BUCKETS * 3))()
+    us = (C.c_float * (TUNE_KERNELS * TUNE_BUCKETS * TUNE_VARIANTS))()
     _check(load().lola_tune_get(ctx, t, us))
     tab = [[int(t[k * TUNE_BUCKETS + b]) for b in range(TUNE_BUCKETS)] for k in range(TUNE_KERNELS)]
-    tim = [[[round(float(us[(k * TUNE_BUCKETS + b) * 3 + v]), 2) for v in range(3)] for b in range(TUNE_BUCKETS)]
+    tim = [[[round(float(us[(k * TUNE_BUCKETS + b) * TUNE_VARIANTS + v]), 2) for v in range(TUNE_VARIANTS)]
+            for b in range(TUNE_BUCKETS)]
            for k in range(TUNE_KERNELS)]
     return {"table": tab, "us": tim}
 
@@ -530,7 +531,7 @@ def lola_profile_read(ctx, kind):
 
 
 ALU_KINDS = {"fwd_butterfly": 0, "inv_butterfly": 1, "fwd_butterfly_c": 2, "mad_lo_u32": 3,
-             "mad_wide_u32": 4, "mul_hi_u32": 5, "mma_s8": 6}
+             "mad_wide_u32": 4, "mul_hi_u32": 5, "mma_s8": 6, "fwd_butterfly_sparse": 7}
 
 
 def lola_alu_rate(ctx, kind) -> tuple:

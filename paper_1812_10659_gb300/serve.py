@@ -120,10 +120,11 @@ class Server:
     def pending(self) -> int:
         return sum(len(q) for q in self.queues.values()) + sum(1 for s in self.slots if s.busy)
 
-    def step(self) -> bool:
-        """Retire finished batches and admit new ones; True if anything changed."""
+    def _retire(self, wait: bool = False) -> bool:
         changed = False
         for s in self.slots:
+            if s.busy and wait:
+                s.busy.event.synchronize()
             if s.busy and s.busy.event.query():
                 now = time.perf_counter()
                 for r in s.busy.reqs:
@@ -131,6 +132,16 @@ class Server:
                     self.done.append(r)
                 s.busy = None
                 changed = True
+        return changed
+
+    def settle(self):
+        """Wait for the batches already running and retire them; queued
+        requests stay queued (e.g. to stop a saturated run)."""
+        self._retire(wait=True)
+
+    def step(self) -> bool:
+        """Retire finished batches and admit new ones; True if anything changed."""
+        changed = self._retire()
         for s in self.slots:
             if s.busy:
                 continue

@@ -114,3 +114,15 @@ def test_op_counts_by_level_match_the_plan(workload):
     assert ev.c == bench.OP_COUNTS_LEVELS.get(workload, {3: bench.OP_COUNTS[workload]})
     for op in ("rot", "square", "mul_plain", "mul_scalar", "add"):
         assert sum(c[op] for c in ev.c.values()) == bench.OP_COUNTS[workload][op]
+
+
+def test_oracle_end_to_end_inference_dense64():
+    """The CPU baseline's end-to-end oracle inference (spawned worker per
+    residue) runs the single dense layer + square, decrypts to the integer
+    network mod t and counts the plan's operations."""
+    r = bench.oracle_e2e_inference("dense64", 3, None)
+    assert r["ok"] and r["residues"] == 1 and r["eval_s"] > 0
+    assert r["ops_per_residue"]["rot"] == bench.OP_COUNTS["dense64"]["rot"]
+    assert r["ops_per_residue"]["square"] == 1
+    obj = bench.cpu_baseline_obj("dense64", 3, None)
+    assert obj["kind"] == "oracle end-to-end" and obj["cores"] == 1 and obj["value"] > 0

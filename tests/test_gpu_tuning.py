@@ -40,13 +40,14 @@ def test_every_geometry_and_the_autotuned_table_give_the_same_words():
         slots = np.random.default_rng(61).integers(0, 1 << 16, (len(steps), n))
         src = Lb.lola_encrypt(ctx, sk, slots, 62)
         base = run_ops(Lb, ctx, ev, src, ps, steps)            # library defaults
-        for g in range(3):
+        for g in range(Lb.TUNE_VARIANTS):                     # incl. the 4-CTA clusters
             Lb.lola_tune_set(ctx, [[g] * 6 for _ in range(4)])
             got = run_ops(Lb, ctx, ev, src, ps, steps)
             assert np.array_equal(got[0], base[0]) and np.array_equal(got[1], base[1]), g
         Lb.lola_tune_set(ctx, None)
         res = Lb.lola_autotune(ctx)
-        assert len(res["table"]) == 4 and all(len(r) == 6 and all(v in (0, 1, 2) for v in r) for r in res["table"])
+        assert len(res["table"]) == 4 and all(len(r) == 6 and all(v in range(Lb.TUNE_VARIANTS) for v in r)
+                                         for r in res["table"])
         assert sum(1 for k in range(4) for b in range(6) if all(x > 0 for x in res["us"][k][b])) >= 10
         got = run_ops(Lb, ctx, ev, src, ps, steps)
         assert np.array_equal(got[0], base[0]) and np.array_equal(got[1], base[1])
@@ -75,6 +76,8 @@ def test_tune_table_checks():
             Lb.lola_tune_set(ctx, [[1] * 6 for _ in range(4)])  # clusters exist at n = 16384 only
         with pytest.raises(Lb.LolaError):
             Lb.lola_tune_set(ctx, [[3] * 6 for _ in range(4)])
+        with pytest.raises(Lb.LolaError):
+            Lb.lola_tune_set(ctx, [[Lb.TUNE_VARIANTS] * 6 for _ in range(4)])   # no such geometry
         res = Lb.lola_autotune(ctx)                            # one geometry: all entries 0
         assert res["table"] == [[0] * 6 for _ in range(4)]
         Lb.lola_tune_set(ctx, None)
