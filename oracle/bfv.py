@@ -18,12 +18,17 @@ row/column rotations) but not SEAL's internals.  The readings used here:
   [-(t-1)/2, (t-1)/2] before reduction mod q_j.
 * ct (x) ct: centered lifts of both ciphertexts to Z, the negacyclic tensor
   product over Z, then [round(t d_k / Q)]_Q for each of the three parts.
-* Key switching of a polynomial d from s' to s: digits d_i = [d]_{q_i} in
-  [0, q_i) (one per ciphertext prime); key row i is
-  b_i = -a_i s + e_i + (i == j) [P]_{q_i} s'  (mod q_j), b_i = -a_i s + e_i
-  (mod P); u = sum_i d_i (b_i, a_i) over Q*P; result (x - x~) P^-1 mod Q
-  with x~ the centered residue of x mod P.  With K = 0 there is no P and no
-  division.
+* Key switching of a polynomial d from s' to s: the ciphertext primes are
+  grouped alpha at a time, G_g = {q_(g alpha), ..., q_(g alpha + alpha - 1)}
+  (the last group may be shorter), Q_g their product; digit g is the
+  integer polynomial d_g = [d]_(Q_g) with coefficients in [0, Q_g) (the CRT
+  lift of d's residues on G_g; alpha = 1: d_i = [d]_(q_i)).  Key row g is
+  b_g = -a_g s + e_g + [q_j in G_g] [P]_(q_j) s'  (mod q_j),
+  b_g = -a_g s + e_g (mod each special prime); u = sum_g d_g (b_g, a_g) over
+  Q*P, P the product of the K special primes; result (x - x~) P^-1 mod Q
+  with x~ the centered residue of x mod P.  Since d_g = d mod every prime of
+  G_g, the key terms sum to P d s' mod Q.  With K = 0 there is no P and no
+  division (alpha = 1 then).
 * Rotation by k (0 < k < n/2) is the Galois automorphism x -> x^g with
   g = 3^(n/2 - k) mod 2n followed by a key switch from tau_g(s) to s; it
   shifts each row of the 2 x n/2 slot matrix right by k (Sec. 3.1).  The row
@@ -56,11 +61,13 @@ class Params:
     L: int
     K: int
     t: list            # plaintext CRT moduli
+    alpha: int = 1     # ciphertext primes per key-switching digit
 
     def __post_init__(self):
         self.q = [int(x) for x in self.q]
         self.t = [int(x) for x in self.t]
-        assert len(self.q) == self.L + self.K and self.K in (0, 1)
+        assert len(self.q) == self.L + self.K and self.K in (0, 1, 2)
+        assert self.alpha >= 1 and (self.K > 0 or self.alpha == 1)
 
     @property
     def Q(self) -> int:
@@ -68,7 +75,14 @@ class Params:
 
     @property
     def P(self) -> int:
-        return self.q[self.L] if self.K else 1
+        """Product of the special primes (1 when K = 0)."""
+        return prod(self.q[self.L:self.L + self.K])
+
+    @property
+    def groups(self) -> list:
+        """Digit groups: indices of the ciphertext primes of each digit."""
+        a = self.alpha
+        return [list(range(g, min(g + a, self.L))) for g in range(0, self.L, a)]
 
     @property
     def qbasis(self) -> Basis:
@@ -132,7 +146,7 @@ class PublicKey:
 
 @dataclass
 class KeySwitchKey:
-    b: np.ndarray              # (L digits, L+K primes, n)
+    b: np.ndarray              # (digits, L+K primes, n)
     a: np.ndarray
 
 
@@ -162,23 +176,25 @@ def gen_public(params: Params, sk: SecretKey, seed: int) -> PublicKey:
 def gen_switch_key(params: Params, sk: SecretKey, s_from: np.ndarray, key_id: int, seed: int) -> KeySwitchKey:
     """Key that switches a polynomial multiplying s_from (given mod every prime
     of Q*P, shape (L+K, n)) to one multiplying s.  key_id selects the stream
-    (0 = relinearisation, else the Galois element)."""
+    (0 = relinearisation, else the Galois element).  Row g (digit group G_g)
+    carries [P]_(q_j) s_from on the primes of G_g."""
     n, L, K = params.n, params.L, params.K
     primes = params.q
     s = _reduce_int_poly(sk.s, primes)
     P = params.P
-    b = np.zeros((L, L + K, n), dtype=np.uint64)
-    a = np.zeros((L, L + K, n), dtype=np.uint64)
-    for i in range(L):
-        e = sampling.sample_gaussian(seed, TAG_KSK_E, key_id, i, n)
+    G = params.groups
+    b = np.zeros((len(G), L + K, n), dtype=np.uint64)
+    a = np.zeros((len(G), L + K, n), dtype=np.uint64)
+    for g, grp in enumerate(G):
+        e = sampling.sample_gaussian(seed, TAG_KSK_E, key_id, g, n)
         for j, pj in enumerate(primes):
-            aij = sampling.sample_uniform(seed, TAG_KSK_A, key_id, i * 256 + j, pj, n)
-            v = ring.vec_neg(ring.poly_mul(aij, s[j], pj), pj)
+            agj = sampling.sample_uniform(seed, TAG_KSK_A, key_id, g * 256 + j, pj, n)
+            v = ring.vec_neg(ring.poly_mul(agj, s[j], pj), pj)
             v = ring.vec_add(v, ring.reduce_signed(e, pj), pj)
-            if i == j:
+            if j in grp:
                 v = ring.vec_add(v, ring.vec_scalar_mul(s_from[j], P % pj, pj), pj)
-            b[i, j] = v
-            a[i, j] = aij
+            b[g, j] = v
+            a[g, j] = agj
     return KeySwitchKey(b, a)
 
 
@@ -289,41 +305,55 @@ def mul_scalar(params: Params, ct: Ciphertext, w: int) -> Ciphertext:
                        for x in ct.c], ct.t)
 
 
-def key_switch(params: Params, d: np.ndarray, ksk: KeySwitchKey):
-    """Switch d (shape (L, n), mod Q) from s' to s; returns (u0, u1) mod Q.
-    Digits: [d]_{q_i} in [0, q_i), lifted unchanged to every other prime."""
-    return key_switch_digits(params, [d[i].astype(np.int64) for i in range(params.L)], ksk)
+def raise_digits(params: Params, d: np.ndarray) -> list:
+    """The digits of d (shape (L, n), mod Q) raised to Q*P: entry g is the
+    (L+K, n) array of the integer digit d_g = [d]_(Q_g) in [0, Q_g) reduced
+    mod every prime (for a single-prime group, d_i itself on its prime)."""
+    out = []
+    for grp in params.groups:
+        if len(grp) == 1:
+            vals = d[grp[0]].astype(np.int64)
+            out.append(np.stack([np.mod(vals, np.int64(p)).astype(np.uint64) for p in params.q]))
+        else:
+            ints = Basis([params.q[i] for i in grp]).lift(d[grp])      # [0, Q_g)
+            out.append(np.stack([np.array([v % p for v in ints], dtype=np.uint64) for p in params.q]))
+    return out
 
 
-def key_switch_digits(params: Params, digits, ksk: KeySwitchKey):
-    """The key-switch inner product sum_i digit_i * ksk_i over Q * P and the
-    ModDown, for digits given as integer polynomials (digit i must be
-    congruent mod q_i to the polynomial being switched)."""
-    L, K, primes = params.L, params.K, params.q
+def mod_down(params: Params, x: np.ndarray) -> np.ndarray:
+    """(x - x~) P^-1 mod Q for x given mod every prime of Q*P (shape
+    (L+K, n)), x~ the centered residue of x mod P; identity when K = 0."""
+    L, K = params.L, params.K
+    if K == 0:
+        return x[:L]
+    P = params.P
+    xt = Basis(params.q[L:L + K]).lift_centered(x[L:L + K])
+    res = []
+    for j in range(L):
+        qj = params.q[j]
+        pinv = pow(P, -1, qj)
+        res.append(np.array([((int(x[j][c]) - xt[c]) * pinv) % qj for c in range(params.n)], dtype=np.uint64))
+    return np.stack(res)
+
+
+def key_switch_raised(params: Params, D: list, ksk: KeySwitchKey):
+    """The key-switch inner product sum_g D_g * ksk_g over Q * P and the
+    mod-down, for raised digits D (raise_digits, possibly permuted)."""
     u = []
     for comp in (ksk.b, ksk.a):
         acc = []
-        for j, pj in enumerate(primes):
+        for j, pj in enumerate(params.q):
             s = np.zeros(params.n, dtype=np.uint64)
-            for i in range(L):
-                di = np.mod(digits[i], np.int64(pj)).astype(np.uint64)   # digit i lifted to Z, mod p_j
-                s = ring.vec_add(s, ring.poly_mul(di, comp[i, j], pj), pj)
+            for g in range(len(D)):
+                s = ring.vec_add(s, ring.poly_mul(D[g][j], comp[g, j], pj), pj)
             acc.append(s)
-        u.append(np.stack(acc))
-    if K == 0:
-        return u[0], u[1]
-    P = params.P
-    out = []
-    for x in u:
-        xt = [centered(int(v), P) for v in x[L]]
-        res = []
-        for j in range(L):
-            qj = primes[j]
-            pinv = pow(P, -1, qj)
-            res.append(np.array([((int(x[j][c]) - xt[c]) * pinv) % qj for c in range(params.n)],
-                                dtype=np.uint64))
-        out.append(np.stack(res))
-    return out[0], out[1]
+        u.append(mod_down(params, np.stack(acc)))
+    return u[0], u[1]
+
+
+def key_switch(params: Params, d: np.ndarray, ksk: KeySwitchKey):
+    """Switch d (shape (L, n), mod Q) from s' to s; returns (u0, u1) mod Q."""
+    return key_switch_raised(params, raise_digits(params, d), ksk)
 
 
 def apply_galois(params: Params, ct: Ciphertext, g: int, ksk: KeySwitchKey) -> Ciphertext:
@@ -341,20 +371,23 @@ def rotate(params: Params, keys: Keys, ct: Ciphertext, k: int) -> Ciphertext:
 
 def rotate_hoisted(params: Params, keys: Keys, ct: Ciphertext, steps) -> list:
     """Rotations of one ciphertext by several steps sharing one digit
-    decomposition (hoisting; step 0 = row swap).  The digits of c1 are
-    d_i = [c1]_{q_i} as integer polynomials with coefficients in [0, q_i),
-    computed once; rotation g switches tau_g(c1) with the digits tau_g(d_i)
-    taken over Z (coefficients in (-q_i, q_i)), which are congruent to
-    tau_g(c1) mod q_i, then adds tau_g(c0).  At g = 1 the digits are those of
-    key_switch; for other g the result differs from apply_galois by a
-    different (equally valid) key-switching noise."""
+    decomposition (hoisting; step 0 = row swap).  The digits of c1 are raised
+    to Q*P once (raise_digits: the integer digits d_g in [0, Q_g)); rotation
+    g switches tau_g(c1) with the digits tau_g(d_g) taken over Z
+    (coefficients in (-Q_g, Q_g)), which are congruent to tau_g(c1) mod the
+    primes of G_g, then adds tau_g(c0).  tau_g of an integer polynomial
+    reduced mod p is tau_g of its residues mod p, so the raised digits are
+    permuted prime by prime.  At g = 1 the digits are those of key_switch;
+    for other g the result differs from apply_galois by a different (equally
+    valid) key-switching noise."""
     qs = params.q[:params.L]
-    d = [ct.c[1][i].astype(np.int64) for i in range(params.L)]
+    D = raise_digits(params, ct.c[1])
     out = []
     for k in steps:
         g = galois_row_swap(params.n) if k == 0 else galois_for_rotation(params.n, k)
         c0 = _auto_rns(ct.c[0], g, qs)
-        u0, u1 = key_switch_digits(params, [ring.automorphism_int(di, g) for di in d], keys.galois[g])
+        Dg = [np.stack([ring.automorphism(Dd[j], g, p) for j, p in enumerate(params.q)]) for Dd in D]
+        u0, u1 = key_switch_raised(params, Dg, keys.galois[g])
         out.append(Ciphertext([_add_rns(c0, u0, qs), u1], ct.t))
     return out
 
@@ -368,22 +401,25 @@ def rotate_rows(params: Params, keys: Keys, ct: Ciphertext) -> Ciphertext:
 
 def params_at_level(params: Params, Lv: int) -> Params:
     """Parameters of a ciphertext that keeps the first Lv primes of Q (after
-    modulus switching); the special prime and the plaintext moduli stay."""
+    modulus switching); the special primes, the digit size and the plaintext
+    moduli stay (the digit groups are those of the first Lv primes)."""
     assert 1 <= Lv <= params.L
-    return Params(params.n, params.q[:Lv] + params.q[params.L:], Lv, params.K, params.t)
+    return Params(params.n, params.q[:Lv] + params.q[params.L:], Lv, params.K, params.t, params.alpha)
 
 
 def keys_at_level(keys: Keys, Lv: int) -> Keys:
     """The key set restricted to level Lv: public key on q_0..q_{Lv-1};
-    switching keys on digits i < Lv and primes q_0..q_{Lv-1} plus the special
-    prime.  Every kept entry is unchanged, and it is what gen_switch_key
-    defines for those digits and primes (b_i = -a_i s + e_i + [P]_{q_i} s' on
-    prime i), so the restriction is a key set of params_at_level."""
+    switching keys on the digit groups that meet q_0..q_{Lv-1} and on those
+    primes plus the special primes.  Every kept entry is unchanged, and it is
+    what gen_switch_key defines for the level's groups (a group cut short by
+    the level keeps [P]_(q_j) s' exactly on its remaining primes), so the
+    restriction is a key set of params_at_level."""
     full = keys.params
     sel = list(range(Lv)) + list(range(full.L, full.L + full.K))
+    nd = len(params_at_level(full, Lv).groups)
 
     def cut(k):
-        return None if k is None else KeySwitchKey(k.b[:Lv][:, sel], k.a[:Lv][:, sel])
+        return None if k is None else KeySwitchKey(k.b[:nd][:, sel], k.a[:nd][:, sel])
 
     return Keys(params_at_level(full, Lv), keys.sk, PublicKey(keys.pk.p0[:Lv], keys.pk.p1[:Lv]),
                 cut(keys.relin), {g: cut(k) for g, k in keys.galois.items()})

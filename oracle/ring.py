@@ -152,21 +152,17 @@ def automorphism_int(a: np.ndarray, g: int) -> np.ndarray:
 def automorphism(a: np.ndarray, g: int, q: int) -> np.ndarray:
     """tau_g: a(x) -> a(x^g) in Z_q[x]/(x^n+1), g odd.
 
-    x^(i*g) = x^((i*g) mod 2n), and x^(n+r) = -x^r.
+    x^(i*g) = x^((i*g) mod 2n), and x^(n+r) = -x^r: coefficient i moves to
+    (i g mod 2n) mod n, negated mod q when i g mod 2n >= n.
     """
+    a = np.asarray(a, dtype=np.uint64)
     n = a.shape[-1]
+    e = (np.arange(n, dtype=np.int64) * int(g)) % (2 * n)
+    neg = np.where(a == 0, np.uint64(0), np.uint64(q) - a)
     out = np.zeros(n, dtype=np.uint64)
-    for i in range(n):
-        e = (i * g) % (2 * n)
-        v = int(a[i])
-        if e >= n:
-            out[e - n] = (q - v) % q
-        else:
-            out[e] = v
+    out[e % n] = np.where(e >= n, neg, a)
     return out
 
-
-# ---------------------------------------------------------------- CRT / RNS
 
 class Basis:
     """An RNS basis: CRT constants for lifting residues to Z."""

@@ -454,3 +454,119 @@ def test_fresh_encryption_margin_is_the_public_key_error_term():
     eu = schoolbook_negacyclic([int(x) for x in epk], [int(x) for x in u])
     err = [int(a) + b - c for a, b, c in zip(e1, e2s, eu)]
     assert bfv.noise_margin_bits(P, keys.sk, ct, m) == pytest.approx(closed_form_margin(P, t, m, err), abs=1e-9)
+
+
+# ------------------------------------- key switching with grouped digits
+#
+# Digits of alpha primes each and K = 2 special primes (P = P1 P2 > every
+# digit's modulus Q_g): the textbook CRT identity for the digits, exact
+# mod-down by a two-prime P, the key-switch result u0 + u1 s = d s' + e with
+# a small e, and the negative control that one special prime below the
+# digit modulus leaves e of the size of Q_g / P.
+
+def gparams(n=32, L=5, K=2, alpha=2, t=65537):
+    ps = W.params_small(n, L=L, K=K, t=[t])
+    return bfv.Params(ps.n, ps.q, ps.L, ps.K, ps.t, alpha)
+
+
+def test_digit_groups_and_crt_identity():
+    P = gparams()
+    assert P.groups == [[0, 1], [2, 3], [4]] and P.P == P.q[5] * P.q[6]
+    g = np.random.default_rng(31)
+    d = np.stack([g.integers(0, q, P.n, dtype=np.uint64) for q in P.q[:P.L]])
+    D = bfv.raise_digits(P, d)
+    Q = P.Q
+    # d_g in [0, Q_g), congruent to d on its group's primes (own CRT by hand)
+    recon = [0] * P.n
+    for grp, Dg in zip(P.groups, D):
+        Qg = 1
+        for i in grp:
+            Qg *= P.q[i]
+        Mg = Q // Qg
+        inv = pow(Mg % Qg, -1, Qg)
+        for c in range(P.n):
+            # recover d_g from its residues on two primes outside the group
+            # is not possible; instead rebuild it from the group's residues
+            x = 0
+            for i in grp:
+                hi = Qg // P.q[i]
+                x += int(d[i][c]) * hi * pow(hi % P.q[i], -1, P.q[i])
+            x %= Qg
+            for j, p in enumerate(P.q):
+                assert int(Dg[j][c]) == x % p
+            recon[c] += x * Mg * inv
+    for c in range(P.n):
+        for j in range(P.L):
+            assert recon[c] % P.q[j] == int(d[j][c])
+
+
+def test_mod_down_two_special_primes_is_exact_rounded_division():
+    P = gparams(n=16)
+    QP, Pm = P.Q * P.P, P.P
+    g = np.random.default_rng(32)
+    xs = [int(g.integers(0, 2**62)) * int(g.integers(0, 2**62)) * int(g.integers(0, 2**62)) ** 5 % QP
+          for _ in range(P.n)]
+    xs[0], xs[1] = (Pm - 1) // 2, (Pm + 1) // 2          # either side of the centering boundary
+    res = np.array([[x % p for x in xs] for p in P.q], dtype=np.uint64)
+    out = bfv.mod_down(P, res)
+    for c, x in enumerate(xs):
+        xt = x % Pm
+        xt = xt - Pm if xt > Pm // 2 else xt
+        y = (x - xt) // Pm
+        assert (x - xt) % Pm == 0 and abs(Fraction(x, Pm) - y) <= Fraction(1, 2)
+        for j in range(P.L):
+            assert int(out[j][c]) == y % P.q[j]
+
+
+def switch_error_bits(P, seed=33):
+    """log2 of max |u0 + u1 s - d s'| (centered mod Q) for a random d and a
+    relinearisation key (s' = s^2)."""
+    keys = bfv.keygen(P, seed, relin=True)
+    g = np.random.default_rng(seed)
+    d = np.stack([g.integers(0, q, P.n, dtype=np.uint64) for q in P.q[:P.L]])
+    u0, u1 = bfv.key_switch(P, d, keys.relin)
+    qs = P.q[:P.L]
+    s = bfv._reduce_int_poly(keys.sk.s, qs)
+    s2 = np.stack([ring.poly_mul(s[j], s[j], q) for j, q in enumerate(qs)])
+    err = []
+    for j, q in enumerate(qs):
+        lhs = ring.vec_add(u0[j], ring.poly_mul(u1[j], s[j], q), q)
+        err.append(ring.vec_sub(lhs, ring.poly_mul(d[j], s2[j], q), q))
+    e = P.qbasis.lift_centered(np.stack(err))
+    return math.log2(max(abs(v) for v in e) + 1)
+
+
+@pytest.mark.parametrize("alpha,K", [(1, 1), (2, 2), (1, 2)])
+def test_grouped_key_switch_error_is_small(alpha, K):
+    # error ~ sum_g d_g e_g / P + rounding: below 2^20 at n = 32 whenever P > Q_g
+    P = gparams(alpha=alpha, K=K)
+    assert switch_error_bits(P) < 20
+
+
+@pytest.mark.parametrize("alpha,K", [(2, 1), (3, 2)])
+def test_special_primes_below_the_digit_modulus_leave_a_large_error(alpha, K):
+    # P (K primes) < Q_g (alpha primes): the error grows to about Q_g / P = 2^60
+    P = gparams(alpha=alpha, K=K)
+    assert switch_error_bits(P) > 55
+
+
+def test_grouped_digits_rotate_relinearise_hoist_and_switch_levels():
+    P = gparams(n=32, L=5, K=2, alpha=2)
+    keys = bfv.keygen(P, 34, rotations=[1, 5], relin=True, row_swap=True)
+    t = P.t[0]
+    v = np.random.default_rng(34).integers(0, 16, P.n)
+    c = bfv.encrypt(P, keys.pk, encoding.encode(v, t), t, 3, 0)
+    h = P.n // 2
+    for Lv in (5, 4, 3, 2, 1):
+        Pl, kl = bfv.params_at_level(P, Lv), bfv.keys_at_level(keys, Lv)
+        assert Pl.groups == {5: [[0, 1], [2, 3], [4]], 4: [[0, 1], [2, 3]], 3: [[0, 1], [2]],
+                             2: [[0, 1]], 1: [[0]]}[Lv]
+        assert kl.relin.b.shape[0] == len(Pl.groups) == (Lv + 1) // 2
+        cl = bfv.mod_switch_to(P, c, Lv)
+        assert np.array_equal(dec(Pl, kl, bfv.rotate(Pl, kl, cl, 5)), row_shift(v, 5))
+        assert np.array_equal(dec(Pl, kl, bfv.rotate_rows(Pl, kl, cl)), np.concatenate([v[h:], v[:h]]))
+        outs = bfv.rotate_hoisted(Pl, kl, cl, [1, 0])
+        assert np.array_equal(dec(Pl, kl, outs[0]), row_shift(v, 1))
+        assert np.array_equal(dec(Pl, kl, outs[1]), np.concatenate([v[h:], v[:h]]))
+        if Lv >= 2:
+            assert np.array_equal(dec(Pl, kl, bfv.square(Pl, kl, cl)), (v * v) % t)
