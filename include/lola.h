@@ -115,6 +115,24 @@ int lola_keys_export(lola_ctx* ctx, const lola_keys* keys, int what, int32_t ste
  * Errors: LOLA_E_STATE (no public key), LOLA_E_PARAM, LOLA_E_NOMEM. */
 int lola_encrypt(lola_ctx* ctx, const lola_keys* keys, const int64_t* slots, size_t n_msg, uint64_t seed,
                  lola_ct** out);
+/* Seeded symmetric encryption (a library facility; the paper's E is
+ * public-key BFV): the client holds the secret key (Sec. 1: it encrypts and
+ * decrypts), so it can encrypt with it, c1 = a, c0 = Delta m + e - a s, and
+ * draw a from a seed; the server regenerates c1 from the seed
+ * (lola_ct_upload_seeded), so only c0 crosses the wire and the host-device
+ * link.  a on prime q_j: its evaluation at psi_j^(2i+1) (psi_j the smallest
+ * primitive 2n-th root of unity mod q_j) is ((w_{2i+1} << 64) | w_{2i}) mod
+ * q_j over the Philox4x64-10 word stream (seed, 9, id, j); e: Gaussian
+ * stream (seed, 10, id, 0); id = message * k_t + residue.  slots as in
+ * lola_encrypt.  keys must hold the secret key (else LOLA_E_STATE). */
+int lola_encrypt_symmetric(lola_ctx* ctx, const lola_keys* keys, const int64_t* slots, size_t n_msg, uint64_t seed,
+                           lola_ct** out);
+/* Upload the c0 halves of seeded symmetric ciphertexts and regenerate their
+ * c1 on the device: host_c0 [n_msg][k_t][L][n] (NTT form, the c0 limbs of
+ * lola_encrypt_symmetric's output; pinned memory for an asynchronous copy),
+ * ct at the full level, seed and ids as at encryption.  Stream-ordered on
+ * `stream`.  Errors: LOLA_E_PARAM, LOLA_E_CUDA. */
+int lola_ct_upload_seeded(lola_ctx* ctx, lola_ct* ct, const uint64_t* host_c0, uint64_t seed, void* stream);
 /* Decrypt and recombine the k_t residues by CRT (Sec. 4.4) into signed
  * values in (-T/2, T/2], T = prod t_i.  out: host, n_msg x n pairs of int64
  * (low word, high word) of a signed 128-bit integer.
@@ -124,6 +142,8 @@ int lola_decrypt(lola_ctx* ctx, const lola_keys* keys, const lola_ct* ct, int64_
 int lola_decrypt_residues(lola_ctx* ctx, const lola_keys* keys, const lola_ct* ct, uint64_t* out);
 int lola_ct_create(lola_ctx* ctx, size_t n_msg, lola_ct** out); /* all-zero ciphertexts */
 size_t lola_ct_messages(const lola_ct* ct);
+/* Device bytes the handle holds (its capacity at the context's full level). */
+size_t lola_ct_bytes(const lola_ct* ct);
 /* Device pointer to the ciphertext words ([n_msg][k_t][2][L][n], NTT form);
  * valid until lola_ct_destroy. */
 uint64_t* lola_ct_data(lola_ct* ct);

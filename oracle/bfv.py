@@ -51,7 +51,7 @@ import numpy as np
 from . import ring, sampling
 from .ring import Basis
 from .sampling import (TAG_ENC_E1, TAG_ENC_E2, TAG_ENC_U, TAG_KSK_A, TAG_KSK_E,
-                       TAG_PK_A, TAG_PK_E, TAG_SECRET)
+                       TAG_PK_A, TAG_PK_E, TAG_SECRET, TAG_SYM_A, TAG_SYM_E)
 
 
 @dataclass
@@ -242,6 +242,36 @@ def encrypt(params: Params, pk: PublicKey, m: np.ndarray, t: int, seed: int, ct_
     c0 = _add_rns(_add_rns(dm, _mul_rns(pk.p0, u, qs), qs), e1, qs)
     c1 = _add_rns(_mul_rns(pk.p1, u, qs), e2, qs)
     return Ciphertext([c0, c1], t)
+
+
+def seeded_c1(params: Params, seed: int, ct_id: int) -> np.ndarray:
+    """The c1 of a seeded symmetric encryption, shape (L, n), coefficient
+    form: on prime q_j its evaluations a(psi_j^(2i+1)), i = 0..n-1 (psi_j
+    the smallest primitive 2n-th root of unity mod q_j), are the residues
+    uniform_wide(seed, TAG_SYM_A, ct_id, j) -- so a server can regenerate c1
+    in the evaluation domain from (seed, ct_id) alone."""
+    n = params.n
+    out = []
+    for j, q in enumerate(params.q[:params.L]):
+        ev = sampling.uniform_wide(seed, TAG_SYM_A, ct_id, j, q, n)
+        out.append(ring.inverse_transform(ev, q, ring.smallest_primitive_2n_root(q, n)))
+    return np.stack(out)
+
+
+def encrypt_symmetric(params: Params, sk: SecretKey, m: np.ndarray, t: int, seed: int, ct_id: int) -> Ciphertext:
+    """Symmetric (secret-key) encryption with a seeded c1: c1 = a from
+    seeded_c1, c0 = [Delta m + e - a s]_Q with e Gaussian from stream
+    (seed, TAG_SYM_E, ct_id, 0).  Decrypts like encrypt's output (phase
+    Delta m + e).  The client holds s (Sec. 1: it encrypts and decrypts), so
+    it may encrypt this way and send c0 and the seed instead of c1."""
+    n, qs = params.n, params.q[:params.L]
+    a = seeded_c1(params, seed, ct_id)
+    e = _reduce_int_poly(sampling.sample_gaussian(seed, TAG_SYM_E, ct_id, 0, n), qs)
+    s = _reduce_int_poly(sk.s, qs)
+    D = delta(params, t)
+    dm = np.stack([ring.vec_scalar_mul(ring.reduce_signed(m, q), D % q, q) for q in qs])
+    c0 = _sub_rns(_add_rns(dm, e, qs), _mul_rns(a, s, qs), qs)
+    return Ciphertext([c0, a], t)
 
 
 def _phase(params: Params, sk: SecretKey, ct: Ciphertext) -> list:

@@ -42,6 +42,8 @@ TAG_KSK_E = 5
 TAG_ENC_U = 6
 TAG_ENC_E1 = 7
 TAG_ENC_E2 = 8
+TAG_SYM_A = 9      # seeded c1 of symmetric encryption (evaluation values)
+TAG_SYM_E = 10     # error of symmetric encryption
 
 
 class Stream:
@@ -143,6 +145,14 @@ def gaussian(stream: Stream, n: int) -> list:
             k += 1
         out.append(-k if sign else k)
     return out
+
+
+def uniform_wide(seed, tag, a, b, q, n) -> np.ndarray:
+    """n residues mod q, residue i = ((w_{2i+1} << 64) | w_{2i}) mod q over the
+    stream's words (no rejection; the distance from uniform is below
+    q / 2^128)."""
+    w = Stream(seed, tag, a, b).words(2 * n)
+    return np.array([((int(w[2 * i + 1]) << 64) | int(w[2 * i])) % q for i in range(n)], dtype=np.uint64)
 
 
 def sample_uniform(seed, tag, a, b, q, n) -> np.ndarray:

@@ -110,6 +110,7 @@ int lola_ct_create(lola_ctx* ctx, size_t n_msg, lola_ct** out) {
 }
 
 size_t lola_ct_messages(const lola_ct* ct) { return ct ? ct->ct.n_msg : 0; }
+size_t lola_ct_bytes(const lola_ct* ct) { return ct ? ct->ct.buf.bytes : 0; }
 uint64_t* lola_ct_data(lola_ct* ct) { return ct ? ct->ct.buf.u64() : nullptr; }
 
 void lola_ct_destroy(lola_ct* ct) { delete ct; }
@@ -126,6 +127,32 @@ int lola_encrypt(lola_ctx* ctx, const lola_keys* keys, const int64_t* slots, siz
   }
   *out = h;
   return LOLA_OK;
+}
+
+int lola_encrypt_symmetric(lola_ctx* ctx, const lola_keys* keys, const int64_t* slots, size_t n_msg, uint64_t seed,
+                           lola_ct** out) {
+  CHECK(ctx && keys && out && (slots || !n_msg), LOLA_E_PARAM, "null argument");
+  lola_ct* h = nullptr;
+  TRY(new_ct(ctx->c, n_msg, &h));
+  int rc = encrypt_symmetric(ctx->c, keys->k, slots, n_msg, seed, h->ct.buf.u64(), nullptr);
+  if (rc != LOLA_OK) {
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return LOLA_OK;
+}
+
+int lola_ct_upload_seeded(lola_ctx* ctx, lola_ct* ct, const uint64_t* host_c0, uint64_t seed, void* stream) {
+  CHECK(ctx && ct && host_c0, LOLA_E_PARAM, "null argument");
+  Ctx* c = ctx->c;
+  CHECK(ct->ct.L() == c->L, LOLA_E_PARAM, "seeded upload needs a ciphertext at the full level");
+  const size_t count = ct->ct.n_msg * c->kt, limbs = (size_t)c->L * c->n;
+  if (!count) return LOLA_OK;
+  cudaStream_t s = to_stream(stream);
+  LOLA_CUDA_TRY(cudaMemcpy2DAsync(ct->ct.buf.p, 2 * limbs * 8, host_c0, limbs * 8, limbs * 8, count,
+                                  cudaMemcpyHostToDevice, s));
+  return seeded_c1(c, ct->ct.buf.u64(), count, seed, 0, s);
 }
 
 // the context of a handle's level

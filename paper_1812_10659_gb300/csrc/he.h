@@ -38,6 +38,12 @@ int encrypt(Ctx* c, const KeySet* ks, const int64_t* slots, size_t n_msg, uint64
             cudaStream_t s);
 int decrypt_residues(Ctx* c, const KeySet* ks, const uint64_t* d_ct, size_t n_msg, uint64_t* host_slots,
                      cudaStream_t s);
+// Seeded symmetric encryption (seeded.cu): c1 regenerated from (seed, id)
+// in the evaluation domain, c0 = Delta m + e - c1 s.  seeded_c1 writes the
+// c1 limbs of `count` ciphertexts [ct][2][L][n] with ids id0, id0 + 1, ...
+int encrypt_symmetric(Ctx* c, const KeySet* ks, const int64_t* slots, size_t n_msg, uint64_t seed, uint64_t* d_out,
+                      cudaStream_t s);
+int seeded_c1(Ctx* c, uint64_t* d_ct, size_t count, uint64_t seed, uint64_t id0, cudaStream_t s);
 int to_coeff(Ctx* c, const uint64_t* d_ct, uint64_t* d_out, size_t count, cudaStream_t s);
 int from_coeff(Ctx* c, const uint64_t* d_in, uint64_t* d_out, size_t count, cudaStream_t s);
 

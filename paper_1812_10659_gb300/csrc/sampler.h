@@ -18,7 +18,7 @@ namespace lola {
 
 enum StreamTag : uint64_t {
   TAG_SECRET = 1, TAG_PK_A = 2, TAG_PK_E = 3, TAG_KSK_A = 4, TAG_KSK_E = 5,
-  TAG_ENC_U = 6, TAG_ENC_E1 = 7, TAG_ENC_E2 = 8,
+  TAG_ENC_U = 6, TAG_ENC_E1 = 7, TAG_ENC_E2 = 8, TAG_SYM_A = 9, TAG_SYM_E = 10,
 };
 
 class PhiloxStream {

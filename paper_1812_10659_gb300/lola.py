@@ -108,6 +108,9 @@ _SIGS = {
                                     C.POINTER(C.c_uint64)]),
     "lola_profile_kinds": (C.c_int, []),
     "lola_alu_rate": (C.c_int, [P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "lola_encrypt_symmetric": (C.c_int, [P, P, I64P, C.c_size_t, C.c_uint64, C.POINTER(P)]),
+    "lola_ct_upload_seeded": (C.c_int, [P, P, C.c_void_p, C.c_uint64, P]),
+    "lola_ct_bytes": (C.c_size_t, [P]),
     "lola_profile_name": (C.c_char_p, [C.c_int]),
     "lola_launch_count": (C.c_uint64, [P]),
     "lola_last_error": (C.c_char_p, []),
@@ -222,6 +225,26 @@ def lola_encrypt(ctx, keys, slots, seed):
     out = P()
     _check(lib.lola_encrypt(ctx, keys, sp, s.shape[0], seed, C.byref(out)))
     return out
+
+
+def lola_encrypt_symmetric(ctx, keys, slots, seed):
+    """Seeded symmetric encryption with the secret key (c1 regenerable from the seed)."""
+    lib = load()
+    s, sp = _i64(np.atleast_2d(slots))
+    out = P()
+    _check(lib.lola_encrypt_symmetric(ctx, keys, sp, s.shape[0], seed, C.byref(out)))
+    return out
+
+
+def lola_ct_upload_seeded(ctx, ct, host_c0_ptr: int, seed, stream=None):
+    """Copy the c0 halves [n_msg][k_t][L][n] at host address host_c0_ptr into
+    ct and regenerate c1 from the seed on the device (stream-ordered)."""
+    _check(load().lola_ct_upload_seeded(ctx, ct, C.c_void_p(host_c0_ptr), seed, stream_handle(stream)))
+
+
+def lola_ct_bytes(ct) -> int:
+    """Device bytes held by a ciphertext handle."""
+    return int(load().lola_ct_bytes(ct))
 
 
 def lola_ct_messages(ct) -> int:

@@ -13,7 +13,8 @@ at once (e.g. the MNIST-shaped network and the transfer-learning head):
   served: the largest power-of-two batch of its waiting requests that fits
   the batch cap and the free device memory is copied into the slot's input
   buffer, evaluated (CUDA-graph replay) and scattered into per-request
-  output ciphertexts;
+  output ciphertexts, which are taken from a pool (or allocated) only at
+  admission, so a backlog of queued requests holds no device memory;
 * requests that arrive while others run are admitted as soon as a slot and
   memory free up, and their batches overlap on the device with the batches
   already running on other slots.
@@ -86,6 +87,7 @@ class Server:
         self.next_id = 0
         self.done = []
         self.bytes_per_request = {}                  # measured executor footprint per request
+        self.out_bytes = {}                          # device bytes of one output handle
 
     # ---------------------------------------------------------------- API
     def submit(self, kind: str, ct_in, t_arrival: float | None = None) -> int:
@@ -94,13 +96,6 @@ class Server:
         rid = self.next_id
         self.next_id += 1
         r = Request(rid, kind, ct_in, time.perf_counter() if t_arrival is None else t_arrival)
-        if self.free_outputs[kind]:
-            r.ct_out = self.free_outputs[kind].pop()
-        else:
-            # a new handle is zero-filled on the default stream; finish that
-            # before a slot stream writes into it
-            r.ct_out = L.lola_ct_create(self.kctx[kind], self.shape[kind][1])
-            self.torch.cuda.default_stream().synchronize()
         self.requests[rid] = r
         self.queues[kind].append(r)
         return rid
@@ -196,20 +191,46 @@ class Server:
                 best, t = k, q[0].t_arrival
         return best
 
+    def _out_bytes(self, kind: str) -> int:
+        """Device bytes of one request's output handle."""
+        if kind not in self.out_bytes:
+            h = self._output(kind)
+            self.out_bytes[kind] = L.lola_ct_bytes(h)
+            self.free_outputs[kind].append(h)
+        return self.out_bytes[kind]
+
     def _admit_size(self, s: _Slot, kind: str) -> int:
+        """Largest power-of-two batch of waiting requests within the cap whose
+        executor (if not built yet) and new output handles fit the free
+        device memory above the reserve; 0 = wait for memory."""
         n = min(len(self.queues[kind]), self.max_batch[kind])
         B = 1
         while B * 2 <= n:
             B *= 2
+        free = None
         while B >= 1:
-            if (kind, B) in s.bufs:
+            need = max(0, B - len(self.free_outputs[kind])) * self._out_bytes(kind)
+            if (kind, B) not in s.bufs:
+                need += (self.bytes_per_request.get(kind) or 0) * B
+            if need == 0:
                 return B
-            per = self.bytes_per_request.get(kind)
-            free, _ = self.torch.cuda.mem_get_info()
-            if per is None or free - self.memory_reserve >= per * B:
+            if free is None:
+                free, _ = self.torch.cuda.mem_get_info()
+            if free - self.memory_reserve >= need:
                 return B
             B //= 2
         return 0
+
+    def _output(self, kind: str):
+        """An output handle from the pool, or a new one (allocated at
+        admission, so queued requests hold no device memory)."""
+        if self.free_outputs[kind]:
+            return self.free_outputs[kind].pop()
+        h = L.lola_ct_create(self.kctx[kind], self.shape[kind][1])
+        # a new handle is zero-filled on the default stream; finish that
+        # before a slot stream writes into it
+        self.torch.cuda.default_stream().synchronize()
+        return h
 
     def _prepare(self, s: _Slot, kind: str, B: int):
         if (kind, B) in s.bufs:
@@ -238,6 +259,7 @@ class Server:
         for i, r in enumerate(reqs):
             r.t_admit = now
             r.batch = B
+            r.ct_out = self._output(kind)
             L.lola_ct_copy_messages(ctx, ci, i * n_in, r.ct_in, 0, n_in, s.stream)
         L.lola_eval_network(ctx, self.kkeys[kind], s.nets[kind], ci, co, s.stream, graph=self.graph)
         for i, r in enumerate(reqs):

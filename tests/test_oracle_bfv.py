@@ -570,3 +570,37 @@ def test_grouped_digits_rotate_relinearise_hoist_and_switch_levels():
         assert np.array_equal(dec(Pl, kl, outs[1]), np.concatenate([v[h:], v[:h]]))
         if Lv >= 2:
             assert np.array_equal(dec(Pl, kl, bfv.square(Pl, kl, cl)), (v * v) % t)
+
+
+# ------------------------------------------- seeded symmetric encryption
+
+def test_uniform_wide_is_the_128_bit_word_pair_reduced():
+    from oracle import sampling
+    q = W.Q60[0]
+    w = sampling.Stream(5, sampling.TAG_SYM_A, 3, 1).words(16)
+    got = sampling.uniform_wide(5, sampling.TAG_SYM_A, 3, 1, q, 8)
+    for i in range(8):
+        assert int(got[i]) == (int(w[2 * i]) + int(w[2 * i + 1]) * 2**64) % q
+
+
+def test_symmetric_encryption_phase_is_delta_m_plus_the_sampled_error():
+    from oracle import sampling
+    P = mkparams(32)
+    keys = bfv.keygen(P, 3)
+    t = P.t[0]
+    v = np.random.default_rng(41).integers(0, t, P.n)
+    m = encoding.encode(v, t)
+    ct = bfv.encrypt_symmetric(P, keys.sk, m, t, 7, 5)
+    assert np.array_equal(dec(P, keys, ct), v)
+    e = sampling.sample_gaussian(7, sampling.TAG_SYM_E, 5, 0, P.n)
+    assert bfv.noise_margin_bits(P, keys.sk, ct, m) == pytest.approx(closed_form_margin(P, t, m, e), abs=1e-9)
+    # c1's evaluations at psi^(2i+1) are the seeded residues (brute-force evaluation)
+    for j, q in enumerate(P.q[:P.L]):
+        psi = ring.smallest_primitive_2n_root(q, P.n)
+        ev = sampling.uniform_wide(7, sampling.TAG_SYM_A, 5, j, q, P.n)
+        for i in (0, 1, 17, P.n - 1):
+            x = pow(psi, 2 * i + 1, q)
+            assert sum(int(c) * pow(x, k, q) for k, c in enumerate(ct.c[1][j])) % q == int(ev[i])
+    # and it is a ciphertext like any other: it rotates and squares
+    keys2 = bfv.keygen(P, 3, rotations=[2], relin=True)
+    assert np.array_equal(dec(P, keys2, bfv.rotate(P, keys2, ct, 2)), row_shift(v, 2))
