@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=None,
                     help="requests per batched step (per GPU; default 16, 2 for cifar)")
     ap.add_argument("--plain", type=int, default=8, help="single-request evaluations for plain latency")
+    ap.add_argument("--grouped-digits", action="store_true",
+                    help="mnist: key-switching digits of two primes with two special primes")
     ap.add_argument("--L", type=int, default=None,
                     help="ciphertext primes (default: 5 for mnist, 6 for lola_dense)")
     ap.add_argument("--workload", choices=["mnist", "lola_dense", "cifar", "head", "dense64"], default="mnist",
@@ -178,7 +180,10 @@ def workload_params(workload, L):
     import workloads as W
     if workload == "dense64":
         return W.params_dense64()
-    return {"cifar": W.params_cifar, "head": W.params_head}.get(workload, W.params_mnist)(L)
+    if workload == "mnist_grouped":
+        return W.params_mnist_grouped(L)
+    return {"cifar": W.params_cifar, "head": W.params_head, "lola_dense": W.params_lola_dense}.get(
+        workload, W.params_mnist)(L)
 
 
 def oracle_sample(n_rot=1, n_sq=1, workload="mnist", L=5, levels=None):
@@ -192,7 +197,7 @@ def oracle_sample(n_rot=1, n_sq=1, workload="mnist", L=5, levels=None):
     import workloads as W
     from oracle import bfv, encoding
     ps = workload_params(workload, L)
-    P = bfv.Params(ps.n, ps.q, ps.L, ps.K, ps.t)
+    P = bfv.Params(ps.n, ps.q, ps.L, ps.K, ps.t, ps.alpha)
     keys = bfv.keygen(P, 5, rotations=[1], relin=True)
     t = ps.t[0]
     v = np.random.default_rng(0).integers(0, 16, ps.n)
@@ -256,7 +261,7 @@ def oracle_residue_inference(workload, L, levels, ti):
     import workloads as W
     from oracle import bfv, encoding, lola as OL
     ps = workload_params(workload, L)
-    P = bfv.Params(ps.n, ps.q, ps.L, ps.K, ps.t)
+    P = bfv.Params(ps.n, ps.q, ps.L, ps.K, ps.t, ps.alpha)
     n, t, kt = ps.n, ps.t[ti], len(ps.t)
     if workload == "mnist":
         mnet, img = W.mnist_net(), W.image()
@@ -508,10 +513,11 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
 
-    ps = workload_params(args.workload, args.L)
+    ps = workload_params("mnist_grouped" if args.grouped_digits and args.workload == "mnist" else args.workload,
+                         args.L)
     n, kt, Lq = ps.n, len(ps.t), ps.L
     mnet = W.mnist_net()
-    ctx = L.lola_ctx_create(ps.n, ps.q, ps.L, ps.K, ps.t, device=local)
+    ctx = L.lola_ctx_create(ps.n, ps.q, ps.L, ps.K, ps.t, alpha=ps.alpha, device=local)
     t_tune = time.perf_counter()
     tune = L.lola_autotune(ctx, stream) if not args.no_autotune else None   # key-switch launch geometry
     t_tune = time.perf_counter() - t_tune
@@ -790,6 +796,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": WORKLOAD_NAME[args.workload], "batch_per_gpu": B, "n": n, "L": Lq, "K": ps.K, "k_t": kt,
+                       "key_switch_digit_primes": ps.alpha,
                        "levels": [Lq] + list(args.levels or []),
                        "autotune": ({"table": tune["table"], "seconds": round(t_tune, 2)} if tune else "defaults"),
                        "aux_primes": len(L.lola_ctx_aux_primes(ctx)), "parallelism": f"replicas x{world}",
@@ -919,7 +926,7 @@ def run_primitives(args):
     alu = None
     for n, Lq, batches in grid:
         ps = W.params_sweep(n, Lq)
-        ctx = L.lola_ctx_create(ps.n, ps.q, ps.L, ps.K, ps.t)
+        ctx = L.lola_ctx_create(ps.n, ps.q, ps.L, ps.K, ps.t, alpha=ps.alpha)
         if not args.no_autotune:
             L.lola_autotune(ctx)
         if alu is None:
@@ -960,8 +967,8 @@ def run_serve(args):
 
     ps2, ps4 = W.params_mnist(args.L), W.params_head()
     n = ps2.n
-    ctx2 = L.lola_ctx_create(ps2.n, ps2.q, ps2.L, ps2.K, ps2.t)
-    ctx4 = L.lola_ctx_create(ps4.n, ps4.q, ps4.L, ps4.K, ps4.t)
+    ctx2 = L.lola_ctx_create(ps2.n, ps2.q, ps2.L, ps2.K, ps2.t, alpha=ps2.alpha)
+    ctx4 = L.lola_ctx_create(ps4.n, ps4.q, ps4.L, ps4.K, ps4.t, alpha=ps4.alpha)
     if not args.no_autotune:
         L.lola_autotune(ctx2)
         L.lola_autotune(ctx4)

@@ -64,10 +64,17 @@ typedef struct lola_net lola_net;
  * order-2n root of unity mod t for batching).
  *   n      ring degree, power of two, 16 <= n <= 16384
  *   L      number of ciphertext primes (Q = q_0 ... q_{L-1}), 1 <= L <= 12
- *   K      special primes for key switching: 0 or 1 (P = q_L when 1)
+ *   K      special primes for key switching: 0, 1 or 2 (P = their product,
+ *          q_L q_{L+1})
  *   q      L + K distinct primes, each = 1 mod 2n and < 2^61 - 2^30
  *   k_t    number of plaintext moduli (CRT pipelines), 1 <= k_t <= 4
  *   t      k_t distinct primes = 1 mod 2n, < 2^31, coprime to all q
+ *   alpha  ciphertext primes per key-switching digit: 0 or 1 (one digit per
+ *          prime), or 2 (digits of two consecutive primes, the last one
+ *          single when L is odd; needs K > 0, and P above every digit's
+ *          modulus for a small switching error, e.g. K = 2 with primes of
+ *          one size).  A digit is the residue of the switched polynomial
+ *          modulo its primes' product, in [0, that product).
  * The library adds its own auxiliary primes for exact ct x ct scaling.
  * Errors: LOLA_E_PARAM for an invalid set, LOLA_E_CUDA / LOLA_E_NOMEM. */
 typedef struct {
@@ -77,6 +84,7 @@ typedef struct {
   const uint64_t* q; /* host, L + K entries, special prime last */
   uint32_t k_t;
   const uint64_t* t; /* host, k_t entries */
+  uint32_t alpha;
 } lola_params;
 
 int lola_ctx_create(const lola_params* params, int device, lola_ctx** out);
@@ -206,9 +214,10 @@ int lola_multiply(lola_ctx* ctx, const lola_keys* keys, const uint64_t* a, const
  * call before any stream capture.  Calls share the array: calls that overlap
  * on the GPU race and must be serialised by the caller.  No part of the
  * array needs clearing between calls.  A count whose scratch does not fit
- * returns LOLA_E_PARAM; the scratch is count * (L + L*(L+K) + 2) * n words,
- * plus count * 2 * (L+K) * n words when L = 1 (a separate inner-product
- * area); missing key: LOLA_E_NOKEY. */
+ * returns LOLA_E_PARAM; the scratch is count * (L + D*(L+K) + 2K) * n words
+ * (D = key-switching digits, ceil(L / alpha)), plus count * 2 * (L+K) * n
+ * words when D = 1 (a separate inner-product area); missing key:
+ * LOLA_E_NOKEY. */
 #define LOLA_ROTATE_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
 int lola_rotate_noalloc(lola_ctx* ctx, const lola_keys* keys, const uint64_t* in, uint64_t* out, size_t count,
                         int32_t step, void* stream);

@@ -64,7 +64,7 @@ int autotune(Ctx* c0, cudaStream_t s) {
   const size_t n = c->n, L = c->L, LK = c->L + c->K;
   Tune t;
   t.on = true;
-  const size_t per[TUNE_KERNELS] = {L, L * (LK - 1), 2, 2 * L};
+  const size_t per[TUNE_KERNELS] = {L, c->host.mu_n[1], 2 * (size_t)c->K, 2 * L};
   // start from the defaults (the table then reproduces them exactly where
   // nothing is measured faster)
   for (int kern = 0; kern < TUNE_KERNELS; ++kern)
@@ -78,7 +78,7 @@ int autotune(Ctx* c0, cudaStream_t s) {
     return LOLA_OK;
   }
   // buffers: input and output ciphertexts, rotation scratch, a zero key
-  const size_t w_ct = kMaxCts * c->ct_words(), w_scr = rotate_scratch_words(c, kMaxCts), w_key = 2 * L * LK * n;
+  const size_t w_ct = kMaxCts * c->ct_words(), w_scr = rotate_scratch_words(c, kMaxCts), w_key = 2 * c->dnum * LK * n;
   const size_t words = 2 * w_ct + w_scr + w_key;
   void* buf = nullptr;
   LOLA_CUDA_TRY(cudaMallocAsync(&buf, words * 8, s));

@@ -31,9 +31,13 @@ struct MrcDev {
   uint64_t half[MAXB];             // mixed-radix digits of (prod b - 1) / 2
 };
 
+// modup work items of one ciphertext: (digit, target prime) pairs
+constexpr int MAXMU = MAXL * (MAXL + 2);
+
 struct CtxDev {
   uint32_t n, logn, L, K, M, kt, np;
-  int iP;                          // index of P (= L) when K = 1
+  uint32_t alpha, dnum;            // primes per key-switching digit, digits (ceil(L / alpha))
+  int iP;                          // index of the first special prime (= L) when K > 0
   int iB;                          // first auxiliary prime index (= L + K)
   int iT;                          // first plaintext modulus index (= L + K + M)
   // 1 when every prime of Q and P is below 8x the smallest one: a digit
@@ -59,19 +63,32 @@ struct CtxDev {
   uint64_t QinvT[MAXT], QinvT_s[MAXT];            // Q^-1 mod t
   uint64_t deltaQ[MAXT][MAXB];                    // floor(Q/t) mod q_i
   uint64_t deltaQ_s[MAXT][MAXB];
-  // --- key switching (K = 1) ---
+  // --- key switching (P = product of the K special primes) ---
   uint64_t PmodQ[MAXB], PmodQ_s[MAXB];
   uint64_t PinvQ[MAXB], PinvQ_s[MAXB];            // P^-1 mod q_i
+  // mod-up work items: [0] every (digit g, prime j), [1] those with q_j
+  // outside digit g's group (the diagonal blocks come from decompose)
+  uint32_t mu_n[2];
+  uint8_t mu_g[2][MAXMU], mu_j[2][MAXMU];
+  // digits of two primes (q_a, q_b = q_{a+1}, a = alpha g): q_a^-1 mod q_b
+  // and q_a mod every prime of Q P (the digit is a + q_a ((b - a) q_a^-1 mod q_b))
+  uint64_t grp_inv[MAXL], grp_inv_s[MAXL];
+  uint64_t grp_qa[MAXL][MAXL + 2], grp_qa_s[MAXL][MAXL + 2];
+  uint32_t modup_lazy_a;           // 1 when q_a < 6 q_j for all primes (a digit's q_a-part needs no reduction)
+  // K = 2 mod-down: x = x1 + P1 v, v = (x2 - x1) P1^-1 mod P2; (P - 1) / 2 =
+  // ph1 + P1 phv; P1 P^-1 mod q_i
+  uint64_t P1invP2, P1invP2_s, ph1, phv;
+  uint64_t P1PinvQ[MAXB], P1PinvQ_s[MAXB];
   uint64_t PmontQ[MAXB];                          // (P mod q_i) 2^64 mod q_i (P = 1 when K = 0)
   // switching keys are stored as k * P^-1 * 2^64 mod q_j on the L ciphertext
   // primes (k * 2^64 on the special prime), so the inner product already
   // carries the ModDown factor P^-1:
   uint64_t KskR2[MAXB];                           // 2^128 P^-1 mod q_j; 2^128 mod P on P
   uint64_t KskOut[MAXB];                          // P mod q_j; 1 on P (Montgomery factor back to k)
-  // geometry of the switching keys, which belong to the full context: kL
-  // digits of kL + K primes, the special prime at prime index kL (kL = L
+  // geometry of the switching keys, which belong to the full context: kdnum
+  // digits of kL + K primes, the special primes at prime index kL (kL = L
   // except in a context reached by modulus switching)
-  uint32_t kL, kLK;
+  uint32_t kL, kLK, kdnum;
 };
 
 // host-side error reporting

@@ -204,9 +204,13 @@ static int build_ctx(Ctx* c, const lola_params* p) {
   c->L = p->L;
   c->K = p->K;
   c->kt = p->k_t;
+  c->alpha = p->alpha ? p->alpha : 1;
   if ((1u << c->logn) != p->n || c->logn < 4 || c->logn > 14) return fail(LOLA_E_PARAM, "n must be a power of two in [16, 16384]");
   if (p->L < 1 || p->L > MAXL) return fail(LOLA_E_PARAM, "L out of range");
-  if (p->K > 1) return fail(LOLA_E_PARAM, "K must be 0 or 1");
+  if (p->K > 2) return fail(LOLA_E_PARAM, "K must be 0, 1 or 2");
+  if (c->alpha > 2) return fail(LOLA_E_PARAM, "alpha must be 0, 1 or 2");
+  if (c->alpha > 1 && p->K == 0) return fail(LOLA_E_PARAM, "digits of several primes need a special prime (K > 0)");
+  c->dnum = (c->L + c->alpha - 1) / c->alpha;
   if (p->k_t < 1 || p->k_t > MAXT) return fail(LOLA_E_PARAM, "k_t out of range");
   if (!p->q || !p->t) return fail(LOLA_E_PARAM, "null prime list");
   const uint64_t two_n = 2ull * p->n;
@@ -263,6 +267,42 @@ static int build_ctx(Ctx* c, const lola_params* p) {
   H.iT = c->iT();
   H.kL = c->L;
   H.kLK = c->L + c->K;
+  H.alpha = c->alpha;
+  H.dnum = c->dnum;
+  H.kdnum = c->dnum;
+  {
+    // mod-up work items and the two-prime digit constants
+    const uint32_t LK = c->L + c->K;
+    H.mu_n[0] = H.mu_n[1] = 0;
+    for (uint32_t g = 0; g < c->dnum; ++g)
+      for (uint32_t j = 0; j < LK; ++j) {
+        const bool own = j < c->L && j / c->alpha == g;
+        for (int skip = 0; skip < 2; ++skip) {
+          if (skip && own) continue;
+          H.mu_g[skip][H.mu_n[skip]] = (uint8_t)g;
+          H.mu_j[skip][H.mu_n[skip]] = (uint8_t)j;
+          ++H.mu_n[skip];
+        }
+      }
+    uint64_t qlo = ~0ull, qhi = 0;
+    for (uint32_t j = 0; j < LK; ++j) {
+      qlo = std::min(qlo, qp[j]);
+      qhi = std::max(qhi, qp[j]);
+    }
+    H.modup_lazy_a = qhi / 6 < qlo ? 1u : 0u;
+    for (uint32_t g = 0; g < c->dnum; ++g) {
+      const uint32_t a = g * c->alpha;
+      if (c->alpha < 2 || a + 1 >= c->L) continue;     // single-prime digit
+      const uint64_t qa = qp[a], qb = qp[a + 1];
+      if (qa / 2 >= qb) return fail(LOLA_E_PARAM, "a two-prime digit needs its first prime below twice its second");
+      H.grp_inv[g] = invmod_h(qa % qb, qb);
+      H.grp_inv_s[g] = shoup_h(H.grp_inv[g], qb);
+      for (uint32_t j = 0; j < LK; ++j) {
+        H.grp_qa[g][j] = qa % qp[j];
+        H.grp_qa_s[g][j] = shoup_h(H.grp_qa[g][j], qp[j]);
+      }
+    }
+  }
   const uint64_t n = c->n;
   std::vector<uint64_t> tw((size_t)4 * np * n);
   uint64_t* twf = tw.data();                  // [np][n][2]: (w, w')
@@ -342,17 +382,31 @@ static int build_ctx(Ctx* c, const lola_params* p) {
     H.QinvT[ti] = invmod_h(prefix_prod_mod(Qb, (int)c->L, t), t);
     H.QinvT_s[ti] = shoup_h(H.QinvT[ti], t);
   }
-  const uint64_t P = c->K ? qp[c->L] : 1;
+  // P = product of the special primes, reduced mod each ciphertext prime
   for (uint32_t i = 0; i < c->L; ++i) {
     const uint64_t q = Qb[i];
-    H.PmodQ[i] = P % q;
+    uint64_t Pq = 1 % q;
+    for (uint32_t k2 = 0; k2 < c->K; ++k2) Pq = mulmod_h(Pq, qp[c->L + k2] % q, q);
+    H.PmodQ[i] = Pq;
     H.PmodQ_s[i] = shoup_h(H.PmodQ[i], q);
-    H.PinvQ[i] = c->K ? invmod_h(P % q, q) : 1;
+    H.PinvQ[i] = c->K ? invmod_h(Pq, q) : 1;
     H.PinvQ_s[i] = shoup_h(H.PinvQ[i], q);
     const uint64_t r1 = (uint64_t)(((u128)1 << 64) % q);
-    H.PmontQ[i] = mulmod_h(P % q, r1, q);
+    H.PmontQ[i] = mulmod_h(Pq, r1, q);
     H.KskR2[i] = mulmod_h(H.pr[i].r2, H.PinvQ[i], q);
     H.KskOut[i] = H.PmodQ[i];
+    if (c->K == 2) {
+      H.P1PinvQ[i] = mulmod_h(qp[c->L] % q, H.PinvQ[i], q);
+      H.P1PinvQ_s[i] = shoup_h(H.P1PinvQ[i], q);
+    }
+  }
+  if (c->K == 2) {
+    const uint64_t P1 = qp[c->L], P2 = qp[c->L + 1];
+    H.P1invP2 = invmod_h(P1 % P2, P2);
+    H.P1invP2_s = shoup_h(H.P1invP2, P2);
+    const u128 half = ((u128)P1 * P2 - 1) / 2;
+    H.ph1 = (uint64_t)(half % P1);
+    H.phv = (uint64_t)(half / P1);
   }
   for (uint32_t i = c->L; i < c->L + c->K; ++i) {
     H.KskR2[i] = H.pr[i].r2;
@@ -420,7 +474,7 @@ int ctx_level(Ctx* c, uint32_t Lv, Ctx** out) {
   std::vector<uint64_t> q(r->primes.begin(), r->primes.begin() + Lv);
   q.insert(q.end(), r->primes.begin() + r->L, r->primes.begin() + r->L + r->K);
   std::vector<uint64_t> t(r->primes.begin() + r->iT(), r->primes.begin() + r->iT() + r->kt);
-  lola_params p{r->n, Lv, r->K, q.data(), r->kt, t.data()};
+  lola_params p{r->n, Lv, r->K, q.data(), r->kt, t.data(), r->alpha};
   std::unique_ptr<Ctx> lc(new Ctx());
   lc->device = r->device;
   LOLA_CUDA_TRY(cudaSetDevice(r->device));
@@ -429,6 +483,7 @@ int ctx_level(Ctx* c, uint32_t Lv, Ctx** out) {
   lc->root = r;
   lc->host.kL = r->L;
   lc->host.kLK = r->L + r->K;
+  lc->host.kdnum = r->dnum;
   LOLA_CUDA_TRY(cudaMemcpy(lc->d_const.p, &lc->host, sizeof(CtxDev), cudaMemcpyHostToDevice));
   *out = lc.get();
   r->levels[Lv] = std::move(lc);

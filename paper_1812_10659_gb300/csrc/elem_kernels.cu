@@ -42,12 +42,15 @@ __device__ __forceinline__ uint64_t redc128(unsigned __int128 T, uint64_t q, uin
 // pair (k, k+1) maps to the aligned pair holding gal_src(k) and
 // gal_src(k) ^ 1, so each pair is still one 16-byte load (swapped when
 // gal_src(k) is odd).
-// LT > 0: the digit count as a compile-time constant (fully unrolled digit
+// DT > 0: the digit count as a compile-time constant (fully unrolled digit
 // loop, all loads of a thread issued together); 0: read it from the context.
+// Digits: one per ciphertext prime, or one per group of alpha primes (D is
+// [ct][digits][L+K][n]; key row g of component c at (c kdnum + g) kLK).
 // At most 64 registers, so that 32 warps per SM keep loads in flight.
-template <int LT>
+template <int DT>
 __global__ void __launch_bounds__(256, 4) ke_ks_ip(const CtxDev* __restrict__ C, KsDev a, int final_out) {
-  const int L = LT > 0 ? LT : C->L, LK = L + C->K, logn = C->logn;
+  const int L = C->L, LK = L + C->K, logn = C->logn;
+  const int dn = DT > 0 ? DT : (int)C->dnum;
   const size_t n = C->n, half = n >> 1;
   const int J = final_out ? L : LK;
   const size_t total = a.count * J * half;
@@ -61,7 +64,7 @@ __global__ void __launch_bounds__(256, 4) ke_ks_ip(const CtxDev* __restrict__ C,
     // the keys have kL digits over kL + K primes (the full context's): prime
     // j of this context is key prime j, the special primes follow kL
     const size_t kLK = C->kLK, jk = j < L ? (size_t)j : (size_t)C->kL + (j - L);
-    const size_t krow1 = (size_t)C->kL * kLK;
+    const size_t krow1 = (size_t)C->kdnum * kLK;
     const size_t src = a.src_mod ? ct % a.src_mod : ct;
     size_t kd = k;                                // gathered pair of tau_g (D and/or c0)
     bool swp = false;
@@ -77,8 +80,8 @@ __global__ void __launch_bounds__(256, 4) ke_ks_ip(const CtxDev* __restrict__ C,
     uint64_t acc0[2] = {0, 0}, acc1[2] = {0, 0};
     unsigned __int128 s0[2] = {0, 0}, s1[2] = {0, 0};
 #pragma unroll
-    for (int i = 0; i < (LT > 0 ? LT : L); ++i) {
-      ulonglong2 d = *(const ulonglong2*)(a.D + ((src * L + i) * LK + j) * n + kD);
+    for (int i = 0; i < (DT > 0 ? DT : dn); ++i) {
+      ulonglong2 d = *(const ulonglong2*)(a.D + ((src * dn + i) * LK + j) * n + kD);
       if (swpD) d = make_ulonglong2(d.y, d.x);
       const ulonglong2 k0 = __ldg((const ulonglong2*)(key + ((size_t)i * kLK + jk) * n + k));
       const ulonglong2 k1 = __ldg((const ulonglong2*)(key + (krow1 + (size_t)i * kLK + jk) * n + k));
@@ -86,7 +89,7 @@ __global__ void __launch_bounds__(256, 4) ke_ks_ip(const CtxDev* __restrict__ C,
       s0[1] += (unsigned __int128)d.y * k0.y;
       s1[0] += (unsigned __int128)d.x * k1.x;
       s1[1] += (unsigned __int128)d.y * k1.y;
-      if ((i & 7) == 7 || i == L - 1) {
+      if ((i & 7) == 7 || i == dn - 1) {
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
           acc0[e] = add_mod(acc0[e], redc128(s0[e], P.q, P.qinv), P.q);
@@ -204,15 +207,17 @@ __global__ void ke_keygen_switch(const CtxDev* __restrict__ C, const uint64_t* a
                                  const uint64_t* s_mont, const uint64_t* sfrom, uint64_t* out) {
   const int L = C->L, LK = C->L + C->K, logn = C->logn;
   const size_t n = C->n;
-  const size_t total = (size_t)L * LK * n;
+  const size_t total = (size_t)C->dnum * LK * n;
   for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < total; w += (size_t)gridDim.x * blockDim.x) {
     const size_t k = w & (n - 1);
     const int j = (w >> logn) % LK;
-    const int i = (int)((w >> logn) / LK);
+    const int g = (int)((w >> logn) / LK);
     const PrimeDev& P = C->pr[j];
     uint64_t b = neg_mod(mont_mul(a[w], s_mont[(size_t)j * n + k], P.q, P.qinv), P.q);
     b = add_mod(b, e[w], P.q);
-    if (i == j) b = add_mod(b, mont_mul(sfrom[(size_t)j * n + k], C->PmontQ[j], P.q, P.qinv), P.q);
+    // [P]_{q_j} s' on the primes of digit g's group
+    if (j < L && j / (int)C->alpha == g)
+      b = add_mod(b, mont_mul(sfrom[(size_t)j * n + k], C->PmontQ[j], P.q, P.qinv), P.q);
     out[w] = mont_mul(b, C->KskR2[j], P.q, P.qinv);
     out[total + w] = mont_mul(a[w], C->KskR2[j], P.q, P.qinv);
   }
@@ -509,7 +514,8 @@ namespace k {
 
 int ks_ip(Ctx* c, const KsDev& a, bool final_out, cudaStream_t s) {
   const size_t pairs = a.count * (final_out ? c->L : c->L + c->K) * (c->n / 2);
-  switch (c->L) {
+  switch (c->dnum) {
+    case 1: ELEM_LAUNCH(KI_KS_IP_Q, ke_ks_ip<1>, pairs, c->dev, a, (int)final_out); break;
     case 2: ELEM_LAUNCH(KI_KS_IP_Q, ke_ks_ip<2>, pairs, c->dev, a, (int)final_out); break;
     case 3: ELEM_LAUNCH(KI_KS_IP_Q, ke_ks_ip<3>, pairs, c->dev, a, (int)final_out); break;
     case 4: ELEM_LAUNCH(KI_KS_IP_Q, ke_ks_ip<4>, pairs, c->dev, a, (int)final_out); break;
@@ -559,7 +565,7 @@ int neg_axpe(Ctx* c, const uint64_t* a, const uint64_t* s_mont, const uint64_t* 
 
 int keygen_switch(Ctx* c, const uint64_t* a, const uint64_t* e, const uint64_t* s_mont, const uint64_t* sfrom,
                   uint64_t* out, cudaStream_t s) {
-  const size_t total = (size_t)c->L * (c->L + c->K) * c->n;
+  const size_t total = (size_t)c->dnum * (c->L + c->K) * c->n;
   ELEM_LAUNCH(KI_MISC, ke_keygen_switch, total, c->dev, a, e, s_mont, sfrom, out);
   return post(c);
 }

@@ -109,15 +109,16 @@ struct AsyncBuf {
   } while (0)
 
 // --------------------------------------------------------------- key switching
-// scratch: digits [count][L][n], mod-up limbs D [count][L][L+K][n], x_P
-// [count][2][n]; the inner products live in place over D's digit rows 0 and
-// 1 (a separate [count][2][L+K][n] area when L = 1).  tau_g(c0) has no area:
-// rotate() always has the inner product gather it from the input (c0_gather),
-// and lola_rotate_noalloc's size check relies on this count.
+// scratch: digits [count][L][n], mod-up limbs D [count][dnum][L+K][n], x_P
+// [count][2][K][n]; the inner products live in place over D's digit rows 0
+// and 1 (a separate [count][2][L+K][n] area when there is one digit).
+// tau_g(c0) has no area: rotate() always has the inner product gather it
+// from the input (c0_gather), and lola_rotate_noalloc's size check relies on
+// this count.
 size_t rotate_scratch_words(const Ctx* c, size_t count) {
   const size_t LK = c->L + c->K;
-  size_t w = count * (c->L + c->L * LK + 2) * (size_t)c->n;   // digits, D, x_P
-  if (c->L < 2) w += count * 2 * LK * (size_t)c->n;
+  size_t w = count * (c->L + c->dnum * LK + 2 * (size_t)c->K) * (size_t)c->n;   // digits, D, x_P
+  if (c->dnum < 2) w += count * 2 * LK * (size_t)c->n;
   return w;
 }
 
@@ -125,14 +126,14 @@ size_t rotate_scratch_words(const Ctx* c, size_t count) {
 // (have_diag: decompose wrote the diagonal limbs D[i][i]) and
 // relinearisation.
 static int ks_switch(Ctx* c, KsDev& a, uint64_t* extra_acc, bool have_diag, cudaStream_t s) {
-  const size_t n = c->n, L = c->L, LK = c->L + c->K;
+  const size_t n = c->n, LK = c->L + c->K;
   if (!c->K) {
     TRY(k::ks_modup(c, a, have_diag, s));
     return k::ks_ip(c, a, true, s);
   }
-  if (L >= 2) {
+  if (c->dnum >= 2) {
     a.acc = a.D;
-    a.acc_stride = L * LK * n;
+    a.acc_stride = c->dnum * LK * n;
   } else {
     a.acc = extra_acc;
     a.acc_stride = 2 * LK * n;
@@ -155,7 +156,7 @@ int rotate(Ctx* c, const uint64_t* in, uint64_t* out, const uint64_t* accum, siz
   a.out = out;
   a.dig = scratch;
   a.D = a.dig + count * L * n;
-  a.xP = a.D + count * L * LK * n;
+  a.xP = a.D + count * c->dnum * LK * n;
   a.c0_gather = 1;                            // the inner product gathers tau_g(c0)
   a.count = count;
   a.d_gal = r.d_gal;
@@ -164,7 +165,7 @@ int rotate(Ctx* c, const uint64_t* in, uint64_t* out, const uint64_t* accum, siz
   a.key = r.key;
   a.gal_div = r.div ? r.div : 1;
   TRY(k::ks_decompose(c, a, s));
-  return ks_switch(c, a, a.xP + count * 2 * n, true, s);
+  return ks_switch(c, a, a.xP + count * 2 * c->K * n, true, s);
 }
 
 // Hoisted rotations: every one of `count` ciphertexts rotated by each of
@@ -177,7 +178,7 @@ static size_t hoisted_chunk(size_t count, size_t S) { return std::min(S, std::ma
 
 size_t rotate_hoisted_scratch_words(const Ctx* c, size_t count, size_t S) {
   const size_t n = c->n, L = c->L, LK = c->L + c->K;
-  return count * (L + L * LK) * n + hoisted_chunk(count, S) * count * (2 * LK + 2) * n;
+  return count * (L + c->dnum * LK) * n + hoisted_chunk(count, S) * count * (2 * LK + 2 * c->K) * n;
 }
 
 int rotate_hoisted(Ctx* c, const uint64_t* in, uint64_t* out, size_t count, size_t S, const uint32_t* d_gal,
@@ -201,7 +202,7 @@ int rotate_hoisted(Ctx* c, const uint64_t* in, uint64_t* out, size_t count, size
     b.c0 = in;
     b.out = out + s0 * count * c->ct_words();
     b.D = a.D;
-    b.acc = a.D + count * L * LK * n;
+    b.acc = a.D + count * c->dnum * LK * n;
     b.acc_stride = 2 * LK * n;
     b.xP = b.acc + sc * count * 2 * LK * n;
     b.count = sc * count;
@@ -259,8 +260,8 @@ size_t multiply_scratch_words(const Ctx* c, size_t count, bool square) {
   if (!square) w *= 2;                                 // Y, YB
   w += count * 3 * (L + M) * n;                        // T
   w += count * 2 * L * n + count * L * n;              // E, DIG
-  w += count * L * LK * n + count * 2 * n;             // D, xP
-  if (L < 2) w += count * 2 * LK * n;                  // inner products (L = 1)
+  w += count * c->dnum * LK * n + count * 2 * c->K * n;   // D, xP
+  if (c->dnum < 2) w += count * 2 * LK * n;            // inner products (one digit)
   return w;
 }
 
@@ -283,7 +284,7 @@ int multiply(Ctx* c, const uint64_t* x, const uint64_t* y, uint64_t* out, size_t
   uint64_t* E = T + count * 3 * (L + M) * n;
   uint64_t* DIG = E + count * 2 * L * n;
   uint64_t* D = DIG + count * L * n;
-  uint64_t* xP = D + count * L * LK * n;
+  uint64_t* xP = D + count * c->dnum * LK * n;
 
   PrimeMap qmap = prime_map(L), bmap = prime_map(M, c->iB());
   PrimeMap qbmap{};
@@ -314,19 +315,19 @@ int multiply(Ctx* c, const uint64_t* x, const uint64_t* y, uint64_t* out, size_t
   a.gal = 1;
   a.key = relin_key;
   a.gal_div = 1;
-  return ks_switch(c, a, xP + count * 2 * n, false, s);
+  return ks_switch(c, a, xP + count * 2 * c->K * n, false, s);
 }
 
 // --------------------------------------------------------------------- keys
 static int gen_switch_key(Ctx* c, const DevBuf& s_mont, const uint64_t* d_sfrom, uint64_t key_id, uint64_t seed,
                           std::shared_ptr<SwitchKey>* out, cudaStream_t s) {
-  const size_t n = c->n, L = c->L, LK = c->L + c->K;
-  std::vector<int64_t> e(L * n);
-  std::vector<uint64_t> a(L * LK * n);
-  for (size_t i = 0; i < L; ++i) {
-    sample_gaussian(seed, TAG_KSK_E, key_id, i, e.data() + i * n, n);
+  const size_t n = c->n, D = c->dnum, LK = c->L + c->K;
+  std::vector<int64_t> e(D * n);
+  std::vector<uint64_t> a(D * LK * n);
+  for (size_t g = 0; g < D; ++g) {          // one row per digit (group of alpha primes)
+    sample_gaussian(seed, TAG_KSK_E, key_id, g, e.data() + g * n, n);
     for (size_t j = 0; j < LK; ++j)
-      sample_uniform(seed, TAG_KSK_A, key_id, i * 256 + j, c->primes[j], a.data() + (i * LK + j) * n, n);
+      sample_uniform(seed, TAG_KSK_A, key_id, g * 256 + j, c->primes[j], a.data() + (g * LK + j) * n, n);
   }
   AsyncBuf de, da, dE;
   TRY(de.alloc(e.size() * 8, s));
@@ -335,10 +336,10 @@ static int gen_switch_key(Ctx* c, const DevBuf& s_mont, const uint64_t* d_sfrom,
   LOLA_CUDA_TRY(cudaMemcpyAsync(de.p, e.data(), e.size() * 8, cudaMemcpyHostToDevice, s));
   LOLA_CUDA_TRY(cudaMemcpyAsync(da.p, a.data(), a.size() * 8, cudaMemcpyHostToDevice, s));
   PrimeMap lk = prime_map(LK);
-  TRY(k::ntt_fwd_map(c, da.as<uint64_t>(), da.as<uint64_t>(), L * LK, LK, lk, s));
-  TRY(k::ntt_fwd_from_signed(c, de.as<int64_t>(), dE.as<uint64_t>(), L, LK, 0, s));
+  TRY(k::ntt_fwd_map(c, da.as<uint64_t>(), da.as<uint64_t>(), D * LK, LK, lk, s));
+  TRY(k::ntt_fwd_from_signed(c, de.as<int64_t>(), dE.as<uint64_t>(), D, LK, 0, s));
   auto key = std::make_shared<SwitchKey>();
-  TRY(key->buf.alloc(2 * L * LK * n * 8));
+  TRY(key->buf.alloc(2 * D * LK * n * 8));
   TRY(k::keygen_switch(c, da.as<uint64_t>(), dE.as<uint64_t>(), s_mont.u64(), d_sfrom, key->buf.u64(), s));
   LOLA_CUDA_TRY(cudaStreamSynchronize(s));
   *out = key;
@@ -446,7 +447,7 @@ int keys_export(Ctx* c, const KeySet* ks, int what, int32_t step, uint64_t* host
       break;
     case 2:
       if (!ks->ev->relin) return fail(LOLA_E_NOKEY, "no relinearisation key");
-      need = 2 * L * LK * n;
+      need = 2 * c->dnum * LK * n;
       src = ks->ev->relin->buf.u64();
       limbs = LK;
       break;
@@ -454,7 +455,7 @@ int keys_export(Ctx* c, const KeySet* ks, int what, int32_t step, uint64_t* host
       if (step < 0 || (uint32_t)step >= c->n / 2) return fail(LOLA_E_PARAM, "bad step");
       const SwitchKey* k2 = ks->galois_key(galois_for_step(c->n, step));
       if (!k2) return fail(LOLA_E_NOKEY, "no Galois key for this step");
-      need = 2 * L * LK * n;
+      need = 2 * c->dnum * LK * n;
       src = k2->buf.u64();
       limbs = LK;
       break;

@@ -82,6 +82,7 @@ int tune_bucket(size_t units);
 struct Ctx {
   int device = 0;
   uint32_t n = 0, logn = 0, L = 0, K = 0, M = 0, kt = 0;
+  uint32_t alpha = 1, dnum = 0;   // primes per key-switching digit, digits (ceil(L / alpha))
   std::vector<uint64_t> primes;   // [Q..][P][aux..][t..]
   CtxDev host;                    // host copy of the device constants
   CtxDev* dev = nullptr;          // device copy
@@ -118,7 +119,7 @@ struct ProfScope {
 
 // ---------------------------------------------------------------------- keys
 struct SwitchKey {
-  DevBuf buf;   // [2 (b, a)][L digits][L+K primes][n], NTT form, Montgomery (x 2^64)
+  DevBuf buf;   // [2 (b, a)][dnum digits][L+K primes][n], NTT form, Montgomery (x 2^64)
 };
 
 // ---------------------------------------------------------------- ciphertexts

@@ -141,6 +141,9 @@ int ntt_fwd_map(Ctx* c, const uint64_t* in, uint64_t* out, size_t n_polys, uint3
                 cudaStream_t s) {
   if (!n_polys) return LOLA_OK;
   ProfScope ps(c, KI_NTT_FWD, s, n_polys);
+  if (c->logn == CL_LOGN && n_polys < LOLA_NTT_CL2_UNITS)
+    return ntt_fwd_cluster(c, in, out, n_polys, limbs, pm, s,
+                           n_polys < LOLA_NTT_CL4_UNITS ? TV_CLUSTER4_16 : TV_CLUSTER16);
   LOLA_DISPATCH_CFG(CfgM, c->logn, kn_fwd, n_polys, s, c->dev, in, out, limbs, pm);
   return post_launch(c, s);
 }
@@ -149,6 +152,9 @@ int ntt_inv_map(Ctx* c, const uint64_t* in, uint64_t* out, size_t n_polys, uint3
                 bool mont_fix, cudaStream_t s) {
   if (!n_polys) return LOLA_OK;
   ProfScope ps(c, KI_NTT_INV, s, n_polys);
+  if (c->logn == CL_LOGN && n_polys < LOLA_NTT_CL2_UNITS)
+    return ntt_inv_cluster(c, in, out, n_polys, limbs, pm, mont_fix, s,
+                           n_polys < LOLA_NTT_CL4_UNITS ? TV_CLUSTER4_16 : TV_CLUSTER16);
   LOLA_DISPATCH_CFG(CfgM, c->logn, kn_inv, n_polys, s, c->dev, in, out, limbs, pm, (int)mont_fix);
   return post_launch(c, s);
 }

@@ -15,14 +15,14 @@ template <int LOGN>
 __global__ void __launch_bounds__(Cfg<LOGN>::T) kn_ks_decompose(const CtxDev* __restrict__ C, KsDev a) {
   extern __shared__ uint64_t sm[];
   constexpr int N = Cfg<LOGN>::N, T = Cfg<LOGN>::T, LOGE = Cfg<LOGN>::LOGE;
-  const int L = C->L, LK = C->L + C->K;
+  const int L = C->L, LK = C->L + C->K, dnum = C->dnum;
   const size_t ct = blockIdx.x / L;
   const int i = blockIdx.x % L;
   const uint32_t g = a.d_gal ? a.d_gal[ct / a.gal_div] : a.gal;
   const uint32_t ginv = inv_odd32(g) & ((2u << LOGN) - 1);
   const int tid = threadIdx.x;
   const uint64_t* src1 = a.c1 + (ct * 2 * L + L + i) * (size_t)N;
-  uint64_t* diag = a.D + ((ct * L + i) * LK + i) * (size_t)N;
+  uint64_t* diag = a.D + ((ct * dnum + i / C->alpha) * LK + i) * (size_t)N;
   uint64_t* dig = a.dig + (ct * L + i) * (size_t)N;
   const PrimeDev& P = C->pr[i];
   uint64_t v[N / T];
@@ -40,37 +40,46 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T) kn_ks_decompose(const CtxDev* __
   ntt_inverse_smem<LOGN, LOGE>(sm, TW_I(C, i), P.q, P.ninv, P.ninv_s, [&](int k2, uint64_t v) { dig[k2] = v; });
 }
 
-// B: digit i reduced mod prime j, forward transform -> D[i][j]
-template <int LOGN>
-__global__ void __launch_bounds__(CfgM<LOGN>::T) kn_ks_modup(const CtxDev* __restrict__ C, KsDev a, int skip_diag) {
+// B: digit g (one or two primes) reduced mod prime j, forward transform -> D[g][j]
+template <int LOGN, bool GROUPED>
+__device__ __forceinline__ void ks_modup_body(const CtxDev* __restrict__ C, const KsDev& a, int skip_diag) {
   extern __shared__ uint64_t sm[];
   constexpr int N = CfgM<LOGN>::N;
-  const int L = C->L, LK = C->L + C->K;
-  const int per = skip_diag ? L * (LK - 1) : L * LK;
+  const int L = C->L, LK = C->L + C->K, dnum = C->dnum;
+  const int per = (int)C->mu_n[skip_diag];
   const size_t ct = blockIdx.x / per;
   const int r = blockIdx.x % per;
-  const int i = r / (skip_diag ? LK - 1 : LK);
-  int j = r % (skip_diag ? LK - 1 : LK);
-  if (skip_diag && j >= i) ++j;
-  const uint64_t* dig = a.dig + (ct * L + i) * (size_t)N;
-  uint64_t* dst = a.D + ((ct * L + i) * LK + j) * (size_t)N;
+  const int g = C->mu_g[skip_diag][r], j = C->mu_j[skip_diag][r];
+  uint64_t* dst = a.D + ((ct * dnum + g) * LK + j) * (size_t)N;
   const PrimeDev& P = C->pr[j];
-  const bool raw = C->modup_raw != 0;
-  ntt_forward<LOGN, CfgM<LOGN>::LOGE>(sm, TW_F(C, j), P.q, P.f64, [&](int k) { return raw ? dig[k] : reduce64(dig[k], P.q, P.f64); },
+  ntt_forward<LOGN, CfgM<LOGN>::LOGE>(sm, TW_F(C, j), P.q, P.f64,
+                                      modup_digit<GROUPED>(C, a.dig + ct * L * (size_t)N, g, j, N),
                                       [&](int k, uint64_t v) { dst[k] = v; });
 }
 
-// D: inverse transform of the special-prime inner products (both components)
+template <int LOGN>
+__global__ void __launch_bounds__(CfgM<LOGN>::T) kn_ks_modup(const CtxDev* __restrict__ C, KsDev a, int skip_diag) {
+  ks_modup_body<LOGN, false>(C, a, skip_diag);
+}
+
+template <int LOGN>
+__global__ void __launch_bounds__(CfgM<LOGN>::T) kn_ks_modup2(const CtxDev* __restrict__ C, KsDev a, int skip_diag) {
+  ks_modup_body<LOGN, true>(C, a, skip_diag);
+}
+
+// D: inverse transform of the special-prime inner products (both components,
+//    each special prime) into x_P [ct][2][K][n]
 template <int LOGN>
 __global__ void __launch_bounds__(Cfg<LOGN>::T) kn_ks_intt_p(const CtxDev* __restrict__ C, KsDev a) {
   extern __shared__ uint64_t sm[];
   constexpr int N = Cfg<LOGN>::N;
-  const int LK = C->L + C->K, ip = C->iP;
-  const size_t ct = blockIdx.x >> 1;
-  const int comp = blockIdx.x & 1;
+  const int LK = C->L + C->K, K = C->K;
+  const size_t ct = blockIdx.x / (2 * K);
+  const int r = blockIdx.x % (2 * K);
+  const int comp = r / K, sp = r % K, ip = C->iP + sp;
   const PrimeDev& P = C->pr[ip];
   const uint64_t* src = a.acc + ct * a.acc_stride + (size_t)(comp * LK + ip) * N;
-  uint64_t* dst = a.xP + (ct * 2 + comp) * (size_t)N;
+  uint64_t* dst = a.xP + ((ct * 2 + comp) * K + sp) * (size_t)N;
   ntt_inverse<LOGN, Cfg<LOGN>::LOGE>(sm, TW_I(C, ip), P.q, P.ninv, P.ninv_s, [&](int k) { return src[k]; },
                                       [&](int k, uint64_t v) { dst[k] = v; });
 }
@@ -78,12 +87,11 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T) kn_ks_intt_p(const CtxDev* __res
 
 // E: output limb out[comp][j] = ACC'[comp][j] - NTT(x~ P^-1 mod q_j), with
 //    x~ = centered(x mod P); the inner-product kernel left ACC' = ACC P^-1 +
-//    addend + accumulator (the keys carry P^-1).  The loader multiplies the
-//    raw residue x in [0, P) by P^-1 mod q_j (Shoup, any 64-bit input) and
-//    subtracts 1 = P P^-1 where x~ = x - P; its value stays below 4q, which
-//    the forward butterflies accept.
-template <int LOGN>
-__global__ void __launch_bounds__(CfgM<LOGN>::T) kn_ks_moddown(const CtxDev* __restrict__ C, KsDev a) {
+//    addend + accumulator (the keys carry P^-1).  The loader (ModDownLoad)
+//    forms x~ P^-1 mod q_j from the special-prime limbs in coefficient form;
+//    its value stays below 6q, which the forward butterflies accept.
+template <int LOGN, bool K2>
+__device__ __forceinline__ void ks_moddown_body(const CtxDev* __restrict__ C, const KsDev& a) {
   extern __shared__ uint64_t sm[];
   constexpr int N = CfgM<LOGN>::N;
   const int L = C->L, LK = C->L + C->K;
@@ -92,17 +100,19 @@ __global__ void __launch_bounds__(CfgM<LOGN>::T) kn_ks_moddown(const CtxDev* __r
   const int comp = r / L, j = r % L;
   const uint64_t* accp = a.acc + ct * a.acc_stride + (size_t)(comp * LK + j) * N;
   const PrimeDev& P = C->pr[j];
-  const uint64_t Phalf = (C->pr[C->iP].q - 1) / 2, q2m1 = 2 * P.q - 1;
-  const uint64_t Pinv = C->PinvQ[j], Pinv_s = C->PinvQ_s[j];
-  const uint64_t* x = a.xP + (ct * 2 + comp) * (size_t)N;
   uint64_t* dst = a.out + ((ct * 2 + comp) * L + j) * (size_t)N;
-  ntt_forward<LOGN, CfgM<LOGN>::LOGE>(
-      sm, TW_F(C, j), P.q, P.f64,
-      [&](int k) {
-        const uint64_t v = x[k];
-        return shoup_mul_lazy(v, Pinv, Pinv_s, P.q) + (v > Phalf ? q2m1 : 0);
-      },
-      ModDownStore{accp, dst, P.q});
+  ntt_forward<LOGN, CfgM<LOGN>::LOGE>(sm, TW_F(C, j), P.q, P.f64, moddown_load<K2>(C, a.xP, ct, comp, j, N),
+                                      ModDownStore{accp, dst, P.q});
+}
+
+template <int LOGN>
+__global__ void __launch_bounds__(CfgM<LOGN>::T) kn_ks_moddown(const CtxDev* __restrict__ C, KsDev a) {
+  ks_moddown_body<LOGN, false>(C, a);
+}
+
+template <int LOGN>
+__global__ void __launch_bounds__(CfgM<LOGN>::T) kn_ks_moddown2(const CtxDev* __restrict__ C, KsDev a) {
+  ks_moddown_body<LOGN, true>(C, a);
 }
 
 // Modulus switching (drop q_l, l = L1 - 1, from ciphertexts of L1 primes):
@@ -216,19 +226,21 @@ int ks_decompose(Ctx* c, const KsDev& a, cudaStream_t s) {
 }
 
 int ks_modup(Ctx* c, const KsDev& a, bool skip_diag, cudaStream_t s) {
-  const uint32_t LK = c->L + c->K;
-  const size_t per = skip_diag ? (size_t)c->L * (LK - 1) : (size_t)c->L * LK;
+  const size_t per = c->host.mu_n[skip_diag ? 1 : 0];
   if (!per) return LOLA_OK;
   const size_t units = a.count * per;
   ProfScope ps(c, KI_KS_MODUP, s, units);
   const int g = geometry(c, 1, units);
   if (g != TV_CTA) return ks_modup_cluster(c, a, skip_diag, s, g);
-  LOLA_DISPATCH_CFG(CfgM, c->logn, kn_ks_modup, units, s, c->dev, a, (int)skip_diag);
+  if (c->alpha > 1)
+    LOLA_DISPATCH_CFG(CfgM, c->logn, kn_ks_modup2, units, s, c->dev, a, (int)skip_diag);
+  else
+    LOLA_DISPATCH_CFG(CfgM, c->logn, kn_ks_modup, units, s, c->dev, a, (int)skip_diag);
   return post_launch(c, s);
 }
 
 int ks_intt_p(Ctx* c, const KsDev& a, cudaStream_t s) {
-  const size_t units = a.count * 2;
+  const size_t units = a.count * 2 * c->K;
   ProfScope ps(c, KI_KS_IP_P, s, units);
   const int g = geometry(c, 2, units);
   if (g != TV_CTA) return ks_intt_p_cluster(c, a, s, g);
@@ -241,7 +253,10 @@ int ks_moddown(Ctx* c, const KsDev& a, cudaStream_t s) {
   ProfScope ps(c, KI_KS_MODDOWN, s, units);
   const int g = geometry(c, 3, units);
   if (g != TV_CTA) return ks_moddown_cluster(c, a, s, g);
-  LOLA_DISPATCH_CFG(CfgM, c->logn, kn_ks_moddown, units, s, c->dev, a);
+  if (c->K > 1)
+    LOLA_DISPATCH_CFG(CfgM, c->logn, kn_ks_moddown2, units, s, c->dev, a);
+  else
+    LOLA_DISPATCH_CFG(CfgM, c->logn, kn_ks_moddown, units, s, c->dev, a);
   return post_launch(c, s);
 }
 

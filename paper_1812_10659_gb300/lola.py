@@ -39,7 +39,7 @@ class LolaError(RuntimeError):
 
 class lola_params(C.Structure):
     _fields_ = [("n", C.c_uint32), ("L", C.c_uint32), ("K", C.c_uint32), ("q", C.POINTER(C.c_uint64)),
-                ("k_t", C.c_uint32), ("t", C.POINTER(C.c_uint64))]
+                ("k_t", C.c_uint32), ("t", C.POINTER(C.c_uint64)), ("alpha", C.c_uint32)]
 
 
 class lola_layer(C.Structure):
@@ -172,11 +172,12 @@ def stream_handle(stream) -> int | None:
 
 # ------------------------------------------------------------------ context
 
-def lola_ctx_create(n, q, L, K, t, device=0):
+def lola_ctx_create(n, q, L, K, t, device=0, alpha=1):
+    """alpha: ciphertext primes per key-switching digit (1 or 2)."""
     lib = load()
     q_arr, qp = _u64(q)
     t_arr, tp = _u64(t)
-    p = lola_params(n, L, K, qp, len(t_arr), tp)
+    p = lola_params(n, L, K, qp, len(t_arr), tp, alpha)
     out = P()
     _check(lib.lola_ctx_create(C.byref(p), device, C.byref(out)))
     return out

@@ -25,12 +25,12 @@ def lib():
 
 
 def oracle_params(ps: W.ParamSet) -> bfv.Params:
-    return bfv.Params(ps.n, ps.q, ps.L, ps.K, ps.t)
+    return bfv.Params(ps.n, ps.q, ps.L, ps.K, ps.t, ps.alpha)
 
 
 def make_ctx(ps: W.ParamSet):
     L = lib()
-    return L.lola_ctx_create(ps.n, ps.q, ps.L, ps.K, ps.t, device=0)
+    return L.lola_ctx_create(ps.n, ps.q, ps.L, ps.K, ps.t, alpha=ps.alpha, device=0)
 
 
 def ct_stack(cts, kt=1):

@@ -44,7 +44,7 @@ def mnist_residue(ti: int, key_seed: int, enc_seed: int, img_idx: int = 0, msg0:
     message * k_t + ti).  Returns the output ciphertexts as an array
     [message][2][L_out][n] and the output positions (message, slot)."""
     ps = W.params_mnist()
-    P = bfv.Params(ps.n, ps.q, ps.L, ps.K, ps.t)
+    P = bfv.Params(ps.n, ps.q, ps.L, ps.K, ps.t, ps.alpha)
     kt, t = len(ps.t), ps.t[ti]
     net, img = W.mnist_net(), W.image(idx=img_idx)
     layers = W.layers_mnist(net, ps.n, W.MNIST_LEVELS)
@@ -64,7 +64,7 @@ def head(key_seed: int, enc_seed: int, idx: int = 0):
     output ciphertexts [message][2][L][n], output positions and the plan's
     rotation steps."""
     ps = W.params_head()
-    P = bfv.Params(ps.n, ps.q, ps.L, ps.K, ps.t)
+    P = bfv.Params(ps.n, ps.q, ps.L, ps.K, ps.t, ps.alpha)
     n, t = ps.n, ps.t[0]
     Wh = W.head_weights()
     layers = W.layers_head(Wh, n)

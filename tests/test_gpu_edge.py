@@ -158,14 +158,15 @@ def test_hoisted_rotation_in_step_chunks():
         Lb.lola_ctx_destroy(ctx)
 
 
-@pytest.mark.parametrize("L", [1, 2, 5])
-def test_key_switch_at_full_ring(L):
-    # n = 16384 with a special prime (2-CTA cluster transforms): rotation and
-    # relinearisation (L = 1: inner products in scratch of their own; L >= 2:
-    # in place over the digit rows)
+@pytest.mark.parametrize("L,K,alpha", [(1, 1, 1), (2, 1, 1), (5, 1, 1), (2, 2, 2), (5, 2, 2), (4, 2, 1)])
+def test_key_switch_at_full_ring(L, K, alpha):
+    # n = 16384 with special primes (cluster transforms): rotation and
+    # relinearisation (one digit: inner products in scratch of their own;
+    # two or more: in place over the digit rows); alpha = 2: digits of two
+    # primes with two special primes (L = 2: one digit; L = 5: 2 + 2 + 1)
     need_gpu()
     n = 16384
-    ps = W.ParamSet(f"full_ring_L{L}", n, W.Q60[:L + 1], L, 1, [W.T30[0]])
+    ps = W.ParamSet(f"full_ring_L{L}_K{K}_a{alpha}", n, W.Q60[:L + K], L, K, [W.T30[0]], alpha)
     g = np.random.default_rng(100 + L)
     slots = [g.integers(0, 1 << 12, n), g.integers(0, 1 << 12, n)]
     # one 60-bit prime at n = 16384 has no noise budget for a square: words only

@@ -69,14 +69,16 @@ def test_dense64_bit_exact_vs_oracle():
         Lb.lola_ctx_destroy(ctx)
 
 
-@pytest.mark.parametrize("levels", [None, (4, 2), (3, 1)])
-def test_mini_mnist_bit_exact_vs_oracle(levels):
+@pytest.mark.parametrize("levels,K,alpha", [(None, 1, 1), ((4, 2), 1, 1), ((3, 1), 1, 1), ((4, 2), 2, 2),
+                                            ((3, 1), 2, 2)])
+def test_mini_mnist_bit_exact_vs_oracle(levels, K, alpha):
     # levels: modulus switching after each square (every later ciphertext,
-    # including the relinearisation at level 4 or 3, compared word for word)
+    # including the relinearisation at level 4 or 3, compared word for word);
+    # K = 2, alpha = 2: key-switching digits of two primes (the MNIST workload's)
     need_gpu()
     Lb = lib()
     n = 1024
-    ps = W.params_small(n, L=5, K=1, t=W.T30[:1])
+    ps = W.params_small(n, L=5, K=K, t=W.T30[:1], alpha=alpha)
     P = oracle_params(ps)
     t = ps.t[0]
     mnet = W.mnist_net(seed=7, maps=2, hidden=12, classes=3, h=12, w=12, k=3, stride=2)
@@ -285,7 +287,7 @@ def test_mini_lola_dense_bit_exact_vs_oracle(levels):
 def test_full_lola_dense_batched_decrypts_to_integer_network():
     need_gpu()
     Lb = lib()
-    ps = W.params_mnist(6)
+    ps = W.params_lola_dense(6)
     n = ps.n
     mnet = W.mnist_net()
     layers = W.layers_lola_dense(mnet, n, levels=W.LOLA_DENSE_LEVELS)

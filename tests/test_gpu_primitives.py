@@ -44,11 +44,15 @@ def test_ntt_matches_oracle_transform(n, L):
         Lb.lola_ctx_destroy(ctx)
 
 
-@pytest.fixture(scope="module", params=[("K1", 32, 3, 1), ("K0", 32, 3, 0), ("K1big", 1024, 4, 1)])
+# K1 / K0: one digit per prime with one / no special prime; K2a2: digits of
+# two primes (the last single for odd L) with two special primes; K2a1: one
+# digit per prime with two special primes
+@pytest.fixture(scope="module", params=[("K1", 32, 3, 1, 1), ("K0", 32, 3, 0, 1), ("K1big", 1024, 4, 1, 1),
+                                        ("K2a2", 32, 5, 2, 2), ("K2a2big", 1024, 4, 2, 2), ("K2a1", 32, 3, 2, 1)])
 def setup(request):
     need_gpu()
-    _, n, L, K = request.param
-    ps = W.params_small(n, L=L, K=K, t=[65537, W.T30[0]])
+    _, n, L, K, alpha = request.param
+    ps = W.params_small(n, L=L, K=K, t=[65537, W.T30[0]], alpha=alpha)
     P = oracle_params(ps)
     steps = [1, 3, n // 4]
     seed = 4242
@@ -69,11 +73,12 @@ def test_keys_match_oracle(setup):
     assert list(s) == list(ok.sk.s)
     pk = Lb.lola_keys_export(ctx, sk, 1).reshape(2, P.L, P.n)
     assert np.array_equal(pk[0], ok.pk.p0) and np.array_equal(pk[1], ok.pk.p1)
-    rk = Lb.lola_keys_export(ctx, sk, 2).reshape(2, P.L, P.L + P.K, P.n)
+    D = len(P.groups)
+    rk = Lb.lola_keys_export(ctx, sk, 2).reshape(2, D, P.L + P.K, P.n)
     assert np.array_equal(rk[0], ok.relin.b) and np.array_equal(rk[1], ok.relin.a)
     for step in S["steps"] + [0]:
         g = bfv.galois_row_swap(P.n) if step == 0 else bfv.galois_for_rotation(P.n, step)
-        gk = Lb.lola_keys_export(ctx, sk, 3, step).reshape(2, P.L, P.L + P.K, P.n)
+        gk = Lb.lola_keys_export(ctx, sk, 3, step).reshape(2, D, P.L + P.K, P.n)
         assert np.array_equal(gk[0], ok.galois[g].b) and np.array_equal(gk[1], ok.galois[g].a), step
     # the evaluation-only handle holds no secret or public key
     with pytest.raises(Lb.LolaError):

@@ -18,7 +18,7 @@ from oracle import bfv, encoding, ring
 
 def mkparams(n, L=3, K=1, t=65537):
     ps = W.params_small(n, L=L, K=K, t=[t])
-    return bfv.Params(ps.n, ps.q, ps.L, ps.K, ps.t)
+    return bfv.Params(ps.n, ps.q, ps.L, ps.K, ps.t, ps.alpha)
 
 
 def row_shift(v, k):
@@ -269,7 +269,7 @@ def test_noise_margin_positive_and_shrinks(small):
 def test_full_size_rotation_and_square():
     """n = 16384, L = 5, K = 1: the MNIST-network parameters."""
     ps = W.params_mnist()
-    P = bfv.Params(ps.n, ps.q, ps.L, ps.K, ps.t)
+    P = bfv.Params(ps.n, ps.q, ps.L, ps.K, ps.t, ps.alpha)
     keys = bfv.keygen(P, 8, rotations=[1], relin=True)
     t = ps.t[0]
     v = np.random.default_rng(8).integers(0, 16, P.n)

@@ -181,7 +181,7 @@ def test_dense64_plan_wraps_mod_t():
 
 def test_dense64_encrypted_oracle_run():
     ps = W.params_dense64()
-    P = bfv.Params(ps.n, ps.q, ps.L, ps.K, ps.t)
+    P = bfv.Params(ps.n, ps.q, ps.L, ps.K, ps.t, ps.alpha)
     keys = bfv.keygen(P, W.DEFAULT_SEED, rotations=[1, 2, 4, 8, 16, 32], relin=True)
     t = 65537
     Wd, x = W.dense_weights(), W.dense_vector()
@@ -209,7 +209,7 @@ def mini_mnist():
 def test_mini_mnist_encrypted_oracle_run():
     n = 1024
     ps = W.params_small(n, L=5, K=1, t=W.T30[:1])
-    P = bfv.Params(ps.n, ps.q, ps.L, ps.K, ps.t)
+    P = bfv.Params(ps.n, ps.q, ps.L, ps.K, ps.t, ps.alpha)
     net, img = mini_mnist()
     layers = W.layers_mnist(net, n)
     assert layers[3]["copies"] == 8 and -(-12 // 8) == 2
@@ -316,7 +316,7 @@ def mini_lola_dense_layers(n):
 def test_mini_lola_dense_encrypted_oracle_run():
     n = 1024
     ps = W.params_small(n, L=5, K=1, t=W.T30[:1])
-    P = bfv.Params(ps.n, ps.q, ps.L, ps.K, ps.t)
+    P = bfv.Params(ps.n, ps.q, ps.L, ps.K, ps.t, ps.alpha)
     net, img, width, layers = mini_lola_dense_layers(n)
     t = ps.t[0]
 
@@ -390,7 +390,7 @@ def mini_cifar():
 def test_mini_cifar_encrypted_oracle_run():
     n = 1024
     ps = W.params_small(n, L=5, K=1, t=W.T30[:1])
-    P = bfv.Params(ps.n, ps.q, ps.L, ps.K, ps.t)
+    P = bfv.Params(ps.n, ps.q, ps.L, ps.K, ps.t, ps.alpha)
     net, img = mini_cifar()
     layers = W.layers_cifar(net, n)
     t = ps.t[0]
@@ -454,7 +454,7 @@ def test_full_mnist_with_modulus_switching_keeps_its_noise_margin():
     20 bits of noise margin (about a minute on one core)."""
     n = 16384
     ps = W.params_mnist()
-    P = bfv.Params(ps.n, ps.q, ps.L, ps.K, ps.t)
+    P = bfv.Params(ps.n, ps.q, ps.L, ps.K, ps.t, ps.alpha)
     t = ps.t[0]
     net, img = W.mnist_net(), W.image()
     layers = W.layers_mnist(net, n, W.MNIST_LEVELS)

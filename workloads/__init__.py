@@ -39,13 +39,14 @@ T30 = [1073643521, 1073479681, 1073184769, 1073053697]
 class ParamSet:
     name: str
     n: int
-    q: list          # L + K primes, special prime last
+    q: list          # L + K primes, special primes last
     L: int
     K: int
     t: list
+    alpha: int = 1   # ciphertext primes per key-switching digit
 
     def as_dict(self):
-        return dict(n=self.n, q=list(self.q), L=self.L, K=self.K, t=list(self.t))
+        return dict(n=self.n, q=list(self.q), L=self.L, K=self.K, t=list(self.t), alpha=self.alpha)
 
 
 def params_dense64() -> ParamSet:
@@ -56,9 +57,29 @@ def params_dense64() -> ParamSet:
 
 def params_mnist(L: int = 5) -> ParamSet:
     """MNIST-shaped network and transfer-learning head: n = 16384, L
-    ciphertext primes of 60 bits plus one 60-bit special prime, three ~30-bit
-    plaintext CRT moduli."""
+    ciphertext primes of 60 bits plus one 60-bit special prime, one-prime
+    key-switching digits, three ~30-bit plaintext CRT moduli.  (Two-prime
+    digits with two special primes also hold the noise, +25.2 bits at the
+    output against +24.2, and need fewer mod-up transforms, but their second
+    special prime doubles the INTT mod P and widens mod-down's load: measured
+    262.9 against 269.0 inferences/s, so the default keeps one-prime digits;
+    params_mnist_grouped gives the other set.)"""
     return ParamSet(f"mnist_n16384_L{L}", 16384, Q60[:L + 1], L, 1, T30[:3])
+
+
+def params_mnist_grouped(L: int = 5) -> ParamSet:
+    """The MNIST-shaped network's parameters with key-switching digits of two
+    primes (the last one single when L is odd) and two 60-bit special
+    primes (420 bits at L = 5, within the 438-bit budget)."""
+    return ParamSet(f"mnist_grouped_n16384_L{L}", 16384, Q60[:L + 2], L, 2, T30[:3], alpha=2)
+
+
+def params_lola_dense(L: int = 6) -> ParamSet:
+    """LoLa-Dense (App. C): n = 16384, six 60-bit primes plus one 60-bit
+    special prime (420 bits, within the 438-bit budget; a second special
+    prime would exceed it), one-prime key-switching digits, three ~30-bit
+    plaintext CRT moduli."""
+    return ParamSet(f"lola_dense_n16384_L{L}", 16384, Q60[:L + 1], L, 1, T30[:3])
 
 
 def params_cifar(L: int = 6) -> ParamSet:
@@ -81,9 +102,9 @@ def params_sweep(n: int, L: int) -> ParamSet:
     return ParamSet(f"sweep_n{n}_L{L}", n, Q60[:L + 1], L, 1, T30[:1])
 
 
-def params_small(n: int, L: int = 3, K: int = 1, t=None) -> ParamSet:
+def params_small(n: int, L: int = 3, K: int = 1, t=None, alpha: int = 1) -> ParamSet:
     """Reduced ring sizes for fast parity tests (same 60-bit primes)."""
-    return ParamSet(f"small_n{n}_L{L}_K{K}", n, Q60[:L + K], L, K, list(t or T30[:1]))
+    return ParamSet(f"small_n{n}_L{L}_K{K}_a{alpha}", n, Q60[:L + K], L, K, list(t or T30[:1]), alpha)
 
 
 def rng(seed: int, purpose: int) -> np.random.Generator:
