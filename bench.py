@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--batch", type=int, default=None,
                     help="requests per batched step (per GPU; default 16, 2 for cifar)")
     ap.add_argument("--plain", type=int, default=8, help="single-request evaluations for plain latency")
+    ap.add_argument("--paper-last-layer", action="store_true",
+                    help="mnist / lola_dense: the paper's interleaved row-major last layer (rotate-and-sum over "
+                         "all n slots, 14 rotations per output) instead of the sum over the occupied slots (7)")
     ap.add_argument("--grouped-digits", action="store_true",
                     help="mnist: key-switching digits of two primes with two special primes")
     ap.add_argument("--L", type=int, default=None,
@@ -99,22 +102,41 @@ def parse():
 HEAD_L = 3
 
 # per-residue operation counts of one inference (the plan's, checked by the CPU tests)
-OP_COUNTS = {"mnist": {"rot": 224, "square": 2, "mul_plain": 24, "mul_scalar": 125, "add": 344},
-             "lola_dense": {"rot": 326, "square": 2, "mul_plain": 61, "mul_scalar": 125, "add": 422},
+OP_COUNTS = {"mnist": {"rot": 154, "square": 2, "mul_plain": 24, "mul_scalar": 125, "add": 274},
+             "mnist_paper": {"rot": 224, "square": 2, "mul_plain": 24, "mul_scalar": 125, "add": 344},
+             "lola_dense": {"rot": 256, "square": 2, "mul_plain": 61, "mul_scalar": 125, "add": 352},
+             "lola_dense_paper": {"rot": 326, "square": 2, "mul_plain": 61, "mul_scalar": 125, "add": 422},
              "cifar": {"rot": 57273, "square": 2, "mul_plain": 8162, "mul_scalar": 15936, "add": 77200},
              "head": {"rot": 339, "square": 0, "mul_plain": 52, "mul_scalar": 0, "add": 339},
              "dense64": {"rot": 6, "square": 1, "mul_plain": 1, "mul_scalar": 0, "add": 6}}
 # the networks with modulus switching (to 4 primes after the first square,
-# to 2 after the second): the same counts split by level
+# to 2 after the second): the same counts split by level.  "mnist" and
+# "lola_dense" sum the last layer's dot products over the interleaved
+# vector's occupied slots (7 rotations per output); "_paper" is the paper's
+# interleaved row-major product (14 per output).
 OP_COUNTS_LEVELS = {"mnist": {5: {"rot": 4, "square": 1, "mul_plain": 0, "mul_scalar": 125, "add": 124},
                               4: {"rot": 80, "square": 1, "mul_plain": 14, "mul_scalar": 0, "add": 80},
-                              2: {"rot": 140, "square": 0, "mul_plain": 10, "mul_scalar": 0, "add": 140}},
+                              2: {"rot": 70, "square": 0, "mul_plain": 10, "mul_scalar": 0, "add": 70}},
+                    "mnist_paper": {5: {"rot": 4, "square": 1, "mul_plain": 0, "mul_scalar": 125, "add": 124},
+                                    4: {"rot": 80, "square": 1, "mul_plain": 14, "mul_scalar": 0, "add": 80},
+                                    2: {"rot": 140, "square": 0, "mul_plain": 10, "mul_scalar": 0, "add": 140}},
                     "lola_dense": {6: {"rot": 28, "square": 1, "mul_plain": 25, "mul_scalar": 125, "add": 124},
                                    4: {"rot": 158, "square": 1, "mul_plain": 26, "mul_scalar": 0, "add": 158},
-                                   2: {"rot": 140, "square": 0, "mul_plain": 10, "mul_scalar": 0, "add": 140}},
+                                   2: {"rot": 70, "square": 0, "mul_plain": 10, "mul_scalar": 0, "add": 70}},
+                    "lola_dense_paper": {6: {"rot": 28, "square": 1, "mul_plain": 25, "mul_scalar": 125, "add": 124},
+                                         4: {"rot": 158, "square": 1, "mul_plain": 26, "mul_scalar": 0, "add": 158},
+                                         2: {"rot": 140, "square": 0, "mul_plain": 10, "mul_scalar": 0, "add": 140}},
                     "cifar": {6: {"rot": 83, "square": 1, "mul_plain": 2, "mul_scalar": 15936, "add": 15936},
                               4: {"rot": 57050, "square": 1, "mul_plain": 8150, "mul_scalar": 0, "add": 61124},
                               2: {"rot": 140, "square": 0, "mul_plain": 10, "mul_scalar": 0, "add": 140}}}
+SUPPORT_SUM_WORKLOADS = ("mnist", "lola_dense")
+
+
+def counts_key(workload: str, paper_plan: bool) -> str:
+    """Key of OP_COUNTS for a workload and its last-layer variant."""
+    return workload + "_paper" if paper_plan and workload in SUPPORT_SUM_WORKLOADS else workload
+
+
 WORKLOAD_NAME = {"mnist": "mnist_lola_n16384", "lola_dense": "lola_dense_n16384", "cifar": "cifar_lola_n16384",
                  "head": "transfer_head_n16384", "dense64": "dense64_n4096"}
 
@@ -186,7 +208,7 @@ def workload_params(workload, L):
         workload, W.params_mnist)(L)
 
 
-def oracle_sample(n_rot=1, n_sq=1, workload="mnist", L=5, levels=None):
+def oracle_sample(n_rot=1, n_sq=1, workload="mnist", L=5, levels=None, paper_plan=False):
     """Time the CPU oracle's operations on the network's parameters (one CRT
     residue) and scale by the network's operation counts for one inference
     over all residues; with modulus switching, each level's operations are
@@ -209,7 +231,8 @@ def oracle_sample(n_rot=1, n_sq=1, workload="mnist", L=5, levels=None):
         for _ in range(reps):
             fn()
         return (time.perf_counter() - t0) / reps
-    by_level = OP_COUNTS_LEVELS[workload] if levels else {L: OP_COUNTS[workload]}
+    key = counts_key(workload, paper_plan)
+    by_level = OP_COUNTS_LEVELS[key] if levels else {L: OP_COUNTS[key]}
     sec, parts, total = 0.0, [], {}
     for lv, counts in sorted(by_level.items(), reverse=True):
         Pl, kl = bfv.params_at_level(P, lv), bfv.keys_at_level(keys, lv)
@@ -251,7 +274,7 @@ def _slot_rotation_steps(layers, n, t, st):
     return sorted(seen)
 
 
-def oracle_residue_inference(workload, L, levels, ti):
+def oracle_residue_inference(workload, L, levels, ti, paper_plan=False):
     """One CRT residue of one end-to-end oracle inference (run in a spawned
     worker): key generation, encryption of one synthetic request, the whole
     layer list on ciphertexts, decryption, and a check against the integer
@@ -265,7 +288,7 @@ def oracle_residue_inference(workload, L, levels, ti):
     n, t, kt = ps.n, ps.t[ti], len(ps.t)
     if workload == "mnist":
         mnet, img = W.mnist_net(), W.image()
-        layers = W.layers_mnist(mnet, n, levels)
+        layers = W.layers_mnist(mnet, n, levels, support_sum=not paper_plan)
         msgs, pos = OL.pack_convolution(img, mnet.kh, mnet.kw, mnet.stride, n)
         want = plain_mnist(img, mnet)
     elif workload == "dense64":
@@ -303,7 +326,7 @@ def oracle_residue_inference(workload, L, levels, ti):
             "ok": out == [w % t for w in want], "ops": dict(ev.counts)}
 
 
-def oracle_e2e_inference(workload="mnist", L=5, levels=None) -> dict:
+def oracle_e2e_inference(workload="mnist", L=5, levels=None, paper_plan=False) -> dict:
     """One whole inference on the CPU oracle, its CRT residues in parallel
     spawned processes (one core each).  Seconds per phase are the slowest
     residue's; `eval_s` (the layer list on ciphertexts) is the figure the
@@ -313,7 +336,8 @@ def oracle_e2e_inference(workload="mnist", L=5, levels=None) -> dict:
     kt = len(workload_params(workload, L).t)
     t0 = time.perf_counter()
     with ProcessPoolExecutor(max_workers=kt, mp_context=multiprocessing.get_context("spawn")) as ex:
-        res = list(ex.map(oracle_residue_inference, [workload] * kt, [L] * kt, [levels] * kt, range(kt)))
+        res = list(ex.map(oracle_residue_inference, [workload] * kt, [L] * kt, [levels] * kt, range(kt),
+                          [paper_plan] * kt))
     wall = time.perf_counter() - t0
     agg = {k: max(r[k] for r in res) for k in ("keygen_s", "encrypt_s", "eval_s", "decrypt_s")}
     agg.update({"ok": all(r["ok"] for r in res), "residues": kt, "wall_s": wall, "ops_per_residue": res[0]["ops"]})
@@ -323,13 +347,13 @@ def oracle_e2e_inference(workload="mnist", L=5, levels=None) -> dict:
 E2E_WORKLOADS = ("mnist", "head", "dense64")
 
 
-def cpu_baseline_obj(workload="mnist", L=5, levels=None):
+def cpu_baseline_obj(workload="mnist", L=5, levels=None, paper_plan=False):
     """The oracle timed on this host: for the MNIST-shaped network and the
     head, one whole inference end to end (residues in parallel processes);
     for the larger networks, per-operation samples scaled by the plan's
     operation counts."""
     if workload in E2E_WORKLOADS:
-        r = oracle_e2e_inference(workload, L, levels)
+        r = oracle_e2e_inference(workload, L, levels, paper_plan)
         return {"value": 1.0 / r["eval_s"], "unit": "inferences/s", "cores": r["residues"],
                 "kind": "oracle end-to-end",
                 "sample": (f"one whole inference of one synthetic request: the layer list on ciphertexts for all "
@@ -339,7 +363,7 @@ def cpu_baseline_obj(workload="mnist", L=5, levels=None):
                 "decrypt_s": r["decrypt_s"], "ops_per_residue": r["ops_per_residue"],
                 "sample_wall_s": round(r["wall_s"], 1)}
     t0 = time.perf_counter()
-    sec, desc = oracle_sample(workload=workload, L=L, levels=levels)
+    sec, desc = oracle_sample(workload=workload, L=L, levels=levels, paper_plan=paper_plan)
     return {"value": 1.0 / sec, "unit": "inferences/s", "cores": 1, "kind": "oracle (per-op samples x op counts)",
             "sample": desc, "sample_wall_s": round(time.perf_counter() - t0, 1)}
 
@@ -356,18 +380,18 @@ def run_reference(args):
     if rank != 0:
         return
     for _ in range(args.warmup):
-        oracle_sample(1, 1, args.workload, args.L, args.levels)
+        oracle_sample(1, 1, args.workload, args.L, args.levels, args.paper_last_layer)
     secs = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        s, desc = oracle_sample(1, 1, args.workload, args.L, args.levels)
+        s, desc = oracle_sample(1, 1, args.workload, args.L, args.levels, args.paper_last_layer)
         secs.append(s)
     wall = time.perf_counter() - t0
     sec = statistics.median(secs)
     value = 1.0 / sec
     e2e_run = None
     if args.workload in E2E_WORKLOADS and not args.no_cpu_baseline:
-        r = oracle_e2e_inference(args.workload, args.L, args.levels)
+        r = oracle_e2e_inference(args.workload, args.L, args.levels, args.paper_last_layer)
         e2e_run = {"value": 1.0 / r["eval_s"], "unit": "inferences/s", "cores": r["residues"],
                    "eval_s": r["eval_s"], "correct": r["ok"], "wall_s": round(r["wall_s"], 1)}
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "inferences/s", "n_gpus": args.gpus,
@@ -528,7 +552,7 @@ def run_ours(args):
         net = L.lola_net_create(ctx, {"repr": "convolution", "n_msgs": 3 * cnet.k1 * cnet.k1,
                                       "n_elems": cnet.o1 * cnet.o1}, layers)
     elif args.workload == "lola_dense":
-        layers = W.layers_lola_dense(mnet, n, levels=args.levels)
+        layers = W.layers_lola_dense(mnet, n, levels=args.levels, support_sum=not args.paper_last_layer)
         img_slots = np.asarray(W.dense_image_slots(), dtype=np.int64)
         net = L.lola_net_create(ctx, {"repr": "dense", "n_msgs": 1, "n_elems": 784, "slot": img_slots}, layers)
     elif args.workload == "head":
@@ -542,7 +566,7 @@ def run_ours(args):
         net = L.lola_net_create(ctx, {"repr": "stacked", "n_msgs": 1, "n_elems": Wd.shape[1], "d": 6,
                                       "copies": copies}, layers)
     else:
-        layers = W.layers_mnist(mnet, n, args.levels)
+        layers = W.layers_mnist(mnet, n, args.levels, support_sum=not args.paper_last_layer)
         net = L.lola_net_create(ctx, {"repr": "convolution", "n_msgs": 25, "n_elems": 169}, layers)
     n_in, n_out = net.shape()
     steps_needed = net.rotation_steps()
@@ -787,7 +811,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline_obj(args.workload, args.L, args.levels)
+        cpu = cpu_baseline_obj(args.workload, args.L, args.levels, args.paper_last_layer)
 
     if rank == 0:
         srt = sorted(step_ms)
@@ -797,6 +821,9 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": WORKLOAD_NAME[args.workload], "batch_per_gpu": B, "n": n, "L": Lq, "K": ps.K, "k_t": kt,
                        "key_switch_digit_primes": ps.alpha,
+                       "last_layer": ("interleaved row-major, rotate-and-sum over all n slots (the paper's)"
+                                      if args.paper_last_layer or args.workload not in SUPPORT_SUM_WORKLOADS else
+                                      "interleaved row-major, rotate-and-sum over the occupied slots only"),
                        "levels": [Lq] + list(args.levels or []),
                        "autotune": ({"table": tune["table"], "seconds": round(t_tune, 2)} if tune else "defaults"),
                        "aux_primes": len(L.lola_ctx_aux_primes(ctx)), "parallelism": f"replicas x{world}",
@@ -973,7 +1000,8 @@ def run_serve(args):
         L.lola_autotune(ctx2)
         L.lola_autotune(ctx4)
     mnet, Wh = W.mnist_net(), W.head_weights()
-    d2, l2 = {"repr": "convolution", "n_msgs": 25, "n_elems": 169}, W.layers_mnist(mnet, n, W.MNIST_LEVELS)
+    d2, l2 = {"repr": "convolution", "n_msgs": 25, "n_elems": 169}, W.layers_mnist(mnet, n, W.MNIST_LEVELS,
+                                                                                        support_sum=True)
     d4, l4 = {"repr": "dense", "n_msgs": 1, "n_elems": 4096}, W.layers_head(Wh, n)
     keys = {}
     for name, ctx, d, layers in (("mnist", ctx2, d2, l2), ("head", ctx4, d4, l4)):

@@ -311,8 +311,15 @@ typedef enum {
   LOLA_LAYER_PLACE = 10,               /* k dense messages -> 1 with element e at slot weights[e] (one target
                                           per element, both slot rows; Sec. 6.2 combine of 83 maps); the
                                           messages must hold zeros outside their elements' slots */
-  LOLA_LAYER_MOD_SWITCH = 11           /* modulus switching to the first d primes of Q (lola_mod_switch);
+  LOLA_LAYER_MOD_SWITCH = 11,          /* modulus switching to the first d primes of Q (lola_mod_switch);
                                           no slot changes, later layers run on d primes; not in the paper */
+  LOLA_LAYER_INTERLEAVED_ROWMAJOR_SUPPORT = 12
+                                       /* interleaved/dense -> one message per row, each dot product summed
+                                          over the vector's occupied slots only: when they form one cyclic run
+                                          of 2^k slots modulo a period 2^p in each row, rotations 1 .. 2^(k-1),
+                                          then 2^p .. n/4, then the row swap if both rows are occupied (the
+                                          fewest such steps; the full support gives the interleaved row-major
+                                          product's); output r at the one slot holding the whole sum */
 } lola_layer_op;
 
 typedef struct {

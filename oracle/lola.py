@@ -19,6 +19,8 @@ Layer list entries (dicts):
   {"op": "stacked_rowmajor", "weights": W, "d": d, "copies": c}
                                                         Sec. 4.2.2 stacked vector - row major
   {"op": "interleaved_rowmajor", "weights": W}          Sec. 4.2.2 interleaved vector - row major
+  {"op": "interleaved_rowmajor_support", "weights": W}  the same product, each dot product summed
+                                                        over the vector's occupied slots only
   {"op": "dense_rowmajor", "weights": W}                Sec. 4.2.2 dense vector - row major
   {"op": "sparse_colmajor", "weights": W}               Sec. 4.2.2 sparse vector - column major
   {"op": "mod_switch", "L": Lv}                         keep the first Lv primes of Q (modulus
@@ -357,6 +359,69 @@ def layer_interleaved_rowmajor(ev, st: State, W) -> State:
     return State(outs, [(o, 0) for o in range(len(W))])
 
 
+def support_sum_shifts(slots, n: int):
+    """Rotate-and-sum steps that add up every slot of `slots` (occupied slot
+    positions of one message) into one slot, and that slot.
+
+    Reading (not in the paper, whose interleaved row-major product sums all
+    n slots with log2(n) rotations): when the occupied slots of each row lie
+    in one cyclic run of 2^k slots modulo a period 2^p, the run shifts 1, 2,
+    ..., 2^(k-1), then the period shifts 2^p, ..., n/4 (right rotations
+    within the rows), then the row swap if both rows are occupied, add every
+    occupied slot exactly once into one slot.  The pair (p, k) with the
+    fewest steps is taken, the smallest p on ties; the full support (p = 0)
+    gives the paper's 1, 2, ..., n/4 and the row swap.  The result slot is
+    the smallest slot whose sum covers every occupied slot, found by running
+    the steps on occupancy counts."""
+    h = n // 2
+    logh = h.bit_length() - 1
+    rows = sorted({s // h for s in slots})
+    cols = sorted({s % h for s in slots})
+    best = None
+    for lp in range(logh + 1):
+        per = 1 << lp
+        res = sorted({c % per for c in cols})
+        for k in range(lp + 1):
+            run = 1 << k
+            if any(all((c - o) % per < run for c in res) for o in res):
+                cand = (k + (logh - lp) + (1 if len(rows) > 1 else 0), lp, k)
+                if best is None or cand < best:
+                    best = cand
+                break
+    _, lp, k = best
+    shifts = [1 << j for j in range(k)] + [1 << j for j in range(lp, logh)] + ([0] if len(rows) > 1 else [])
+    cnt = np.zeros(n, dtype=np.int64)
+    cnt[list(slots)] = 1
+    for sh in shifts:
+        if sh == 0:
+            cnt = cnt + np.concatenate([cnt[h:], cnt[:h]])
+        else:
+            cnt = cnt + np.concatenate([np.roll(cnt[:h], sh), np.roll(cnt[h:], sh)])
+    full = np.nonzero(cnt == len(set(slots)))[0]
+    return shifts, int(full[0])
+
+
+def layer_interleaved_rowmajor_support(ev, st: State, W) -> State:
+    """Interleaved vector - row major with each dot product summed over the
+    vector's occupied slots only (support_sum_shifts): the products are
+    those of layer_interleaved_rowmajor (column i of W at element i's
+    slot), the rotate-and-sum uses the support's shifts, and output o is
+    message o at the one slot that holds the whole sum."""
+    n = ev.n
+    assert len(st.msgs) == 1 and len(W[0]) == len(st.pos)
+    slots = np.array([slot for (_, slot) in st.pos], dtype=np.int64)
+    shifts, p = support_sum_shifts([int(x) for x in slots], n)
+    outs = []
+    for o in range(len(W)):
+        V = np.zeros(n, dtype=np.int64)
+        V[slots] = np.asarray(W[o], dtype=np.int64)
+        y = ev.mul_plain(st.msgs[0], V)
+        for sh in shifts:
+            y = ev.add(y, ev.rot_rows(y) if sh == 0 else ev.rot(y, sh))
+        outs.append(y)
+    return State(outs, [(o, p) for o in range(len(W))])
+
+
 def layer_sparse_colmajor(ev, st: State, W) -> State:
     """Sparse vector - column major (Sec. 4.2.2): W v = sum_i v_i c^i.
     Message i holds v_i in every slot (sparse representation); multiply it
@@ -394,6 +459,8 @@ def run_network(ev, layers, st: State) -> State:
             st = layer_stacked_rowmajor(ev, st, L["weights"], L["d"], L["copies"])
         elif op in ("interleaved_rowmajor", "dense_rowmajor"):
             st = layer_interleaved_rowmajor(ev, st, L["weights"])
+        elif op == "interleaved_rowmajor_support":
+            st = layer_interleaved_rowmajor_support(ev, st, L["weights"])
         elif op == "sparse_colmajor":
             st = layer_sparse_colmajor(ev, st, L["weights"])
         elif op == "mod_switch":

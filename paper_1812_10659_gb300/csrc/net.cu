@@ -539,6 +539,115 @@ static int layer_rowmajor_sparse(Builder& b, const lola_layer& L, Repr& r, bool 
   return LOLA_OK;
 }
 
+// Rotate-and-sum steps that add every occupied slot of a message into one
+// slot, and that slot (the support-summed row-major product).  When the
+// occupied slots of each row lie in one cyclic run of 2^k slots modulo a
+// period 2^p, the right rotations 1 .. 2^(k-1) (the run), then 2^p .. n/4
+// (the period), then the row swap if both rows are occupied add each
+// occupied slot exactly once into one slot; the (p, k) with the fewest steps
+// is taken, the smallest p on ties.  The full support (p = 0) gives the
+// interleaved row-major product's 1, 2, ..., n/4 and the row swap.  The
+// result slot is the smallest slot whose occupancy count after the steps
+// equals the number of occupied slots.
+static void support_sum_shifts(const std::vector<uint32_t>& slots, uint32_t n, std::vector<int32_t>* shifts,
+                               uint32_t* result_slot) {
+  const uint32_t h = n / 2;
+  uint32_t logh = 0;
+  while ((1u << logh) < h) ++logh;
+  std::set<uint32_t> rows, cols;
+  for (uint32_t s : slots) {
+    rows.insert(s / h);
+    cols.insert(s % h);
+  }
+  int best = -1;
+  uint32_t best_p = 0, best_k = 0;
+  for (uint32_t lp = 0; lp <= logh; ++lp) {
+    const uint32_t per = 1u << lp;
+    std::set<uint32_t> res;
+    for (uint32_t c : cols) res.insert(c % per);
+    for (uint32_t k = 0; k <= lp; ++k) {
+      const uint32_t run = 1u << k;
+      bool ok = false;
+      for (uint32_t o : res) {
+        bool all = true;
+        for (uint32_t c : res)
+          if ((c + per - o) % per >= run) {
+            all = false;
+            break;
+          }
+        if (all) {
+          ok = true;
+          break;
+        }
+      }
+      if (!ok) continue;
+      const int cnt = (int)(k + (logh - lp) + (rows.size() > 1 ? 1 : 0));
+      if (best < 0 || cnt < best) {
+        best = cnt;
+        best_p = lp;
+        best_k = k;
+      }
+      break;
+    }
+  }
+  shifts->clear();
+  for (uint32_t j = 0; j < best_k; ++j) shifts->push_back((int32_t)(1u << j));
+  for (uint32_t j = best_p; j < logh; ++j) shifts->push_back((int32_t)(1u << j));
+  if (rows.size() > 1) shifts->push_back(0);
+  std::vector<uint32_t> cnt(n, 0), nxt(n);
+  for (uint32_t s : slots) cnt[s] = 1;
+  for (int32_t sh : *shifts) {
+    for (uint32_t i = 0; i < n; ++i) {
+      const uint32_t r = i / h, c = i % h;
+      const uint32_t src = sh == 0 ? (r ^ 1) * h + c : r * h + (c + h - (uint32_t)sh) % h;
+      nxt[i] = cnt[i] + cnt[src];
+    }
+    cnt.swap(nxt);
+  }
+  const uint32_t want = (uint32_t)std::set<uint32_t>(slots.begin(), slots.end()).size();
+  *result_slot = 0;
+  for (uint32_t i = 0; i < n; ++i)
+    if (cnt[i] == want) {
+      *result_slot = i;
+      break;
+    }
+}
+
+// Interleaved vector - row major with each dot product summed over the
+// vector's occupied slots only (support_sum_shifts): the products of
+// layer_rowmajor_sparse, the support's rotate-and-sum, output o = message o
+// at the one slot holding the whole sum.
+static int layer_rowmajor_support(Builder& b, const lola_layer& L, Repr& r) {
+  const uint32_t n = b.c->n;
+  if (r.msgs != 1 || (r.kind != LOLA_REPR_INTERLEAVED && r.kind != LOLA_REPR_DENSE))
+    return fail(LOLA_E_REPR, "support-summed row-major product needs one interleaved or dense message");
+  if (!L.weights || L.cols != r.pos.size() || L.rows == 0) return fail(LOLA_E_PARAM, "weights must be rows x vector length");
+  const uint32_t rows = L.rows;
+  std::vector<std::vector<int64_t>> V(rows, std::vector<int64_t>(n, 0));
+  std::vector<uint32_t> slots;
+  for (auto& p : r.pos) slots.push_back(p.second);
+  for (uint32_t o = 0; o < rows; ++o)
+    for (uint32_t i = 0; i < L.cols; ++i) V[o][r.pos[i].second] = L.weights[(size_t)o * L.cols + i];
+  Op mp;
+  mp.kind = OP_MULPT;
+  mp.src = r.reg;
+  mp.src_stride = 0;
+  mp.dst = b.vreg(rows);
+  mp.msgs = rows;
+  mp.pt_first = b.add_plaintexts(V);
+  b.net->ops.push_back(mp);
+  std::vector<int32_t> shifts;
+  uint32_t slot = 0;
+  support_sum_shifts(slots, n, &shifts, &slot);
+  Repr out;
+  out.kind = LOLA_REPR_DENSE;
+  out.msgs = rows;
+  out.reg = b.rotate_and_sum(mp.dst, rows, shifts);
+  for (uint32_t o = 0; o < rows; ++o) out.pos.push_back({o, slot});
+  r = out;
+  return LOLA_OK;
+}
+
 // Sparse vector - column major (Sec. 4.2.2): W v = sum_i v_i c^i.  Message i
 // holds v_i in every slot; multiply it by column i of W laid out densely
 // (slot o = W[o][i]) and add the products.  No rotations; dense result.
@@ -624,6 +733,7 @@ int net_create(Ctx* c, const lola_input* in, const lola_layer* layers, size_t n_
       case LOLA_LAYER_DENSE_ROWMAJOR: rc = layer_rowmajor_sparse(b, L, r, true); break;
       case LOLA_LAYER_SPARSE_COLMAJOR: rc = layer_sparse_colmajor(b, L, r); break;
       case LOLA_LAYER_MOD_SWITCH: rc = layer_mod_switch(b, L, r); break;
+      case LOLA_LAYER_INTERLEAVED_ROWMAJOR_SUPPORT: rc = layer_rowmajor_support(b, L, r); break;
       default: return fail(LOLA_E_PARAM, "unknown layer op");
     }
     if (rc != LOLA_OK) return rc;

@@ -24,10 +24,12 @@ LOLA_KEY_ROW_SWAP = 2
 REPR = {"dense": 1, "sparse": 2, "stacked": 3, "interleaved": 4, "convolution": 5}
 LAYER = {"conv": 1, "combine": 2, "square": 3, "stack": 4, "stacked_rowmajor": 5,
          "interleaved_rowmajor": 6, "dense_rowmajor": 7, "sparse_colmajor": 8, "masked_shifts": 9, "place": 10,
+         "interleaved_rowmajor_support": 12,
          "mod_switch": 11}
 # representation each layer consumes / produces (0 = not checked)
 LAYER_REPR = {"conv": (5, 1), "combine": (1, 1), "square": (0, 0), "stack": (1, 3),
               "stacked_rowmajor": (3, 4), "interleaved_rowmajor": (4, 2), "dense_rowmajor": (1, 2),
+              "interleaved_rowmajor_support": (4, 1),
               "sparse_colmajor": (2, 1), "masked_shifts": (1, 5), "place": (1, 1), "mod_switch": (0, 0)}
 
 

@@ -38,7 +38,8 @@ def rotation_steps(layers, n, t, st):
 
 
 def mnist_residue(ti: int, key_seed: int, enc_seed: int, img_idx: int = 0, msg0: int = 0):
-    """Full MNIST-shaped network (n = 16384, L = 5 -> 4 -> 2) for CRT residue
+    """Full MNIST-shaped network (n = 16384, L = 5 -> 4 -> 2, the last layer
+    summed over the occupied slots as bench.py runs it) for CRT residue
     ti of image img_idx, whose 25 messages are messages msg0 ... msg0 + 24 of
     a batch encrypted with k_t = len(t) residues per message (ciphertext id =
     message * k_t + ti).  Returns the output ciphertexts as an array
@@ -47,7 +48,7 @@ def mnist_residue(ti: int, key_seed: int, enc_seed: int, img_idx: int = 0, msg0:
     P = bfv.Params(ps.n, ps.q, ps.L, ps.K, ps.t, ps.alpha)
     kt, t = len(ps.t), ps.t[ti]
     net, img = W.mnist_net(), W.image(idx=img_idx)
-    layers = W.layers_mnist(net, ps.n, W.MNIST_LEVELS)
+    layers = W.layers_mnist(net, ps.n, W.MNIST_LEVELS, support_sum=True)
     keys = bfv.keygen(P, key_seed, rotations=MNIST_STEPS, relin=True, row_swap=True)
     msgs, pos = OL.pack_convolution(img, net.kh, net.kw, net.stride, ps.n)
     cts = [bfv.encrypt(P, keys.pk, encoding.encode(m, t), t, enc_seed, (msg0 + i) * kt + ti)

@@ -40,7 +40,7 @@ def test_plain_cifar_matches_oracle_integer_network():
     assert bench.plain_cifar(img, net) == OL.int_dense(x, net.w3)
 
 
-@pytest.mark.parametrize("workload", ["mnist", "lola_dense", "cifar", "head"])
+@pytest.mark.parametrize("workload", ["mnist", "mnist_paper", "lola_dense", "lola_dense_paper", "cifar", "head"])
 def test_op_counts_by_level_match_the_plan(workload):
     """bench.py's per-level operation counts (used to scale the oracle's
     per-operation times) are the plan's, counted on slot vectors with the
@@ -89,15 +89,15 @@ def test_op_counts_by_level_match_the_plan(workload):
 
     n, t = 16384, W.T30[0]
     net = W.mnist_net()
-    if workload == "mnist":
+    if workload.startswith("mnist"):
         ev = LevelCount(n, t, 5)
         msgs, pos = lola.pack_convolution(W.image(), net.kh, net.kw, net.stride, n)
-        layers = W.layers_mnist(net, n, W.MNIST_LEVELS)
-    elif workload == "lola_dense":
+        layers = W.layers_mnist(net, n, W.MNIST_LEVELS, support_sum=not workload.endswith("_paper"))
+    elif workload.startswith("lola_dense"):
         ev = LevelCount(n, t, 6)
         v, pos = lola.pack_image_rows(W.image(), W.DENSE_IMAGE_WIDTH, n)
         msgs = [v]
-        layers = W.layers_lola_dense(net, n, levels=W.LOLA_DENSE_LEVELS)
+        layers = W.layers_lola_dense(net, n, levels=W.LOLA_DENSE_LEVELS, support_sum=not workload.endswith("_paper"))
     elif workload == "head":
         ev = LevelCount(n, t, 3)
         Wh = W.head_weights()

@@ -1,8 +1,9 @@
 """Word-for-word GPU parity at full size, in the configuration bench.py times.
 
 The MNIST-shaped network (n = 16384, five 60-bit primes switched to four and
-two after the squares, three CRT plaintext moduli, batch of 16 requests,
-autotuned launch geometry, CUDA-graph replay) and the transfer-learning head
+two after the squares, three CRT plaintext moduli, the last layer summed
+over the occupied slots, batch of 16 requests, autotuned launch geometry,
+CUDA-graph replay) and the transfer-learning head
 (n = 16384, three primes, one plaintext modulus, batch of 64): for one
 sampled request and one CRT residue the oracle runs the same layer list on
 the same encrypted input with the same keys, and every output ciphertext
@@ -49,7 +50,7 @@ def test_full_mnist_batch16_every_output_ciphertext_matches_oracle(oracle_runs):
     ps = W.params_mnist()
     n = ps.n
     mnet = W.mnist_net()
-    layers = W.layers_mnist(mnet, n, W.MNIST_LEVELS)
+    layers = W.layers_mnist(mnet, n, W.MNIST_LEVELS, support_sum=True)
     ctx = make_ctx(ps)
     try:
         Lb.lola_autotune(ctx)                 # the geometry table bench.py times with

@@ -69,9 +69,10 @@ def test_dense64_bit_exact_vs_oracle():
         Lb.lola_ctx_destroy(ctx)
 
 
-@pytest.mark.parametrize("levels,K,alpha", [(None, 1, 1), ((4, 2), 1, 1), ((3, 1), 1, 1), ((4, 2), 2, 2),
-                                            ((3, 1), 2, 2)])
-def test_mini_mnist_bit_exact_vs_oracle(levels, K, alpha):
+@pytest.mark.parametrize("levels,K,alpha,support", [(None, 1, 1, False), ((4, 2), 1, 1, False), ((3, 1), 1, 1, False),
+                                                    ((4, 2), 2, 2, False), ((3, 1), 2, 2, False), ((4, 2), 1, 1, True),
+                                                    (None, 2, 2, True)])
+def test_mini_mnist_bit_exact_vs_oracle(levels, K, alpha, support):
     # levels: modulus switching after each square (every later ciphertext,
     # including the relinearisation at level 4 or 3, compared word for word);
     # K = 2, alpha = 2: key-switching digits of two primes (the MNIST workload's)
@@ -83,7 +84,7 @@ def test_mini_mnist_bit_exact_vs_oracle(levels, K, alpha):
     t = ps.t[0]
     mnet = W.mnist_net(seed=7, maps=2, hidden=12, classes=3, h=12, w=12, k=3, stride=2)
     img = W.image(seed=7, h=12, w=12)
-    layers = W.layers_mnist(mnet, n, levels)
+    layers = W.layers_mnist(mnet, n, levels, support_sum=support)
     ctx = make_ctx(ps)
     try:
         msgs, win = Lb.lola_pack_convolution(img, 3, 3, 2, n)
@@ -97,6 +98,7 @@ def test_mini_mnist_bit_exact_vs_oracle(levels, K, alpha):
         ok = oracle_keys(P, net, 11)
         octs = [bfv.encrypt(P, ok.pk, encoding.encode(m, t), t, 5, i) for i, m in enumerate(msgs)]
         st = OL.run_network(OL.HEEval(P, ok, t), layers, OL.State(octs, [(0, i) for i in range(win)]))
+        assert [(int(m), int(s)) for m, s in net.output_map()] == [(int(m), int(s)) for m, s in st.pos]
         for o in range(3):
             assert np.array_equal(got[o, 0], st.msgs[o].c[0]) and np.array_equal(got[o, 1], st.msgs[o].c[1]), o
         if levels != (3, 1):     # one 60-bit prime leaves no noise budget for the last layer (oracle: -15 bits)

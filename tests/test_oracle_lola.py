@@ -473,3 +473,79 @@ def test_full_mnist_with_modulus_switching_keeps_its_noise_margin():
         vals[:] = want[m]                       # sparse output: the value in every slot
         margin = bfv.noise_margin_bits(ev.p, keys.sk, st.msgs[m], encoding.encode(vals, t))
         assert margin > 20, margin
+
+
+# ------------------------------- row-major product summed over the support
+
+def test_support_sum_shifts_against_brute_force():
+    # for random supports built as (run mod period) lattices, and a few
+    # irregular ones, the chosen shifts are the fewest of every (period, run)
+    # choice checked by brute force, and the result slot holds every
+    # occupied slot exactly once
+    import itertools
+    n = 64
+    h = n // 2
+    g = np.random.default_rng(9)
+    cases = [list(range(n)), [5], [3, 40], [1, 2, 9, 10, 17, 18, 25, 26]]
+    for _ in range(20):
+        lp = int(g.integers(0, 6))
+        per = 1 << lp
+        run = int(g.integers(1, per + 1))
+        o = int(g.integers(0, per))
+        rows = [0] if g.random() < 0.5 else [0, 1]
+        cols = [c for c in range(h) if (c - o) % per < run and g.random() < 0.8] or [o]
+        cases.append([r * h + c for r in rows for c in cols])
+    for slots in cases:
+        shifts, p = lola.support_sum_shifts(slots, n)
+        # exactly-once coverage at p, by brute force over subset sums
+        cover = {}
+        rowswap = 0 in shifts
+        row_shifts = [s for s in shifts if s]
+        for sub in itertools.product([0, 1], repeat=len(row_shifts)):
+            off = sum(s for s, b in zip(row_shifts, sub) if b)
+            for sw in ([0, 1] if rowswap else [0]):
+                src_row = (p // h) ^ sw
+                src = src_row * h + ((p % h) - off) % h
+                cover[src] = cover.get(src, 0) + 1
+        assert all(cover.get(s, 0) == 1 for s in set(slots)), (slots, shifts, p)
+        # no (period, run) choice does it in fewer steps
+        logh = h.bit_length() - 1
+        best = min(k + (logh - q) + (1 if len({s // h for s in slots}) > 1 else 0)
+                   for q in range(logh + 1) for k in range(q + 1)
+                   if any(all(((c % h) - o2) % (1 << q) < (1 << k) for c in slots) for o2 in range(1 << q)))
+        assert len(shifts) == best
+
+
+def test_mnist_support_sum_plan_matches_integer_network():
+    # the MNIST-shaped plan with the support-summed last layer: 7 rotations
+    # per output instead of 14 (154 per residue instead of 224), same outputs
+    n = 16384
+    net, img = W.mnist_net(), W.image(idx=4)
+    want = mnist_int(net, img)
+    layers = W.layers_mnist(net, n, W.MNIST_LEVELS, support_sum=True)
+    msgs, pos = lola.pack_convolution(img, net.kh, net.kw, net.stride, n)
+    for t in W.T30[:3]:
+        ev = Counting(n, t)
+        st = lola.run_network(ev, layers, lola.State([np.array(m, np.int64) % t for m in msgs], pos))
+        assert ev.c["rot"] == 224 - 70 and ev.c["square"] == 2
+        assert [int(st.msgs[m][s]) for m, s in st.pos] == [v % t for v in want]
+        assert len({s for _, s in st.pos}) == 1                 # one result slot for all outputs
+
+
+def test_support_sum_on_ciphertexts_small():
+    # the same layer on oracle ciphertexts (n = 64): decrypts to the dot products
+    n, t = 64, W.T30[0]
+    P = bfv.Params(n, W.Q60[:4], 3, 1, [t])
+    keys = bfv.keygen(P, 3, rotations=[1, 2, 4, 8, 16], relin=False, row_swap=True)
+    g = np.random.default_rng(10)
+    slots = [0, 1, 2, 16, 17, 18, 32, 33, 34, 48, 49, 50]     # runs of 3 every 16 slots, both rows
+    x = g.integers(0, 16, len(slots))
+    Wm = g.integers(-3, 4, (3, len(slots)))
+    v = np.zeros(n, np.int64)
+    v[slots] = x
+    ct = bfv.encrypt(P, keys.pk, encoding.encode(v, t), t, 4, 0)
+    st = lola.run_network(lola.HEEval(P, keys, t), [{"op": "interleaved_rowmajor_support", "weights": Wm}],
+                          lola.State([ct], [(0, s) for s in slots]))
+    for o, (m, s) in enumerate(st.pos):
+        dec = encoding.decode(bfv.decrypt(P, keys.sk, st.msgs[m]), t)
+        assert int(dec[s]) == int(np.dot(Wm[o], x)) % t

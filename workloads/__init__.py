@@ -255,11 +255,14 @@ def _ceil_log2(k: int) -> int:
 MNIST_LEVELS = (4, 2)
 
 
-def layers_mnist(net: MnistNet, n: int, levels=None) -> list:
+def layers_mnist(net: MnistNet, n: int, levels=None, support_sum: bool = False) -> list:
     """Sec. 4.3 / Table 1: conv (convolution representation) -> combine maps
     -> square -> stack -> stacked row-major dense -> square -> interleaved
     row-major dense.  levels = (L1, L2): switch modulus to L1 primes after the
-    first square and to L2 after the second (None: no switching)."""
+    first square and to L2 after the second (None: no switching).
+    support_sum: the last layer sums each dot product over the interleaved
+    vector's occupied slots only (7 rotations per output at n = 16384
+    instead of the paper's 14; output o at one slot of message o)."""
     maps, hidden = net.conv_w.shape[0], net.dense1_w.shape[0]
     oh = -(-(net.h - net.kh) // net.stride) + 1
     ow = -(-(net.w - net.kw) // net.stride) + 1
@@ -276,7 +279,7 @@ def layers_mnist(net: MnistNet, n: int, levels=None) -> list:
         {"op": "stacked_rowmajor", "weights": net.dense1_w, "d": d, "copies": copies},
         {"op": "square"},
         *ms[1],
-        {"op": "interleaved_rowmajor", "weights": net.dense2_w},
+        {"op": "interleaved_rowmajor_support" if support_sum else "interleaved_rowmajor", "weights": net.dense2_w},
     ]
 
 
@@ -339,7 +342,8 @@ def _with_levels(layers: list, after_squares, levels) -> list:
     return out
 
 
-def layers_lola_dense(net: MnistNet, n: int, width: int = DENSE_IMAGE_WIDTH, levels=None) -> list:
+def layers_lola_dense(net: MnistNet, n: int, width: int = DENSE_IMAGE_WIDTH, levels=None,
+                      support_sum: bool = False) -> list:
     """LoLa-Dense (App. C, Table 3): one dense image message masked into the
     convolution representation (window (i, j) at the slot of its upper-left
     pixel), convolution row-major, maps combined by collision-free shifts,
@@ -361,7 +365,7 @@ def layers_lola_dense(net: MnistNet, n: int, width: int = DENSE_IMAGE_WIDTH, lev
         {"op": "stack", "d": d, "copies": copies},
         {"op": "stacked_rowmajor", "weights": net.dense1_w, "d": d, "copies": copies},
         {"op": "square"},
-        {"op": "interleaved_rowmajor", "weights": net.dense2_w},
+        {"op": "interleaved_rowmajor_support" if support_sum else "interleaved_rowmajor", "weights": net.dense2_w},
     ], [3, 6], levels)
 
 
