@@ -366,10 +366,11 @@ def mod_down(params: Params, x: np.ndarray) -> np.ndarray:
     return np.stack(res)
 
 
-def key_switch_raised(params: Params, D: list, ksk: KeySwitchKey):
-    """The key-switch inner product sum_g D_g * ksk_g over Q * P and the
-    mod-down, for raised digits D (raise_digits, possibly permuted)."""
-    u = []
+def key_switch_inner(params: Params, D: list, ksk: KeySwitchKey) -> list:
+    """The key-switch inner products sum_g D_g * ksk_g over Q * P, one
+    (L+K, n) array per key component (b, a), for raised digits D
+    (raise_digits, possibly permuted); no mod-down."""
+    out = []
     for comp in (ksk.b, ksk.a):
         acc = []
         for j, pj in enumerate(params.q):
@@ -377,8 +378,15 @@ def key_switch_raised(params: Params, D: list, ksk: KeySwitchKey):
             for g in range(len(D)):
                 s = ring.vec_add(s, ring.poly_mul(D[g][j], comp[g, j], pj), pj)
             acc.append(s)
-        u.append(mod_down(params, np.stack(acc)))
-    return u[0], u[1]
+        out.append(np.stack(acc))
+    return out
+
+
+def key_switch_raised(params: Params, D: list, ksk: KeySwitchKey):
+    """The key-switch inner product sum_g D_g * ksk_g over Q * P and the
+    mod-down, for raised digits D (raise_digits, possibly permuted)."""
+    acc = key_switch_inner(params, D, ksk)
+    return mod_down(params, acc[0]), mod_down(params, acc[1])
 
 
 def key_switch(params: Params, d: np.ndarray, ksk: KeySwitchKey):
@@ -420,6 +428,34 @@ def rotate_hoisted(params: Params, keys: Keys, ct: Ciphertext, steps) -> list:
         u0, u1 = key_switch_raised(params, Dg, keys.galois[g])
         out.append(Ciphertext([_add_rns(c0, u0, qs), u1], ct.t))
     return out
+
+
+def rotate_sum_hoisted(params: Params, keys: Keys, ct: Ciphertext, steps) -> Ciphertext:
+    """ct plus its rotations by every step of `steps` (step 0 = row swap; a
+    step may repeat) with one digit raising and one mod-down.
+
+    Reading (not in the paper, whose rotate-and-sum takes one rotation per
+    doubling step, Sec. 4.1): two doubling steps x + rot(x, a), then
+    + rot(., b), equal x + rot(x, a) + rot(x, b) + rot(x, a + b), rotations of
+    one ciphertext.  Their digits are raised once and permuted per step as in
+    rotate_hoisted; the inner products with each step's key are added over
+    Q * P and brought down by a single mod-down, and tau_g(c0) of every step
+    is added to c0 (c1 keeps its own term).  The result decrypts to the sum
+    of the rotations; against adding the hoisted rotations one by one it
+    differs by the rounding of one mod-down instead of one per step: at most
+    (len(steps) + 1) / 2 per coefficient in absolute value."""
+    qs = params.q[:params.L]
+    D = raise_digits(params, ct.c[1])
+    c0 = ct.c[0].copy()
+    acc = None
+    for k in steps:
+        g = galois_row_swap(params.n) if k == 0 else galois_for_rotation(params.n, k)
+        c0 = _add_rns(c0, _auto_rns(ct.c[0], g, qs), qs)
+        Dg = [np.stack([ring.automorphism(Dd[j], g, p) for j, p in enumerate(params.q)]) for Dd in D]
+        ip = key_switch_inner(params, Dg, keys.galois[g])
+        acc = ip if acc is None else [_add_rns(acc[c], ip[c], params.q) for c in range(2)]
+    u0, u1 = mod_down(params, acc[0]), mod_down(params, acc[1])
+    return Ciphertext([_add_rns(c0, u0, qs), _add_rns(ct.c[1], u1, qs)], ct.t)
 
 
 def rotate_rows(params: Params, keys: Keys, ct: Ciphertext) -> Ciphertext:

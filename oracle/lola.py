@@ -25,6 +25,9 @@ Layer list entries (dicts):
   {"op": "sparse_colmajor", "weights": W}               Sec. 4.2.2 sparse vector - column major
   {"op": "mod_switch", "L": Lv}                         keep the first Lv primes of Q (modulus
                                                         switching; no change to any slot value)
+The layers with a rotate-and-sum (stack, stacked_rowmajor, interleaved_rowmajor(_support),
+dense_rowmajor) take an optional "hoist": m, the doubling steps summed per key switch
+(rotate_and_sum, hoist_groups; 1 = the paper's one rotation per step).
 """
 from __future__ import annotations
 
@@ -59,6 +62,13 @@ class SlotEval:
         h = self.n // 2
         return np.concatenate([a[h:], a[:h]])
 
+    def rot_sum(self, a, steps):
+        """a plus its rotations by every step (0 = row swap)."""
+        out = a
+        for k in steps:
+            out = self.add(out, self.rot_rows(a) if k == 0 else self.rot(a, k))
+        return out
+
     def mul_plain(self, a, slots):
         return (a * (np.asarray(slots, dtype=np.int64) % self.t)) % self.t
 
@@ -79,7 +89,7 @@ class HEEval:
         self.p, self.keys, self.t = params, keys, t
         self.full_keys = keys
         self.n = params.n
-        self.counts = {"rot": 0, "mul_plain": 0, "mul_scalar": 0, "square": 0, "add": 0}
+        self.counts = {"rot": 0, "rot_sum": 0, "mul_plain": 0, "mul_scalar": 0, "square": 0, "add": 0}
 
     def add(self, a, b):
         self.counts["add"] += 1
@@ -96,6 +106,11 @@ class HEEval:
     def rot_hoisted(self, a, steps):
         self.counts["rot"] += len(steps)
         return bfv.rotate_hoisted(self.p, self.keys, a, steps)
+
+    def rot_sum(self, a, steps):
+        """One key switch (one mod-down) for all of the steps' rotations."""
+        self.counts["rot_sum"] += 1
+        return bfv.rotate_sum_hoisted(self.p, self.keys, a, steps)
 
     def mul_plain(self, a, slots):
         self.counts["mul_plain"] += 1
@@ -127,10 +142,50 @@ class State:
     copies: int = 0
 
 
-def rotate_and_sum(ev, x, shifts):
-    """x <- x + rot(x, s) for s in shifts, in order (Sec. 4.1 and its footnote)."""
+def hoist_groups(shifts, m: int, n: int) -> list:
+    """The rotate-and-sum steps `shifts` (0 = row swap) taken up to m at a
+    time: each run of up to m consecutive nonzero shifts a_1 .. a_r becomes
+    the rotation steps of the 2^r - 1 nonempty subsets, sum_{i in S} a_i mod
+    n/2 (subset S as a bit mask, ascending), whose rotations added to x give
+    the r doubling steps at once; a row swap is a group of its own.  A run
+    with a subset sum of 0 mod n/2 (no rotation) is left as single steps.
+    m <= 1: every shift is a group of its own."""
+    h = n // 2
+    groups, run = [], []
+
+    def flush():
+        if not run:
+            return
+        sums = [sum(a for i, a in enumerate(run) if mask >> i & 1) % h for mask in range(1, 1 << len(run))]
+        if len(run) == 1 or 0 in sums:
+            groups.extend([a] for a in run)
+        else:
+            groups.append(sums)
+        run.clear()
     for s in shifts:
-        x = ev.add(x, ev.rot(x, s))
+        if s == 0:
+            flush()
+            groups.append([0])
+            continue
+        run.append(s)
+        if len(run) >= max(m, 1):
+            flush()
+    flush()
+    return groups
+
+
+def rotate_and_sum(ev, x, shifts, hoist: int = 1):
+    """x <- x + rot(x, s) for s in shifts, in order (Sec. 4.1 and its
+    footnote; s = 0 is the row swap).  With hoist = m > 1, each group of
+    hoist_groups with more than one step is one hoisted rotate-sum (x plus
+    its rotations by all of the group's steps, one key switch); single steps
+    stay x + rot(x, s)."""
+    for grp in hoist_groups(shifts, hoist, ev.n):
+        if len(grp) > 1:
+            x = ev.rot_sum(x, grp)
+        else:
+            s = grp[0]
+            x = ev.add(x, ev.rot_rows(x) if s == 0 else ev.rot(x, s))
     return x
 
 
@@ -268,7 +323,7 @@ def layer_mod_switch(ev, st: State, Lv: int) -> State:
     return State(ev.mod_switch(st.msgs, Lv), st.pos, st.block, st.copies)
 
 
-def layer_stack(ev, st: State, d: int, copies: int) -> State:
+def layer_stack(ev, st: State, d: int, copies: int, hoist: int = 1) -> State:
     """Stacked representation (Sec. 4.2.1): copies of the vector every 2^d
     slots.  Built by x <- x + rot(x, s) for s = 2^d, 2^(d+1), ... within a
     row, then x <- x + rot_rows(x) when the copies fill both rows."""
@@ -276,13 +331,14 @@ def layer_stack(ev, st: State, d: int, copies: int) -> State:
     assert len(st.msgs) == 1 and all(m == 0 and slot < s for m, slot in st.pos)
     assert copies & (copies - 1) == 0 and copies * s <= n
     per_row = min(copies, h // s)
-    x = st.msgs[0]
+    shifts = []
     shift = s
     while shift < per_row * s:
-        x = ev.add(x, ev.rot(x, shift))
+        shifts.append(shift)
         shift *= 2
     if copies > per_row:
-        x = ev.add(x, ev.rot_rows(x))
+        shifts.append(0)
+    x = rotate_and_sum(ev, st.msgs[0], shifts, hoist)
     return State([x], st.pos, s, copies)
 
 
@@ -293,7 +349,7 @@ def stacked_output_slot(n: int, s: int, b: int, r: int) -> int:
     return row * h + (col + r) % h
 
 
-def layer_stacked_rowmajor(ev, st: State, W, d: int, copies: int) -> State:
+def layer_stacked_rowmajor(ev, st: State, W, d: int, copies: int, hoist: int = 1) -> State:
     """Stacked vector - row major (Sec. 4.2.2 and its footnote).
 
     Round r multiplies the stacked vector by rows r*c .. r*c+c-1 of W
@@ -320,7 +376,7 @@ def layer_stacked_rowmajor(ev, st: State, W, d: int, copies: int) -> State:
             for i, (_, slot) in enumerate(st.pos):
                 P[b * s + slot] = int(W[row][i])
         y = ev.mul_plain(x, P)
-        y = rotate_and_sum(ev, y, [1 << j for j in range(d)])
+        y = rotate_and_sum(ev, y, [1 << j for j in range(d)], hoist)
         outs.append(y)
     if R == 1:
         pos = [(0, stacked_output_slot(n, s, b, 0)) for b in range(rows)]
@@ -339,7 +395,7 @@ def layer_stacked_rowmajor(ev, st: State, W, d: int, copies: int) -> State:
     return State([acc], pos)
 
 
-def layer_interleaved_rowmajor(ev, st: State, W) -> State:
+def layer_interleaved_rowmajor(ev, st: State, W, hoist: int = 1) -> State:
     """Interleaved vector - row major (Sec. 4.2.2): the dense row-major dot
     product with the columns of W placed at the vector's slots.  Each output
     sums all n slots: right rotations 1, 2, ..., n/4 within the rows, then
@@ -353,8 +409,7 @@ def layer_interleaved_rowmajor(ev, st: State, W) -> State:
         V = np.zeros(n, dtype=np.int64)
         V[slots] = np.asarray(W[o], dtype=np.int64)     # column i of W at element i's slot
         y = ev.mul_plain(st.msgs[0], V)
-        y = rotate_and_sum(ev, y, shifts)
-        y = ev.add(y, ev.rot_rows(y))
+        y = rotate_and_sum(ev, y, shifts + [0], hoist)
         outs.append(y)
     return State(outs, [(o, 0) for o in range(len(W))])
 
@@ -401,7 +456,7 @@ def support_sum_shifts(slots, n: int):
     return shifts, int(full[0])
 
 
-def layer_interleaved_rowmajor_support(ev, st: State, W) -> State:
+def layer_interleaved_rowmajor_support(ev, st: State, W, hoist: int = 1) -> State:
     """Interleaved vector - row major with each dot product summed over the
     vector's occupied slots only (support_sum_shifts): the products are
     those of layer_interleaved_rowmajor (column i of W at element i's
@@ -416,8 +471,7 @@ def layer_interleaved_rowmajor_support(ev, st: State, W) -> State:
         V = np.zeros(n, dtype=np.int64)
         V[slots] = np.asarray(W[o], dtype=np.int64)
         y = ev.mul_plain(st.msgs[0], V)
-        for sh in shifts:
-            y = ev.add(y, ev.rot_rows(y) if sh == 0 else ev.rot(y, sh))
+        y = rotate_and_sum(ev, y, shifts, hoist)
         outs.append(y)
     return State(outs, [(o, p) for o in range(len(W))])
 
@@ -454,13 +508,13 @@ def run_network(ev, layers, st: State) -> State:
         elif op == "square":
             st = layer_square(ev, st)
         elif op == "stack":
-            st = layer_stack(ev, st, L["d"], L["copies"])
+            st = layer_stack(ev, st, L["d"], L["copies"], L.get("hoist", 1))
         elif op == "stacked_rowmajor":
-            st = layer_stacked_rowmajor(ev, st, L["weights"], L["d"], L["copies"])
+            st = layer_stacked_rowmajor(ev, st, L["weights"], L["d"], L["copies"], L.get("hoist", 1))
         elif op in ("interleaved_rowmajor", "dense_rowmajor"):
-            st = layer_interleaved_rowmajor(ev, st, L["weights"])
+            st = layer_interleaved_rowmajor(ev, st, L["weights"], L.get("hoist", 1))
         elif op == "interleaved_rowmajor_support":
-            st = layer_interleaved_rowmajor_support(ev, st, L["weights"])
+            st = layer_interleaved_rowmajor_support(ev, st, L["weights"], L.get("hoist", 1))
         elif op == "sparse_colmajor":
             st = layer_sparse_colmajor(ev, st, L["weights"])
         elif op == "mod_switch":

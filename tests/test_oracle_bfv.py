@@ -604,3 +604,94 @@ def test_symmetric_encryption_phase_is_delta_m_plus_the_sampled_error():
     # and it is a ciphertext like any other: it rotates and squares
     keys2 = bfv.keygen(P, 3, rotations=[2], relin=True)
     assert np.array_equal(dec(P, keys2, bfv.rotate(P, keys2, ct, 2)), row_shift(v, 2))
+
+
+# ------------------------------------------- hoisted rotate-and-sum (one mod-down)
+
+def centered_diff(P, a, b):
+    """max |a - b| over the coefficients, centered mod Q (a, b: (L, n) mod Q)."""
+    qs = P.q[:P.L]
+    d = P.qbasis.lift_centered(np.stack([ring.vec_sub(a[j], b[j], q) for j, q in enumerate(qs)]))
+    return max(abs(int(x)) for x in d)
+
+
+@pytest.mark.parametrize("k", [3, 0])
+def test_rotate_sum_of_one_step_is_the_ciphertext_plus_its_hoisted_rotation(small, k):
+    P, keys = small
+    keys3 = bfv.keygen(P, 3, rotations=[1, 2, 3, 4, 7], relin=False, row_swap=True)
+    ct = enc(P, keys3, np.random.default_rng(40).integers(0, 65537, P.n))
+    got = bfv.rotate_sum_hoisted(P, keys3, ct, [k])
+    want = bfv.add(P, ct, bfv.rotate_hoisted(P, keys3, ct, [k])[0])
+    assert np.array_equal(got.c[0], want.c[0]) and np.array_equal(got.c[1], want.c[1])
+
+
+@pytest.mark.parametrize("steps", [[1, 2, 3], [4, 0, 4], [1, 2, 3, 4, 5, 6, 7]])
+def test_rotate_sum_decrypts_to_the_sum_of_the_rotations(steps):
+    P = mkparams(32)
+    keys = bfv.keygen(P, 41, rotations=sorted({s for s in steps if s}), relin=False, row_swap=True)
+    v = np.random.default_rng(41).integers(0, 65537, P.n)
+    ct = enc(P, keys, v)
+    h = P.n // 2
+    want = v.copy()
+    for s in steps:
+        want = want + (np.concatenate([v[h:], v[:h]]) if s == 0 else row_shift(v, s))
+    out = bfv.rotate_sum_hoisted(P, keys, ct, steps)
+    assert np.array_equal(dec(P, keys, out), want % 65537)
+
+
+def test_rotate_sum_rounds_once_instead_of_once_per_step():
+    # mod_down(sum x_k) - sum mod_down(x_k) = (sum x~_k - (sum x)~) / P: an
+    # integer of absolute value at most (G + 1) / 2, and not always 0
+    P = mkparams(64)
+    steps = [1, 2, 3]
+    keys = bfv.keygen(P, 42, rotations=steps, relin=False, row_swap=False)
+    ct = enc(P, keys, np.random.default_rng(42).integers(0, 65537, P.n))
+    got = bfv.rotate_sum_hoisted(P, keys, ct, steps)
+    ref = ct
+    for o in bfv.rotate_hoisted(P, keys, ct, steps):
+        ref = bfv.add(P, ref, o)
+    d0, d1 = centered_diff(P, got.c[0], ref.c[0]), centered_diff(P, got.c[1], ref.c[1])
+    assert d0 <= 2 and d1 <= 2
+    assert d0 + d1 > 0
+
+
+def test_rotate_sum_without_special_primes_is_the_sum_of_hoisted_rotations():
+    # K = 0: no mod-down, so no rounding to share: the sum is exact
+    P = mkparams(32, L=3, K=0)
+    steps = [1, 2, 3, 0]
+    keys = bfv.keygen(P, 43, rotations=[1, 2, 3], relin=False, row_swap=True)
+    ct = enc(P, keys, np.random.default_rng(43).integers(0, 16, P.n))
+    got = bfv.rotate_sum_hoisted(P, keys, ct, steps)
+    ref = ct
+    for o in bfv.rotate_hoisted(P, keys, ct, steps):
+        ref = bfv.add(P, ref, o)
+    assert np.array_equal(got.c[0], ref.c[0]) and np.array_equal(got.c[1], ref.c[1])
+
+
+def test_rotate_sum_noise_is_no_worse_than_two_doubling_steps():
+    P = mkparams(64)
+    keys = bfv.keygen(P, 44, rotations=[1, 2, 3], relin=False)
+    v = np.random.default_rng(44).integers(0, 16, P.n)
+    ct = enc(P, keys, v)
+    seq = bfv.add(P, ct, bfv.rotate(P, keys, ct, 1))
+    seq = bfv.add(P, seq, bfv.rotate(P, keys, seq, 2))
+    hz = bfv.rotate_sum_hoisted(P, keys, ct, [1, 2, 3])
+    want = (v + row_shift(v, 1) + row_shift(v, 2) + row_shift(v, 3)) % 65537
+    m = encoding.encode(want, 65537)
+    assert np.array_equal(dec(P, keys, hz), want) and np.array_equal(dec(P, keys, seq), want)
+    assert bfv.noise_margin_bits(P, keys.sk, hz, m) >= bfv.noise_margin_bits(P, keys.sk, seq, m) - 1
+
+
+def test_rotate_sum_with_grouped_digits_and_two_special_primes():
+    P = gparams(n=32, L=5, K=2, alpha=2)
+    keys = bfv.keygen(P, 45, rotations=[1, 2, 3], relin=False, row_swap=True)
+    t = P.t[0]
+    v = np.random.default_rng(45).integers(0, 16, P.n)
+    ct = bfv.encrypt(P, keys.pk, encoding.encode(v, t), t, 3, 0)
+    h = P.n // 2
+    for Lv in (5, 2):
+        Pl, kl = bfv.params_at_level(P, Lv), bfv.keys_at_level(keys, Lv)
+        cl = bfv.mod_switch_to(P, ct, Lv)
+        out = bfv.rotate_sum_hoisted(Pl, kl, cl, [1, 2, 3, 0])
+        want = v + row_shift(v, 1) + row_shift(v, 2) + row_shift(v, 3) + np.concatenate([v[h:], v[:h]])
+        assert np.array_equal(dec(Pl, kl, out), want % t)

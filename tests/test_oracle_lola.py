@@ -549,3 +549,61 @@ def test_support_sum_on_ciphertexts_small():
     for o, (m, s) in enumerate(st.pos):
         dec = encoding.decode(bfv.decrypt(P, keys.sk, st.msgs[m]), t)
         assert int(dec[s]) == int(np.dot(Wm[o], x)) % t
+
+
+# ------------------------------------------------ hoisted rotate-and-sum groups
+
+def test_hoist_groups_examples():
+    n = 64                                       # rows of 32 slots
+    assert lola.hoist_groups([1, 2, 4, 8, 16], 1, n) == [[1], [2], [4], [8], [16]]
+    assert lola.hoist_groups([1, 2, 4, 8, 16], 2, n) == [[1, 2, 3], [4, 8, 12], [16]]
+    assert lola.hoist_groups([1, 2, 4, 0, 8], 3, n) == [[1, 2, 3, 4, 5, 6, 7], [0], [8]]
+    assert lola.hoist_groups([16, 16], 2, n) == [[16], [16]]          # 16 + 16 = 0 mod 32: no rotation
+    assert lola.hoist_groups([8, 16], 2, n) == [[8, 16, 24]]
+
+
+@pytest.mark.parametrize("m", [2, 3, 4])
+def test_hoisted_rotate_and_sum_equals_the_doubling_steps(m):
+    # brute force on slot vectors: every grouping gives the sequential sum
+    n, t = 64, 65537
+    g = np.random.default_rng(m)
+    ev = lola.SlotEval(n, t)
+    for trial in range(20):
+        shifts = [int(x) for x in g.integers(0, n // 2, g.integers(1, 8))]
+        x = g.integers(0, t, n)
+        assert np.array_equal(lola.rotate_and_sum(ev, x, shifts, m), lola.rotate_and_sum(ev, x, shifts, 1)), shifts
+
+
+def test_mini_mnist_hoisted_encrypted_oracle_run():
+    # the reduced MNIST-shaped network with the rotate-and-sums hoisted two
+    # steps per key switch (three in the last layer): same outputs, fewer
+    # key switches
+    n = 1024
+    ps = W.params_small(n, L=5, K=1, t=W.T30[:1])
+    P = bfv.Params(ps.n, ps.q, ps.L, ps.K, ps.t, ps.alpha)
+    net, img = mini_mnist()
+    layers = W.layers_mnist(net, n, support_sum=True, hoist=(2, 2, 3))
+    t = ps.t[0]
+    msgs, pos = lola.pack_convolution(img, net.kh, net.kw, net.stride, n)
+    steps = set()
+
+    class Rec(lola.SlotEval):
+        def rot(self, a, k):
+            steps.add(k)
+            return super().rot(a, k)
+
+        def rot_rows(self, a):
+            steps.add(0)
+            return super().rot_rows(a)
+    lola.run_network(Rec(n, t), layers, lola.State([np.array(m, np.int64) % t for m in msgs], pos))
+    keys = bfv.keygen(P, 12, rotations=sorted(s for s in steps if s), relin=True, row_swap=0 in steps)
+    cts = [bfv.encrypt(P, keys.pk, encoding.encode(m, t), t, 5, i) for i, m in enumerate(msgs)]
+    ev = lola.HEEval(P, keys, t)
+    st = lola.run_network(ev, layers, lola.State(cts, pos))
+    got = [int(encoding.decode(bfv.decrypt(P, keys.sk, st.msgs[m]), t)[s]) for m, s in st.pos]
+    assert got == [v % t for v in mnist_int(net, img)]
+    # key switches: combine 1; stack [128, 256 | row swap] 1 + 1; stacked
+    # row-major 2 rounds x [1, 2 | 4, 8 | 16, 32 | 64] 2 x (3 + 1); round
+    # combine 1; last layer 3 outputs x 4 support steps as 3 + 1: 3 x (1 + 1)
+    # -> 8 single rotations and 10 rotate-sums (31 rotations without hoisting)
+    assert (ev.counts["rot"], ev.counts["rot_sum"]) == (8, 10)

@@ -255,14 +255,29 @@ def _ceil_log2(k: int) -> int:
 MNIST_LEVELS = (4, 2)
 
 
-def layers_mnist(net: MnistNet, n: int, levels=None, support_sum: bool = False) -> list:
+def _hoist3(hoist) -> tuple:
+    """(stack, stacked row-major, last layer) rotate-and-sum steps per key switch."""
+    h = (hoist,) * 3 if isinstance(hoist, int) else tuple(hoist)
+    assert len(h) == 3
+    return h
+
+
+def _with_hoist(layer: dict, m: int) -> dict:
+    return {**layer, "hoist": m} if m > 1 else layer
+
+
+def layers_mnist(net: MnistNet, n: int, levels=None, support_sum: bool = False, hoist=1) -> list:
     """Sec. 4.3 / Table 1: conv (convolution representation) -> combine maps
     -> square -> stack -> stacked row-major dense -> square -> interleaved
     row-major dense.  levels = (L1, L2): switch modulus to L1 primes after the
     first square and to L2 after the second (None: no switching).
     support_sum: the last layer sums each dot product over the interleaved
     vector's occupied slots only (7 rotations per output at n = 16384
-    instead of the paper's 14; output o at one slot of message o)."""
+    instead of the paper's 14; output o at one slot of message o).
+    hoist: rotate-and-sum doubling steps per key switch in the stack, the
+    stacked row-major and the last layer (an int for all three, or a
+    3-tuple; 1 = one key switch per step)."""
+    hs, hr, hl = _hoist3(hoist)
     maps, hidden = net.conv_w.shape[0], net.dense1_w.shape[0]
     oh = -(-(net.h - net.kh) // net.stride) + 1
     ow = -(-(net.w - net.kw) // net.stride) + 1
@@ -275,11 +290,12 @@ def layers_mnist(net: MnistNet, n: int, levels=None, support_sum: bool = False) 
         {"op": "combine", "stride": oh * ow},
         {"op": "square"},
         *ms[0],
-        {"op": "stack", "d": d, "copies": copies},
-        {"op": "stacked_rowmajor", "weights": net.dense1_w, "d": d, "copies": copies},
+        _with_hoist({"op": "stack", "d": d, "copies": copies}, hs),
+        _with_hoist({"op": "stacked_rowmajor", "weights": net.dense1_w, "d": d, "copies": copies}, hr),
         {"op": "square"},
         *ms[1],
-        {"op": "interleaved_rowmajor_support" if support_sum else "interleaved_rowmajor", "weights": net.dense2_w},
+        _with_hoist({"op": "interleaved_rowmajor_support" if support_sum else "interleaved_rowmajor",
+                     "weights": net.dense2_w}, hl),
     ]
 
 
@@ -343,12 +359,14 @@ def _with_levels(layers: list, after_squares, levels) -> list:
 
 
 def layers_lola_dense(net: MnistNet, n: int, width: int = DENSE_IMAGE_WIDTH, levels=None,
-                      support_sum: bool = False) -> list:
+                      support_sum: bool = False, hoist=1) -> list:
     """LoLa-Dense (App. C, Table 3): one dense image message masked into the
     convolution representation (window (i, j) at the slot of its upper-left
     pixel), convolution row-major, maps combined by collision-free shifts,
     square, stack, stacked row-major, square, interleaved row-major.
-    levels = (L1, L2): modulus switching after the two squares."""
+    levels = (L1, L2): modulus switching after the two squares; support_sum
+    and hoist as in layers_mnist."""
+    hs, hr, hl = _hoist3(hoist)
     G = conv_gather(net)
     slots = dense_image_slots(net.h, net.w, width)
     corner = [slots[int(g)] for g in G[0]]
@@ -362,10 +380,11 @@ def layers_lola_dense(net: MnistNet, n: int, width: int = DENSE_IMAGE_WIDTH, lev
         {"op": "conv", "weights": net.conv_w},
         {"op": "combine", "shifts": shifts},
         {"op": "square"},
-        {"op": "stack", "d": d, "copies": copies},
-        {"op": "stacked_rowmajor", "weights": net.dense1_w, "d": d, "copies": copies},
+        _with_hoist({"op": "stack", "d": d, "copies": copies}, hs),
+        _with_hoist({"op": "stacked_rowmajor", "weights": net.dense1_w, "d": d, "copies": copies}, hr),
         {"op": "square"},
-        {"op": "interleaved_rowmajor_support" if support_sum else "interleaved_rowmajor", "weights": net.dense2_w},
+        _with_hoist({"op": "interleaved_rowmajor_support" if support_sum else "interleaved_rowmajor",
+                     "weights": net.dense2_w}, hl),
     ], [3, 6], levels)
 
 
