@@ -3,26 +3,31 @@
 
 One step = one batched evaluation of the whole network (conv row-major,
 combine, square, stack, stacked row-major dense, square, interleaved
-row-major dense; 224 rotations and 2 squares per CRT residue, 3 residues)
-on B encrypted synthetic 28x28 images whose ciphertexts are already resident
-in HBM.  The ciphertexts start with five primes and are modulus-switched to
-four after the first square and to two after the second (the same decrypted
-outputs; --no-mod-switch keeps five throughout).  Reported beside it:
+row-major dense summed over the occupied slots; per CRT residue 154
+rotations taken as 70 key switches, up to three doubling steps of each
+rotate-and-sum per key switch, and 2 squares; 3 residues) on B encrypted
+synthetic 28x28 images whose ciphertexts are already resident in HBM.
+--paper-last-layer --hoist 1 runs the paper's plan (224 rotations, one key
+switch each).  The ciphertexts start with five primes and are
+modulus-switched to four after the first square and to two after the second
+(the same decrypted outputs; --no-mod-switch keeps five throughout).
+Reported beside it:
 
 * plain: the same network for one request at a time (B = 1, eager launches,
   no CUDA graph), p50 / p99 latency;
 * e2e: the batched step through the public API with host buffers: pinned
   host -> device copy of the input ciphertexts, evaluation, device -> host
   copy of the output ciphertexts, all inside the timed region;
-* roofline: the kernel with the largest device time, its algorithmic bytes
-  per launch over its CUDA-event-timed average duration, against the
-  measured HBM copy bandwidth;
-* cpu_baseline: the CPU oracle's per-operation times on the same parameters
-  scaled by the network's operation counts.
+* roofline: the kernel with the largest device time, its algorithmic work
+  per launch (butterflies for the transforms, 64 x 64-bit products for the
+  rotate-sum inner product, bytes for the rest) over its CUDA-event-timed
+  average duration, against the measured rate of the same operation
+  (lola_alu_rate) or the measured HBM copy bandwidth;
+* cpu_baseline: one whole inference on the CPU oracle, end to end.
 
 `--workload lola_dense` runs LoLa-Dense instead (App. C: one dense image
 message per request, masked into the convolution representation on the
-server; 326 rotations per residue, six ciphertext primes).
+server; six ciphertext primes).
 `--impl reference` times that CPU oracle as the reference arm.
 Multi-GPU (torchrun): independent replicas, one per GPU, no collective on
 the data path; the barrier and the max over ranks are for timing only.
@@ -56,6 +61,10 @@ def parse():
     ap.add_argument("--paper-last-layer", action="store_true",
                     help="mnist / lola_dense: the paper's interleaved row-major last layer (rotate-and-sum over "
                          "all n slots, 14 rotations per output) instead of the sum over the occupied slots (7)")
+    ap.add_argument("--hoist", default=None,
+                    help="mnist / lola_dense: rotate-and-sum doubling steps per key switch in the stack, the "
+                         "stacked row-major and the last layer ('a,b,c' or one number for all three; 1 = one "
+                         "rotation per step, the paper's; default: the workload's)")
     ap.add_argument("--grouped-digits", action="store_true",
                     help="mnist: key-switching digits of two primes with two special primes")
     ap.add_argument("--L", type=int, default=None,
@@ -95,6 +104,13 @@ def parse():
             args.levels = W.CIFAR_LEVELS
     if args.batch is None:
         args.batch = {"cifar": 2, "head": 64, "dense64": 256}.get(args.workload, 16)
+    if args.hoist is None:
+        args.hoist = {"mnist": W.MNIST_HOIST, "lola_dense": W.LOLA_DENSE_HOIST,
+                      "dense64": (W.DENSE64_HOIST,) * 3}.get(args.workload, (1, 1, 1))
+    else:
+        h = tuple(int(x) for x in str(args.hoist).split(","))
+        args.hoist = h * 3 if len(h) == 1 else h
+    args.hoist = tuple(args.hoist)
     return args
 
 
@@ -135,6 +151,108 @@ SUPPORT_SUM_WORKLOADS = ("mnist", "lola_dense")
 def counts_key(workload: str, paper_plan: bool) -> str:
     """Key of OP_COUNTS for a workload and its last-layer variant."""
     return workload + "_paper" if paper_plan and workload in SUPPORT_SUM_WORKLOADS else workload
+
+
+def plan_layers(workload, L, levels, paper_plan=False, hoist=(1, 1, 1)):
+    """(n, layers, input positions, stacked-state keywords, input slot
+    vectors) of a workload's plan at its full size, for slot-level runs."""
+    import numpy as np
+
+    import workloads as W
+    from oracle import lola as OL
+    n = 16384
+    net = W.mnist_net()
+    if workload == "mnist":
+        msgs, pos = OL.pack_convolution(W.image(), net.kh, net.kw, net.stride, n)
+        return n, W.layers_mnist(net, n, levels, support_sum=not paper_plan, hoist=hoist), pos, {}, msgs
+    if workload == "lola_dense":
+        v, pos = OL.pack_image_rows(W.image(), W.DENSE_IMAGE_WIDTH, n)
+        return n, W.layers_lola_dense(net, n, levels=levels, support_sum=not paper_plan, hoist=hoist), pos, {}, [v]
+    if workload == "head":
+        Wh = W.head_weights()
+        v = np.zeros(n, np.int64)
+        v[:Wh.shape[1]] = W.feature_vector()
+        return n, W.layers_head(Wh, n), [(0, i) for i in range(Wh.shape[1])], {}, [v]
+    if workload == "dense64":
+        Wd = W.dense_weights()
+        copies = W.dense64_input_copies(Wd)
+        v, pos = OL.pack_stacked(W.dense_vector(), 6, copies, 4096)
+        return (4096, W.layers_dense64(Wd, 4096, hoist[1]), pos, {"block": 64, "copies": copies},
+                [np.asarray(v, np.int64)])
+    cnet = W.cifar_net()
+    msgs, pos = OL.pack_convolution(W.cifar_padded(W.cifar_image(), cnet.pad), cnet.k1, cnet.k1, cnet.stride, n)
+    return n, W.layers_cifar(cnet, n, levels=levels), pos, {}, msgs
+
+
+def plan_counts(workload, L, levels, paper_plan=False, hoist=(1, 1, 1)) -> dict:
+    """Per-level operation counts of one inference, one residue, counted on
+    slot vectors: {level: {"rot", "rot_sum": {steps: count}, "square",
+    "mul_plain", "mul_scalar", "add"}}; "rot" counts single rotations (key
+    switches), a rotate-sum of G steps counts once under rot_sum[G]."""
+    import numpy as np
+
+    import workloads as W
+    from oracle import lola as OL
+    n, layers, pos, stacked, msgs = plan_layers(workload, L, levels, paper_plan, hoist)
+
+    class Count(OL.SlotEval):
+        def __init__(self):
+            super().__init__(n, W.T30[0])
+            self.level, self.c, self.inner = L, {}, False
+
+        def _k(self, op, G=None):
+            if self.inner:
+                return
+            d = self.c.setdefault(self.level, {"rot": 0, "rot_sum": {}, "square": 0, "mul_plain": 0,
+                                               "mul_scalar": 0, "add": 0})
+            if G is None:
+                d[op] += 1
+            else:
+                d["rot_sum"][G] = d["rot_sum"].get(G, 0) + 1
+
+        def add(self, a, b):
+            self._k("add")
+            return super().add(a, b)
+
+        def rot(self, a, k):
+            self._k("rot")
+            return super().rot(a, k)
+
+        def rot_rows(self, a):
+            self._k("rot")
+            return super().rot_rows(a)
+
+        def rot_hoisted(self, a, steps):
+            return [self.rot_rows(a) if k == 0 else self.rot(a, k) for k in steps]
+
+        def rot_sum(self, a, steps):
+            self._k(None, len(steps))
+            self.inner = True
+            try:
+                return super().rot_sum(a, steps)
+            finally:
+                self.inner = False
+
+        def mul_plain(self, a, v):
+            self._k("mul_plain")
+            return super().mul_plain(a, v)
+
+        def mul_scalar(self, a, w):
+            self._k("mul_scalar")
+            return super().mul_scalar(a, w)
+
+        def square(self, a):
+            self._k("square")
+            return super().square(a)
+
+        def mod_switch(self, msgs, Lv):
+            self.level = Lv
+            return msgs
+
+    ev = Count()
+    t = W.T30[0]
+    OL.run_network(ev, layers, OL.State([np.asarray(m, np.int64) % t for m in msgs], pos, **stacked))
+    return ev.c
 
 
 WORKLOAD_NAME = {"mnist": "mnist_lola_n16384", "lola_dense": "lola_dense_n16384", "cifar": "cifar_lola_n16384",
@@ -208,19 +326,22 @@ def workload_params(workload, L):
         workload, W.params_mnist)(L)
 
 
-def oracle_sample(n_rot=1, n_sq=1, workload="mnist", L=5, levels=None, paper_plan=False):
+def oracle_sample(n_rot=1, n_sq=1, workload="mnist", L=5, levels=None, paper_plan=False, hoist=(1, 1, 1)):
     """Time the CPU oracle's operations on the network's parameters (one CRT
     residue) and scale by the network's operation counts for one inference
-    over all residues; with modulus switching, each level's operations are
-    timed at that level (ciphertexts switched by the oracle).  Returns
-    (seconds per inference, description)."""
+    over all residues (plan_counts); with modulus switching, each level's
+    operations are timed at that level (ciphertexts switched by the oracle),
+    a rotate-sum of G steps timed at its G.  Returns (seconds per inference,
+    description)."""
     import numpy as np
 
     import workloads as W
     from oracle import bfv, encoding
     ps = workload_params(workload, L)
     P = bfv.Params(ps.n, ps.q, ps.L, ps.K, ps.t, ps.alpha)
-    keys = bfv.keygen(P, 5, rotations=[1], relin=True)
+    by_level = plan_counts(workload, L, levels, paper_plan, hoist)
+    gmax = max([max(c["rot_sum"], default=1) for c in by_level.values()] + [1])
+    keys = bfv.keygen(P, 5, rotations=list(range(1, gmax + 1)), relin=True)
     t = ps.t[0]
     v = np.random.default_rng(0).integers(0, 16, ps.n)
     ct = bfv.encrypt(P, keys.pk, encoding.encode(v, t), t, 1, 0)
@@ -231,8 +352,6 @@ def oracle_sample(n_rot=1, n_sq=1, workload="mnist", L=5, levels=None, paper_pla
         for _ in range(reps):
             fn()
         return (time.perf_counter() - t0) / reps
-    key = counts_key(workload, paper_plan)
-    by_level = OP_COUNTS_LEVELS[key] if levels else {L: OP_COUNTS[key]}
     sec, parts, total = 0.0, [], {}
     for lv, counts in sorted(by_level.items(), reverse=True):
         Pl, kl = bfv.params_at_level(P, lv), bfv.keys_at_level(keys, lv)
@@ -242,11 +361,15 @@ def oracle_sample(n_rot=1, n_sq=1, workload="mnist", L=5, levels=None, paper_pla
         t_pt = timed(lambda: bfv.mul_plain(Pl, cl, w), 1) if counts["mul_plain"] else 0.0
         t_sc = timed(lambda: bfv.mul_scalar(Pl, cl, -3), 3) if counts["mul_scalar"] else 0.0
         t_add = timed(lambda: bfv.add(Pl, cl, cl), 3)
+        t_rs = {G: timed(lambda: bfv.rotate_sum_hoisted(Pl, kl, cl, list(range(1, G + 1))), 1)
+                for G in counts["rot_sum"]}
         sec += (counts["rot"] * t_rot + counts["square"] * t_sq + counts["mul_plain"] * t_pt
-                + counts["mul_scalar"] * t_sc + counts["add"] * t_add) * len(ps.t)
+                + counts["mul_scalar"] * t_sc + counts["add"] * t_add
+                + sum(c * t_rs[G] for G, c in counts["rot_sum"].items())) * len(ps.t)
+        rs = "".join(f", rotate-sum of {G} {t_rs[G]:.3f}s x {c}" for G, c in sorted(counts["rot_sum"].items()))
         parts.append(f"L={lv}: rotation {t_rot:.3f}s, square+relin {t_sq:.3f}s, ct*pt {t_pt:.3f}s, "
                      f"ct*scalar {t_sc:.4f}s, add {t_add:.4f}s x ({counts['rot']} rot, {counts['square']} sq, "
-                     f"{counts['mul_plain']} ct*pt, {counts['mul_scalar']} ct*scalar, {counts['add']} add)")
+                     f"{counts['mul_plain']} ct*pt, {counts['mul_scalar']} ct*scalar, {counts['add']} add){rs}")
     desc = (f"oracle per-op times on n={ps.n} x op counts of one inference per level; " + "; ".join(parts)
             + f"; x {len(ps.t)} CRT residues")
     return sec, desc
@@ -274,7 +397,7 @@ def _slot_rotation_steps(layers, n, t, st):
     return sorted(seen)
 
 
-def oracle_residue_inference(workload, L, levels, ti, paper_plan=False):
+def oracle_residue_inference(workload, L, levels, ti, paper_plan=False, hoist=(1, 1, 1)):
     """One CRT residue of one end-to-end oracle inference (run in a spawned
     worker): key generation, encryption of one synthetic request, the whole
     layer list on ciphertexts, decryption, and a check against the integer
@@ -288,13 +411,13 @@ def oracle_residue_inference(workload, L, levels, ti, paper_plan=False):
     n, t, kt = ps.n, ps.t[ti], len(ps.t)
     if workload == "mnist":
         mnet, img = W.mnist_net(), W.image()
-        layers = W.layers_mnist(mnet, n, levels, support_sum=not paper_plan)
+        layers = W.layers_mnist(mnet, n, levels, support_sum=not paper_plan, hoist=hoist)
         msgs, pos = OL.pack_convolution(img, mnet.kh, mnet.kw, mnet.stride, n)
         want = plain_mnist(img, mnet)
     elif workload == "dense64":
         Wd, x = W.dense_weights(), W.dense_vector()
         copies = W.dense64_input_copies(Wd)
-        layers = W.layers_dense64(Wd, n)
+        layers = W.layers_dense64(Wd, n, hoist[1])
         v, pos = OL.pack_stacked(x, 6, copies, n)
         msgs = [np.asarray(v, np.int64)]
         want = [v * v for v in plain_dense(x, Wd)]
@@ -326,7 +449,7 @@ def oracle_residue_inference(workload, L, levels, ti, paper_plan=False):
             "ok": out == [w % t for w in want], "ops": dict(ev.counts)}
 
 
-def oracle_e2e_inference(workload="mnist", L=5, levels=None, paper_plan=False) -> dict:
+def oracle_e2e_inference(workload="mnist", L=5, levels=None, paper_plan=False, hoist=(1, 1, 1)) -> dict:
     """One whole inference on the CPU oracle, its CRT residues in parallel
     spawned processes (one core each).  Seconds per phase are the slowest
     residue's; `eval_s` (the layer list on ciphertexts) is the figure the
@@ -337,7 +460,7 @@ def oracle_e2e_inference(workload="mnist", L=5, levels=None, paper_plan=False) -
     t0 = time.perf_counter()
     with ProcessPoolExecutor(max_workers=kt, mp_context=multiprocessing.get_context("spawn")) as ex:
         res = list(ex.map(oracle_residue_inference, [workload] * kt, [L] * kt, [levels] * kt, range(kt),
-                          [paper_plan] * kt))
+                          [paper_plan] * kt, [hoist] * kt))
     wall = time.perf_counter() - t0
     agg = {k: max(r[k] for r in res) for k in ("keygen_s", "encrypt_s", "eval_s", "decrypt_s")}
     agg.update({"ok": all(r["ok"] for r in res), "residues": kt, "wall_s": wall, "ops_per_residue": res[0]["ops"]})
@@ -347,13 +470,13 @@ def oracle_e2e_inference(workload="mnist", L=5, levels=None, paper_plan=False) -
 E2E_WORKLOADS = ("mnist", "head", "dense64")
 
 
-def cpu_baseline_obj(workload="mnist", L=5, levels=None, paper_plan=False):
+def cpu_baseline_obj(workload="mnist", L=5, levels=None, paper_plan=False, hoist=(1, 1, 1)):
     """The oracle timed on this host: for the MNIST-shaped network and the
     head, one whole inference end to end (residues in parallel processes);
     for the larger networks, per-operation samples scaled by the plan's
     operation counts."""
     if workload in E2E_WORKLOADS:
-        r = oracle_e2e_inference(workload, L, levels, paper_plan)
+        r = oracle_e2e_inference(workload, L, levels, paper_plan, hoist)
         return {"value": 1.0 / r["eval_s"], "unit": "inferences/s", "cores": r["residues"],
                 "kind": "oracle end-to-end",
                 "sample": (f"one whole inference of one synthetic request: the layer list on ciphertexts for all "
@@ -363,7 +486,7 @@ def cpu_baseline_obj(workload="mnist", L=5, levels=None, paper_plan=False):
                 "decrypt_s": r["decrypt_s"], "ops_per_residue": r["ops_per_residue"],
                 "sample_wall_s": round(r["wall_s"], 1)}
     t0 = time.perf_counter()
-    sec, desc = oracle_sample(workload=workload, L=L, levels=levels, paper_plan=paper_plan)
+    sec, desc = oracle_sample(workload=workload, L=L, levels=levels, paper_plan=paper_plan, hoist=hoist)
     return {"value": 1.0 / sec, "unit": "inferences/s", "cores": 1, "kind": "oracle (per-op samples x op counts)",
             "sample": desc, "sample_wall_s": round(time.perf_counter() - t0, 1)}
 
@@ -380,18 +503,18 @@ def run_reference(args):
     if rank != 0:
         return
     for _ in range(args.warmup):
-        oracle_sample(1, 1, args.workload, args.L, args.levels, args.paper_last_layer)
+        oracle_sample(1, 1, args.workload, args.L, args.levels, args.paper_last_layer, args.hoist)
     secs = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        s, desc = oracle_sample(1, 1, args.workload, args.L, args.levels, args.paper_last_layer)
+        s, desc = oracle_sample(1, 1, args.workload, args.L, args.levels, args.paper_last_layer, args.hoist)
         secs.append(s)
     wall = time.perf_counter() - t0
     sec = statistics.median(secs)
     value = 1.0 / sec
     e2e_run = None
     if args.workload in E2E_WORKLOADS and not args.no_cpu_baseline:
-        r = oracle_e2e_inference(args.workload, args.L, args.levels, args.paper_last_layer)
+        r = oracle_e2e_inference(args.workload, args.L, args.levels, args.paper_last_layer, args.hoist)
         e2e_run = {"value": 1.0 / r["eval_s"], "unit": "inferences/s", "cores": r["residues"],
                    "eval_s": r["eval_s"], "correct": r["ok"], "wall_s": round(r["wall_s"], 1)}
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "inferences/s", "n_gpus": args.gpus,
@@ -476,6 +599,9 @@ KERNEL_BYTES = {
     "ks_intt_p": lambda n, L: 16 * n,                # special-prime inner product in, x_P out
     # inner product: one unit = two coefficients of one (ct, prime): L digit words in, 2 words out, each x2
     "ks_ip": lambda n, L: 2 * 8 * (L + 2),
+    # rotate-sum inner product: one unit = one 64 x 64-bit product, which reads
+    # one key word (the digits are read once for all elements and components)
+    "ks_ip_sum": lambda n, L: 8,
     "ntt_fwd": lambda n, L: 16 * n,
     "ntt_inv": lambda n, L: 16 * n,
     # element-wise kernels: one unit = one output word
@@ -552,7 +678,8 @@ def run_ours(args):
         net = L.lola_net_create(ctx, {"repr": "convolution", "n_msgs": 3 * cnet.k1 * cnet.k1,
                                       "n_elems": cnet.o1 * cnet.o1}, layers)
     elif args.workload == "lola_dense":
-        layers = W.layers_lola_dense(mnet, n, levels=args.levels, support_sum=not args.paper_last_layer)
+        layers = W.layers_lola_dense(mnet, n, levels=args.levels, support_sum=not args.paper_last_layer,
+                                     hoist=args.hoist)
         img_slots = np.asarray(W.dense_image_slots(), dtype=np.int64)
         net = L.lola_net_create(ctx, {"repr": "dense", "n_msgs": 1, "n_elems": 784, "slot": img_slots}, layers)
     elif args.workload == "head":
@@ -562,11 +689,11 @@ def run_ours(args):
     elif args.workload == "dense64":
         Wd = W.dense_weights()
         copies = W.dense64_input_copies(Wd)
-        layers = W.layers_dense64(Wd, n)
+        layers = W.layers_dense64(Wd, n, args.hoist[1])
         net = L.lola_net_create(ctx, {"repr": "stacked", "n_msgs": 1, "n_elems": Wd.shape[1], "d": 6,
                                       "copies": copies}, layers)
     else:
-        layers = W.layers_mnist(mnet, n, args.levels, support_sum=not args.paper_last_layer)
+        layers = W.layers_mnist(mnet, n, args.levels, support_sum=not args.paper_last_layer, hoist=args.hoist)
         net = L.lola_net_create(ctx, {"repr": "convolution", "n_msgs": 25, "n_elems": 169}, layers)
     n_in, n_out = net.shape()
     steps_needed = net.rotation_steps()
@@ -802,6 +929,15 @@ def run_ours(args):
     else:
         roofline.update({"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": (hbm_achieved / hbm_peak) if hbm_achieved else None, "peak_source": peak_src})
+    if dom == "ks_ip_sum":
+        # the rotate-sum inner product: 64 x 64-bit products per second against
+        # the measured rate of the same multiply-accumulate on register data
+        peak_mac = alu["mac64"] / 1e9
+        achieved = d["units"] / (d["ms"] / 1000.0) / 1e9
+        roofline.update({"bound": "alu", "achieved": achieved, "peak": peak_mac, "unit": "G products/s",
+                         "frac": achieved / peak_mac,
+                         "peak_source": "measured: lola_alu_rate mac64 (the inner product's 64 x 64 -> 128-bit "
+                                        "multiply-accumulate with REDC on register data, CUDA events)"})
     roofline["traffic"] = traffic
     # NTT rate of the mod-up transforms as limb bytes (read + write, 16 n) per second
     ntt_gbs = None
@@ -811,7 +947,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline_obj(args.workload, args.L, args.levels, args.paper_last_layer)
+        cpu = cpu_baseline_obj(args.workload, args.L, args.levels, args.paper_last_layer, args.hoist)
 
     if rank == 0:
         srt = sorted(step_ms)
@@ -824,6 +960,10 @@ def run_ours(args):
                        "last_layer": ("interleaved row-major, rotate-and-sum over all n slots (the paper's)"
                                       if args.paper_last_layer or args.workload not in SUPPORT_SUM_WORKLOADS else
                                       "interleaved row-major, rotate-and-sum over the occupied slots only"),
+                       "rotate_and_sum_steps_per_key_switch": (
+                           dict(zip(("stack", "stacked_rowmajor", "last_layer"), args.hoist))
+                           if args.workload in SUPPORT_SUM_WORKLOADS else
+                           {"stacked_rowmajor": args.hoist[1]} if args.workload == "dense64" else 1),
                        "levels": [Lq] + list(args.levels or []),
                        "autotune": ({"table": tune["table"], "seconds": round(t_tune, 2)} if tune else "defaults"),
                        "aux_primes": len(L.lola_ctx_aux_primes(ctx)), "parallelism": f"replicas x{world}",
@@ -898,6 +1038,9 @@ def primitives_case(L, ctx, ps, ev, pool, B, args, alu):
         "ntt_inv": (lambda: L.lola_ntt_inverse(ctx, work, 2 * B, Lq, stream), B),
         "rotate": (lambda: L.lola_rotate(ctx, ev, ps_src, ps_dst, B, steps, stream), B),
         "rotate_hoisted_x8": (lambda: L.lola_rotate_hoisted(ctx, ev, ps_src, hout, B, hsteps, stream), B * len(hsteps)),
+        # x plus its rotations by 3 / 7 steps, one key switch per ciphertext
+        "rotate_sum_x3": (lambda: L.lola_rotate_sum(ctx, ev, ps_src, ps_dst, B, hsteps[:3], stream), B),
+        "rotate_sum_x7": (lambda: L.lola_rotate_sum(ctx, ev, ps_src, ps_dst, B, hsteps[:7], stream), B),
         "multiply_relin": (lambda: L.lola_multiply(ctx, ev, ps_src, ps_src + (half * ct_bytes if B > 1 else 0),
                                                    ps_prod, half, stream=stream), half),
     }
@@ -933,9 +1076,11 @@ def run_primitives(args):
     `--n`, `--L` 60-bit primes + a special prime, `--batch` ciphertexts):
     forward NTT and inverse NTT of all 2 B L limb-polynomials, B rotations by
     random steps in [1, n/2) (drawn from a pool of up to 32 distinct steps,
-    one Galois key each), B/2 ct x ct products with relinearisation, and
+    one Galois key each), B/2 ct x ct products with relinearisation,
     rotate_hoisted_x8 (every ciphertext rotated by 8 of the steps sharing one
-    decomposition); one launch per operation.  Per operation: device time
+    decomposition) and rotate_sum_x3 / _x7 (every ciphertext plus its
+    rotations by 3 / 7 of the steps, one key switch); one launch per
+    operation.  Per operation: device time
     per launch (CUDA events), per ciphertext, and the transforms' rate
     against the measured butterfly rate (lola_alu_rate).  `--sweep` runs the
     whole grid B in {1, 2, 4, ..., 256} x n in {8192, 16384} x L in 4..8 (the
@@ -1001,7 +1146,8 @@ def run_serve(args):
         L.lola_autotune(ctx4)
     mnet, Wh = W.mnist_net(), W.head_weights()
     d2, l2 = {"repr": "convolution", "n_msgs": 25, "n_elems": 169}, W.layers_mnist(mnet, n, W.MNIST_LEVELS,
-                                                                                        support_sum=True)
+                                                                                        support_sum=True,
+                                                                                        hoist=W.MNIST_HOIST)
     d4, l4 = {"repr": "dense", "n_msgs": 1, "n_elems": 4096}, W.layers_head(Wh, n)
     keys = {}
     for name, ctx, d, layers in (("mnist", ctx2, d2, l2), ("head", ctx4, d4, l4)):

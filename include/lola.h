@@ -233,6 +233,23 @@ int lola_rotate_noalloc(lola_ctx* ctx, const lola_keys* keys, const uint64_t* in
  * LOLA_E_PARAM, LOLA_E_CUDA, LOLA_E_NOMEM (scratch is allocated per call). */
 int lola_rotate_hoisted(lola_ctx* ctx, const lola_keys* keys, const uint64_t* in, uint64_t* out, size_t count,
                         const int32_t* steps, size_t n_steps, void* stream);
+/* Rotate-sum (the rotate-and-sum of Sec. 4.1 with several doubling steps in
+ * one key switch; not in the paper, which takes one rotation per step):
+ * out_i = in_i + sum_s rot(in_i, steps[s]) for each of `count` ciphertexts
+ * (device, [count][2][L][n], NTT form; out caller-owned, same layout, must
+ * not overlap in).  Steps: 0 < step < n/2 right shifts of each slot row, 0 =
+ * row swap, repeats allowed, at most 64; two doubling steps x + rot(x, a),
+ * then + rot(., b), are steps {a, b, a + b}.  The digits of c1 are raised
+ * to Q*P once; the inner products with every step's key (digits permuted as
+ * in lola_rotate_hoisted) are added over Q*P and brought down by one
+ * mod-down, so the result decrypts to the sum of the rotations and differs
+ * from adding lola_rotate_hoisted's outputs by the rounding of one mod-down
+ * instead of one per step.  n_steps = 0 copies in to out.  Errors:
+ * LOLA_E_NOKEY, LOLA_E_PARAM, LOLA_E_CUDA, LOLA_E_NOMEM (scratch is
+ * allocated per call: count * (L + D*(L+K) + 2(L+K) + 2K) * n words, D the
+ * key-switching digits). */
+int lola_rotate_sum(lola_ctx* ctx, const lola_keys* keys, const uint64_t* in, uint64_t* out, size_t count,
+                    const int32_t* steps, size_t n_steps, void* stream);
 /* Modulus switching (BFV; not in the paper, which leaves SEAL's modulus
  * management unstated): every ciphertext of in (device, [count][2][L_from][n]
  * over q_0..q_{L_from-1}) becomes one over the first L_to primes, out
@@ -331,6 +348,13 @@ typedef struct {
   uint32_t d;             /* STACK / STACKED_ROWMAJOR: block size 2^d; MOD_SWITCH: primes kept */
   uint32_t copies;        /* STACK / STACKED_ROWMAJOR: number of copies (power of two) */
   uint32_t stride;        /* COMBINE: slot offset between consecutive messages */
+  uint32_t hoist;         /* STACK, STACKED_ROWMAJOR, INTERLEAVED_ROWMAJOR(_SUPPORT), DENSE_ROWMAJOR:
+                             rotate-and-sum doubling steps per key switch.  0 or 1: one rotation per
+                             step (the paper's).  m > 1: each run of up to m consecutive nonzero
+                             shifts a_1 .. a_r (r > 1) is one lola_rotate_sum over the 2^r - 1 subset
+                             sums of the a_i (mod n/2, ascending bit mask); a row swap, a lone shift
+                             or a run with a subset sum of 0 mod n/2 stays one rotation per step.
+                             The network then needs the keys of those subset sums. */
 } lola_layer;
 
 /* Input description: n_msgs messages per request, n_elems vector elements
@@ -385,7 +409,8 @@ int lola_pack_stacked(const int64_t* vec, uint32_t k, uint32_t d, uint32_t copie
  * or -1 in lola_profile_enable for all of them.  Read returns the summed
  * device milliseconds, the launch count and the work units processed since
  * the last enable: limb-polynomials (one n-word limb) for transform kernels,
- * 64-bit words or coefficient positions for element-wise kernels. */
+ * 64-bit words or coefficient positions for element-wise kernels, 64 x
+ * 64-bit products for the rotate-sum inner product (ks_ip_sum). */
 int lola_profile_enable(lola_ctx* ctx, int kind, int on);
 int lola_profile_read(lola_ctx* ctx, int kind, double* ms, uint64_t* launches, uint64_t* units);
 int lola_profile_kinds(void);
@@ -407,6 +432,9 @@ const char* lola_profile_name(int kind);
  *   LOLA_ALU_FWD_BUTTERFLY_SPARSE  forward butterflies for a prime of the
  *                            form 2^60 - c 2^32 + 1, whose product qh q
  *                            needs one 32-bit multiply, per second
+ *   LOLA_ALU_MAC64           the key-switch inner products' operation: 64 x
+ *                            64 -> 128-bit products of 60-bit words summed four
+ *                            at a time and reduced (REDC), products per second
  * per_second and ms (best kernel time) may be NULL.  Errors: LOLA_E_PARAM
  * (unknown kind), LOLA_E_CUDA, LOLA_E_NOMEM. */
 #define LOLA_ALU_FWD_BUTTERFLY 0
@@ -417,6 +445,7 @@ const char* lola_profile_name(int kind);
 #define LOLA_ALU_MUL_HI_U32 5
 #define LOLA_ALU_MMA_S8 6
 #define LOLA_ALU_FWD_BUTTERFLY_SPARSE 7
+#define LOLA_ALU_MAC64 8
 int lola_alu_rate(lola_ctx* ctx, int kind, double* per_second, double* ms);
 /* Kernel launches issued by the library since context creation (launches
  * inside a replayed CUDA graph are counted once, when captured). */

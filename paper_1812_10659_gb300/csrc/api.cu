@@ -360,6 +360,42 @@ int lola_rotate_hoisted(lola_ctx* ctx, const lola_keys* keys, const uint64_t* in
   return rc;
 }
 
+int lola_rotate_sum(lola_ctx* ctx, const lola_keys* keys, const uint64_t* in, uint64_t* out, size_t count,
+                    const int32_t* steps, size_t n_steps, void* stream) {
+  CHECK(ctx && keys && ((in && out && (steps || !n_steps)) || !count), LOLA_E_PARAM, "null argument");
+  Ctx* c = ctx->c;
+  if (!count) return LOLA_OK;
+  const size_t ctb = c->ct_words() * 8;
+  CHECK((const char*)out + count * ctb <= (const char*)in || (const char*)in + count * ctb <= (const char*)out,
+        LOLA_E_PARAM, "rotate-sum output must not overlap its input");
+  CHECK(n_steps <= 64, LOLA_E_PARAM, "at most 64 steps per rotate-sum");
+  cudaStream_t s = to_stream(stream);
+  std::vector<uint32_t> g(n_steps);
+  std::vector<const uint64_t*> kp(n_steps);
+  for (size_t i = 0; i < n_steps; ++i) {
+    CHECK(steps[i] >= 0 && (uint32_t)steps[i] < c->n / 2, LOLA_E_PARAM, "rotation step out of range");
+    g[i] = galois_for_step(c->n, steps[i]);
+    const SwitchKey* key = keys->k->galois_key(g[i]);
+    CHECK(key, LOLA_E_NOKEY, "missing Galois key for step " + std::to_string(steps[i]));
+    kp[i] = key->buf.u64();
+  }
+  const size_t sw = rotate_sum_scratch_words(c, count);
+  void* buf = nullptr;
+  LOLA_CUDA_TRY(cudaMallocAsync(&buf, sw * 8 + n_steps * 16, s));
+  uint64_t* scratch = (uint64_t*)buf;
+  const uint64_t** dkeys = (const uint64_t**)(scratch + sw);
+  uint32_t* dgal = (uint32_t*)(dkeys + n_steps);
+  int rc = LOLA_OK;
+  if (n_steps && (cudaMemcpyAsync(dkeys, kp.data(), n_steps * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+                  cudaMemcpyAsync(dgal, g.data(), n_steps * 4, cudaMemcpyHostToDevice, s) != cudaSuccess))
+    rc = fail(LOLA_E_CUDA, "upload of rotation tables failed");
+  if (rc == LOLA_OK) rc = rotate_sum(c, in, out, count, (uint32_t)n_steps, dgal, dkeys, (uint32_t)count, scratch, s);
+  // the host vectors above must outlive the async copies
+  cudaStreamSynchronize(s);
+  cudaFreeAsync(buf, s);
+  return rc;
+}
+
 int lola_mod_switch(lola_ctx* ctx, const uint64_t* in, uint64_t* out, size_t count, uint32_t L_from, uint32_t L_to,
                     void* stream) {
   CHECK(ctx && ((in && out) || !count), LOLA_E_PARAM, "null argument");

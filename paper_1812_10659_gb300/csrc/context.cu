@@ -128,7 +128,7 @@ const char* kernel_name(int id) {
       "ntt_fwd", "ntt_inv", "ntt_fwd_signed", "encode_lift", "slots_to_coeff", "coeff_to_slots", "enc_msg",
       "ks_decompose", "ks_modup", "ks_intt_p", "ks_moddown", "ks_ip",
       "add", "mul_plain", "mac_scalar", "tensor", "lift_q_to_b", "scale_round", "decrypt_round", "misc",
-      "mod_switch"};
+      "mod_switch", "ks_ip_sum"};
   return (id >= 0 && id < KI_COUNT) ? names[id] : "?";
 }
 

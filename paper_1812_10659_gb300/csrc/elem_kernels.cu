@@ -23,12 +23,6 @@ static unsigned grid_for(size_t items, int threads) {
 }
 
 // ------------------------------------------------------------- key switching
-// REDC of a 128-bit sum T < q 2^64: T 2^-64 mod q in [0, q).
-__device__ __forceinline__ uint64_t redc128(unsigned __int128 T, uint64_t q, uint64_t qinv) {
-  const uint64_t lo = (uint64_t)T, hi = (uint64_t)(T >> 64);
-  const uint64_t m = lo * qinv;
-  return csub(hi + mulhi64(m, q) + (lo != 0), q);
-}
 
 // Inner product over the digits, both key components at once:
 //   ACC[comp][j] = sum_i D[i][j] * key[comp][i][j]   (keys are Montgomery-scaled)
@@ -139,6 +133,89 @@ __global__ void __launch_bounds__(256, 4) ke_ks_ip(const CtxDev* __restrict__ C,
       uint64_t* A1 = a.acc + ct * a.acc_stride + (size_t)(LK + j) * n + k;
       *(ulonglong2*)A0 = make_ulonglong2(acc0[0], acc0[1]);
       *(ulonglong2*)A1 = make_ulonglong2(acc1[0], acc1[1]);
+    }
+  }
+}
+
+// Inner product of a rotate-sum (x plus its rotations by G Galois elements,
+// one key switch): D holds the raised digits of x's own c1 (decomposed
+// without an automorphism).  For every element g of the entry the digits are
+// gathered through tau_g as in the hoisted rotations and multiplied by g's
+// key; all G * digits products go into one inner product mod q_j, so the one
+// mod-down that follows rounds once.  The addends are x itself (a.accum: c0
+// and c1) and tau_g(c0) of every element.  Entry
+// ct / gal_div uses elements and keys [e G, e G + G) of d_gal / d_keys.
+// Each element's products are reduced on their own (as in ke_ks_ip); the
+// reductions are exact, so the sum mod q_j is the same however it is split.
+// ACC must not overlap D: other threads gather D words at any position.
+// Up to 128 registers (the gathered and key loads of all digits are issued
+// together; at 64 registers they spill).
+template <int DT>
+__global__ void __launch_bounds__(256, 2) ke_ks_ip_sum(const CtxDev* __restrict__ C, KsDev a, int final_out) {
+  const int L = C->L, LK = L + C->K, logn = C->logn;
+  const int dn = DT > 0 ? DT : (int)C->dnum;
+  const int G = (int)a.gsum;
+  const size_t n = C->n, half = n >> 1;
+  const int J = final_out ? L : LK;
+  const size_t total = a.count * J * half;
+  for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < total; w += (size_t)gridDim.x * blockDim.x) {
+    const size_t k = 2 * (w % half);
+    const size_t r = w / half;
+    const int j = r % J;
+    const size_t ct = r / J;
+    const PrimeDev& P = C->pr[j];
+    const size_t kLK = C->kLK, jk = j < L ? (size_t)j : (size_t)C->kL + (j - L);
+    const size_t krow1 = (size_t)C->kdnum * kLK;
+    const size_t e0 = (ct / a.gal_div) * (size_t)G;
+    uint64_t acc0[2] = {0, 0}, acc1[2] = {0, 0}, c0s[2] = {0, 0};
+    for (int gi = 0; gi < G; ++gi) {
+      const uint64_t* key = a.d_keys[e0 + gi];
+      const uint32_t m = gal_src((uint32_t)k, a.d_gal[e0 + gi], logn);
+      const size_t kd = m & ~1u;
+      const bool swp = (m & 1u) != 0;
+      // each element's digits reduced on their own (at most 8 terms per sum)
+      unsigned __int128 s0[2] = {0, 0}, s1[2] = {0, 0};
+#pragma unroll
+      for (int i = 0; i < (DT > 0 ? DT : dn); ++i) {
+        ulonglong2 d = *(const ulonglong2*)(a.D + ((ct * dn + i) * LK + j) * n + kd);
+        if (swp) d = make_ulonglong2(d.y, d.x);
+        const ulonglong2 k0 = __ldg((const ulonglong2*)(key + ((size_t)i * kLK + jk) * n + k));
+        const ulonglong2 k1 = __ldg((const ulonglong2*)(key + (krow1 + (size_t)i * kLK + jk) * n + k));
+        s0[0] += (unsigned __int128)d.x * k0.x;
+        s0[1] += (unsigned __int128)d.y * k0.y;
+        s1[0] += (unsigned __int128)d.x * k1.x;
+        s1[1] += (unsigned __int128)d.y * k1.y;
+        if ((i & 7) == 7 || i == dn - 1) {
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            acc0[e] = add_mod(acc0[e], redc128(s0[e], P.q, P.qinv), P.q);
+            acc1[e] = add_mod(acc1[e], redc128(s1[e], P.q, P.qinv), P.q);
+            s0[e] = s1[e] = 0;
+          }
+        }
+      }
+      if (j < L) {
+        const uint64_t* c0p = a.c0 + (ct * 2 * L + j) * n + kd;
+        c0s[0] = add_mod(c0s[0], c0p[swp ? 1 : 0], P.q);
+        c0s[1] = add_mod(c0s[1], c0p[swp ? 0 : 1], P.q);
+      }
+    }
+    if (j < L) {
+      // x itself and the gathered tau_g(c0); on the ciphertext primes the
+      // keys carry P^-1, so ACC + addends is what the mod-down expects
+      const ulonglong2 x0 = *(const ulonglong2*)(a.accum + ((ct * 2 + 0) * L + j) * n + k);
+      const ulonglong2 x1 = *(const ulonglong2*)(a.accum + ((ct * 2 + 1) * L + j) * n + k);
+      acc0[0] = add_mod(add_mod(acc0[0], c0s[0], P.q), x0.x, P.q);
+      acc0[1] = add_mod(add_mod(acc0[1], c0s[1], P.q), x0.y, P.q);
+      acc1[0] = add_mod(acc1[0], x1.x, P.q);
+      acc1[1] = add_mod(acc1[1], x1.y, P.q);
+    }
+    if (final_out) {
+      *(ulonglong2*)(a.out + ((ct * 2 + 0) * L + j) * n + k) = make_ulonglong2(acc0[0], acc0[1]);
+      *(ulonglong2*)(a.out + ((ct * 2 + 1) * L + j) * n + k) = make_ulonglong2(acc1[0], acc1[1]);
+    } else {
+      *(ulonglong2*)(a.acc + ct * a.acc_stride + (size_t)j * n + k) = make_ulonglong2(acc0[0], acc0[1]);
+      *(ulonglong2*)(a.acc + ct * a.acc_stride + (size_t)(LK + j) * n + k) = make_ulonglong2(acc1[0], acc1[1]);
     }
   }
 }
@@ -524,6 +601,24 @@ int ks_ip(Ctx* c, const KsDev& a, bool final_out, cudaStream_t s) {
     case 7: ELEM_LAUNCH(KI_KS_IP_Q, ke_ks_ip<7>, pairs, c->dev, a, (int)final_out); break;
     case 8: ELEM_LAUNCH(KI_KS_IP_Q, ke_ks_ip<8>, pairs, c->dev, a, (int)final_out); break;
     default: ELEM_LAUNCH(KI_KS_IP_Q, ke_ks_ip<0>, pairs, c->dev, a, (int)final_out); break;
+  }
+  return post(c);
+}
+
+// profiled units: 64 x 64-bit products (each pair of coefficients takes
+// G x digits x 2 components x 2 of them)
+int ks_ip_sum(Ctx* c, const KsDev& a, bool final_out, cudaStream_t s) {
+  const size_t pairs = a.count * (final_out ? c->L : c->L + c->K) * (c->n / 2);
+  ProfScope ps_(c, KI_KS_IP_SUM, s, (uint64_t)pairs * a.gsum * c->dnum * 4);
+  const unsigned grid = grid_for(pairs, 256);
+  switch (c->dnum) {
+    case 1: ke_ks_ip_sum<1><<<grid, 256, 0, s>>>(c->dev, a, (int)final_out); break;
+    case 2: ke_ks_ip_sum<2><<<grid, 256, 0, s>>>(c->dev, a, (int)final_out); break;
+    case 3: ke_ks_ip_sum<3><<<grid, 256, 0, s>>>(c->dev, a, (int)final_out); break;
+    case 4: ke_ks_ip_sum<4><<<grid, 256, 0, s>>>(c->dev, a, (int)final_out); break;
+    case 5: ke_ks_ip_sum<5><<<grid, 256, 0, s>>>(c->dev, a, (int)final_out); break;
+    case 6: ke_ks_ip_sum<6><<<grid, 256, 0, s>>>(c->dev, a, (int)final_out); break;
+    default: ke_ks_ip_sum<0><<<grid, 256, 0, s>>>(c->dev, a, (int)final_out); break;
   }
   return post(c);
 }

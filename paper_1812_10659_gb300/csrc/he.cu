@@ -222,6 +222,51 @@ int rotate_hoisted(Ctx* c, const uint64_t* in, uint64_t* out, size_t count, size
   return LOLA_OK;
 }
 
+// Rotate-sum (several rotate-and-sum doubling steps in one key switch): c1
+// is decomposed without an automorphism and raised to Q * P once; one inner
+// product adds, for every element g, the gathered digits tau_g(D) times g's
+// key, plus x and every tau_g(c0); one INTT mod P and one mod-down follow.
+// scratch: digits [count][L][n], D [count][dnum][L+K][n], the inner
+// products [count][2][L+K][n] (not over D: the gathers read all of it), x_P
+// [count][2][K][n].
+size_t rotate_sum_scratch_words(const Ctx* c, size_t count) {
+  const size_t LK = c->L + c->K;
+  return count * (c->L + c->dnum * LK + 2 * LK + 2 * (size_t)c->K) * (size_t)c->n;
+}
+
+int rotate_sum(Ctx* c, const uint64_t* in, uint64_t* out, size_t count, uint32_t G, const uint32_t* d_gal,
+               const uint64_t* const* d_keys, uint32_t gal_div, uint64_t* scratch, cudaStream_t s) {
+  if (!count) return LOLA_OK;
+  const size_t n = c->n, L = c->L, LK = c->L + c->K;
+  if (!G) {
+    LOLA_CUDA_TRY(cudaMemcpyAsync(out, in, count * c->ct_words() * 8, cudaMemcpyDeviceToDevice, s));
+    return LOLA_OK;
+  }
+  KsDev a{};
+  a.c0 = in;
+  a.c1 = in;
+  a.accum = in;
+  a.out = out;
+  a.dig = scratch;
+  a.D = a.dig + count * L * n;
+  a.acc = a.D + count * c->dnum * LK * n;
+  a.acc_stride = 2 * LK * n;
+  a.xP = a.acc + count * 2 * LK * n;
+  a.count = count;
+  a.gal = 1;                                  // decompose: no automorphism
+  a.gal_div = 1;
+  TRY(k::ks_decompose(c, a, s));
+  TRY(k::ks_modup(c, a, true, s));
+  a.d_gal = d_gal;
+  a.d_keys = d_keys;
+  a.gal_div = gal_div ? gal_div : 1;
+  a.gsum = G;
+  TRY(k::ks_ip_sum(c, a, c->K == 0, s));
+  if (!c->K) return LOLA_OK;
+  TRY(k::ks_intt_p(c, a, s));
+  return k::ks_moddown(c, a, s);
+}
+
 // ------------------------------------------------------- modulus switching
 // scratch: the dropped limbs in coefficient form [count][2][n], and two
 // intermediate ciphertext arrays when more than one prime is dropped

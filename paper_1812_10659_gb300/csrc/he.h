@@ -62,6 +62,14 @@ int rotate_hoisted(Ctx* c, const uint64_t* in, uint64_t* out, size_t count, size
                    const uint64_t* const* d_keys, uint64_t* scratch, cudaStream_t s);
 int rotate(Ctx* c, const uint64_t* in, uint64_t* out, const uint64_t* accum, size_t count, const RotSpec& r,
            uint64_t* scratch, cudaStream_t s);
+// Rotate-sum: out = in + sum over G Galois elements of tau_g(in), one key
+// switch per ciphertext (the digits raised once, one inner product over all
+// elements, one mod-down).  Entry e = i / gal_div of the `count` ciphertexts
+// uses elements and keys [e G, e G + G) of the device arrays d_gal / d_keys.
+// out must not overlap in.
+size_t rotate_sum_scratch_words(const Ctx* c, size_t count);
+int rotate_sum(Ctx* c, const uint64_t* in, uint64_t* out, size_t count, uint32_t G, const uint32_t* d_gal,
+               const uint64_t* const* d_keys, uint32_t gal_div, uint64_t* scratch, cudaStream_t s);
 
 // Modulus switching of `count` ciphertexts [count][2][L_from][n] to
 // [count][2][L_to][n] (L_to <= L_from <= c->L; the first primes of Q stay):

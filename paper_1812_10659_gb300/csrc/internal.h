@@ -41,7 +41,7 @@ enum KernelId {
   KI_NTT_FWD = 0, KI_NTT_INV, KI_NTT_SIGNED, KI_ENCODE_LIFT, KI_SLOTS_TO_COEFF, KI_COEFF_TO_SLOTS, KI_ENC_MSG,
   KI_KS_DECOMPOSE, KI_KS_MODUP, KI_KS_IP_P, KI_KS_MODDOWN, KI_KS_IP_Q,
   KI_ADD, KI_MUL_PLAIN, KI_MAC_SCALAR, KI_TENSOR, KI_LIFT_Q_TO_B, KI_SCALE_ROUND, KI_DECRYPT_ROUND, KI_MISC,
-  KI_MOD_SWITCH, KI_COUNT
+  KI_MOD_SWITCH, KI_KS_IP_SUM, KI_COUNT
 };
 const char* kernel_name(int id);
 

@@ -55,6 +55,9 @@ struct KsDev {
   uint32_t ip_gather;
   // rotation: the inner product adds tau_g(c0) by gathering c0 itself
   uint32_t c0_gather;
+  // rotate-sum (ks_ip_sum): Galois elements per entry; entry e's elements and
+  // keys are d_gal / d_keys [e gsum, e gsum + gsum)
+  uint32_t gsum;
 };
 
 namespace k {
@@ -92,6 +95,7 @@ int ks_moddown(Ctx* c, const KsDev& a, cudaStream_t s);
 
 // element-wise / basis conversion (elem_kernels.cu)
 int ks_ip(Ctx* c, const KsDev& a, bool final_out, cudaStream_t s);   // inner product over digits
+int ks_ip_sum(Ctx* c, const KsDev& a, bool final_out, cudaStream_t s);   // the same over a rotate-sum's elements
 int add(Ctx* c, const uint64_t* a, const uint64_t* b, uint64_t* out, size_t count, cudaStream_t s);
 int sub(Ctx* c, const uint64_t* a, const uint64_t* b, uint64_t* out, size_t count, cudaStream_t s);
 // mode: MONT_TO x -> x 2^64; MONT_FROM x -> x 2^-64; MONT_FROM_KSK a stored

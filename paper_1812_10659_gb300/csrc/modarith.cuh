@@ -110,6 +110,13 @@ __device__ __forceinline__ uint64_t mont_mul(uint64_t a, uint64_t b, uint64_t q,
   return csub(t, q);
 }
 
+// REDC of a 128-bit sum T < q 2^64: T 2^-64 mod q in [0, q).
+__device__ __forceinline__ uint64_t redc128(unsigned __int128 T, uint64_t q, uint64_t qinv) {
+  const uint64_t lo = (uint64_t)T, hi = (uint64_t)(T >> 64);
+  const uint64_t m = lo * qinv;
+  return csub(hi + mulhi64(m, q) + (lo != 0), q);
+}
+
 // x mod q for any 64-bit x, given f = floor(2^64 / q).
 __device__ __forceinline__ uint64_t reduce64(uint64_t x, uint64_t q, uint64_t f) {
   uint64_t r = x - mulhi64(x, f) * q;

@@ -60,13 +60,57 @@ struct Builder {
     for (int32_t s : st) steps.insert(s);
     net->ops.push_back(o);
   }
-  // x <- x + rot(x, s) for s in shifts, on all `msgs` messages of x
-  int rotate_and_sum(int x, uint32_t msgs, const std::vector<int32_t>& shifts) {
-    for (int32_t s : shifts) {
+  // x <- x + rot(x, s) for s in shifts (0 = row swap), on all `msgs`
+  // messages of x.  hoist = m > 1: runs of up to m consecutive nonzero
+  // shifts a_1 .. a_r (r > 1) become one rotate-sum over the 2^r - 1 subset
+  // sums (sum_{i in S} a_i mod n/2, S as a bit mask, ascending), which adds
+  // the same rotations of x in one key switch; a row swap, a lone shift, or
+  // a run with a subset sum of 0 mod n/2 stays x + rot(x, s) per step.
+  int rotate_and_sum(int x, uint32_t msgs, const std::vector<int32_t>& shifts, uint32_t hoist = 1) {
+    const uint32_t h = c->n / 2;
+    std::vector<int32_t> run;
+    auto single = [&](int32_t s) {
       const int y = vreg(msgs);
       rot(y, x, x, msgs, std::vector<int32_t>(msgs, s));
       x = y;
+    };
+    auto flush = [&]() {
+      if (run.empty()) return;
+      std::vector<int32_t> sums;
+      bool zero = false;
+      for (uint32_t mask = 1; mask < (1u << run.size()); ++mask) {
+        uint64_t t = 0;
+        for (size_t i = 0; i < run.size(); ++i)
+          if (mask >> i & 1) t += (uint64_t)run[i];
+        t %= h;
+        zero |= t == 0;
+        sums.push_back((int32_t)t);
+      }
+      if (run.size() == 1 || zero) {
+        for (int32_t s : run) single(s);
+      } else {
+        Op o;
+        o.kind = OP_ROT_SUM;
+        o.src = x;
+        o.dst = vreg(msgs);
+        o.msgs = msgs;
+        o.steps = sums;
+        for (int32_t s : sums) steps.insert(s);
+        net->ops.push_back(o);
+        x = o.dst;
+      }
+      run.clear();
+    };
+    for (int32_t s : shifts) {
+      if (s == 0) {
+        flush();
+        single(0);
+        continue;
+      }
+      run.push_back(s);
+      if (run.size() >= std::max<uint32_t>(hoist, 1)) flush();
     }
+    flush();
     return x;
   }
   size_t add_plaintexts(const std::vector<std::vector<int64_t>>& v) {
@@ -428,7 +472,7 @@ static int layer_stack(Builder& b, const lola_layer& L, Repr& r) {
   std::vector<int32_t> shifts;
   for (uint32_t sh = s; sh < per_row * s; sh *= 2) shifts.push_back((int32_t)sh);
   if (L.copies > per_row) shifts.push_back(0);   // row swap
-  r.reg = b.rotate_and_sum(r.reg, 1, shifts);
+  r.reg = b.rotate_and_sum(r.reg, 1, shifts, L.hoist);
   r.kind = LOLA_REPR_STACKED;
   r.block = s;
   r.copies = L.copies;
@@ -466,7 +510,7 @@ static int layer_stacked_rowmajor(Builder& b, const lola_layer& L, Repr& r) {
   b.net->ops.push_back(mp);
   std::vector<int32_t> shifts;
   for (uint32_t j = 0; j < L.d; ++j) shifts.push_back((int32_t)(1u << j));
-  int y = b.rotate_and_sum(mp.dst, R, shifts);
+  int y = b.rotate_and_sum(mp.dst, R, shifts, L.hoist);
   Repr out;
   out.kind = LOLA_REPR_INTERLEAVED;
   out.msgs = 1;
@@ -533,7 +577,7 @@ static int layer_rowmajor_sparse(Builder& b, const lola_layer& L, Repr& r, bool 
   Repr out;
   out.kind = LOLA_REPR_SPARSE;
   out.msgs = rows;
-  out.reg = b.rotate_and_sum(mp.dst, rows, shifts);
+  out.reg = b.rotate_and_sum(mp.dst, rows, shifts, L.hoist);
   for (uint32_t o = 0; o < rows; ++o) out.pos.push_back({o, 0});
   r = out;
   return LOLA_OK;
@@ -642,7 +686,7 @@ static int layer_rowmajor_support(Builder& b, const lola_layer& L, Repr& r) {
   Repr out;
   out.kind = LOLA_REPR_DENSE;
   out.msgs = rows;
-  out.reg = b.rotate_and_sum(mp.dst, rows, shifts);
+  out.reg = b.rotate_and_sum(mp.dst, rows, shifts, L.hoist);
   for (uint32_t o = 0; o < rows; ++o) out.pos.push_back({o, slot});
   r = out;
   return LOLA_OK;
@@ -849,11 +893,12 @@ static int build_executor(Ctx* c, Net* net, uint32_t B, Executor* ex) {
     const Ctx* lc = net->lctx.at(o.level);
     const size_t cnt = (size_t)o.msgs * B * kt;
     maxcnt = std::max(maxcnt, cnt);
-    if (o.kind == OP_ROT) {
+    if (o.kind == OP_ROT || o.kind == OP_ROT_SUM) {
       const size_t per_msg = (size_t)B * kt;
       const size_t chunk_msgs = std::max<size_t>(1, kMaxRotCts / per_msg);
       const size_t mc = std::min<size_t>(o.msgs, chunk_msgs);
-      sw = std::max(sw, rotate_scratch_words(lc, mc * per_msg) + 2 * mc);
+      sw = std::max(sw, o.kind == OP_ROT ? rotate_scratch_words(lc, mc * per_msg) + 2 * mc
+                                         : rotate_sum_scratch_words(lc, mc * per_msg));
     }
     if (o.kind == OP_SQUARE) sw = std::max(sw, multiply_scratch_words(lc, cnt, true));
     if (o.kind == OP_ROT_HOISTED) sw = std::max(sw, rotate_hoisted_scratch_words(lc, (size_t)B * kt, o.msgs));
@@ -876,19 +921,20 @@ static int bind_keys(Ctx* c, Net* net, Executor* ex, const KeySet* ks) {
   ex->op_keys.resize(net->ops.size());
   for (size_t i = 0; i < net->ops.size(); ++i) {
     const Op& o = net->ops[i];
-    if (o.kind != OP_ROT && o.kind != OP_ROT_HOISTED) continue;
-    std::vector<uint32_t> g(o.msgs);
-    std::vector<const uint64_t*> kp(o.msgs);
-    for (uint32_t m = 0; m < o.msgs; ++m) {
+    if (o.kind != OP_ROT && o.kind != OP_ROT_HOISTED && o.kind != OP_ROT_SUM) continue;
+    const size_t ne = o.kind == OP_ROT_SUM ? o.steps.size() : o.msgs;   // table entries
+    std::vector<uint32_t> g(ne);
+    std::vector<const uint64_t*> kp(ne);
+    for (size_t m = 0; m < ne; ++m) {
       g[m] = galois_for_step(c->n, o.steps[m]);
       const SwitchKey* key = ks->galois_key(g[m]);
       if (!key) return fail(LOLA_E_NOKEY, "missing Galois key for rotation step " + std::to_string(o.steps[m]));
       kp[m] = key->buf.u64();
     }
-    TRY(ex->op_gal[i].alloc(o.msgs * 4));
-    TRY(ex->op_keys[i].alloc(o.msgs * 8));
-    LOLA_CUDA_TRY(cudaMemcpy(ex->op_gal[i].p, g.data(), o.msgs * 4, cudaMemcpyHostToDevice));
-    LOLA_CUDA_TRY(cudaMemcpy(ex->op_keys[i].p, kp.data(), o.msgs * 8, cudaMemcpyHostToDevice));
+    TRY(ex->op_gal[i].alloc(ne * 4));
+    TRY(ex->op_keys[i].alloc(ne * 8));
+    LOLA_CUDA_TRY(cudaMemcpy(ex->op_gal[i].p, g.data(), ne * 4, cudaMemcpyHostToDevice));
+    LOLA_CUDA_TRY(cudaMemcpy(ex->op_keys[i].p, kp.data(), ne * 8, cudaMemcpyHostToDevice));
   }
   if (ex->graph) {
     cudaGraphExecDestroy(ex->graph);
@@ -935,6 +981,18 @@ static int run_ops(Ctx* root, Net* net, Executor* ex, const KeySet* ks, cudaStre
           TRY(rotate(c, reg(o.src, o.src_off + m0), reg(o.dst, o.dst_off + m0),
                      o.aux >= 0 ? reg(o.aux, o.aux_off + m0) : nullptr, (size_t)mc * per_msg, rs, ex->scratch.u64(),
                      s));
+        }
+        break;
+      }
+      case OP_ROT_SUM: {
+        const uint32_t per_msg = (uint32_t)(B * kt);
+        const uint32_t chunk = std::max<uint32_t>(1, kMaxRotCts / per_msg);
+        for (uint32_t m0 = 0; m0 < o.msgs; m0 += chunk) {
+          const uint32_t mc = std::min(chunk, o.msgs - m0);
+          // every ciphertext of the chunk uses the op's one list of steps
+          TRY(rotate_sum(c, reg(o.src, o.src_off + m0), reg(o.dst, o.dst_off + m0), (size_t)mc * per_msg,
+                         (uint32_t)o.steps.size(), (const uint32_t*)ex->op_gal[i].p,
+                         (const uint64_t* const*)ex->op_keys[i].p, mc * per_msg, ex->scratch.u64(), s));
         }
         break;
       }

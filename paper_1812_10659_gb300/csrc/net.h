@@ -8,7 +8,10 @@
 
 namespace lola {
 
-enum OpKind { OP_MAC = 1, OP_ROT = 2, OP_SUM = 3, OP_MULPT = 4, OP_SQUARE = 5, OP_ROT_HOISTED = 6, OP_MODSWITCH = 7 };
+enum OpKind {
+  OP_MAC = 1, OP_ROT = 2, OP_SUM = 3, OP_MULPT = 4, OP_SQUARE = 5, OP_ROT_HOISTED = 6, OP_MODSWITCH = 7,
+  OP_ROT_SUM = 8
+};
 
 // A register holds `msgs` messages for every request of the batch and every
 // plaintext modulus: layout [msg][request][t_i][2][L'][n], L' the register's
@@ -22,6 +25,8 @@ struct Op {
   uint32_t level_to = 0;              // OP_MODSWITCH: primes of the result
   // OP_ROT: per-message rotation step (0 = row swap); aux = accumulator register (or -1)
   // OP_ROT_HOISTED: message src_off of src rotated by steps[m] into message m of dst
+  // OP_ROT_SUM: message m of src plus its rotations by every one of steps
+  // (the same steps for all messages) into message m of dst, one key switch
   std::vector<int32_t> steps;
   // OP_MULPT: plaintexts [msgs][kt][level][n] at pt_first (in plaintext blocks
   // of the op's level); src_stride 0 = broadcast

@@ -15,7 +15,9 @@
 //    thread;
 //  * mma.sync m16n8k32 s8 x s8 -> s32 (the integer tensor-core path an
 //    int8-split matrix transform would use): four independent accumulators
-//    per warp, 2 * 16 * 8 * 32 integer operations per instruction.
+//    per warp, 2 * 16 * 8 * 32 integer operations per instruction;
+//  * the key-switch inner product's multiply-accumulate (64 x 64 -> 128-bit
+//    products summed four at a time, then REDC).
 #include <cuda_runtime.h>
 
 #include "internal.h"
@@ -210,6 +212,41 @@ __global__ void __launch_bounds__(kThreads) kb_mma_s8(int iters, uint64_t* __res
   sink[tid] = acc;
 }
 
+// The inner products' operation: 64 x 64 -> 128-bit products of a digit
+// word and a key word summed in 128 bits, four digits per sum, two key
+// components and two coefficients per thread, one REDC and modular add per
+// sum (as ke_ks_ip / ke_ks_ip_sum do at four digits).  The digits depend on
+// the previous iteration's sums (one XOR each), so nothing is hoisted out of
+// the loop.
+__global__ void __launch_bounds__(kThreads) kb_mac64(uint64_t q, uint64_t qinv, int iters,
+                                                     uint64_t* __restrict__ sink) {
+  const uint64_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  uint64_t d[2][4], k0[4], k1[4], a0[2] = {0, 0}, a1[2] = {0, 0};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    d[0][i] = (tid * 8 + i) % q;
+    d[1][i] = (tid * 8 + 4 + i) % q;
+    k0[i] = (0x9E3779B97F4A7C15ull * (i + 1)) % q;
+    k1[i] = (0xBB67AE8584CAA73Bull * (i + 1)) % q;
+  }
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      unsigned __int128 s0 = 0, s1 = 0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        s0 += (unsigned __int128)d[e][i] * k0[i];
+        s1 += (unsigned __int128)d[e][i] * k1[i];
+      }
+      a0[e] = add_mod(a0[e], redc128(s0, q, qinv), q);
+      a1[e] = add_mod(a1[e], redc128(s1, q, qinv), q);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) d[e][i] ^= a0[e];   // stays below 2^60 (both are)
+    }
+  }
+  sink[tid] = a0[0] ^ a0[1] ^ a1[0] ^ a1[1];
+}
+
 }  // namespace
 
 // operations per thread per loop iteration of each kind
@@ -218,17 +255,18 @@ static double ops_per_iter(int kind) {
     case 0: case 1: case 2: case 7: return 32; // butterflies (4 stages x 8)
     case 3: case 4: case 5: return 64;         // instructions (8 rounds x 8 chains)
     case 6: return 4.0 * 2 * 16 * 8 * 32 / 32; // int8 operations per thread (4 mma per warp)
+    case 8: return 16;                         // 64 x 64-bit products (2 coefficients x 2 components x 4)
     default: return 0;
   }
 }
 
 int alu_rate(Ctx* c, int kind, double* per_second, double* ms_out) {
-  if (kind < 0 || kind > 7) return fail(LOLA_E_PARAM, "unknown ALU benchmark kind");
+  if (kind < 0 || kind > 8) return fail(LOLA_E_PARAM, "unknown ALU benchmark kind");
   LOLA_CUDA_TRY(cudaSetDevice(c->device));
   int sms = 0;
   LOLA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
   const int blocks = sms * kCtasPerSm;
-  const int iters = (kind <= 2 || kind == 7) ? 2048 : (kind <= 5 ? 16384 : 8192);
+  const int iters = (kind <= 2 || kind == 7) ? 2048 : (kind <= 5 ? 16384 : (kind == 8 ? 4096 : 8192));
   DevBuf sink, tw;
   TRY_OK(sink.alloc((size_t)blocks * kThreads * 8));
   TRY_OK(tw.alloc(16 * 8));
@@ -264,6 +302,7 @@ int alu_rate(Ctx* c, int kind, double* per_second, double* ms_out) {
       case 4: kb_imad<1><<<blocks, kThreads>>>(0x9E3779B9u, iters, sink.u64()); break;
       case 5: kb_imad<2><<<blocks, kThreads>>>(0x9E3779B9u, iters, sink.u64()); break;
       case 6: kb_mma_s8<<<blocks, kThreads>>>(iters, sink.u64()); break;
+      case 8: kb_mac64<<<blocks, kThreads>>>(q, c->host.pr[0].qinv, iters, sink.u64()); break;
     }
     cudaEventRecord(e1, nullptr);
     cudaError_t err = cudaEventSynchronize(e1);

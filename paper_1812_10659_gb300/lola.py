@@ -47,7 +47,7 @@ class lola_params(C.Structure):
 class lola_layer(C.Structure):
     _fields_ = [("op", C.c_int), ("in_repr", C.c_int), ("out_repr", C.c_int), ("rows", C.c_uint32),
                 ("cols", C.c_uint32), ("weights", C.POINTER(C.c_int64)), ("d", C.c_uint32),
-                ("copies", C.c_uint32), ("stride", C.c_uint32)]
+                ("copies", C.c_uint32), ("stride", C.c_uint32), ("hoist", C.c_uint32)]
 
 
 class lola_input(C.Structure):
@@ -95,6 +95,7 @@ _SIGS = {
     "lola_mul_plain": (C.c_int, [P, P, I64P, P, C.c_size_t, U32P, P]),
     "lola_rotate_noalloc": (C.c_int, [P, P, P, P, C.c_size_t, C.c_int32, P]),
     "lola_rotate_hoisted": (C.c_int, [P, P, P, P, C.c_size_t, I32P, C.c_size_t, P]),
+    "lola_rotate_sum": (C.c_int, [P, P, P, P, C.c_size_t, I32P, C.c_size_t, P]),
     "lola_net_create": (C.c_int, [P, C.POINTER(lola_input), C.POINTER(lola_layer), C.c_size_t, C.POINTER(P)]),
     "lola_net_destroy": (None, [P]),
     "lola_net_rotation_steps": (C.c_int, [P, I32P, C.POINTER(C.c_size_t)]),
@@ -355,6 +356,14 @@ def lola_rotate_hoisted(ctx, keys, inp, out, count, steps, stream=None):
                                       stream_handle(stream)))
 
 
+def lola_rotate_sum(ctx, keys, inp, out, count, steps, stream=None):
+    """out_i = in_i + sum of its rotations by every step in `steps`, one key
+    switch per ciphertext (see include/lola.h)."""
+    st = np.ascontiguousarray(np.asarray(steps, dtype=np.int32))
+    _check(load().lola_rotate_sum(ctx, keys, dptr(inp), dptr(out), count, st.ctypes.data_as(I32P), st.size,
+                                  stream_handle(stream)))
+
+
 def lola_rotate_noalloc(ctx, keys, inp, out, count, step, stream=None):
     """Rotation of `count` ciphertexts by one step using the library's static
     scratch area (no device allocation); see include/lola.h."""
@@ -366,7 +375,7 @@ NOALLOC_SCRATCH_BYTES = 32 << 20
 
 TUNE_KERNELS, TUNE_BUCKETS, TUNE_VARIANTS = 4, 6, 4
 TUNE_NAMES = ("ks_decompose", "ks_modup", "ks_intt_p", "ks_moddown")
-TUNE_GEOMETRY = ("cta", "cluster16", "cluster32")
+TUNE_GEOMETRY = ("cta", "cluster16", "cluster32", "cluster4x16")
 
 
 def lola_autotune(ctx, stream=None) -> dict:
@@ -483,7 +492,7 @@ class Network:
 
 def lola_net_create(ctx, input_desc: dict, layers: list) -> Network:
     """input_desc: {"repr", "n_msgs", "n_elems", "slot"=None, "d"=0, "copies"=0};
-    layers: dicts as produced by workloads.layers_* ({"op", "weights", "d", "copies", "stride"})."""
+    layers: dicts as produced by workloads.layers_* ({"op", "weights", "d", "copies", "stride", "hoist"})."""
     keep = []
     slot = input_desc.get("slot")
     if slot is not None:
@@ -509,7 +518,8 @@ def lola_net_create(ctx, input_desc: dict, layers: list) -> Network:
             wp = wa.ctypes.data_as(I64P)
         rin, rout = LAYER_REPR[op]
         d = Ld["L"] if op == "mod_switch" else Ld.get("d", 0)
-        arr[i] = lola_layer(LAYER[op], rin, rout, rows, cols, wp, d, Ld.get("copies", 0), Ld.get("stride", 0))
+        arr[i] = lola_layer(LAYER[op], rin, rout, rows, cols, wp, d, Ld.get("copies", 0), Ld.get("stride", 0),
+                            Ld.get("hoist", 0))
     out = P()
     _check(load().lola_net_create(ctx, C.byref(inp), arr, len(layers), C.byref(out)))
     return Network(out, keep)
@@ -557,7 +567,7 @@ def lola_profile_read(ctx, kind):
 
 
 ALU_KINDS = {"fwd_butterfly": 0, "inv_butterfly": 1, "fwd_butterfly_c": 2, "mad_lo_u32": 3,
-             "mad_wide_u32": 4, "mul_hi_u32": 5, "mma_s8": 6, "fwd_butterfly_sparse": 7}
+             "mad_wide_u32": 4, "mul_hi_u32": 5, "mma_s8": 6, "fwd_butterfly_sparse": 7, "mac64": 8}
 
 
 def lola_alu_rate(ctx, kind) -> tuple:

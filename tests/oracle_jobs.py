@@ -13,9 +13,6 @@ if ROOT not in sys.path:
 import workloads as W  # noqa: E402
 from oracle import bfv, encoding, lola as OL  # noqa: E402
 
-MNIST_STEPS = sorted({169, 338, 507, 676} | {1 << j for j in range(13)} | set(range(1, 7)))
-
-
 def rotation_steps(layers, n, t, st):
     """Rotation steps the plan uses (0 = row swap), from a slot-level run."""
     seen = set()
@@ -37,9 +34,25 @@ def rotation_steps(layers, n, t, st):
     return sorted(seen)
 
 
+def mnist_layers():
+    """The MNIST-shaped layer list bench.py runs: modulus switching, the last
+    layer summed over the occupied slots, hoisted rotate-and-sums."""
+    return W.layers_mnist(W.mnist_net(), W.params_mnist().n, W.MNIST_LEVELS, support_sum=True, hoist=W.MNIST_HOIST)
+
+
+def mnist_steps():
+    """Nonzero rotation steps of that plan (its Galois keys besides the row swap)."""
+    ps = W.params_mnist()
+    net = W.mnist_net()
+    msgs, pos = OL.pack_convolution(W.image(), net.kh, net.kw, net.stride, ps.n)
+    t = ps.t[0]
+    st = OL.State([np.asarray(m, np.int64) % t for m in msgs], pos)
+    return [s for s in rotation_steps(mnist_layers(), ps.n, t, st) if s]
+
+
 def mnist_residue(ti: int, key_seed: int, enc_seed: int, img_idx: int = 0, msg0: int = 0):
-    """Full MNIST-shaped network (n = 16384, L = 5 -> 4 -> 2, the last layer
-    summed over the occupied slots as bench.py runs it) for CRT residue
+    """Full MNIST-shaped network (n = 16384, L = 5 -> 4 -> 2, the plan of
+    mnist_layers as bench.py runs it) for CRT residue
     ti of image img_idx, whose 25 messages are messages msg0 ... msg0 + 24 of
     a batch encrypted with k_t = len(t) residues per message (ciphertext id =
     message * k_t + ti).  Returns the output ciphertexts as an array
@@ -48,8 +61,8 @@ def mnist_residue(ti: int, key_seed: int, enc_seed: int, img_idx: int = 0, msg0:
     P = bfv.Params(ps.n, ps.q, ps.L, ps.K, ps.t, ps.alpha)
     kt, t = len(ps.t), ps.t[ti]
     net, img = W.mnist_net(), W.image(idx=img_idx)
-    layers = W.layers_mnist(net, ps.n, W.MNIST_LEVELS, support_sum=True)
-    keys = bfv.keygen(P, key_seed, rotations=MNIST_STEPS, relin=True, row_swap=True)
+    layers = mnist_layers()
+    keys = bfv.keygen(P, key_seed, rotations=mnist_steps(), relin=True, row_swap=True)
     msgs, pos = OL.pack_convolution(img, net.kh, net.kw, net.stride, ps.n)
     cts = [bfv.encrypt(P, keys.pk, encoding.encode(m, t), t, enc_seed, (msg0 + i) * kt + ti)
            for i, m in enumerate(msgs)]

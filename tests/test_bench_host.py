@@ -126,3 +126,26 @@ def test_oracle_end_to_end_inference_dense64():
     assert r["ops_per_residue"]["square"] == 1
     obj = bench.cpu_baseline_obj("dense64", 3, None)
     assert obj["kind"] == "oracle end-to-end" and obj["cores"] == 1 and obj["value"] > 0
+
+
+def test_plan_counts_without_hoisting_are_the_op_count_tables():
+    for workload in ("mnist", "lola_dense"):
+        for paper in (False, True):
+            c = bench.plan_counts(workload, {"mnist": 5}.get(workload, 6),
+                                  W.MNIST_LEVELS if workload == "mnist" else W.LOLA_DENSE_LEVELS, paper, (1, 1, 1))
+            want = bench.OP_COUNTS_LEVELS[bench.counts_key(workload, paper)]
+            assert {lv: {k: v for k, v in d.items() if k != "rot_sum"} for lv, d in c.items()} == want
+            assert all(d["rot_sum"] == {} for d in c.values())
+
+
+def test_plan_counts_of_the_hoisted_mnist_plan():
+    # at 4 primes: the stack's [1024, 2048 | 4096 | row swap] and 7 rounds of
+    # [1, 2 | 4, 8 | ... | 256, 512] -> 1 + 35 rotate-sums of 3 rotations, 2
+    # single rotations + 6 for the rounds' combine; at 2 primes 10 outputs x
+    # [1, 2, 4 | 1024, 2048, 4096 | row swap] -> 20 rotate-sums of 7, 10 single
+    c = bench.plan_counts("mnist", 5, W.MNIST_LEVELS, False, (2, 2, 3))
+    assert {lv: (d["rot"], d["rot_sum"]) for lv, d in c.items()} == {5: (4, {}), 4: (8, {3: 36}), 2: (10, {7: 20})}
+    # three steps per key switch everywhere: the stack's [1024, 2048, 4096 |
+    # row swap], 7 rounds of [1, 2, 4 | 8, 16, 32 | 64, 128, 256 | 512]
+    c = bench.plan_counts("mnist", 5, W.MNIST_LEVELS, False, (3, 3, 3))
+    assert {lv: (d["rot"], d["rot_sum"]) for lv, d in c.items()} == {5: (4, {}), 4: (14, {7: 22}), 2: (10, {7: 20})}

@@ -2,7 +2,8 @@
 
 The MNIST-shaped network (n = 16384, five 60-bit primes switched to four and
 two after the squares, three CRT plaintext moduli, the last layer summed
-over the occupied slots, batch of 16 requests, autotuned launch geometry,
+over the occupied slots, the rotate-and-sums hoisted several doubling steps
+per key switch, batch of 16 requests, autotuned launch geometry,
 CUDA-graph replay) and the transfer-learning head
 (n = 16384, three primes, one plaintext modulus, batch of 64): for one
 sampled request and one CRT residue the oracle runs the same layer list on
@@ -50,13 +51,13 @@ def test_full_mnist_batch16_every_output_ciphertext_matches_oracle(oracle_runs):
     ps = W.params_mnist()
     n = ps.n
     mnet = W.mnist_net()
-    layers = W.layers_mnist(mnet, n, W.MNIST_LEVELS, support_sum=True)
+    layers = J.mnist_layers()
     ctx = make_ctx(ps)
     try:
         Lb.lola_autotune(ctx)                 # the geometry table bench.py times with
         packed = [Lb.lola_pack_convolution(W.image(idx=i), 5, 5, 2, n) for i in range(MNIST_B)]
         net = Lb.lola_net_create(ctx, {"repr": "convolution", "n_msgs": 25, "n_elems": packed[0][1]}, layers)
-        assert sorted(s for s in net.rotation_steps() if s) == J.MNIST_STEPS
+        assert sorted(s for s in net.rotation_steps() if s) == J.mnist_steps()
         sk, ev = gpu_keys(Lb, ctx, net, KEY_SEED)
         ct = Lb.lola_encrypt(ctx, sk, np.concatenate([p[0] for p in packed]), ENC_SEED)
         out = Lb.lola_ct_create(ctx, MNIST_B * 10)

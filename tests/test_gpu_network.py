@@ -69,13 +69,16 @@ def test_dense64_bit_exact_vs_oracle():
         Lb.lola_ctx_destroy(ctx)
 
 
-@pytest.mark.parametrize("levels,K,alpha,support", [(None, 1, 1, False), ((4, 2), 1, 1, False), ((3, 1), 1, 1, False),
-                                                    ((4, 2), 2, 2, False), ((3, 1), 2, 2, False), ((4, 2), 1, 1, True),
-                                                    (None, 2, 2, True)])
-def test_mini_mnist_bit_exact_vs_oracle(levels, K, alpha, support):
+@pytest.mark.parametrize("levels,K,alpha,support,hoist", [
+    (None, 1, 1, False, 1), ((4, 2), 1, 1, False, 1), ((3, 1), 1, 1, False, 1), ((4, 2), 2, 2, False, 1),
+    ((3, 1), 2, 2, False, 1), ((4, 2), 1, 1, True, 1), (None, 2, 2, True, 1), ((4, 2), 1, 1, True, (2, 2, 3)),
+    ((4, 2), 1, 1, False, (2, 3, 2)), (None, 2, 2, True, (3, 3, 4))])
+def test_mini_mnist_bit_exact_vs_oracle(levels, K, alpha, support, hoist):
     # levels: modulus switching after each square (every later ciphertext,
     # including the relinearisation at level 4 or 3, compared word for word);
-    # K = 2, alpha = 2: key-switching digits of two primes (the MNIST workload's)
+    # K = 2, alpha = 2: key-switching digits of two primes; hoist: rotate-and-
+    # sum doubling steps per key switch in the stack, the stacked row-major
+    # and the last layer (rotate-sums next to single rotations)
     need_gpu()
     Lb = lib()
     n = 1024
@@ -84,7 +87,7 @@ def test_mini_mnist_bit_exact_vs_oracle(levels, K, alpha, support):
     t = ps.t[0]
     mnet = W.mnist_net(seed=7, maps=2, hidden=12, classes=3, h=12, w=12, k=3, stride=2)
     img = W.image(seed=7, h=12, w=12)
-    layers = W.layers_mnist(mnet, n, levels, support_sum=support)
+    layers = W.layers_mnist(mnet, n, levels, support_sum=support, hoist=hoist)
     ctx = make_ctx(ps)
     try:
         msgs, win = Lb.lola_pack_convolution(img, 3, 3, 2, n)

@@ -184,6 +184,57 @@ def test_hoisted_rotations_match_oracle(setup):
         Lb.lola_ct_destroy(dst)
 
 
+@pytest.mark.parametrize("which", [0, 1, 2])
+def test_rotate_sum_matches_oracle(setup, which):
+    """x plus its rotations by several steps in one key switch (one raising,
+    one inner product over every step's key, one mod-down): bit-exact against
+    the oracle's rotate_sum_hoisted, and decrypting to the summed slots."""
+    S = setup
+    Lb, ctx, ev, sk, P, ok = S["L"], S["ctx"], S["ev"], S["sk"], S["P"], S["okeys"]
+    kt, n = len(P.t), P.n
+    steps = [[1], [1, 3], [3, 0, n // 4, 1, 1]][which]
+    slots = np.random.default_rng(17 + which).integers(0, 1000, (3, n))
+    cts = oracle_encrypt_all(S, slots, 18)                       # 3 messages x kt residues
+    src = Lb.lola_ct_import(ctx, ct_stack(cts, kt))
+    dst = Lb.lola_ct_create(ctx, 3)
+    try:
+        Lb.lola_rotate_sum(ctx, ev, Lb.lola_ct_data(src), Lb.lola_ct_data(dst), 3 * kt, steps)
+        got = Lb.lola_ct_export(ctx, dst, (kt, 2, P.L, n)).reshape(-1, 2, P.L, n)
+        for i, c in enumerate(cts):
+            ref = bfv.rotate_sum_hoisted(P, ok, c, steps)
+            assert np.array_equal(got[i, 0], ref.c[0]) and np.array_equal(got[i, 1], ref.c[1]), i
+        h = n // 2
+        dec = Lb.lola_decrypt_residues(ctx, sk, dst, kt, n)
+        for m in range(3):
+            for ti, t in enumerate(P.t):
+                v = slots[m] % t
+                want = v.copy()
+                for k in steps:
+                    want = want + (np.concatenate([v[h:], v[:h]]) if k == 0 else
+                                   np.concatenate([np.roll(v[:h], k), np.roll(v[h:], k)]))
+                assert np.array_equal(dec[m, ti], want % t), (m, ti)
+    finally:
+        Lb.lola_ct_destroy(src)
+        Lb.lola_ct_destroy(dst)
+
+
+def test_rotate_sum_rejects_overlap_and_missing_keys(setup):
+    S = setup
+    Lb, ctx, ev = S["L"], S["ctx"], S["ev"]
+    src = Lb.lola_ct_create(ctx, 1)
+    dst = Lb.lola_ct_create(ctx, 1)
+    try:
+        with pytest.raises(Lb.LolaError) as ei:
+            Lb.lola_rotate_sum(ctx, ev, Lb.lola_ct_data(src), Lb.lola_ct_data(dst), 1, [1, 2])
+        assert ei.value.code == -3
+        with pytest.raises(Lb.LolaError) as ei:
+            Lb.lola_rotate_sum(ctx, ev, Lb.lola_ct_data(src), Lb.lola_ct_data(src), 1, [1])
+        assert ei.value.code == -1
+    finally:
+        Lb.lola_ct_destroy(src)
+        Lb.lola_ct_destroy(dst)
+
+
 def test_rotation_missing_key_is_an_error(setup):
     S = setup
     Lb, ctx, ev = S["L"], S["ctx"], S["ev"]

@@ -248,6 +248,14 @@ def _ceil_log2(k: int) -> int:
     return max(0, (k - 1).bit_length())
 
 
+# Rotate-and-sum doubling steps per key switch (stack, stacked row-major,
+# last layer) of the MNIST-shaped network and LoLa-Dense, and of the single
+# dense layer: three steps (seven rotations) per key switch, the fastest of
+# the groupings measured on the MNIST network (1, 2, 3, (2, 3, 3), (3, 3, 4)).
+MNIST_HOIST = (3, 3, 3)
+LOLA_DENSE_HOIST = (3, 3, 3)
+DENSE64_HOIST = 3
+
 # Ciphertext primes kept after each square of the MNIST-shaped network at
 # L = 5: the oracle's exact noise measurement (full network, n = 16384)
 # leaves a 23-bit margin at the output either way, because modulus switching
@@ -444,13 +452,14 @@ def layers_head(Wh: np.ndarray, n: int) -> list:
     ]
 
 
-def layers_dense64(Wd: np.ndarray, n: int) -> list:
+def layers_dense64(Wd: np.ndarray, n: int, hoist: int = 1) -> list:
     """Single dense layer + square; the input arrives already stacked
-    (one copy per output row) so no server-side stacking rotations."""
+    (one copy per output row) so no server-side stacking rotations.
+    hoist: rotate-and-sum doubling steps per key switch."""
     d = _ceil_log2(Wd.shape[1])
     copies = 1 << _ceil_log2(Wd.shape[0])
     return [
-        {"op": "stacked_rowmajor", "weights": Wd, "d": d, "copies": copies},
+        _with_hoist({"op": "stacked_rowmajor", "weights": Wd, "d": d, "copies": copies}, hoist),
         {"op": "square"},
     ]
 
