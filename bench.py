@@ -599,9 +599,9 @@ KERNEL_BYTES = {
     "ks_intt_p": lambda n, L: 16 * n,                # special-prime inner product in, x_P out
     # inner product: one unit = two coefficients of one (ct, prime): L digit words in, 2 words out, each x2
     "ks_ip": lambda n, L: 2 * 8 * (L + 2),
-    # rotate-sum inner product: one unit = one 64 x 64-bit product, which reads
-    # one key word (the digits are read once for all elements and components)
-    "ks_ip_sum": lambda n, L: 8,
+    # (ks_ip_sum, the rotate-sum inner product, counts 64 x 64-bit products
+    # and is stated against the measured multiply-accumulate rate; its DRAM
+    # traffic depends on the number of elements, so no byte model here)
     "ntt_fwd": lambda n, L: 16 * n,
     "ntt_inv": lambda n, L: 16 * n,
     # element-wise kernels: one unit = one output word

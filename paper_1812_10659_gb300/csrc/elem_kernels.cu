@@ -6,6 +6,7 @@
 // conversions, which need every limb of one coefficient at once).
 #include "internal.h"
 #include "kernels.h"
+#include "mac.cuh"
 
 namespace lola {
 
@@ -145,11 +146,10 @@ __global__ void __launch_bounds__(256, 4) ke_ks_ip(const CtxDev* __restrict__ C,
 // mod-down that follows rounds once.  The addends are x itself (a.accum: c0
 // and c1) and tau_g(c0) of every element.  Entry
 // ct / gal_div uses elements and keys [e G, e G + G) of d_gal / d_keys.
-// Each element's products are reduced on their own (as in ke_ks_ip); the
-// reductions are exact, so the sum mod q_j is the same however it is split.
 // ACC must not overlap D: other threads gather D words at any position.
-// Up to 128 registers (the gathered and key loads of all digits are issued
-// together; at 64 registers they spill).
+// The digit and key words are below q (mod-up and key generation reduce
+// them), so each product is below q^2.  Up to 128 registers (the gathered
+// and key loads of all digits are issued together; at 64 they spill).
 template <int DT>
 __global__ void __launch_bounds__(256, 2) ke_ks_ip_sum(const CtxDev* __restrict__ C, KsDev a, int final_out) {
   const int L = C->L, LK = L + C->K, logn = C->logn;
@@ -167,38 +167,45 @@ __global__ void __launch_bounds__(256, 2) ke_ks_ip_sum(const CtxDev* __restrict_
     const size_t kLK = C->kLK, jk = j < L ? (size_t)j : (size_t)C->kL + (j - L);
     const size_t krow1 = (size_t)C->kdnum * kLK;
     const size_t e0 = (ct / a.gal_div) * (size_t)G;
-    uint64_t acc0[2] = {0, 0}, acc1[2] = {0, 0}, c0s[2] = {0, 0};
+    // one 128-bit sum (hi:lo) per component and coefficient over all G x
+    // digits products, kept below q 2^64 by subtracting q from hi after every
+    // digit group of at most 8 products (each below q^2, 8 q < 2^64), then
+    // one REDC: the same residue as reducing every element on its own
+    uint64_t lo0[2] = {0, 0}, hi0[2] = {0, 0}, lo1[2] = {0, 0}, hi1[2] = {0, 0}, c0s[2] = {0, 0};
     for (int gi = 0; gi < G; ++gi) {
       const uint64_t* key = a.d_keys[e0 + gi];
       const uint32_t m = gal_src((uint32_t)k, a.d_gal[e0 + gi], logn);
-      const size_t kd = m & ~1u;
+      const size_t kd = m & ~1u;                  // the aligned pair holding m (swapped when m is odd)
       const bool swp = (m & 1u) != 0;
-      // each element's digits reduced on their own (at most 8 terms per sum)
-      unsigned __int128 s0[2] = {0, 0}, s1[2] = {0, 0};
 #pragma unroll
       for (int i = 0; i < (DT > 0 ? DT : dn); ++i) {
-        ulonglong2 d = *(const ulonglong2*)(a.D + ((ct * dn + i) * LK + j) * n + kd);
-        if (swp) d = make_ulonglong2(d.y, d.x);
+        const ulonglong2 dv = *(const ulonglong2*)(a.D + ((ct * dn + i) * LK + j) * n + kd);
         const ulonglong2 k0 = __ldg((const ulonglong2*)(key + ((size_t)i * kLK + jk) * n + k));
         const ulonglong2 k1 = __ldg((const ulonglong2*)(key + (krow1 + (size_t)i * kLK + jk) * n + k));
-        s0[0] += (unsigned __int128)d.x * k0.x;
-        s0[1] += (unsigned __int128)d.y * k0.y;
-        s1[0] += (unsigned __int128)d.x * k1.x;
-        s1[1] += (unsigned __int128)d.y * k1.y;
+        const uint64_t d0 = swp ? dv.y : dv.x, d1 = swp ? dv.x : dv.y;
+        mac128(lo0[0], hi0[0], d0, k0.x);
+        mac128(lo0[1], hi0[1], d1, k0.y);
+        mac128(lo1[0], hi1[0], d0, k1.x);
+        mac128(lo1[1], hi1[1], d1, k1.y);
         if ((i & 7) == 7 || i == dn - 1) {
 #pragma unroll
           for (int e = 0; e < 2; ++e) {
-            acc0[e] = add_mod(acc0[e], redc128(s0[e], P.q, P.qinv), P.q);
-            acc1[e] = add_mod(acc1[e], redc128(s1[e], P.q, P.qinv), P.q);
-            s0[e] = s1[e] = 0;
+            hi0[e] = csub(hi0[e], P.q);
+            hi1[e] = csub(hi1[e], P.q);
           }
         }
       }
       if (j < L) {
-        const uint64_t* c0p = a.c0 + (ct * 2 * L + j) * n + kd;
-        c0s[0] = add_mod(c0s[0], c0p[swp ? 1 : 0], P.q);
-        c0s[1] = add_mod(c0s[1], c0p[swp ? 0 : 1], P.q);
+        const ulonglong2 cg = *(const ulonglong2*)(a.c0 + (ct * 2 * L + j) * n + kd);
+        c0s[0] = add_mod(c0s[0], swp ? cg.y : cg.x, P.q);
+        c0s[1] = add_mod(c0s[1], swp ? cg.x : cg.y, P.q);
       }
+    }
+    uint64_t acc0[2], acc1[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      acc0[e] = redc128(((unsigned __int128)hi0[e] << 64) | lo0[e], P.q, P.qinv);
+      acc1[e] = redc128(((unsigned __int128)hi1[e] << 64) | lo1[e], P.q, P.qinv);
     }
     if (j < L) {
       // x itself and the gathered tau_g(c0); on the ciphertext primes the

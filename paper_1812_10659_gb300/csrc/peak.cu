@@ -16,11 +16,12 @@
 //  * mma.sync m16n8k32 s8 x s8 -> s32 (the integer tensor-core path an
 //    int8-split matrix transform would use): four independent accumulators
 //    per warp, 2 * 16 * 8 * 32 integer operations per instruction;
-//  * the key-switch inner product's multiply-accumulate (64 x 64 -> 128-bit
-//    products summed four at a time, then REDC).
+//  * the rotate-sum inner product's multiply-accumulate (64 x 64 -> 128-bit
+//    products accumulated with carry, one REDC per 16).
 #include <cuda_runtime.h>
 
 #include "internal.h"
+#include "mac.cuh"
 #include "modarith.cuh"
 
 namespace lola {
@@ -212,15 +213,17 @@ __global__ void __launch_bounds__(kThreads) kb_mma_s8(int iters, uint64_t* __res
   sink[tid] = acc;
 }
 
-// The inner products' operation: 64 x 64 -> 128-bit products of a digit
-// word and a key word summed in 128 bits, four digits per sum, two key
-// components and two coefficients per thread, one REDC and modular add per
-// sum (as ke_ks_ip / ke_ks_ip_sum do at four digits).  The digits depend on
-// the previous iteration's sums (one XOR each), so nothing is hoisted out of
-// the loop.
+// The rotate-sum inner product's operation: 64 x 64 -> 128-bit products
+// accumulated with carry (mac128), two key components and two coefficients
+// per thread, four products per sum between conditional subtractions of q
+// from the high word, one REDC and modular add per 16 products (four
+// elements of four digits, as ke_ks_ip_sum runs them).  Every 16 products the
+// digits take the reduced sums in (one masked XOR each), so nothing is
+// hoisted out of the loop.
 __global__ void __launch_bounds__(kThreads) kb_mac64(uint64_t q, uint64_t qinv, int iters,
                                                      uint64_t* __restrict__ sink) {
   const uint64_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t mask = (1ull << 59) - 1;
   uint64_t d[2][4], k0[4], k1[4], a0[2] = {0, 0}, a1[2] = {0, 0};
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
@@ -229,19 +232,24 @@ __global__ void __launch_bounds__(kThreads) kb_mac64(uint64_t q, uint64_t qinv, 
     k0[i] = (0x9E3779B97F4A7C15ull * (i + 1)) % q;
     k1[i] = (0xBB67AE8584CAA73Bull * (i + 1)) % q;
   }
-  for (int it = 0; it < iters; ++it) {
+  for (int it = 0; it < iters; it += 4) {
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
-      unsigned __int128 s0 = 0, s1 = 0;
+      uint64_t lo0 = 0, hi0 = 0, lo1 = 0, hi1 = 0;
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        s0 += (unsigned __int128)d[e][i] * k0[i];
-        s1 += (unsigned __int128)d[e][i] * k1[i];
+      for (int g = 0; g < 4; ++g) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          mac128(lo0, hi0, d[e][i], k0[i]);
+          mac128(lo1, hi1, d[e][i], k1[i]);
+        }
+        hi0 = csub(hi0, q);
+        hi1 = csub(hi1, q);
       }
-      a0[e] = add_mod(a0[e], redc128(s0, q, qinv), q);
-      a1[e] = add_mod(a1[e], redc128(s1, q, qinv), q);
+      a0[e] = add_mod(a0[e], redc128(((unsigned __int128)hi0 << 64) | lo0, q, qinv), q);
+      a1[e] = add_mod(a1[e], redc128(((unsigned __int128)hi1 << 64) | lo1, q, qinv), q);
 #pragma unroll
-      for (int i = 0; i < 4; ++i) d[e][i] ^= a0[e];   // stays below 2^60 (both are)
+      for (int i = 0; i < 4; ++i) d[e][i] ^= a0[e] & mask;   // d stays below 2^60
     }
   }
   sink[tid] = a0[0] ^ a0[1] ^ a1[0] ^ a1[1];
@@ -256,6 +264,7 @@ static double ops_per_iter(int kind) {
     case 3: case 4: case 5: return 64;         // instructions (8 rounds x 8 chains)
     case 6: return 4.0 * 2 * 16 * 8 * 32 / 32; // int8 operations per thread (4 mma per warp)
     case 8: return 16;                         // 64 x 64-bit products (2 coefficients x 2 components x 4)
+                                               // per iteration (the kernel counts iterations of 4 elements)
     default: return 0;
   }
 }
