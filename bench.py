@@ -65,8 +65,9 @@ def parse():
                     help="mnist / lola_dense: rotate-and-sum doubling steps per key switch in the stack, the "
                          "stacked row-major and the last layer ('a,b,c' or one number for all three; 1 = one "
                          "rotation per step, the paper's; default: the workload's)")
-    ap.add_argument("--grouped-digits", action="store_true",
-                    help="mnist: key-switching digits of two primes with two special primes")
+    ap.add_argument("--one-prime-digits", action="store_true",
+                    help="mnist: key-switching digits of one prime with one special prime (default: digits of "
+                         "two primes with two special primes)")
     ap.add_argument("--L", type=int, default=None,
                     help="ciphertext primes (default: 5 for mnist, 6 for lola_dense)")
     ap.add_argument("--workload", choices=["mnist", "lola_dense", "cifar", "head", "dense64"], default="mnist",
@@ -105,8 +106,8 @@ def parse():
     if args.batch is None:
         args.batch = {"cifar": 2, "head": 64, "dense64": 256}.get(args.workload, 16)
     if args.hoist is None:
-        args.hoist = {"mnist": W.MNIST_HOIST, "lola_dense": W.LOLA_DENSE_HOIST,
-                      "dense64": (W.DENSE64_HOIST,) * 3}.get(args.workload, (1, 1, 1))
+        args.hoist = {"mnist": W.MNIST_HOIST, "lola_dense": W.LOLA_DENSE_HOIST, "cifar": W.CIFAR_HOIST,
+                      "dense64": (W.DENSE64_HOIST,) * 3, "head": (W.HEAD_HOIST,) * 3}.get(args.workload, (1, 1, 1))
     else:
         h = tuple(int(x) for x in str(args.hoist).split(","))
         args.hoist = h * 3 if len(h) == 1 else h
@@ -146,6 +147,8 @@ OP_COUNTS_LEVELS = {"mnist": {5: {"rot": 4, "square": 1, "mul_plain": 0, "mul_sc
                               4: {"rot": 57050, "square": 1, "mul_plain": 8150, "mul_scalar": 0, "add": 61124},
                               2: {"rot": 140, "square": 0, "mul_plain": 10, "mul_scalar": 0, "add": 140}}}
 SUPPORT_SUM_WORKLOADS = ("mnist", "lola_dense")
+# networks whose last product bench.py sums over the occupied slots
+SUPPORT_SUM_LAST_LAYER = ("mnist", "lola_dense", "cifar")
 
 
 def counts_key(workload: str, paper_plan: bool) -> str:
@@ -172,7 +175,7 @@ def plan_layers(workload, L, levels, paper_plan=False, hoist=(1, 1, 1)):
         Wh = W.head_weights()
         v = np.zeros(n, np.int64)
         v[:Wh.shape[1]] = W.feature_vector()
-        return n, W.layers_head(Wh, n), [(0, i) for i in range(Wh.shape[1])], {}, [v]
+        return n, W.layers_head(Wh, n, hoist[1]), [(0, i) for i in range(Wh.shape[1])], {}, [v]
     if workload == "dense64":
         Wd = W.dense_weights()
         copies = W.dense64_input_copies(Wd)
@@ -181,7 +184,7 @@ def plan_layers(workload, L, levels, paper_plan=False, hoist=(1, 1, 1)):
                 [np.asarray(v, np.int64)])
     cnet = W.cifar_net()
     msgs, pos = OL.pack_convolution(W.cifar_padded(W.cifar_image(), cnet.pad), cnet.k1, cnet.k1, cnet.stride, n)
-    return n, W.layers_cifar(cnet, n, levels=levels), pos, {}, msgs
+    return n, W.layers_cifar(cnet, n, levels=levels, hoist=hoist, support_sum=not paper_plan), pos, {}, msgs
 
 
 def plan_counts(workload, L, levels, paper_plan=False, hoist=(1, 1, 1)) -> dict:
@@ -317,13 +320,16 @@ class ClockSampler:
 
 # ------------------------------------------------------------ CPU baseline
 def workload_params(workload, L):
+    """Parameter set of a workload: the MNIST-shaped network uses key-switching
+    digits of two primes with two special primes ("mnist_one_prime": one-prime
+    digits, one special prime)."""
     import workloads as W
     if workload == "dense64":
         return W.params_dense64()
-    if workload == "mnist_grouped":
-        return W.params_mnist_grouped(L)
+    if workload == "mnist_one_prime":
+        return W.params_mnist(L)
     return {"cifar": W.params_cifar, "head": W.params_head, "lola_dense": W.params_lola_dense}.get(
-        workload, W.params_mnist)(L)
+        workload, W.params_mnist_grouped)(L)
 
 
 def oracle_sample(n_rot=1, n_sq=1, workload="mnist", L=5, levels=None, paper_plan=False, hoist=(1, 1, 1)):
@@ -423,7 +429,7 @@ def oracle_residue_inference(workload, L, levels, ti, paper_plan=False, hoist=(1
         want = [v * v for v in plain_dense(x, Wd)]
     else:
         Wh = W.head_weights()
-        layers = W.layers_head(Wh, n)
+        layers = W.layers_head(Wh, n, hoist[1])
         v = np.zeros(n, np.int64)
         x = W.feature_vector()
         v[:len(x)] = x
@@ -663,7 +669,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
 
-    ps = workload_params("mnist_grouped" if args.grouped_digits and args.workload == "mnist" else args.workload,
+    ps = workload_params("mnist_one_prime" if args.one_prime_digits and args.workload == "mnist" else args.workload,
                          args.L)
     n, kt, Lq = ps.n, len(ps.t), ps.L
     mnet = W.mnist_net()
@@ -674,7 +680,8 @@ def run_ours(args):
     B = args.batch
     if args.workload == "cifar":
         cnet = W.cifar_net()
-        layers = W.layers_cifar(cnet, n, levels=args.levels)
+        layers = W.layers_cifar(cnet, n, levels=args.levels, hoist=args.hoist,
+                                support_sum=not args.paper_last_layer)
         net = L.lola_net_create(ctx, {"repr": "convolution", "n_msgs": 3 * cnet.k1 * cnet.k1,
                                       "n_elems": cnet.o1 * cnet.o1}, layers)
     elif args.workload == "lola_dense":
@@ -684,7 +691,7 @@ def run_ours(args):
         net = L.lola_net_create(ctx, {"repr": "dense", "n_msgs": 1, "n_elems": 784, "slot": img_slots}, layers)
     elif args.workload == "head":
         Wh = W.head_weights()
-        layers = W.layers_head(Wh, n)
+        layers = W.layers_head(Wh, n, args.hoist[1])
         net = L.lola_net_create(ctx, {"repr": "dense", "n_msgs": 1, "n_elems": Wh.shape[1]}, layers)
     elif args.workload == "dense64":
         Wd = W.dense_weights()
@@ -957,13 +964,15 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": WORKLOAD_NAME[args.workload], "batch_per_gpu": B, "n": n, "L": Lq, "K": ps.K, "k_t": kt,
                        "key_switch_digit_primes": ps.alpha,
-                       "last_layer": ("interleaved row-major, rotate-and-sum over all n slots (the paper's)"
-                                      if args.paper_last_layer or args.workload not in SUPPORT_SUM_WORKLOADS else
-                                      "interleaved row-major, rotate-and-sum over the occupied slots only"),
+                       "last_layer": ("row-major, rotate-and-sum over all n slots (the paper's)"
+                                      if args.paper_last_layer or args.workload not in SUPPORT_SUM_LAST_LAYER else
+                                      "row-major, rotate-and-sum over the occupied slots only"),
                        "rotate_and_sum_steps_per_key_switch": (
                            dict(zip(("stack", "stacked_rowmajor", "last_layer"), args.hoist))
                            if args.workload in SUPPORT_SUM_WORKLOADS else
-                           {"stacked_rowmajor": args.hoist[1]} if args.workload == "dense64" else 1),
+                           dict(zip(("dense_rowmajor", "last_layer"), args.hoist[1:])) if args.workload == "cifar"
+                           else {"stack": args.hoist[1], "stacked_rowmajor": args.hoist[1]} if args.workload == "head"
+                           else {"stacked_rowmajor": args.hoist[1]}),
                        "levels": [Lq] + list(args.levels or []),
                        "autotune": ({"table": tune["table"], "seconds": round(t_tune, 2)} if tune else "defaults"),
                        "aux_primes": len(L.lola_ctx_aux_primes(ctx)), "parallelism": f"replicas x{world}",
@@ -1137,7 +1146,7 @@ def run_serve(args):
     import workloads as W
     from paper_1812_10659_gb300 import lola as L, serve
 
-    ps2, ps4 = W.params_mnist(args.L), W.params_head()
+    ps2, ps4 = W.params_mnist_grouped(args.L), W.params_head()
     n = ps2.n
     ctx2 = L.lola_ctx_create(ps2.n, ps2.q, ps2.L, ps2.K, ps2.t, alpha=ps2.alpha)
     ctx4 = L.lola_ctx_create(ps4.n, ps4.q, ps4.L, ps4.K, ps4.t, alpha=ps4.alpha)
@@ -1148,7 +1157,7 @@ def run_serve(args):
     d2, l2 = {"repr": "convolution", "n_msgs": 25, "n_elems": 169}, W.layers_mnist(mnet, n, W.MNIST_LEVELS,
                                                                                         support_sum=True,
                                                                                         hoist=W.MNIST_HOIST)
-    d4, l4 = {"repr": "dense", "n_msgs": 1, "n_elems": 4096}, W.layers_head(Wh, n)
+    d4, l4 = {"repr": "dense", "n_msgs": 1, "n_elems": 4096}, W.layers_head(Wh, n, W.HEAD_HOIST)
     keys = {}
     for name, ctx, d, layers in (("mnist", ctx2, d2, l2), ("head", ctx4, d4, l4)):
         h = L.lola_net_create(ctx, d, layers)

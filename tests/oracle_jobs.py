@@ -36,13 +36,14 @@ def rotation_steps(layers, n, t, st):
 
 def mnist_layers():
     """The MNIST-shaped layer list bench.py runs: modulus switching, the last
-    layer summed over the occupied slots, hoisted rotate-and-sums."""
+    layer summed over the occupied slots, hoisted rotate-and-sums (on the
+    parameters of params_mnist_grouped, key-switching digits of two primes)."""
     return W.layers_mnist(W.mnist_net(), W.params_mnist().n, W.MNIST_LEVELS, support_sum=True, hoist=W.MNIST_HOIST)
 
 
 def mnist_steps():
     """Nonzero rotation steps of that plan (its Galois keys besides the row swap)."""
-    ps = W.params_mnist()
+    ps = W.params_mnist_grouped()
     net = W.mnist_net()
     msgs, pos = OL.pack_convolution(W.image(), net.kh, net.kw, net.stride, ps.n)
     t = ps.t[0]
@@ -57,7 +58,7 @@ def mnist_residue(ti: int, key_seed: int, enc_seed: int, img_idx: int = 0, msg0:
     a batch encrypted with k_t = len(t) residues per message (ciphertext id =
     message * k_t + ti).  Returns the output ciphertexts as an array
     [message][2][L_out][n] and the output positions (message, slot)."""
-    ps = W.params_mnist()
+    ps = W.params_mnist_grouped()
     P = bfv.Params(ps.n, ps.q, ps.L, ps.K, ps.t, ps.alpha)
     kt, t = len(ps.t), ps.t[ti]
     net, img = W.mnist_net(), W.image(idx=img_idx)
@@ -73,7 +74,8 @@ def mnist_residue(ti: int, key_seed: int, enc_seed: int, img_idx: int = 0, msg0:
 
 
 def head(key_seed: int, enc_seed: int, idx: int = 0):
-    """Transfer-learning head (n = 16384, L = 3, one t) on feature vector idx,
+    """Transfer-learning head (n = 16384, L = 3, one t; rotate-and-sums hoisted
+    as bench.py runs them) on feature vector idx,
     encrypted as message idx of a batch (ciphertext id idx).  Returns the
     output ciphertexts [message][2][L][n], output positions and the plan's
     rotation steps."""
@@ -81,7 +83,7 @@ def head(key_seed: int, enc_seed: int, idx: int = 0):
     P = bfv.Params(ps.n, ps.q, ps.L, ps.K, ps.t, ps.alpha)
     n, t = ps.n, ps.t[0]
     Wh = W.head_weights()
-    layers = W.layers_head(Wh, n)
+    layers = W.layers_head(Wh, n, W.HEAD_HOIST)
     steps = rotation_steps(layers, n, t, OL.State([np.zeros(n, np.int64)], [(0, i) for i in range(4096)]))
     keys = bfv.keygen(P, key_seed, rotations=[s for s in steps if s], relin=True, row_swap=0 in steps)
     v = np.zeros(n, np.int64)

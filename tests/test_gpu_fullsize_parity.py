@@ -1,11 +1,13 @@
 """Word-for-word GPU parity at full size, in the configuration bench.py times.
 
 The MNIST-shaped network (n = 16384, five 60-bit primes switched to four and
-two after the squares, three CRT plaintext moduli, the last layer summed
+two after the squares, key-switching digits of two primes with two special
+primes, three CRT plaintext moduli, the last layer summed
 over the occupied slots, the rotate-and-sums hoisted several doubling steps
 per key switch, batch of 16 requests, autotuned launch geometry,
 CUDA-graph replay) and the transfer-learning head
-(n = 16384, three primes, one plaintext modulus, batch of 64): for one
+(n = 16384, three primes, one plaintext modulus, hoisted rotate-and-sums,
+batch of 64): for one
 sampled request and one CRT residue the oracle runs the same layer list on
 the same encrypted input with the same keys, and every output ciphertext
 must match the GPU's word for word.  The oracle runs (a minute or two each
@@ -48,7 +50,7 @@ def gpu_keys(Lb, ctx, net, seed):
 
 def test_full_mnist_batch16_every_output_ciphertext_matches_oracle(oracle_runs):
     Lb = lib()
-    ps = W.params_mnist()
+    ps = W.params_mnist_grouped()
     n = ps.n
     mnet = W.mnist_net()
     layers = J.mnist_layers()
@@ -85,7 +87,7 @@ def test_full_head_batch64_every_output_ciphertext_matches_oracle(oracle_runs):
     ps = W.params_head()
     n = ps.n
     Wh = W.head_weights()
-    layers = W.layers_head(Wh, n)
+    layers = W.layers_head(Wh, n, W.HEAD_HOIST)
     ctx = make_ctx(ps)
     try:
         Lb.lola_autotune(ctx)

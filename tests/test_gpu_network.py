@@ -381,8 +381,11 @@ def cifar_int(net, img):
     return OL.int_dense(x, net.w3)
 
 
-@pytest.mark.parametrize("levels", [None, (4, 2)])
-def test_mini_cifar_bit_exact_vs_oracle(levels):
+@pytest.mark.parametrize("levels,hoist,support", [(None, 1, False), ((4, 2), 1, False), ((4, 2), 3, True),
+                                                  (None, (1, 2, 4), True)])
+def test_mini_cifar_bit_exact_vs_oracle(levels, hoist, support):
+    # hoist / support: the two row-major products' rotate-and-sums hoisted,
+    # and the last one summed over its occupied slots, as bench.py runs them
     need_gpu()
     Lb = lib()
     n = 1024
@@ -391,7 +394,7 @@ def test_mini_cifar_bit_exact_vs_oracle(levels):
     t = ps.t[0]
     net_ = W.cifar_net(seed=9, C=2, h=8, w=8, pad=2, k1=4, maps1=6, k2=2, maps2=3, classes=2)
     img = W.cifar_image(seed=9, C=2, h=8, w=8)
-    layers = W.layers_cifar(net_, n, levels=levels)
+    layers = W.layers_cifar(net_, n, levels=levels, hoist=hoist, support_sum=support)
     msgs, pos = OL.pack_convolution(W.cifar_padded(img, net_.pad), net_.k1, net_.k1, net_.stride, n)
     ctx = make_ctx(ps)
     try:

@@ -607,3 +607,21 @@ def test_mini_mnist_hoisted_encrypted_oracle_run():
     # combine 1; last layer 3 outputs x 4 support steps as 3 + 1: 3 x (1 + 1)
     # -> 8 single rotations and 10 rotate-sums (31 rotations without hoisting)
     assert (ev.counts["rot"], ev.counts["rot_sum"]) == (8, 10)
+
+
+def test_hoisted_head_and_cifar_plans_match_integer_network():
+    # the plans bench.py runs: the head's stack and stacked row-major and
+    # CIFAR's two row-major products hoisted three doubling steps per key
+    # switch, CIFAR's last product summed over its 4075 occupied slots
+    n, t = 16384, W.T30[0]
+    Wh, x = W.head_weights(), W.feature_vector()
+    v, pos = lola.pack_dense(x, n)
+    st = lola.run_network(lola.SlotEval(n, t), W.layers_head(Wh, n, W.HEAD_HOIST),
+                          lola.State([np.array(v, np.int64) % t], pos))
+    got = [int(st.msgs[m][s]) for m, s in st.pos]
+    assert [g - t if g > t // 2 else g for g in got] == lola.int_dense(x, Wh)
+    net, img = W.cifar_net(), W.cifar_image(idx=2)
+    msgs, pos = lola.pack_convolution(W.cifar_padded(img, net.pad), net.k1, net.k1, net.stride, n)
+    st = lola.run_network(lola.SlotEval(n, t), W.layers_cifar(net, n, hoist=W.CIFAR_HOIST, support_sum=True),
+                          lola.State([np.array(m, np.int64) % t for m in msgs], pos))
+    assert [int(st.msgs[m][s]) for m, s in st.pos] == [x % t for x in cifar_int(net, img)]

@@ -56,21 +56,22 @@ def params_dense64() -> ParamSet:
 
 
 def params_mnist(L: int = 5) -> ParamSet:
-    """MNIST-shaped network and transfer-learning head: n = 16384, L
-    ciphertext primes of 60 bits plus one 60-bit special prime, one-prime
-    key-switching digits, three ~30-bit plaintext CRT moduli.  (Two-prime
-    digits with two special primes also hold the noise, +25.2 bits at the
-    output against +24.2, and need fewer mod-up transforms, but their second
-    special prime doubles the INTT mod P and widens mod-down's load: measured
-    262.9 against 269.0 inferences/s, so the default keeps one-prime digits;
-    params_mnist_grouped gives the other set.)"""
+    """MNIST-shaped network: n = 16384, L ciphertext primes of 60 bits plus
+    one 60-bit special prime, one-prime key-switching digits, three ~30-bit
+    plaintext CRT moduli.  bench.py runs the network on params_mnist_grouped
+    (digits of two primes): with the hoisted rotate-and-sums the inner
+    products weigh more than the second special prime's transforms, 492.7
+    against 462.8 inferences/s (without hoisting it was the other way,
+    262.9 against 269.0)."""
     return ParamSet(f"mnist_n16384_L{L}", 16384, Q60[:L + 1], L, 1, T30[:3])
 
 
 def params_mnist_grouped(L: int = 5) -> ParamSet:
     """The MNIST-shaped network's parameters with key-switching digits of two
     primes (the last one single when L is odd) and two 60-bit special
-    primes (420 bits at L = 5, within the 438-bit budget)."""
+    primes (420 bits at L = 5, within the 438-bit budget; +25.2 bits of
+    noise margin at the output of the oracle's full-size run, against +24.2
+    with one-prime digits).  The parameter set bench.py times."""
     return ParamSet(f"mnist_grouped_n16384_L{L}", 16384, Q60[:L + 2], L, 2, T30[:3], alpha=2)
 
 
@@ -255,6 +256,8 @@ def _ceil_log2(k: int) -> int:
 MNIST_HOIST = (3, 3, 3)
 LOLA_DENSE_HOIST = (3, 3, 3)
 DENSE64_HOIST = 3
+HEAD_HOIST = 3
+CIFAR_HOIST = (3, 3, 3)
 
 # Ciphertext primes kept after each square of the MNIST-shaped network at
 # L = 5: the oracle's exact noise measurement (full network, n = 16384)
@@ -420,12 +423,18 @@ def cifar_place_targets(maps: int, per_map: int, n: int) -> list:
     return T
 
 
-def layers_cifar(net: CifarNet, n: int, dense2: np.ndarray | None = None, levels=None) -> list:
+def layers_cifar(net: CifarNet, n: int, dense2: np.ndarray | None = None, levels=None, hoist=1,
+                 support_sum: bool = False) -> list:
     """Sec. 6.2: convolution row-major on the convolution representation
     (C*k1*k1 messages), the maps combined into one message, square, the
     second convolution as dense row-major (sparse output), sparse -> dense by
     masks and additions (column-major with the identity), square, dense
-    row-major.  levels = (L1, L2): modulus switching after the two squares."""
+    row-major.  levels = (L1, L2): modulus switching after the two squares.
+    hoist: rotate-and-sum doubling steps per key switch in the two row-major
+    products (an int, or a 3-tuple whose last two entries are used, as in
+    layers_mnist); support_sum: the last product summed over the occupied
+    slots of its dense input (output o at one slot of message o)."""
+    _, h2, h3 = _hoist3(hoist)
     maps1 = net.w1.shape[0]
     per = net.o1 * net.o1
     D2 = cifar_dense2(net) if dense2 is None else dense2
@@ -434,21 +443,23 @@ def layers_cifar(net: CifarNet, n: int, dense2: np.ndarray | None = None, levels
         {"op": "conv", "weights": net.w1},
         {"op": "place", "weights": np.array([cifar_place_targets(maps1, per, n)], dtype=np.int64)},
         {"op": "square"},
-        {"op": "dense_rowmajor", "weights": D2},
+        _with_hoist({"op": "dense_rowmajor", "weights": D2}, h2),
         {"op": "sparse_colmajor", "weights": np.eye(k2, dtype=np.int64)},
         {"op": "square"},
-        {"op": "dense_rowmajor", "weights": net.w3},
+        _with_hoist({"op": "interleaved_rowmajor_support" if support_sum else "dense_rowmajor",
+                     "weights": net.w3}, h3),
     ], [2, 5], levels)
 
 
-def layers_head(Wh: np.ndarray, n: int) -> list:
+def layers_head(Wh: np.ndarray, n: int, hoist: int = 1) -> list:
     """Sec. 5 transfer-learning head as stacked row-major: dense input
-    stacked n / 2^d times, then rounds of stacked row-major products."""
+    stacked n / 2^d times, then rounds of stacked row-major products.
+    hoist: rotate-and-sum doubling steps per key switch."""
     d = _ceil_log2(Wh.shape[1])
     copies = n >> d
     return [
-        {"op": "stack", "d": d, "copies": copies},
-        {"op": "stacked_rowmajor", "weights": Wh, "d": d, "copies": copies},
+        _with_hoist({"op": "stack", "d": d, "copies": copies}, hoist),
+        _with_hoist({"op": "stacked_rowmajor", "weights": Wh, "d": d, "copies": copies}, hoist),
     ]
 
 
