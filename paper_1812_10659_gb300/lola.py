@@ -29,7 +29,7 @@ LAYER = {"conv": 1, "combine": 2, "square": 3, "stack": 4, "stacked_rowmajor": 5
 # representation each layer consumes / produces (0 = not checked)
 LAYER_REPR = {"conv": (5, 1), "combine": (1, 1), "square": (0, 0), "stack": (1, 3),
               "stacked_rowmajor": (3, 4), "interleaved_rowmajor": (4, 2), "dense_rowmajor": (1, 2),
-              "interleaved_rowmajor_support": (4, 1),
+              "interleaved_rowmajor_support": (0, 1),   # interleaved or dense input (checked by the library)
               "sparse_colmajor": (2, 1), "masked_shifts": (1, 5), "place": (1, 1), "mod_switch": (0, 0)}
 
 
