@@ -4,6 +4,8 @@
 // is its limb index in the ciphertext basis.  All kernels are grid-stride
 // loops over words (or over coefficient positions for the basis
 // conversions, which need every limb of one coefficient at once).
+#include <type_traits>
+
 #include "internal.h"
 #include "kernels.h"
 #include "mac.cuh"
@@ -344,35 +346,60 @@ __global__ void ke_mul_plain_multi(const CtxDev* __restrict__ C, const uint64_t*
 
 // convolution row-major: out[m][b][t] = sum_r w[r][t][j][m] in[r][b][t]
 // in: [R][B][kt][2][L][n]; w, ws: [R][kt][L][maps] scalars (Shoup).  A
-// thread accumulates MB maps for one input word, so every input word is
-// read once per block of MB maps.
-template <int MB>
+// thread accumulates MB maps for WPT adjacent input words (one 8- or 16-byte
+// load per input), so every input word is read once per block of MB maps
+// and each weight load serves WPT words.
+#ifndef LOLA_MAC_WPT
+#define LOLA_MAC_WPT 2
+#endif
+template <int MB, int WPT>
 __global__ void ke_mac_scalar(const CtxDev* __restrict__ C, const uint64_t* in, uint32_t R, const uint64_t* w,
                               const uint64_t* ws, uint64_t* out, uint32_t maps, uint32_t B) {
+  using VecT = typename std::conditional<WPT == 2, ulonglong2, unsigned long long>::type;
   const int L = C->L, logn = C->logn, kt = C->kt;
   const size_t n = C->n;
   const size_t ctw = 2 * (size_t)L * n;
   const size_t per_msg = (size_t)B * kt * ctw;
-  const size_t total = (size_t)((maps + MB - 1) / MB) * per_msg;
+  const size_t per_thr = per_msg / WPT;
+  const size_t total = (size_t)((maps + MB - 1) / MB) * per_thr;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-    const uint32_t m0 = (uint32_t)(i / per_msg) * MB;
-    const size_t off = i % per_msg;
+    const uint32_t m0 = (uint32_t)(i / per_thr) * MB;
+    const size_t off = (i % per_thr) * WPT;
     const int j = (off >> logn) % L;
     const int t = (off / ctw) % kt;
     const uint64_t q = C->pr[j].q;
-    uint64_t acc[MB];
+    uint64_t acc[MB][WPT];
 #pragma unroll
-    for (int mm = 0; mm < MB; ++mm) acc[mm] = 0;
+    for (int mm = 0; mm < MB; ++mm)
+#pragma unroll
+      for (int e = 0; e < WPT; ++e) acc[mm][e] = 0;
     for (uint32_t r = 0; r < R; ++r) {
-      const uint64_t x = in[r * per_msg + off];
+      const VecT xv = *(const VecT*)(in + r * per_msg + off);
+      uint64_t x[WPT];
+      if constexpr (WPT == 2) {
+        x[0] = xv.x;
+        x[1] = xv.y;
+      } else {
+        x[0] = xv;
+      }
       const size_t wb = (((size_t)r * kt + t) * L + j) * maps + m0;
 #pragma unroll
       for (int mm = 0; mm < MB; ++mm)
-        if (m0 + mm < maps) acc[mm] = add_mod(acc[mm], shoup_mul(x, __ldg(w + wb + mm), __ldg(ws + wb + mm), q), q);
+        if (m0 + mm < maps) {
+          const uint64_t wv = __ldg(w + wb + mm), wsv = __ldg(ws + wb + mm);
+#pragma unroll
+          for (int e = 0; e < WPT; ++e) acc[mm][e] = add_mod(acc[mm][e], shoup_mul(x[e], wv, wsv, q), q);
+        }
     }
 #pragma unroll
     for (int mm = 0; mm < MB; ++mm)
-      if (m0 + mm < maps) out[(m0 + mm) * per_msg + off] = acc[mm];
+      if (m0 + mm < maps) {
+        if constexpr (WPT == 2) {
+          *(ulonglong2*)(out + (m0 + mm) * per_msg + off) = make_ulonglong2(acc[mm][0], acc[mm][1]);
+        } else {
+          out[(m0 + mm) * per_msg + off] = acc[mm][0];
+        }
+      }
   }
 }
 
@@ -699,12 +726,13 @@ int mac_scalar(Ctx* c, const uint64_t* in, uint32_t R, const uint64_t* w, const 
   const size_t per_msg = (size_t)B * c->kt * c->ct_words();
   if (!maps || !per_msg) return LOLA_OK;
   ProfScope ps_(c, KI_MAC_SCALAR, s, (uint64_t)maps * per_msg);   // units: output words
+  constexpr int WPT = LOLA_MAC_WPT;        // n is a power of two >= 16, so WPT divides every limb
   if (maps <= 4) {
-    const size_t items = per_msg * ((maps + 3) / 4);
-    ke_mac_scalar<4><<<grid_for(items, 256), 256, 0, s>>>(c->dev, in, R, w, ws, out, maps, B);
+    const size_t items = per_msg / WPT * ((maps + 3) / 4);
+    ke_mac_scalar<4, WPT><<<grid_for(items, 256), 256, 0, s>>>(c->dev, in, R, w, ws, out, maps, B);
   } else {
-    const size_t items = per_msg * ((maps + 7) / 8);
-    ke_mac_scalar<8><<<grid_for(items, 256), 256, 0, s>>>(c->dev, in, R, w, ws, out, maps, B);
+    const size_t items = per_msg / WPT * ((maps + 7) / 8);
+    ke_mac_scalar<8, WPT><<<grid_for(items, 256), 256, 0, s>>>(c->dev, in, R, w, ws, out, maps, B);
   }
   return post(c);
 }
