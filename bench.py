@@ -6,9 +6,10 @@ combine, square, stack, stacked row-major dense, square, interleaved
 row-major dense summed over the occupied slots; per CRT residue 154
 rotations taken as 70 key switches, up to three doubling steps of each
 rotate-and-sum per key switch, and 2 squares; 3 residues) on B encrypted
-synthetic 28x28 images whose ciphertexts are already resident in HBM.
---paper-last-layer --hoist 1 runs the paper's plan (224 rotations, one key
-switch each).  The ciphertexts start with five primes and are
+synthetic 28x28 images whose ciphertexts are already resident in HBM, with
+key-switching digits of two primes and two special primes.
+--paper-last-layer --hoist 1 --one-prime-digits runs the paper's plan (224
+rotations, one key switch each) on one-prime digits.  The ciphertexts start with five primes and are
 modulus-switched to four after the first square and to two after the second
 (the same decrypted outputs; --no-mod-switch keeps five throughout).
 Reported beside it:
