@@ -85,6 +85,8 @@ def parse():
     ap.add_argument("--profile-steps", type=int, default=1)
     ap.add_argument("--mode", choices=["network", "serve", "primitives"], default="network")
     ap.add_argument("--n", type=int, default=16384, help="primitives mode: ring degree")
+    ap.add_argument("--two-prime-digits", action="store_true",
+                    help="primitives mode: key-switching digits of two primes with two special primes")
     ap.add_argument("--sweep", action="store_true",
                     help="primitives mode: the grid B = 1..256 x n in {8192, 16384} x L = 4..8")
     ap.add_argument("--rates", default="25,100,200", help="serve mode: Poisson arrival rates (requests/s)")
@@ -1107,7 +1109,7 @@ def run_primitives(args):
     summary = []
     alu = None
     for n, Lq, batches in grid:
-        ps = W.params_sweep(n, Lq)
+        ps = W.params_sweep(n, Lq, 2 if args.two_prime_digits else 1)
         ctx = L.lola_ctx_create(ps.n, ps.q, ps.L, ps.K, ps.t, alpha=ps.alpha)
         if not args.no_autotune:
             L.lola_autotune(ctx)
@@ -1117,10 +1119,11 @@ def run_primitives(args):
         sk, ev = L.lola_keygen(ctx, 11, pool, L.LOLA_KEY_RELIN)
         for B in batches:
             res = primitives_case(L, ctx, ps, ev, pool, B, args, alu)
-            line = {"mode": "primitives", "n": n, "L": Lq, "K": ps.K, "batch": B, "steps": args.steps,
+            line = {"mode": "primitives", "n": n, "L": Lq, "K": ps.K, "key_switch_digit_primes": ps.alpha,
+                    "batch": B, "steps": args.steps,
                     "data": "synthetic uniform residues, random rotation steps",
                     "security": ("128-bit (HE standard: log2 QP <= 218 at n = 8192, 438 at n = 16384)"
-                                 if (Lq + 1) * 60 <= {8192: 218, 16384: 438}.get(n, 0) else
+                                 if (Lq + ps.K) * 60 <= {8192: 218, 16384: 438}.get(n, 0) else
                                  "below 128-bit (kernel sweep only)"),
                     "alu_peak_gbutterfly_s": {"fwd": alu["fwd_butterfly"] / 1e9, "inv": alu["inv_butterfly"] / 1e9,
                                               "source": "measured (lola_alu_rate)"},

@@ -97,10 +97,12 @@ def params_head(L: int = 3) -> ParamSet:
     return ParamSet(f"head_n16384_L{L}", 16384, Q60[:L + 1], L, 1, T30[:1])
 
 
-def params_sweep(n: int, L: int) -> ParamSet:
+def params_sweep(n: int, L: int, alpha: int = 1) -> ParamSet:
     """Batched primitive sweep: n in {8192, 16384}, L in 4..8 primes of 60
-    bits plus a special prime (security not considered: random residues)."""
-    return ParamSet(f"sweep_n{n}_L{L}", n, Q60[:L + 1], L, 1, T30[:1])
+    bits plus a special prime, or two with key-switching digits of two primes
+    (alpha = 2); security not considered: random residues."""
+    K = 2 if alpha == 2 else 1
+    return ParamSet(f"sweep_n{n}_L{L}_a{alpha}", n, Q60[:L + K], L, K, T30[:1], alpha)
 
 
 def params_small(n: int, L: int = 3, K: int = 1, t=None, alpha: int = 1) -> ParamSet:
