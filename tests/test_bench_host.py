@@ -149,3 +149,16 @@ def test_plan_counts_of_the_hoisted_mnist_plan():
     # row swap], 7 rounds of [1, 2, 4 | 8, 16, 32 | 64, 128, 256 | 512]
     c = bench.plan_counts("mnist", 5, W.MNIST_LEVELS, False, (3, 3, 3))
     assert {lv: (d["rot"], d["rot_sum"]) for lv, d in c.items()} == {5: (4, {}), 4: (14, {7: 22}), 2: (10, {7: 20})}
+
+
+def test_plan_counts_of_the_hoisted_head_and_cifar_plans():
+    # head: stack [4096 | row swap] and 26 rounds of [1, 2, 4 | ... | 512, 1024, 2048],
+    # 25 round shifts -> 27 single rotations and 26 x 4 rotate-sums of 7;
+    # CIFAR: 4075 outputs of [1, 2, 4 | ... | 512, 1024, 2048 | 4096 | row swap] at 4 primes
+    # (4 rotate-sums, then the last shift and the row swap alone) and the last product's 10
+    # outputs summed over 4075 slots ([1, 2, 4 | ... | 512, 1024, 2048]: 4 rotate-sums) at 2
+    c = bench.plan_counts("head", 3, None, False, (3, 3, 3))
+    assert {lv: (d["rot"], d["rot_sum"]) for lv, d in c.items()} == {3: (27, {7: 104})}
+    c = bench.plan_counts("cifar", 6, W.CIFAR_LEVELS, False, (3, 3, 3))
+    assert {lv: (d["rot"], d["rot_sum"]) for lv, d in c.items()} == {6: (83, {}), 4: (8150, {7: 16300}),
+                                                                     2: (0, {7: 40})}
